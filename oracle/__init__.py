@@ -1,0 +1,301 @@
+"""ctypes wrapper of the FP64 CPU oracle (test infrastructure only).
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import
+this package. The planner library never imports or links it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import functools
+from typing import Dict, List
+
+import numpy as np
+
+from . import build as _build
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+_U8 = C.POINTER(C.c_ubyte)
+
+
+class OrcProblem(C.Structure):
+    _fields_ = [("dof", C.c_int), ("arm", C.c_int), ("dh", _D), ("qlo", _D), ("qhi", _D),
+                ("n_sph", C.c_int), ("sph", _D), ("vmax", C.c_double), ("n_obs", C.c_int),
+                ("n_way", C.c_int), ("obs_r", _D), ("way", _D), ("qs", _D), ("qg", _D)]
+
+
+class OrcParams(C.Structure):
+    _fields_ = [("variant", C.c_int), ("n_roots", C.c_int), ("workers", C.c_int),
+                ("max_iters", C.c_int), ("eta", C.c_double), ("res", C.c_double),
+                ("dt", C.c_double), ("p_new", C.c_double), ("p_guided", C.c_double),
+                ("H", C.c_double), ("seed", C.c_ulonglong), ("problem_id", C.c_uint),
+                ("flag_tol", C.c_double), ("flag_clear", C.c_double)]
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+@functools.lru_cache(maxsize=1)
+def lib():
+    path = _build.build()
+    L = C.CDLL(path)
+    L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint), C.POINTER(C.c_uint), C.POINTER(C.c_uint)]
+    L.orc_fk.argtypes = [C.POINTER(OrcProblem), _D, _D, _D, _D]
+    L.orc_obstacle_position.argtypes = [C.POINTER(OrcProblem), C.c_int, C.c_double, _D]
+    L.orc_state_free.argtypes = [C.POINTER(OrcProblem), _D, C.c_double, _D]
+    L.orc_state_free.restype = C.c_int
+    L.orc_check_edges.argtypes = [C.POINTER(OrcProblem), C.c_int, _D, _D, _D, _D, C.c_double, _U8,
+                                  _D, _I, _D]
+    L.orc_interval_partition.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_double,
+                                         C.c_long, C.c_int, _U8, _D, _D, _D, C.c_int]
+    L.orc_interval_partition.restype = C.c_int
+    L.orc_interval_sample.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_double,
+                                      C.c_long, C.c_int, _U8, C.c_int, C.c_double, C.c_double,
+                                      C.c_double, _I]
+    L.orc_interval_sample.restype = C.c_double
+    L.orc_recycle_update.argtypes = [C.c_int, _D, _I, _I, _I, C.c_double, C.c_long, C.c_int, _U8,
+                                     C.c_double]
+    L.orc_recycle_update.restype = C.c_int
+    L.orc_plan.argtypes = [C.POINTER(OrcProblem), C.POINTER(OrcParams), C.POINTER(C.c_void_p)]
+    L.orc_plan.restype = C.c_int
+    L.orc_result_summary.argtypes = [C.c_void_p, _D]
+    L.orc_result_path.argtypes = [C.c_void_p, _D]
+    L.orc_result_arena_size.argtypes = [C.c_void_p, C.c_int]
+    L.orc_result_arena_size.restype = C.c_int
+    L.orc_result_arena.argtypes = [C.c_void_p, C.c_int, _D, _I, _D, _D, _I, _I]
+    L.orc_result_history.argtypes = [C.c_void_p, _D, _D, _D]
+    L.orc_nn_spacetime.argtypes = [C.c_int, C.c_int, _D, _D, C.c_int, C.c_double, _D, C.c_double,
+                                   C.c_int, C.c_double, _D]
+    L.orc_nn_spacetime.restype = C.c_int
+    L.orc_result_margin_types.argtypes = [C.c_void_p, _D]
+    L.orc_result_slots.argtypes = [C.c_void_p, _D, _I, _I, _I]
+    L.orc_result_trees.argtypes = [C.c_void_p, _I, _D]
+    L.orc_result_goal_grid.argtypes = [C.c_void_p, C.POINTER(C.c_long), _D, C.c_int]
+    L.orc_result_goal_grid.restype = C.c_int
+    L.orc_result_incumbent.argtypes = [C.c_void_p, _I, _I, _I]
+    L.orc_result_free.argtypes = [C.c_void_p]
+    return L
+
+
+class _ProblemHandle:
+    """Keeps the numpy buffers alive for an OrcProblem struct."""
+
+    def __init__(self, prob):
+        self.bufs = []
+
+        def keep(a):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            self.bufs.append(a)
+            return _dptr(a)
+
+        dh = prob.dh if prob.dh is not None else np.zeros((prob.dof, 4))
+        self.s = OrcProblem(prob.dof, 1 if prob.arm else 0, keep(dh), keep(prob.qlo), keep(prob.qhi),
+                            len(prob.spheres), keep(prob.spheres), float(prob.vmax),
+                            len(prob.obs_r), prob.way.shape[1], keep(prob.obs_r), keep(prob.way),
+                            keep(prob.qs), keep(prob.qg))
+
+    @property
+    def ref(self):
+        return C.byref(self.s)
+
+
+def philox(ctr, key) -> np.ndarray:
+    c = (C.c_uint * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (C.c_uint * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (C.c_uint * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return np.array(list(o), dtype=np.uint32)
+
+
+def fk(prob, q):
+    h = _ProblemHandle(prob)
+    S = len(prob.spheres)
+    nf = prob.dof + 1 if prob.arm else 1
+    cen = np.zeros((S, 3))
+    org = np.zeros((nf, 3))
+    rot = np.zeros((nf, 9))
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    lib().orc_fk(h.ref, _dptr(q), _dptr(cen), _dptr(org), _dptr(rot))
+    return cen, org, rot.reshape(nf, 3, 3)
+
+
+def obstacle_position(prob, m, t):
+    h = _ProblemHandle(prob)
+    o = np.zeros(3)
+    lib().orc_obstacle_position(h.ref, int(m), float(t), _dptr(o))
+    return o
+
+
+def state_free(prob, q, t):
+    h = _ProblemHandle(prob)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    clr = C.c_double()
+    ok = lib().orc_state_free(h.ref, _dptr(q), float(t), C.byref(clr))
+    return bool(ok), clr.value
+
+
+def check_edges(prob, qa, ta, qb, tb, res):
+    """FP64 verdicts (1 = free), clearance, check-point count and the distance
+    of the check-count argument from an integer, for a batch of edges."""
+    h = _ProblemHandle(prob)
+    qa = np.ascontiguousarray(qa, dtype=np.float64)
+    qb = np.ascontiguousarray(qb, dtype=np.float64)
+    ta = np.ascontiguousarray(ta, dtype=np.float64)
+    tb = np.ascontiguousarray(tb, dtype=np.float64)
+    n = len(ta)
+    v = np.zeros(n, dtype=np.uint8)
+    clr = np.zeros(n)
+    nc = np.zeros(n, dtype=np.int32)
+    im = np.zeros(n)
+    lib().orc_check_edges(h.ref, n, _dptr(qa), _dptr(ta), _dptr(qb), _dptr(tb), float(res),
+                          v.ctypes.data_as(_U8), _dptr(clr), nc.ctypes.data_as(_I), _dptr(im))
+    return v, clr, nc, im
+
+
+def nn_spacetime(x, qr, tr, sigma, vmax, troot=None, U=float("inf")):
+    """Index of argmin rho_sigma over nodes x [n][d+1] (or -1) and the value."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n, d1 = x.shape
+    qr = np.ascontiguousarray(qr, dtype=np.float64)
+    tro = np.ascontiguousarray(troot if troot is not None else np.zeros(n), dtype=np.float64)
+    rho = C.c_double()
+    i = lib().orc_nn_spacetime(n, d1 - 1, _dptr(x), _dptr(tro), 1 if troot is not None else 0, float(U),
+                               _dptr(qr), float(tr), int(sigma), float(vmax), C.byref(rho))
+    return i, rho.value
+
+
+def interval_partition(Lg, H, dt, N, U, kmin, free_flags):
+    f = np.ascontiguousarray(free_flags, dtype=np.uint8)
+    uni = np.zeros(N)
+    w = C.c_double()
+    cap = len(f) + N + 4
+    pcs = np.zeros((cap, 3))
+    n = lib().orc_interval_partition(float(Lg), float(H), float(dt), int(N), float(U), int(kmin), len(f),
+                                     f.ctypes.data_as(_U8), _dptr(uni), C.byref(w), _dptr(pcs), cap)
+    return uni, w.value, pcs[:n]
+
+
+def interval_sample(Lg, H, dt, N, U, kmin, free_flags, group, u_coin, u_pos, p_guided):
+    f = np.ascontiguousarray(free_flags, dtype=np.uint8)
+    g = C.c_int()
+    T = lib().orc_interval_sample(float(Lg), float(H), float(dt), int(N), float(U), int(kmin), len(f),
+                                  f.ctypes.data_as(_U8), int(group), float(u_coin), float(u_pos),
+                                  float(p_guided), C.byref(g))
+    return T, bool(g.value)
+
+
+def recycle_update(T, has_root, active, gen, U, kmin, free_flags, dt):
+    T = np.array(T, dtype=np.float64)
+    hr = np.array(has_root, dtype=np.int32)
+    ac = np.array(active, dtype=np.int32)
+    gn = np.array(gen, dtype=np.int32)
+    f = np.ascontiguousarray(free_flags, dtype=np.uint8)
+    n = lib().orc_recycle_update(len(T), _dptr(T), hr.ctypes.data_as(_I), ac.ctypes.data_as(_I),
+                                 gn.ctypes.data_as(_I), float(U), int(kmin), len(f),
+                                 f.ctypes.data_as(_U8), float(dt))
+    return T, hr, ac, gn, n
+
+
+@dataclasses.dataclass
+class Arena:
+    x: np.ndarray       # [n][dof+1]  (q..., t)
+    parent: np.ndarray  # [n]
+    troot: np.ndarray
+    cost: np.ndarray
+    tree: np.ndarray
+    iter: np.ndarray
+
+
+@dataclasses.dataclass
+class PlanResult:
+    U: float
+    C: float
+    iters: int
+    first_iter: int
+    ext_checked: int
+    bridge_checked: int
+    root_checked: int
+    inserted: int
+    path: np.ndarray
+    status: int
+    fwd: Arena
+    seg: List[Arena]
+    U_hist: np.ndarray
+    margin_hist: np.ndarray
+    clear_hist: np.ndarray
+    margin_types: np.ndarray  # [iters][6] nn, count, interval, bounds, rank, clearance
+    slots: Dict[str, np.ndarray]
+    trees: Dict[str, np.ndarray]
+    incumbent: tuple
+    goal_kmin: int
+    goal_clearance: np.ndarray
+
+
+def make_params(params, **over) -> OrcParams:
+    p = dataclasses.replace(params, **over) if over else params
+    return OrcParams(p.variant, p.n_roots, p.workers, p.max_iters, p.eta, p.res, p.dt, p.p_new,
+                     p.p_guided, p.H, p.seed, p.problem_id, 0.0, 0.0)
+
+
+def plan(prob, params, **over) -> PlanResult:
+    L = lib()
+    h = _ProblemHandle(prob)
+    prm = make_params(params, **over)
+    handle = C.c_void_p()
+    L.orc_plan(h.ref, C.byref(prm), C.byref(handle))
+    try:
+        s = np.zeros(12)
+        L.orc_result_summary(handle, _dptr(s))
+        d = prob.dof
+        plen = int(s[8])
+        path = np.zeros((plen, d + 1))
+        if plen:
+            L.orc_result_path(handle, _dptr(path))
+
+        def arena(i):
+            n = L.orc_result_arena_size(handle, i)
+            x = np.zeros((n, d + 1))
+            par = np.zeros(n, dtype=np.int32)
+            tr = np.zeros(n)
+            co = np.zeros(n)
+            tree = np.zeros(n, dtype=np.int32)
+            it = np.zeros(n, dtype=np.int32)
+            if n:
+                L.orc_result_arena(handle, i, _dptr(x), par.ctypes.data_as(_I), _dptr(tr), _dptr(co),
+                                   tree.ctypes.data_as(_I), it.ctypes.data_as(_I))
+            return Arena(x, par, tr, co, tree, it)
+
+        iters = int(s[2])
+        Uh = np.zeros(iters)
+        Mh = np.zeros(iters)
+        Ch = np.zeros(iters)
+        MT = np.zeros((iters, 6))
+        if iters:
+            L.orc_result_history(handle, _dptr(Uh), _dptr(Mh), _dptr(Ch))
+            L.orc_result_margin_types(handle, _dptr(MT))
+        N = prm.n_roots
+        sl = {"T": np.zeros(N), "has_root": np.zeros(N, dtype=np.int32),
+              "active": np.zeros(N, dtype=np.int32), "gen": np.zeros(N, dtype=np.int32)}
+        if prm.variant == 1:
+            L.orc_result_slots(handle, _dptr(sl["T"]), sl["has_root"].ctypes.data_as(_I),
+                               sl["active"].ctypes.data_as(_I), sl["gen"].ctypes.data_as(_I))
+        nt = int(s[10])
+        tr = {"group": np.zeros(nt, dtype=np.int32), "T": np.zeros(nt)}
+        if nt:
+            L.orc_result_trees(handle, tr["group"].ctypes.data_as(_I), _dptr(tr["T"]))
+        f, sg, b = C.c_int(), C.c_int(), C.c_int()
+        L.orc_result_incumbent(handle, C.byref(f), C.byref(sg), C.byref(b))
+        kmin = C.c_long()
+        gcap = 1 << 20
+        gcl = np.zeros(gcap)
+        ng = L.orc_result_goal_grid(handle, C.byref(kmin), _dptr(gcl), gcap)
+        return PlanResult(U=s[0], C=s[1], iters=iters, first_iter=int(s[3]), ext_checked=int(s[4]),
+                          bridge_checked=int(s[5]), root_checked=int(s[6]), inserted=int(s[7]),
+                          path=path, status=int(s[11]), fwd=arena(-1),
+                          seg=[arena(i) for i in range(N)], U_hist=Uh, margin_hist=Mh, clear_hist=Ch,
+                          margin_types=MT, slots=sl, trees=tr, incumbent=(f.value, sg.value, b.value),
+                          goal_kmin=kmin.value, goal_clearance=gcl[:ng].copy())
+    finally:
+        L.orc_result_free(handle)

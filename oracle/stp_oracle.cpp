@@ -1,0 +1,1351 @@
+// ST-pRRTC oracle: plain, slow, single-threaded FP64 CPU restatement of the
+// batch-synchronous space-time Extend loop (Sec. "Space-Time pRRTC": interval
+// root, Algorithms 1-2, Eqs. goal-time-lower-bound, conditional-query-time,
+// space-time-metric; Sec. "Practical Root Recycling": Algorithm 3,
+// Eq. max-speed-extension; problem model of Sec. "Problem Formulation").
+//
+// TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and bench.py's
+// CPU-baseline leg may load this library. It shares no code, header, table or
+// constant with the CUDA path; the CUDA library must never call it.
+//
+// Floating point is double throughout. The file is compiled with
+// -ffp-contract=off so that x86 and Arm hosts round identically.
+//
+// Readings of points the paper leaves open are marked "Reading:" in comments.
+// Philox4x32-10 follows its published definition (Salmon, Moraes, Dror, Shaw,
+// "Parallel random numbers: as easy as 1, 2, 3", SC'11).
+//
+// Parity status: every function here is pinned by tests/test_oracle_*.py
+// (worked examples of Figs. interval-root and method, closed forms, brute force,
+// invariants); end-to-end success rates and arrival values of the synthetic
+// workloads are parity unpinned (the paper's suites are not available).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+namespace {
+
+const double kInf = std::numeric_limits<double>::infinity();
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (SC'11). Counter (c0,c1,c2,c3), key (k0,k1).
+// ---------------------------------------------------------------------------
+const uint32_t kPhiloxM0 = 0xD2511F53u;
+const uint32_t kPhiloxM1 = 0xCD9E8D57u;
+const uint32_t kPhiloxW0 = 0x9E3779B9u;
+const uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += kPhiloxW0;
+            k1 += kPhiloxW1;
+        }
+        uint64_t p0 = (uint64_t)kPhiloxM0 * (uint64_t)c[0];
+        uint64_t p1 = (uint64_t)kPhiloxM1 * (uint64_t)c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0;
+        uint32_t n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+    for (int i = 0; i < 4; ++i) out[i] = c[i];
+}
+
+// Reading (RNG unnamed in the paper): per (problem p, iteration k, worker w)
+// the draws are slots s = 0,1,2,...: slot s is word s%4 of the Philox block with
+// counter (s/4, w, k, p) and key (seed lo, seed hi).
+// Slot map: 0 group, 1 guided coin, 2 T position, 3 new-root coin,
+// 4..4+d-1 configuration sample q_r, 4+d query time t_r.
+struct Draws {
+    uint32_t raw[16];
+    void fill(uint64_t seed, uint32_t problem, uint32_t iter, uint32_t worker, int nslots) {
+        uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        for (int b = 0; b * 4 < nslots; ++b) {
+            uint32_t ctr[4] = {(uint32_t)b, worker, iter, problem};
+            philox4x32_10(ctr, key, &raw[4 * b]);
+        }
+    }
+    // u = (x >> 8) * 2^-24, exactly representable in single and double.
+    double u(int slot) const { return (double)(raw[slot] >> 8) * (1.0 / 16777216.0); }
+    // group index floor(u * N) evaluated exactly in integers.
+    int group(int slot, int n) const {
+        return (int)(((uint64_t)(raw[slot] >> 8) * (uint64_t)n) >> 24);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Problem model (Sec. "Problem Formulation"): C subset of R^d with Euclidean
+// metric, velocity bound v_max, horizon [0,H], known obstacle trajectories.
+// ---------------------------------------------------------------------------
+struct Problem {
+    int dof = 0;
+    bool arm = false;              // false: point robot (translation only)
+    std::vector<double> dh;        // [dof][4] a, alpha, d, theta0 (standard DH)
+    std::vector<double> qlo, qhi;  // [dof]
+    std::vector<int> sph_link;     // [S] frame index 0..dof
+    std::vector<double> sph_p;     // [S][3] local centre
+    std::vector<double> sph_r;     // [S]
+    double vmax = 1.0;
+    int n_obs = 0, n_way = 0;
+    std::vector<double> obs_r;     // [M]
+    std::vector<double> way;       // [M][K][4] t, x, y, z
+    std::vector<double> qs, qg;    // [dof]
+};
+
+double dist(const double* a, const double* b, int d) {
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double e = b[j] - a[j];
+        s += e * e;
+    }
+    return std::sqrt(s);
+}
+
+// A rigid frame: rotation R (row-major 3x3) and origin o.
+struct Frame {
+    double R[9];
+    double o[3];
+};
+
+// Standard DH link transform A = Rz(theta) Tz(d) Tx(a) Rx(alpha).
+Frame dh_transform(double a, double alpha, double d, double theta) {
+    double ct = std::cos(theta), st = std::sin(theta);
+    double ca = std::cos(alpha), sa = std::sin(alpha);
+    Frame f;
+    f.R[0] = ct; f.R[1] = -st * ca; f.R[2] = st * sa;
+    f.R[3] = st; f.R[4] = ct * ca;  f.R[5] = -ct * sa;
+    f.R[6] = 0;  f.R[7] = sa;       f.R[8] = ca;
+    f.o[0] = a * ct;
+    f.o[1] = a * st;
+    f.o[2] = d;
+    return f;
+}
+
+Frame compose(const Frame& A, const Frame& B) {
+    Frame C;
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A.R[3 * i + k] * B.R[3 * k + j];
+            C.R[3 * i + j] = s;
+        }
+        double s = A.o[i];
+        for (int k = 0; k < 3; ++k) s += A.R[3 * i + k] * B.o[k];
+        C.o[i] = s;
+    }
+    return C;
+}
+
+// Frames 0..dof. Frame 0 is the base. For the point robot, frame 0 is the
+// identity rotation placed at (q0, q1, q2) (missing coordinates are 0) and the
+// configuration is a position in the plane or space.
+void forward_kinematics(const Problem& P, const double* q, std::vector<Frame>& frames) {
+    Frame base;
+    for (int i = 0; i < 9; ++i) base.R[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    base.o[0] = base.o[1] = base.o[2] = 0.0;
+    frames.assign(1, base);
+    if (!P.arm) {
+        for (int j = 0; j < 3 && j < P.dof; ++j) frames[0].o[j] = q[j];
+        return;
+    }
+    for (int j = 0; j < P.dof; ++j) {
+        const double* row = &P.dh[4 * j];
+        Frame A = dh_transform(row[0], row[1], row[2], row[3] + q[j]);
+        frames.push_back(compose(frames.back(), A));
+    }
+}
+
+void sphere_centres(const Problem& P, const std::vector<Frame>& frames, std::vector<double>& c) {
+    int S = (int)P.sph_r.size();
+    c.assign(3 * S, 0.0);
+    for (int s = 0; s < S; ++s) {
+        const Frame& F = frames[P.sph_link[s]];
+        const double* p = &P.sph_p[3 * s];
+        for (int i = 0; i < 3; ++i) {
+            double v = F.o[i];
+            for (int k = 0; k < 3; ++k) v += F.R[3 * i + k] * p[k];
+            c[3 * s + i] = v;
+        }
+    }
+}
+
+// Obstacle position at absolute time t: piecewise-linear interpolation of the
+// waypoints (Sec. "Simulation Protocol": positions interpolated at each
+// absolute query time). Reading: before the first / after the last waypoint the
+// obstacle holds that waypoint.
+void obstacle_position(const Problem& P, int m, double t, double out[3]) {
+    const double* W = &P.way[(size_t)m * P.n_way * 4];
+    int K = P.n_way;
+    if (t <= W[0]) {
+        for (int i = 0; i < 3; ++i) out[i] = W[1 + i];
+        return;
+    }
+    if (t >= W[4 * (K - 1)]) {
+        for (int i = 0; i < 3; ++i) out[i] = W[4 * (K - 1) + 1 + i];
+        return;
+    }
+    int k = 0;
+    while (!(t < W[4 * (k + 1)])) ++k;  // W[4k] <= t < W[4(k+1)]
+    double t0 = W[4 * k], t1 = W[4 * (k + 1)];
+    double f = (t - t0) / (t1 - t0);
+    for (int i = 0; i < 3; ++i) {
+        double a = W[4 * k + 1 + i], b = W[4 * (k + 1) + 1 + i];
+        out[i] = a + f * (b - a);
+    }
+}
+
+bool in_bounds(const Problem& P, const double* q) {
+    for (int j = 0; j < P.dof; ++j)
+        if (q[j] < P.qlo[j] || q[j] > P.qhi[j]) return false;
+    return true;
+}
+
+// Clearance of state (q,t): min over sphere pairs of |p - o| - r - r_o.
+// Reading (collision predicate): a pair collides iff |p-o|^2 < (r+r_o)^2;
+// touching is free; a configuration outside the bounds collides.
+// Returns true iff collision-free.
+bool state_free(const Problem& P, const double* q, double t, double* clearance) {
+    std::vector<Frame> frames;
+    std::vector<double> c;
+    forward_kinematics(P, q, frames);
+    sphere_centres(P, frames, c);
+    bool free = in_bounds(P, q);
+    double clr = kInf;
+    int S = (int)P.sph_r.size();
+    for (int m = 0; m < P.n_obs; ++m) {
+        double o[3];
+        obstacle_position(P, m, t, o);
+        for (int s = 0; s < S; ++s) {
+            double dx = c[3 * s] - o[0], dy = c[3 * s + 1] - o[1], dz = c[3 * s + 2] - o[2];
+            double d2 = dx * dx + dy * dy + dz * dz;
+            double rr = P.sph_r[s] + P.obs_r[m];
+            if (d2 < rr * rr) free = false;
+            double cl = std::sqrt(d2) - rr;
+            if (cl < clr) clr = cl;
+        }
+    }
+    if (clearance) *clearance = clr;
+    return free;
+}
+
+// Reading (edge resolution): an edge (q_a,t_a)->(q_b,t_b) is checked at
+// c = max(1, ceil(max(D, v_max |t_b - t_a|) / res)) points s_j = j/c,
+// j = 1..c (the start state was validated when it was inserted).
+int edge_check_count(const Problem& P, const double* qa, double ta, const double* qb, double tb,
+                     double res, double* int_margin) {
+    double D = dist(qa, qb, P.dof);
+    double L = std::max(D, P.vmax * std::fabs(tb - ta));
+    double x = L / res;
+    double c = std::ceil(x);
+    if (int_margin) {
+        double fr = x - std::floor(x);
+        *int_margin = std::min(fr, 1.0 - fr);
+    }
+    return std::max(1, (int)c);
+}
+
+// Edge verdict with its FP64 clearance (min over all check points, no early
+// exit) and check-point count.
+bool edge_free(const Problem& P, const double* qa, double ta, const double* qb, double tb, double res,
+               double* clearance, int* nchk, double* int_margin) {
+    int c = edge_check_count(P, qa, ta, qb, tb, res, int_margin);
+    bool free = true;
+    double clr = kInf;
+    std::vector<double> q(P.dof);
+    for (int j = 1; j <= c; ++j) {
+        double s = (double)j / (double)c;
+        for (int i = 0; i < P.dof; ++i) q[i] = qa[i] + s * (qb[i] - qa[i]);
+        double t = ta + s * (tb - ta);
+        double cl;
+        if (!state_free(P, q.data(), t, &cl)) free = false;
+        if (cl < clr) clr = cl;
+    }
+    if (clearance) *clearance = clr;
+    if (nchk) *nchk = c;
+    return free;
+}
+
+// ---------------------------------------------------------------------------
+// Goal-time grid (Eq. goal-time-lower-bound): L_g = D(q_s,q_g)/v_max,
+// k_min = ceil(L_g/dt); goal checks at k dt in [L_g, H].
+// ---------------------------------------------------------------------------
+struct GoalGrid {
+    double Lg = 0, dt = 0, H = 0;
+    long kmin = 0, kmax = 0;        // checks k = kmin..kmax (k dt <= H)
+    std::vector<char> free;         // [kmax - kmin + 1]
+    std::vector<double> clearance;  // [kmax - kmin + 1]
+    bool is_free(long k) const {
+        if (k < kmin || k > kmax) return false;
+        return free[k - kmin] != 0;
+    }
+};
+
+void build_goal_grid(const Problem& P, double H, double dt, GoalGrid& G) {
+    G.Lg = dist(P.qs.data(), P.qg.data(), P.dof) / P.vmax;
+    G.dt = dt;
+    G.H = H;
+    G.kmin = (long)std::ceil(G.Lg / dt);
+    G.kmax = (long)std::floor(H / dt);
+    long n = G.kmax - G.kmin + 1;
+    if (n < 0) n = 0;
+    G.free.assign(n, 0);
+    G.clearance.assign(n, 0.0);
+    for (long i = 0; i < n; ++i) {
+        double t = (double)(G.kmin + i) * dt;
+        double cl;
+        G.free[i] = state_free(P, P.qg.data(), t, &cl) ? 1 : 0;
+        G.clearance[i] = cl;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Interval-root allocation (Sec. "Interval Root").
+// ---------------------------------------------------------------------------
+struct Piece {
+    double lo, hi;
+    int group;
+};
+
+struct IntervalAlloc {
+    double Lg = 0, H = 0, dt = 0;
+    int N = 0;
+    std::vector<std::pair<double, double>> windows;  // guided windows in [L_g, H]
+    double Ubar = 0, width = 0;                      // uniform interval width
+    std::vector<Piece> pieces;                       // time order
+    std::vector<std::vector<int>> group_pieces;      // indices into pieces
+    std::vector<double> group_measure;
+};
+
+// Each collision-free check k marks [k dt - dt/2, k dt + dt/2] clipped to
+// [L_g, H]; adjacent windows merge into guided windows.
+void build_windows(IntervalAlloc& A, long kmin, long kmax, const char* free_flags) {
+    A.windows.clear();
+    long k = kmin;
+    while (k <= kmax) {
+        if (!free_flags[k - kmin]) {
+            ++k;
+            continue;
+        }
+        long k0 = k;
+        while (k + 1 <= kmax && free_flags[k + 1 - kmin]) ++k;
+        double lo = (double)k0 * A.dt - 0.5 * A.dt;
+        double hi = (double)k * A.dt + 0.5 * A.dt;
+        lo = std::max(lo, A.Lg);
+        hi = std::min(hi, A.H);
+        if (hi > lo) A.windows.push_back({lo, hi});
+        ++k;
+    }
+}
+
+// With Ubar = min(H, U): N equal uniform intervals on [L_g, Ubar); the guided
+// windows below Ubar are concatenated in time order (gaps skipped) and group g
+// receives the measure in [g G/N, (g+1) G/N) of the concatenation.
+void partition(IntervalAlloc& A, double U) {
+    A.Ubar = std::min(A.H, U);
+    A.width = (A.Ubar - A.Lg) / (double)A.N;
+    A.pieces.clear();
+    A.group_pieces.assign(A.N, {});
+    A.group_measure.assign(A.N, 0.0);
+    std::vector<std::pair<double, double>> clipped;
+    for (auto& w : A.windows) {
+        if (w.first >= A.Ubar) continue;
+        double hi = std::min(w.second, A.Ubar);
+        if (hi > w.first) clipped.push_back({w.first, hi});
+    }
+    std::vector<double> start_measure(clipped.size());
+    double G = 0.0;
+    for (size_t i = 0; i < clipped.size(); ++i) {
+        start_measure[i] = G;
+        G += clipped[i].second - clipped[i].first;
+    }
+    if (G <= 0.0) return;
+    for (int g = 0; g < A.N; ++g) {
+        double mlo = G * (double)g / (double)A.N;
+        double mhi = (g == A.N - 1) ? G : G * (double)(g + 1) / (double)A.N;
+        for (size_t i = 0; i < clipped.size(); ++i) {
+            double m0 = start_measure[i];
+            double m1 = (i + 1 < clipped.size()) ? start_measure[i + 1] : G;
+            double a = std::max(mlo, m0), b = std::min(mhi, m1);
+            if (b > a) {
+                Piece p;
+                p.lo = clipped[i].first + (a - m0);
+                p.hi = clipped[i].first + (b - m0);
+                p.group = g;
+                A.group_pieces[g].push_back((int)A.pieces.size());
+                A.pieces.push_back(p);
+                A.group_measure[g] += p.hi - p.lo;
+            }
+        }
+    }
+}
+
+// Group i samples T from its guided portions with probability p_guided (falling
+// back to the uniform interval when they are empty), else from I_i.
+double sample_goal_time(const IntervalAlloc& A, int g, double u_coin, double u_pos, double p_guided,
+                        bool* guided) {
+    if (u_coin < p_guided && A.group_measure[g] > 0.0) {
+        *guided = true;
+        double p = u_pos * A.group_measure[g];
+        const std::vector<int>& idx = A.group_pieces[g];
+        for (size_t j = 0; j < idx.size(); ++j) {
+            const Piece& pc = A.pieces[idx[j]];
+            double len = pc.hi - pc.lo;
+            if (p < len || j + 1 == idx.size()) return std::min(pc.lo + p, pc.hi);
+            p -= len;
+        }
+    }
+    *guided = false;
+    double lo = A.Lg + (double)g * A.width;
+    return lo + u_pos * A.width;
+}
+
+// ---------------------------------------------------------------------------
+// Planner state.
+// ---------------------------------------------------------------------------
+struct Node {
+    std::vector<double> q;
+    double t;
+    int parent;    // index in the same arena, -1 for a root
+    double troot;  // backward: root (arrival) time of the tree; forward: 0
+    double cost;   // configuration-space path length to the tree root
+    int tree;      // interval root: backward tree id; root recycling: slot generation
+    int iter;      // iteration that inserted the node (-1: initial roots)
+};
+
+struct Tree {  // interval-root backward tree
+    int group;
+    double T;
+};
+
+struct Slot {  // root-recycling slot
+    bool has_root = false;
+    bool active = false;
+    double T = kInf;
+    long k = -1;  // grid index of T (T = k dt)
+    int gen = 0;
+};
+
+// Root recycling on an incumbent decrease (Algorithm 3): roots with T_i >= U
+// become inactive; slots with T_i > U (and empty slots) are donors. Reading
+// (replacement placement): with K_U grid indices in [L_grid, U) and m donors
+// in slot order, donor j targets index kmin + floor((2j+1) K_U / (2m)) and
+// scans outward, below first, for a free goal check not held by an active root.
+// A donor without a candidate stays inactive. Returns the replaced slots.
+template <class IsFree>
+std::vector<int> recycle_rule(std::vector<Slot>& slots, double U, long kmin, double dt, IsFree is_free) {
+    long kU = kmin;
+    while ((double)kU * dt < U) ++kU;  // first index with k dt >= U
+    std::vector<long> held;
+    std::vector<int> donors, replaced;
+    for (size_t i = 0; i < slots.size(); ++i) {
+        Slot& s = slots[i];
+        if (s.has_root && s.T >= U) s.active = false;
+        if (!s.has_root || s.T > U) donors.push_back((int)i);
+        if (s.has_root && s.active) held.push_back(s.k);
+    }
+    int m = (int)donors.size();
+    long KU = kU - kmin;
+    for (int j = 0; j < m && KU > 0; ++j) {
+        long target = kmin + ((2L * j + 1) * KU) / (2L * m);
+        long found = -1;
+        for (long o = 0; o < KU && found < 0; ++o) {
+            long cand[2] = {target - o, target + o};
+            for (int c = 0; c < (o == 0 ? 1 : 2); ++c) {
+                long k = cand[c];
+                if (k < kmin || k >= kU) continue;
+                if (!is_free(k)) continue;
+                if (std::find(held.begin(), held.end(), k) != held.end()) continue;
+                found = k;
+                break;
+            }
+        }
+        if (found < 0) continue;
+        Slot& s = slots[donors[j]];
+        s.has_root = true;
+        s.active = true;
+        s.k = found;
+        s.T = (double)found * dt;
+        s.gen += 1;
+        held.push_back(found);
+        replaced.push_back(donors[j]);
+    }
+    return replaced;
+}
+
+struct Params {
+    int variant = 0;  // 0 interval root, 1 root recycling
+    int N = 4;
+    int W = 64;
+    int max_iters = 100;
+    double eta = 0.1, res = 0.01, dt = 0.02, p_new = 0.05, p_guided = 0.95, H = 10.0;
+    uint64_t seed = 0;
+    uint32_t problem_id = 0;
+    double flag_tol = 1e-4;    // margin below which an FP decision is flagged
+    double flag_clear = 1e-5;  // clearance band (m)
+};
+
+struct Margin {  // smallest decision margins seen during one iteration
+    double nn = kInf, clearance = kInf, count = kInf, interval = kInf, bounds = kInf, rank = kInf;
+    double min_all() const {
+        return std::min(std::min(std::min(nn, count), std::min(interval, bounds)), rank);
+    }
+};
+
+struct Result {
+    int dof = 0, N = 0, variant = 0;
+    std::vector<Node> fwd;
+    std::vector<std::vector<Node>> seg;
+    std::vector<Tree> trees;
+    std::vector<Slot> slots;
+    double U = kInf, C = kInf;
+    int inc_fwd = -1, inc_seg = -1, inc_bwd = -1;
+    int iters = 0, first_iter = -1;
+    long long ext_checked = 0, bridge_checked = 0, root_checked = 0, inserted = 0;
+    std::vector<double> path;  // [len][dof+1]
+    std::vector<double> U_hist, margin_hist, clear_hist;
+    std::vector<double> margin_types;  // [iters][6]: nn, count, interval, bounds, rank, clearance
+    int status = 0;  // 0 solved, 5 no solution
+    std::vector<double> goal_clearance;
+    long goal_kmin = 0;
+};
+
+struct Proposal {
+    bool ok = false;
+    bool forward = true;
+    int seg = -1;           // group (interval) or slot (recycling)
+    int parent = -1;        // index in the arena, -1 = virtual root
+    double T = 0;           // virtual-root time
+    std::vector<double> x;  // q_new (dof) then t_new
+};
+
+// Directed space-time distance (Eq. space-time-metric).
+double rho_sigma(const double* q, double t, const double* qr, double tr, int sigma, int d, double v) {
+    double Delta = (double)sigma * (tr - t);
+    double D = dist(q, qr, d);
+    if (!(Delta > 0.0) || !(D <= v * Delta)) return kInf;
+    return std::sqrt((D * D + v * v * (tr - t) * (tr - t)) / 2.0);
+}
+
+void note(double& slot, double v) {
+    v = std::fabs(v);
+    if (v < slot) slot = v;
+}
+
+// NN under rho_sigma over arena[0, n) restricted to nodes with troot < U when
+// filter is set. Returns -1 if every rho is infinite. Tie: lowest index.
+// Margins: the gap between the two smallest finite rho, and admissibility
+// boundaries of nodes that would be competitive.
+int nn_spacetime(const std::vector<Node>& A, int n, bool filter, double U, const double* qr, double tr,
+                 int sigma, int d, double v, double* best_rho, Margin& M, double tol) {
+    int best = -1;
+    double b1 = kInf, b2 = kInf;
+    for (int i = 0; i < n; ++i) {
+        if (filter && !(A[i].troot < U)) continue;
+        double r = rho_sigma(A[i].q.data(), A[i].t, qr, tr, sigma, d, v);
+        if (r < b1) {
+            b2 = b1;
+            b1 = r;
+            best = i;
+        } else if (r < b2) {
+            b2 = r;
+        }
+    }
+    if (best >= 0 && b2 < kInf) note(M.nn, b2 - b1);
+    for (int i = 0; i < n; ++i) {
+        if (filter && !(A[i].troot < U)) continue;
+        double Delta = (double)sigma * (tr - A[i].t);
+        double D = dist(A[i].q.data(), qr, d);
+        double madm = std::min(std::fabs(Delta), std::fabs(v * Delta - D));
+        if (madm < tol) {
+            double r = std::sqrt((D * D + v * v * (tr - A[i].t) * (tr - A[i].t)) / 2.0);
+            if (r <= b1 + tol) note(M.nn, madm);
+        }
+    }
+    *best_rho = b1;
+    return best;
+}
+
+// Configuration-distance NN (root recycling) over arena[0, n). Tie: lowest index.
+int nn_config(const std::vector<Node>& A, int n, const double* qr, int d, double* best_D, Margin& M) {
+    int best = -1;
+    double b1 = kInf, b2 = kInf;
+    for (int i = 0; i < n; ++i) {
+        double D = dist(A[i].q.data(), qr, d);
+        if (D < b1) {
+            b2 = b1;
+            b1 = D;
+            best = i;
+        } else if (D < b2) {
+            b2 = D;
+        }
+    }
+    if (b2 < kInf) note(M.nn, b2 - b1);
+    *best_D = b1;
+    return best;
+}
+
+class Planner {
+public:
+    Planner(const Problem& P, const Params& prm) : P(P), prm(prm) {}
+
+    Result run();
+
+private:
+    const Problem& P;
+    const Params& prm;
+    Result R;
+    GoalGrid grid;
+    IntervalAlloc alloc;
+    long kend = 0;  // first grid index with k dt >= H (recycling roots lie in [L_grid, H))
+
+    int d() const { return P.dof; }
+    void check_edge(const double* qa, double ta, const double* qb, double tb, bool* ok, Margin& M) {
+        double clr, im;
+        int c;
+        *ok = edge_free(P, qa, ta, qb, tb, prm.res, &clr, &c, &im);
+        note(M.clearance, clr);
+        note(M.count, im);
+    }
+    void init_recycling();
+    void recycle(double U);
+    Proposal propose_interval(int k, int w, const std::vector<int>& seg_n, int fwd_n, double U0,
+                              const std::vector<int>& group_active, Margin& M);
+    Proposal propose_recycling(int k, int w, const std::vector<int>& seg_n, int fwd_n,
+                               const std::vector<int>& active_slots, Margin& M);
+    void extract_path();
+};
+
+void Planner::init_recycling() {
+    // Reading (root initialisation): the grid indices of [L_grid, H) are split
+    // into N equal integer ranges; slot i takes the first collision-free goal
+    // check of its range, scanning upward; none found leaves the slot empty.
+    long K = kend - grid.kmin;
+    R.slots.assign(prm.N, Slot());
+    R.seg.assign(prm.N, {});
+    for (int i = 0; i < prm.N; ++i) {
+        long a = grid.kmin + (K * i) / prm.N;
+        long b = grid.kmin + (K * (i + 1)) / prm.N;
+        for (long k = a; k < b; ++k) {
+            if (grid.is_free(k)) {
+                Slot& s = R.slots[i];
+                s.has_root = true;
+                s.active = true;
+                s.k = k;
+                s.T = (double)k * prm.dt;
+                s.gen = 0;
+                Node root;
+                root.q = P.qg;
+                root.t = s.T;
+                root.parent = -1;
+                root.troot = s.T;
+                root.cost = 0.0;
+                root.tree = 0;
+                root.iter = -1;
+                R.seg[i].push_back(root);
+                break;
+            }
+        }
+    }
+}
+
+void Planner::recycle(double U) {
+    std::vector<int> rep = recycle_rule(R.slots, U, grid.kmin, prm.dt, [&](long k) { return grid.is_free(k); });
+    for (int i : rep) {
+        // Invalidate the old generation and install the empty root (q_g, T_i').
+        const Slot& s = R.slots[i];
+        Node root;
+        root.q = P.qg;
+        root.t = s.T;
+        root.parent = -1;
+        root.troot = s.T;
+        root.cost = 0.0;
+        root.tree = s.gen;
+        root.iter = R.iters - 1;
+        R.seg[i].assign(1, root);
+    }
+}
+
+Proposal Planner::propose_interval(int k, int w, const std::vector<int>& seg_n, int fwd_n, double U0,
+                                   const std::vector<int>& group_active, Margin& M) {
+    Proposal pr;
+    int dd = d();
+    Draws dr;
+    dr.fill(prm.seed, prm.problem_id, (uint32_t)k, (uint32_t)w, 5 + dd);
+    pr.forward = ((w + k) % 2) == 0;
+    int g = dr.group(0, prm.N);
+    pr.seg = g;
+    bool guided;
+    double T = sample_goal_time(alloc, g, dr.u(1), dr.u(2), prm.p_guided, &guided);
+    pr.T = T;
+    // Each proposed root is collision-checked at its sampled time; a rejected
+    // root skips the attempt (Algorithm 2).
+    {
+        double cl;
+        bool ok = state_free(P, P.qg.data(), T, &cl);
+        R.root_checked++;
+        note(M.clearance, cl);
+        if (!ok) return pr;
+    }
+    // Conditional query sample (Eq. conditional-query-time).
+    std::vector<double> qr(dd);
+    for (int j = 0; j < dd; ++j) qr[j] = P.qlo[j] + dr.u(4 + j) * (P.qhi[j] - P.qlo[j]);
+    double lo = dist(P.qs.data(), qr.data(), dd) / P.vmax;
+    double hi = T - dist(qr.data(), P.qg.data(), dd) / P.vmax;
+    note(M.interval, hi - lo);
+    if (lo > hi) return pr;
+    double tr = lo + dr.u(4 + dd) * (hi - lo);
+
+    // Source set and NN (Algorithm 1).
+    const double* qn;
+    double tn;
+    double rho;
+    int sigma = pr.forward ? 1 : -1;
+    if (pr.forward) {
+        int i = nn_spacetime(R.fwd, fwd_n, false, U0, qr.data(), tr, 1, dd, P.vmax, &rho, M, prm.flag_tol);
+        if (i < 0) return pr;
+        pr.parent = i;
+        qn = R.fwd[i].q.data();
+        tn = R.fwd[i].t;
+    } else {
+        bool use_new = (group_active[g] == 0) || (dr.u(3) <= prm.p_new);
+        if (use_new) {
+            rho = rho_sigma(P.qg.data(), T, qr.data(), tr, -1, dd, P.vmax);
+            if (!(rho < kInf)) return pr;
+            pr.parent = -1;
+            qn = P.qg.data();
+            tn = T;
+        } else {
+            int i = nn_spacetime(R.seg[g], seg_n[g], true, U0, qr.data(), tr, -1, dd, P.vmax, &rho, M,
+                                 prm.flag_tol);
+            if (i < 0) return pr;
+            pr.parent = i;
+            qn = R.seg[g][i].q.data();
+            tn = R.seg[g][i].t;
+        }
+    }
+    (void)sigma;
+    // Steering: x_new = x_n + alpha (x_r - x_n), alpha = min(1, eta / rho).
+    double alpha = std::min(1.0, prm.eta / rho);
+    pr.x.assign(dd + 1, 0.0);
+    for (int j = 0; j < dd; ++j) pr.x[j] = qn[j] + alpha * (qr[j] - qn[j]);
+    double tnew = tn + alpha * (tr - tn);
+    pr.x[dd] = tnew;
+    note(M.bounds, tnew);
+    note(M.bounds, prm.H - tnew);
+    if (tnew < 0.0 || tnew > prm.H) return pr;
+    bool ok;
+    check_edge(qn, tn, pr.x.data(), tnew, &ok, M);
+    R.ext_checked++;
+    pr.ok = ok;
+    return pr;
+}
+
+Proposal Planner::propose_recycling(int k, int w, const std::vector<int>& seg_n, int fwd_n,
+                                    const std::vector<int>& active_slots, Margin& M) {
+    Proposal pr;
+    int dd = d();
+    pr.forward = ((w + k) % 2) == 0;
+    // Reading (round-robin): the backward worker with ordinal floor(w/2) in this
+    // iteration takes active slot number ordinal mod (#active), in slot order.
+    if (!pr.forward) {
+        if (active_slots.empty()) return pr;
+        pr.seg = active_slots[(w / 2) % active_slots.size()];
+    }
+    Draws dr;
+    dr.fill(prm.seed, prm.problem_id, (uint32_t)k, (uint32_t)w, 4 + dd);
+    std::vector<double> qr(dd);
+    for (int j = 0; j < dd; ++j) qr[j] = P.qlo[j] + dr.u(4 + j) * (P.qhi[j] - P.qlo[j]);
+    const std::vector<Node>& A = pr.forward ? R.fwd : R.seg[pr.seg];
+    int n = pr.forward ? fwd_n : seg_n[pr.seg];
+    double D;
+    int i = nn_config(A, n, qr.data(), dd, &D, M);
+    note(M.bounds, D);
+    if (i < 0 || !(D > 0.0)) return pr;
+    pr.parent = i;
+    const double* qn = A[i].q.data();
+    double tn = A[i].t;
+    // Max-speed extension (Eq. max-speed-extension), configuration step capped at eta.
+    double s = std::min(1.0, prm.eta / D);
+    pr.x.assign(dd + 1, 0.0);
+    for (int j = 0; j < dd; ++j) pr.x[j] = qn[j] + s * (qr[j] - qn[j]);
+    double Dn = dist(qn, pr.x.data(), dd);
+    double tnew = tn + (pr.forward ? 1.0 : -1.0) * Dn / P.vmax;
+    pr.x[dd] = tnew;
+    note(M.bounds, tnew);
+    note(M.bounds, prm.H - tnew);
+    if (tnew < 0.0 || tnew > prm.H) return pr;
+    bool ok;
+    check_edge(qn, tn, pr.x.data(), tnew, &ok, M);
+    R.ext_checked++;
+    pr.ok = ok;
+    return pr;
+}
+
+void Planner::extract_path() {
+    R.path.clear();
+    if (R.inc_fwd < 0) return;
+    int dd = d();
+    std::vector<int> chain;
+    for (int i = R.inc_fwd; i >= 0; i = R.fwd[i].parent) chain.push_back(i);
+    std::reverse(chain.begin(), chain.end());
+    for (int i : chain) {
+        for (int j = 0; j < dd; ++j) R.path.push_back(R.fwd[i].q[j]);
+        R.path.push_back(R.fwd[i].t);
+    }
+    const std::vector<Node>& B = R.seg[R.inc_seg];
+    for (int i = R.inc_bwd; i >= 0; i = B[i].parent) {
+        for (int j = 0; j < dd; ++j) R.path.push_back(B[i].q[j]);
+        R.path.push_back(B[i].t);
+    }
+}
+
+Result Planner::run() {
+    int dd = d();
+    R.dof = dd;
+    R.N = prm.N;
+    R.variant = prm.variant;
+    // Forward tree rooted at (q_s, 0).
+    Node s0;
+    s0.q = P.qs;
+    s0.t = 0.0;
+    s0.parent = -1;
+    s0.troot = 0.0;
+    s0.cost = 0.0;
+    s0.tree = 0;
+    s0.iter = -1;
+    R.fwd.push_back(s0);
+
+    // Early return when q_s = q_g and x_s is free (first line of Algorithms 2, 3).
+    bool same = true;
+    for (int j = 0; j < dd; ++j)
+        if (P.qs[j] != P.qg[j]) same = false;
+    if (same && state_free(P, P.qs.data(), 0.0, nullptr)) {
+        R.U = 0.0;
+        R.C = 0.0;
+        R.inc_fwd = 0;
+        R.path.assign(P.qs.begin(), P.qs.end());
+        R.path.push_back(0.0);
+        R.seg.assign(prm.N, {});
+        R.status = 0;
+        return R;
+    }
+    if (!state_free(P, P.qs.data(), 0.0, nullptr)) {
+        R.seg.assign(prm.N, {});
+        R.status = 5;
+        return R;
+    }
+
+    build_goal_grid(P, prm.H, prm.dt, grid);
+    R.goal_clearance = grid.clearance;
+    R.goal_kmin = grid.kmin;
+    kend = grid.kmin;
+    while ((double)kend * prm.dt < prm.H) ++kend;
+
+    if (prm.variant == 0) {
+        alloc.Lg = grid.Lg;
+        alloc.H = prm.H;
+        alloc.dt = prm.dt;
+        alloc.N = prm.N;
+        if (grid.kmax >= grid.kmin) build_windows(alloc, grid.kmin, grid.kmax, grid.free.data());
+        partition(alloc, kInf);
+        R.seg.assign(prm.N, {});
+    } else {
+        init_recycling();
+    }
+
+    for (int k = 0; k < prm.max_iters; ++k) {
+        if (prm.variant == 0 && !(grid.Lg < std::min(prm.H, R.U))) break;
+        Margin M;
+        const double U0 = R.U, C0 = R.C;
+        const int fwd_n = (int)R.fwd.size();
+        std::vector<int> seg_n(prm.N);
+        for (int i = 0; i < prm.N; ++i) seg_n[i] = (int)R.seg[i].size();
+        std::vector<int> group_active(prm.N, 0);
+        std::vector<int> active_slots;
+        if (prm.variant == 0) {
+            for (const Tree& t : R.trees)
+                if (t.T < U0) group_active[t.group]++;
+        } else {
+            for (int i = 0; i < prm.N; ++i)
+                if (R.slots[i].active) active_slots.push_back(i);
+        }
+
+        // 1. Every worker proposes against the start-of-iteration state.
+        std::vector<Proposal> props(prm.W);
+        for (int w = 0; w < prm.W; ++w) {
+            props[w] = (prm.variant == 0) ? propose_interval(k, w, seg_n, fwd_n, U0, group_active, M)
+                                          : propose_recycling(k, w, seg_n, fwd_n, active_slots, M);
+        }
+
+        // 2. Ordered insertion (worker order).
+        struct Inserted {
+            int w;
+            bool forward;
+            int seg;
+            int idx;
+        };
+        std::vector<Inserted> ins;
+        for (int w = 0; w < prm.W; ++w) {
+            Proposal& pr = props[w];
+            if (!pr.ok) continue;
+            Node nd;
+            nd.q.assign(pr.x.begin(), pr.x.begin() + dd);
+            nd.t = pr.x[dd];
+            nd.iter = k;
+            if (pr.forward) {
+                const Node& par = R.fwd[pr.parent];
+                nd.parent = pr.parent;
+                nd.troot = 0.0;
+                nd.cost = par.cost + dist(par.q.data(), nd.q.data(), dd);
+                nd.tree = 0;
+                R.fwd.push_back(nd);
+                ins.push_back({w, true, -1, (int)R.fwd.size() - 1});
+            } else {
+                std::vector<Node>& A = R.seg[pr.seg];
+                if (pr.parent < 0) {
+                    // Materialise the virtual root as a new backward tree.
+                    Node root;
+                    root.q = P.qg;
+                    root.t = pr.T;
+                    root.parent = -1;
+                    root.troot = pr.T;
+                    root.cost = 0.0;
+                    root.tree = (int)R.trees.size();
+                    root.iter = k;
+                    R.trees.push_back({pr.seg, pr.T});
+                    A.push_back(root);
+                    nd.parent = (int)A.size() - 1;
+                } else {
+                    nd.parent = pr.parent;
+                }
+                const Node& par = A[nd.parent];
+                nd.troot = par.troot;
+                nd.cost = par.cost + dist(par.q.data(), nd.q.data(), dd);
+                nd.tree = par.tree;
+                A.push_back(nd);
+                ins.push_back({w, false, pr.seg, (int)A.size() - 1});
+            }
+            R.inserted++;
+        }
+
+        // 3. Bridge: the best-ranked admissible vertex of the opposite
+        // start-of-iteration set (arrival time, then space-time distance; tie:
+        // lowest (segment, index)) is validated if it would improve (U0, C0).
+        int best_w = -1;
+        double bestU = kInf, bestC = kInf;
+        int best_f = -1, best_s = -1, best_b = -1;
+        for (const Inserted& in : ins) {
+            const Node& a = in.forward ? R.fwd[in.idx] : R.seg[in.seg][in.idx];
+            double cU = kInf, cRho = kInf;
+            int cs = -1, ci = -1;
+            double s1U = kInf, s1R = kInf;  // runner-up key for margins
+            auto consider = [&](int s, int i, const Node& v, double Uv, double r) {
+                bool better = (Uv < cU) || (Uv == cU && r < cRho);
+                if (better) {
+                    s1U = cU;
+                    s1R = cRho;
+                    cU = Uv;
+                    cRho = r;
+                    cs = s;
+                    ci = i;
+                } else if ((Uv < s1U) || (Uv == s1U && r < s1R)) {
+                    s1U = Uv;
+                    s1R = r;
+                }
+                (void)v;
+            };
+            if (in.forward) {
+                for (int s = 0; s < prm.N; ++s) {
+                    for (int i = 0; i < seg_n[s]; ++i) {
+                        const Node& v = R.seg[s][i];
+                        if (!(v.troot < U0)) continue;
+                        double r = rho_sigma(a.q.data(), a.t, v.q.data(), v.t, 1, dd, P.vmax);
+                        double Delta = v.t - a.t, D = dist(a.q.data(), v.q.data(), dd);
+                        double madm = std::min(std::fabs(Delta), std::fabs(P.vmax * Delta - D));
+                        if (madm < prm.flag_tol && v.troot <= cU + prm.flag_tol) note(M.rank, madm);
+                        if (r < kInf) consider(s, i, v, v.troot, r);
+                    }
+                }
+            } else {
+                for (int i = 0; i < fwd_n; ++i) {
+                    const Node& v = R.fwd[i];
+                    double r = rho_sigma(v.q.data(), v.t, a.q.data(), a.t, 1, dd, P.vmax);
+                    double Delta = a.t - v.t, D = dist(a.q.data(), v.q.data(), dd);
+                    double madm = std::min(std::fabs(Delta), std::fabs(P.vmax * Delta - D));
+                    if (madm < prm.flag_tol) note(M.rank, madm);
+                    if (r < kInf) consider(-1, i, v, a.troot, r);
+                }
+            }
+            if (ci < 0) continue;
+            if (s1U == cU && s1R < kInf) note(M.rank, s1R - cRho);
+            if (s1U != cU && s1U < kInf) note(M.rank, s1U - cU);
+            const Node& b = in.forward ? R.seg[cs][ci] : R.fwd[ci];
+            const Node& fnode = in.forward ? a : b;
+            const Node& bnode = in.forward ? b : a;
+            double Dab = dist(fnode.q.data(), bnode.q.data(), dd);
+            double Uc = bnode.troot;
+            double Cc = fnode.cost + Dab + bnode.cost;
+            bool improves = (Uc < U0) || (Uc == U0 && Cc < C0);
+            if (Uc != U0 && U0 < kInf) note(M.rank, Uc - U0);
+            if (Uc == U0) note(M.rank, Cc - C0);
+            if (!improves) continue;
+            bool ok;
+            check_edge(fnode.q.data(), fnode.t, bnode.q.data(), bnode.t, &ok, M);
+            R.bridge_checked++;
+            if (!ok) continue;
+            // 4. Publish: lexicographic min of (U, C), tie: lowest worker.
+            bool win = (Uc < bestU) || (Uc == bestU && Cc < bestC);
+            if (best_w >= 0) {
+                if (Uc != bestU) note(M.rank, Uc - bestU);
+                else note(M.rank, Cc - bestC);
+            }
+            if (win) {
+                bestU = Uc;
+                bestC = Cc;
+                best_w = in.w;
+                best_f = in.forward ? in.idx : ci;
+                best_s = in.forward ? cs : in.seg;
+                best_b = in.forward ? ci : in.idx;
+            }
+        }
+        R.iters = k + 1;
+        bool decreased = false;
+        if (best_w >= 0) {
+            decreased = bestU < R.U;
+            R.U = bestU;
+            R.C = bestC;
+            R.inc_fwd = best_f;
+            R.inc_seg = best_s;
+            R.inc_bwd = best_b;
+            if (R.first_iter < 0) R.first_iter = k;
+        }
+        // 5. Allocation update when U decreased.
+        if (decreased) {
+            if (prm.variant == 0) {
+                partition(alloc, R.U);
+            } else {
+                recycle(R.U);
+            }
+        }
+        R.U_hist.push_back(R.U);
+        R.margin_hist.push_back(M.min_all());
+        double mt[6] = {M.nn, M.count, M.interval, M.bounds, M.rank, M.clearance};
+        R.margin_types.insert(R.margin_types.end(), mt, mt + 6);
+        R.clear_hist.push_back(M.clearance);
+    }
+    extract_path();
+    R.status = (R.inc_fwd >= 0) ? 0 : 5;
+    return R;
+}
+
+// ---------------------------------------------------------------------------
+// C interface (ctypes).
+// ---------------------------------------------------------------------------
+}  // namespace
+
+extern "C" {
+
+typedef struct {
+    int dof;
+    int arm;
+    const double* dh;
+    const double* qlo;
+    const double* qhi;
+    int n_sph;
+    const double* sph;  // [S][5] link, x, y, z, r
+    double vmax;
+    int n_obs;
+    int n_way;
+    const double* obs_r;
+    const double* way;  // [M][K][4]
+    const double* qs;
+    const double* qg;
+} orc_problem;
+
+typedef struct {
+    int variant;
+    int n_roots;
+    int workers;
+    int max_iters;
+    double eta, res, dt, p_new, p_guided, H;
+    unsigned long long seed;
+    unsigned int problem_id;
+    double flag_tol, flag_clear;
+} orc_params;
+
+static Problem to_problem(const orc_problem* p) {
+    Problem P;
+    P.dof = p->dof;
+    P.arm = p->arm != 0;
+    if (P.arm) P.dh.assign(p->dh, p->dh + 4 * p->dof);
+    P.qlo.assign(p->qlo, p->qlo + p->dof);
+    P.qhi.assign(p->qhi, p->qhi + p->dof);
+    for (int s = 0; s < p->n_sph; ++s) {
+        P.sph_link.push_back((int)p->sph[5 * s]);
+        for (int i = 0; i < 3; ++i) P.sph_p.push_back(p->sph[5 * s + 1 + i]);
+        P.sph_r.push_back(p->sph[5 * s + 4]);
+    }
+    P.vmax = p->vmax;
+    P.n_obs = p->n_obs;
+    P.n_way = p->n_way;
+    P.obs_r.assign(p->obs_r, p->obs_r + p->n_obs);
+    P.way.assign(p->way, p->way + (size_t)p->n_obs * p->n_way * 4);
+    P.qs.assign(p->qs, p->qs + p->dof);
+    P.qg.assign(p->qg, p->qg + p->dof);
+    return P;
+}
+
+void orc_philox4x32_10(const unsigned int ctr[4], const unsigned int key[2], unsigned int out[4]) {
+    philox4x32_10(ctr, key, out);
+}
+
+// Sphere centres [S][3] and frame origins [dof+1][3], rotations [dof+1][9].
+void orc_fk(const orc_problem* prob, const double* q, double* centres, double* origins, double* rots) {
+    Problem P = to_problem(prob);
+    std::vector<Frame> frames;
+    std::vector<double> c;
+    forward_kinematics(P, q, frames);
+    sphere_centres(P, frames, c);
+    if (centres) std::memcpy(centres, c.data(), c.size() * sizeof(double));
+    for (size_t f = 0; f < frames.size(); ++f) {
+        if (origins) std::memcpy(origins + 3 * f, frames[f].o, 3 * sizeof(double));
+        if (rots) std::memcpy(rots + 9 * f, frames[f].R, 9 * sizeof(double));
+    }
+}
+
+void orc_obstacle_position(const orc_problem* prob, int m, double t, double* out) {
+    Problem P = to_problem(prob);
+    obstacle_position(P, m, t, out);
+}
+
+int orc_state_free(const orc_problem* prob, const double* q, double t, double* clearance) {
+    Problem P = to_problem(prob);
+    return state_free(P, q, t, clearance) ? 1 : 0;
+}
+
+// Batch edge check: edges given in double, [n][dof] and [n].
+void orc_check_edges(const orc_problem* prob, int n, const double* qa, const double* ta, const double* qb,
+                     const double* tb, double res, unsigned char* verdict, double* clearance, int* nchk,
+                     double* int_margin) {
+    Problem P = to_problem(prob);
+    int d = P.dof;
+    for (int e = 0; e < n; ++e) {
+        double clr, im;
+        int c;
+        bool ok = edge_free(P, qa + (size_t)e * d, ta[e], qb + (size_t)e * d, tb[e], res, &clr, &c, &im);
+        verdict[e] = ok ? 1 : 0;
+        if (clearance) clearance[e] = clr;
+        if (nchk) nchk[e] = c;
+        if (int_margin) int_margin[e] = im;
+    }
+}
+
+// Interval-root partition from explicit grid flags (k = kmin..kmin+nk-1).
+// Outputs: uniform lower bounds and width; pieces [n][3] (lo, hi, group).
+int orc_interval_partition(double Lg, double H, double dt, int N, double U, long kmin, int nk,
+                           const unsigned char* free_flags, double* uni_lo, double* uni_width,
+                           double* pieces, int max_pieces) {
+    IntervalAlloc A;
+    A.Lg = Lg;
+    A.H = H;
+    A.dt = dt;
+    A.N = N;
+    std::vector<char> f(free_flags, free_flags + nk);
+    if (nk > 0) build_windows(A, kmin, kmin + nk - 1, f.data());
+    partition(A, U);
+    for (int g = 0; g < N; ++g) uni_lo[g] = Lg + (double)g * A.width;
+    *uni_width = A.width;
+    int n = (int)A.pieces.size();
+    for (int i = 0; i < n && i < max_pieces; ++i) {
+        pieces[3 * i] = A.pieces[i].lo;
+        pieces[3 * i + 1] = A.pieces[i].hi;
+        pieces[3 * i + 2] = (double)A.pieces[i].group;
+    }
+    return n;
+}
+
+// Goal-time sample from an interval partition (for distribution tests).
+double orc_interval_sample(double Lg, double H, double dt, int N, double U, long kmin, int nk,
+                           const unsigned char* free_flags, int group, double u_coin, double u_pos,
+                           double p_guided, int* guided) {
+    IntervalAlloc A;
+    A.Lg = Lg;
+    A.H = H;
+    A.dt = dt;
+    A.N = N;
+    std::vector<char> f(free_flags, free_flags + nk);
+    if (nk > 0) build_windows(A, kmin, kmin + nk - 1, f.data());
+    partition(A, U);
+    bool g;
+    double T = sample_goal_time(A, group, u_coin, u_pos, p_guided, &g);
+    *guided = g ? 1 : 0;
+    return T;
+}
+
+// Root-recycling update on its own: slots (T, has_root, active, gen) in/out.
+// Grid: goal checks k = kmin..kmin+nk-1 with flags; dt grid spacing. Slot
+// times must lie on the grid. Returns the number of replaced slots.
+int orc_recycle_update(int N, double* T, int* has_root, int* active, int* gen, double U, long kmin, int nk,
+                       const unsigned char* free_flags, double dt) {
+    std::vector<Slot> slots(N);
+    for (int i = 0; i < N; ++i) {
+        slots[i].has_root = has_root[i] != 0;
+        slots[i].active = active[i] != 0;
+        slots[i].T = has_root[i] ? T[i] : kInf;
+        slots[i].k = has_root[i] ? (long)std::llround(T[i] / dt) : -1;
+        slots[i].gen = gen[i];
+    }
+    auto is_free = [&](long k) { return k >= kmin && k - kmin < nk && free_flags[k - kmin] != 0; };
+    std::vector<int> rep = recycle_rule(slots, U, kmin, dt, is_free);
+    for (int i = 0; i < N; ++i) {
+        T[i] = slots[i].T;
+        has_root[i] = slots[i].has_root;
+        active[i] = slots[i].active;
+        gen[i] = slots[i].gen;
+    }
+    return (int)rep.size();
+}
+
+struct orc_result {
+    Result R;
+};
+
+int orc_plan(const orc_problem* prob, const orc_params* p, orc_result** out) {
+    Problem P = to_problem(prob);
+    Params prm;
+    prm.variant = p->variant;
+    prm.N = p->n_roots;
+    prm.W = p->workers;
+    prm.max_iters = p->max_iters;
+    prm.eta = p->eta;
+    prm.res = p->res;
+    prm.dt = p->dt;
+    prm.p_new = p->p_new;
+    prm.p_guided = p->p_guided;
+    prm.H = p->H;
+    prm.seed = p->seed;
+    prm.problem_id = p->problem_id;
+    if (p->flag_tol > 0) prm.flag_tol = p->flag_tol;
+    if (p->flag_clear > 0) prm.flag_clear = p->flag_clear;
+    Planner pl(P, prm);
+    orc_result* r = new orc_result;
+    r->R = pl.run();
+    *out = r;
+    return r->R.status;
+}
+
+// summary: [U, C, iters, first_iter, ext_checked, bridge_checked, root_checked,
+//           inserted, path_len, n_fwd, n_trees, status]
+void orc_result_summary(const orc_result* r, double* s) {
+    const Result& R = r->R;
+    s[0] = R.U;
+    s[1] = R.C;
+    s[2] = R.iters;
+    s[3] = R.first_iter;
+    s[4] = (double)R.ext_checked;
+    s[5] = (double)R.bridge_checked;
+    s[6] = (double)R.root_checked;
+    s[7] = (double)R.inserted;
+    s[8] = R.dof > 0 ? (double)(R.path.size() / (R.dof + 1)) : 0.0;
+    s[9] = (double)R.fwd.size();
+    s[10] = (double)R.trees.size();
+    s[11] = R.status;
+}
+
+void orc_result_path(const orc_result* r, double* path) {
+    std::memcpy(path, r->R.path.data(), r->R.path.size() * sizeof(double));
+}
+
+// arena -1: forward tree; arena i >= 0: backward group / slot i.
+int orc_result_arena_size(const orc_result* r, int arena) {
+    if (arena < 0) return (int)r->R.fwd.size();
+    if (arena >= (int)r->R.seg.size()) return 0;
+    return (int)r->R.seg[arena].size();
+}
+
+void orc_result_arena(const orc_result* r, int arena, double* x, int* parent, double* troot, double* cost,
+                      int* tree, int* iter) {
+    const std::vector<Node>& A = arena < 0 ? r->R.fwd : r->R.seg[arena];
+    int d = r->R.dof;
+    for (size_t i = 0; i < A.size(); ++i) {
+        for (int j = 0; j < d; ++j) x[i * (d + 1) + j] = A[i].q[j];
+        x[i * (d + 1) + d] = A[i].t;
+        parent[i] = A[i].parent;
+        troot[i] = A[i].troot;
+        cost[i] = A[i].cost;
+        tree[i] = A[i].tree;
+        iter[i] = A[i].iter;
+    }
+}
+
+// Per-iteration U, smallest decision margin and smallest |clearance|.
+void orc_result_history(const orc_result* r, double* U, double* margin, double* clear) {
+    size_t n = r->R.U_hist.size();
+    for (size_t i = 0; i < n; ++i) {
+        U[i] = r->R.U_hist[i];
+        margin[i] = r->R.margin_hist[i];
+        clear[i] = r->R.clear_hist[i];
+    }
+}
+
+// NN under rho_sigma over explicit nodes x [n][d+1] (q..., t), tie: lowest index.
+int orc_nn_spacetime(int n, int d, const double* x, const double* troot, int filter, double U, const double* qr,
+                     double tr, int sigma, double vmax, double* rho) {
+    std::vector<Node> A(n);
+    for (int i = 0; i < n; ++i) {
+        A[i].q.assign(x + (size_t)i * (d + 1), x + (size_t)i * (d + 1) + d);
+        A[i].t = x[(size_t)i * (d + 1) + d];
+        A[i].troot = troot ? troot[i] : 0.0;
+    }
+    Margin M;
+    return nn_spacetime(A, n, filter != 0, U, qr, tr, sigma, d, vmax, rho, M, 1e-4);
+}
+
+void orc_result_margin_types(const orc_result* r, double* out) {
+    std::memcpy(out, r->R.margin_types.data(), r->R.margin_types.size() * sizeof(double));
+}
+
+// Slots (root recycling): T, has_root, active, gen per slot; trees (interval): group, T.
+void orc_result_slots(const orc_result* r, double* T, int* has_root, int* active, int* gen) {
+    for (size_t i = 0; i < r->R.slots.size(); ++i) {
+        T[i] = r->R.slots[i].T;
+        has_root[i] = r->R.slots[i].has_root;
+        active[i] = r->R.slots[i].active;
+        gen[i] = r->R.slots[i].gen;
+    }
+}
+
+void orc_result_trees(const orc_result* r, int* group, double* T) {
+    for (size_t i = 0; i < r->R.trees.size(); ++i) {
+        group[i] = r->R.trees[i].group;
+        T[i] = r->R.trees[i].T;
+    }
+}
+
+int orc_result_goal_grid(const orc_result* r, long* kmin, double* clearance, int cap) {
+    *kmin = r->R.goal_kmin;
+    int n = (int)r->R.goal_clearance.size();
+    for (int i = 0; i < n && i < cap; ++i) clearance[i] = r->R.goal_clearance[i];
+    return n;
+}
+
+void orc_result_incumbent(const orc_result* r, int* f, int* s, int* b) {
+    *f = r->R.inc_fwd;
+    *s = r->R.inc_seg;
+    *b = r->R.inc_bwd;
+}
+
+void orc_result_free(orc_result* r) { delete r; }
+
+}  // extern "C"
