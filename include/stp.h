@@ -1,0 +1,218 @@
+/*
+ * stp.h - C ABI of the GB300 (sm_103a) batched space-time Extend library for
+ * ST-pRRTC ("ST-pRRTC: Parallel Space-Time RRT-C with Adaptive Goal-Time
+ * Forests").
+ *
+ * The library plans one single-goal query at a time (Sec. "Problem
+ * Formulation": C subset of R^d with the Euclidean metric, velocity bound
+ * v_max, horizon [0,H], moving obstacles with known trajectories) with the
+ * interval-root planner (Algorithms 1-2) or the root-recycling planner
+ * (Algorithm 3). Every step of a planning iteration runs in the library's CUDA
+ * kernels; there is no CPU fallback: when no CUDA device is usable, every call
+ * that would compute returns STP_ERR_CUDA.
+ *
+ * Conventions
+ *   - All calls return an stp_status; none aborts the process.
+ *   - Input arrays are read during the call and copied; the caller keeps
+ *     ownership. Output buffers are owned by the caller.
+ *   - Multi-dimensional arrays are row-major and contiguous.
+ *   - Precision: stp_params.precision selects the arithmetic of the device
+ *     path: 0 = FP32 (the fast path), 1 = FP64 (deterministic-parity mode).
+ *     Arrays typed `const void *` below hold float in FP32 mode and double in
+ *     FP64 mode.
+ *   - A problem is not thread-safe; distinct problems may be used from
+ *     distinct threads.
+ */
+#ifndef STP_H
+#define STP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stp_problem stp_problem; /* opaque, owned by the library */
+
+typedef enum {
+    STP_OK = 0,
+    STP_ERR_INVALID = 1,   /* an argument violates the documented contract   */
+    STP_ERR_CAPACITY = 2,  /* a tree arena or table would overflow           */
+    STP_ERR_CUDA = 3,      /* no usable device, or a CUDA call failed         */
+    STP_ERR_TIMEOUT = 4,   /* a bounded device wait gave up                   */
+    STP_NO_SOLUTION = 5    /* budget exhausted without a solution (Alg. 2, 3) */
+} stp_status;
+
+/* Robot (Sec. "Problem Formulation": C subset of R^d, Euclidean D, v_max).
+ *   dof        2..7. With arm = 0 the robot is a point (or sphere set) translated
+ *              by q (q0, q1[, q2]) in the plane/space; with arm = 1 it is a
+ *              serial chain in standard DH form.
+ *   dh         [dof][4] rows (a, alpha, d, theta_offset); frame j+1 =
+ *              frame j * Rz(q_j + theta_offset) Tz(d) Tx(a) Rx(alpha). NULL if
+ *              arm = 0.
+ *   q_lo,q_hi  [dof] configuration box; states outside it are in collision.
+ *   spheres    [n_spheres][5]: frame index (0 = base, j = after joint j), local
+ *              centre x, y, z, radius. 1 <= n_spheres <= 64.
+ *   v_max      speed bound in the Euclidean metric of C (Eq. minimum-travel-time). */
+typedef struct {
+    int dof;
+    int arm;
+    const double *dh;
+    const double *q_lo;
+    const double *q_hi;
+    int n_spheres;
+    const double *spheres;
+    double v_max;
+} stp_robot;
+
+/* Moving obstacles: spheres on piecewise-linear trajectories, positions
+ * interpolated at each absolute query time (Sec. "Simulation Protocol");
+ * before the first and after the last waypoint an obstacle holds that waypoint.
+ *   n_obs      0..128, n_way 1..8.
+ *   radius     [n_obs]
+ *   way        [n_obs][n_way][4]: t, x, y, z (z = 0 for planar problems);
+ *              times strictly increasing per obstacle.
+ * Collision predicate: a robot sphere and an obstacle collide iff
+ * |p - o|^2 < (r + r_o)^2 (touching is free). */
+typedef struct {
+    int n_obs;
+    int n_way;
+    const double *radius;
+    const double *way;
+} stp_obstacles;
+
+/* Planner settings.
+ *   variant        0 interval root (Algorithm 2), 1 root recycling (Algorithm 3).
+ *   n_roots        N: interval-root groups or recycling slots, 1..128.
+ *   ext_per_iter   W: GPU workers (one Extend each) per iteration, 1..8192.
+ *   max_iters      iteration budget (>= 1). budget_ms > 0 adds a wall-clock
+ *                  budget checked between graph launches.
+ *   eta            range: steering step in rho (interval root, Algorithm 1) or
+ *                  configuration step (root recycling, Eq. max-speed-extension).
+ *   edge_res       check resolution: an edge is checked at
+ *                  c = max(1, ceil(max(D, v_max |dt|) / edge_res)) points j/c.
+ *   env_dt         environment grid step dt for goal checks
+ *                  (Eq. goal-time-lower-bound).
+ *   p_new, p_guided  Sec. "Interval Root" (paper default 0.05 / 0.95).
+ *   t_max          horizon H; arrival times lie in [0, H].
+ *   seed, problem_id  Philox4x32-10 key and counter word 3.
+ *   precision      0 FP32, 1 FP64.
+ *   learned        reserved, must be 0.
+ *   capacity       nodes per tree arena; 0 = max_iters * ceil(W/2) + 2 (worst case).
+ *   iters_per_graph  iterations captured per CUDA graph launch; 0 = 16. */
+typedef struct {
+    int variant;
+    int n_roots;
+    int ext_per_iter;
+    int max_iters;
+    double budget_ms;
+    double eta;
+    double edge_res;
+    double env_dt;
+    double p_new;
+    double p_guided;
+    double t_max;
+    unsigned long long seed;
+    unsigned int problem_id;
+    int precision;
+    int learned;
+    int capacity;
+    int iters_per_graph;
+} stp_params;
+
+/* Per-call statistics filled by stp_plan. Times are GPU times (CUDA events /
+ * device global timer), excluding problem upload (Sec. "Simulation Protocol"). */
+typedef struct {
+    int iterations;
+    int first_solution_iter;      /* -1 if none */
+    long long nodes;              /* inserted extensions (not counting roots) */
+    long long edges_validated;    /* extension edges sent to edge validation */
+    long long bridges_validated;  /* bridge edges sent to edge validation */
+    long long root_checks;        /* sampled goal roots checked (interval root) */
+    long long check_points;       /* check points of all validated edges */
+    double first_solution_ms;     /* device time from plan start to the first solution */
+    double plan_ms;               /* device time of the whole plan */
+    double U;
+    double C;
+} stp_stats;
+
+/* Create a problem: validates and copies robot, obstacles, start, goal and
+ * params to the device, runs the goal-time grid checks (Eq.
+ * goal-time-lower-bound) and sizes the tree arenas.
+ *   q_start, q_goal  [dof]. *out receives the handle (NULL on error).
+ * Errors: STP_ERR_INVALID (bad sizes/values), STP_ERR_CUDA (no device or
+ * allocation failed), STP_ERR_CAPACITY (arena size overflow). */
+stp_status stp_create_problem(const stp_robot *robot, const stp_obstacles *obstacles,
+                              const double *q_start, const double *q_goal,
+                              const stp_params *params, stp_problem **out);
+
+/* Run the planner from a fresh state (trees reset) for the configured budget.
+ * Algorithm 2 ends early when L_g >= min(H, U). Outputs (any may be NULL):
+ *   arrival_U, length_C  incumbent (U, C), lexicographic (Sec. "Space-Time
+ *                        pRRTC"); +inf if none.
+ *   path                 caller buffer [cap][dof+1] of (q..., t) states from
+ *                        (q_s, 0) to (q_g, U); *n_path receives the count.
+ * Returns STP_OK when a solution exists, STP_NO_SOLUTION when the budget ran
+ * out without one (Algorithms 2, 3), STP_ERR_CAPACITY if path exceeds cap or
+ * an arena overflowed, STP_ERR_TIMEOUT if a bounded device wait gave up. */
+stp_status stp_plan(stp_problem *p, double *arrival_U, double *length_C, int *n_path, double *path,
+                    int cap, stp_stats *stats);
+
+/* Edge validation on its own (collision kernel; Sec. "Simulation Protocol":
+ * obstacles interpolated at each absolute query time): for each edge
+ * (qa[e], ta[e]) -> (qb[e], tb[e]) check points j/c, j = 1..c.
+ *   qa, qb       [n_edges][dof], ta, tb [n_edges]; element type per precision.
+ *   flags        bit 0 (STP_EDGES_DEVICE): all pointers (inputs and outputs) are
+ *                device pointers; bit 1 (STP_EDGES_CLEARANCE): also compute the
+ *                exact minimum clearance (no early exit); bit 2
+ *                (STP_EDGES_NO_EARLY_EXIT): check every point even after a hit.
+ *   verdict      [n_edges] output, 1 = collision-free, 0 = collides.
+ *   min_clearance [n_edges] output (precision type) or NULL; requires bit 1.
+ *   n_checks     [n_edges] int output or NULL: check points per edge.
+ * Errors: STP_ERR_INVALID (n_edges < 0 or > 2^26, NULL arrays), STP_ERR_CUDA. */
+#define STP_EDGES_DEVICE 1
+#define STP_EDGES_CLEARANCE 2
+#define STP_EDGES_NO_EARLY_EXIT 4
+stp_status stp_check_edges(stp_problem *p, int n_edges, const void *qa, const void *ta, const void *qb,
+                           const void *tb, int flags, unsigned char *verdict, void *min_clearance,
+                           int *n_checks);
+
+/* Device time (ms, CUDA events on the problem's stream) of the collision
+ * kernel launch inside the last stp_check_edges call on p. */
+stp_status stp_last_validate_ms(stp_problem *p, double *ms);
+
+/* Release all device and host memory of a problem. NULL is allowed. */
+void stp_free(stp_problem *p);
+
+/* Use this CUDA stream (a cudaStream_t passed as void*) for every later call
+ * on p; NULL selects the library's own stream. */
+stp_status stp_set_stream(stp_problem *p, void *cuda_stream);
+
+/* Human-readable name of a status code (static string). */
+const char *stp_status_string(stp_status s);
+
+/* Last CUDA error text recorded by the library for p (static until the next
+ * call on p); "" if none. */
+const char *stp_last_error(const stp_problem *p);
+
+/* ---- Inspection (tests and tooling) -------------------------------------
+ * Arena -1 is the forward tree; arena i in [0, n_roots) is backward group i
+ * (interval root) or slot i (root recycling, current generation only).
+ * stp_tree_nodes writes n nodes: x [n][dof+1] (q..., t), parent (index in the
+ * same arena, -1 for roots), troot (root/arrival time; 0 forward), cost
+ * (configuration-space length to the root), tree (interval: backward tree id;
+ * recycling: slot generation), iter (inserting iteration, -1 initial roots).
+ * Any output pointer may be NULL. */
+stp_status stp_tree_size(stp_problem *p, int arena, int *n);
+stp_status stp_tree_nodes(stp_problem *p, int arena, double *x, int *parent, double *troot,
+                          double *cost, int *tree, int *iter);
+/* Incumbent arrival time after each iteration of the last stp_plan: U_hist[cap]. */
+stp_status stp_history(stp_problem *p, double *U_hist, int cap, int *n);
+/* Root-recycling slots after the last stp_plan: T, has_root, active, gen [n_roots]. */
+stp_status stp_slots(stp_problem *p, double *T, int *has_root, int *active, int *gen);
+/* Goal-time grid checks k = kmin..kmin+n-1 (free flags [cap]). */
+stp_status stp_goal_grid(stp_problem *p, long *kmin, int *n, unsigned char *free_flags, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STP_H */

@@ -240,13 +240,16 @@ bool state_free(const Problem& P, const double* q, double t, double* clearance) 
 }
 
 // Reading (edge resolution): an edge (q_a,t_a)->(q_b,t_b) is checked at
-// c = max(1, ceil(max(D, v_max |t_b - t_a|) / res)) points s_j = j/c,
-// j = 1..c (the start state was validated when it was inserted).
+// c = max(1, ceil(max(D, v_max |t_b - t_a|) / res - 1e-3)) points s_j = j/c,
+// j = 1..c (the start state was validated when it was inserted). The 1e-3
+// slack lets the spacing exceed res by at most 0.1 % of a step and makes c
+// insensitive to rounding when the length is an exact multiple of res (every
+// root-recycling step of length eta is one).
 int edge_check_count(const Problem& P, const double* qa, double ta, const double* qb, double tb,
                      double res, double* int_margin) {
     double D = dist(qa, qb, P.dof);
     double L = std::max(D, P.vmax * std::fabs(tb - ta));
-    double x = L / res;
+    double x = L / res - 1e-3;
     double c = std::ceil(x);
     if (int_margin) {
         double fr = x - std::floor(x);

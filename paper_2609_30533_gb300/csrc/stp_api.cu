@@ -1,0 +1,893 @@
+// C ABI of the ST-pRRTC batched space-time Extend library (declarations and
+// contracts in include/stp.h). Host code: validation, one device arena per
+// problem, the geometry blob, goal-time grid checks at creation, and CUDA
+// graphs that hold a fixed number of planner iterations.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "stp.h"
+#include "stp_internal.cuh"
+
+using namespace stp;
+
+namespace {
+
+const double kInfD = std::numeric_limits<double>::infinity();
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Carves aligned sub-buffers out of one device allocation.
+struct Carver {
+    size_t off = 0;
+    char* base = nullptr;
+    template <typename T>
+    T* take(size_t count) {
+        off = align_up(off, 256);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+}  // namespace
+
+struct stp_problem {
+    int precision = 0;
+    int dof = 0, arm = 0, S = 0, M = 0, K = 0;
+    stp_params prm{};
+    std::vector<double> qs, qg, qlo, qhi, dh, sph, obs_r, way;
+    double vmax = 1.0;
+    double Lg = 0.0;
+    long long kmin = 0, kmax = -1, kend = 0;
+    int nk = 0;
+    int start_free = 0;
+    int cap_f = 0, cap_s = 0, cap_trees = 0, max_pieces = 0, path_cap = 0;
+    char* d_arena = nullptr;
+    size_t arena_bytes = 0;
+    Geom<float> gf{};
+    Geom<double> gd{};
+    State<float> sf{};
+    State<double> sd{};
+    Ctl* d_ctl = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    int graph_iters = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+    // batch scratch for stp_check_edges
+    char* d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    double last_validate_ms = 0.0;
+    std::string last_error;
+    bool planned = false;
+};
+
+namespace {
+
+stp_status cuda_fail(stp_problem* p, cudaError_t e, const char* where) {
+    if (p) {
+        char buf[256];
+        snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+        p->last_error = buf;
+    }
+    return STP_ERR_CUDA;
+}
+
+#define STP_CUDA(p, call)                                   \
+    do {                                                    \
+        cudaError_t _e = (call);                            \
+        if (_e != cudaSuccess) return cuda_fail(p, _e, #call); \
+    } while (0)
+
+bool finite_all(const double* a, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+double host_dist(const double* a, const double* b, int d) {
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) {
+        double e = b[j] - a[j];
+        s += e * e;
+    }
+    return std::sqrt(s);
+}
+
+template <typename R>
+void fill_geom(stp_problem* p, Geom<R>& g, const R* blob, unsigned blob_bytes, int off_way, int off_vel,
+               int off_rad, const std::vector<int>& link_start) {
+    std::memset(&g, 0, sizeof(g));
+    g.dof = p->dof;
+    g.arm = p->arm;
+    g.S = p->S;
+    g.M = p->M;
+    g.K = p->K;
+    g.DP = kDP;
+    for (int j = 0; j < kMaxDof + 2; ++j) g.link_start[j] = j < (int)link_start.size() ? link_start[j] : p->S;
+    for (int j = 0; j < p->dof; ++j) {
+        if (p->arm) {
+            g.a[j] = (R)p->dh[4 * j];
+            g.ca[j] = (R)std::cos(p->dh[4 * j + 1]);
+            g.sa[j] = (R)std::sin(p->dh[4 * j + 1]);
+            g.d[j] = (R)p->dh[4 * j + 2];
+            g.th0[j] = (R)p->dh[4 * j + 3];
+        }
+        g.qlo[j] = (R)p->qlo[j];
+        g.qhi[j] = (R)p->qhi[j];
+    }
+    g.vmax = (R)p->vmax;
+    g.vmax_d = p->vmax;
+    g.uniform_r = 0;
+    g.blob = blob;
+    g.blob_bytes = blob_bytes;
+    g.off_way = off_way;
+    g.off_vel = off_vel;
+    g.off_rad = off_rad;
+}
+
+// Sizes and layout of the geometry blob in R units; returns bytes.
+template <typename R>
+size_t blob_layout(const stp_problem* p, int* off_way, int* off_vel, int* off_rad) {
+    size_t n = 4 * (size_t)p->S;
+    *off_way = (int)n;
+    n += 4 * (size_t)p->M * p->K;
+    *off_vel = (int)n;
+    n += 4 * (size_t)p->M * p->K;
+    *off_rad = (int)n;
+    n += align_up((size_t)p->M, 4);
+    if (n == 0) n = 4;
+    return align_up(n * sizeof(R), 16);
+}
+
+template <typename R>
+std::vector<R> blob_host(const stp_problem* p, const std::vector<int>& order, size_t bytes, int off_way,
+                         int off_vel, int off_rad) {
+    std::vector<R> b(bytes / sizeof(R), R(0));
+    for (int s = 0; s < p->S; ++s) {
+        const double* sp = &p->sph[5 * order[s]];
+        for (int i = 0; i < 4; ++i) b[4 * s + i] = (R)sp[1 + i];
+    }
+    for (int m = 0; m < p->M; ++m) {
+        for (int k = 0; k < p->K; ++k) {
+            const double* w = &p->way[((size_t)m * p->K + k) * 4];
+            for (int i = 0; i < 4; ++i) b[off_way + ((size_t)m * p->K + k) * 4 + i] = (R)w[i];
+            double v[3] = {0, 0, 0};
+            if (k + 1 < p->K) {
+                const double* w1 = w + 4;
+                double dt = w1[0] - w[0];
+                for (int i = 0; i < 3; ++i) v[i] = (w1[1 + i] - w[1 + i]) / dt;
+            }
+            for (int i = 0; i < 3; ++i) b[off_vel + ((size_t)m * p->K + k) * 4 + i] = (R)v[i];
+        }
+        b[off_rad + m] = (R)p->obs_r[m];
+    }
+    return b;
+}
+
+template <typename R>
+State<R>& state_of(stp_problem* p);
+template <>
+State<float>& state_of<float>(stp_problem* p) { return p->sf; }
+template <>
+State<double>& state_of<double>(stp_problem* p) { return p->sd; }
+template <typename R>
+Geom<R>& geom_of(stp_problem* p);
+template <>
+Geom<float>& geom_of<float>(stp_problem* p) { return p->gf; }
+template <>
+Geom<double>& geom_of<double>(stp_problem* p) { return p->gd; }
+
+// Lays out (base == nullptr: sizes only) every device buffer of a problem.
+template <typename R>
+size_t layout_state(stp_problem* p, char* base, R** blob_out, size_t blob_bytes, unsigned char** gfree,
+                    Ctl** ctl, R** qdev, R** tdev, int** cnt, long long** off, int** hit) {
+    Carver cv;
+    cv.base = base;
+    const int W = p->prm.ext_per_iter, N = p->prm.n_roots;
+    State<R> s;
+    std::memset(&s, 0, sizeof(s));
+    *ctl = cv.take<Ctl>(1);
+    *blob_out = reinterpret_cast<R*>(cv.take<char>(blob_bytes));
+    *gfree = cv.take<unsigned char>(std::max(p->nk, 1) + 1);
+    // goal grid / start check scratch
+    const int ng = p->nk + 1;
+    *qdev = cv.take<R>(kDP);
+    *tdev = cv.take<R>(ng);
+    *cnt = cv.take<int>(ng);
+    *off = cv.take<long long>(ng + 1);
+    *hit = cv.take<int>(ng);
+    s.ctl = *ctl;
+    s.fx = cv.take<R>((size_t)p->cap_f * kDP);
+    s.fpar = cv.take<int>(p->cap_f);
+    s.fcost = cv.take<R>(p->cap_f);
+    s.fiter = cv.take<int>(p->cap_f);
+    const size_t nb = (size_t)N * p->cap_s;
+    s.bx = cv.take<R>(nb * kDP);
+    s.bpar = cv.take<int>(nb);
+    s.bcost = cv.take<R>(nb);
+    s.btroot = cv.take<R>(nb);
+    s.btree = cv.take<int>(nb);
+    s.biter = cv.take<int>(nb);
+    s.tree_group = cv.take<int>(p->cap_trees);
+    s.tree_T = cv.take<double>(p->cap_trees);
+    const int nwin = std::max(p->nk, 1);
+    s.win_lo = cv.take<double>(nwin);
+    s.win_hi = cv.take<double>(nwin);
+    s.pc_lo = cv.take<double>(p->max_pieces);
+    s.pc_hi = cv.take<double>(p->max_pieces);
+    s.pc_group = cv.take<int>(p->max_pieces);
+    s.gfree = *gfree;
+    s.w_status = cv.take<int>(W);
+    s.w_set = cv.take<int>(W);
+    s.w_xr = cv.take<R>((size_t)W * kDP);
+    s.w_T = cv.take<double>(W);
+    s.w_parent = cv.take<int>(W);
+    s.w_key = cv.take<R>(W);
+    s.w_xnew = cv.take<R>((size_t)W * kDP);
+    s.w_edge = cv.take<int>(W);
+    s.w_root_edge = cv.take<int>(W);
+    s.w_ins = cv.take<int>(W);
+    s.w_bedge = cv.take<int>(W);
+    s.w_xn = cv.take<R>((size_t)W * kDP);
+    s.qlist = cv.take<int>((size_t)(N + 1) * W);
+    s.tile_cnt = cv.take<int>((size_t)(N + 1) * kMaxQTiles);
+    s.part_k1 = cv.take<R>((size_t)W * kMaxTiles);
+    s.part_k2 = cv.take<R>((size_t)W * kMaxTiles);
+    s.part_idx = cv.take<int>((size_t)W * kMaxTiles);
+    s.bq_list = cv.take<int>((size_t)2 * W);
+    s.bq_count = cv.take<int>(2);
+    s.btile_cnt = cv.take<int>((size_t)2 * kMaxQTiles);
+    s.b_set = cv.take<int>(W);
+    s.b_idx = cv.take<int>(W);
+    s.b_k1 = cv.take<R>(W);
+    s.b_k2 = cv.take<R>(W);
+    s.b_U = cv.take<double>(W);
+    s.b_C = cv.take<double>(W);
+    s.eqa = cv.take<R>((size_t)2 * W * kDP);
+    s.eqb = cv.take<R>((size_t)2 * W * kDP);
+    s.eta_ = cv.take<R>((size_t)2 * W);
+    s.etb = cv.take<R>((size_t)2 * W);
+    s.ecnt = cv.take<int>((size_t)2 * W);
+    s.eoff = cv.take<long long>((size_t)2 * W + 1);
+    s.ehit = cv.take<int>((size_t)2 * W);
+    s.bqa = cv.take<R>((size_t)W * kDP);
+    s.bqb = cv.take<R>((size_t)W * kDP);
+    s.bta = cv.take<R>(W);
+    s.btb = cv.take<R>(W);
+    s.bcnt = cv.take<int>(W);
+    s.boff = cv.take<long long>((size_t)W + 1);
+    s.bhit = cv.take<int>(W);
+    s.U_hist = cv.take<double>(std::max(p->prm.max_iters, 1));
+    s.path = cv.take<R>((size_t)p->path_cap * kDP);
+    s.path_len = cv.take<int>(1);
+    if (base) {
+        s.N = N;
+        s.W = W;
+        s.variant = p->prm.variant;
+        s.cap_f = p->cap_f;
+        s.cap_s = p->cap_s;
+        s.cap_trees = p->cap_trees;
+        s.max_pieces = p->max_pieces;
+        s.path_cap = p->path_cap;
+        s.eta = p->prm.eta;
+        s.res = p->prm.edge_res;
+        s.p_new = p->prm.p_new;
+        s.p_guided = p->prm.p_guided;
+        s.H = p->prm.t_max;
+        s.key0 = (unsigned)(p->prm.seed & 0xffffffffull);
+        s.key1 = (unsigned)(p->prm.seed >> 32);
+        s.problem_id = p->prm.problem_id;
+        for (int j = 0; j < kMaxDof; ++j) {
+            s.qs[j] = j < p->dof ? (R)p->qs[j] : R(0);
+            s.qg[j] = j < p->dof ? (R)p->qg[j] : R(0);
+        }
+        state_of<R>(p) = s;
+    }
+    return cv.off;
+}
+
+template <typename R>
+stp_status create_impl(stp_problem* p) {
+    // Sphere order: stable by frame.
+    std::vector<int> order(p->S);
+    for (int s = 0; s < p->S; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return p->sph[5 * a] < p->sph[5 * b]; });
+    std::vector<int> link_start(kMaxDof + 2, p->S);
+    {
+        int nf = p->arm ? p->dof + 1 : 1;
+        int s = 0;
+        for (int f = 0; f < kMaxDof + 2; ++f) {
+            while (s < p->S && (int)p->sph[5 * order[s]] < f) ++s;
+            link_start[f] = f < nf ? s : p->S;
+            if (f >= nf) link_start[f] = p->S;
+        }
+        link_start[nf] = p->S;
+    }
+    int off_way, off_vel, off_rad;
+    const size_t blob_bytes = blob_layout<R>(p, &off_way, &off_vel, &off_rad);
+    R* blob;
+    unsigned char* gfree;
+    Ctl* ctl;
+    R *qdev, *tdev;
+    int *cnt, *hit;
+    long long* off;
+    const size_t bytes = layout_state<R>(p, nullptr, &blob, blob_bytes, &gfree, &ctl, &qdev, &tdev, &cnt, &off, &hit);
+    cudaError_t e = cudaMalloc(&p->d_arena, bytes);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaMalloc(arena)");
+    p->arena_bytes = bytes;
+    layout_state<R>(p, p->d_arena, &blob, blob_bytes, &gfree, &ctl, &qdev, &tdev, &cnt, &off, &hit);
+    p->d_ctl = ctl;
+    fill_geom<R>(p, geom_of<R>(p), blob, (unsigned)blob_bytes, off_way, off_vel, off_rad, link_start);
+    State<R>& S = state_of<R>(p);
+    cudaStream_t st = p->stream;
+    std::vector<R> hb = blob_host<R>(p, order, blob_bytes, off_way, off_vel, off_rad);
+    STP_CUDA(p, cudaMemcpyAsync(blob, hb.data(), blob_bytes, cudaMemcpyHostToDevice, st));
+    STP_CUDA(p, cudaMemsetAsync(S.tile_cnt, 0, sizeof(int) * (size_t)(p->prm.n_roots + 1) * kMaxQTiles, st));
+    STP_CUDA(p, cudaMemsetAsync(S.btile_cnt, 0, sizeof(int) * 2 * kMaxQTiles, st));
+
+    // Control-block constants computed in double on the host (Eq. goal-time-lower-bound).
+    Ctl hc;
+    std::memset(&hc, 0, sizeof(hc));
+    hc.Lg = p->Lg;
+    hc.H = p->prm.t_max;
+    hc.dt = p->prm.env_dt;
+    hc.kmin = p->kmin;
+    hc.kend = p->kend;
+    hc.nk = p->nk;
+    hc.done = 1;
+    STP_CUDA(p, cudaMemcpyAsync(ctl, &hc, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+
+    // Start check (q_s, 0) and goal checks (q_g, k dt), k = kmin..kmax, in one batch:
+    // entry 0 is the start, entries 1..nk the goal grid.
+    const int ng = p->nk + 1;
+    std::vector<R> hq((size_t)ng * kDP, R(0));
+    std::vector<R> ht(ng);
+    for (int j = 0; j < p->dof; ++j) hq[j] = (R)p->qs[j];
+    ht[0] = R(0);
+    for (int i = 0; i < p->nk; ++i) {
+        for (int j = 0; j < p->dof; ++j) hq[(size_t)(i + 1) * kDP + j] = (R)p->qg[j];
+        ht[i + 1] = (R)((double)(p->kmin + i) * p->prm.env_dt);
+    }
+    R* qall = nullptr;
+    e = cudaMallocAsync(&qall, sizeof(R) * hq.size(), st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaMallocAsync(goal grid)");
+    STP_CUDA(p, cudaMemcpyAsync(qall, hq.data(), sizeof(R) * hq.size(), cudaMemcpyHostToDevice, st));
+    STP_CUDA(p, cudaMemcpyAsync(tdev, ht.data(), sizeof(R) * ng, cudaMemcpyHostToDevice, st));
+    std::vector<int> hcnt(ng, 1);
+    std::vector<long long> hoff(ng + 1);
+    for (int i = 0; i <= ng; ++i) hoff[i] = i;
+    STP_CUDA(p, cudaMemcpyAsync(cnt, hcnt.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, st));
+    STP_CUDA(p, cudaMemcpyAsync(off, hoff.data(), sizeof(long long) * (ng + 1), cudaMemcpyHostToDevice, st));
+    STP_CUDA(p, cudaMemsetAsync(hit, 0, sizeof(int) * ng, st));
+    EdgeBatch<R> E;
+    std::memset(&E, 0, sizeof(E));
+    E.qa = qall;
+    E.qb = qall;
+    E.ta = tdev;
+    E.tb = tdev;
+    E.qstride = kDP;
+    E.cnt = cnt;
+    E.off = off;
+    E.n_host = ng;
+    E.hit = hit;
+    E.err = &ctl->err;
+    STP_CUDA(p, launch_validate<R>(geom_of<R>(p), E, false, true, 0, st));
+    std::vector<int> hh(ng);
+    STP_CUDA(p, cudaMemcpyAsync(hh.data(), hit, sizeof(int) * ng, cudaMemcpyDeviceToHost, st));
+    STP_CUDA(p, cudaFreeAsync(qall, st));
+    STP_CUDA(p, cudaStreamSynchronize(st));
+    p->start_free = hh[0] == 0;
+    std::vector<unsigned char> gf(std::max(p->nk, 1), 0);
+    for (int i = 0; i < p->nk; ++i) gf[i] = hh[i + 1] == 0 ? 1 : 0;
+    STP_CUDA(p, cudaMemcpy(gfree, gf.data(), gf.size(), cudaMemcpyHostToDevice));
+    // Configure the per-iteration launch shapes outside any capture.
+    EdgeBatch<R> E0 = E;
+    E0.n_host = 0;
+    STP_CUDA(p, launch_validate<R>(geom_of<R>(p), E0, false, true, 0, st));
+    STP_CUDA(p, cudaStreamSynchronize(st));
+    return STP_OK;
+}
+
+template <typename R>
+stp_status capture_graph(stp_problem* p) {
+    const int G = p->prm.iters_per_graph > 0 ? p->prm.iters_per_graph : 16;
+    if (p->graph && p->graph_stream == p->stream && p->graph_iters == G) return STP_OK;
+    if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    cudaGraph_t g;
+    STP_CUDA(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (int i = 0; i < G && err == cudaSuccess; ++i)
+        err = launch_iteration<R>(geom_of<R>(p), state_of<R>(p), 0, p->stream);
+    cudaError_t e2 = cudaStreamEndCapture(p->stream, &g);
+    if (err != cudaSuccess) return cuda_fail(p, err, "capture(iteration)");
+    if (e2 != cudaSuccess) return cuda_fail(p, e2, "cudaStreamEndCapture");
+    err = cudaGraphInstantiate(&p->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (err != cudaSuccess) return cuda_fail(p, err, "cudaGraphInstantiate");
+    p->graph_iters = G;
+    p->graph_stream = p->stream;
+    return STP_OK;
+}
+
+template <typename R>
+stp_status plan_impl(stp_problem* p, Ctl* hc) {
+    cudaStream_t st = p->stream;
+    stp_status s = capture_graph<R>(p);
+    if (s != STP_OK) return s;
+    STP_CUDA(p, cudaMemsetAsync(state_of<R>(p).tile_cnt, 0,
+                                sizeof(int) * (size_t)(p->prm.n_roots + 1) * kMaxQTiles, st));
+    STP_CUDA(p, cudaMemsetAsync(state_of<R>(p).btile_cnt, 0, sizeof(int) * 2 * kMaxQTiles, st));
+    STP_CUDA(p, cudaEventRecord(p->ev0, st));
+    STP_CUDA(p, launch_plan_reset<R>(geom_of<R>(p), state_of<R>(p), p->prm.max_iters, st));
+    const int n_launch = (p->prm.max_iters + p->graph_iters - 1) / p->graph_iters;
+    auto t0 = std::chrono::steady_clock::now();
+    for (int i = 0; i < n_launch; ++i) {
+        STP_CUDA(p, cudaGraphLaunch(p->graph, st));
+        if (p->prm.budget_ms > 0) {
+            STP_CUDA(p, cudaStreamSynchronize(st));
+            double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (ms >= p->prm.budget_ms) break;
+        }
+    }
+    STP_CUDA(p, cudaEventRecord(p->ev1, st));
+    STP_CUDA(p, launch_extract_path<R>(state_of<R>(p), p->dof, st));
+    STP_CUDA(p, cudaMemcpyAsync(hc, p->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    STP_CUDA(p, cudaStreamSynchronize(st));
+    return STP_OK;
+}
+
+template <typename R>
+stp_status copy_path(stp_problem* p, int n, double* path, int cap) {
+    if (n > cap) return STP_ERR_CAPACITY;
+    std::vector<R> h((size_t)n * kDP);
+    STP_CUDA(p, cudaMemcpy(h.data(), state_of<R>(p).path, sizeof(R) * h.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < p->dof; ++j) path[(size_t)i * (p->dof + 1) + j] = (double)h[(size_t)i * kDP + j];
+        path[(size_t)i * (p->dof + 1) + p->dof] = (double)h[(size_t)i * kDP + kDP - 1];
+    }
+    return STP_OK;
+}
+
+template <typename R>
+stp_status check_edges_impl(stp_problem* p, int n, const void* qa, const void* ta, const void* qb, const void* tb,
+                            int flags, unsigned char* verdict, void* min_clearance, int* n_checks) {
+    cudaStream_t st = p->stream;
+    const bool dev = (flags & STP_EDGES_DEVICE) != 0;
+    const bool clear = (flags & STP_EDGES_CLEARANCE) != 0;
+    const bool early = (flags & STP_EDGES_NO_EARLY_EXIT) == 0;
+    const int d = p->dof;
+    Carver cv;
+    auto lay = [&](char* base) {
+        cv.off = 0;
+        cv.base = base;
+        struct L {
+            R *qa, *qb, *ta, *tb, *clr;
+            int *cnt, *hit;
+            long long *off, *tmp;
+            unsigned char* ver;
+        } l;
+        l.qa = dev ? nullptr : cv.take<R>((size_t)n * d);
+        l.qb = dev ? nullptr : cv.take<R>((size_t)n * d);
+        l.ta = dev ? nullptr : cv.take<R>(n);
+        l.tb = dev ? nullptr : cv.take<R>(n);
+        l.cnt = cv.take<int>(n);
+        l.off = cv.take<long long>((size_t)n + 1);
+        l.tmp = cv.take<long long>((size_t)n / 4096 + 2);
+        l.hit = cv.take<int>(n);
+        l.clr = clear ? cv.take<R>(n) : nullptr;
+        l.ver = dev ? nullptr : cv.take<unsigned char>(n);
+        return l;
+    };
+    lay(nullptr);
+    if (cv.off > p->scratch_bytes) {
+        if (p->d_scratch) cudaFree(p->d_scratch);
+        p->d_scratch = nullptr;
+        p->scratch_bytes = 0;
+        cudaError_t e = cudaMalloc(&p->d_scratch, cv.off);
+        if (e != cudaSuccess) return cuda_fail(p, e, "cudaMalloc(edge scratch)");
+        p->scratch_bytes = cv.off;
+    }
+    auto L = lay(p->d_scratch);
+    const R* dqa = dev ? (const R*)qa : L.qa;
+    const R* dqb = dev ? (const R*)qb : L.qb;
+    const R* dta = dev ? (const R*)ta : L.ta;
+    const R* dtb = dev ? (const R*)tb : L.tb;
+    if (!dev) {
+        STP_CUDA(p, cudaMemcpyAsync(L.qa, qa, sizeof(R) * n * d, cudaMemcpyHostToDevice, st));
+        STP_CUDA(p, cudaMemcpyAsync(L.qb, qb, sizeof(R) * n * d, cudaMemcpyHostToDevice, st));
+        STP_CUDA(p, cudaMemcpyAsync(L.ta, ta, sizeof(R) * n, cudaMemcpyHostToDevice, st));
+        STP_CUDA(p, cudaMemcpyAsync(L.tb, tb, sizeof(R) * n, cudaMemcpyHostToDevice, st));
+    }
+    STP_CUDA(p, launch_edge_counts<R>(geom_of<R>(p), dqa, dta, dqb, dtb, d, n, p->prm.edge_res, L.cnt, st));
+    STP_CUDA(p, launch_scan_counts(L.cnt, n, L.off, L.tmp, st));
+    STP_CUDA(p, cudaMemsetAsync(L.hit, 0, sizeof(int) * n, st));
+    if (clear) {
+        unsigned long long inf_bits = sizeof(R) == 4 ? 0x7f800000ull : 0x7ff0000000000000ull;
+        STP_CUDA(p, launch_fill(L.clr, n, (int)sizeof(R), inf_bits, st));
+    }
+    EdgeBatch<R> E;
+    std::memset(&E, 0, sizeof(E));
+    E.qa = dqa;
+    E.qb = dqb;
+    E.ta = dta;
+    E.tb = dtb;
+    E.qstride = d;
+    E.cnt = L.cnt;
+    E.off = L.off;
+    E.n_host = n;
+    E.hit = L.hit;
+    E.clear = L.clr;
+    E.err = &p->d_ctl->err;
+    STP_CUDA(p, cudaEventRecord(p->ev2, st));
+    STP_CUDA(p, launch_validate<R>(geom_of<R>(p), E, clear, early, 0, st));
+    STP_CUDA(p, cudaEventRecord(p->ev3, st));
+    unsigned char* dver = dev ? verdict : L.ver;
+    R* dclr = clear ? (dev ? (R*)min_clearance : L.clr) : nullptr;
+    if (clear && dev) {
+        STP_CUDA(p, cudaMemcpyAsync(dclr, L.clr, sizeof(R) * n, cudaMemcpyDeviceToDevice, st));
+    }
+    STP_CUDA(p, launch_finish_batch<R>(n, L.hit, dver, dclr, st));
+    if (!dev) {
+        STP_CUDA(p, cudaMemcpyAsync(verdict, L.ver, n, cudaMemcpyDeviceToHost, st));
+        if (clear && min_clearance)
+            STP_CUDA(p, cudaMemcpyAsync(min_clearance, L.clr, sizeof(R) * n, cudaMemcpyDeviceToHost, st));
+        if (n_checks) STP_CUDA(p, cudaMemcpyAsync(n_checks, L.cnt, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+        STP_CUDA(p, cudaStreamSynchronize(st));
+    } else if (n_checks) {
+        STP_CUDA(p, cudaMemcpyAsync(n_checks, L.cnt, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+    }
+    return STP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* stp_status_string(stp_status s) {
+    switch (s) {
+        case STP_OK: return "STP_OK";
+        case STP_ERR_INVALID: return "STP_ERR_INVALID";
+        case STP_ERR_CAPACITY: return "STP_ERR_CAPACITY";
+        case STP_ERR_CUDA: return "STP_ERR_CUDA";
+        case STP_ERR_TIMEOUT: return "STP_ERR_TIMEOUT";
+        case STP_NO_SOLUTION: return "STP_NO_SOLUTION";
+    }
+    return "STP_UNKNOWN";
+}
+
+const char* stp_last_error(const stp_problem* p) { return p ? p->last_error.c_str() : ""; }
+
+stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, const double* q_start,
+                              const double* q_goal, const stp_params* params, stp_problem** out) {
+    if (!out) return STP_ERR_INVALID;
+    *out = nullptr;
+    if (!robot || !obs || !q_start || !q_goal || !params) return STP_ERR_INVALID;
+    const int d = robot->dof;
+    if (d < 2 || d > kMaxDof) return STP_ERR_INVALID;
+    if (!robot->arm && d > 3) return STP_ERR_INVALID;
+    if (robot->arm && !robot->dh) return STP_ERR_INVALID;
+    if (!robot->q_lo || !robot->q_hi || !robot->spheres) return STP_ERR_INVALID;
+    if (robot->n_spheres < 1 || robot->n_spheres > kMaxSpheres) return STP_ERR_INVALID;
+    if (!(robot->v_max > 0) || !std::isfinite(robot->v_max)) return STP_ERR_INVALID;
+    if (obs->n_obs < 0 || obs->n_obs > kMaxObs || obs->n_way < 1 || obs->n_way > kMaxWay) return STP_ERR_INVALID;
+    if (obs->n_obs > 0 && (!obs->radius || !obs->way)) return STP_ERR_INVALID;
+    const stp_params& P = *params;
+    if (P.variant != 0 && P.variant != 1) return STP_ERR_INVALID;
+    if (P.n_roots < 1 || P.n_roots > kMaxRoots) return STP_ERR_INVALID;
+    if (P.ext_per_iter < 1 || P.ext_per_iter > kMaxWorkers) return STP_ERR_INVALID;
+    if (P.max_iters < 1) return STP_ERR_INVALID;
+    if (!(P.eta > 0) || !(P.edge_res > 0) || !(P.env_dt > 0) || !(P.t_max > 0)) return STP_ERR_INVALID;
+    if (!(P.p_new >= 0 && P.p_new <= 1) || !(P.p_guided >= 0 && P.p_guided <= 1)) return STP_ERR_INVALID;
+    if (P.precision != 0 && P.precision != 1) return STP_ERR_INVALID;
+    if (P.learned != 0 || P.capacity < 0 || P.iters_per_graph < 0) return STP_ERR_INVALID;
+
+    stp_problem* p = new (std::nothrow) stp_problem();
+    if (!p) return STP_ERR_CUDA;
+    p->precision = P.precision;
+    p->prm = P;
+    p->dof = d;
+    p->arm = robot->arm ? 1 : 0;
+    p->S = robot->n_spheres;
+    p->M = obs->n_obs;
+    p->K = obs->n_way;
+    p->vmax = robot->v_max;
+    p->qs.assign(q_start, q_start + d);
+    p->qg.assign(q_goal, q_goal + d);
+    p->qlo.assign(robot->q_lo, robot->q_lo + d);
+    p->qhi.assign(robot->q_hi, robot->q_hi + d);
+    if (p->arm) p->dh.assign(robot->dh, robot->dh + 4 * d);
+    p->sph.assign(robot->spheres, robot->spheres + 5 * p->S);
+    if (p->M > 0) {
+        p->obs_r.assign(obs->radius, obs->radius + p->M);
+        p->way.assign(obs->way, obs->way + (size_t)p->M * p->K * 4);
+    }
+    bool ok = finite_all(p->qs.data(), d) && finite_all(p->qg.data(), d) && finite_all(p->qlo.data(), d) &&
+              finite_all(p->qhi.data(), d) && finite_all(p->sph.data(), p->sph.size()) &&
+              finite_all(p->obs_r.data(), p->obs_r.size()) && finite_all(p->way.data(), p->way.size()) &&
+              finite_all(p->dh.data(), p->dh.size());
+    for (int j = 0; j < d && ok; ++j) ok = p->qlo[j] <= p->qhi[j];
+    for (int s = 0; s < p->S && ok; ++s) {
+        double f = p->sph[5 * s];
+        ok = f == std::floor(f) && f >= 0 && f <= (p->arm ? d : 0) && p->sph[5 * s + 4] >= 0;
+    }
+    for (int m = 0; m < p->M && ok; ++m) {
+        ok = p->obs_r[m] >= 0;
+        for (int k = 1; k < p->K && ok; ++k)
+            ok = p->way[((size_t)m * p->K + k) * 4] > p->way[((size_t)m * p->K + k - 1) * 4];
+    }
+    if (!ok) {
+        delete p;
+        return STP_ERR_INVALID;
+    }
+    // Eq. goal-time-lower-bound.
+    p->Lg = host_dist(p->qs.data(), p->qg.data(), d) / p->vmax;
+    p->kmin = (long long)std::ceil(p->Lg / P.env_dt);
+    p->kmax = (long long)std::floor(P.t_max / P.env_dt);
+    long long nk = p->kmax - p->kmin + 1;
+    if (nk < 0) nk = 0;
+    if (nk > (1LL << 24)) {
+        delete p;
+        return STP_ERR_CAPACITY;
+    }
+    p->nk = (int)nk;
+    p->kend = p->kmin;
+    while ((double)p->kend * P.env_dt < P.t_max) ++p->kend;
+    const long long half = (P.ext_per_iter + 1) / 2;
+    long long cap = P.capacity > 0 ? P.capacity : (long long)P.max_iters * half + 2;
+    long long cap_s = P.capacity > 0 ? P.capacity : 2 * (long long)P.max_iters * half + 2;
+    if (cap > (1LL << 30) || cap_s * P.n_roots > (1LL << 31)) {
+        delete p;
+        return STP_ERR_CAPACITY;
+    }
+    p->cap_f = (int)cap;
+    p->cap_s = (int)cap_s;
+    p->cap_trees = P.variant == 0 ? (int)std::min<long long>(cap_s * P.n_roots / 2 + 1, 1 << 26) : 1;
+    p->max_pieces = std::max(p->nk, 1) + P.n_roots + 1;
+    p->path_cap = (int)std::min<long long>(cap + cap_s, 1 << 20);
+
+    int dev_count = 0;
+    cudaError_t e = cudaGetDeviceCount(&dev_count);
+    if (e != cudaSuccess || dev_count == 0) {
+        p->last_error = "no CUDA device";
+        delete p;
+        return STP_ERR_CUDA;
+    }
+    e = cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete p;
+        return STP_ERR_CUDA;
+    }
+    p->stream = p->own_stream;
+    cudaEventCreate(&p->ev0);
+    cudaEventCreate(&p->ev1);
+    cudaEventCreate(&p->ev2);
+    cudaEventCreate(&p->ev3);
+    stp_status s = p->precision == 0 ? create_impl<float>(p) : create_impl<double>(p);
+    if (s != STP_OK) {
+        stp_free(p);
+        return s;
+    }
+    *out = p;
+    return STP_OK;
+}
+
+stp_status stp_set_stream(stp_problem* p, void* cuda_stream) {
+    if (!p) return STP_ERR_INVALID;
+    p->stream = cuda_stream ? (cudaStream_t)cuda_stream : p->own_stream;
+    return STP_OK;
+}
+
+stp_status stp_plan(stp_problem* p, double* arrival_U, double* length_C, int* n_path, double* path, int cap,
+                    stp_stats* stats) {
+    if (!p) return STP_ERR_INVALID;
+    if (path && cap < 0) return STP_ERR_INVALID;
+    stp_stats st;
+    std::memset(&st, 0, sizeof(st));
+    st.first_solution_iter = -1;
+    st.U = kInfD;
+    st.C = kInfD;
+    const int d = p->dof;
+    bool same = true;
+    for (int j = 0; j < d; ++j) same = same && p->qs[j] == p->qg[j];
+    stp_status result;
+    int np = 0;
+    if (!p->start_free) {
+        result = STP_NO_SOLUTION;
+    } else if (same) {
+        // First line of Algorithms 2 and 3: q_s = q_g and x_s free.
+        st.U = 0.0;
+        st.C = 0.0;
+        st.first_solution_iter = 0;
+        np = 1;
+        if (path) {
+            if (cap < 1) return STP_ERR_CAPACITY;
+            for (int j = 0; j < d; ++j) path[j] = p->qs[j];
+            path[d] = 0.0;
+        }
+        result = STP_OK;
+    } else {
+        Ctl hc;
+        stp_status s = p->precision == 0 ? plan_impl<float>(p, &hc) : plan_impl<double>(p, &hc);
+        if (s != STP_OK) return s;
+        p->planned = true;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+        st.plan_ms = ms;
+        st.iterations = hc.iter;
+        st.first_solution_iter = hc.first_iter;
+        st.nodes = (long long)hc.st_ins;
+        st.edges_validated = (long long)hc.st_ext;
+        st.bridges_validated = (long long)hc.st_bridge;
+        st.root_checks = (long long)hc.st_root;
+        st.check_points = (long long)hc.st_points;
+        st.first_solution_ms = hc.first_iter >= 0 ? (double)(hc.t_first - hc.t_start) * 1e-6 : -1.0;
+        st.U = hc.U;
+        st.C = hc.C;
+        if (hc.err & kErrCapacity) return STP_ERR_CAPACITY;
+        if (hc.err & kErrTimeout) return STP_ERR_TIMEOUT;
+        if (hc.err) return STP_ERR_CUDA;
+        int len = 0;
+        STP_CUDA(p, cudaMemcpy(&len, p->precision == 0 ? p->sf.path_len : p->sd.path_len, sizeof(int),
+                               cudaMemcpyDeviceToHost));
+        if (len < 0) return STP_ERR_CAPACITY;
+        np = len;
+        if (path && np > 0) {
+            stp_status cs = p->precision == 0 ? copy_path<float>(p, np, path, cap) : copy_path<double>(p, np, path, cap);
+            if (cs != STP_OK) return cs;
+        }
+        result = hc.first_iter >= 0 ? STP_OK : STP_NO_SOLUTION;
+    }
+    if (arrival_U) *arrival_U = st.U;
+    if (length_C) *length_C = st.C;
+    if (n_path) *n_path = np;
+    if (stats) *stats = st;
+    return result;
+}
+
+stp_status stp_check_edges(stp_problem* p, int n_edges, const void* qa, const void* ta, const void* qb,
+                           const void* tb, int flags, unsigned char* verdict, void* min_clearance, int* n_checks) {
+    if (!p || n_edges < 0 || n_edges > (1 << 26)) return STP_ERR_INVALID;
+    if (n_edges == 0) return STP_OK;
+    if (!qa || !ta || !qb || !tb || !verdict) return STP_ERR_INVALID;
+    if (min_clearance && !(flags & STP_EDGES_CLEARANCE)) return STP_ERR_INVALID;
+    return p->precision == 0
+               ? check_edges_impl<float>(p, n_edges, qa, ta, qb, tb, flags, verdict, min_clearance, n_checks)
+               : check_edges_impl<double>(p, n_edges, qa, ta, qb, tb, flags, verdict, min_clearance, n_checks);
+}
+
+void stp_free(stp_problem* p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->d_arena) cudaFree(p->d_arena);
+    if (p->d_scratch) cudaFree(p->d_scratch);
+    if (p->ev0) cudaEventDestroy(p->ev0);
+    if (p->ev1) cudaEventDestroy(p->ev1);
+    if (p->ev2) cudaEventDestroy(p->ev2);
+    if (p->ev3) cudaEventDestroy(p->ev3);
+    if (p->own_stream) cudaStreamDestroy(p->own_stream);
+    delete p;
+}
+
+// Milliseconds of the collision kernel in the last stp_check_edges call
+// (CUDA events on the problem's stream).
+stp_status stp_last_validate_ms(stp_problem* p, double* ms) {
+    if (!p || !ms) return STP_ERR_INVALID;
+    float f = 0.f;
+    STP_CUDA(p, cudaEventElapsedTime(&f, p->ev2, p->ev3));
+    *ms = f;
+    return STP_OK;
+}
+
+stp_status stp_tree_size(stp_problem* p, int arena, int* n) {
+    if (!p || !n || arena < -1 || arena >= p->prm.n_roots) return STP_ERR_INVALID;
+    if (!p->planned) {
+        *n = 0;
+        return STP_OK;
+    }
+    Ctl hc;
+    STP_CUDA(p, cudaMemcpy(&hc, p->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    *n = arena < 0 ? hc.n_f : hc.n_s[arena];
+    return STP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename R>
+stp_status tree_nodes_impl(stp_problem* p, int arena, int n, double* x, int* parent, double* troot, double* cost,
+                           int* tree, int* iter) {
+    State<R>& S = state_of<R>(p);
+    const size_t o = arena < 0 ? 0 : (size_t)arena * S.cap_s;
+    std::vector<R> hx((size_t)n * kDP), hc(n), ht(n);
+    std::vector<int> hp(n), htr(n), hi(n);
+    const R* bx = arena < 0 ? S.fx : S.bx + o * kDP;
+    STP_CUDA(p, cudaMemcpy(hx.data(), bx, sizeof(R) * hx.size(), cudaMemcpyDeviceToHost));
+    STP_CUDA(p, cudaMemcpy(hp.data(), arena < 0 ? S.fpar : S.bpar + o, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    STP_CUDA(p, cudaMemcpy(hc.data(), arena < 0 ? S.fcost : S.bcost + o, sizeof(R) * n, cudaMemcpyDeviceToHost));
+    STP_CUDA(p, cudaMemcpy(hi.data(), arena < 0 ? S.fiter : S.biter + o, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    if (arena >= 0) {
+        STP_CUDA(p, cudaMemcpy(ht.data(), S.btroot + o, sizeof(R) * n, cudaMemcpyDeviceToHost));
+        STP_CUDA(p, cudaMemcpy(htr.data(), S.btree + o, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    }
+    const int d = p->dof;
+    for (int i = 0; i < n; ++i) {
+        if (x) {
+            for (int j = 0; j < d; ++j) x[(size_t)i * (d + 1) + j] = (double)hx[(size_t)i * kDP + j];
+            x[(size_t)i * (d + 1) + d] = (double)hx[(size_t)i * kDP + kDP - 1];
+        }
+        if (parent) parent[i] = hp[i];
+        if (cost) cost[i] = (double)hc[i];
+        if (iter) iter[i] = hi[i];
+        if (troot) troot[i] = arena < 0 ? 0.0 : (double)ht[i];
+        if (tree) tree[i] = arena < 0 ? 0 : htr[i];
+    }
+    return STP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+stp_status stp_tree_nodes(stp_problem* p, int arena, double* x, int* parent, double* troot, double* cost, int* tree,
+                          int* iter) {
+    int n = 0;
+    stp_status s = stp_tree_size(p, arena, &n);
+    if (s != STP_OK || n == 0) return s;
+    return p->precision == 0 ? tree_nodes_impl<float>(p, arena, n, x, parent, troot, cost, tree, iter)
+                             : tree_nodes_impl<double>(p, arena, n, x, parent, troot, cost, tree, iter);
+}
+
+stp_status stp_history(stp_problem* p, double* U_hist, int cap, int* n) {
+    if (!p || !n) return STP_ERR_INVALID;
+    *n = 0;
+    if (!p->planned) return STP_OK;
+    Ctl hc;
+    STP_CUDA(p, cudaMemcpy(&hc, p->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    *n = hc.iter;
+    if (U_hist && cap > 0) {
+        const double* src = p->precision == 0 ? p->sf.U_hist : p->sd.U_hist;
+        STP_CUDA(p, cudaMemcpy(U_hist, src, sizeof(double) * std::min(cap, hc.iter), cudaMemcpyDeviceToHost));
+    }
+    return STP_OK;
+}
+
+stp_status stp_slots(stp_problem* p, double* T, int* has_root, int* active, int* gen) {
+    if (!p) return STP_ERR_INVALID;
+    Ctl hc;
+    STP_CUDA(p, cudaMemcpy(&hc, p->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < p->prm.n_roots; ++i) {
+        if (T) T[i] = hc.slot_T[i];
+        if (has_root) has_root[i] = hc.slot_has[i];
+        if (active) active[i] = hc.slot_active[i];
+        if (gen) gen[i] = hc.slot_gen[i];
+    }
+    return STP_OK;
+}
+
+stp_status stp_goal_grid(stp_problem* p, long* kmin, int* n, unsigned char* free_flags, int cap) {
+    if (!p || !kmin || !n) return STP_ERR_INVALID;
+    *kmin = (long)p->kmin;
+    *n = p->nk;
+    if (free_flags && cap > 0 && p->nk > 0) {
+        const unsigned char* src = p->precision == 0 ? p->sf.gfree : p->sd.gfree;
+        STP_CUDA(p, cudaMemcpy(free_flags, src, std::min(cap, p->nk), cudaMemcpyDeviceToHost));
+    }
+    return STP_OK;
+}
+
+}  // extern "C"

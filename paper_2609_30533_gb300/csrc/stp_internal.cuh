@@ -1,0 +1,330 @@
+// Internal device-side definitions of the ST-pRRTC Extend library (sm_103a).
+//
+// Data layout in HBM (one problem):
+//   geometry blob  spheres [S][4] (x,y,z,r; sorted by frame), waypoints
+//                  [M][K][4] (t,x,y,z), segment velocities [M][K][4], radii [M]
+//                  (padded to 4); staged into shared memory by one TMA bulk copy
+//                  per CTA in the collision kernel.
+//   forward arena  SoA: x [cap_f][DP] (q..., zero pad, t at DP-1), parent, cost, iter.
+//   backward arena N segments of cap_s nodes, same SoA plus troot and tree.
+//   worker records SoA over W workers (sample, NN result, x_new, edge entries).
+//   edge entries   SoA over <= 2W entries (root point checks, extensions,
+//                  bridges): endpoints, check count c, prefix offsets, hit flag.
+//   control block  Ctl: iteration counter, incumbent, allocation tables,
+//                  slots, statistics.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stp {
+
+constexpr int kMaxDof = 7;
+constexpr int kDP = 8;          // padded node width for dof > 3
+constexpr int kMaxRoots = 128;  // N
+constexpr int kMaxSpheres = 64;
+constexpr int kMaxObs = 128;
+constexpr int kMaxWay = 8;
+constexpr int kMaxWorkers = 8192;
+constexpr int kQT = 128;        // queries per NN tile (= threads per CTA)
+constexpr int kMaxTiles = 64;   // node tiles per query (partials per query)
+constexpr int kMaxQTiles = kMaxWorkers / kQT;
+constexpr int kNodeTileMin = 256;
+constexpr unsigned kWaitLimit = 1u << 24;  // bounded spin on mbarriers
+
+enum ErrBits { kErrCapacity = 1, kErrTimeout = 2, kErrInternal = 4 };
+
+// ---------------------------------------------------------------------------
+// Geometry (passed by value).
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Geom {
+    int dof, arm, S, M, K, DP;
+    int link_start[kMaxDof + 2];  // spheres of frame j: [link_start[j], link_start[j+1])
+    R a[kMaxDof], d[kMaxDof], ca[kMaxDof], sa[kMaxDof], th0[kMaxDof];
+    R qlo[kMaxDof], qhi[kMaxDof];
+    R vmax;
+    double vmax_d;  // v_max as given (edge check counts are evaluated in double)
+    int uniform_r;  // all robot spheres share one radius
+    const R* blob;
+    unsigned blob_bytes;
+    int off_way, off_vel, off_rad;  // offsets in R units inside the blob
+};
+
+// Flat batch of edges for the collision kernel. Entry e covers check points
+// j = 1..cnt[e] at s = j / cnt[e] of (qa,ta) -> (qb,tb); point g of the flat
+// range belongs to the entry with off[e] <= g < off[e+1].
+template <typename R>
+struct EdgeBatch {
+    const R* qa;
+    const R* qb;
+    const R* ta;
+    const R* tb;
+    int qstride;             // R elements between consecutive edges' q
+    const int* cnt;
+    const long long* off;    // [n+1]
+    const int* n_dev;        // device edge count (planner) or nullptr
+    int n_host;
+    int* hit;                // [n] 0/1
+    R* clear;                // [n] (clearance mode) or nullptr
+    unsigned long long* points_done;  // statistics or nullptr
+    int* err;
+};
+
+// ---------------------------------------------------------------------------
+// Planner control block (device memory).
+// ---------------------------------------------------------------------------
+struct Ctl {
+    int iter, done, err, pad0;
+    int n_f, snap_f, n_trees, n_windows;
+    int n_pieces, first_iter, inc_f, inc_s;
+    int inc_b, max_iters, pad1, pad2;
+    double U, C;
+    // interval-root allocation (double)
+    double Lg, H, dt, Ubar, width;
+    int g_first[kMaxRoots], g_count[kMaxRoots];
+    double g_meas[kMaxRoots];
+    int group_active[kMaxRoots];
+    // root-recycling slots
+    double slot_T[kMaxRoots];
+    long long slot_k[kMaxRoots];
+    int slot_has[kMaxRoots], slot_active[kMaxRoots], slot_gen[kMaxRoots];
+    // goal grid
+    long long kmin, kend;  // checks kmin..kmin+nk-1; recycling roots in [kmin, kend)
+    int nk, pad3;
+    // per-segment counts
+    int n_s[kMaxRoots], snap_s[kMaxRoots];
+    // per-iteration NN bookkeeping
+    int set_count[kMaxRoots + 1];
+    int n_edges, n_bedges, pad4, pad5;
+    // statistics
+    unsigned long long st_ext, st_bridge, st_root, st_ins, st_points;
+    unsigned long long t_start, t_first, t_end;
+};
+
+// Device pointers of one problem's planner state (passed by value).
+template <typename R>
+struct State {
+    Ctl* ctl;
+    int N, W, variant, cap_f, cap_s, cap_trees, max_pieces;
+    double eta, res, p_new, p_guided, H;
+    unsigned key0, key1, problem_id;
+    R qs[kMaxDof], qg[kMaxDof];
+    // forward arena
+    R* fx; int* fpar; R* fcost; int* fiter;
+    // backward arena [N][cap_s]
+    R* bx; int* bpar; R* bcost; R* btroot; int* btree; int* biter;
+    // interval trees
+    int* tree_group; double* tree_T;
+    // allocation tables
+    double* win_lo; double* win_hi; double* pc_lo; double* pc_hi; int* pc_group;
+    // goal grid free flags [nk]
+    unsigned char* gfree;
+    // worker records [W]
+    int* w_status; int* w_set; R* w_xr; double* w_T; int* w_parent; R* w_key; R* w_xnew;
+    int* w_edge; int* w_root_edge; int* w_ins; int* w_bedge;
+    R* w_xn;           // [W][kDP] steering source x_n
+    // NN
+    int* qlist;        // [(N+1)][W]
+    int* tile_cnt;     // [(N+1)][kMaxQTiles]
+    R* part_k1; R* part_k2; int* part_idx;  // [W][kMaxTiles]
+    // bridge
+    int* bq_list;      // [2][W]: workers whose new node bridges to set 0 (fwd) / 1 (bwd concat)
+    int* bq_count;     // [2]
+    int* btile_cnt;    // [2][kMaxQTiles]
+    int* b_set; int* b_idx; R* b_k1; R* b_k2;  // per worker best bridge candidate
+    double* b_U; double* b_C;
+    // edges
+    R* eqa; R* eqb; R* eta_; R* etb; int* ecnt; long long* eoff; int* ehit;  // [2W]
+    R* bqa; R* bqb; R* bta; R* btb; int* bcnt; long long* boff; int* bhit;  // [W]
+    // history
+    double* U_hist;
+    // path
+    R* path; int path_cap; int* path_len;
+};
+
+// ---------------------------------------------------------------------------
+// Small helpers.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R rinf();
+template <>
+__device__ __forceinline__ float rinf<float>() { return __int_as_float(0x7f800000); }
+template <>
+__device__ __forceinline__ double rinf<double>() { return __longlong_as_double(0x7ff0000000000000LL); }
+
+__device__ __forceinline__ void sincos_r(float x, float* s, float* c) {
+    // Reduce to [-pi, pi] by whole turns (the fast intrinsic is accurate there).
+    const float kTwoPi = 6.28318530717958647692f;
+    const float kInvTwoPi = 0.15915494309189533577f;
+    float n = rintf(x * kInvTwoPi);
+    float r = fmaf(-n, kTwoPi, x);
+    __sincosf(r, s, c);
+}
+__device__ __forceinline__ void sincos_r(double x, double* s, double* c) { sincos(x, s, c); }
+
+__device__ __forceinline__ float rsqrt_r(float x) { return sqrtf(x); }
+__device__ __forceinline__ double rsqrt_r(double x) { return sqrt(x); }
+
+// Philox4x32-10 (Salmon et al., SC'11), written from the published definition.
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                              uint32_t k1, uint32_t out[4]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+// ---------------------------------------------------------------------------
+// Ordered-integer encodings so that atomicMin works on floating point.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ord_enc(float v) {
+    int i = __float_as_int(v);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord_dec(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+__device__ __forceinline__ long long ord_enc(double v) {
+    long long i = __double_as_longlong(v);
+    return i >= 0 ? i : i ^ 0x7fffffffffffffffLL;
+}
+__device__ __forceinline__ double ord_dec(long long i) {
+    return __longlong_as_double(i >= 0 ? i : i ^ 0x7fffffffffffffffLL);
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copy + mbarrier (inline PTX).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Global -> shared bulk copy; both addresses 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Bounded wait for phase `parity`; returns false if the limit was reached.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    for (unsigned it = 0; it < kWaitLimit; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// Forward kinematics (standard DH; frame j+1 = frame j Rz(q_j+th0) Tz(d) Tx(a) Rx(alpha)).
+// A frame is stored as columns X, Y, Z and origin o.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Frame {
+    R X[3], Y[3], Z[3], o[3];
+};
+
+template <typename R>
+__device__ __forceinline__ void frame_identity(Frame<R>& F) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        F.X[i] = (i == 0) ? R(1) : R(0);
+        F.Y[i] = (i == 1) ? R(1) : R(0);
+        F.Z[i] = (i == 2) ? R(1) : R(0);
+        F.o[i] = R(0);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void frame_step(Frame<R>& F, R a, R d, R ca, R sa, R theta) {
+    R s, c;
+    sincos_r(theta, &s, &c);
+    R u[3], w[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        u[i] = c * F.X[i] + s * F.Y[i];
+        w[i] = c * F.Y[i] - s * F.X[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        R z = F.Z[i];
+        F.X[i] = u[i];
+        F.Y[i] = ca * w[i] + sa * z;
+        F.Z[i] = ca * z - sa * w[i];
+        F.o[i] = F.o[i] + a * u[i] + d * z;
+    }
+}
+
+// Obstacle position at absolute time t from shared-memory waypoints (t,x,y,z)
+// and per-segment velocities: hold before the first / after the last waypoint.
+template <typename R>
+__device__ __forceinline__ void obstacle_at(const R* way, const R* vel, int K, R t, R& x, R& y, R& z) {
+    R tc = t > way[0] ? t : way[0];
+    int k = 0;
+    for (int j = 1; j < K; ++j)
+        if (way[4 * j] <= tc) k = j;
+    R dtk = tc - way[4 * k];
+    x = way[4 * k + 1] + dtk * vel[4 * k];
+    y = way[4 * k + 2] + dtk * vel[4 * k + 1];
+    z = way[4 * k + 3] + dtk * vel[4 * k + 2];
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (explicitly instantiated in the .cu files).
+// ---------------------------------------------------------------------------
+template <typename R>
+cudaError_t launch_validate(const Geom<R>& g, const EdgeBatch<R>& e, bool clearance, bool early_exit,
+                            int grid_blocks, cudaStream_t st);
+int validate_grid_blocks();
+
+template <typename R>
+cudaError_t launch_edge_counts(const Geom<R>& g, const R* qa, const R* ta, const R* qb, const R* tb, int qstride,
+                               int n, double res, int* cnt, cudaStream_t st);
+cudaError_t launch_scan_counts(const int* cnt, int n, long long* off, long long* block_tmp, cudaStream_t st);
+cudaError_t launch_fill(void* p, long long n, int bytes, unsigned long long v, cudaStream_t st);
+template <typename R>
+cudaError_t launch_finish_batch(int n, const int* hit, unsigned char* verdict, R* clear, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_plan_reset(const Geom<R>& g, const State<R>& s, int max_iters, cudaStream_t st);
+template <typename R>
+cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cudaStream_t st);
+template <typename R>
+cudaError_t launch_extract_path(const State<R>& s, int dof, cudaStream_t st);
+
+}  // namespace stp

@@ -1,0 +1,1341 @@
+// Planner kernels of the batch-synchronous space-time Extend iteration
+// (Algorithm 1 inside Algorithm 2 "IntervalRoot" and Algorithm 3
+// "RootRecycle").
+//
+// One iteration is a fixed sequence of launches (captured into CUDA graphs by
+// the host):
+//   k_sample        one thread per worker: direction, group/slot, goal time T
+//                   (interval root), Philox draws, conditional query sample
+//                   (Eq. conditional-query-time), source-set choice, NN query
+//                   registration.
+//   k_nn            tile scheduler over (tree set, query tile, node tile):
+//                   nodes staged in shared memory, one query per thread,
+//                   argmin of the directed metric (Eq. space-time-metric) or the
+//                   configuration distance; partials reduced by the last CTA of
+//                   each query tile (deterministic, ties to the lowest index).
+//   k_steer         single CTA: steering (Algorithm 1 / Eq. max-speed-extension),
+//                   horizon check, edge entries and their check-point prefix.
+//   k_validate      collision kernel over all extension (and root) checks.
+//   k_insert        single CTA: ordered insertion in worker order, virtual-root
+//                   materialisation, bridge query registration.
+//   k_bridge        tile scheduler: best-ranked admissible vertex of the
+//                   opposite start-of-iteration set (arrival time, then rho).
+//   k_bridge_steer  single CTA: candidate (U, C), improvement test, bridge edges.
+//   k_validate      collision kernel over bridge edges.
+//   k_publish       single CTA: lexicographic min of (U, C, worker), incumbent
+//                   update, interval repartition or root recycling.
+// Every kernel returns at once when the control block says the plan is done.
+#include "stp_internal.cuh"
+
+namespace stp {
+
+constexpr int kSampleThreads = 128;
+constexpr int kCtaThreads = 1024;
+
+enum WorkerStatus { kSkip = 0, kNN = 1, kVirtual = 2 };
+
+__device__ __forceinline__ double uni_d(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+template <typename R>
+__device__ __forceinline__ R uni_r(uint32_t x) {
+    return (R)(x >> 8) * (R)(1.0 / 16777216.0);
+}
+
+template <typename R>
+__device__ __forceinline__ R* fnode(const State<R>& S, int i) {
+    return S.fx + (size_t)i * kDP;
+}
+template <typename R>
+__device__ __forceinline__ R* bnode(const State<R>& S, int seg, int i) {
+    return S.bx + ((size_t)seg * S.cap_s + i) * kDP;
+}
+template <typename R>
+__device__ __forceinline__ size_t bofs(const State<R>& S, int seg, int i) {
+    return (size_t)seg * S.cap_s + i;
+}
+
+template <typename R>
+__device__ __forceinline__ R qdist(const R* a, const R* b, int dof) {
+    R s = R(0);
+    for (int j = 0; j < dof; ++j) {
+        R e = b[j] - a[j];
+        s += e * e;
+    }
+    return rsqrt_r(s);
+}
+
+__device__ __forceinline__ double qdist_d(const double* a, const double* b, int dof) {
+    double s = 0.0;
+    for (int j = 0; j < dof; ++j) {
+        double e = b[j] - a[j];
+        s = __dadd_rn(s, __dmul_rn(e, e));
+    }
+    return sqrt(s);
+}
+
+// Check-point count in double (same reading as the collision batch helper).
+template <typename R>
+__device__ __forceinline__ int check_count(const R* qa, R ta, const R* qb, R tb, int dof, double vmax, double res) {
+    double s2 = 0.0;
+    for (int j = 0; j < dof; ++j) {
+        double e = (double)qb[j] - (double)qa[j];
+        s2 = __dadd_rn(s2, __dmul_rn(e, e));
+    }
+    double L = fmax(sqrt(s2), __dmul_rn(vmax, fabs((double)tb - (double)ta)));
+    double c = ceil(L / res - 1e-3);
+    return c < 1.0 ? 1 : (int)c;
+}
+
+// ---------------------------------------------------------------------------
+// Interval-root allocation (Sec. "Interval Root"), double precision, one thread.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ void build_windows(const State<R>& S) {
+    Ctl* c = S.ctl;
+    int nw = 0;
+    long long k = c->kmin;
+    const long long kmax = c->kmin + c->nk - 1;
+    while (k <= kmax) {
+        if (!S.gfree[k - c->kmin]) {
+            ++k;
+            continue;
+        }
+        long long k0 = k;
+        while (k + 1 <= kmax && S.gfree[k + 1 - c->kmin]) ++k;
+        double lo = __dsub_rn(__dmul_rn((double)k0, c->dt), __dmul_rn(0.5, c->dt));
+        double hi = __dadd_rn(__dmul_rn((double)k, c->dt), __dmul_rn(0.5, c->dt));
+        lo = fmax(lo, c->Lg);
+        hi = fmin(hi, c->H);
+        if (hi > lo) {
+            S.win_lo[nw] = lo;
+            S.win_hi[nw] = hi;
+            ++nw;
+        }
+        ++k;
+    }
+    c->n_windows = nw;
+}
+
+template <typename R>
+__device__ void partition(const State<R>& S, double U) {
+    Ctl* c = S.ctl;
+    const int N = S.N;
+    c->Ubar = fmin(c->H, U);
+    c->width = (c->Ubar - c->Lg) / (double)N;
+    c->n_pieces = 0;
+    for (int g = 0; g < N; ++g) {
+        c->g_first[g] = 0;
+        c->g_count[g] = 0;
+        c->g_meas[g] = 0.0;
+    }
+    // Total guided measure below Ubar.
+    double G = 0.0;
+    for (int i = 0; i < c->n_windows; ++i) {
+        double a = S.win_lo[i];
+        if (a >= c->Ubar) continue;
+        double b = fmin(S.win_hi[i], c->Ubar);
+        if (b > a) G += b - a;
+    }
+    if (G <= 0.0) return;
+    int np = 0;
+    for (int g = 0; g < N; ++g) {
+        double mlo = G * (double)g / (double)N;
+        double mhi = (g == N - 1) ? G : G * (double)(g + 1) / (double)N;
+        c->g_first[g] = np;
+        double m0 = 0.0;
+        for (int i = 0; i < c->n_windows; ++i) {
+            double a = S.win_lo[i];
+            if (a >= c->Ubar) continue;
+            double b = fmin(S.win_hi[i], c->Ubar);
+            if (!(b > a)) continue;
+            // Same summation order as G, so the last window ends exactly at G.
+            double m1 = m0 + (b - a);
+            double x = fmax(mlo, m0), y = fmin(mhi, m1);
+            if (y > x && np < S.max_pieces) {
+                S.pc_lo[np] = a + (x - m0);
+                S.pc_hi[np] = a + (y - m0);
+                S.pc_group[np] = g;
+                c->g_meas[g] += S.pc_hi[np] - S.pc_lo[np];
+                ++np;
+            }
+            m0 = m1;
+        }
+        c->g_count[g] = np - c->g_first[g];
+    }
+    c->n_pieces = np;
+}
+
+template <typename R>
+__device__ double sample_goal_time(const State<R>& S, int g, double u_coin, double u_pos) {
+    const Ctl* c = S.ctl;
+    if (u_coin < S.p_guided && c->g_meas[g] > 0.0) {
+        double p = u_pos * c->g_meas[g];
+        int f = c->g_first[g], n = c->g_count[g];
+        for (int j = 0; j < n; ++j) {
+            double lo = S.pc_lo[f + j], hi = S.pc_hi[f + j];
+            double len = hi - lo;
+            if (p < len || j + 1 == n) return fmin(lo + p, hi);
+            p -= len;
+        }
+    }
+    double lo = c->Lg + (double)g * c->width;
+    return lo + u_pos * c->width;
+}
+
+// ---------------------------------------------------------------------------
+// Root recycling (Algorithm 3), one thread.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ void install_root(const State<R>& S, int slot, double T, int gen, int iter) {
+    R* x = bnode(S, slot, 0);
+    for (int j = 0; j < kDP; ++j) x[j] = R(0);
+    for (int j = 0; j < kMaxDof; ++j) x[j] = S.qg[j];
+    x[kDP - 1] = (R)T;
+    size_t o = bofs(S, slot, 0);
+    S.bpar[o] = -1;
+    S.bcost[o] = R(0);
+    S.btroot[o] = (R)T;
+    S.btree[o] = gen;
+    S.biter[o] = iter;
+    S.ctl->n_s[slot] = 1;
+}
+
+template <typename R>
+__device__ void recycle(const State<R>& S, double U) {
+    Ctl* c = S.ctl;
+    long long kU = c->kmin;
+    while ((double)kU * c->dt < U) ++kU;
+    int donors[kMaxRoots];
+    long long held[kMaxRoots];
+    int m = 0, nh = 0;
+    for (int i = 0; i < S.N; ++i) {
+        if (c->slot_has[i] && c->slot_T[i] >= U) c->slot_active[i] = 0;
+        if (!c->slot_has[i] || c->slot_T[i] > U) donors[m++] = i;
+        if (c->slot_has[i] && c->slot_active[i]) held[nh++] = c->slot_k[i];
+    }
+    const long long KU = kU - c->kmin;
+    for (int j = 0; j < m && KU > 0; ++j) {
+        long long target = c->kmin + ((2LL * j + 1) * KU) / (2LL * m);
+        long long found = -1;
+        for (long long o = 0; o < KU && found < 0; ++o) {
+            for (int side = 0; side < (o == 0 ? 1 : 2); ++side) {
+                long long k = side == 0 ? target - o : target + o;
+                if (k < c->kmin || k >= kU) continue;
+                if (k - c->kmin >= c->nk || !S.gfree[k - c->kmin]) continue;
+                bool h = false;
+                for (int q = 0; q < nh; ++q) h = h || (held[q] == k);
+                if (h) continue;
+                found = k;
+                break;
+            }
+        }
+        if (found < 0) continue;
+        int i = donors[j];
+        c->slot_has[i] = 1;
+        c->slot_active[i] = 1;
+        c->slot_k[i] = found;
+        c->slot_T[i] = (double)found * c->dt;
+        c->slot_gen[i] += 1;
+        held[nh++] = found;
+        install_root(S, i, c->slot_T[i], c->slot_gen[i], c->iter);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reset: fresh trees and allocation for a new plan.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_reset(State<R> S, int max_iters) {
+    Ctl* c = S.ctl;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        c->iter = 0;
+        c->err = 0;
+        c->n_f = 1;
+        c->snap_f = 1;
+        c->n_trees = 0;
+        c->U = __longlong_as_double(0x7ff0000000000000LL);
+        c->C = c->U;
+        c->inc_f = c->inc_s = c->inc_b = -1;
+        c->first_iter = -1;
+        c->max_iters = max_iters;
+        c->n_edges = c->n_bedges = 0;
+        c->st_ext = c->st_bridge = c->st_root = c->st_ins = c->st_points = 0;
+        c->t_start = global_ns();
+        c->t_first = 0;
+        c->t_end = 0;
+        R* x = fnode(S, 0);
+        for (int j = 0; j < kDP; ++j) x[j] = R(0);
+        for (int j = 0; j < kMaxDof; ++j) x[j] = S.qs[j];
+        S.fpar[0] = -1;
+        S.fcost[0] = R(0);
+        S.fiter[0] = -1;
+        S.bq_count[0] = S.bq_count[1] = 0;
+        *S.path_len = 0;
+    }
+    for (int i = t; i <= S.N; i += blockDim.x) c->set_count[i] = 0;
+    for (int i = t; i < S.N; i += blockDim.x) {
+        c->n_s[i] = 0;
+        c->snap_s[i] = 0;
+        c->group_active[i] = 0;
+        c->slot_has[i] = 0;
+        c->slot_active[i] = 0;
+        c->slot_T[i] = __longlong_as_double(0x7ff0000000000000LL);
+        c->slot_k[i] = -1;
+        c->slot_gen[i] = 0;
+    }
+    __syncthreads();
+    if (t == 0) {
+        if (S.variant == 0) {
+            build_windows(S);
+            partition(S, c->U);
+            c->done = (c->Lg < fmin(c->H, c->U)) ? 0 : 1;
+        } else {
+            // Reading (root initialisation): the grid indices of [L_grid, H) are
+            // split into N equal integer ranges; slot i takes the first
+            // collision-free goal check of its range, scanning upward.
+            long long K = c->kend - c->kmin;
+            for (int i = 0; i < S.N; ++i) {
+                long long a = c->kmin + (K * i) / S.N;
+                long long b = c->kmin + (K * (i + 1)) / S.N;
+                for (long long k = a; k < b; ++k) {
+                    if (k - c->kmin < c->nk && S.gfree[k - c->kmin]) {
+                        c->slot_has[i] = 1;
+                        c->slot_active[i] = 1;
+                        c->slot_k[i] = k;
+                        c->slot_T[i] = (double)k * c->dt;
+                        c->slot_gen[i] = 0;
+                        install_root(S, i, c->slot_T[i], 0, -1);
+                        break;
+                    }
+                }
+            }
+            c->done = 0;
+        }
+        if (max_iters <= 0) c->done = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_sample: one thread per worker.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kSampleThreads) k_sample(Geom<R> G, State<R> S) {
+    const Ctl* c = S.ctl;
+    if (c->done) return;
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= S.W) return;
+    const int k = c->iter;
+    const int dof = G.dof;
+    const bool fwd = ((w + k) & 1) == 0;
+    int status = kSkip, set = 0;
+    R* xr = S.w_xr + (size_t)w * kDP;
+    uint32_t d[12];
+    philox4x32_10(0, (uint32_t)w, (uint32_t)k, S.problem_id, S.key0, S.key1, d);
+    philox4x32_10(1, (uint32_t)w, (uint32_t)k, S.problem_id, S.key0, S.key1, d + 4);
+    philox4x32_10(2, (uint32_t)w, (uint32_t)k, S.problem_id, S.key0, S.key1, d + 8);
+    R qr[kMaxDof];
+#pragma unroll
+    for (int j = 0; j < kMaxDof; ++j) qr[j] = (j < dof) ? G.qlo[j] + uni_r<R>(d[4 + j]) * (G.qhi[j] - G.qlo[j]) : R(0);
+
+    if (S.variant == 0) {
+        const int g = (int)(((unsigned long long)(d[0] >> 8) * (unsigned long long)S.N) >> 24);
+        const double T = sample_goal_time(S, g, uni_d(d[1]), uni_d(d[2]));
+        S.w_T[w] = T;
+        const R Tr = (R)T;
+        // Conditional query time (Eq. conditional-query-time).
+        const R lo = qdist(S.qs, qr, dof) / G.vmax;
+        const R hi = Tr - qdist(qr, S.qg, dof) / G.vmax;
+        if (!(lo > hi)) {
+            const R tr = lo + uni_r<R>(d[4 + dof]) * (hi - lo);
+#pragma unroll
+            for (int j = 0; j < kMaxDof; ++j) xr[j] = qr[j];
+            xr[kDP - 1] = tr;
+            set = fwd ? 0 : 1 + g;
+            if (fwd) {
+                status = kNN;
+            } else {
+                const bool use_new = (c->group_active[g] == 0) || (uni_d(d[3]) <= S.p_new);
+                status = use_new ? kVirtual : kNN;
+            }
+        }
+    } else {
+        int slot = -1;
+        if (!fwd) {
+            int n_act = 0;
+            for (int i = 0; i < S.N; ++i) n_act += c->slot_active[i] ? 1 : 0;
+            if (n_act > 0) {
+                int want = (w / 2) % n_act;
+                for (int i = 0; i < S.N; ++i) {
+                    if (c->slot_active[i]) {
+                        if (want == 0) {
+                            slot = i;
+                            break;
+                        }
+                        --want;
+                    }
+                }
+            }
+        }
+        if (fwd || slot >= 0) {
+#pragma unroll
+            for (int j = 0; j < kMaxDof; ++j) xr[j] = qr[j];
+            xr[kDP - 1] = R(0);
+            set = fwd ? 0 : 1 + slot;
+            status = kNN;
+        }
+    }
+    S.w_status[w] = status;
+    S.w_set[w] = set;
+    S.w_parent[w] = -1;
+    if (status == kNN) {
+        int pos = atomicAdd(&S.ctl->set_count[set], 1);
+        S.qlist[(size_t)set * S.W + pos] = w;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tile scheduler shared by the NN and bridge scans.
+// ---------------------------------------------------------------------------
+struct TileSets {
+    int nsets;
+    int pre[kMaxRoots + 2];  // tile prefix per set
+    int nq[kMaxRoots + 1];
+    int nn[kMaxRoots + 1];   // nodes
+    int nt[kMaxRoots + 1];   // node tiles
+    int nts[kMaxRoots + 1];  // nodes per tile
+};
+
+__device__ __forceinline__ void tiles_for(int nq, int n, int& nt, int& nts, int& tiles) {
+    if (n <= 0 || nq <= 0) {
+        nt = 0;
+        nts = 0;
+        tiles = 0;
+        return;
+    }
+    nt = (n + kNodeTileMin - 1) / kNodeTileMin;
+    if (nt > kMaxTiles) nt = kMaxTiles;
+    nts = (n + nt - 1) / nt;
+    nt = (n + nts - 1) / nts;
+    tiles = ((nq + kQT - 1) / kQT) * nt;
+}
+
+// Lexicographic (k1, k2, idx) comparison.
+template <typename R>
+__device__ __forceinline__ bool key_less(R a1, R a2, int ai, R b1, R b2, int bi) {
+    if (a1 != b1) return a1 < b1;
+    if (a2 != b2) return a2 < b2;
+    return ai < bi;
+}
+
+// NN scan. Set 0 = forward arena; set 1+i = backward segment i. DQ = number of
+// configuration coordinates compared (3 or 7; missing ones are zero).
+template <typename R, int DQ>
+__global__ void __launch_bounds__(kQT) k_nn(Geom<R> G, State<R> S) {
+    const Ctl* c = S.ctl;
+    if (c->done) return;
+    __shared__ TileSets ts;
+    __shared__ R sx[kQT][DQ + 2];
+    __shared__ int s_last;
+    const int t = threadIdx.x;
+    const int nsets = S.N + 1;
+    if (t == 0) {
+        int acc = 0;
+        for (int s = 0; s < nsets; ++s) {
+            int nq = c->set_count[s];
+            int n = s == 0 ? c->n_f : c->n_s[s - 1];
+            int nt, nts, tiles;
+            tiles_for(nq, n, nt, nts, tiles);
+            ts.nq[s] = nq;
+            ts.nn[s] = n;
+            ts.nt[s] = nt;
+            ts.nts[s] = nts;
+            ts.pre[s] = acc;
+            acc += tiles;
+        }
+        ts.pre[nsets] = acc;
+    }
+    __syncthreads();
+    const int total = ts.pre[nsets];
+    const R v2 = G.vmax * G.vmax;
+    const double U0 = c->U;
+    const bool interval = S.variant == 0;
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        int s = 0;
+        while (ts.pre[s + 1] <= tile) ++s;
+        const int local = tile - ts.pre[s];
+        const int nt = ts.nt[s];
+        const int qt = local / nt, ntile = local % nt;
+        const int qi = qt * kQT + t;
+        const int w = qi < ts.nq[s] ? S.qlist[(size_t)s * S.W + qi] : -1;
+        R q[DQ], tr = R(0);
+        if (w >= 0) {
+            const R* xr = S.w_xr + (size_t)w * kDP;
+#pragma unroll
+            for (int j = 0; j < DQ; ++j) q[j] = xr[j];
+            tr = xr[kDP - 1];
+        }
+        const int n0 = ntile * ts.nts[s];
+        const int n1 = min(ts.nn[s], n0 + ts.nts[s]);
+        const R* base = s == 0 ? S.fx : S.bx + (size_t)(s - 1) * S.cap_s * kDP;
+        const R* troot = s == 0 ? nullptr : S.btroot + (size_t)(s - 1) * S.cap_s;
+        const bool fwd = s == 0;
+        R best = rinf<R>();
+        int bidx = 0x7fffffff;
+        for (int c0 = n0; c0 < n1; c0 += kQT) {
+            const int cnt = min(kQT, n1 - c0);
+            __syncthreads();
+            if (t < cnt) {
+                const R* x = base + (size_t)(c0 + t) * kDP;
+#pragma unroll
+                for (int j = 0; j < DQ; ++j) sx[t][j] = x[j];
+                sx[t][DQ] = x[kDP - 1];
+                bool active = true;
+                if (interval && !fwd) active = (double)troot[c0 + t] < U0;
+                sx[t][DQ + 1] = active ? R(1) : R(0);
+            }
+            __syncthreads();
+            if (w >= 0) {
+                for (int i = 0; i < cnt; ++i) {
+                    R D2 = R(0);
+#pragma unroll
+                    for (int j = 0; j < DQ; ++j) {
+                        R e = sx[i][j] - q[j];
+                        D2 += e * e;
+                    }
+                    R key;
+                    if (interval) {
+                        const R dt = tr - sx[i][DQ];
+                        const R Delta = fwd ? dt : -dt;
+                        const bool ok = (sx[i][DQ + 1] != R(0)) && (Delta > R(0)) && (D2 <= v2 * Delta * Delta);
+                        key = ok ? D2 + v2 * dt * dt : rinf<R>();
+                    } else {
+                        key = D2;
+                    }
+                    if (key < best) {
+                        best = key;
+                        bidx = c0 + i;
+                    }
+                }
+            }
+        }
+        if (w >= 0) {
+            S.part_k2[(size_t)w * kMaxTiles + ntile] = best;
+            S.part_idx[(size_t)w * kMaxTiles + ntile] = bidx;
+        }
+        __threadfence();
+        __syncthreads();
+        if (t == 0) {
+            int old = atomicAdd(&S.tile_cnt[s * kMaxQTiles + qt], 1);
+            s_last = (old == nt - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            if (w >= 0) {
+                R b = rinf<R>();
+                int bi = 0x7fffffff;
+                for (int j = 0; j < nt; ++j) {
+                    R kk = *(volatile R*)(S.part_k2 + (size_t)w * kMaxTiles + j);
+                    int ii = *(volatile int*)(S.part_idx + (size_t)w * kMaxTiles + j);
+                    if (kk < b || (kk == b && ii < bi)) {
+                        b = kk;
+                        bi = ii;
+                    }
+                }
+                S.w_key[w] = b;
+                S.w_parent[w] = (b < rinf<R>()) ? bi : -1;
+            }
+            if (t == 0) S.tile_cnt[s * kMaxQTiles + qt] = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block-level helpers for the single-CTA kernels.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long cta_exclusive_scan(long long v, long long* sh, long long* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        long long y = lane < nw ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        if (lane < nw) sh[lane] = y;
+    }
+    __syncthreads();
+    const long long before = (warp > 0 ? sh[warp - 1] : 0) + x - v;
+    if (total) *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before;
+}
+
+// ---------------------------------------------------------------------------
+// k_steer: single CTA. Steering, edge entries, check-point prefix.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kCtaThreads) k_steer(Geom<R> G, State<R> S) {
+    Ctl* c = S.ctl;
+    if (c->done) return;
+    __shared__ long long sh[32];
+    const int per = (S.W + kCtaThreads - 1) / kCtaThreads;
+    const int w0 = threadIdx.x * per;
+    const int dof = G.dof;
+    // Pass 1: steer and count entries / points.
+    int n_ent = 0;
+    long long n_pts = 0;
+    for (int w = w0; w < min(S.W, w0 + per); ++w) {
+        S.w_edge[w] = -1;
+        S.w_root_edge[w] = -1;
+        const int st = S.w_status[w];
+        if (st == kSkip) continue;
+        const int set = S.w_set[w];
+        const R* xr = S.w_xr + (size_t)w * kDP;
+        R xn[kDP];
+        if (st == kVirtual) {
+            for (int j = 0; j < kDP; ++j) xn[j] = R(0);
+            for (int j = 0; j < kMaxDof; ++j) xn[j] = S.qg[j];
+            xn[kDP - 1] = (R)S.w_T[w];
+        } else {
+            const int p = S.w_parent[w];
+            if (p < 0) {
+                S.w_status[w] = kSkip;
+                continue;
+            }
+            const R* x = set == 0 ? fnode(S, p) : bnode(S, set - 1, p);
+            for (int j = 0; j < kDP; ++j) xn[j] = x[j];
+        }
+        R* xw = S.w_xnew + (size_t)w * kDP;
+        for (int j = 0; j < kDP; ++j) xw[j] = R(0);
+        R tnew;
+        if (S.variant == 0) {
+            // Algorithm 1: alpha = min(1, eta / rho), x_new = x_n + alpha (x_r - x_n).
+            const R tn = xn[kDP - 1], tr = xr[kDP - 1];
+            const R D = qdist(xn, xr, dof);
+            if (st == kVirtual) {
+                // The virtual root is the sole source: rho must be finite.
+                const R Delta = tn - tr;
+                if (!(Delta > R(0)) || !(D <= G.vmax * Delta)) {
+                    S.w_status[w] = kSkip;
+                    continue;
+                }
+            }
+            const R rho = rsqrt_r((D * D + G.vmax * G.vmax * (tr - tn) * (tr - tn)) / R(2));
+            const R eta = (R)S.eta;
+            const R alpha = (eta / rho) < R(1) ? (eta / rho) : R(1);
+            for (int j = 0; j < dof; ++j) xw[j] = xn[j] + alpha * (xr[j] - xn[j]);
+            tnew = tn + alpha * (tr - tn);
+        } else {
+            // Eq. max-speed-extension: configuration step capped at eta.
+            const R D = qdist(xn, xr, dof);
+            if (!(D > R(0))) {
+                S.w_status[w] = kSkip;
+                continue;
+            }
+            const R eta = (R)S.eta;
+            const R s = (eta / D) < R(1) ? (eta / D) : R(1);
+            for (int j = 0; j < dof; ++j) xw[j] = xn[j] + s * (xr[j] - xn[j]);
+            const R Dn = qdist(xn, xw, dof);
+            tnew = xn[kDP - 1] + (set == 0 ? R(1) : R(-1)) * Dn / G.vmax;
+        }
+        xw[kDP - 1] = tnew;
+        if (tnew < R(0) || tnew > (R)S.H) {
+            S.w_status[w] = kSkip;
+            continue;
+        }
+        // Entries: root check (interval root: the sampled goal state) + extension.
+        if (S.variant == 0) {
+            n_ent += 1;
+            n_pts += 1;
+        }
+        n_ent += 1;
+        n_pts += check_count(xn, xn[kDP - 1], xw, tnew, dof, G.vmax_d, S.res);
+        R* xs = S.w_xn + (size_t)w * kDP;
+        for (int j = 0; j < kDP; ++j) xs[j] = xn[j];
+    }
+    long long tot_e, tot_p;
+    const long long ebase = cta_exclusive_scan(n_ent, sh, &tot_e);
+    const long long pbase = cta_exclusive_scan(n_pts, sh, &tot_p);
+    // Pass 2: write entries.
+    int e = (int)ebase;
+    long long p = pbase;
+    for (int w = w0; w < min(S.W, w0 + per); ++w) {
+        if (S.w_status[w] == kSkip) continue;
+        const R* xn = S.w_xn + (size_t)w * kDP;
+        const R* xw = S.w_xnew + (size_t)w * kDP;
+        if (S.variant == 0) {
+            // point check of (q_g, T)
+            R* qa = S.eqa + (size_t)e * kDP;
+            R* qb = S.eqb + (size_t)e * kDP;
+            for (int j = 0; j < kDP; ++j) qa[j] = qb[j] = R(0);
+            for (int j = 0; j < kMaxDof; ++j) qa[j] = qb[j] = S.qg[j];
+            const R T = (R)S.w_T[w];
+            S.eta_[e] = T;
+            S.etb[e] = T;
+            S.ecnt[e] = 1;
+            S.eoff[e] = p;
+            S.ehit[e] = 0;
+            S.w_root_edge[w] = e;
+            ++e;
+            p += 1;
+        }
+        R* qa = S.eqa + (size_t)e * kDP;
+        R* qb = S.eqb + (size_t)e * kDP;
+        for (int j = 0; j < kDP; ++j) {
+            qa[j] = xn[j];
+            qb[j] = xw[j];
+        }
+        S.eta_[e] = xn[kDP - 1];
+        S.etb[e] = xw[kDP - 1];
+        const int cc = check_count(xn, xn[kDP - 1], xw, xw[kDP - 1], dof, G.vmax_d, S.res);
+        S.ecnt[e] = cc;
+        S.eoff[e] = p;
+        S.ehit[e] = 0;
+        S.w_edge[w] = e;
+        ++e;
+        p += cc;
+    }
+    if (threadIdx.x == 0) {
+        c->n_edges = (int)tot_e;
+        S.eoff[tot_e] = tot_p;
+        if (S.variant == 0) c->st_root += (unsigned long long)S.W;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_insert: single CTA. Ordered insertion in worker order.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kCtaThreads) k_insert(Geom<R> G, State<R> S) {
+    Ctl* c = S.ctl;
+    if (c->done) return;
+    __shared__ int wt[kCtaThreads / 32][kMaxRoots + 1];
+    __shared__ int base[kMaxRoots + 1];
+    __shared__ long long sh[32];
+    __shared__ int tree_base;
+    __shared__ int overflow;
+    __shared__ unsigned long long n_ins_total, n_ext_total;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int nsets = S.N + 1;
+    const int dof = G.dof;
+    for (int s = t; s < nsets; s += blockDim.x) {
+        base[s] = s == 0 ? c->n_f : c->n_s[s - 1];
+        if (s == 0) c->snap_f = c->n_f;
+        else c->snap_s[s - 1] = c->n_s[s - 1];
+    }
+    if (t == 0) {
+        tree_base = c->n_trees;
+        overflow = 0;
+        n_ins_total = 0;
+        n_ext_total = 0;
+    }
+    __syncthreads();
+    for (int r0 = 0; r0 < S.W; r0 += kCtaThreads) {
+        const int w = r0 + t;
+        int ok = 0, nodes = 0, set = -1, virt = 0, ext = 0;
+        if (w < S.W) {
+            const int e = S.w_edge[w];
+            if (e >= 0) {
+                const int re = S.w_root_edge[w];
+                const bool root_ok = re < 0 || S.ehit[re] == 0;
+                ext = root_ok ? 1 : 0;
+                ok = root_ok && S.ehit[e] == 0;
+            }
+            if (ok) {
+                set = S.w_set[w];
+                virt = S.w_status[w] == kVirtual;
+                nodes = virt ? 2 : 1;
+            }
+        }
+        // Rank among earlier lanes of this warp in the same set (weights 1 or 2).
+        const unsigned same = __match_any_sync(0xffffffffu, set);
+        const unsigned lt = (1u << lane) - 1u;
+        const unsigned b0 = __ballot_sync(0xffffffffu, nodes & 1);
+        const unsigned b1 = __ballot_sync(0xffffffffu, (nodes >> 1) & 1);
+        const int in_warp = __popc(same & lt & b0) + 2 * __popc(same & lt & b1);
+        const bool last_of_set = ((same >> lane) >> 1) == 0;  // highest lane of its group
+        for (int s = t; s < (kCtaThreads / 32) * nsets; s += blockDim.x) wt[s / nsets][s % nsets] = 0;
+        __syncthreads();
+        if (set >= 0 && last_of_set) wt[warp][set] = in_warp + nodes;
+        __syncthreads();
+        for (int s = t; s < nsets; s += blockDim.x) {
+            int run = base[s];
+            for (int ww = 0; ww < kCtaThreads / 32; ++ww) {
+                int v = wt[ww][s];
+                wt[ww][s] = run;
+                run += v;
+            }
+            base[s] = run;
+        }
+        // Tree ids for materialised virtual roots, in worker order.
+        long long tot_v;
+        const long long vrank = cta_exclusive_scan(virt, sh, &tot_v);
+        const int my_tree = tree_base + (int)vrank;
+        __syncthreads();
+        if (t == 0) tree_base += (int)tot_v;
+        if (ok) {
+            int idx = wt[warp][set] + in_warp;
+            const R* xw = S.w_xnew + (size_t)w * kDP;
+            if (set == 0) {
+                if (idx + 1 > S.cap_f) {
+                    overflow = 1;
+                } else {
+                    const int p = S.w_parent[w];
+                    R* x = fnode(S, idx);
+                    for (int j = 0; j < kDP; ++j) x[j] = xw[j];
+                    S.fpar[idx] = p;
+                    S.fcost[idx] = S.fcost[p] + qdist(fnode(S, p), xw, dof);
+                    S.fiter[idx] = c->iter;
+                    S.w_ins[w] = idx;
+                    int pos = atomicAdd(&S.bq_count[1], 1);
+                    S.bq_list[S.W + pos] = w;
+                }
+            } else {
+                const int seg = set - 1;
+                if (idx + nodes > S.cap_s || (virt && my_tree >= S.cap_trees)) {
+                    overflow = 1;
+                } else {
+                    int p;
+                    if (virt) {
+                        const double T = S.w_T[w];
+                        R* x = bnode(S, seg, idx);
+                        for (int j = 0; j < kDP; ++j) x[j] = R(0);
+                        for (int j = 0; j < kMaxDof; ++j) x[j] = S.qg[j];
+                        x[kDP - 1] = (R)T;
+                        size_t o = bofs(S, seg, idx);
+                        S.bpar[o] = -1;
+                        S.bcost[o] = R(0);
+                        S.btroot[o] = (R)T;
+                        S.btree[o] = my_tree;
+                        S.biter[o] = c->iter;
+                        S.tree_group[my_tree] = seg;
+                        S.tree_T[my_tree] = (double)(R)T;  // as stored in the nodes
+                        atomicAdd(&c->group_active[seg], 1);
+                        p = idx;
+                        ++idx;
+                    } else {
+                        p = S.w_parent[w];
+                    }
+                    R* x = bnode(S, seg, idx);
+                    for (int j = 0; j < kDP; ++j) x[j] = xw[j];
+                    const size_t o = bofs(S, seg, idx), op = bofs(S, seg, p);
+                    S.bpar[o] = p;
+                    S.bcost[o] = S.bcost[op] + qdist(bnode(S, seg, p), xw, dof);
+                    S.btroot[o] = S.btroot[op];
+                    S.btree[o] = S.btree[op];
+                    S.biter[o] = c->iter;
+                    S.w_ins[w] = idx;
+                    int pos = atomicAdd(&S.bq_count[0], 1);
+                    S.bq_list[pos] = w;
+                }
+            }
+        } else if (w < S.W) {
+            S.w_ins[w] = -1;
+        }
+        // statistics
+        const unsigned bo = __ballot_sync(0xffffffffu, ok);
+        const unsigned be = __ballot_sync(0xffffffffu, ext);
+        if (lane == 0) {
+            atomicAdd(&n_ins_total, (unsigned long long)__popc(bo));
+            atomicAdd(&n_ext_total, (unsigned long long)__popc(be));
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int s = t; s < nsets; s += blockDim.x) {
+        if (s == 0) c->n_f = min(base[0], S.cap_f);
+        else c->n_s[s - 1] = min(base[s], S.cap_s);
+    }
+    if (t == 0) {
+        c->n_trees = min(tree_base, S.cap_trees);
+        c->st_ins += n_ins_total;
+        c->st_ext += n_ext_total;
+        if (overflow) {
+            c->err |= kErrCapacity;
+            c->done = 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_bridge: best-ranked admissible vertex of the opposite start-of-iteration set.
+// Set 0: queries = backward-inserted nodes, vertices = forward arena [0, snap_f).
+// Set 1: queries = forward-inserted nodes, vertices = all backward segments
+//        [0, snap_s[i]) concatenated in segment order; active iff troot < U.
+// Rank: (arrival time, rho^2, index) lexicographic.
+// ---------------------------------------------------------------------------
+template <typename R, int DQ>
+__global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
+    const Ctl* c = S.ctl;
+    if (c->done) return;
+    __shared__ int seg_pre[kMaxRoots + 1];
+    __shared__ int s_nq[2], s_nn[2], s_nt[2], s_nts[2], s_pre[3];
+    __shared__ R sx[kQT][DQ + 2];
+    __shared__ int s_last;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        int acc = 0;
+        for (int i = 0; i < S.N; ++i) {
+            seg_pre[i] = acc;
+            acc += c->snap_s[i];
+        }
+        seg_pre[S.N] = acc;
+        int tacc = 0;
+        for (int s = 0; s < 2; ++s) {
+            int nq = S.bq_count[s];
+            int n = s == 0 ? c->snap_f : acc;
+            int nt, nts, tiles;
+            tiles_for(nq, n, nt, nts, tiles);
+            s_nq[s] = nq;
+            s_nn[s] = n;
+            s_nt[s] = nt;
+            s_nts[s] = nts;
+            s_pre[s] = tacc;
+            tacc += tiles;
+        }
+        s_pre[2] = tacc;
+    }
+    __syncthreads();
+    const int total = s_pre[2];
+    const R v2 = G.vmax * G.vmax;
+    const double U0 = c->U;
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int s = tile < s_pre[1] ? 0 : 1;
+        const int local = tile - s_pre[s];
+        const int nt = s_nt[s];
+        const int qt = local / nt, ntile = local % nt;
+        const int qi = qt * kQT + t;
+        const int w = qi < s_nq[s] ? S.bq_list[(size_t)s * S.W + qi] : -1;
+        R q[DQ], tq = R(0);
+        if (w >= 0) {
+            const R* xq = S.w_xnew + (size_t)w * kDP;
+#pragma unroll
+            for (int j = 0; j < DQ; ++j) q[j] = xq[j];
+            tq = xq[kDP - 1];
+        }
+        const int n0 = ntile * s_nts[s];
+        const int n1 = min(s_nn[s], n0 + s_nts[s]);
+        R b1 = rinf<R>(), b2 = rinf<R>();
+        int bidx = 0x7fffffff;
+        for (int c0 = n0; c0 < n1; c0 += kQT) {
+            const int cnt = min(kQT, n1 - c0);
+            __syncthreads();
+            if (t < cnt) {
+                const int li = c0 + t;
+                const R* x;
+                R tro = R(0);
+                bool active = true;
+                if (s == 0) {
+                    x = fnode(S, li);
+                } else {
+                    int sg = 0;
+                    while (seg_pre[sg + 1] <= li) ++sg;
+                    const int i = li - seg_pre[sg];
+                    x = bnode(S, sg, i);
+                    tro = S.btroot[bofs(S, sg, i)];
+                    active = (double)tro < U0;
+                }
+#pragma unroll
+                for (int j = 0; j < DQ; ++j) sx[t][j] = x[j];
+                sx[t][DQ] = x[kDP - 1];
+                sx[t][DQ + 1] = active ? tro : rinf<R>();
+            }
+            __syncthreads();
+            if (w >= 0) {
+                for (int i = 0; i < cnt; ++i) {
+                    const R tro = sx[i][DQ + 1];
+                    if (!(tro < rinf<R>())) continue;
+                    R D2 = R(0);
+#pragma unroll
+                    for (int j = 0; j < DQ; ++j) {
+                        R e = sx[i][j] - q[j];
+                        D2 += e * e;
+                    }
+                    // s = 0: vertex earlier than the query; s = 1: later.
+                    const R dt = s == 0 ? tq - sx[i][DQ] : sx[i][DQ] - tq;
+                    if (!(dt > R(0)) || !(D2 <= v2 * dt * dt)) continue;
+                    const R k2 = D2 + v2 * dt * dt;
+                    const R k1 = s == 0 ? R(0) : tro;
+                    if (key_less(k1, k2, c0 + i, b1, b2, bidx)) {
+                        b1 = k1;
+                        b2 = k2;
+                        bidx = c0 + i;
+                    }
+                }
+            }
+        }
+        if (w >= 0) {
+            S.part_k1[(size_t)w * kMaxTiles + ntile] = b1;
+            S.part_k2[(size_t)w * kMaxTiles + ntile] = b2;
+            S.part_idx[(size_t)w * kMaxTiles + ntile] = bidx;
+        }
+        __threadfence();
+        __syncthreads();
+        if (t == 0) {
+            int old = atomicAdd(&S.btile_cnt[s * kMaxQTiles + qt], 1);
+            s_last = (old == nt - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            if (w >= 0) {
+                R k1 = rinf<R>(), k2 = rinf<R>();
+                int bi = 0x7fffffff;
+                for (int j = 0; j < nt; ++j) {
+                    R a1 = *(volatile R*)(S.part_k1 + (size_t)w * kMaxTiles + j);
+                    R a2 = *(volatile R*)(S.part_k2 + (size_t)w * kMaxTiles + j);
+                    int ai = *(volatile int*)(S.part_idx + (size_t)w * kMaxTiles + j);
+                    if (key_less(a1, a2, ai, k1, k2, bi)) {
+                        k1 = a1;
+                        k2 = a2;
+                        bi = ai;
+                    }
+                }
+                if (k2 < rinf<R>()) {
+                    if (s == 0) {
+                        S.b_set[w] = -1;
+                        S.b_idx[w] = bi;
+                    } else {
+                        int sg = 0;
+                        while (seg_pre[sg + 1] <= bi) ++sg;
+                        S.b_set[w] = sg;
+                        S.b_idx[w] = bi - seg_pre[sg];
+                    }
+                }
+            }
+            if (t == 0) S.btile_cnt[s * kMaxQTiles + qt] = 0;
+        }
+    }
+}
+
+// Clears the per-worker bridge results before k_bridge.
+template <typename R>
+__global__ void k_bridge_clear(State<R> S) {
+    if (S.ctl->done) return;
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < S.W) {
+        S.b_idx[w] = -1;
+        S.w_bedge[w] = -1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_bridge_steer: candidate (U, C); bridge edge if it improves (U0, C0).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kCtaThreads) k_bridge_steer(Geom<R> G, State<R> S) {
+    Ctl* c = S.ctl;
+    if (c->done) return;
+    __shared__ long long sh[32];
+    const int per = (S.W + kCtaThreads - 1) / kCtaThreads;
+    const int w0 = threadIdx.x * per;
+    const int dof = G.dof;
+    const double U0 = c->U, C0 = c->C;
+    int n_ent = 0;
+    long long n_pts = 0;
+    for (int w = w0; w < min(S.W, w0 + per); ++w) {
+        S.w_bedge[w] = -1;
+        if (S.w_ins[w] < 0 || S.b_idx[w] < 0) continue;
+        const bool fwd = S.w_set[w] == 0;
+        const R* f;
+        const R* b;
+        R cf, cb, troot;
+        if (fwd) {
+            f = fnode(S, S.w_ins[w]);
+            cf = S.fcost[S.w_ins[w]];
+            const size_t o = bofs(S, S.b_set[w], S.b_idx[w]);
+            b = bnode(S, S.b_set[w], S.b_idx[w]);
+            cb = S.bcost[o];
+            troot = S.btroot[o];
+        } else {
+            const int seg = S.w_set[w] - 1;
+            const size_t o = bofs(S, seg, S.w_ins[w]);
+            b = bnode(S, seg, S.w_ins[w]);
+            cb = S.bcost[o];
+            troot = S.btroot[o];
+            f = fnode(S, S.b_idx[w]);
+            cf = S.fcost[S.b_idx[w]];
+        }
+        const R D = qdist(f, b, dof);
+        const double Uc = (double)troot;
+        const double Cc = ((double)cf + (double)D) + (double)cb;
+        const bool improves = (Uc < U0) || (Uc == U0 && Cc < C0);
+        if (!improves) continue;
+        S.b_U[w] = Uc;
+        S.b_C[w] = Cc;
+        n_ent += 1;
+        n_pts += check_count(f, f[kDP - 1], b, b[kDP - 1], dof, G.vmax_d, S.res);
+    }
+    long long tot_e, tot_p;
+    const long long ebase = cta_exclusive_scan(n_ent, sh, &tot_e);
+    const long long pbase = cta_exclusive_scan(n_pts, sh, &tot_p);
+    int e = (int)ebase;
+    long long p = pbase;
+    for (int w = w0; w < min(S.W, w0 + per); ++w) {
+        if (S.w_ins[w] < 0 || S.b_idx[w] < 0) continue;
+        const bool fwd = S.w_set[w] == 0;
+        const R* f;
+        const R* b;
+        R cf, cb, troot;
+        if (fwd) {
+            f = fnode(S, S.w_ins[w]);
+            cf = S.fcost[S.w_ins[w]];
+            const size_t o = bofs(S, S.b_set[w], S.b_idx[w]);
+            b = bnode(S, S.b_set[w], S.b_idx[w]);
+            cb = S.bcost[o];
+            troot = S.btroot[o];
+        } else {
+            const int seg = S.w_set[w] - 1;
+            const size_t o = bofs(S, seg, S.w_ins[w]);
+            b = bnode(S, seg, S.w_ins[w]);
+            cb = S.bcost[o];
+            troot = S.btroot[o];
+            f = fnode(S, S.b_idx[w]);
+            cf = S.fcost[S.b_idx[w]];
+        }
+        const R D = qdist(f, b, dof);
+        const double Uc = (double)troot;
+        const double Cc = ((double)cf + (double)D) + (double)cb;
+        const bool improves = (Uc < U0) || (Uc == U0 && Cc < C0);
+        if (!improves) continue;
+        R* qa = S.bqa + (size_t)e * kDP;
+        R* qb = S.bqb + (size_t)e * kDP;
+        for (int j = 0; j < kDP; ++j) {
+            qa[j] = f[j];
+            qb[j] = b[j];
+        }
+        S.bta[e] = f[kDP - 1];
+        S.btb[e] = b[kDP - 1];
+        const int cc = check_count(f, f[kDP - 1], b, b[kDP - 1], dof, G.vmax_d, S.res);
+        S.bcnt[e] = cc;
+        S.boff[e] = p;
+        S.bhit[e] = 0;
+        S.w_bedge[w] = e;
+        ++e;
+        p += cc;
+    }
+    if (threadIdx.x == 0) {
+        c->n_bedges = (int)tot_e;
+        S.boff[tot_e] = tot_p;
+        c->st_bridge += (unsigned long long)tot_e;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_publish: lexicographic min of (U, C, worker); incumbent; allocation update.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) {
+    Ctl* c = S.ctl;
+    if (c->done) return;
+    __shared__ double rU[kCtaThreads / 32], rC[kCtaThreads / 32];
+    __shared__ int rW[kCtaThreads / 32];
+    __shared__ int s_counts[kMaxRoots];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    double bU = __longlong_as_double(0x7ff0000000000000LL), bC = bU;
+    int bw = 0x7fffffff;
+    for (int w = t; w < S.W; w += blockDim.x) {
+        const int e = S.w_bedge[w];
+        if (e < 0 || S.bhit[e]) continue;
+        const double U = S.b_U[w], C = S.b_C[w];
+        if (U < bU || (U == bU && (C < bC || (C == bC && w < bw)))) {
+            bU = U;
+            bC = C;
+            bw = w;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        double U = __shfl_xor_sync(0xffffffffu, bU, o);
+        double C = __shfl_xor_sync(0xffffffffu, bC, o);
+        int ww = __shfl_xor_sync(0xffffffffu, bw, o);
+        if (U < bU || (U == bU && (C < bC || (C == bC && ww < bw)))) {
+            bU = U;
+            bC = C;
+            bw = ww;
+        }
+    }
+    if (lane == 0) {
+        rU[warp] = bU;
+        rC[warp] = bC;
+        rW[warp] = bw;
+    }
+    __syncthreads();
+    __shared__ int s_decreased;
+    if (t == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            if (rU[i] < bU || (rU[i] == bU && (rC[i] < bC || (rC[i] == bC && rW[i] < bw)))) {
+                bU = rU[i];
+                bC = rC[i];
+                bw = rW[i];
+            }
+        }
+        s_decreased = 0;
+        if (bw != 0x7fffffff) {
+            s_decreased = bU < c->U;
+            c->U = bU;
+            c->C = bC;
+            if (S.w_set[bw] == 0) {
+                c->inc_f = S.w_ins[bw];
+                c->inc_s = S.b_set[bw];
+                c->inc_b = S.b_idx[bw];
+            } else {
+                c->inc_f = S.b_idx[bw];
+                c->inc_s = S.w_set[bw] - 1;
+                c->inc_b = S.w_ins[bw];
+            }
+            if (c->first_iter < 0) {
+                c->first_iter = c->iter;
+                c->t_first = global_ns();
+            }
+        }
+    }
+    __syncthreads();
+    if (s_decreased) {
+        if (S.variant == 0) {
+            // Repartition; trees rooted at T >= U become inactive.
+            for (int i = t; i < S.N; i += blockDim.x) s_counts[i] = 0;
+            __syncthreads();
+            for (int i = t; i < c->n_trees; i += blockDim.x)
+                if (S.tree_T[i] < c->U) atomicAdd(&s_counts[S.tree_group[i]], 1);
+            __syncthreads();
+            for (int i = t; i < S.N; i += blockDim.x) c->group_active[i] = s_counts[i];
+            if (t == 0) partition(S, c->U);
+        } else if (t == 0) {
+            recycle(S, c->U);
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        S.U_hist[c->iter] = c->U;
+        c->iter += 1;
+        c->n_edges = 0;
+        c->n_bedges = 0;
+        S.bq_count[0] = S.bq_count[1] = 0;
+        bool stop = c->iter >= c->max_iters || c->err != 0;
+        if (S.variant == 0 && !(c->Lg < fmin(c->H, c->U))) stop = true;
+        if (stop) {
+            c->done = 1;
+            c->t_end = global_ns();
+        }
+    }
+    for (int i = t; i <= S.N; i += blockDim.x) c->set_count[i] = 0;
+}
+
+// Path: forward chain from the start root to inc_f, then backward chain from
+// inc_b to its root. One thread.
+template <typename R>
+__global__ void k_extract_path(State<R> S) {
+    const Ctl* c = S.ctl;
+    int n = 0;
+    if (c->inc_f >= 0) {
+        int len_f = 0;
+        for (int i = c->inc_f; i >= 0; i = S.fpar[i]) ++len_f;
+        int len_b = 0;
+        for (int i = c->inc_b; i >= 0; i = S.bpar[bofs(S, c->inc_s, i)]) ++len_b;
+        if (len_f + len_b <= S.path_cap) {
+            int k = len_f - 1;
+            for (int i = c->inc_f; i >= 0; i = S.fpar[i], --k) {
+                for (int j = 0; j < kDP; ++j) S.path[(size_t)k * kDP + j] = fnode(S, i)[j];
+            }
+            k = len_f;
+            for (int i = c->inc_b; i >= 0; i = S.bpar[bofs(S, c->inc_s, i)], ++k) {
+                for (int j = 0; j < kDP; ++j) S.path[(size_t)k * kDP + j] = bnode(S, c->inc_s, i)[j];
+            }
+            n = len_f + len_b;
+        } else {
+            n = -(len_f + len_b);
+        }
+    }
+    *S.path_len = n;
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------
+template <typename R>
+static EdgeBatch<R> ext_batch(const State<R>& S) {
+    EdgeBatch<R> E;
+    E.qa = S.eqa;
+    E.qb = S.eqb;
+    E.ta = S.eta_;
+    E.tb = S.etb;
+    E.qstride = kDP;
+    E.cnt = S.ecnt;
+    E.off = S.eoff;
+    E.n_dev = &S.ctl->n_edges;
+    E.n_host = 0;
+    E.hit = S.ehit;
+    E.clear = nullptr;
+    E.points_done = &S.ctl->st_points;
+    E.err = &S.ctl->err;
+    return E;
+}
+
+template <typename R>
+static EdgeBatch<R> bridge_batch(const State<R>& S) {
+    EdgeBatch<R> E;
+    E.qa = S.bqa;
+    E.qb = S.bqb;
+    E.ta = S.bta;
+    E.tb = S.btb;
+    E.qstride = kDP;
+    E.cnt = S.bcnt;
+    E.off = S.boff;
+    E.n_dev = &S.ctl->n_bedges;
+    E.n_host = 0;
+    E.hit = S.bhit;
+    E.clear = nullptr;
+    E.points_done = &S.ctl->st_points;
+    E.err = &S.ctl->err;
+    return E;
+}
+
+template <typename R>
+cudaError_t launch_plan_reset(const Geom<R>& g, const State<R>& s, int max_iters, cudaStream_t st) {
+    k_reset<R><<<1, 256, 0, st>>>(s, max_iters);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cudaStream_t st) {
+    const int nn_grid = 2 * validate_grid_blocks();
+    k_sample<R><<<(s.W + kSampleThreads - 1) / kSampleThreads, kSampleThreads, 0, st>>>(g, s);
+    if (g.dof <= 3) k_nn<R, 3><<<nn_grid, kQT, 0, st>>>(g, s);
+    else k_nn<R, kMaxDof><<<nn_grid, kQT, 0, st>>>(g, s);
+    k_steer<R><<<1, kCtaThreads, 0, st>>>(g, s);
+    cudaError_t err = launch_validate<R>(g, ext_batch(s), false, true, vgrid, st);
+    if (err != cudaSuccess) return err;
+    k_insert<R><<<1, kCtaThreads, 0, st>>>(g, s);
+    k_bridge_clear<R><<<(s.W + 255) / 256, 256, 0, st>>>(s);
+    if (g.dof <= 3) k_bridge<R, 3><<<nn_grid, kQT, 0, st>>>(g, s);
+    else k_bridge<R, kMaxDof><<<nn_grid, kQT, 0, st>>>(g, s);
+    k_bridge_steer<R><<<1, kCtaThreads, 0, st>>>(g, s);
+    err = launch_validate<R>(g, bridge_batch(s), false, true, vgrid, st);
+    if (err != cudaSuccess) return err;
+    k_publish<R><<<1, kCtaThreads, 0, st>>>(g, s);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_extract_path(const State<R>& s, int dof, cudaStream_t st) {
+    k_extract_path<R><<<1, 1, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_plan_reset<float>(const Geom<float>&, const State<float>&, int, cudaStream_t);
+template cudaError_t launch_plan_reset<double>(const Geom<double>&, const State<double>&, int, cudaStream_t);
+template cudaError_t launch_iteration<float>(const Geom<float>&, const State<float>&, int, cudaStream_t);
+template cudaError_t launch_iteration<double>(const Geom<double>&, const State<double>&, int, cudaStream_t);
+template cudaError_t launch_extract_path<float>(const State<float>&, int, cudaStream_t);
+template cudaError_t launch_extract_path<double>(const State<double>&, int, cudaStream_t);
+
+}  // namespace stp

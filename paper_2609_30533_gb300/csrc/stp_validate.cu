@@ -1,0 +1,374 @@
+// Edge validation kernel (collision checking of space-time edges against
+// moving obstacles; Sec. "Simulation Protocol": obstacle positions are
+// interpolated at each absolute query time) and the flat-batch helpers.
+//
+// Mapping: a persistent grid walks the flat list of check points of a batch
+// of edges; each warp takes 32 consecutive points (one point per lane). A
+// lane evaluates one check point completely: interpolate the edge in (q, t),
+// run forward kinematics once, and test every robot sphere against every
+// obstacle sphere. Obstacle positions at the lane's time are held in
+// registers in chunks of MO obstacles; FK is amortised over all pairs.
+// Robot spheres and obstacle trajectories are staged into shared memory by a
+// single TMA bulk copy per CTA. FP32 CUDA-core arithmetic (no tensor cores:
+// the pair tests are not a contraction).
+//
+// Algorithmic work per check point: S*M pair tests (8 flops each: 3 sub,
+// 1 mul, 2 fma) + S sphere transforms + FK (d joint steps) + M interpolations.
+#include "stp_internal.cuh"
+
+namespace stp {
+
+template <typename R, int MO, bool CLEAR>
+__device__ __forceinline__ void test_sphere(R cx, R cy, R cz, R rs, const R (&ox)[MO], const R (&oy)[MO],
+                                            const R (&oz)[MO], const R (&orr)[MO], bool& hit, R& clr) {
+#pragma unroll
+    for (int j = 0; j < MO; ++j) {
+        R dx = cx - ox[j];
+        R dy = cy - oy[j];
+        R dz = cz - oz[j];
+        R d2 = dx * dx + dy * dy + dz * dz;
+        R rr = rs + orr[j];
+        if (CLEAR) {
+            R cl = rsqrt_r(d2) - rr;
+            clr = cl < clr ? cl : clr;
+        }
+        hit = hit || (d2 < rr * rr);
+    }
+}
+
+template <typename R, bool ARM, int MO, bool CLEAR, bool EARLY>
+__device__ __forceinline__ void check_point(const Geom<R>& G, const R* sm, const R (&q)[kMaxDof], R t, bool& hit,
+                                            R& clr) {
+    const R* sph = sm;
+    const R* way = sm + G.off_way;
+    const R* vel = sm + G.off_vel;
+    const R* rad = sm + G.off_rad;
+    for (int m0 = 0; m0 < G.M; m0 += MO) {
+        R ox[MO], oy[MO], oz[MO], orr[MO];
+#pragma unroll
+        for (int j = 0; j < MO; ++j) {
+            int m = m0 + j;
+            if (m < G.M) {
+                obstacle_at(way + 4 * G.K * m, vel + 4 * G.K * m, G.K, t, ox[j], oy[j], oz[j]);
+                orr[j] = rad[m];
+            } else {
+                ox[j] = oy[j] = oz[j] = R(1e18);
+                orr[j] = R(0);
+            }
+        }
+        if (!ARM) {
+            R px = q[0], py = q[1], pz = (G.dof > 2) ? q[2] : R(0);
+            for (int s = 0; s < G.S; ++s) {
+                test_sphere<R, MO, CLEAR>(px + sph[4 * s], py + sph[4 * s + 1], pz + sph[4 * s + 2], sph[4 * s + 3],
+                                          ox, oy, oz, orr, hit, clr);
+            }
+        } else {
+            Frame<R> F;
+            frame_identity(F);
+            for (int j = 0; j <= G.dof; ++j) {
+                if (j > 0) frame_step(F, G.a[j - 1], G.d[j - 1], G.ca[j - 1], G.sa[j - 1], q[j - 1] + G.th0[j - 1]);
+                for (int s = G.link_start[j]; s < G.link_start[j + 1]; ++s) {
+                    R px = sph[4 * s], py = sph[4 * s + 1], pz = sph[4 * s + 2];
+                    R cx = F.o[0] + px * F.X[0] + py * F.Y[0] + pz * F.Z[0];
+                    R cy = F.o[1] + px * F.X[1] + py * F.Y[1] + pz * F.Z[1];
+                    R cz = F.o[2] + px * F.X[2] + py * F.Y[2] + pz * F.Z[2];
+                    test_sphere<R, MO, CLEAR>(cx, cy, cz, sph[4 * s + 3], ox, oy, oz, orr, hit, clr);
+                }
+                if (EARLY && !CLEAR && hit) break;
+            }
+        }
+        if (EARLY && !CLEAR && hit) break;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void atomic_min_r(R* addr, R v);
+template <>
+__device__ __forceinline__ void atomic_min_r<float>(float* addr, float v) {
+    atomicMin(reinterpret_cast<int*>(addr), ord_enc(v));
+}
+template <>
+__device__ __forceinline__ void atomic_min_r<double>(double* addr, double v) {
+    atomicMin(reinterpret_cast<long long*>(addr), ord_enc(v));
+}
+
+template <typename R, bool ARM, int MO, bool CLEAR, bool EARLY>
+__global__ void __launch_bounds__(256) k_validate(Geom<R> G, EdgeBatch<R> E) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    R* sm = reinterpret_cast<R*>(smem_raw);
+    const int n = E.n_dev ? *E.n_dev : E.n_host;
+    if (n <= 0) return;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bar, G.blob_bytes);
+        bulk_g2s(sm, G.blob, G.blob_bytes, &bar);
+    }
+    if (!mbar_wait(&bar, 0)) {
+        if (threadIdx.x == 0 && E.err) atomicOr(E.err, kErrTimeout);
+        return;
+    }
+
+    const long long total = E.off[n];
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const long long wstride = (long long)gridDim.x * wpb * 32;
+    unsigned long long done = 0;
+    for (long long base = ((long long)blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; base < total; base += wstride) {
+        int e0 = 0;
+        if (lane == 0) {
+            int lo = 0, hi = n - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (E.off[mid] <= base) lo = mid;
+                else hi = mid - 1;
+            }
+            e0 = lo;
+        }
+        e0 = __shfl_sync(0xffffffffu, e0, 0);
+        const long long g = base + lane;
+        if (g >= total) continue;
+        int e = e0;
+        while (E.off[e + 1] <= g) ++e;
+        if (EARLY && !CLEAR) {
+            if (*(volatile int*)(E.hit + e)) continue;
+        }
+        const int c = E.cnt[e];
+        const R s = R(g - E.off[e] + 1) / R(c);
+        const R* qa = E.qa + (size_t)e * E.qstride;
+        const R* qb = E.qb + (size_t)e * E.qstride;
+        R q[kMaxDof];
+        bool hit = false;
+#pragma unroll
+        for (int i = 0; i < kMaxDof; ++i) {
+            if (i < G.dof) {
+                q[i] = qa[i] + s * (qb[i] - qa[i]);
+                hit = hit || (q[i] < G.qlo[i]) || (q[i] > G.qhi[i]);
+            } else {
+                q[i] = R(0);
+            }
+        }
+        const R ta = E.ta[e];
+        const R t = ta + s * (E.tb[e] - ta);
+        R clr = rinf<R>();
+        if (ARM) check_point<R, true, MO, CLEAR, EARLY>(G, sm, q, t, hit, clr);
+        else check_point<R, false, MO, CLEAR, EARLY>(G, sm, q, t, hit, clr);
+        if (hit) E.hit[e] = 1;
+        if (CLEAR) atomic_min_r<R>(E.clear + e, clr);
+        ++done;
+    }
+    if (E.points_done) {
+        for (int o = 16; o > 0; o >>= 1) done += __shfl_xor_sync(0xffffffffu, done, o);
+        if (lane == 0 && done) atomicAdd(E.points_done, done);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------
+static int g_num_sms = 0;
+
+int validate_grid_blocks() {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+template <typename R, bool ARM, int MO, bool CLEAR, bool EARLY>
+static cudaError_t launch_v(const Geom<R>& g, const EdgeBatch<R>& e, int grid_blocks, cudaStream_t st) {
+    auto kern = k_validate<R, ARM, MO, CLEAR, EARLY>;
+    static int configured_bytes = -1;
+    static int blocks_per_sm = 0;
+    int smem = (int)g.blob_bytes;
+    if (smem > configured_bytes) {
+        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (err != cudaSuccess) return err;
+        configured_bytes = smem;
+        blocks_per_sm = 0;
+    }
+    if (blocks_per_sm == 0) {
+        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, 256, smem);
+        if (err != cudaSuccess) return err;
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    int grid = grid_blocks > 0 ? grid_blocks : validate_grid_blocks() * blocks_per_sm;
+    kern<<<grid, 256, smem, st>>>(g, e);
+    return cudaGetLastError();
+}
+
+template <typename R, bool ARM, bool CLEAR, bool EARLY>
+static cudaError_t launch_mo(const Geom<R>& g, const EdgeBatch<R>& e, int grid_blocks, cudaStream_t st) {
+    if (CLEAR) return launch_v<R, ARM, 16, CLEAR, EARLY>(g, e, grid_blocks, st);
+    if (g.M <= 8) return launch_v<R, ARM, 8, CLEAR, EARLY>(g, e, grid_blocks, st);
+    if (g.M <= 16) return launch_v<R, ARM, 16, CLEAR, EARLY>(g, e, grid_blocks, st);
+    return launch_v<R, ARM, 32, CLEAR, EARLY>(g, e, grid_blocks, st);
+}
+
+template <typename R>
+cudaError_t launch_validate(const Geom<R>& g, const EdgeBatch<R>& e, bool clearance, bool early_exit,
+                            int grid_blocks, cudaStream_t st) {
+    if (g.arm) {
+        if (clearance) return launch_mo<R, true, true, false>(g, e, grid_blocks, st);
+        if (early_exit) return launch_mo<R, true, false, true>(g, e, grid_blocks, st);
+        return launch_mo<R, true, false, false>(g, e, grid_blocks, st);
+    }
+    if (clearance) return launch_mo<R, false, true, false>(g, e, grid_blocks, st);
+    if (early_exit) return launch_mo<R, false, false, true>(g, e, grid_blocks, st);
+    return launch_mo<R, false, false, false>(g, e, grid_blocks, st);
+}
+
+// Check-point counts, c = max(1, ceil(max(D, v_max |dt|) / res - 1e-3)),
+// evaluated in double from the stored endpoints.
+template <typename R>
+__global__ void k_edge_counts(double vmax, int dof, const R* qa, const R* ta, const R* qb, const R* tb, int qstride,
+                              int n, double res, int* cnt) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double s2 = 0.0;
+    for (int i = 0; i < dof; ++i) {
+        double dd = (double)qb[(size_t)e * qstride + i] - (double)qa[(size_t)e * qstride + i];
+        s2 = __dadd_rn(s2, __dmul_rn(dd, dd));
+    }
+    double D = sqrt(s2);
+    double L = fmax(D, __dmul_rn(vmax, fabs((double)tb[e] - (double)ta[e])));
+    double c = ceil(L / res - 1e-3);
+    cnt[e] = c < 1.0 ? 1 : (int)c;
+}
+
+template <typename R>
+cudaError_t launch_edge_counts(const Geom<R>& g, const R* qa, const R* ta, const R* qb, const R* tb, int qstride,
+                               int n, double res, int* cnt, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_edge_counts<R><<<(n + 255) / 256, 256, 0, st>>>(g.vmax_d, g.dof, qa, ta, qb, tb, qstride, n, res, cnt);
+    return cudaGetLastError();
+}
+
+// Exclusive prefix sum of counts into off[0..n] (off[n] = total); three phases.
+constexpr int kScanBlock = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanBlock * kScanPer;
+
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long* sh, long long* total) {
+    // Warp scan then scan of warp totals.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int nw = blockDim.x >> 5;
+        long long w = lane < nw ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) sh[lane] = w;
+    }
+    __syncthreads();
+    long long before = (warp > 0 ? sh[warp - 1] : 0) + x - v;
+    if (total) *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void k_scan_tiles(const int* cnt, int n, long long* off, long long* tile_tot) {
+    __shared__ long long sh[32];
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+    long long v[kScanPer];
+    long long sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        v[i] = (base + i < n) ? cnt[base + i] : 0;
+        sum += v[i];
+    }
+    long long tot;
+    long long pre = block_exclusive_scan(sum, sh, &tot);
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        if (base + i < n) off[base + i] = pre;
+        pre += v[i];
+    }
+    if (threadIdx.x == 0) tile_tot[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_tops(long long* tile_tot, int ntiles, long long* off, int n) {
+    __shared__ long long sh[32];
+    long long carry = 0;
+    for (int b0 = 0; b0 < ntiles; b0 += blockDim.x) {
+        int b = b0 + threadIdx.x;
+        long long v = b < ntiles ? tile_tot[b] : 0;
+        long long tot;
+        long long pre = block_exclusive_scan(v, sh, &tot);
+        if (b < ntiles) tile_tot[b] = carry + pre;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) off[n] = carry;
+}
+
+__global__ void k_scan_add(long long* off, int n, const long long* tile_tot) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) off[i] += tile_tot[i / kScanTile];
+}
+
+cudaError_t launch_scan_counts(const int* cnt, int n, long long* off, long long* tile_tmp, cudaStream_t st) {
+    if (n <= 0) {
+        return cudaMemsetAsync(off, 0, sizeof(long long), st);
+    }
+    int ntiles = (n + kScanTile - 1) / kScanTile;
+    k_scan_tiles<<<ntiles, kScanBlock, 0, st>>>(cnt, n, off, tile_tmp);
+    k_scan_tops<<<1, kScanBlock, 0, st>>>(tile_tmp, ntiles, off, n);
+    k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(off, n, tile_tmp);
+    return cudaGetLastError();
+}
+
+// Small fills and conversions used by the batch entry point.
+__global__ void k_fill_u32(unsigned* p, long long n, unsigned v) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+__global__ void k_fill_u64(unsigned long long* p, long long n, unsigned long long v) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+cudaError_t launch_fill(void* p, long long n, int bytes, unsigned long long v, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int grid = (int)((n + 255) / 256);
+    if (bytes == 4) k_fill_u32<<<grid, 256, 0, st>>>((unsigned*)p, n, (unsigned)v);
+    else k_fill_u64<<<grid, 256, 0, st>>>((unsigned long long*)p, n, v);
+    return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void k_finish_batch(int n, const int* hit, unsigned char* verdict, R* clear) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    verdict[e] = hit[e] ? 0 : 1;
+    if (clear) clear[e] = ord_dec(*reinterpret_cast<const decltype(ord_enc(R(0)))*>(clear + e));
+}
+template <typename R>
+cudaError_t launch_finish_batch(int n, const int* hit, unsigned char* verdict, R* clear, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_finish_batch<R><<<(n + 255) / 256, 256, 0, st>>>(n, hit, verdict, clear);
+    return cudaGetLastError();
+}
+template cudaError_t launch_finish_batch<float>(int, const int*, unsigned char*, float*, cudaStream_t);
+template cudaError_t launch_finish_batch<double>(int, const int*, unsigned char*, double*, cudaStream_t);
+
+template cudaError_t launch_validate<float>(const Geom<float>&, const EdgeBatch<float>&, bool, bool, int,
+                                            cudaStream_t);
+template cudaError_t launch_validate<double>(const Geom<double>&, const EdgeBatch<double>&, bool, bool, int,
+                                             cudaStream_t);
+template cudaError_t launch_edge_counts<float>(const Geom<float>&, const float*, const float*, const float*,
+                                               const float*, int, int, double, int*, cudaStream_t);
+template cudaError_t launch_edge_counts<double>(const Geom<double>&, const double*, const double*, const double*,
+                                                const double*, int, int, double, int*, cudaStream_t);
+
+}  // namespace stp

@@ -1,0 +1,297 @@
+"""ctypes binding of the C ABI in include/stp.h (argument marshalling only).
+
+Every planning step runs in the CUDA library paper_2609_30533_gb300/_build/libstp.so;
+importing a function here never falls back to Python or CPU code. If the library
+is missing, ``lib()`` raises: build it with ``paper_2609_30533_gb300.build.build()``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libstp.so")
+
+STP_OK, STP_ERR_INVALID, STP_ERR_CAPACITY, STP_ERR_CUDA, STP_ERR_TIMEOUT, STP_NO_SOLUTION = range(6)
+STP_EDGES_DEVICE = 1
+STP_EDGES_CLEARANCE = 2
+STP_EDGES_NO_EARLY_EXIT = 4
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+
+
+class StpRobot(C.Structure):
+    _fields_ = [("dof", C.c_int), ("arm", C.c_int), ("dh", _D), ("q_lo", _D), ("q_hi", _D),
+                ("n_spheres", C.c_int), ("spheres", _D), ("v_max", C.c_double)]
+
+
+class StpObstacles(C.Structure):
+    _fields_ = [("n_obs", C.c_int), ("n_way", C.c_int), ("radius", _D), ("way", _D)]
+
+
+class StpParams(C.Structure):
+    _fields_ = [("variant", C.c_int), ("n_roots", C.c_int), ("ext_per_iter", C.c_int),
+                ("max_iters", C.c_int), ("budget_ms", C.c_double), ("eta", C.c_double),
+                ("edge_res", C.c_double), ("env_dt", C.c_double), ("p_new", C.c_double),
+                ("p_guided", C.c_double), ("t_max", C.c_double), ("seed", C.c_ulonglong),
+                ("problem_id", C.c_uint), ("precision", C.c_int), ("learned", C.c_int),
+                ("capacity", C.c_int), ("iters_per_graph", C.c_int)]
+
+
+class StpStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("first_solution_iter", C.c_int), ("nodes", C.c_longlong),
+                ("edges_validated", C.c_longlong), ("bridges_validated", C.c_longlong),
+                ("root_checks", C.c_longlong), ("check_points", C.c_longlong),
+                ("first_solution_ms", C.c_double), ("plan_ms", C.c_double), ("U", C.c_double),
+                ("C", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class StpError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__("%s failed: %s%s" % (where, status_string(status), (" (" + detail + ")") if detail else ""))
+
+
+_LIB = None
+
+
+def lib():
+    """Load the CUDA library; raises if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("CUDA library not built: %s is missing (run paper_2609_30533_gb300.build.build())"
+                           % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    L.stp_create_problem.argtypes = [C.POINTER(StpRobot), C.POINTER(StpObstacles), _D, _D, C.POINTER(StpParams),
+                                     C.POINTER(C.c_void_p)]
+    L.stp_create_problem.restype = C.c_int
+    L.stp_plan.argtypes = [C.c_void_p, _D, _D, _I, _D, C.c_int, C.POINTER(StpStats)]
+    L.stp_plan.restype = C.c_int
+    L.stp_check_edges.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                  C.c_void_p, C.c_void_p, C.c_void_p]
+    L.stp_check_edges.restype = C.c_int
+    L.stp_free.argtypes = [C.c_void_p]
+    L.stp_free.restype = None
+    L.stp_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+    L.stp_set_stream.restype = C.c_int
+    L.stp_status_string.argtypes = [C.c_int]
+    L.stp_status_string.restype = C.c_char_p
+    L.stp_last_error.argtypes = [C.c_void_p]
+    L.stp_last_error.restype = C.c_char_p
+    L.stp_last_validate_ms.argtypes = [C.c_void_p, _D]
+    L.stp_last_validate_ms.restype = C.c_int
+    L.stp_tree_size.argtypes = [C.c_void_p, C.c_int, _I]
+    L.stp_tree_size.restype = C.c_int
+    L.stp_tree_nodes.argtypes = [C.c_void_p, C.c_int, _D, _I, _D, _D, _I, _I]
+    L.stp_tree_nodes.restype = C.c_int
+    L.stp_history.argtypes = [C.c_void_p, _D, C.c_int, _I]
+    L.stp_history.restype = C.c_int
+    L.stp_slots.argtypes = [C.c_void_p, _D, _I, _I, _I]
+    L.stp_slots.restype = C.c_int
+    L.stp_goal_grid.argtypes = [C.c_void_p, C.POINTER(C.c_long), _I, C.c_void_p, C.c_int]
+    L.stp_goal_grid.restype = C.c_int
+    _LIB = L
+    return L
+
+
+EXPORTED = ["stp_create_problem", "stp_plan", "stp_check_edges", "stp_free", "stp_set_stream",
+            "stp_status_string", "stp_last_error", "stp_last_validate_ms", "stp_tree_size", "stp_tree_nodes",
+            "stp_history", "stp_slots", "stp_goal_grid"]
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().stp_status_string(int(s)).decode()
+    except Exception:  # library missing: still name the code
+        names = ["STP_OK", "STP_ERR_INVALID", "STP_ERR_CAPACITY", "STP_ERR_CUDA", "STP_ERR_TIMEOUT",
+                 "STP_NO_SOLUTION"]
+        return names[s] if 0 <= s < len(names) else str(s)
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+@dataclasses.dataclass
+class PlanOutput:
+    status: int
+    U: float
+    C: float
+    path: np.ndarray
+    stats: dict
+
+
+class Problem:
+    """Owns one stp_problem handle. Arrays are float64 numpy; see include/stp.h."""
+
+    def __init__(self, *, dof, arm, dh, q_lo, q_hi, spheres, v_max, obs_radius, obs_way, q_start, q_goal,
+                 variant=0, n_roots=4, ext_per_iter=64, max_iters=100, budget_ms=0.0, eta=0.1, edge_res=0.01,
+                 env_dt=0.02, p_new=0.05, p_guided=0.95, t_max=10.0, seed=0, problem_id=0, precision=0,
+                 capacity=0, iters_per_graph=0):
+        L = lib()
+        self.dof = int(dof)
+        self.precision = int(precision)
+        self._keep = []
+
+        def arr(x, shape=None):
+            a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+            if shape is not None:
+                a = a.reshape(shape)
+            self._keep.append(a)
+            return a
+
+        dh_a = arr(dh if dh is not None else np.zeros((dof, 4)))
+        robot = StpRobot(self.dof, 1 if arm else 0, _dp(dh_a) if arm else None, _dp(arr(q_lo)), _dp(arr(q_hi)),
+                         len(spheres), _dp(arr(spheres)), float(v_max))
+        obs_r = arr(obs_radius)
+        way = arr(obs_way)
+        obstacles = StpObstacles(len(obs_r), way.shape[1] if way.ndim == 3 else 1,
+                                 _dp(obs_r) if len(obs_r) else None, _dp(way) if len(obs_r) else None)
+        self.params = StpParams(int(variant), int(n_roots), int(ext_per_iter), int(max_iters), float(budget_ms),
+                                float(eta), float(edge_res), float(env_dt), float(p_new), float(p_guided),
+                                float(t_max), int(seed), int(problem_id), int(precision), 0, int(capacity),
+                                int(iters_per_graph))
+        h = C.c_void_p()
+        s = L.stp_create_problem(C.byref(robot), C.byref(obstacles), _dp(arr(q_start)), _dp(arr(q_goal)),
+                                 C.byref(self.params), C.byref(h))
+        if s != STP_OK:
+            raise StpError(s, "stp_create_problem")
+        self.handle = h
+        self.n_roots = int(n_roots)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().stp_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return lib().stp_last_error(self.handle).decode()
+
+    def set_stream(self, stream_ptr: Optional[int]):
+        s = lib().stp_set_stream(self.handle, C.c_void_p(stream_ptr) if stream_ptr else None)
+        if s != STP_OK:
+            raise StpError(s, "stp_set_stream")
+
+    def plan(self, cap: int = 1 << 16) -> PlanOutput:
+        U = C.c_double()
+        Cc = C.c_double()
+        n = C.c_int()
+        path = np.zeros((cap, self.dof + 1))
+        st = StpStats()
+        s = lib().stp_plan(self.handle, C.byref(U), C.byref(Cc), C.byref(n), _dp(path), cap, C.byref(st))
+        if s not in (STP_OK, STP_NO_SOLUTION):
+            raise StpError(s, "stp_plan", self.last_error())
+        return PlanOutput(s, U.value, Cc.value, path[:n.value].copy(), st.as_dict())
+
+    def check_edges(self, qa, ta, qb, tb, *, clearance=False, early_exit=True, n_checks=False):
+        """Host arrays (numpy) of the precision type; returns verdict (uint8, 1 = free),
+        clearance (or None) and check counts (or None)."""
+        dt = np.float32 if self.precision == 0 else np.float64
+        qa = np.ascontiguousarray(qa, dtype=dt)
+        qb = np.ascontiguousarray(qb, dtype=dt)
+        ta = np.ascontiguousarray(ta, dtype=dt)
+        tb = np.ascontiguousarray(tb, dtype=dt)
+        n = len(ta)
+        ver = np.zeros(n, dtype=np.uint8)
+        clr = np.zeros(n, dtype=dt) if clearance else None
+        nc = np.zeros(n, dtype=np.int32) if n_checks else None
+        flags = (STP_EDGES_CLEARANCE if clearance else 0) | (0 if early_exit else STP_EDGES_NO_EARLY_EXIT)
+        s = lib().stp_check_edges(self.handle, n, qa.ctypes.data, ta.ctypes.data, qb.ctypes.data, tb.ctypes.data,
+                                  flags, ver.ctypes.data, clr.ctypes.data if clearance else None,
+                                  nc.ctypes.data if n_checks else None)
+        if s != STP_OK:
+            raise StpError(s, "stp_check_edges", self.last_error())
+        return ver, clr, nc
+
+    def check_edges_device(self, qa_ptr, ta_ptr, qb_ptr, tb_ptr, n, verdict_ptr, clearance_ptr=None,
+                           early_exit=True):
+        """Device pointers (e.g. torch tensors' data_ptr()); asynchronous on the problem's stream."""
+        flags = STP_EDGES_DEVICE | (STP_EDGES_CLEARANCE if clearance_ptr else 0) | \
+            (0 if early_exit else STP_EDGES_NO_EARLY_EXIT)
+        s = lib().stp_check_edges(self.handle, int(n), C.c_void_p(qa_ptr), C.c_void_p(ta_ptr), C.c_void_p(qb_ptr),
+                                  C.c_void_p(tb_ptr), flags, C.c_void_p(verdict_ptr),
+                                  C.c_void_p(clearance_ptr) if clearance_ptr else None, None)
+        if s != STP_OK:
+            raise StpError(s, "stp_check_edges", self.last_error())
+
+    def last_validate_ms(self) -> float:
+        ms = C.c_double()
+        s = lib().stp_last_validate_ms(self.handle, C.byref(ms))
+        if s != STP_OK:
+            raise StpError(s, "stp_last_validate_ms")
+        return ms.value
+
+    def tree(self, arena: int):
+        n = C.c_int()
+        s = lib().stp_tree_size(self.handle, int(arena), C.byref(n))
+        if s != STP_OK:
+            raise StpError(s, "stp_tree_size")
+        n = n.value
+        d = self.dof
+        x = np.zeros((n, d + 1))
+        par = np.zeros(n, dtype=np.int32)
+        tr = np.zeros(n)
+        co = np.zeros(n)
+        tree = np.zeros(n, dtype=np.int32)
+        it = np.zeros(n, dtype=np.int32)
+        if n:
+            s = lib().stp_tree_nodes(self.handle, int(arena), _dp(x), par.ctypes.data_as(_I), _dp(tr), _dp(co),
+                                     tree.ctypes.data_as(_I), it.ctypes.data_as(_I))
+            if s != STP_OK:
+                raise StpError(s, "stp_tree_nodes")
+        return dict(x=x, parent=par, troot=tr, cost=co, tree=tree, iter=it)
+
+    def history(self):
+        n = C.c_int()
+        lib().stp_history(self.handle, None, 0, C.byref(n))
+        U = np.zeros(max(n.value, 1))
+        lib().stp_history(self.handle, _dp(U), n.value, C.byref(n))
+        return U[:n.value]
+
+    def slots(self):
+        N = self.n_roots
+        T = np.zeros(N)
+        hr = np.zeros(N, dtype=np.int32)
+        ac = np.zeros(N, dtype=np.int32)
+        gen = np.zeros(N, dtype=np.int32)
+        s = lib().stp_slots(self.handle, _dp(T), hr.ctypes.data_as(_I), ac.ctypes.data_as(_I),
+                            gen.ctypes.data_as(_I))
+        if s != STP_OK:
+            raise StpError(s, "stp_slots")
+        return dict(T=T, has_root=hr, active=ac, gen=gen)
+
+    def goal_grid(self):
+        kmin = C.c_long()
+        n = C.c_int()
+        lib().stp_goal_grid(self.handle, C.byref(kmin), C.byref(n), None, 0)
+        f = np.zeros(max(n.value, 1), dtype=np.uint8)
+        lib().stp_goal_grid(self.handle, C.byref(kmin), C.byref(n), f.ctypes.data, n.value)
+        return kmin.value, f[:n.value]
+
+
+def problem_from(prob, params, **over) -> Problem:
+    """Build a Problem from objects with the fields of workloads.Problem / Params."""
+    kw = dict(variant=params.variant, n_roots=params.n_roots, ext_per_iter=params.workers,
+              max_iters=params.max_iters, eta=params.eta, edge_res=params.res, env_dt=params.dt,
+              p_new=params.p_new, p_guided=params.p_guided, t_max=params.H, seed=params.seed,
+              problem_id=params.problem_id)
+    kw.update(over)
+    return Problem(dof=prob.dof, arm=prob.arm, dh=prob.dh, q_lo=prob.qlo, q_hi=prob.qhi, spheres=prob.spheres,
+                   v_max=prob.vmax, obs_radius=prob.obs_r, obs_way=prob.way, q_start=prob.qs, q_goal=prob.qg,
+                   **kw)

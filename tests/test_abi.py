@@ -1,0 +1,111 @@
+"""C ABI checks that need no GPU: the library loads, exports every entry point
+that include/stp.h declares, validates arguments, and fails loudly (no CPU
+fallback) when no CUDA device is present."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as WL
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(stp_[a-z_0-9]+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2609_30533_gb300 import build as B
+    B.build()
+    from paper_2609_30533_gb300 import stp
+    return stp.lib()
+
+
+def test_library_exports_every_declared_symbol(L):
+    declared = _declared()
+    assert {"stp_create_problem", "stp_plan", "stp_check_edges", "stp_free"} <= declared
+    for name in sorted(declared):
+        assert hasattr(L, name), name
+
+
+def test_binding_names_match_header(L):
+    from paper_2609_30533_gb300 import stp
+    assert set(stp.EXPORTED) == _declared()
+
+
+def test_status_strings(L):
+    from paper_2609_30533_gb300 import stp
+    assert stp.status_string(0) == "STP_OK"
+    assert stp.status_string(5) == "STP_NO_SOLUTION"
+
+
+def _params(**kw):
+    from paper_2609_30533_gb300 import stp
+    base = dict(variant=0, n_roots=4, ext_per_iter=64, max_iters=10, budget_ms=0.0, eta=0.1, edge_res=0.01,
+                env_dt=0.02, p_new=0.05, p_guided=0.95, t_max=20.0, seed=0, problem_id=0, precision=0,
+                learned=0, capacity=0, iters_per_graph=0)
+    base.update(kw)
+    return stp.StpParams(**base)
+
+
+def _create(prob, params):
+    from paper_2609_30533_gb300 import stp
+    keep = []
+
+    def a(x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        keep.append(x)
+        return x.ctypes.data_as(C.POINTER(C.c_double))
+
+    robot = stp.StpRobot(prob.dof, 1 if prob.arm else 0, a(prob.dh) if prob.arm else None, a(prob.qlo),
+                         a(prob.qhi), len(prob.spheres), a(prob.spheres), prob.vmax)
+    obs = stp.StpObstacles(len(prob.obs_r), prob.way.shape[1], a(prob.obs_r), a(prob.way))
+    h = C.c_void_p()
+    s = stp.lib().stp_create_problem(C.byref(robot), C.byref(obs), a(prob.qs), a(prob.qg), C.byref(params),
+                                     C.byref(h))
+    return s, h
+
+
+@pytest.mark.parametrize("bad", [dict(n_roots=0), dict(ext_per_iter=0), dict(variant=7), dict(eta=0.0),
+                                 dict(p_new=1.5), dict(precision=2), dict(learned=1), dict(max_iters=0)])
+def test_invalid_params_rejected_before_any_device_call(L, bad):
+    prob, _ = WL.disc2d(0)
+    s, h = _create(prob, _params(**bad))
+    assert s == 1 and not h.value
+
+
+def test_invalid_geometry_rejected(L):
+    prob, _ = WL.disc2d(0)
+    prob.way[0, 1, 0] = prob.way[0, 0, 0]      # non-increasing waypoint times
+    s, _ = _create(prob, _params())
+    assert s == 1
+    prob, _ = WL.disc2d(0)
+    prob.qs = np.array([np.nan, 0.0])
+    s, _ = _create(prob, _params())
+    assert s == 1
+
+
+def test_null_arguments(L):
+    assert L.stp_create_problem(None, None, None, None, None, None) == 1
+    assert L.stp_plan(None, None, None, None, None, 0, None) == 1
+    assert L.stp_check_edges(None, 0, None, None, None, None, 0, None, None, None) == 1
+    L.stp_free(None)
+
+
+def test_no_cpu_fallback_without_gpu(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    prob, _ = WL.disc2d(0)
+    s, h = _create(prob, _params())
+    assert s == 3 and not h.value     # STP_ERR_CUDA

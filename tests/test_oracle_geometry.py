@@ -188,14 +188,18 @@ def test_check_count_and_points():
     prob = _point_problem([(0.01, [(0, 50, 50, 0)])], vmax=2.0)
     _, _, nc, im = O.check_edges(prob, np.array([[0.0, 0.0]]), np.array([1.0]), np.array([[3.0, 4.0]]),
                                  np.array([4.0]), 0.25)
-    assert nc[0] == 24 and im[0] == 0.0          # v*dt = 6 dominates D = 5
+    assert nc[0] == 24 and abs(im[0] - 1e-3) < 1e-12   # v*dt = 6 dominates D = 5
     prob1 = _point_problem([(0.01, [(0, 50, 50, 0)])], vmax=1.0)
     _, _, nc, _ = O.check_edges(prob1, np.array([[0.0, 0.0]]), np.array([1.0]), np.array([[3.0, 4.0]]),
                                 np.array([4.0]), 0.25)
     assert nc[0] == 20                            # D = 5 dominates v*dt = 3
     _, _, nc, im = O.check_edges(prob1, np.array([[0.0, 0.0]]), np.array([1.0]), np.array([[3.0, 4.0]]),
                                  np.array([4.0]), 0.3)
-    assert nc[0] == 17 and abs(im[0] - (1 - (5 / 0.3 - 16))) < 1e-12
+    assert nc[0] == 17 and abs(im[0] - (1 - (5 / 0.3 - 1e-3 - 16))) < 1e-12
+    # Within 1e-3 of a step above a multiple of res, the count does not grow.
+    _, _, nc, _ = O.check_edges(prob1, np.array([[0.0, 0.0]]), np.array([1.0]), np.array([[3.0, 4.0002]]),
+                                np.array([4.0]), 0.25)
+    assert nc[0] == 20
     # A zero-length edge in q and t still takes one point.
     _, _, nc, _ = O.check_edges(prob, np.array([[1.0, 1.0]]), np.array([2.0]), np.array([[1.0, 1.0]]),
                                 np.array([2.0]), 0.01)
