@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark: validated space-time edges/s of the batched Extend planner on GB300.
+
+Workload (default, one GPU): UR5e (standard DH) with 32 link spheres among 16
+sphere obstacles (r = 0.06 m) on 4-waypoint paths in a 1.2 m cube, joint
+v_max pi/2, horizon 15 s, root recycling with N = 8 slots, W = 1024 Extend
+workers per iteration, FP32. A step is one stp_plan call from a fresh state
+running --iters iterations (every iteration: Philox sampling, NN scan, steering,
+edge validation, ordered insertion, bridge scan and validation, publish, root
+recycling). The metric counts validated edges (extension + bridge edges sent to
+the collision kernel) per second of device time.
+
+Timing: CUDA events on the library's stream around each step; an L2 flush
+(512 MB write) runs between steps outside the events; a second pass of the same
+steps records CUDA events between the kernels inside the captured graphs to give
+per-kernel times and the collision kernel's roofline. The 2^20-edge collision
+microbenchmark and the FP64 oracle (CPU baseline) are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): independent problem replicas per rank (seed = rank), no
+collective on the data path; value = all ranks' edges / max rank time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as WL  # noqa: E402
+
+WORKLOAD = "ur5e-6dof-32sph-16obs-recycling-N8-W1024"
+METRIC = "validated space-time edges/s"
+UNIT = "edges/s"
+FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def fp32_peak_tflops(n_sm, mhz):
+    """FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    return n_sm * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def point_flops(prob):
+    """Per check point, excluding pair tests: sphere transforms (18 flops per
+    sphere), forward kinematics (about 60 flops per joint) and obstacle
+    interpolation (9 flops per obstacle); each pair test adds 8 flops."""
+    S = len(prob.spheres)
+    M = len(prob.obs_r)
+    return 18 * S + 60 * prob.dof + 9 * M
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_reference(args):
+    """The oracle (single-threaded FP64 CPU) on the same workload and metric; each
+    step is a bounded sample: --ref-iters iterations of the same W = 1024 plan."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    prob, prm = WL.ur5e(0)
+    import dataclasses
+    prm = dataclasses.replace(prm, max_iters=args.ref_iters)
+    for _ in range(args.warmup):
+        O.plan(prob, dataclasses.replace(prm, max_iters=1))
+    edges = 0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        r = O.plan(prob, dataclasses.replace(prm, seed=k))
+        edges += r.ext_checked + r.bridge_checked
+    secs = time.perf_counter() - t0
+    value = edges / secs
+    sample = "%d steps x %d iterations x W=1024 of the %s plan" % (args.steps, args.ref_iters, WORKLOAD)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "iters_per_step": args.ref_iters, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def cpu_baseline(args):
+    import dataclasses
+
+    import oracle as O
+    prob, prm = WL.ur5e(0)
+    prm = dataclasses.replace(prm, max_iters=args.cpu_iters)
+    t0 = time.perf_counter()
+    r = O.plan(prob, prm)
+    secs = time.perf_counter() - t0
+    edges = r.ext_checked + r.bridge_checked
+    return {"value": edges / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d iterations x W=1024 of the %s plan (%d edges, %.1f s)" % (
+                args.cpu_iters, WORKLOAD, edges, secs)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--iters", type=int, default=32, help="planner iterations per step")
+    ap.add_argument("--ref-iters", type=int, default=2)
+    ap.add_argument("--cpu-iters", type=int, default=8)
+    ap.add_argument("--micro-edges", type=int, default=1 << 20)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2609_30533_gb300 import build as B
+    B.build()
+    from paper_2609_30533_gb300 import stp
+
+    prob, prm = WL.ur5e(rank)
+    P = stp.problem_from(prob, prm, precision=0, max_iters=args.iters, iters_per_graph=args.iters)
+    stream = torch.cuda.Stream()
+    P.set_stream(stream.cuda_stream)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step_timed():
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = P.plan()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    for _ in range(args.warmup):
+        step_timed()
+
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms = 0.0
+    edges = 0
+    launches = 0
+    plan_ms = []
+    fs_ms = []
+    for k in range(args.steps):
+        ms, out = step_timed()
+        total_ms += ms
+        st = out.stats
+        edges += st["edges_validated"] + st["bridges_validated"]
+        plan_ms.append(st["plan_ms"])
+        if st["first_solution_ms"] >= 0:
+            fs_ms.append(st["first_solution_ms"])
+        launches += 2 + 10 * args.iters
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+
+    # Kernel-timing pass: the same steps with CUDA events between the kernels
+    # inside the captured graphs.
+    prof_tot = {}
+    pairs = points = 0
+    prof_step_ms = 0.0
+    prof_error = None
+    try:
+        P.set_profiling(True)
+        for k in range(args.steps):
+            ms, out = step_timed()
+            prof_step_ms += ms
+            for name, (kms, n) in P.profile().items():
+                a = prof_tot.setdefault(name, [0.0, 0])
+                a[0] += kms
+                a[1] += n
+            pairs += out.stats["pair_tests"]
+            points += out.stats["check_points"]
+    except Exception as exc:  # report, keep the measured value
+        prof_error = str(exc)
+        prof_tot = {}
+    finally:
+        P.set_profiling(False)
+
+    # End to end through the C ABI with host buffers: create (H2D of the
+    # problem), plan, read the path back (D2H), free.
+    h2d = sum(np.asarray(a, dtype=np.float64).nbytes for a in
+              (prob.dh, prob.qlo, prob.qhi, prob.spheres, prob.obs_r, prob.way, prob.qs, prob.qg))
+    e2e_edges = 0
+    d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        Q = stp.problem_from(prob, prm, precision=0, max_iters=args.iters, iters_per_graph=args.iters)
+        out = Q.plan(cap=4096)
+        e2e_edges += out.stats["edges_validated"] + out.stats["bridges_validated"]
+        d2h = out.path.size * 8 + 8 * 16
+        Q.close()
+    torch.cuda.synchronize()
+    e2e_secs = time.perf_counter() - t0
+
+    # Collision microbenchmark: 2^20 edges resident on the device.
+    n = args.micro_edges
+    qa, ta, qb, tb = WL.microbench_edges(prob, n, prm.eta, prm.H, seed=rank)
+    dev = torch.device("cuda", local)
+    tq = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev) for a in (qa, ta, qb, tb)]
+    ver = torch.zeros(n, dtype=torch.uint8, device=dev)
+    micro = {}
+    for label, early in (("early_exit", True), ("no_early_exit", False)):
+        for _ in range(3):
+            P.check_edges_device(tq[0].data_ptr(), tq[1].data_ptr(), tq[2].data_ptr(), tq[3].data_ptr(), n,
+                                 ver.data_ptr(), early_exit=early)
+        kms, kpts, kpairs, call_ms = [], 0, 0, []
+        for _ in range(5):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.check_edges_device(tq[0].data_ptr(), tq[1].data_ptr(), tq[2].data_ptr(), tq[3].data_ptr(), n,
+                                 ver.data_ptr(), early_exit=early)
+            e1.record(stream)
+            e1.synchronize()
+            call_ms.append(e0.elapsed_time(e1))
+            ms, pts, prs = P.last_validate()
+            kms.append(ms)
+            kpts, kpairs = pts, prs
+        k_ms = statistics.median(kms)
+        flops = kpairs * 8 + kpts * point_flops(prob)
+        micro[label] = {"edges_per_s": n / (statistics.median(call_ms) * 1e-3),
+                        "kernel_ms": k_ms, "check_points": kpts, "pair_tests": kpairs,
+                        "achieved_tflops": flops / (k_ms * 1e-3) / 1e12,
+                        "free_fraction": float(ver.float().mean().item())}
+
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peaks = _peaks()
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(n_sm, max_mhz)
+    for m in micro.values():
+        m["frac"] = m["achieved_tflops"] / peak
+
+    # Aggregate over ranks: edges summed, time = max over ranks.
+    vals = torch.tensor([float(edges), total_ms, float(e2e_edges), e2e_secs], dtype=torch.float64, device="cuda")
+    if dist:
+        tot = vals.clone()
+        dist.all_reduce(tot[0:1], op=dist.ReduceOp.SUM)
+        dist.all_reduce(tot[2:3], op=dist.ReduceOp.SUM)
+        mx = vals.clone()
+        dist.all_reduce(mx[1:2], op=dist.ReduceOp.MAX)
+        dist.all_reduce(mx[3:4], op=dist.ReduceOp.MAX)
+        vals = torch.stack([tot[0], mx[1], tot[2], mx[3]])
+    edges_all, ms_max, e2e_edges_all, e2e_max = [float(x) for x in vals.cpu()]
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    value = edges_all / (ms_max * 1e-3)
+    kv = prof_tot.get("k_validate(ext)", [0.0, 0])
+    kb = prof_tot.get("k_validate(bridge)", [0.0, 0])
+    val_ms = kv[0] + kb[0]
+    val_launches = kv[1] + kb[1]
+    flops = pairs * 8 + points * point_flops(prob)
+    achieved = flops / (val_ms * 1e-3) / 1e12 if val_ms > 0 else 0.0
+    kernels = {k: {"ms_total": round(v[0], 4), "launches": v[1],
+                   "share": round(v[0] / max(sum(x[0] for x in prof_tot.values()), 1e-12), 4)}
+               for k, v in prof_tot.items()}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "iters_per_step": args.iters, "workers": prm.workers,
+                   "n_roots": prm.n_roots, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": e2e_edges_all / e2e_max, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h),
+                "note": "per step: stp_create_problem from host arrays, stp_plan, path read back, stp_free"},
+        "gpu_launches": launches * world,
+        "roofline": {"bound": "alu", "kernel": "k_validate", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
+                     "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz (max SM clock)" % (
+                         n_sm, max_mhz),
+                     "launches": val_launches, "avg_launch_ms": val_ms / max(val_launches, 1),
+                     "flops_per_launch": flops / max(val_launches, 1)},
+        "kernels": kernels,
+        "profiled_ms_per_step": prof_step_ms / args.steps,
+        "profiling_error": prof_error,
+        "plan_ms_p50": statistics.median(plan_ms),
+        "first_solution_ms_p50": statistics.median(fs_ms) if fs_ms else None,
+        "microbench": dict(micro, n_edges=n, peak_tflops=peak),
+    }
+    if clk:
+        line["clocks"] = clk
+    if not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -128,6 +128,7 @@ typedef struct {
     long long bridges_validated;  /* bridge edges sent to edge validation */
     long long root_checks;        /* sampled goal roots checked (interval root) */
     long long check_points;       /* check points of all validated edges */
+    long long pair_tests;         /* robot-sphere / obstacle pair tests executed */
     double first_solution_ms;     /* device time from plan start to the first solution */
     double plan_ms;               /* device time of the whole plan */
     double U;
@@ -175,9 +176,19 @@ stp_status stp_check_edges(stp_problem *p, int n_edges, const void *qa, const vo
                            const void *tb, int flags, unsigned char *verdict, void *min_clearance,
                            int *n_checks);
 
-/* Device time (ms, CUDA events on the problem's stream) of the collision
- * kernel launch inside the last stp_check_edges call on p. */
-stp_status stp_last_validate_ms(stp_problem *p, double *ms);
+/* The collision-kernel launch inside the last stp_check_edges call on p:
+ * device time in ms (CUDA events on the problem's stream), check points
+ * evaluated and sphere-obstacle pair tests executed. Any output may be NULL. */
+stp_status stp_last_validate(stp_problem *p, double *ms, long long *points, long long *pairs);
+
+/* Kernel profiling of stp_plan. With on != 0 the captured iteration graphs
+ * record a CUDA event before every kernel and after the last one, and stp_plan
+ * accumulates the device time of each kernel kind over the iterations that
+ * ran (the host waits after every graph launch while profiling is on). */
+stp_status stp_set_profiling(stp_problem *p, int on);
+/* Per-kernel totals of the last profiled stp_plan: for k < *n (at most cap):
+ * names[k] (static strings), ms[k] total device time, launches[k]. */
+stp_status stp_profile(stp_problem *p, int cap, const char **names, double *ms, long long *launches, int *n);
 
 /* Release all device and host memory of a problem. NULL is allowed. */
 void stp_free(stp_problem *p);

@@ -47,7 +47,7 @@ def lib():
     L.orc_state_free.argtypes = [C.POINTER(OrcProblem), _D, C.c_double, _D]
     L.orc_state_free.restype = C.c_int
     L.orc_check_edges.argtypes = [C.POINTER(OrcProblem), C.c_int, _D, _D, _D, _D, C.c_double, _U8,
-                                  _D, _I, _D]
+                                  _D, _I, _D, _D]
     L.orc_interval_partition.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_double,
                                          C.c_long, C.c_int, _U8, _D, _D, _D, C.c_int]
     L.orc_interval_partition.restype = C.c_int
@@ -136,9 +136,11 @@ def state_free(prob, q, t):
     return bool(ok), clr.value
 
 
-def check_edges(prob, qa, ta, qb, tb, res):
+def check_edges(prob, qa, ta, qb, tb, res, bounds=False):
     """FP64 verdicts (1 = free), clearance, check-point count and the distance
-    of the check-count argument from an integer, for a batch of edges."""
+    of the check-count argument from an integer, for a batch of edges; with
+    bounds=True also the signed margin of the checked states from the
+    configuration-box boundary."""
     h = _ProblemHandle(prob)
     qa = np.ascontiguousarray(qa, dtype=np.float64)
     qb = np.ascontiguousarray(qb, dtype=np.float64)
@@ -149,8 +151,11 @@ def check_edges(prob, qa, ta, qb, tb, res):
     clr = np.zeros(n)
     nc = np.zeros(n, dtype=np.int32)
     im = np.zeros(n)
+    bm = np.zeros(n)
     lib().orc_check_edges(h.ref, n, _dptr(qa), _dptr(ta), _dptr(qb), _dptr(tb), float(res),
-                          v.ctypes.data_as(_U8), _dptr(clr), nc.ctypes.data_as(_I), _dptr(im))
+                          v.ctypes.data_as(_U8), _dptr(clr), nc.ctypes.data_as(_I), _dptr(im), _dptr(bm))
+    if bounds:
+        return v, clr, nc, im, bm
     return v, clr, nc, im
 
 

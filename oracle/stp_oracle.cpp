@@ -260,15 +260,20 @@ int edge_check_count(const Problem& P, const double* qa, double ta, const double
 
 // Edge verdict with its FP64 clearance (min over all check points, no early
 // exit) and check-point count.
+// bound_margin: min over check points and joints of (q - lo, hi - q), the
+// signed distance of the checked states from the configuration-box boundary.
 bool edge_free(const Problem& P, const double* qa, double ta, const double* qb, double tb, double res,
-               double* clearance, int* nchk, double* int_margin) {
+               double* clearance, int* nchk, double* int_margin, double* bound_margin = nullptr) {
     int c = edge_check_count(P, qa, ta, qb, tb, res, int_margin);
     bool free = true;
-    double clr = kInf;
+    double clr = kInf, bm = kInf;
     std::vector<double> q(P.dof);
     for (int j = 1; j <= c; ++j) {
         double s = (double)j / (double)c;
-        for (int i = 0; i < P.dof; ++i) q[i] = qa[i] + s * (qb[i] - qa[i]);
+        for (int i = 0; i < P.dof; ++i) {
+            q[i] = qa[i] + s * (qb[i] - qa[i]);
+            bm = std::min(bm, std::min(q[i] - P.qlo[i], P.qhi[i] - q[i]));
+        }
         double t = ta + s * (tb - ta);
         double cl;
         if (!state_free(P, q.data(), t, &cl)) free = false;
@@ -276,6 +281,7 @@ bool edge_free(const Problem& P, const double* qa, double ta, const double* qb, 
     }
     if (clearance) *clearance = clr;
     if (nchk) *nchk = c;
+    if (bound_margin) *bound_margin = bm;
     return free;
 }
 
@@ -494,12 +500,22 @@ struct Params {
     double eta = 0.1, res = 0.01, dt = 0.02, p_new = 0.05, p_guided = 0.95, H = 10.0;
     uint64_t seed = 0;
     uint32_t problem_id = 0;
-    double flag_tol = 1e-4;    // margin below which an FP decision is flagged
+    // Margin below which a decision is flagged as rounding-sensitive. FP32 runs
+    // carry coordinate errors up to a few 1e-6 (steering accumulates about
+    // eps |q| / alpha per tree level), so 1e-5 keeps a safety factor above it.
+    double flag_tol = 1e-5;
     double flag_clear = 1e-5;  // clearance band (m)
 };
 
-struct Margin {  // smallest decision margins seen during one iteration
+// Smallest decision margins seen during one iteration (test diagnostics for
+// comparing a reduced-precision run with this FP64 one). Trees depend on NN
+// choices, admissibility, check counts, interval emptiness, horizon and box
+// boundaries, bridge ranks (which edge is tested and so which U is found) and
+// clearances; comparisons of path length C alone only choose between
+// solutions of equal U and never change a tree, so they are kept apart.
+struct Margin {
     double nn = kInf, clearance = kInf, count = kInf, interval = kInf, bounds = kInf, rank = kInf;
+    double cost = kInf;
     double min_all() const {
         return std::min(std::min(std::min(nn, count), std::min(interval, bounds)), rank);
     }
@@ -614,11 +630,12 @@ private:
 
     int d() const { return P.dof; }
     void check_edge(const double* qa, double ta, const double* qb, double tb, bool* ok, Margin& M) {
-        double clr, im;
+        double clr, im, bm;
         int c;
-        *ok = edge_free(P, qa, ta, qb, tb, prm.res, &clr, &c, &im);
+        *ok = edge_free(P, qa, ta, qb, tb, prm.res, &clr, &c, &im, &bm);
         note(M.clearance, clr);
         note(M.count, im);
+        note(M.bounds, bm);
     }
     void init_recycling();
     void recycle(double U);
@@ -953,7 +970,7 @@ Result Planner::run() {
             double cU = kInf, cRho = kInf;
             int cs = -1, ci = -1;
             double s1U = kInf, s1R = kInf;  // runner-up key for margins
-            auto consider = [&](int s, int i, const Node& v, double Uv, double r) {
+            auto consider = [&](int s, int i, double Uv, double r) {
                 bool better = (Uv < cU) || (Uv == cU && r < cRho);
                 if (better) {
                     s1U = cU;
@@ -966,30 +983,44 @@ Result Planner::run() {
                     s1U = Uv;
                     s1R = r;
                 }
-                (void)v;
             };
-            if (in.forward) {
-                for (int s = 0; s < prm.N; ++s) {
-                    for (int i = 0; i < seg_n[s]; ++i) {
-                        const Node& v = R.seg[s][i];
-                        if (!(v.troot < U0)) continue;
-                        double r = rho_sigma(a.q.data(), a.t, v.q.data(), v.t, 1, dd, P.vmax);
-                        double Delta = v.t - a.t, D = dist(a.q.data(), v.q.data(), dd);
+            // Candidate v of the opposite start-of-iteration set, seen from a:
+            // forward a -> later backward v; backward a -> earlier forward v.
+            auto scan = [&](bool second_pass) {
+                if (in.forward) {
+                    for (int s = 0; s < prm.N; ++s) {
+                        for (int i = 0; i < seg_n[s]; ++i) {
+                            const Node& v = R.seg[s][i];
+                            if (!(v.troot < U0)) continue;
+                            double r = rho_sigma(a.q.data(), a.t, v.q.data(), v.t, 1, dd, P.vmax);
+                            if (!second_pass) {
+                                if (r < kInf) consider(s, i, v.troot, r);
+                                continue;
+                            }
+                            double Delta = v.t - a.t, D = dist(a.q.data(), v.q.data(), dd);
+                            double madm = std::min(std::fabs(Delta), std::fabs(P.vmax * Delta - D));
+                            double ru = std::sqrt((D * D + P.vmax * P.vmax * Delta * Delta) / 2.0);
+                            if (madm < prm.flag_tol && v.troot <= cU + prm.flag_tol && ru <= cRho + prm.flag_tol)
+                                note(M.rank, madm);
+                        }
+                    }
+                } else {
+                    for (int i = 0; i < fwd_n; ++i) {
+                        const Node& v = R.fwd[i];
+                        double r = rho_sigma(v.q.data(), v.t, a.q.data(), a.t, 1, dd, P.vmax);
+                        if (!second_pass) {
+                            if (r < kInf) consider(-1, i, a.troot, r);
+                            continue;
+                        }
+                        double Delta = a.t - v.t, D = dist(a.q.data(), v.q.data(), dd);
                         double madm = std::min(std::fabs(Delta), std::fabs(P.vmax * Delta - D));
-                        if (madm < prm.flag_tol && v.troot <= cU + prm.flag_tol) note(M.rank, madm);
-                        if (r < kInf) consider(s, i, v, v.troot, r);
+                        double ru = std::sqrt((D * D + P.vmax * P.vmax * Delta * Delta) / 2.0);
+                        if (madm < prm.flag_tol && ru <= cRho + prm.flag_tol) note(M.rank, madm);
                     }
                 }
-            } else {
-                for (int i = 0; i < fwd_n; ++i) {
-                    const Node& v = R.fwd[i];
-                    double r = rho_sigma(v.q.data(), v.t, a.q.data(), a.t, 1, dd, P.vmax);
-                    double Delta = a.t - v.t, D = dist(a.q.data(), v.q.data(), dd);
-                    double madm = std::min(std::fabs(Delta), std::fabs(P.vmax * Delta - D));
-                    if (madm < prm.flag_tol) note(M.rank, madm);
-                    if (r < kInf) consider(-1, i, v, a.troot, r);
-                }
-            }
+            };
+            scan(false);
+            scan(true);
             if (ci < 0) continue;
             if (s1U == cU && s1R < kInf) note(M.rank, s1R - cRho);
             if (s1U != cU && s1U < kInf) note(M.rank, s1U - cU);
@@ -1001,7 +1032,7 @@ Result Planner::run() {
             double Cc = fnode.cost + Dab + bnode.cost;
             bool improves = (Uc < U0) || (Uc == U0 && Cc < C0);
             if (Uc != U0 && U0 < kInf) note(M.rank, Uc - U0);
-            if (Uc == U0) note(M.rank, Cc - C0);
+            if (Uc == U0) note(M.cost, Cc - C0);
             if (!improves) continue;
             bool ok;
             check_edge(fnode.q.data(), fnode.t, bnode.q.data(), bnode.t, &ok, M);
@@ -1011,7 +1042,7 @@ Result Planner::run() {
             bool win = (Uc < bestU) || (Uc == bestU && Cc < bestC);
             if (best_w >= 0) {
                 if (Uc != bestU) note(M.rank, Uc - bestU);
-                else note(M.rank, Cc - bestC);
+                else note(M.cost, Cc - bestC);
             }
             if (win) {
                 bestU = Uc;
@@ -1140,17 +1171,18 @@ int orc_state_free(const orc_problem* prob, const double* q, double t, double* c
 // Batch edge check: edges given in double, [n][dof] and [n].
 void orc_check_edges(const orc_problem* prob, int n, const double* qa, const double* ta, const double* qb,
                      const double* tb, double res, unsigned char* verdict, double* clearance, int* nchk,
-                     double* int_margin) {
+                     double* int_margin, double* bound_margin) {
     Problem P = to_problem(prob);
     int d = P.dof;
     for (int e = 0; e < n; ++e) {
-        double clr, im;
+        double clr, im, bm;
         int c;
-        bool ok = edge_free(P, qa + (size_t)e * d, ta[e], qb + (size_t)e * d, tb[e], res, &clr, &c, &im);
+        bool ok = edge_free(P, qa + (size_t)e * d, ta[e], qb + (size_t)e * d, tb[e], res, &clr, &c, &im, &bm);
         verdict[e] = ok ? 1 : 0;
         if (clearance) clearance[e] = clr;
         if (nchk) nchk[e] = c;
         if (int_margin) int_margin[e] = im;
+        if (bound_margin) bound_margin[e] = bm;
     }
 }
 
@@ -1312,7 +1344,7 @@ int orc_nn_spacetime(int n, int d, const double* x, const double* troot, int fil
         A[i].troot = troot ? troot[i] : 0.0;
     }
     Margin M;
-    return nn_spacetime(A, n, filter != 0, U, qr, tr, sigma, d, vmax, rho, M, 1e-4);
+    return nn_spacetime(A, n, filter != 0, U, qr, tr, sigma, d, vmax, rho, M, 1e-5);
 }
 
 void orc_result_margin_types(const orc_result* r, double* out) {

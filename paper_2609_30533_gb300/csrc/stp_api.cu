@@ -67,9 +67,14 @@ struct stp_problem {
     // batch scratch for stp_check_edges
     char* d_scratch = nullptr;
     size_t scratch_bytes = 0;
-    double last_validate_ms = 0.0;
+    unsigned long long* d_counters = nullptr;  // [2]: points, pairs of stp_check_edges
     std::string last_error;
     bool planned = false;
+    // profiling
+    int profiling = 0;
+    std::vector<cudaEvent_t> prof_ev;
+    double prof_ms[kIterKernels] = {};
+    long long prof_launches[kIterKernels] = {};
 };
 
 namespace {
@@ -403,16 +408,25 @@ stp_status create_impl(stp_problem* p) {
 template <typename R>
 stp_status capture_graph(stp_problem* p) {
     const int G = p->prm.iters_per_graph > 0 ? p->prm.iters_per_graph : 16;
-    if (p->graph && p->graph_stream == p->stream && p->graph_iters == G) return STP_OK;
+    const bool prof = p->profiling != 0;
+    const bool have_prof = !p->prof_ev.empty();
+    if (p->graph && p->graph_stream == p->stream && p->graph_iters == G && prof == have_prof) return STP_OK;
     if (p->graph) {
         cudaGraphExecDestroy(p->graph);
         p->graph = nullptr;
+    }
+    for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
+    p->prof_ev.clear();
+    if (prof) {
+        p->prof_ev.resize((size_t)G * (kIterKernels + 1));
+        for (auto& e : p->prof_ev) STP_CUDA(p, cudaEventCreate(&e));
     }
     cudaGraph_t g;
     STP_CUDA(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t err = cudaSuccess;
     for (int i = 0; i < G && err == cudaSuccess; ++i)
-        err = launch_iteration<R>(geom_of<R>(p), state_of<R>(p), 0, p->stream);
+        err = launch_iteration<R>(geom_of<R>(p), state_of<R>(p), 0, p->stream,
+                                  prof ? &p->prof_ev[(size_t)i * (kIterKernels + 1)] : nullptr);
     cudaError_t e2 = cudaStreamEndCapture(p->stream, &g);
     if (err != cudaSuccess) return cuda_fail(p, err, "capture(iteration)");
     if (e2 != cudaSuccess) return cuda_fail(p, e2, "cudaStreamEndCapture");
@@ -436,8 +450,29 @@ stp_status plan_impl(stp_problem* p, Ctl* hc) {
     STP_CUDA(p, launch_plan_reset<R>(geom_of<R>(p), state_of<R>(p), p->prm.max_iters, st));
     const int n_launch = (p->prm.max_iters + p->graph_iters - 1) / p->graph_iters;
     auto t0 = std::chrono::steady_clock::now();
+    for (int k = 0; k < kIterKernels; ++k) {
+        p->prof_ms[k] = 0.0;
+        p->prof_launches[k] = 0;
+    }
+    int iters_before = 0;
     for (int i = 0; i < n_launch; ++i) {
         STP_CUDA(p, cudaGraphLaunch(p->graph, st));
+        if (p->profiling) {
+            int iters_after = 0;
+            STP_CUDA(p, cudaMemcpyAsync(&iters_after, &p->d_ctl->iter, sizeof(int), cudaMemcpyDeviceToHost, st));
+            STP_CUDA(p, cudaStreamSynchronize(st));
+            const int ran = std::min(p->graph_iters, iters_after - iters_before);
+            for (int it = 0; it < ran; ++it) {
+                cudaEvent_t* ev = &p->prof_ev[(size_t)it * (kIterKernels + 1)];
+                for (int k = 0; k < kIterKernels; ++k) {
+                    float ms = 0.f;
+                    STP_CUDA(p, cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+                    p->prof_ms[k] += ms;
+                    p->prof_launches[k] += 1;
+                }
+            }
+            iters_before = iters_after;
+        }
         if (p->prm.budget_ms > 0) {
             STP_CUDA(p, cudaStreamSynchronize(st));
             double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -533,6 +568,9 @@ stp_status check_edges_impl(stp_problem* p, int n, const void* qa, const void* t
     E.hit = L.hit;
     E.clear = L.clr;
     E.err = &p->d_ctl->err;
+    STP_CUDA(p, cudaMemsetAsync(p->d_counters, 0, 2 * sizeof(unsigned long long), st));
+    E.points_done = p->d_counters;
+    E.pairs_done = p->d_counters + 1;
     STP_CUDA(p, cudaEventRecord(p->ev2, st));
     STP_CUDA(p, launch_validate<R>(geom_of<R>(p), E, clear, early, 0, st));
     STP_CUDA(p, cudaEventRecord(p->ev3, st));
@@ -677,6 +715,11 @@ stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, 
     cudaEventCreate(&p->ev1);
     cudaEventCreate(&p->ev2);
     cudaEventCreate(&p->ev3);
+    e = cudaMalloc(&p->d_counters, 2 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        stp_free(p);
+        return STP_ERR_CUDA;
+    }
     stp_status s = p->precision == 0 ? create_impl<float>(p) : create_impl<double>(p);
     if (s != STP_OK) {
         stp_free(p);
@@ -735,6 +778,7 @@ stp_status stp_plan(stp_problem* p, double* arrival_U, double* length_C, int* n_
         st.bridges_validated = (long long)hc.st_bridge;
         st.root_checks = (long long)hc.st_root;
         st.check_points = (long long)hc.st_points;
+        st.pair_tests = (long long)hc.st_pairs;
         st.first_solution_ms = hc.first_iter >= 0 ? (double)(hc.t_first - hc.t_start) * 1e-6 : -1.0;
         st.U = hc.U;
         st.C = hc.C;
@@ -781,16 +825,40 @@ void stp_free(stp_problem* p) {
     if (p->ev2) cudaEventDestroy(p->ev2);
     if (p->ev3) cudaEventDestroy(p->ev3);
     if (p->own_stream) cudaStreamDestroy(p->own_stream);
+    if (p->d_counters) cudaFree(p->d_counters);
+    for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     delete p;
 }
 
-// Milliseconds of the collision kernel in the last stp_check_edges call
-// (CUDA events on the problem's stream).
-stp_status stp_last_validate_ms(stp_problem* p, double* ms) {
-    if (!p || !ms) return STP_ERR_INVALID;
-    float f = 0.f;
-    STP_CUDA(p, cudaEventElapsedTime(&f, p->ev2, p->ev3));
-    *ms = f;
+stp_status stp_last_validate(stp_problem* p, double* ms, long long* points, long long* pairs) {
+    if (!p) return STP_ERR_INVALID;
+    STP_CUDA(p, cudaStreamSynchronize(p->stream));
+    if (ms) {
+        float f = 0.f;
+        STP_CUDA(p, cudaEventElapsedTime(&f, p->ev2, p->ev3));
+        *ms = f;
+    }
+    unsigned long long c[2];
+    STP_CUDA(p, cudaMemcpy(c, p->d_counters, sizeof(c), cudaMemcpyDeviceToHost));
+    if (points) *points = (long long)c[0];
+    if (pairs) *pairs = (long long)c[1];
+    return STP_OK;
+}
+
+stp_status stp_set_profiling(stp_problem* p, int on) {
+    if (!p) return STP_ERR_INVALID;
+    p->profiling = on ? 1 : 0;
+    return STP_OK;
+}
+
+stp_status stp_profile(stp_problem* p, int cap, const char** names, double* ms, long long* launches, int* n) {
+    if (!p || !n) return STP_ERR_INVALID;
+    *n = std::min(cap, kIterKernels);
+    for (int k = 0; k < *n; ++k) {
+        if (names) names[k] = kIterKernelNames[k];
+        if (ms) ms[k] = p->prof_ms[k];
+        if (launches) launches[k] = p->prof_launches[k];
+    }
     return STP_OK;
 }
 

@@ -68,6 +68,7 @@ struct EdgeBatch {
     int* hit;                // [n] 0/1
     R* clear;                // [n] (clearance mode) or nullptr
     unsigned long long* points_done;  // statistics or nullptr
+    unsigned long long* pairs_done;   // executed sphere-obstacle pair tests or nullptr
     int* err;
 };
 
@@ -98,7 +99,7 @@ struct Ctl {
     int set_count[kMaxRoots + 1];
     int n_edges, n_bedges, pad4, pad5;
     // statistics
-    unsigned long long st_ext, st_bridge, st_root, st_ins, st_points;
+    unsigned long long st_ext, st_bridge, st_root, st_ins, st_points, st_pairs;
     unsigned long long t_start, t_first, t_end;
 };
 
@@ -322,8 +323,13 @@ cudaError_t launch_finish_batch(int n, const int* hit, unsigned char* verdict, R
 
 template <typename R>
 cudaError_t launch_plan_reset(const Geom<R>& g, const State<R>& s, int max_iters, cudaStream_t st);
+// Kernels of one iteration, in launch order (profiling names).
+constexpr int kIterKernels = 10;
+extern const char* const kIterKernelNames[kIterKernels];
+// ev (optional, kIterKernels + 1 events): recorded before each kernel and after the last.
 template <typename R>
-cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cudaStream_t st);
+cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cudaStream_t st,
+                             cudaEvent_t* ev = nullptr);
 template <typename R>
 cudaError_t launch_extract_path(const State<R>& s, int dof, cudaStream_t st);
 

@@ -86,6 +86,13 @@ __device__ __forceinline__ int check_count(const R* qa, R ta, const R* qb, R tb,
     return c < 1.0 ? 1 : (int)c;
 }
 
+// Goal-grid time k dt as stored in the trees (rounded to the working precision,
+// so that slot times, node root times and the incumbent compare consistently).
+template <typename R>
+__device__ __forceinline__ double grid_t(long long k, double dt) {
+    return (double)(R)((double)k * dt);
+}
+
 // ---------------------------------------------------------------------------
 // Interval-root allocation (Sec. "Interval Root"), double precision, one thread.
 // ---------------------------------------------------------------------------
@@ -204,7 +211,7 @@ template <typename R>
 __device__ void recycle(const State<R>& S, double U) {
     Ctl* c = S.ctl;
     long long kU = c->kmin;
-    while ((double)kU * c->dt < U) ++kU;
+    while (grid_t<R>(kU, c->dt) < U) ++kU;
     int donors[kMaxRoots];
     long long held[kMaxRoots];
     int m = 0, nh = 0;
@@ -234,7 +241,7 @@ __device__ void recycle(const State<R>& S, double U) {
         c->slot_has[i] = 1;
         c->slot_active[i] = 1;
         c->slot_k[i] = found;
-        c->slot_T[i] = (double)found * c->dt;
+        c->slot_T[i] = grid_t<R>(found, c->dt);
         c->slot_gen[i] += 1;
         held[nh++] = found;
         install_root(S, i, c->slot_T[i], c->slot_gen[i], c->iter);
@@ -260,7 +267,7 @@ __global__ void k_reset(State<R> S, int max_iters) {
         c->first_iter = -1;
         c->max_iters = max_iters;
         c->n_edges = c->n_bedges = 0;
-        c->st_ext = c->st_bridge = c->st_root = c->st_ins = c->st_points = 0;
+        c->st_ext = c->st_bridge = c->st_root = c->st_ins = c->st_points = c->st_pairs = 0;
         c->t_start = global_ns();
         c->t_first = 0;
         c->t_end = 0;
@@ -303,7 +310,7 @@ __global__ void k_reset(State<R> S, int max_iters) {
                         c->slot_has[i] = 1;
                         c->slot_active[i] = 1;
                         c->slot_k[i] = k;
-                        c->slot_T[i] = (double)k * c->dt;
+                        c->slot_T[i] = grid_t<R>(k, c->dt);
                         c->slot_gen[i] = 0;
                         install_root(S, i, c->slot_T[i], 0, -1);
                         break;
@@ -1237,10 +1244,12 @@ __global__ void k_extract_path(State<R> S) {
     const Ctl* c = S.ctl;
     int n = 0;
     if (c->inc_f >= 0) {
+        // Walks are bounded by the path capacity (parents always precede
+        // children, so a longer walk cannot occur in a consistent tree).
         int len_f = 0;
-        for (int i = c->inc_f; i >= 0; i = S.fpar[i]) ++len_f;
+        for (int i = c->inc_f; i >= 0 && len_f <= S.path_cap; i = S.fpar[i]) ++len_f;
         int len_b = 0;
-        for (int i = c->inc_b; i >= 0; i = S.bpar[bofs(S, c->inc_s, i)]) ++len_b;
+        for (int i = c->inc_b; i >= 0 && len_b <= S.path_cap; i = S.bpar[bofs(S, c->inc_s, i)]) ++len_b;
         if (len_f + len_b <= S.path_cap) {
             int k = len_f - 1;
             for (int i = c->inc_f; i >= 0; i = S.fpar[i], --k) {
@@ -1276,6 +1285,7 @@ static EdgeBatch<R> ext_batch(const State<R>& S) {
     E.hit = S.ehit;
     E.clear = nullptr;
     E.points_done = &S.ctl->st_points;
+    E.pairs_done = &S.ctl->st_pairs;
     E.err = &S.ctl->err;
     return E;
 }
@@ -1295,9 +1305,14 @@ static EdgeBatch<R> bridge_batch(const State<R>& S) {
     E.hit = S.bhit;
     E.clear = nullptr;
     E.points_done = &S.ctl->st_points;
+    E.pairs_done = &S.ctl->st_pairs;
     E.err = &S.ctl->err;
     return E;
 }
+
+const char* const kIterKernelNames[kIterKernels] = {"k_sample", "k_nn", "k_steer", "k_validate(ext)",
+                                                    "k_insert", "k_bridge_clear", "k_bridge", "k_bridge_steer",
+                                                    "k_validate(bridge)", "k_publish"};
 
 template <typename R>
 cudaError_t launch_plan_reset(const Geom<R>& g, const State<R>& s, int max_iters, cudaStream_t st) {
@@ -1306,22 +1321,38 @@ cudaError_t launch_plan_reset(const Geom<R>& g, const State<R>& s, int max_iters
 }
 
 template <typename R>
-cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cudaStream_t st) {
+cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cudaStream_t st, cudaEvent_t* ev) {
     const int nn_grid = 2 * validate_grid_blocks();
+    int ne = 0;
+    auto mark = [&]() {
+        if (ev) cudaEventRecord(ev[ne], st);
+        ++ne;
+    };
+    mark();
     k_sample<R><<<(s.W + kSampleThreads - 1) / kSampleThreads, kSampleThreads, 0, st>>>(g, s);
+    mark();
     if (g.dof <= 3) k_nn<R, 3><<<nn_grid, kQT, 0, st>>>(g, s);
     else k_nn<R, kMaxDof><<<nn_grid, kQT, 0, st>>>(g, s);
+    mark();
     k_steer<R><<<1, kCtaThreads, 0, st>>>(g, s);
+    mark();
     cudaError_t err = launch_validate<R>(g, ext_batch(s), false, true, vgrid, st);
     if (err != cudaSuccess) return err;
+    mark();
     k_insert<R><<<1, kCtaThreads, 0, st>>>(g, s);
+    mark();
     k_bridge_clear<R><<<(s.W + 255) / 256, 256, 0, st>>>(s);
+    mark();
     if (g.dof <= 3) k_bridge<R, 3><<<nn_grid, kQT, 0, st>>>(g, s);
     else k_bridge<R, kMaxDof><<<nn_grid, kQT, 0, st>>>(g, s);
+    mark();
     k_bridge_steer<R><<<1, kCtaThreads, 0, st>>>(g, s);
+    mark();
     err = launch_validate<R>(g, bridge_batch(s), false, true, vgrid, st);
     if (err != cudaSuccess) return err;
+    mark();
     k_publish<R><<<1, kCtaThreads, 0, st>>>(g, s);
+    mark();
     return cudaGetLastError();
 }
 
@@ -1333,8 +1364,10 @@ cudaError_t launch_extract_path(const State<R>& s, int dof, cudaStream_t st) {
 
 template cudaError_t launch_plan_reset<float>(const Geom<float>&, const State<float>&, int, cudaStream_t);
 template cudaError_t launch_plan_reset<double>(const Geom<double>&, const State<double>&, int, cudaStream_t);
-template cudaError_t launch_iteration<float>(const Geom<float>&, const State<float>&, int, cudaStream_t);
-template cudaError_t launch_iteration<double>(const Geom<double>&, const State<double>&, int, cudaStream_t);
+template cudaError_t launch_iteration<float>(const Geom<float>&, const State<float>&, int, cudaStream_t,
+                                            cudaEvent_t*);
+template cudaError_t launch_iteration<double>(const Geom<double>&, const State<double>&, int, cudaStream_t,
+                                             cudaEvent_t*);
 template cudaError_t launch_extract_path<float>(const State<float>&, int, cudaStream_t);
 template cudaError_t launch_extract_path<double>(const State<double>&, int, cudaStream_t);
 

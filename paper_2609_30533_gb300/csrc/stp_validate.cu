@@ -38,7 +38,7 @@ __device__ __forceinline__ void test_sphere(R cx, R cy, R cz, R rs, const R (&ox
 
 template <typename R, bool ARM, int MO, bool CLEAR, bool EARLY>
 __device__ __forceinline__ void check_point(const Geom<R>& G, const R* sm, const R (&q)[kMaxDof], R t, bool& hit,
-                                            R& clr) {
+                                            R& clr, unsigned& pairs) {
     const R* sph = sm;
     const R* way = sm + G.off_way;
     const R* vel = sm + G.off_vel;
@@ -56,12 +56,14 @@ __device__ __forceinline__ void check_point(const Geom<R>& G, const R* sm, const
                 orr[j] = R(0);
             }
         }
+        const unsigned real = (unsigned)min(MO, G.M - m0);
         if (!ARM) {
             R px = q[0], py = q[1], pz = (G.dof > 2) ? q[2] : R(0);
             for (int s = 0; s < G.S; ++s) {
                 test_sphere<R, MO, CLEAR>(px + sph[4 * s], py + sph[4 * s + 1], pz + sph[4 * s + 2], sph[4 * s + 3],
                                           ox, oy, oz, orr, hit, clr);
             }
+            pairs += real * (unsigned)G.S;
         } else {
             Frame<R> F;
             frame_identity(F);
@@ -74,6 +76,7 @@ __device__ __forceinline__ void check_point(const Geom<R>& G, const R* sm, const
                     R cz = F.o[2] + px * F.X[2] + py * F.Y[2] + pz * F.Z[2];
                     test_sphere<R, MO, CLEAR>(cx, cy, cz, sph[4 * s + 3], ox, oy, oz, orr, hit, clr);
                 }
+                pairs += real * (unsigned)(G.link_start[j + 1] - G.link_start[j]);
                 if (EARLY && !CLEAR && hit) break;
             }
         }
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(256) k_validate(Geom<R> G, EdgeBatch<R> E) {
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     const long long wstride = (long long)gridDim.x * wpb * 32;
-    unsigned long long done = 0;
+    unsigned long long done = 0, pairs_total = 0;
     for (long long base = ((long long)blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; base < total; base += wstride) {
         int e0 = 0;
         if (lane == 0) {
@@ -152,15 +155,21 @@ __global__ void __launch_bounds__(256) k_validate(Geom<R> G, EdgeBatch<R> E) {
         const R ta = E.ta[e];
         const R t = ta + s * (E.tb[e] - ta);
         R clr = rinf<R>();
-        if (ARM) check_point<R, true, MO, CLEAR, EARLY>(G, sm, q, t, hit, clr);
-        else check_point<R, false, MO, CLEAR, EARLY>(G, sm, q, t, hit, clr);
+        unsigned pairs = 0;
+        if (ARM) check_point<R, true, MO, CLEAR, EARLY>(G, sm, q, t, hit, clr, pairs);
+        else check_point<R, false, MO, CLEAR, EARLY>(G, sm, q, t, hit, clr, pairs);
         if (hit) E.hit[e] = 1;
         if (CLEAR) atomic_min_r<R>(E.clear + e, clr);
         ++done;
+        pairs_total += pairs;
     }
     if (E.points_done) {
         for (int o = 16; o > 0; o >>= 1) done += __shfl_xor_sync(0xffffffffu, done, o);
         if (lane == 0 && done) atomicAdd(E.points_done, done);
+    }
+    if (E.pairs_done) {
+        for (int o = 16; o > 0; o >>= 1) pairs_total += __shfl_xor_sync(0xffffffffu, pairs_total, o);
+        if (lane == 0 && pairs_total) atomicAdd(E.pairs_done, pairs_total);
     }
 }
 

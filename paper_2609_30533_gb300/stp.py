@@ -46,7 +46,7 @@ class StpParams(C.Structure):
 class StpStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("first_solution_iter", C.c_int), ("nodes", C.c_longlong),
                 ("edges_validated", C.c_longlong), ("bridges_validated", C.c_longlong),
-                ("root_checks", C.c_longlong), ("check_points", C.c_longlong),
+                ("root_checks", C.c_longlong), ("check_points", C.c_longlong), ("pair_tests", C.c_longlong),
                 ("first_solution_ms", C.c_double), ("plan_ms", C.c_double), ("U", C.c_double),
                 ("C", C.c_double)]
 
@@ -88,8 +88,12 @@ def lib():
     L.stp_status_string.restype = C.c_char_p
     L.stp_last_error.argtypes = [C.c_void_p]
     L.stp_last_error.restype = C.c_char_p
-    L.stp_last_validate_ms.argtypes = [C.c_void_p, _D]
-    L.stp_last_validate_ms.restype = C.c_int
+    L.stp_last_validate.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+    L.stp_last_validate.restype = C.c_int
+    L.stp_set_profiling.argtypes = [C.c_void_p, C.c_int]
+    L.stp_set_profiling.restype = C.c_int
+    L.stp_profile.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), _D, C.POINTER(C.c_longlong), _I]
+    L.stp_profile.restype = C.c_int
     L.stp_tree_size.argtypes = [C.c_void_p, C.c_int, _I]
     L.stp_tree_size.restype = C.c_int
     L.stp_tree_nodes.argtypes = [C.c_void_p, C.c_int, _D, _I, _D, _D, _I, _I]
@@ -105,8 +109,8 @@ def lib():
 
 
 EXPORTED = ["stp_create_problem", "stp_plan", "stp_check_edges", "stp_free", "stp_set_stream",
-            "stp_status_string", "stp_last_error", "stp_last_validate_ms", "stp_tree_size", "stp_tree_nodes",
-            "stp_history", "stp_slots", "stp_goal_grid"]
+            "stp_status_string", "stp_last_error", "stp_last_validate", "stp_set_profiling", "stp_profile",
+            "stp_tree_size", "stp_tree_nodes", "stp_history", "stp_slots", "stp_goal_grid"]
 
 
 def status_string(s: int) -> str:
@@ -230,12 +234,32 @@ class Problem:
         if s != STP_OK:
             raise StpError(s, "stp_check_edges", self.last_error())
 
-    def last_validate_ms(self) -> float:
+    def last_validate(self):
+        """(ms, check points, pair tests) of the last collision-kernel launch."""
         ms = C.c_double()
-        s = lib().stp_last_validate_ms(self.handle, C.byref(ms))
+        pts = C.c_longlong()
+        prs = C.c_longlong()
+        s = lib().stp_last_validate(self.handle, C.byref(ms), C.byref(pts), C.byref(prs))
         if s != STP_OK:
-            raise StpError(s, "stp_last_validate_ms")
-        return ms.value
+            raise StpError(s, "stp_last_validate")
+        return ms.value, pts.value, prs.value
+
+    def set_profiling(self, on: bool):
+        s = lib().stp_set_profiling(self.handle, 1 if on else 0)
+        if s != STP_OK:
+            raise StpError(s, "stp_set_profiling")
+
+    def profile(self):
+        """{kernel name: (total ms, launches)} of the last profiled plan."""
+        cap = 16
+        names = (C.c_char_p * cap)()
+        ms = np.zeros(cap)
+        la = (C.c_longlong * cap)()
+        n = C.c_int()
+        s = lib().stp_profile(self.handle, cap, names, _dp(ms), la, C.byref(n))
+        if s != STP_OK:
+            raise StpError(s, "stp_profile")
+        return {names[k].decode(): (float(ms[k]), int(la[k])) for k in range(n.value)}
 
     def tree(self, arena: int):
         n = C.c_int()

@@ -93,7 +93,7 @@ def test_fp64_trees_match_oracle_node_for_node(case):
     P.close()
 
 
-def _first_flag(ref, tol=1e-4, band=1e-5):
+def _first_flag(ref, tol=1e-5, band=1e-5):
     for k in range(ref.iters):
         if ref.margin_hist[k] < tol or ref.clear_hist[k] < band:
             return k

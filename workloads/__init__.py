@@ -254,14 +254,18 @@ WORKLOADS = {"disc2d": disc2d, "ur5e": ur5e, "arm7": arm7}
 
 def microbench_edges(prob: Problem, n_edges: int, eta: float, H: float, seed: int = 0):
     """Random space-time edges for the collision microbenchmark: start uniform
-    in the joint box, a step of length eta in a random direction (clipped to the
-    box), duration D / v_max, start time uniform in [0, H - duration]."""
+    in the joint box, a step of length eta in a random direction (components
+    that would leave the box are reflected, so every step keeps length eta),
+    duration D / v_max, start time uniform in [0, H - duration]."""
     rng = np.random.default_rng(5000 + seed)
     d = prob.dof
     qa = rng.uniform(prob.qlo, prob.qhi, size=(n_edges, d))
     direc = rng.normal(size=(n_edges, d))
     direc /= np.linalg.norm(direc, axis=1, keepdims=True)
-    qb = np.clip(qa + eta * direc, prob.qlo, prob.qhi)
+    step = eta * direc
+    out = (qa + step > prob.qhi) | (qa + step < prob.qlo)
+    step[out] = -step[out]
+    qb = np.clip(qa + step, prob.qlo, prob.qhi)
     D = np.linalg.norm(qb - qa, axis=1)
     dur = D / prob.vmax
     ta = rng.uniform(0.0, 1.0, size=n_edges) * np.maximum(H - dur, 0.0)
