@@ -161,6 +161,49 @@ def cpu_baseline(args):
                 args.cpu_iters, WORKLOAD, edges, secs)}
 
 
+def microbench(args, P, prob, prm, stream, flush, rank, local):
+    """Collision kernel alone on 2^20 UR5e edges resident on the device, with
+    and without early exit; kernel time from CUDA events around the launch."""
+    import torch
+    n = args.micro_edges
+    qa, ta, qb, tb = WL.microbench_edges(prob, n, prm.eta, prm.H, seed=rank)
+    dev = torch.device("cuda", local)
+    tq = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev) for a in (qa, ta, qb, tb)]
+    ver = torch.zeros(n, dtype=torch.uint8, device=dev)
+    micro = {}
+    for label, early in (("early_exit", True), ("no_early_exit", False)):
+        for _ in range(3):
+            P.check_edges_device(tq[0].data_ptr(), tq[1].data_ptr(), tq[2].data_ptr(), tq[3].data_ptr(), n,
+                                 ver.data_ptr(), early_exit=early)
+        kms, kpts, kpairs, call_ms = [], 0, 0, []
+        for _ in range(5):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.check_edges_device(tq[0].data_ptr(), tq[1].data_ptr(), tq[2].data_ptr(), tq[3].data_ptr(), n,
+                                 ver.data_ptr(), early_exit=early)
+            e1.record(stream)
+            e1.synchronize()
+            call_ms.append(e0.elapsed_time(e1))
+            ms, pts, prs = P.last_validate()
+            kms.append(ms)
+            kpts, kpairs = pts, prs
+        k_ms = statistics.median(kms)
+        flops = kpairs * 8 + kpts * point_flops(prob)
+        micro[label] = {"edges_per_s": n / (statistics.median(call_ms) * 1e-3),
+                        "kernel_ms": k_ms, "check_points": kpts, "pair_tests": kpairs,
+                        "achieved_tflops": flops / (k_ms * 1e-3) / 1e12,
+                        "free_fraction": float(ver.float().mean().item())}
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    max_mhz = float(_peaks().get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(n_sm, max_mhz)
+    for m in micro.values():
+        m["frac"] = m["achieved_tflops"] / peak
+    return micro, peak
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -172,6 +215,8 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=8)
     ap.add_argument("--micro-edges", type=int, default=1 << 20)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", default="", choices=["", "micro"],
+                    help="micro: run only the collision microbenchmark (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -199,6 +244,10 @@ def main():
     stream = torch.cuda.Stream()
     P.set_stream(stream.cuda_stream)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    if args.only == "micro":
+        micro, peak = microbench(args, P, prob, prm, stream, flush, rank, local)
+        print(json.dumps({"microbench": dict(micro, n_edges=args.micro_edges, peak_tflops=peak)}))
+        return
 
     def step_timed():
         with torch.cuda.stream(stream):
@@ -278,45 +327,10 @@ def main():
     torch.cuda.synchronize()
     e2e_secs = time.perf_counter() - t0
 
-    # Collision microbenchmark: 2^20 edges resident on the device.
+    micro, peak = microbench(args, P, prob, prm, stream, flush, rank, local)
     n = args.micro_edges
-    qa, ta, qb, tb = WL.microbench_edges(prob, n, prm.eta, prm.H, seed=rank)
-    dev = torch.device("cuda", local)
-    tq = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev) for a in (qa, ta, qb, tb)]
-    ver = torch.zeros(n, dtype=torch.uint8, device=dev)
-    micro = {}
-    for label, early in (("early_exit", True), ("no_early_exit", False)):
-        for _ in range(3):
-            P.check_edges_device(tq[0].data_ptr(), tq[1].data_ptr(), tq[2].data_ptr(), tq[3].data_ptr(), n,
-                                 ver.data_ptr(), early_exit=early)
-        kms, kpts, kpairs, call_ms = [], 0, 0, []
-        for _ in range(5):
-            with torch.cuda.stream(stream):
-                flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            P.check_edges_device(tq[0].data_ptr(), tq[1].data_ptr(), tq[2].data_ptr(), tq[3].data_ptr(), n,
-                                 ver.data_ptr(), early_exit=early)
-            e1.record(stream)
-            e1.synchronize()
-            call_ms.append(e0.elapsed_time(e1))
-            ms, pts, prs = P.last_validate()
-            kms.append(ms)
-            kpts, kpairs = pts, prs
-        k_ms = statistics.median(kms)
-        flops = kpairs * 8 + kpts * point_flops(prob)
-        micro[label] = {"edges_per_s": n / (statistics.median(call_ms) * 1e-3),
-                        "kernel_ms": k_ms, "check_points": kpts, "pair_tests": kpairs,
-                        "achieved_tflops": flops / (k_ms * 1e-3) / 1e12,
-                        "free_fraction": float(ver.float().mean().item())}
-
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    peaks = _peaks()
-    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = fp32_peak_tflops(n_sm, max_mhz)
-    for m in micro.values():
-        m["frac"] = m["achieved_tflops"] / peak
+    max_mhz = float(_peaks().get("sm_max_mhz", 2070.0))
 
     # Aggregate over ranks: edges summed, time = max over ranks.
     vals = torch.tensor([float(edges), total_ms, float(e2e_edges), e2e_secs], dtype=torch.float64, device="cuda")

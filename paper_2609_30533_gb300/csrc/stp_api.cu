@@ -79,12 +79,18 @@ struct stp_problem {
 
 namespace {
 
+// Last failure of any call (also of calls that have no problem handle yet).
+thread_local std::string g_last_error;
+
+// A non-sticky error left by an earlier runtime call of this thread (ours or
+// the caller's) must not be reported by our own launch checks.
+void clear_stale_error() { (void)cudaGetLastError(); }
+
 stp_status cuda_fail(stp_problem* p, cudaError_t e, const char* where) {
-    if (p) {
-        char buf[256];
-        snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
-        p->last_error = buf;
-    }
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+    if (p) p->last_error = buf;
+    g_last_error = buf;
     return STP_ERR_CUDA;
 }
 
@@ -245,6 +251,7 @@ size_t layout_state(stp_problem* p, char* base, R** blob_out, size_t blob_bytes,
     s.w_ins = cv.take<int>(W);
     s.w_bedge = cv.take<int>(W);
     s.w_xn = cv.take<R>((size_t)W * kDP);
+    s.w_nnkey = cv.take<unsigned long long>(W);
     s.qlist = cv.take<int>((size_t)(N + 1) * W);
     s.tile_cnt = cv.take<int>((size_t)(N + 1) * kMaxQTiles);
     s.part_k1 = cv.take<R>((size_t)W * kMaxTiles);
@@ -264,14 +271,12 @@ size_t layout_state(stp_problem* p, char* base, R** blob_out, size_t blob_bytes,
     s.eta_ = cv.take<R>((size_t)2 * W);
     s.etb = cv.take<R>((size_t)2 * W);
     s.ecnt = cv.take<int>((size_t)2 * W);
-    s.eoff = cv.take<long long>((size_t)2 * W + 1);
     s.ehit = cv.take<int>((size_t)2 * W);
     s.bqa = cv.take<R>((size_t)W * kDP);
     s.bqb = cv.take<R>((size_t)W * kDP);
     s.bta = cv.take<R>(W);
     s.btb = cv.take<R>(W);
     s.bcnt = cv.take<int>(W);
-    s.boff = cv.take<long long>((size_t)W + 1);
     s.bhit = cv.take<int>(W);
     s.U_hist = cv.take<double>(std::max(p->prm.max_iters, 1));
     s.path = cv.take<R>((size_t)p->path_cap * kDP);
@@ -378,6 +383,7 @@ stp_status create_impl(stp_problem* p) {
     STP_CUDA(p, cudaMemsetAsync(hit, 0, sizeof(int) * ng, st));
     EdgeBatch<R> E;
     std::memset(&E, 0, sizeof(E));
+    E.done = nullptr;
     E.qa = qall;
     E.qb = qall;
     E.ta = tdev;
@@ -608,10 +614,11 @@ const char* stp_status_string(stp_status s) {
     return "STP_UNKNOWN";
 }
 
-const char* stp_last_error(const stp_problem* p) { return p ? p->last_error.c_str() : ""; }
+const char* stp_last_error(const stp_problem* p) { return p ? p->last_error.c_str() : g_last_error.c_str(); }
 
 stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, const double* q_start,
                               const double* q_goal, const stp_params* params, stp_problem** out) {
+    clear_stale_error();
     if (!out) return STP_ERR_INVALID;
     *out = nullptr;
     if (!robot || !obs || !q_start || !q_goal || !params) return STP_ERR_INVALID;
@@ -701,12 +708,13 @@ stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, 
     int dev_count = 0;
     cudaError_t e = cudaGetDeviceCount(&dev_count);
     if (e != cudaSuccess || dev_count == 0) {
-        p->last_error = "no CUDA device";
+        g_last_error = "no CUDA device";
         delete p;
         return STP_ERR_CUDA;
     }
     e = cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
+        cuda_fail(p, e, "cudaStreamCreateWithFlags");
         delete p;
         return STP_ERR_CUDA;
     }
@@ -717,6 +725,7 @@ stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, 
     cudaEventCreate(&p->ev3);
     e = cudaMalloc(&p->d_counters, 2 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
+        cuda_fail(p, e, "cudaMalloc(counters)");
         stp_free(p);
         return STP_ERR_CUDA;
     }
@@ -737,6 +746,7 @@ stp_status stp_set_stream(stp_problem* p, void* cuda_stream) {
 
 stp_status stp_plan(stp_problem* p, double* arrival_U, double* length_C, int* n_path, double* path, int cap,
                     stp_stats* stats) {
+    clear_stale_error();
     if (!p) return STP_ERR_INVALID;
     if (path && cap < 0) return STP_ERR_INVALID;
     stp_stats st;
@@ -805,6 +815,7 @@ stp_status stp_plan(stp_problem* p, double* arrival_U, double* length_C, int* n_
 
 stp_status stp_check_edges(stp_problem* p, int n_edges, const void* qa, const void* ta, const void* qb,
                            const void* tb, int flags, unsigned char* verdict, void* min_clearance, int* n_checks) {
+    clear_stale_error();
     if (!p || n_edges < 0 || n_edges > (1 << 26)) return STP_ERR_INVALID;
     if (n_edges == 0) return STP_OK;
     if (!qa || !ta || !qb || !tb || !verdict) return STP_ERR_INVALID;

@@ -70,6 +70,7 @@ struct EdgeBatch {
     unsigned long long* points_done;  // statistics or nullptr
     unsigned long long* pairs_done;   // executed sphere-obstacle pair tests or nullptr
     int* err;
+    const int* done;                  // planner: skip the launch when set (or nullptr)
 };
 
 // ---------------------------------------------------------------------------
@@ -97,7 +98,7 @@ struct Ctl {
     int n_s[kMaxRoots], snap_s[kMaxRoots];
     // per-iteration NN bookkeeping
     int set_count[kMaxRoots + 1];
-    int n_edges, n_bedges, pad4, pad5;
+    int pad4, pad5, pad6, pad7;
     // statistics
     unsigned long long st_ext, st_bridge, st_root, st_ins, st_points, st_pairs;
     unsigned long long t_start, t_first, t_end;
@@ -125,6 +126,7 @@ struct State {
     int* w_status; int* w_set; R* w_xr; double* w_T; int* w_parent; R* w_key; R* w_xnew;
     int* w_edge; int* w_root_edge; int* w_ins; int* w_bedge;
     R* w_xn;           // [W][kDP] steering source x_n
+    unsigned long long* w_nnkey;  // [W] packed FP32 NN key (key bits << 32 | index)
     // NN
     int* qlist;        // [(N+1)][W]
     int* tile_cnt;     // [(N+1)][kMaxQTiles]
@@ -136,8 +138,8 @@ struct State {
     int* b_set; int* b_idx; R* b_k1; R* b_k2;  // per worker best bridge candidate
     double* b_U; double* b_C;
     // edges
-    R* eqa; R* eqb; R* eta_; R* etb; int* ecnt; long long* eoff; int* ehit;  // [2W]
-    R* bqa; R* bqb; R* bta; R* btb; int* bcnt; long long* boff; int* bhit;  // [W]
+    R* eqa; R* eqb; R* eta_; R* etb; int* ecnt; int* ehit;  // [2W]: entry 2w root check, 2w+1 extension
+    R* bqa; R* bqb; R* bta; R* btb; int* bcnt; int* bhit;    // [W]: bridge of worker w
     // history
     double* U_hist;
     // path
@@ -324,7 +326,7 @@ cudaError_t launch_finish_batch(int n, const int* hit, unsigned char* verdict, R
 template <typename R>
 cudaError_t launch_plan_reset(const Geom<R>& g, const State<R>& s, int max_iters, cudaStream_t st);
 // Kernels of one iteration, in launch order (profiling names).
-constexpr int kIterKernels = 10;
+constexpr int kIterKernels = 8;
 extern const char* const kIterKernelNames[kIterKernels];
 // ev (optional, kIterKernels + 1 events): recorded before each kernel and after the last.
 template <typename R>

@@ -11,16 +11,19 @@
 //   k_nn            tile scheduler over (tree set, query tile, node tile):
 //                   nodes staged in shared memory, one query per thread,
 //                   argmin of the directed metric (Eq. space-time-metric) or the
-//                   configuration distance; partials reduced by the last CTA of
-//                   each query tile (deterministic, ties to the lowest index).
-//   k_steer         single CTA: steering (Algorithm 1 / Eq. max-speed-extension),
-//                   horizon check, edge entries and their check-point prefix.
+//                   configuration distance; FP32 keys reduced with a packed
+//                   64-bit atomicMin (key, index), FP64 keys by the last CTA of
+//                   each query tile (both deterministic, ties to lowest index).
+//   k_steer         one thread per worker: steering (Algorithm 1 /
+//                   Eq. max-speed-extension), horizon check, edge entries
+//                   (virtual-root workers are steered inside k_sample).
 //   k_validate      collision kernel over all extension (and root) checks.
 //   k_insert        single CTA: ordered insertion in worker order, virtual-root
 //                   materialisation, bridge query registration.
 //   k_bridge        tile scheduler: best-ranked admissible vertex of the
-//                   opposite start-of-iteration set (arrival time, then rho).
-//   k_bridge_steer  single CTA: candidate (U, C), improvement test, bridge edges.
+//                   opposite start-of-iteration set (arrival time, then rho);
+//                   the last CTA of a query tile computes the candidate (U, C),
+//                   tests the improvement and emits the bridge edge.
 //   k_validate      collision kernel over bridge edges.
 //   k_publish       single CTA: lexicographic min of (U, C, worker), incumbent
 //                   update, interval repartition or root recycling.
@@ -266,7 +269,6 @@ __global__ void k_reset(State<R> S, int max_iters) {
         c->inc_f = c->inc_s = c->inc_b = -1;
         c->first_iter = -1;
         c->max_iters = max_iters;
-        c->n_edges = c->n_bedges = 0;
         c->st_ext = c->st_bridge = c->st_root = c->st_ins = c->st_points = c->st_pairs = 0;
         c->t_start = global_ns();
         c->t_first = 0;
@@ -324,6 +326,94 @@ __global__ void k_reset(State<R> S, int max_iters) {
 }
 
 // ---------------------------------------------------------------------------
+// Steering and edge entries. Worker w owns extension-batch entries 2w (the
+// point check of its sampled goal root, interval root only) and 2w+1 (the
+// extension edge); a count of 0 leaves an entry out of the batch.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ int check_count_r(const R* qa, R ta, const R* qb, R tb, int dof, R vmax, R res) {
+    R s2 = R(0);
+    for (int j = 0; j < dof; ++j) {
+        R e = qb[j] - qa[j];
+        s2 += e * e;
+    }
+    R dt = tb - ta;
+    R L = rsqrt_r(s2);
+    R Lt = vmax * (dt < R(0) ? -dt : dt);
+    if (Lt > L) L = Lt;
+    R c = ceil(L / res - R(1e-3));
+    return c < R(1) ? 1 : (int)c;
+}
+
+// Steer from x_n toward the worker's sample (Algorithm 1 / Eq.
+// max-speed-extension), check the horizon and emit the entries. Returns false
+// when the attempt is skipped.
+template <typename R>
+__device__ bool steer_and_emit(const Geom<R>& G, const State<R>& S, int w, int set, bool virt, const R* xn) {
+    const int dof = G.dof;
+    const R* xr = S.w_xr + (size_t)w * kDP;
+    R xw[kDP];
+    for (int j = 0; j < kDP; ++j) xw[j] = R(0);
+    R tnew;
+    if (S.variant == 0) {
+        const R tn = xn[kDP - 1], tr = xr[kDP - 1];
+        const R D = qdist(xn, xr, dof);
+        if (virt) {
+            // The virtual root is the sole source: rho must be finite.
+            const R Delta = tn - tr;
+            if (!(Delta > R(0)) || !(D <= G.vmax * Delta)) return false;
+        }
+        const R rho = rsqrt_r((D * D + G.vmax * G.vmax * (tr - tn) * (tr - tn)) / R(2));
+        const R eta = (R)S.eta;
+        const R alpha = (eta / rho) < R(1) ? (eta / rho) : R(1);
+        for (int j = 0; j < dof; ++j) xw[j] = xn[j] + alpha * (xr[j] - xn[j]);
+        tnew = tn + alpha * (tr - tn);
+    } else {
+        const R D = qdist(xn, xr, dof);
+        if (!(D > R(0))) return false;
+        const R eta = (R)S.eta;
+        const R sc = (eta / D) < R(1) ? (eta / D) : R(1);
+        for (int j = 0; j < dof; ++j) xw[j] = xn[j] + sc * (xr[j] - xn[j]);
+        const R Dn = qdist(xn, xw, dof);
+        tnew = xn[kDP - 1] + (set == 0 ? R(1) : R(-1)) * Dn / G.vmax;
+    }
+    xw[kDP - 1] = tnew;
+    if (tnew < R(0) || tnew > (R)S.H) return false;
+    R* xo = S.w_xnew + (size_t)w * kDP;
+    R* xs = S.w_xn + (size_t)w * kDP;
+    for (int j = 0; j < kDP; ++j) {
+        xo[j] = xw[j];
+        xs[j] = xn[j];
+    }
+    const R res = (R)S.res;
+    if (S.variant == 0) {
+        // Point check of the sampled goal root (q_g, T).
+        const int e = 2 * w;
+        R* qa = S.eqa + (size_t)e * kDP;
+        R* qb = S.eqb + (size_t)e * kDP;
+        for (int j = 0; j < kDP; ++j) qa[j] = qb[j] = R(0);
+        for (int j = 0; j < kMaxDof; ++j) qa[j] = qb[j] = S.qg[j];
+        const R T = (R)S.w_T[w];
+        S.eta_[e] = T;
+        S.etb[e] = T;
+        S.ecnt[e] = 1;
+        S.w_root_edge[w] = e;
+    }
+    const int e = 2 * w + 1;
+    R* qa = S.eqa + (size_t)e * kDP;
+    R* qb = S.eqb + (size_t)e * kDP;
+    for (int j = 0; j < kDP; ++j) {
+        qa[j] = xn[j];
+        qb[j] = xw[j];
+    }
+    S.eta_[e] = xn[kDP - 1];
+    S.etb[e] = tnew;
+    S.ecnt[e] = check_count_r(xn, xn[kDP - 1], xw, tnew, dof, G.vmax, res);
+    S.w_edge[w] = e;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // k_sample: one thread per worker.
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -337,6 +427,13 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(Geom<R> G, State<R> S
     const bool fwd = ((w + k) & 1) == 0;
     int status = kSkip, set = 0;
     R* xr = S.w_xr + (size_t)w * kDP;
+    S.ecnt[2 * w] = 0;
+    S.ecnt[2 * w + 1] = 0;
+    S.ehit[2 * w] = 0;
+    S.ehit[2 * w + 1] = 0;
+    S.w_edge[w] = -1;
+    S.w_root_edge[w] = -1;
+    S.w_nnkey[w] = ~0ull;
     uint32_t d[12];
     philox4x32_10(0, (uint32_t)w, (uint32_t)k, S.problem_id, S.key0, S.key1, d);
     philox4x32_10(1, (uint32_t)w, (uint32_t)k, S.problem_id, S.key0, S.key1, d + 4);
@@ -392,6 +489,14 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(Geom<R> G, State<R> S
             status = kNN;
         }
     }
+    if (status == kVirtual) {
+        // The virtual root (q_g, T) is the sole source: steer at once.
+        R xn[kDP];
+        for (int j = 0; j < kDP; ++j) xn[j] = R(0);
+        for (int j = 0; j < kMaxDof; ++j) xn[j] = S.qg[j];
+        xn[kDP - 1] = (R)S.w_T[w];
+        if (!steer_and_emit(G, S, w, set, true, xn)) status = kSkip;
+    }
     S.w_status[w] = status;
     S.w_set[w] = set;
     S.w_parent[w] = -1;
@@ -405,7 +510,6 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(Geom<R> G, State<R> S
 // Tile scheduler shared by the NN and bridge scans.
 // ---------------------------------------------------------------------------
 struct TileSets {
-    int nsets;
     int pre[kMaxRoots + 2];  // tile prefix per set
     int nq[kMaxRoots + 1];
     int nn[kMaxRoots + 1];   // nodes
@@ -433,6 +537,13 @@ __device__ __forceinline__ bool key_less(R a1, R a2, int ai, R b1, R b2, int bi)
     if (a1 != b1) return a1 < b1;
     if (a2 != b2) return a2 < b2;
     return ai < bi;
+}
+
+// Packed 64-bit NN key: non-negative FP32 key bits above the node index, so
+// that an unsigned atomicMin keeps the smallest key and, among equal keys, the
+// lowest index.
+__device__ __forceinline__ unsigned long long pack_key(float k, int idx) {
+    return ((unsigned long long)__float_as_uint(k) << 32) | (unsigned)idx;
 }
 
 // NN scan. Set 0 = forward arena; set 1+i = backward segment i. DQ = number of
@@ -526,36 +637,69 @@ __global__ void __launch_bounds__(kQT) k_nn(Geom<R> G, State<R> S) {
                 }
             }
         }
-        if (w >= 0) {
-            S.part_k2[(size_t)w * kMaxTiles + ntile] = best;
-            S.part_idx[(size_t)w * kMaxTiles + ntile] = bidx;
-        }
-        __threadfence();
-        __syncthreads();
-        if (t == 0) {
-            int old = atomicAdd(&S.tile_cnt[s * kMaxQTiles + qt], 1);
-            s_last = (old == nt - 1);
-        }
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
+        if constexpr (sizeof(R) == 4) {
+            if (w >= 0 && best < rinf<R>()) atomicMin(S.w_nnkey + w, pack_key((float)best, bidx));
+        } else {
+            // FP64: keys do not fit a 64-bit word with the index; per-tile
+            // partials, reduced in tile order by the last CTA of the query tile.
             if (w >= 0) {
-                R b = rinf<R>();
-                int bi = 0x7fffffff;
-                for (int j = 0; j < nt; ++j) {
-                    R kk = *(volatile R*)(S.part_k2 + (size_t)w * kMaxTiles + j);
-                    int ii = *(volatile int*)(S.part_idx + (size_t)w * kMaxTiles + j);
-                    if (kk < b || (kk == b && ii < bi)) {
-                        b = kk;
-                        bi = ii;
-                    }
-                }
-                S.w_key[w] = b;
-                S.w_parent[w] = (b < rinf<R>()) ? bi : -1;
+                S.part_k2[(size_t)w * kMaxTiles + ntile] = best;
+                S.part_idx[(size_t)w * kMaxTiles + ntile] = bidx;
             }
-            if (t == 0) S.tile_cnt[s * kMaxQTiles + qt] = 0;
+            __threadfence();
+            __syncthreads();
+            if (t == 0) {
+                int old = atomicAdd(&S.tile_cnt[s * kMaxQTiles + qt], 1);
+                s_last = (old == nt - 1);
+            }
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                if (w >= 0) {
+                    R b = rinf<R>();
+                    int bi = 0x7fffffff;
+                    for (int j = 0; j < nt; ++j) {
+                        R kk = __ldcg(S.part_k2 + (size_t)w * kMaxTiles + j);
+                        int ii = __ldcg(S.part_idx + (size_t)w * kMaxTiles + j);
+                        if (kk < b || (kk == b && ii < bi)) {
+                            b = kk;
+                            bi = ii;
+                        }
+                    }
+                    S.w_parent[w] = (b < rinf<R>()) ? bi : -1;
+                }
+                if (t == 0) S.tile_cnt[s * kMaxQTiles + qt] = 0;
+            }
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// k_steer: one thread per worker with an NN query.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kSampleThreads) k_steer(Geom<R> G, State<R> S) {
+    const Ctl* c = S.ctl;
+    if (c->done) return;
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= S.W || S.w_status[w] != kNN) return;
+    int p;
+    if constexpr (sizeof(R) == 4) {
+        const unsigned long long key = S.w_nnkey[w];
+        p = (key == ~0ull) ? -1 : (int)(unsigned)(key & 0xffffffffull);
+    } else {
+        p = S.w_parent[w];
+    }
+    S.w_parent[w] = p;
+    const int set = S.w_set[w];
+    bool ok = p >= 0;
+    if (ok) {
+        const R* x = set == 0 ? fnode(S, p) : bnode(S, set - 1, p);
+        R xn[kDP];
+        for (int j = 0; j < kDP; ++j) xn[j] = x[j];
+        ok = steer_and_emit(G, S, w, set, false, xn);
+    }
+    if (!ok) S.w_status[w] = kSkip;
 }
 
 // ---------------------------------------------------------------------------
@@ -587,139 +731,8 @@ __device__ __forceinline__ long long cta_exclusive_scan(long long v, long long* 
 }
 
 // ---------------------------------------------------------------------------
-// k_steer: single CTA. Steering, edge entries, check-point prefix.
-// ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(kCtaThreads) k_steer(Geom<R> G, State<R> S) {
-    Ctl* c = S.ctl;
-    if (c->done) return;
-    __shared__ long long sh[32];
-    const int per = (S.W + kCtaThreads - 1) / kCtaThreads;
-    const int w0 = threadIdx.x * per;
-    const int dof = G.dof;
-    // Pass 1: steer and count entries / points.
-    int n_ent = 0;
-    long long n_pts = 0;
-    for (int w = w0; w < min(S.W, w0 + per); ++w) {
-        S.w_edge[w] = -1;
-        S.w_root_edge[w] = -1;
-        const int st = S.w_status[w];
-        if (st == kSkip) continue;
-        const int set = S.w_set[w];
-        const R* xr = S.w_xr + (size_t)w * kDP;
-        R xn[kDP];
-        if (st == kVirtual) {
-            for (int j = 0; j < kDP; ++j) xn[j] = R(0);
-            for (int j = 0; j < kMaxDof; ++j) xn[j] = S.qg[j];
-            xn[kDP - 1] = (R)S.w_T[w];
-        } else {
-            const int p = S.w_parent[w];
-            if (p < 0) {
-                S.w_status[w] = kSkip;
-                continue;
-            }
-            const R* x = set == 0 ? fnode(S, p) : bnode(S, set - 1, p);
-            for (int j = 0; j < kDP; ++j) xn[j] = x[j];
-        }
-        R* xw = S.w_xnew + (size_t)w * kDP;
-        for (int j = 0; j < kDP; ++j) xw[j] = R(0);
-        R tnew;
-        if (S.variant == 0) {
-            // Algorithm 1: alpha = min(1, eta / rho), x_new = x_n + alpha (x_r - x_n).
-            const R tn = xn[kDP - 1], tr = xr[kDP - 1];
-            const R D = qdist(xn, xr, dof);
-            if (st == kVirtual) {
-                // The virtual root is the sole source: rho must be finite.
-                const R Delta = tn - tr;
-                if (!(Delta > R(0)) || !(D <= G.vmax * Delta)) {
-                    S.w_status[w] = kSkip;
-                    continue;
-                }
-            }
-            const R rho = rsqrt_r((D * D + G.vmax * G.vmax * (tr - tn) * (tr - tn)) / R(2));
-            const R eta = (R)S.eta;
-            const R alpha = (eta / rho) < R(1) ? (eta / rho) : R(1);
-            for (int j = 0; j < dof; ++j) xw[j] = xn[j] + alpha * (xr[j] - xn[j]);
-            tnew = tn + alpha * (tr - tn);
-        } else {
-            // Eq. max-speed-extension: configuration step capped at eta.
-            const R D = qdist(xn, xr, dof);
-            if (!(D > R(0))) {
-                S.w_status[w] = kSkip;
-                continue;
-            }
-            const R eta = (R)S.eta;
-            const R s = (eta / D) < R(1) ? (eta / D) : R(1);
-            for (int j = 0; j < dof; ++j) xw[j] = xn[j] + s * (xr[j] - xn[j]);
-            const R Dn = qdist(xn, xw, dof);
-            tnew = xn[kDP - 1] + (set == 0 ? R(1) : R(-1)) * Dn / G.vmax;
-        }
-        xw[kDP - 1] = tnew;
-        if (tnew < R(0) || tnew > (R)S.H) {
-            S.w_status[w] = kSkip;
-            continue;
-        }
-        // Entries: root check (interval root: the sampled goal state) + extension.
-        if (S.variant == 0) {
-            n_ent += 1;
-            n_pts += 1;
-        }
-        n_ent += 1;
-        n_pts += check_count(xn, xn[kDP - 1], xw, tnew, dof, G.vmax_d, S.res);
-        R* xs = S.w_xn + (size_t)w * kDP;
-        for (int j = 0; j < kDP; ++j) xs[j] = xn[j];
-    }
-    long long tot_e, tot_p;
-    const long long ebase = cta_exclusive_scan(n_ent, sh, &tot_e);
-    const long long pbase = cta_exclusive_scan(n_pts, sh, &tot_p);
-    // Pass 2: write entries.
-    int e = (int)ebase;
-    long long p = pbase;
-    for (int w = w0; w < min(S.W, w0 + per); ++w) {
-        if (S.w_status[w] == kSkip) continue;
-        const R* xn = S.w_xn + (size_t)w * kDP;
-        const R* xw = S.w_xnew + (size_t)w * kDP;
-        if (S.variant == 0) {
-            // point check of (q_g, T)
-            R* qa = S.eqa + (size_t)e * kDP;
-            R* qb = S.eqb + (size_t)e * kDP;
-            for (int j = 0; j < kDP; ++j) qa[j] = qb[j] = R(0);
-            for (int j = 0; j < kMaxDof; ++j) qa[j] = qb[j] = S.qg[j];
-            const R T = (R)S.w_T[w];
-            S.eta_[e] = T;
-            S.etb[e] = T;
-            S.ecnt[e] = 1;
-            S.eoff[e] = p;
-            S.ehit[e] = 0;
-            S.w_root_edge[w] = e;
-            ++e;
-            p += 1;
-        }
-        R* qa = S.eqa + (size_t)e * kDP;
-        R* qb = S.eqb + (size_t)e * kDP;
-        for (int j = 0; j < kDP; ++j) {
-            qa[j] = xn[j];
-            qb[j] = xw[j];
-        }
-        S.eta_[e] = xn[kDP - 1];
-        S.etb[e] = xw[kDP - 1];
-        const int cc = check_count(xn, xn[kDP - 1], xw, xw[kDP - 1], dof, G.vmax_d, S.res);
-        S.ecnt[e] = cc;
-        S.eoff[e] = p;
-        S.ehit[e] = 0;
-        S.w_edge[w] = e;
-        ++e;
-        p += cc;
-    }
-    if (threadIdx.x == 0) {
-        c->n_edges = (int)tot_e;
-        S.eoff[tot_e] = tot_p;
-        if (S.variant == 0) c->st_root += (unsigned long long)S.W;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// k_insert: single CTA. Ordered insertion in worker order.
+// k_insert: single CTA. Ordered insertion in worker order; also clears the
+// per-worker bridge state of the iteration.
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(kCtaThreads) k_insert(Geom<R> G, State<R> S) {
@@ -750,6 +763,10 @@ __global__ void __launch_bounds__(kCtaThreads) k_insert(Geom<R> G, State<R> S) {
         const int w = r0 + t;
         int ok = 0, nodes = 0, set = -1, virt = 0, ext = 0;
         if (w < S.W) {
+            S.b_idx[w] = -1;
+            S.w_bedge[w] = -1;
+            S.bcnt[w] = 0;
+            S.bhit[w] = 0;
             const int e = S.w_edge[w];
             if (e >= 0) {
                 const int re = S.w_root_edge[w];
@@ -873,21 +890,67 @@ __global__ void __launch_bounds__(kCtaThreads) k_insert(Geom<R> G, State<R> S) {
     }
 }
 
+// Candidate (U, C) of worker w's bridge and, if it improves the incumbent at
+// the start of the iteration, its edge entry (entry index w of the bridge batch).
+template <typename R>
+__device__ int bridge_emit(const Geom<R>& G, const State<R>& S, int w, double U0, double C0) {
+    const bool fwd = S.w_set[w] == 0;
+    const R* f;
+    const R* b;
+    R cf, cb, troot;
+    if (fwd) {
+        f = fnode(S, S.w_ins[w]);
+        cf = S.fcost[S.w_ins[w]];
+        const size_t o = bofs(S, S.b_set[w], S.b_idx[w]);
+        b = bnode(S, S.b_set[w], S.b_idx[w]);
+        cb = S.bcost[o];
+        troot = S.btroot[o];
+    } else {
+        const int seg = S.w_set[w] - 1;
+        const size_t o = bofs(S, seg, S.w_ins[w]);
+        b = bnode(S, seg, S.w_ins[w]);
+        cb = S.bcost[o];
+        troot = S.btroot[o];
+        f = fnode(S, S.b_idx[w]);
+        cf = S.fcost[S.b_idx[w]];
+    }
+    const R D = qdist(f, b, G.dof);
+    const double Uc = (double)troot;
+    const double Cc = ((double)cf + (double)D) + (double)cb;
+    const bool improves = (Uc < U0) || (Uc == U0 && Cc < C0);
+    if (!improves) return 0;
+    S.b_U[w] = Uc;
+    S.b_C[w] = Cc;
+    R* qa = S.bqa + (size_t)w * kDP;
+    R* qb = S.bqb + (size_t)w * kDP;
+    for (int j = 0; j < kDP; ++j) {
+        qa[j] = f[j];
+        qb[j] = b[j];
+    }
+    S.bta[w] = f[kDP - 1];
+    S.btb[w] = b[kDP - 1];
+    S.bcnt[w] = check_count_r(f, f[kDP - 1], b, b[kDP - 1], G.dof, G.vmax, (R)S.res);
+    S.w_bedge[w] = w;
+    return 1;
+}
+
 // ---------------------------------------------------------------------------
 // k_bridge: best-ranked admissible vertex of the opposite start-of-iteration set.
 // Set 0: queries = backward-inserted nodes, vertices = forward arena [0, snap_f).
 // Set 1: queries = forward-inserted nodes, vertices = all backward segments
 //        [0, snap_s[i]) concatenated in segment order; active iff troot < U.
-// Rank: (arrival time, rho^2, index) lexicographic.
+// Rank: (arrival time, rho^2, index) lexicographic. The last CTA of a query
+// tile reduces the per-tile partials in tile order and emits the bridge edges.
 // ---------------------------------------------------------------------------
 template <typename R, int DQ>
 __global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
-    const Ctl* c = S.ctl;
+    Ctl* c = S.ctl;
     if (c->done) return;
     __shared__ int seg_pre[kMaxRoots + 1];
     __shared__ int s_nq[2], s_nn[2], s_nt[2], s_nts[2], s_pre[3];
     __shared__ R sx[kQT][DQ + 2];
     __shared__ int s_last;
+    __shared__ int s_emitted;
     const int t = threadIdx.x;
     if (t == 0) {
         int acc = 0;
@@ -910,11 +973,12 @@ __global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
             tacc += tiles;
         }
         s_pre[2] = tacc;
+        s_emitted = 0;
     }
     __syncthreads();
     const int total = s_pre[2];
     const R v2 = G.vmax * G.vmax;
-    const double U0 = c->U;
+    const double U0 = c->U, C0 = c->C;
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
         const int s = tile < s_pre[1] ? 0 : 1;
         const int local = tile - s_pre[s];
@@ -994,13 +1058,17 @@ __global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
         __syncthreads();
         if (s_last) {
             __threadfence();
+            int emitted = 0;
             if (w >= 0) {
                 R k1 = rinf<R>(), k2 = rinf<R>();
                 int bi = 0x7fffffff;
+                const R* p1 = S.part_k1 + (size_t)w * kMaxTiles;
+                const R* p2 = S.part_k2 + (size_t)w * kMaxTiles;
+                const int* pi = S.part_idx + (size_t)w * kMaxTiles;
+#pragma unroll 4
                 for (int j = 0; j < nt; ++j) {
-                    R a1 = *(volatile R*)(S.part_k1 + (size_t)w * kMaxTiles + j);
-                    R a2 = *(volatile R*)(S.part_k2 + (size_t)w * kMaxTiles + j);
-                    int ai = *(volatile int*)(S.part_idx + (size_t)w * kMaxTiles + j);
+                    const R a1 = __ldcg(p1 + j), a2 = __ldcg(p2 + j);
+                    const int ai = __ldcg(pi + j);
                     if (key_less(a1, a2, ai, k1, k2, bi)) {
                         k1 = a1;
                         k2 = a2;
@@ -1017,128 +1085,20 @@ __global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
                         S.b_set[w] = sg;
                         S.b_idx[w] = bi - seg_pre[sg];
                     }
+                    emitted = bridge_emit(G, S, w, U0, C0);
                 }
             }
+            if (emitted) atomicAdd(&s_emitted, 1);
             if (t == 0) S.btile_cnt[s * kMaxQTiles + qt] = 0;
         }
     }
-}
-
-// Clears the per-worker bridge results before k_bridge.
-template <typename R>
-__global__ void k_bridge_clear(State<R> S) {
-    if (S.ctl->done) return;
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w < S.W) {
-        S.b_idx[w] = -1;
-        S.w_bedge[w] = -1;
-    }
+    __syncthreads();
+    if (t == 0 && s_emitted) atomicAdd(&c->st_bridge, (unsigned long long)s_emitted);
 }
 
 // ---------------------------------------------------------------------------
-// k_bridge_steer: candidate (U, C); bridge edge if it improves (U0, C0).
-// ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(kCtaThreads) k_bridge_steer(Geom<R> G, State<R> S) {
-    Ctl* c = S.ctl;
-    if (c->done) return;
-    __shared__ long long sh[32];
-    const int per = (S.W + kCtaThreads - 1) / kCtaThreads;
-    const int w0 = threadIdx.x * per;
-    const int dof = G.dof;
-    const double U0 = c->U, C0 = c->C;
-    int n_ent = 0;
-    long long n_pts = 0;
-    for (int w = w0; w < min(S.W, w0 + per); ++w) {
-        S.w_bedge[w] = -1;
-        if (S.w_ins[w] < 0 || S.b_idx[w] < 0) continue;
-        const bool fwd = S.w_set[w] == 0;
-        const R* f;
-        const R* b;
-        R cf, cb, troot;
-        if (fwd) {
-            f = fnode(S, S.w_ins[w]);
-            cf = S.fcost[S.w_ins[w]];
-            const size_t o = bofs(S, S.b_set[w], S.b_idx[w]);
-            b = bnode(S, S.b_set[w], S.b_idx[w]);
-            cb = S.bcost[o];
-            troot = S.btroot[o];
-        } else {
-            const int seg = S.w_set[w] - 1;
-            const size_t o = bofs(S, seg, S.w_ins[w]);
-            b = bnode(S, seg, S.w_ins[w]);
-            cb = S.bcost[o];
-            troot = S.btroot[o];
-            f = fnode(S, S.b_idx[w]);
-            cf = S.fcost[S.b_idx[w]];
-        }
-        const R D = qdist(f, b, dof);
-        const double Uc = (double)troot;
-        const double Cc = ((double)cf + (double)D) + (double)cb;
-        const bool improves = (Uc < U0) || (Uc == U0 && Cc < C0);
-        if (!improves) continue;
-        S.b_U[w] = Uc;
-        S.b_C[w] = Cc;
-        n_ent += 1;
-        n_pts += check_count(f, f[kDP - 1], b, b[kDP - 1], dof, G.vmax_d, S.res);
-    }
-    long long tot_e, tot_p;
-    const long long ebase = cta_exclusive_scan(n_ent, sh, &tot_e);
-    const long long pbase = cta_exclusive_scan(n_pts, sh, &tot_p);
-    int e = (int)ebase;
-    long long p = pbase;
-    for (int w = w0; w < min(S.W, w0 + per); ++w) {
-        if (S.w_ins[w] < 0 || S.b_idx[w] < 0) continue;
-        const bool fwd = S.w_set[w] == 0;
-        const R* f;
-        const R* b;
-        R cf, cb, troot;
-        if (fwd) {
-            f = fnode(S, S.w_ins[w]);
-            cf = S.fcost[S.w_ins[w]];
-            const size_t o = bofs(S, S.b_set[w], S.b_idx[w]);
-            b = bnode(S, S.b_set[w], S.b_idx[w]);
-            cb = S.bcost[o];
-            troot = S.btroot[o];
-        } else {
-            const int seg = S.w_set[w] - 1;
-            const size_t o = bofs(S, seg, S.w_ins[w]);
-            b = bnode(S, seg, S.w_ins[w]);
-            cb = S.bcost[o];
-            troot = S.btroot[o];
-            f = fnode(S, S.b_idx[w]);
-            cf = S.fcost[S.b_idx[w]];
-        }
-        const R D = qdist(f, b, dof);
-        const double Uc = (double)troot;
-        const double Cc = ((double)cf + (double)D) + (double)cb;
-        const bool improves = (Uc < U0) || (Uc == U0 && Cc < C0);
-        if (!improves) continue;
-        R* qa = S.bqa + (size_t)e * kDP;
-        R* qb = S.bqb + (size_t)e * kDP;
-        for (int j = 0; j < kDP; ++j) {
-            qa[j] = f[j];
-            qb[j] = b[j];
-        }
-        S.bta[e] = f[kDP - 1];
-        S.btb[e] = b[kDP - 1];
-        const int cc = check_count(f, f[kDP - 1], b, b[kDP - 1], dof, G.vmax_d, S.res);
-        S.bcnt[e] = cc;
-        S.boff[e] = p;
-        S.bhit[e] = 0;
-        S.w_bedge[w] = e;
-        ++e;
-        p += cc;
-    }
-    if (threadIdx.x == 0) {
-        c->n_bedges = (int)tot_e;
-        S.boff[tot_e] = tot_p;
-        c->st_bridge += (unsigned long long)tot_e;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// k_publish: lexicographic min of (U, C, worker); incumbent; allocation update.
+// k_publish: single CTA. Lexicographic min of (U, C, worker); incumbent;
+// allocation update.
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) {
@@ -1224,9 +1184,8 @@ __global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) 
     if (t == 0) {
         S.U_hist[c->iter] = c->U;
         c->iter += 1;
-        c->n_edges = 0;
-        c->n_bedges = 0;
         S.bq_count[0] = S.bq_count[1] = 0;
+        if (S.variant == 0) c->st_root += (unsigned long long)S.W;
         bool stop = c->iter >= c->max_iters || c->err != 0;
         if (S.variant == 0 && !(c->Lg < fmin(c->H, c->U))) stop = true;
         if (stop) {
@@ -1279,14 +1238,15 @@ static EdgeBatch<R> ext_batch(const State<R>& S) {
     E.tb = S.etb;
     E.qstride = kDP;
     E.cnt = S.ecnt;
-    E.off = S.eoff;
-    E.n_dev = &S.ctl->n_edges;
-    E.n_host = 0;
+    E.off = nullptr;  // offsets scanned in the kernel
+    E.n_dev = nullptr;
+    E.n_host = 2 * S.W;
     E.hit = S.ehit;
     E.clear = nullptr;
     E.points_done = &S.ctl->st_points;
     E.pairs_done = &S.ctl->st_pairs;
     E.err = &S.ctl->err;
+    E.done = &S.ctl->done;
     return E;
 }
 
@@ -1299,20 +1259,20 @@ static EdgeBatch<R> bridge_batch(const State<R>& S) {
     E.tb = S.btb;
     E.qstride = kDP;
     E.cnt = S.bcnt;
-    E.off = S.boff;
-    E.n_dev = &S.ctl->n_bedges;
-    E.n_host = 0;
+    E.off = nullptr;
+    E.n_dev = nullptr;
+    E.n_host = S.W;
     E.hit = S.bhit;
     E.clear = nullptr;
     E.points_done = &S.ctl->st_points;
     E.pairs_done = &S.ctl->st_pairs;
     E.err = &S.ctl->err;
+    E.done = &S.ctl->done;
     return E;
 }
 
 const char* const kIterKernelNames[kIterKernels] = {"k_sample", "k_nn", "k_steer", "k_validate(ext)",
-                                                    "k_insert", "k_bridge_clear", "k_bridge", "k_bridge_steer",
-                                                    "k_validate(bridge)", "k_publish"};
+                                                    "k_insert", "k_bridge", "k_validate(bridge)", "k_publish"};
 
 template <typename R>
 cudaError_t launch_plan_reset(const Geom<R>& g, const State<R>& s, int max_iters, cudaStream_t st) {
@@ -1323,30 +1283,29 @@ cudaError_t launch_plan_reset(const Geom<R>& g, const State<R>& s, int max_iters
 template <typename R>
 cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cudaStream_t st, cudaEvent_t* ev) {
     const int nn_grid = 2 * validate_grid_blocks();
+    const int wgrid = (s.W + kSampleThreads - 1) / kSampleThreads;
     int ne = 0;
+    // External event-record nodes: inside a stream capture a plain event record
+    // only adds a dependency edge and cannot be timed.
     auto mark = [&]() {
-        if (ev) cudaEventRecord(ev[ne], st);
+        if (ev) cudaEventRecordWithFlags(ev[ne], st, cudaEventRecordExternal);
         ++ne;
     };
     mark();
-    k_sample<R><<<(s.W + kSampleThreads - 1) / kSampleThreads, kSampleThreads, 0, st>>>(g, s);
+    k_sample<R><<<wgrid, kSampleThreads, 0, st>>>(g, s);
     mark();
     if (g.dof <= 3) k_nn<R, 3><<<nn_grid, kQT, 0, st>>>(g, s);
     else k_nn<R, kMaxDof><<<nn_grid, kQT, 0, st>>>(g, s);
     mark();
-    k_steer<R><<<1, kCtaThreads, 0, st>>>(g, s);
+    k_steer<R><<<wgrid, kSampleThreads, 0, st>>>(g, s);
     mark();
     cudaError_t err = launch_validate<R>(g, ext_batch(s), false, true, vgrid, st);
     if (err != cudaSuccess) return err;
     mark();
     k_insert<R><<<1, kCtaThreads, 0, st>>>(g, s);
     mark();
-    k_bridge_clear<R><<<(s.W + 255) / 256, 256, 0, st>>>(s);
-    mark();
     if (g.dof <= 3) k_bridge<R, 3><<<nn_grid, kQT, 0, st>>>(g, s);
     else k_bridge<R, kMaxDof><<<nn_grid, kQT, 0, st>>>(g, s);
-    mark();
-    k_bridge_steer<R><<<1, kCtaThreads, 0, st>>>(g, s);
     mark();
     err = launch_validate<R>(g, bridge_batch(s), false, true, vgrid, st);
     if (err != cudaSuccess) return err;

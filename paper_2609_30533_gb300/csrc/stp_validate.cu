@@ -95,25 +95,70 @@ __device__ __forceinline__ void atomic_min_r<double>(double* addr, double v) {
     atomicMin(reinterpret_cast<long long*>(addr), ord_enc(v));
 }
 
+// Exclusive block scan (all threads participate).
+__device__ __forceinline__ int block_scan_excl(int v, int* sh, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        int y = lane < nw ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        if (lane < nw) sh[lane] = y;
+    }
+    __syncthreads();
+    const int before = (warp > 0 ? sh[warp - 1] : 0) + x - v;
+    *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before;
+}
+
 template <typename R, bool ARM, int MO, bool CLEAR, bool EARLY>
 __global__ void __launch_bounds__(256) k_validate(Geom<R> G, EdgeBatch<R> E) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ int scan_sh[32];
     R* sm = reinterpret_cast<R*>(smem_raw);
     const int n = E.n_dev ? *E.n_dev : E.n_host;
-    if (n <= 0) return;
+    if (n <= 0 || (E.done && *E.done)) return;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_expect_tx(&bar, G.blob_bytes);
         bulk_g2s(sm, G.blob, G.blob_bytes, &bar);
     }
+    // Without precomputed offsets every CTA scans the (small) count array
+    // into shared memory while the geometry copy is in flight.
+    int* soff = reinterpret_cast<int*>(smem_raw + G.blob_bytes);
+    if (!E.off) {
+        const int per = (n + blockDim.x - 1) / blockDim.x;
+        const int i0 = threadIdx.x * per, i1 = min(n, i0 + per);
+        int sum = 0;
+        for (int i = i0; i < i1; ++i) sum += E.cnt[i];
+        int tot;
+        int pre = block_scan_excl(sum, scan_sh, &tot);
+        for (int i = i0; i < i1; ++i) {
+            soff[i] = pre;
+            pre += E.cnt[i];
+        }
+        if (threadIdx.x == 0) soff[n] = tot;
+        __syncthreads();
+    }
     if (!mbar_wait(&bar, 0)) {
         if (threadIdx.x == 0 && E.err) atomicOr(E.err, kErrTimeout);
         return;
     }
+    auto off_at = [&](int e) -> long long { return E.off ? E.off[e] : (long long)soff[e]; };
 
-    const long long total = E.off[n];
+    const long long total = off_at(n);
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
     const long long wstride = (long long)gridDim.x * wpb * 32;
@@ -124,7 +169,7 @@ __global__ void __launch_bounds__(256) k_validate(Geom<R> G, EdgeBatch<R> E) {
             int lo = 0, hi = n - 1;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
-                if (E.off[mid] <= base) lo = mid;
+                if (off_at(mid) <= base) lo = mid;
                 else hi = mid - 1;
             }
             e0 = lo;
@@ -133,12 +178,12 @@ __global__ void __launch_bounds__(256) k_validate(Geom<R> G, EdgeBatch<R> E) {
         const long long g = base + lane;
         if (g >= total) continue;
         int e = e0;
-        while (E.off[e + 1] <= g) ++e;
+        while (off_at(e + 1) <= g) ++e;
         if (EARLY && !CLEAR) {
             if (*(volatile int*)(E.hit + e)) continue;
         }
         const int c = E.cnt[e];
-        const R s = R(g - E.off[e] + 1) / R(c);
+        const R s = R(g - off_at(e) + 1) / R(c);
         const R* qa = E.qa + (size_t)e * E.qstride;
         const R* qb = E.qb + (size_t)e * E.qstride;
         R q[kMaxDof];
@@ -193,7 +238,7 @@ static cudaError_t launch_v(const Geom<R>& g, const EdgeBatch<R>& e, int grid_bl
     auto kern = k_validate<R, ARM, MO, CLEAR, EARLY>;
     static int configured_bytes = -1;
     static int blocks_per_sm = 0;
-    int smem = (int)g.blob_bytes;
+    int smem = (int)g.blob_bytes + (e.off ? 0 : (int)(sizeof(int) * (e.n_host + 1)));
     if (smem > configured_bytes) {
         cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (err != cudaSuccess) return err;

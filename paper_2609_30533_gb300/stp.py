@@ -169,7 +169,7 @@ class Problem:
         s = L.stp_create_problem(C.byref(robot), C.byref(obstacles), _dp(arr(q_start)), _dp(arr(q_goal)),
                                  C.byref(self.params), C.byref(h))
         if s != STP_OK:
-            raise StpError(s, "stp_create_problem")
+            raise StpError(s, "stp_create_problem", L.stp_last_error(None).decode())
         self.handle = h
         self.n_roots = int(n_roots)
 
