@@ -326,7 +326,7 @@ cudaError_t launch_finish_batch(int n, const int* hit, unsigned char* verdict, R
 template <typename R>
 cudaError_t launch_plan_reset(const Geom<R>& g, const State<R>& s, int max_iters, cudaStream_t st);
 // Kernels of one iteration, in launch order (profiling names).
-constexpr int kIterKernels = 8;
+constexpr int kIterKernels = 7;
 extern const char* const kIterKernelNames[kIterKernels];
 // ev (optional, kIterKernels + 1 events): recorded before each kernel and after the last.
 template <typename R>

@@ -13,10 +13,11 @@
 //                   argmin of the directed metric (Eq. space-time-metric) or the
 //                   configuration distance; FP32 keys reduced with a packed
 //                   64-bit atomicMin (key, index), FP64 keys by the last CTA of
-//                   each query tile (both deterministic, ties to lowest index).
-//   k_steer         one thread per worker: steering (Algorithm 1 /
-//                   Eq. max-speed-extension), horizon check, edge entries
-//                   (virtual-root workers are steered inside k_sample).
+//                   each query tile (both deterministic, ties to lowest index);
+//                   the last CTA of a query tile then steers its queries
+//                   (Algorithm 1 / Eq. max-speed-extension), checks the horizon
+//                   and writes the edge entries. Virtual-root workers are
+//                   steered inside k_sample.
 //   k_validate      collision kernel over all extension (and root) checks.
 //   k_insert        single CTA: ordered insertion in worker order, virtual-root
 //                   materialisation, bridge query registration.
@@ -640,22 +641,29 @@ __global__ void __launch_bounds__(kQT) k_nn(Geom<R> G, State<R> S) {
         if constexpr (sizeof(R) == 4) {
             if (w >= 0 && best < rinf<R>()) atomicMin(S.w_nnkey + w, pack_key((float)best, bidx));
         } else {
-            // FP64: keys do not fit a 64-bit word with the index; per-tile
+            // FP64 keys do not fit one 64-bit word with the index: per-tile
             // partials, reduced in tile order by the last CTA of the query tile.
             if (w >= 0) {
                 S.part_k2[(size_t)w * kMaxTiles + ntile] = best;
                 S.part_idx[(size_t)w * kMaxTiles + ntile] = bidx;
             }
+        }
+        __threadfence();
+        __syncthreads();
+        if (t == 0) {
+            int old = atomicAdd(&S.tile_cnt[s * kMaxQTiles + qt], 1);
+            s_last = (old == nt - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            // Every tile of this query tile is done: decode the NN and steer.
             __threadfence();
-            __syncthreads();
-            if (t == 0) {
-                int old = atomicAdd(&S.tile_cnt[s * kMaxQTiles + qt], 1);
-                s_last = (old == nt - 1);
-            }
-            __syncthreads();
-            if (s_last) {
-                __threadfence();
-                if (w >= 0) {
+            if (w >= 0) {
+                int p;
+                if constexpr (sizeof(R) == 4) {
+                    const unsigned long long key = __ldcg(S.w_nnkey + w);
+                    p = (key == ~0ull) ? -1 : (int)(unsigned)(key & 0xffffffffull);
+                } else {
                     R b = rinf<R>();
                     int bi = 0x7fffffff;
                     for (int j = 0; j < nt; ++j) {
@@ -666,40 +674,22 @@ __global__ void __launch_bounds__(kQT) k_nn(Geom<R> G, State<R> S) {
                             bi = ii;
                         }
                     }
-                    S.w_parent[w] = (b < rinf<R>()) ? bi : -1;
+                    p = (b < rinf<R>()) ? bi : -1;
                 }
-                if (t == 0) S.tile_cnt[s * kMaxQTiles + qt] = 0;
+                S.w_parent[w] = p;
+                bool ok = p >= 0;
+                if (ok) {
+                    const R* x = s == 0 ? fnode(S, p) : bnode(S, s - 1, p);
+                    R xn[kDP];
+#pragma unroll
+                    for (int j = 0; j < kDP; ++j) xn[j] = x[j];
+                    ok = steer_and_emit(G, S, w, s, false, xn);
+                }
+                if (!ok) S.w_status[w] = kSkip;
             }
+            if (t == 0) S.tile_cnt[s * kMaxQTiles + qt] = 0;
         }
     }
-}
-
-// ---------------------------------------------------------------------------
-// k_steer: one thread per worker with an NN query.
-// ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(kSampleThreads) k_steer(Geom<R> G, State<R> S) {
-    const Ctl* c = S.ctl;
-    if (c->done) return;
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= S.W || S.w_status[w] != kNN) return;
-    int p;
-    if constexpr (sizeof(R) == 4) {
-        const unsigned long long key = S.w_nnkey[w];
-        p = (key == ~0ull) ? -1 : (int)(unsigned)(key & 0xffffffffull);
-    } else {
-        p = S.w_parent[w];
-    }
-    S.w_parent[w] = p;
-    const int set = S.w_set[w];
-    bool ok = p >= 0;
-    if (ok) {
-        const R* x = set == 0 ? fnode(S, p) : bnode(S, set - 1, p);
-        R xn[kDP];
-        for (int j = 0; j < kDP; ++j) xn[j] = x[j];
-        ok = steer_and_emit(G, S, w, set, false, xn);
-    }
-    if (!ok) S.w_status[w] = kSkip;
 }
 
 // ---------------------------------------------------------------------------
@@ -763,20 +753,25 @@ __global__ void __launch_bounds__(kCtaThreads) k_insert(Geom<R> G, State<R> S) {
         const int w = r0 + t;
         int ok = 0, nodes = 0, set = -1, virt = 0, ext = 0;
         if (w < S.W) {
+            // Independent loads first (entries of worker w sit at 2w, 2w+1).
+            const int e = S.w_edge[w];
+            const int re = S.w_root_edge[w];
+            const int h_root = S.ehit[2 * w];
+            const int h_ext = S.ehit[2 * w + 1];
+            const int wset = S.w_set[w];
+            const int wst = S.w_status[w];
             S.b_idx[w] = -1;
             S.w_bedge[w] = -1;
             S.bcnt[w] = 0;
             S.bhit[w] = 0;
-            const int e = S.w_edge[w];
             if (e >= 0) {
-                const int re = S.w_root_edge[w];
-                const bool root_ok = re < 0 || S.ehit[re] == 0;
+                const bool root_ok = re < 0 || h_root == 0;
                 ext = root_ok ? 1 : 0;
-                ok = root_ok && S.ehit[e] == 0;
+                ok = root_ok && h_ext == 0;
             }
             if (ok) {
-                set = S.w_set[w];
-                virt = S.w_status[w] == kVirtual;
+                set = wset;
+                virt = wst == kVirtual;
                 nodes = virt ? 2 : 1;
             }
         }
@@ -1065,14 +1060,24 @@ __global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
                 const R* p1 = S.part_k1 + (size_t)w * kMaxTiles;
                 const R* p2 = S.part_k2 + (size_t)w * kMaxTiles;
                 const int* pi = S.part_idx + (size_t)w * kMaxTiles;
-#pragma unroll 4
-                for (int j = 0; j < nt; ++j) {
-                    const R a1 = __ldcg(p1 + j), a2 = __ldcg(p2 + j);
-                    const int ai = __ldcg(pi + j);
-                    if (key_less(a1, a2, ai, k1, k2, bi)) {
-                        k1 = a1;
-                        k2 = a2;
-                        bi = ai;
+                // Groups of 8 independent loads per round trip, in tile order.
+                for (int j0 = 0; j0 < nt; j0 += 8) {
+                    R a1[8], a2[8];
+                    int ai[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int j = j0 + u < nt ? j0 + u : nt - 1;
+                        a1[u] = __ldcg(p1 + j);
+                        a2[u] = __ldcg(p2 + j);
+                        ai[u] = __ldcg(pi + j);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        if (j0 + u < nt && key_less(a1[u], a2[u], ai[u], k1, k2, bi)) {
+                            k1 = a1[u];
+                            k2 = a2[u];
+                            bi = ai[u];
+                        }
                     }
                 }
                 if (k2 < rinf<R>()) {
@@ -1107,13 +1112,23 @@ __global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) 
     __shared__ double rU[kCtaThreads / 32], rC[kCtaThreads / 32];
     __shared__ int rW[kCtaThreads / 32];
     __shared__ int s_counts[kMaxRoots];
+    __shared__ double sU, sC;
+    __shared__ int s_iter, s_first, s_err, s_decreased;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // Control fields staged in parallel with the candidate loads.
+    if (t == 0) sU = c->U;
+    if (t == 32) sC = c->C;
+    if (t == 64) s_iter = c->iter;
+    if (t == 96) s_first = c->first_iter;
+    if (t == 128) s_err = c->err;
     double bU = __longlong_as_double(0x7ff0000000000000LL), bC = bU;
     int bw = 0x7fffffff;
     for (int w = t; w < S.W; w += blockDim.x) {
+        // Bridge entry of worker w is entry w; all loads independent.
         const int e = S.w_bedge[w];
-        if (e < 0 || S.bhit[e]) continue;
+        const int h = S.bhit[w];
         const double U = S.b_U[w], C = S.b_C[w];
+        if (e < 0 || h) continue;
         if (U < bU || (U == bU && (C < bC || (C == bC && w < bw)))) {
             bU = U;
             bC = C;
@@ -1136,7 +1151,6 @@ __global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) 
         rW[warp] = bw;
     }
     __syncthreads();
-    __shared__ int s_decreased;
     if (t == 0) {
         for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
             if (rU[i] < bU || (rU[i] == bU && (rC[i] < bC || (rC[i] == bC && rW[i] < bw)))) {
@@ -1147,20 +1161,23 @@ __global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) 
         }
         s_decreased = 0;
         if (bw != 0x7fffffff) {
-            s_decreased = bU < c->U;
+            const int wset = S.w_set[bw], wins = S.w_ins[bw], bset = S.b_set[bw], bidx = S.b_idx[bw];
+            s_decreased = bU < sU;
+            sU = bU;
+            sC = bC;
             c->U = bU;
             c->C = bC;
-            if (S.w_set[bw] == 0) {
-                c->inc_f = S.w_ins[bw];
-                c->inc_s = S.b_set[bw];
-                c->inc_b = S.b_idx[bw];
+            if (wset == 0) {
+                c->inc_f = wins;
+                c->inc_s = bset;
+                c->inc_b = bidx;
             } else {
-                c->inc_f = S.b_idx[bw];
-                c->inc_s = S.w_set[bw] - 1;
-                c->inc_b = S.w_ins[bw];
+                c->inc_f = bidx;
+                c->inc_s = wset - 1;
+                c->inc_b = wins;
             }
-            if (c->first_iter < 0) {
-                c->first_iter = c->iter;
+            if (s_first < 0) {
+                c->first_iter = s_iter;
                 c->t_first = global_ns();
             }
         }
@@ -1171,23 +1188,24 @@ __global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) 
             // Repartition; trees rooted at T >= U become inactive.
             for (int i = t; i < S.N; i += blockDim.x) s_counts[i] = 0;
             __syncthreads();
-            for (int i = t; i < c->n_trees; i += blockDim.x)
-                if (S.tree_T[i] < c->U) atomicAdd(&s_counts[S.tree_group[i]], 1);
+            const int ntr = c->n_trees;
+            for (int i = t; i < ntr; i += blockDim.x)
+                if (S.tree_T[i] < sU) atomicAdd(&s_counts[S.tree_group[i]], 1);
             __syncthreads();
             for (int i = t; i < S.N; i += blockDim.x) c->group_active[i] = s_counts[i];
-            if (t == 0) partition(S, c->U);
+            if (t == 0) partition(S, sU);
         } else if (t == 0) {
-            recycle(S, c->U);
+            recycle(S, sU);
         }
     }
     __syncthreads();
     if (t == 0) {
-        S.U_hist[c->iter] = c->U;
-        c->iter += 1;
+        S.U_hist[s_iter] = sU;
+        c->iter = s_iter + 1;
         S.bq_count[0] = S.bq_count[1] = 0;
         if (S.variant == 0) c->st_root += (unsigned long long)S.W;
-        bool stop = c->iter >= c->max_iters || c->err != 0;
-        if (S.variant == 0 && !(c->Lg < fmin(c->H, c->U))) stop = true;
+        bool stop = s_iter + 1 >= c->max_iters || s_err != 0;
+        if (S.variant == 0 && !(c->Lg < fmin(c->H, sU))) stop = true;
         if (stop) {
             c->done = 1;
             c->t_end = global_ns();
@@ -1271,8 +1289,8 @@ static EdgeBatch<R> bridge_batch(const State<R>& S) {
     return E;
 }
 
-const char* const kIterKernelNames[kIterKernels] = {"k_sample", "k_nn", "k_steer", "k_validate(ext)",
-                                                    "k_insert", "k_bridge", "k_validate(bridge)", "k_publish"};
+const char* const kIterKernelNames[kIterKernels] = {"k_sample", "k_nn", "k_validate(ext)", "k_insert",
+                                                    "k_bridge", "k_validate(bridge)", "k_publish"};
 
 template <typename R>
 cudaError_t launch_plan_reset(const Geom<R>& g, const State<R>& s, int max_iters, cudaStream_t st) {
@@ -1296,8 +1314,6 @@ cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cud
     mark();
     if (g.dof <= 3) k_nn<R, 3><<<nn_grid, kQT, 0, st>>>(g, s);
     else k_nn<R, kMaxDof><<<nn_grid, kQT, 0, st>>>(g, s);
-    mark();
-    k_steer<R><<<wgrid, kSampleThreads, 0, st>>>(g, s);
     mark();
     cudaError_t err = launch_validate<R>(g, ext_batch(s), false, true, vgrid, st);
     if (err != cudaSuccess) return err;
