@@ -139,6 +139,11 @@ void fill_geom(stp_problem* p, Geom<R>& g, const R* blob, unsigned blob_bytes, i
     }
     g.vmax = (R)p->vmax;
     g.vmax_d = p->vmax;
+    // Reference point for the pair tests: the arm base, or the centre of a
+    // point robot's configuration box.
+    for (int i = 0; i < 3; ++i) g.ref[i] = R(0);
+    if (!p->arm)
+        for (int i = 0; i < 3 && i < p->dof; ++i) g.ref[i] = (R)(0.5 * (p->qlo[i] + p->qhi[i]));
     g.uniform_r = 0;
     g.blob = blob;
     g.blob_bytes = blob_bytes;

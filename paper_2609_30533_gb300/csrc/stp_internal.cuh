@@ -44,6 +44,7 @@ struct Geom {
     R a[kMaxDof], d[kMaxDof], ca[kMaxDof], sa[kMaxDof], th0[kMaxDof];
     R qlo[kMaxDof], qhi[kMaxDof];
     R vmax;
+    R ref[3];       // reference point subtracted from workspace positions in pair tests
     double vmax_d;  // v_max as given (edge check counts are evaluated in double)
     int uniform_r;  // all robot spheres share one radius
     const R* blob;

@@ -14,9 +14,51 @@
 //
 // Algorithmic work per check point: S*M pair tests (8 flops each: 3 sub,
 // 1 mul, 2 fma) + S sphere transforms + FK (d joint steps) + M interpolations.
+//
+// Verdict-only pair test. With positions taken relative to a reference point
+// (the arm base, or the centre of a point robot's box), a robot sphere (c, r_s)
+// and an obstacle (o, r_o) collide iff |c - o|^2 - (r_s + r_o)^2 < 0, i.e.
+//   B_o + (-2 o).c + (-2 r_o) r_s  <  r_s^2 - |c|^2,   B_o = |o|^2 - r_o^2,
+// which is four FMAs per pair against per-obstacle terms computed once per
+// check point, plus one min per pair. Positions are O(1 m) relative to the
+// reference, so the FP32 cancellation error near contact is about 1e-6 m; the
+// clearance variant keeps the direct form |c - o| - r_s - r_o.
 #include "stp_internal.cuh"
 
 namespace stp {
+
+// Per-check-point obstacle terms for the expanded pair test.
+template <typename R, int MO>
+struct ObsTerms {
+    R ox[MO], oy[MO], oz[MO], ro[MO], B[MO];
+};
+
+template <typename R>
+__device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
+
+template <typename R, int MO>
+__device__ __forceinline__ bool sphere_hits(R cx, R cy, R cz, R rs, const ObsTerms<R, MO>& O) {
+    const R negA = rs * rs - (cx * cx + cy * cy + cz * cz);
+    R m0 = rinf<R>(), m1 = rinf<R>();
+#pragma unroll
+    for (int j = 0; j < MO; j += 2) {
+        R a = O.B[j];
+        a = cx * O.ox[j] + a;
+        a = cy * O.oy[j] + a;
+        a = cz * O.oz[j] + a;
+        a = rs * O.ro[j] + a;
+        m0 = rmin(m0, a);
+        if (j + 1 < MO) {
+            R b = O.B[j + 1];
+            b = cx * O.ox[j + 1] + b;
+            b = cy * O.oy[j + 1] + b;
+            b = cz * O.oz[j + 1] + b;
+            b = rs * O.ro[j + 1] + b;
+            m1 = rmin(m1, b);
+        }
+    }
+    return rmin(m0, m1) < negA;
+}
 
 template <typename R, int MO, bool CLEAR>
 __device__ __forceinline__ void test_sphere(R cx, R cy, R cz, R rs, const R (&ox)[MO], const R (&oy)[MO],
@@ -36,9 +78,72 @@ __device__ __forceinline__ void test_sphere(R cx, R cy, R cz, R rs, const R (&ox
     }
 }
 
+// Verdict-only check point (expanded pair test, early exit at frame granularity).
+template <typename R, bool ARM, int MO, bool EARLY>
+__device__ __forceinline__ void check_point_fast(const Geom<R>& G, const R* sm, const R (&q)[kMaxDof], R t,
+                                                 bool& hit, unsigned& pairs) {
+    const R* sph = sm;
+    const R* way = sm + G.off_way;
+    const R* vel = sm + G.off_vel;
+    const R* rad = sm + G.off_rad;
+    for (int m0 = 0; m0 < G.M; m0 += MO) {
+        ObsTerms<R, MO> O;
+#pragma unroll
+        for (int j = 0; j < MO; ++j) {
+            const int m = m0 + j;
+            if (m < G.M) {
+                R x, y, z;
+                obstacle_at(way + 4 * G.K * m, vel + 4 * G.K * m, G.K, t, x, y, z);
+                x -= G.ref[0];
+                y -= G.ref[1];
+                z -= G.ref[2];
+                const R r = rad[m];
+                O.ox[j] = R(-2) * x;
+                O.oy[j] = R(-2) * y;
+                O.oz[j] = R(-2) * z;
+                O.ro[j] = R(-2) * r;
+                O.B[j] = x * x + y * y + z * z - r * r;
+            } else {
+                O.ox[j] = O.oy[j] = O.oz[j] = O.ro[j] = R(0);
+                O.B[j] = R(1e30);
+            }
+        }
+        const unsigned real = (unsigned)min(MO, G.M - m0);
+        if (!ARM) {
+            const R px = q[0] - G.ref[0], py = q[1] - G.ref[1], pz = ((G.dof > 2) ? q[2] : R(0)) - G.ref[2];
+            for (int s = 0; s < G.S; ++s) {
+                if (sphere_hits<R, MO>(px + sph[4 * s], py + sph[4 * s + 1], pz + sph[4 * s + 2], sph[4 * s + 3], O))
+                    hit = true;
+            }
+            pairs += real * (unsigned)G.S;
+        } else {
+            Frame<R> F;
+            frame_identity(F);
+            for (int j = 0; j <= G.dof; ++j) {
+                if (j > 0) frame_step(F, G.a[j - 1], G.d[j - 1], G.ca[j - 1], G.sa[j - 1], q[j - 1] + G.th0[j - 1]);
+                const R ox = F.o[0] - G.ref[0], oy = F.o[1] - G.ref[1], oz = F.o[2] - G.ref[2];
+                for (int s = G.link_start[j]; s < G.link_start[j + 1]; ++s) {
+                    const R px = sph[4 * s], py = sph[4 * s + 1], pz = sph[4 * s + 2];
+                    const R cx = ox + px * F.X[0] + py * F.Y[0] + pz * F.Z[0];
+                    const R cy = oy + px * F.X[1] + py * F.Y[1] + pz * F.Z[1];
+                    const R cz = oz + px * F.X[2] + py * F.Y[2] + pz * F.Z[2];
+                    if (sphere_hits<R, MO>(cx, cy, cz, sph[4 * s + 3], O)) hit = true;
+                }
+                pairs += real * (unsigned)(G.link_start[j + 1] - G.link_start[j]);
+                if (EARLY && hit) break;
+            }
+        }
+        if (EARLY && hit) break;
+    }
+}
+
 template <typename R, bool ARM, int MO, bool CLEAR, bool EARLY>
 __device__ __forceinline__ void check_point(const Geom<R>& G, const R* sm, const R (&q)[kMaxDof], R t, bool& hit,
                                             R& clr, unsigned& pairs) {
+    if (!CLEAR) {
+        check_point_fast<R, ARM, MO, EARLY>(G, sm, q, t, hit, pairs);
+        return;
+    }
     const R* sph = sm;
     const R* way = sm + G.off_way;
     const R* vel = sm + G.off_vel;
