@@ -3,7 +3,11 @@
 // interpolated at each absolute query time) and the flat-batch helpers.
 //
 // Mapping: a persistent grid walks the flat list of check points of a batch
-// of edges; each warp takes 32 consecutive points (one point per lane). A
+// of edges, one check point per lane. Small batches (the planner's, offsets
+// scanned into shared memory by every CTA) spread the whole flat range over
+// all warps; large batches (precomputed offsets) go window by window, 256 edges
+// per CTA window, with the window's offsets staged in shared memory. Either
+// way a lane finds its edge by binary search in shared memory. A
 // lane evaluates one check point completely: interpolate the edge in (q, t),
 // run forward kinematics once, and test every robot sphere against every
 // obstacle sphere. Obstacle positions at the lane's time are held in
@@ -226,6 +230,9 @@ __device__ __forceinline__ int block_scan_excl(int v, int* sh, int* total) {
     return before;
 }
 
+// Edges per shared-memory window in the large-batch mode.
+constexpr int kWin = 256;
+
 template <typename R, bool ARM, int MO, bool CLEAR, bool EARLY>
 __global__ void __launch_bounds__(256) k_validate(Geom<R> G, EdgeBatch<R> E) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -263,32 +270,18 @@ __global__ void __launch_bounds__(256) k_validate(Geom<R> G, EdgeBatch<R> E) {
     }
     auto off_at = [&](int e) -> long long { return E.off ? E.off[e] : (long long)soff[e]; };
 
-    const long long total = off_at(n);
     const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    const long long wstride = (long long)gridDim.x * wpb * 32;
     unsigned long long done = 0, pairs_total = 0;
-    for (long long base = ((long long)blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; base < total; base += wstride) {
-        int e0 = 0;
-        if (lane == 0) {
-            int lo = 0, hi = n - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (off_at(mid) <= base) lo = mid;
-                else hi = mid - 1;
-            }
-            e0 = lo;
-        }
-        e0 = __shfl_sync(0xffffffffu, e0, 0);
-        const long long g = base + lane;
-        if (g >= total) continue;
-        int e = e0;
-        while (off_at(e + 1) <= g) ++e;
+
+    // One check point g of edge e: interpolate, run FK and the pair tests.
+    auto process = [&](long long g, int e, long long e_off) {
         if (EARLY && !CLEAR) {
-            if (*(volatile int*)(E.hit + e)) continue;
+            if (*(volatile int*)(E.hit + e)) return;
         }
         const int c = E.cnt[e];
-        const R s = R(g - off_at(e) + 1) / R(c);
+        const R s = R(g - e_off + 1) / R(c);
         const R* qa = E.qa + (size_t)e * E.qstride;
         const R* qb = E.qb + (size_t)e * E.qstride;
         R q[kMaxDof];
@@ -312,6 +305,44 @@ __global__ void __launch_bounds__(256) k_validate(Geom<R> G, EdgeBatch<R> E) {
         if (CLEAR) atomic_min_r<R>(E.clear + e, clr);
         ++done;
         pairs_total += pairs;
+    };
+
+    if (!E.off) {
+        // Small batches (offsets scanned into shared memory): the flat range of
+        // check points is spread over every warp of the grid; each lane finds
+        // its edge by binary search in shared memory.
+        const long long total = soff[n];
+        const long long stride = (long long)gridDim.x * wpb * 32;
+        for (long long g = ((long long)blockIdx.x * wpb + warp) * 32 + lane; g < total; g += stride) {
+            int lo = 0, hi = n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (soff[mid] <= g) lo = mid;
+                else hi = mid - 1;
+            }
+            process(g, lo, soff[lo]);
+        }
+    } else {
+        // Large batches (precomputed offsets in global memory): CTAs take
+        // windows of kWin consecutive edges, stage the window's offsets in
+        // shared memory and spread its check points over their warps.
+        long long* woff = reinterpret_cast<long long*>(smem_raw + G.blob_bytes);
+        for (int w0 = blockIdx.x * kWin; w0 < n; w0 += gridDim.x * kWin) {
+            const int wn = min(kWin, n - w0);
+            __syncthreads();
+            for (int i = threadIdx.x; i <= wn; i += blockDim.x) woff[i] = E.off[w0 + i];
+            __syncthreads();
+            const long long ob = woff[0], oe = woff[wn];
+            for (long long g = ob + warp * 32 + lane; g < oe; g += wpb * 32) {
+                int lo = 0, hi = wn - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (woff[mid] <= g) lo = mid;
+                    else hi = mid - 1;
+                }
+                process(g, w0 + lo, woff[lo]);
+            }
+        }
     }
     if (E.points_done) {
         for (int o = 16; o > 0; o >>= 1) done += __shfl_xor_sync(0xffffffffu, done, o);
@@ -343,7 +374,8 @@ static cudaError_t launch_v(const Geom<R>& g, const EdgeBatch<R>& e, int grid_bl
     auto kern = k_validate<R, ARM, MO, CLEAR, EARLY>;
     static int configured_bytes = -1;
     static int blocks_per_sm = 0;
-    int smem = (int)g.blob_bytes + (e.off ? 0 : (int)(sizeof(int) * (e.n_host + 1)));
+    int smem = (int)g.blob_bytes + (e.off ? (int)(sizeof(long long) * (kWin + 1))
+                                          : (int)(sizeof(int) * (e.n_host + 1)));
     if (smem > configured_bytes) {
         cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (err != cudaSuccess) return err;
