@@ -190,6 +190,30 @@ stp_status stp_set_profiling(stp_problem *p, int on);
  * names[k] (static strings), ms[k] total device time, launches[k]. */
 stp_status stp_profile(stp_problem *p, int cap, const char **names, double *ms, long long *launches, int *n);
 
+/* Edge validation that allocates nothing, for callers that cannot allocate
+ * device memory while they run: for example a control loop that must not
+ * block in the driver's allocator, or a host process whose device-memory
+ * budget is fixed after start-up. The paper has no counterpart: this is the
+ * collision batch of stp_check_edges with its per-call scratch (check counts,
+ * offsets, hit flags, scan partials) taken from one static device array built
+ * into the library, sized for STP_NOALLOC_MAX_EDGES edges (about 1 MiB, held
+ * on every GPU that loads the library until the process exits).
+ *   qa, qb     [n_edges][dof] DEVICE pointers, ta, tb [n_edges] DEVICE
+ *              pointers, element type per precision (as stp_check_edges).
+ *   verdict    [n_edges] DEVICE output, 1 = collision-free, 0 = collides.
+ * The work is queued on the problem's stream; the call does not wait for it.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) for the current device: make that first call before
+ * any stream capture. Every call uses the same array, which keeps the last
+ * call's contents; calls whose GPU work can overlap (other streams, threads
+ * or problems without ordering between them) race on it, so the caller must
+ * order them.
+ * Errors: STP_ERR_INVALID (NULL pointers, n_edges < 0), STP_ERR_CAPACITY
+ * (n_edges > STP_NOALLOC_MAX_EDGES), STP_ERR_CUDA. n_edges == 0 is a no-op. */
+#define STP_NOALLOC_MAX_EDGES 65536
+stp_status stp_check_edges_noalloc(stp_problem *p, int n_edges, const void *qa, const void *ta, const void *qb,
+                                   const void *tb, unsigned char *verdict);
+
 /* Release all device and host memory of a problem. NULL is allowed. */
 void stp_free(stp_problem *p);
 

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -975,3 +976,96 @@ stp_status stp_goal_grid(stp_problem* p, long* kmin, int* n, unsigned char* free
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Collision batch without allocation (stp_check_edges_noalloc).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t ce_align(size_t x) { return (x + 255) / 256 * 256; }
+constexpr int kNoAllocMaxEdges = STP_NOALLOC_MAX_EDGES;
+constexpr size_t kNoAllocCnt = 0;
+constexpr size_t kNoAllocOff = kNoAllocCnt + ce_align(sizeof(int) * kNoAllocMaxEdges);
+constexpr size_t kNoAllocHit = kNoAllocOff + ce_align(sizeof(long long) * (kNoAllocMaxEdges + 1));
+constexpr size_t kNoAllocTmp = kNoAllocHit + ce_align(sizeof(int) * kNoAllocMaxEdges);
+constexpr size_t kNoAllocBytes = kNoAllocTmp + ce_align(sizeof(long long) * (kNoAllocMaxEdges / 4096 + 2));
+constexpr int kNoAllocMaxDevices = 64;
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+}  // namespace
+
+// Scratch of the allocation-free batch: check counts, offsets, hit flags and
+// scan partials for up to STP_NOALLOC_MAX_EDGES edges. In host code this name
+// is only a handle; its device address is looked up per device below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+// Device address of the static scratch on the current device (looked up once
+// per device, with that device current).
+stp_status noalloc_scratch(stp_problem* p, char** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return STP_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_fail(p, e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = static_cast<char*>(g_noalloc_ptr[dev]);
+    return STP_OK;
+}
+
+template <typename R>
+stp_status check_edges_noalloc_impl(stp_problem* p, int n, const void* qa, const void* ta, const void* qb,
+                                    const void* tb, unsigned char* verdict) {
+    char* base = nullptr;
+    stp_status s = noalloc_scratch(p, &base);
+    if (s != STP_OK) return s;
+    cudaStream_t st = p->stream;
+    int* cnt = reinterpret_cast<int*>(base + kNoAllocCnt);
+    long long* off = reinterpret_cast<long long*>(base + kNoAllocOff);
+    int* hit = reinterpret_cast<int*>(base + kNoAllocHit);
+    long long* tmp = reinterpret_cast<long long*>(base + kNoAllocTmp);
+    const R* dqa = static_cast<const R*>(qa);
+    const R* dqb = static_cast<const R*>(qb);
+    const R* dta = static_cast<const R*>(ta);
+    const R* dtb = static_cast<const R*>(tb);
+    STP_CUDA(p, launch_edge_counts<R>(geom_of<R>(p), dqa, dta, dqb, dtb, p->dof, n, p->prm.edge_res, cnt, st));
+    STP_CUDA(p, launch_scan_counts(cnt, n, off, tmp, st));
+    // The array keeps the previous call's flags: clear them.
+    STP_CUDA(p, cudaMemsetAsync(hit, 0, sizeof(int) * (size_t)n, st));
+    EdgeBatch<R> E;
+    std::memset(&E, 0, sizeof(E));
+    E.qa = dqa;
+    E.qb = dqb;
+    E.ta = dta;
+    E.tb = dtb;
+    E.qstride = p->dof;
+    E.cnt = cnt;
+    E.off = off;
+    E.n_host = n;
+    E.hit = hit;
+    E.err = &p->d_ctl->err;
+    STP_CUDA(p, launch_validate<R>(geom_of<R>(p), E, false, true, 0, st));
+    STP_CUDA(p, launch_finish_batch<R>(n, hit, verdict, nullptr, st));
+    return STP_OK;
+}
+
+}  // namespace
+
+extern "C" stp_status stp_check_edges_noalloc(stp_problem* p, int n_edges, const void* qa, const void* ta,
+                                              const void* qb, const void* tb, unsigned char* verdict) {
+    clear_stale_error();
+    if (!p || n_edges < 0) return STP_ERR_INVALID;
+    if (n_edges > kNoAllocMaxEdges) return STP_ERR_CAPACITY;
+    if (n_edges == 0) return STP_OK;
+    if (!qa || !ta || !qb || !tb || !verdict) return STP_ERR_INVALID;
+    return p->precision == 0 ? check_edges_noalloc_impl<float>(p, n_edges, qa, ta, qb, tb, verdict)
+                             : check_edges_noalloc_impl<double>(p, n_edges, qa, ta, qb, tb, verdict);
+}

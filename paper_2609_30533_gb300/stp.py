@@ -90,6 +90,9 @@ def lib():
     L.stp_last_error.restype = C.c_char_p
     L.stp_last_validate.argtypes = [C.c_void_p, _D, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     L.stp_last_validate.restype = C.c_int
+    L.stp_check_edges_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p]
+    L.stp_check_edges_noalloc.restype = C.c_int
     L.stp_set_profiling.argtypes = [C.c_void_p, C.c_int]
     L.stp_set_profiling.restype = C.c_int
     L.stp_profile.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), _D, C.POINTER(C.c_longlong), _I]
@@ -110,7 +113,8 @@ def lib():
 
 EXPORTED = ["stp_create_problem", "stp_plan", "stp_check_edges", "stp_free", "stp_set_stream",
             "stp_status_string", "stp_last_error", "stp_last_validate", "stp_set_profiling", "stp_profile",
-            "stp_tree_size", "stp_tree_nodes", "stp_history", "stp_slots", "stp_goal_grid"]
+            "stp_tree_size", "stp_tree_nodes", "stp_history", "stp_slots", "stp_goal_grid",
+            "stp_check_edges_noalloc"]
 
 
 def status_string(s: int) -> str:
