@@ -40,8 +40,48 @@ struct ObsTerms {
 template <typename R>
 __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
 
+// Packed FP32x2 helpers (Blackwell fma.rn.f32x2: two FP32 FMAs per
+// instruction, each rounded once like the scalar FMA).
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+template <int MO>
+__device__ __forceinline__ bool sphere_hits_x2(float cx, float cy, float cz, float rs, const ObsTerms<float, MO>& O) {
+    const float negA = rs * rs - (cx * cx + cy * cy + cz * cz);
+    const unsigned long long CX = pk2(cx, cx), CY = pk2(cy, cy), CZ = pk2(cz, cz), RS = pk2(rs, rs);
+    float m0 = rinf<float>(), m1 = rinf<float>();
+#pragma unroll
+    for (int j = 0; j < MO; j += 2) {
+        unsigned long long a = pk2(O.B[j], O.B[j + 1]);
+        a = ffma2(CX, pk2(O.ox[j], O.ox[j + 1]), a);
+        a = ffma2(CY, pk2(O.oy[j], O.oy[j + 1]), a);
+        a = ffma2(CZ, pk2(O.oz[j], O.oz[j + 1]), a);
+        a = ffma2(RS, pk2(O.ro[j], O.ro[j + 1]), a);
+        float lo, hi;
+        upk2(a, lo, hi);
+        m0 = fminf(m0, lo);
+        m1 = fminf(m1, hi);
+    }
+    return fminf(m0, m1) < negA;
+}
+
 template <typename R, int MO>
 __device__ __forceinline__ bool sphere_hits(R cx, R cy, R cz, R rs, const ObsTerms<R, MO>& O) {
+    if constexpr (sizeof(R) == 4 && MO % 2 == 0) {
+        return sphere_hits_x2<MO>(cx, cy, cz, rs, O);
+    }
     const R negA = rs * rs - (cx * cx + cy * cy + cz * cz);
     R m0 = rinf<R>(), m1 = rinf<R>();
 #pragma unroll
@@ -234,7 +274,7 @@ __device__ __forceinline__ int block_scan_excl(int v, int* sh, int* total) {
 constexpr int kWin = 256;
 
 template <typename R, bool ARM, int MO, bool CLEAR, bool EARLY>
-__global__ void __launch_bounds__(256) k_validate(Geom<R> G, EdgeBatch<R> E) {
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && MO <= 16) ? 2 : 1) k_validate(Geom<R> G, EdgeBatch<R> E) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int scan_sh[32];
