@@ -212,12 +212,10 @@ __device__ void install_root(const State<R>& S, int slot, double T, int gen, int
 }
 
 template <typename R>
-__device__ void recycle(const State<R>& S, double U) {
+__device__ void recycle(const State<R>& S, double U, int* donors, long long* held) {
     Ctl* c = S.ctl;
     long long kU = c->kmin;
     while (grid_t<R>(kU, c->dt) < U) ++kU;
-    int donors[kMaxRoots];
-    long long held[kMaxRoots];
     int m = 0, nh = 0;
     for (int i = 0; i < S.N; ++i) {
         if (c->slot_has[i] && c->slot_T[i] >= U) c->slot_active[i] = 0;
@@ -421,6 +419,20 @@ template <typename R>
 __global__ void __launch_bounds__(kSampleThreads) k_sample(Geom<R> G, State<R> S) {
     const Ctl* c = S.ctl;
     if (c->done) return;
+    // Active-slot list (recycling) staged once per block.
+    __shared__ int s_act[kMaxRoots];
+    __shared__ int s_nact;
+    if (S.variant == 1) {
+        for (int i = threadIdx.x; i < S.N; i += blockDim.x) s_act[i] = c->slot_active[i];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int n = 0;
+            for (int i = 0; i < S.N; ++i)
+                if (s_act[i]) s_act[n++] = i;
+            s_nact = n;
+        }
+        __syncthreads();
+    }
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= S.W) return;
     const int k = c->iter;
@@ -466,22 +478,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(Geom<R> G, State<R> S
         }
     } else {
         int slot = -1;
-        if (!fwd) {
-            int n_act = 0;
-            for (int i = 0; i < S.N; ++i) n_act += c->slot_active[i] ? 1 : 0;
-            if (n_act > 0) {
-                int want = (w / 2) % n_act;
-                for (int i = 0; i < S.N; ++i) {
-                    if (c->slot_active[i]) {
-                        if (want == 0) {
-                            slot = i;
-                            break;
-                        }
-                        --want;
-                    }
-                }
-            }
-        }
+        if (!fwd && s_nact > 0) slot = s_act[(w / 2) % s_nact];
         if (fwd || slot >= 0) {
 #pragma unroll
             for (int j = 0; j < kMaxDof; ++j) xr[j] = qr[j];
@@ -558,17 +555,24 @@ __global__ void __launch_bounds__(kQT) k_nn(Geom<R> G, State<R> S) {
     __shared__ int s_last;
     const int t = threadIdx.x;
     const int nsets = S.N + 1;
+    // One thread per set loads its counts (a single round trip), then thread 0
+    // forms the tile prefix in shared memory.
+    for (int s = t; s < nsets; s += blockDim.x) {
+        const int nq = c->set_count[s];
+        const int n = s == 0 ? c->n_f : c->n_s[s - 1];
+        int nt, nts, tiles;
+        tiles_for(nq, n, nt, nts, tiles);
+        ts.nq[s] = nq;
+        ts.nn[s] = n;
+        ts.nt[s] = nt;
+        ts.nts[s] = nts;
+        ts.pre[s] = tiles;
+    }
+    __syncthreads();
     if (t == 0) {
         int acc = 0;
         for (int s = 0; s < nsets; ++s) {
-            int nq = c->set_count[s];
-            int n = s == 0 ? c->n_f : c->n_s[s - 1];
-            int nt, nts, tiles;
-            tiles_for(nq, n, nt, nts, tiles);
-            ts.nq[s] = nq;
-            ts.nn[s] = n;
-            ts.nt[s] = nt;
-            ts.nts[s] = nts;
+            const int tiles = ts.pre[s];
             ts.pre[s] = acc;
             acc += tiles;
         }
@@ -648,16 +652,18 @@ __global__ void __launch_bounds__(kQT) k_nn(Geom<R> G, State<R> S) {
                 S.part_idx[(size_t)w * kMaxTiles + ntile] = bidx;
             }
         }
-        __threadfence();
+        // The block's results are visible to thread 0 after the barrier; its
+        // fence (cumulative) publishes them before the completion count.
         __syncthreads();
         if (t == 0) {
+            __threadfence();
             int old = atomicAdd(&S.tile_cnt[s * kMaxQTiles + qt], 1);
             s_last = (old == nt - 1);
+            if (s_last) __threadfence();
         }
         __syncthreads();
         if (s_last) {
             // Every tile of this query tile is done: decode the NN and steer.
-            __threadfence();
             if (w >= 0) {
                 int p;
                 if constexpr (sizeof(R) == 4) {
@@ -947,11 +953,14 @@ __global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
     __shared__ int s_last;
     __shared__ int s_emitted;
     const int t = threadIdx.x;
+    for (int i = t; i < S.N; i += blockDim.x) seg_pre[i] = c->snap_s[i];
+    __syncthreads();
     if (t == 0) {
         int acc = 0;
         for (int i = 0; i < S.N; ++i) {
+            const int v = seg_pre[i];
             seg_pre[i] = acc;
-            acc += c->snap_s[i];
+            acc += v;
         }
         seg_pre[S.N] = acc;
         int tacc = 0;
@@ -1044,15 +1053,15 @@ __global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
             S.part_k2[(size_t)w * kMaxTiles + ntile] = b2;
             S.part_idx[(size_t)w * kMaxTiles + ntile] = bidx;
         }
-        __threadfence();
         __syncthreads();
         if (t == 0) {
+            __threadfence();
             int old = atomicAdd(&S.btile_cnt[s * kMaxQTiles + qt], 1);
             s_last = (old == nt - 1);
+            if (s_last) __threadfence();
         }
         __syncthreads();
         if (s_last) {
-            __threadfence();
             int emitted = 0;
             if (w >= 0) {
                 R k1 = rinf<R>(), k2 = rinf<R>();
@@ -1114,6 +1123,8 @@ __global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) 
     __shared__ int s_counts[kMaxRoots];
     __shared__ double sU, sC;
     __shared__ int s_iter, s_first, s_err, s_decreased;
+    __shared__ int s_donors[kMaxRoots];
+    __shared__ long long s_held[kMaxRoots];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     // Control fields staged in parallel with the candidate loads.
     if (t == 0) sU = c->U;
@@ -1195,7 +1206,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) 
             for (int i = t; i < S.N; i += blockDim.x) c->group_active[i] = s_counts[i];
             if (t == 0) partition(S, sU);
         } else if (t == 0) {
-            recycle(S, sU);
+            recycle(S, sU, s_donors, s_held);
         }
     }
     __syncthreads();
