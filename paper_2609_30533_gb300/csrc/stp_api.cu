@@ -248,7 +248,7 @@ size_t layout_state(stp_problem* p, char* base, R** blob_out, size_t blob_bytes,
     s.w_status = cv.take<int>(W);
     s.w_set = cv.take<int>(W);
     s.w_xr = cv.take<R>((size_t)W * kDP);
-    s.w_T = cv.take<double>(W);
+    s.w_T = cv.take<R>(W);
     s.w_parent = cv.take<int>(W);
     s.w_key = cv.take<R>(W);
     s.w_xnew = cv.take<R>((size_t)W * kDP);
@@ -270,8 +270,8 @@ size_t layout_state(stp_problem* p, char* base, R** blob_out, size_t blob_bytes,
     s.b_idx = cv.take<int>(W);
     s.b_k1 = cv.take<R>(W);
     s.b_k2 = cv.take<R>(W);
-    s.b_U = cv.take<double>(W);
-    s.b_C = cv.take<double>(W);
+    s.b_U = cv.take<R>(W);
+    s.b_C = cv.take<R>(W);
     s.eqa = cv.take<R>((size_t)2 * W * kDP);
     s.eqb = cv.take<R>((size_t)2 * W * kDP);
     s.eta_ = cv.take<R>((size_t)2 * W);
@@ -301,6 +301,8 @@ size_t layout_state(stp_problem* p, char* base, R** blob_out, size_t blob_bytes,
         s.p_new = p->prm.p_new;
         s.p_guided = p->prm.p_guided;
         s.H = p->prm.t_max;
+        s.thr_guided = (unsigned)std::ceil(p->prm.p_guided * 16777216.0);
+        s.thr_new = (unsigned)std::floor(p->prm.p_new * 16777216.0);
         s.key0 = (unsigned)(p->prm.seed & 0xffffffffull);
         s.key1 = (unsigned)(p->prm.seed >> 32);
         s.problem_id = p->prm.problem_id;

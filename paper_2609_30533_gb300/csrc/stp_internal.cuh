@@ -112,6 +112,9 @@ struct State {
     int N, W, variant, cap_f, cap_s, cap_trees, max_pieces;
     double eta, res, p_new, p_guided, H;
     unsigned key0, key1, problem_id;
+    // Coin thresholds on the 24-bit uniform m (u = m 2^-24):
+    // guided iff m < thr_guided = ceil(p_guided 2^24); new root iff m <= thr_new = floor(p_new 2^24).
+    unsigned thr_guided, thr_new;
     R qs[kMaxDof], qg[kMaxDof];
     // forward arena
     R* fx; int* fpar; R* fcost; int* fiter;
@@ -124,7 +127,7 @@ struct State {
     // goal grid free flags [nk]
     unsigned char* gfree;
     // worker records [W]
-    int* w_status; int* w_set; R* w_xr; double* w_T; int* w_parent; R* w_key; R* w_xnew;
+    int* w_status; int* w_set; R* w_xr; R* w_T; int* w_parent; R* w_key; R* w_xnew;
     int* w_edge; int* w_root_edge; int* w_ins; int* w_bedge;
     R* w_xn;           // [W][kDP] steering source x_n
     unsigned long long* w_nnkey;  // [W] packed FP32 NN key (key bits << 32 | index)
@@ -137,7 +140,7 @@ struct State {
     int* bq_count;     // [2]
     int* btile_cnt;    // [2][kMaxQTiles]
     int* b_set; int* b_idx; R* b_k1; R* b_k2;  // per worker best bridge candidate
-    double* b_U; double* b_C;
+    R* b_U; R* b_C;
     // edges
     R* eqa; R* eqb; R* eta_; R* etb; int* ecnt; int* ehit;  // [2W]: entry 2w root check, 2w+1 extension
     R* bqa; R* bqb; R* bta; R* btb; int* bcnt; int* bhit;    // [W]: bridge of worker w

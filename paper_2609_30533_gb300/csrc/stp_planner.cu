@@ -38,7 +38,6 @@ constexpr int kCtaThreads = 1024;
 
 enum WorkerStatus { kSkip = 0, kNN = 1, kVirtual = 2 };
 
-__device__ __forceinline__ double uni_d(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 
 template <typename R>
 __device__ __forceinline__ R uni_r(uint32_t x) {
@@ -176,21 +175,26 @@ __device__ void partition(const State<R>& S, double U) {
     c->n_pieces = np;
 }
 
+// Goal time of group g (Sec. Interval Root), in the working precision: the
+// guided coin is the integer test m_coin < ceil(p_guided 2^24), equivalent to
+// u_coin < p_guided for u = m 2^-24.
 template <typename R>
-__device__ double sample_goal_time(const State<R>& S, int g, double u_coin, double u_pos) {
+__device__ R sample_goal_time(const State<R>& S, int g, uint32_t m_coin, R u_pos) {
     const Ctl* c = S.ctl;
-    if (u_coin < S.p_guided && c->g_meas[g] > 0.0) {
-        double p = u_pos * c->g_meas[g];
-        int f = c->g_first[g], n = c->g_count[g];
+    const R meas = (R)c->g_meas[g];
+    if (m_coin < S.thr_guided && meas > R(0)) {
+        R p = u_pos * meas;
+        const int f = c->g_first[g], n = c->g_count[g];
         for (int j = 0; j < n; ++j) {
-            double lo = S.pc_lo[f + j], hi = S.pc_hi[f + j];
-            double len = hi - lo;
-            if (p < len || j + 1 == n) return fmin(lo + p, hi);
+            const R lo = (R)S.pc_lo[f + j], hi = (R)S.pc_hi[f + j];
+            const R len = hi - lo;
+            if (p < len || j + 1 == n) return (lo + p) < hi ? (lo + p) : hi;
             p -= len;
         }
     }
-    double lo = c->Lg + (double)g * c->width;
-    return lo + u_pos * c->width;
+    const R width = (R)c->width;
+    const R lo = (R)c->Lg + (R)g * width;
+    return lo + u_pos * width;
 }
 
 // ---------------------------------------------------------------------------
@@ -457,9 +461,8 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(Geom<R> G, State<R> S
 
     if (S.variant == 0) {
         const int g = (int)(((unsigned long long)(d[0] >> 8) * (unsigned long long)S.N) >> 24);
-        const double T = sample_goal_time(S, g, uni_d(d[1]), uni_d(d[2]));
-        S.w_T[w] = T;
-        const R Tr = (R)T;
+        const R Tr = sample_goal_time(S, g, d[1] >> 8, uni_r<R>(d[2]));
+        S.w_T[w] = Tr;
         // Conditional query time (Eq. conditional-query-time).
         const R lo = qdist(S.qs, qr, dof) / G.vmax;
         const R hi = Tr - qdist(qr, S.qg, dof) / G.vmax;
@@ -472,7 +475,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(Geom<R> G, State<R> S
             if (fwd) {
                 status = kNN;
             } else {
-                const bool use_new = (c->group_active[g] == 0) || (uni_d(d[3]) <= S.p_new);
+                const bool use_new = (c->group_active[g] == 0) || ((d[3] >> 8) <= S.thr_new);
                 status = use_new ? kVirtual : kNN;
             }
         }
@@ -581,7 +584,8 @@ __global__ void __launch_bounds__(kQT) k_nn(Geom<R> G, State<R> S) {
     __syncthreads();
     const int total = ts.pre[nsets];
     const R v2 = G.vmax * G.vmax;
-    const double U0 = c->U;
+    // U holds a value stored in the trees (or +inf), so it converts exactly.
+    const R U0r = (R)c->U;
     const bool interval = S.variant == 0;
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
         int s = 0;
@@ -614,7 +618,7 @@ __global__ void __launch_bounds__(kQT) k_nn(Geom<R> G, State<R> S) {
                 for (int j = 0; j < DQ; ++j) sx[t][j] = x[j];
                 sx[t][DQ] = x[kDP - 1];
                 bool active = true;
-                if (interval && !fwd) active = (double)troot[c0 + t] < U0;
+                if (interval && !fwd) active = troot[c0 + t] < U0r;
                 sx[t][DQ + 1] = active ? R(1) : R(0);
             }
             __syncthreads();
@@ -831,7 +835,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_insert(Geom<R> G, State<R> S) {
                 } else {
                     int p;
                     if (virt) {
-                        const double T = S.w_T[w];
+                        const R T = S.w_T[w];
                         R* x = bnode(S, seg, idx);
                         for (int j = 0; j < kDP; ++j) x[j] = R(0);
                         for (int j = 0; j < kMaxDof; ++j) x[j] = S.qg[j];
@@ -894,7 +898,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_insert(Geom<R> G, State<R> S) {
 // Candidate (U, C) of worker w's bridge and, if it improves the incumbent at
 // the start of the iteration, its edge entry (entry index w of the bridge batch).
 template <typename R>
-__device__ int bridge_emit(const Geom<R>& G, const State<R>& S, int w, double U0, double C0) {
+__device__ int bridge_emit(const Geom<R>& G, const State<R>& S, int w, R U0, R C0) {
     const bool fwd = S.w_set[w] == 0;
     const R* f;
     const R* b;
@@ -916,8 +920,8 @@ __device__ int bridge_emit(const Geom<R>& G, const State<R>& S, int w, double U0
         cf = S.fcost[S.b_idx[w]];
     }
     const R D = qdist(f, b, G.dof);
-    const double Uc = (double)troot;
-    const double Cc = ((double)cf + (double)D) + (double)cb;
+    const R Uc = troot;
+    const R Cc = (cf + D) + cb;
     const bool improves = (Uc < U0) || (Uc == U0 && Cc < C0);
     if (!improves) return 0;
     S.b_U[w] = Uc;
@@ -982,7 +986,7 @@ __global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
     __syncthreads();
     const int total = s_pre[2];
     const R v2 = G.vmax * G.vmax;
-    const double U0 = c->U, C0 = c->C;
+    const R U0r = (R)c->U, C0r = (R)c->C;
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
         const int s = tile < s_pre[1] ? 0 : 1;
         const int local = tile - s_pre[s];
@@ -1017,7 +1021,7 @@ __global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
                     const int i = li - seg_pre[sg];
                     x = bnode(S, sg, i);
                     tro = S.btroot[bofs(S, sg, i)];
-                    active = (double)tro < U0;
+                    active = tro < U0r;
                 }
 #pragma unroll
                 for (int j = 0; j < DQ; ++j) sx[t][j] = x[j];
@@ -1099,7 +1103,7 @@ __global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
                         S.b_set[w] = sg;
                         S.b_idx[w] = bi - seg_pre[sg];
                     }
-                    emitted = bridge_emit(G, S, w, U0, C0);
+                    emitted = bridge_emit(G, S, w, U0r, C0r);
                 }
             }
             if (emitted) atomicAdd(&s_emitted, 1);
@@ -1118,7 +1122,7 @@ template <typename R>
 __global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) {
     Ctl* c = S.ctl;
     if (c->done) return;
-    __shared__ double rU[kCtaThreads / 32], rC[kCtaThreads / 32];
+    __shared__ R rU[kCtaThreads / 32], rC[kCtaThreads / 32];
     __shared__ int rW[kCtaThreads / 32];
     __shared__ int s_counts[kMaxRoots];
     __shared__ double sU, sC;
@@ -1132,13 +1136,13 @@ __global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) 
     if (t == 64) s_iter = c->iter;
     if (t == 96) s_first = c->first_iter;
     if (t == 128) s_err = c->err;
-    double bU = __longlong_as_double(0x7ff0000000000000LL), bC = bU;
+    R bU = rinf<R>(), bC = rinf<R>();
     int bw = 0x7fffffff;
     for (int w = t; w < S.W; w += blockDim.x) {
         // Bridge entry of worker w is entry w; all loads independent.
         const int e = S.w_bedge[w];
         const int h = S.bhit[w];
-        const double U = S.b_U[w], C = S.b_C[w];
+        const R U = S.b_U[w], C = S.b_C[w];
         if (e < 0 || h) continue;
         if (U < bU || (U == bU && (C < bC || (C == bC && w < bw)))) {
             bU = U;
@@ -1147,8 +1151,8 @@ __global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) 
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
-        double U = __shfl_xor_sync(0xffffffffu, bU, o);
-        double C = __shfl_xor_sync(0xffffffffu, bC, o);
+        R U = __shfl_xor_sync(0xffffffffu, bU, o);
+        R C = __shfl_xor_sync(0xffffffffu, bC, o);
         int ww = __shfl_xor_sync(0xffffffffu, bw, o);
         if (U < bU || (U == bU && (C < bC || (C == bC && ww < bw)))) {
             bU = U;
@@ -1173,11 +1177,11 @@ __global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) 
         s_decreased = 0;
         if (bw != 0x7fffffff) {
             const int wset = S.w_set[bw], wins = S.w_ins[bw], bset = S.b_set[bw], bidx = S.b_idx[bw];
-            s_decreased = bU < sU;
-            sU = bU;
-            sC = bC;
-            c->U = bU;
-            c->C = bC;
+            s_decreased = bU < (R)sU;
+            sU = (double)bU;
+            sC = (double)bC;
+            c->U = sU;
+            c->C = sC;
             if (wset == 0) {
                 c->inc_f = wins;
                 c->inc_s = bset;
