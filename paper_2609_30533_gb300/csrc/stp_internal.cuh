@@ -29,7 +29,7 @@ constexpr int kMaxWorkers = 8192;
 constexpr int kQT = 128;        // queries per NN tile (= threads per CTA)
 constexpr int kMaxTiles = 64;   // node tiles per query (partials per query)
 constexpr int kMaxQTiles = kMaxWorkers / kQT;
-constexpr int kNodeTileMin = 256;
+constexpr int kNodeTileMin = 128;
 constexpr unsigned kWaitLimit = 1u << 24;  // bounded spin on mbarriers
 
 enum ErrBits { kErrCapacity = 1, kErrTimeout = 2, kErrInternal = 4 };

@@ -623,26 +623,32 @@ __global__ void __launch_bounds__(kQT) k_nn(Geom<R> G, State<R> S) {
             }
             __syncthreads();
             if (w >= 0) {
-                for (int i = 0; i < cnt; ++i) {
+                auto key_of = [&](int i) -> R {
                     R D2 = R(0);
 #pragma unroll
                     for (int j = 0; j < DQ; ++j) {
                         R e = sx[i][j] - q[j];
                         D2 += e * e;
                     }
-                    R key;
-                    if (interval) {
-                        const R dt = tr - sx[i][DQ];
-                        const R Delta = fwd ? dt : -dt;
-                        const bool ok = (sx[i][DQ + 1] != R(0)) && (Delta > R(0)) && (D2 <= v2 * Delta * Delta);
-                        key = ok ? D2 + v2 * dt * dt : rinf<R>();
-                    } else {
-                        key = D2;
-                    }
-                    if (key < best) {
-                        best = key;
-                        bidx = c0 + i;
-                    }
+                    if (!interval) return D2;
+                    const R dt = tr - sx[i][DQ];
+                    const R Delta = fwd ? dt : -dt;
+                    const bool ok = (sx[i][DQ + 1] != R(0)) && (Delta > R(0)) && (D2 <= v2 * Delta * Delta);
+                    return ok ? D2 + v2 * dt * dt : rinf<R>();
+                };
+                // Four independent key chains per step; updates in index order
+                // keep the lowest index on ties.
+                int i = 0;
+                for (; i + 4 <= cnt; i += 4) {
+                    const R k0 = key_of(i), k1 = key_of(i + 1), k2 = key_of(i + 2), k3 = key_of(i + 3);
+                    if (k0 < best) { best = k0; bidx = c0 + i; }
+                    if (k1 < best) { best = k1; bidx = c0 + i + 1; }
+                    if (k2 < best) { best = k2; bidx = c0 + i + 2; }
+                    if (k3 < best) { best = k3; bidx = c0 + i + 3; }
+                }
+                for (; i < cnt; ++i) {
+                    const R k0 = key_of(i);
+                    if (k0 < best) { best = k0; bidx = c0 + i; }
                 }
             }
         }
@@ -1030,9 +1036,11 @@ __global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
             }
             __syncthreads();
             if (w >= 0) {
-                for (int i = 0; i < cnt; ++i) {
+                // Rank key of vertex i: (arrival time, rho^2); rho^2 = inf when
+                // the vertex is inactive or not admissible.
+                auto key_of = [&](int i, R& k1) -> R {
                     const R tro = sx[i][DQ + 1];
-                    if (!(tro < rinf<R>())) continue;
+                    k1 = s == 0 ? R(0) : tro;
                     R D2 = R(0);
 #pragma unroll
                     for (int j = 0; j < DQ; ++j) {
@@ -1041,14 +1049,30 @@ __global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
                     }
                     // s = 0: vertex earlier than the query; s = 1: later.
                     const R dt = s == 0 ? tq - sx[i][DQ] : sx[i][DQ] - tq;
-                    if (!(dt > R(0)) || !(D2 <= v2 * dt * dt)) continue;
-                    const R k2 = D2 + v2 * dt * dt;
-                    const R k1 = s == 0 ? R(0) : tro;
-                    if (key_less(k1, k2, c0 + i, b1, b2, bidx)) {
+                    const bool ok = (tro < rinf<R>()) && (dt > R(0)) && (D2 <= v2 * dt * dt);
+                    return ok ? D2 + v2 * dt * dt : rinf<R>();
+                };
+                auto take = [&](R k1, R k2, int idx) {
+                    if (k2 < rinf<R>() && key_less(k1, k2, idx, b1, b2, bidx)) {
                         b1 = k1;
                         b2 = k2;
-                        bidx = c0 + i;
+                        bidx = idx;
                     }
+                };
+                int i = 0;
+                for (; i + 4 <= cnt; i += 4) {
+                    R a1, b1_, c1, d1;
+                    const R a2 = key_of(i, a1), b2_ = key_of(i + 1, b1_), c2 = key_of(i + 2, c1),
+                            d2 = key_of(i + 3, d1);
+                    take(a1, a2, c0 + i);
+                    take(b1_, b2_, c0 + i + 1);
+                    take(c1, c2, c0 + i + 2);
+                    take(d1, d2, c0 + i + 3);
+                }
+                for (; i < cnt; ++i) {
+                    R a1;
+                    const R a2 = key_of(i, a1);
+                    take(a1, a2, c0 + i);
                 }
             }
         }
@@ -1315,7 +1339,7 @@ cudaError_t launch_plan_reset(const Geom<R>& g, const State<R>& s, int max_iters
 
 template <typename R>
 cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cudaStream_t st, cudaEvent_t* ev) {
-    const int nn_grid = 2 * validate_grid_blocks();
+    const int nn_grid = 4 * validate_grid_blocks();
     const int wgrid = (s.W + kSampleThreads - 1) / kSampleThreads;
     int ne = 0;
     // External event-record nodes: inside a stream capture a plain event record
