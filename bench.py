@@ -204,6 +204,70 @@ def microbench(args, P, prob, prm, stream, flush, rank, local):
     return micro, peak
 
 
+def batched(args, rank):
+    """Batched form: mixed problems (2/6/7-DoF, 4..128 obstacles, 10..60 s
+    horizons) planned together in one graph-captured launch sequence; W and the
+    launch shape are chosen by the autotuner on a sample. Reports throughput and
+    first-solution latency percentiles, beside the same problems planned one by
+    one (plain) on a sample."""
+    import dataclasses
+
+    from paper_2609_30533_gb300 import autotune, stp
+
+    def make(indices, W, iters):
+        out = []
+        for i in indices:
+            prob, prm = WL.mixed(i)
+            prm = dataclasses.replace(prm, workers=W, max_iters=iters, problem_id=i, seed=rank)
+            out.append(stp.problem_from(prob, prm, precision=0, iters_per_graph=16))
+        return out
+
+    sample = list(range(48))
+    choice = autotune.autotune(lambda W: make(sample, W, args.tune_iters), workers=(256, 512),
+                               nn_ctas=(4, 8), validate_ctas=(1, 2))
+    idx = list(range(args.batch_problems))
+    probs = make(idx, choice.workers, args.batch_iters)
+    B = stp.Batch(probs, nn_ctas=choice.nn_ctas, validate_ctas=choice.validate_ctas, iters_per_graph=16)
+    B.plan()
+    runs = []
+    for _ in range(args.batch_reps):
+        ms, stats = B.plan()
+        runs.append((ms, stats))
+    B.close()
+    ms = statistics.median(r[0] for r in runs)
+    stats = runs[0][1]
+    fs = sorted(st["first_solution_ms"] for st in stats if st["first_solution_iter"] >= 0)
+    edges = sum(st["edges_validated"] + st["bridges_validated"] for st in stats)
+
+    # Plain: the same problems one at a time (sample), same W and budget.
+    plain_fs, plain_ms, plain_solved = [], [], 0
+    for i in idx[:args.plain_sample]:
+        out = probs[i].plan()
+        plain_ms.append(out.stats["plan_ms"])
+        if out.stats["first_solution_iter"] >= 0:
+            plain_solved += 1
+            plain_fs.append(out.stats["first_solution_ms"])
+    for P in probs:
+        P.close()
+
+    def pct(v, q):
+        return float(np.percentile(v, q)) if v else None
+
+    return {
+        "workload": "mixed 2/6/7-DoF, 4-128 obstacles, 10-60 s horizons",
+        "problems": len(idx), "iters_budget": args.batch_iters,
+        "autotuned": {"workers": choice.workers, "nn_ctas": choice.nn_ctas, "validate_ctas": choice.validate_ctas,
+                      "trials": [dataclasses.asdict(t) for t in choice.trials]},
+        "batch_ms": ms, "problems_per_s": len(idx) / (ms * 1e-3), "edges_per_s": edges / (ms * 1e-3),
+        "solved": len(fs), "success_rate": len(fs) / len(idx),
+        "first_solution_ms_p50": pct(fs, 50), "first_solution_ms_p99": pct(fs, 99),
+        "plain_sample": {"problems": len(plain_ms), "solved": plain_solved,
+                         "first_solution_ms_p50": pct(plain_fs, 50), "first_solution_ms_p99": pct(plain_fs, 99),
+                         "ms_per_problem_p50": pct(plain_ms, 50), "sequential_ms_per_problem": float(np.mean(plain_ms)),
+                         "batched_ms_per_problem": ms / len(idx)},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -215,7 +279,13 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=8)
     ap.add_argument("--micro-edges", type=int, default=1 << 20)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--only", default="", choices=["", "micro"],
+    ap.add_argument("--batch-problems", type=int, default=512)
+    ap.add_argument("--batch-iters", type=int, default=64)
+    ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--tune-iters", type=int, default=24)
+    ap.add_argument("--plain-sample", type=int, default=48)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--only", default="", choices=["", "micro", "batch"],
                     help="micro: run only the collision microbenchmark (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -247,6 +317,9 @@ def main():
     if args.only == "micro":
         micro, peak = microbench(args, P, prob, prm, stream, flush, rank, local)
         print(json.dumps({"microbench": dict(micro, n_edges=args.micro_edges, peak_tflops=peak)}))
+        return
+    if args.only == "batch":
+        print(json.dumps({"batched": batched(args, rank)}))
         return
 
     def step_timed():
@@ -328,6 +401,7 @@ def main():
     e2e_secs = time.perf_counter() - t0
 
     micro, peak = microbench(args, P, prob, prm, stream, flush, rank, local)
+    batch_result = None if args.no_batch else batched(args, rank)
     n = args.micro_edges
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = float(_peaks().get("sm_max_mhz", 2070.0))
@@ -384,6 +458,8 @@ def main():
     }
     if clk:
         line["clocks"] = clk
+    if not args.no_batch:
+        line["batched"] = batch_result
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line))

@@ -214,6 +214,31 @@ stp_status stp_profile(stp_problem *p, int cap, const char **names, double *ms, 
 stp_status stp_check_edges_noalloc(stp_problem *p, int n_edges, const void *qa, const void *ta, const void *qb,
                                    const void *tb, unsigned char *verdict);
 
+/* ---- Batched planning (many problems in one launch sequence) -------------
+ * A batch runs several FP32 problems' planner iterations together: every
+ * kernel of an iteration covers all problems (one CUDA grid dimension per
+ * problem), and the iterations are captured into one CUDA graph. Problems keep
+ * their own parameters (variant, N, W, budget, ...) and arenas; they must stay
+ * alive while the batch exists. Problems whose start is in collision, or whose
+ * start equals the goal, are resolved without iterations as in stp_plan. */
+typedef struct stp_batch stp_batch;
+typedef struct {
+    int nn_ctas;          /* CTAs per problem for the NN and bridge scans; 0 = 8 */
+    int validate_ctas;    /* CTAs per problem for the collision kernel; 0 = 2 */
+    int iters_per_graph;  /* iterations per graph launch; 0 = 16 */
+} stp_batch_params;
+/* problems [n], n >= 1, all created with precision 0; params may be NULL. */
+stp_status stp_batch_create(stp_problem *const *problems, int n, const stp_batch_params *params,
+                            stp_batch **out);
+/* Plan every problem from a fresh state. stats [n] (or NULL) receives each
+ * problem's statistics (first_solution_ms is measured from the start of the
+ * batch); *batch_ms the device time of the whole batch. Returns STP_OK unless
+ * a CUDA call failed or a problem overflowed (STP_ERR_CAPACITY). */
+stp_status stp_batch_plan(stp_batch *b, stp_stats *stats, double *batch_ms);
+/* Path of problem i after stp_batch_plan: [cap][dof+1]; *n_path = states. */
+stp_status stp_batch_path(stp_batch *b, int i, double *path, int cap, int *n_path);
+void stp_batch_free(stp_batch *b);
+
 /* Release all device and host memory of a problem. NULL is allowed. */
 void stp_free(stp_problem *p);
 

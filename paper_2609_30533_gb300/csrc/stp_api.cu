@@ -1071,3 +1071,200 @@ extern "C" stp_status stp_check_edges_noalloc(stp_problem* p, int n_edges, const
     return p->precision == 0 ? check_edges_noalloc_impl<float>(p, n_edges, qa, ta, qb, tb, verdict)
                              : check_edges_noalloc_impl<double>(p, n_edges, qa, ta, qb, tb, verdict);
 }
+
+// ---------------------------------------------------------------------------
+// Batched planning.
+// ---------------------------------------------------------------------------
+struct stp_batch {
+    std::vector<stp_problem*> probs;
+    std::vector<int> trivial;  // 0 plan, 1 blocked start, 2 start == goal
+    Geom<float>* d_geom = nullptr;
+    State<float>* d_state = nullptr;
+    int* d_iters = nullptr;
+    BatchShape shape{};
+    int iters_per_graph = 16;
+    int max_iters = 0;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<Ctl> ctl;
+    std::string last_error;
+};
+
+extern "C" stp_status stp_batch_create(stp_problem* const* problems, int n, const stp_batch_params* bp,
+                                       stp_batch** out) {
+    clear_stale_error();
+    if (!out || !problems || n < 1 || n > 65535) return STP_ERR_INVALID;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!problems[i] || problems[i]->precision != 0) return STP_ERR_INVALID;
+    stp_batch* b = new (std::nothrow) stp_batch();
+    if (!b) return STP_ERR_CUDA;
+    b->probs.assign(problems, problems + n);
+    b->iters_per_graph = bp && bp->iters_per_graph > 0 ? bp->iters_per_graph : 16;
+    BatchShape& sh = b->shape;
+    sh.P = n;
+    sh.nn_ctas = bp && bp->nn_ctas > 0 ? bp->nn_ctas : 8;
+    sh.validate_ctas = bp && bp->validate_ctas > 0 ? bp->validate_ctas : 2;
+    std::vector<Geom<float>> hg(n);
+    std::vector<State<float>> hs(n);
+    std::vector<int> iters(n);
+    int max_blob = 0;
+    b->trivial.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        stp_problem* p = problems[i];
+        bool same = true;
+        for (int j = 0; j < p->dof; ++j) same = same && p->qs[j] == p->qg[j];
+        b->trivial[i] = !p->start_free ? 1 : (same ? 2 : 0);
+        hg[i] = p->gf;
+        hs[i] = p->sf;
+        iters[i] = b->trivial[i] ? 0 : p->prm.max_iters;
+        b->max_iters = std::max(b->max_iters, iters[i]);
+        sh.max_W = std::max(sh.max_W, p->prm.ext_per_iter);
+        sh.max_obs = std::max(sh.max_obs, p->M);
+        max_blob = std::max(max_blob, (int)p->gf.blob_bytes);
+    }
+    sh.validate_smem = max_blob + (int)sizeof(int) * (2 * sh.max_W + 1);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_geom, sizeof(Geom<float>) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_state, sizeof(State<float>) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_iters, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_geom, hg.data(), sizeof(Geom<float>) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_state, hs.data(), sizeof(State<float>) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_iters, iters.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    if (e == cudaSuccess) {
+        // Configure the batched collision kernel outside the capture.
+        e = launch_validate_batch<float>(b->d_geom, b->d_state, 0, 0, sh.max_obs, 1, sh.validate_smem, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t g;
+        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        cudaError_t le = cudaSuccess;
+        for (int i = 0; i < b->iters_per_graph && e == cudaSuccess && le == cudaSuccess; ++i)
+            le = launch_iteration_batch<float>(b->d_geom, b->d_state, sh, b->stream);
+        cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+        if (e == cudaSuccess) e = le != cudaSuccess ? le : ee;
+        if (e == cudaSuccess) {
+            e = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+        }
+    }
+    if (e != cudaSuccess) {
+        char buf[256];
+        snprintf(buf, sizeof(buf), "stp_batch_create: %s", cudaGetErrorString(e));
+        g_last_error = buf;
+        stp_batch_free(b);
+        return STP_ERR_CUDA;
+    }
+    b->ctl.resize(n);
+    *out = b;
+    return STP_OK;
+}
+
+extern "C" stp_status stp_batch_plan(stp_batch* b, stp_stats* stats, double* batch_ms) {
+    clear_stale_error();
+    if (!b) return STP_ERR_INVALID;
+    const int n = (int)b->probs.size();
+    cudaStream_t st = b->stream;
+    auto fail = [&](cudaError_t e, const char* where) {
+        char buf[256];
+        snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+        b->last_error = buf;
+        g_last_error = buf;
+        return STP_ERR_CUDA;
+    };
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        stp_problem* p = b->probs[i];
+        e = cudaMemsetAsync(p->sf.tile_cnt, 0, sizeof(int) * (size_t)(p->prm.n_roots + 1) * kMaxQTiles, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->sf.btile_cnt, 0, sizeof(int) * 2 * kMaxQTiles, st);
+    }
+    if (e != cudaSuccess) return fail(e, "memset");
+    if ((e = cudaEventRecord(b->ev0, st)) != cudaSuccess) return fail(e, "cudaEventRecord");
+    if ((e = launch_plan_reset_batch<float>(b->d_state, b->shape, b->d_iters, st)) != cudaSuccess)
+        return fail(e, "reset");
+    const int n_launch = (b->max_iters + b->iters_per_graph - 1) / b->iters_per_graph;
+    for (int i = 0; i < n_launch; ++i)
+        if ((e = cudaGraphLaunch(b->graph, st)) != cudaSuccess) return fail(e, "cudaGraphLaunch");
+    if ((e = cudaEventRecord(b->ev1, st)) != cudaSuccess) return fail(e, "cudaEventRecord");
+    if ((e = launch_extract_path_batch<float>(b->d_state, b->shape, st)) != cudaSuccess) return fail(e, "path");
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(&b->ctl[i], b->probs[i]->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(e, "readback");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+    if (batch_ms) *batch_ms = ms;
+    stp_status result = STP_OK;
+    for (int i = 0; i < n; ++i) {
+        const Ctl& hc = b->ctl[i];
+        stp_problem* p = b->probs[i];
+        p->planned = b->trivial[i] == 0;
+        stp_stats s;
+        std::memset(&s, 0, sizeof(s));
+        s.first_solution_iter = -1;
+        s.first_solution_ms = -1.0;
+        s.U = kInfD;
+        s.C = kInfD;
+        if (b->trivial[i] == 2) {
+            s.U = 0.0;
+            s.C = 0.0;
+            s.first_solution_iter = 0;
+            s.first_solution_ms = 0.0;
+        } else if (b->trivial[i] == 0) {
+            s.iterations = hc.iter;
+            s.first_solution_iter = hc.first_iter;
+            s.nodes = (long long)hc.st_ins;
+            s.edges_validated = (long long)hc.st_ext;
+            s.bridges_validated = (long long)hc.st_bridge;
+            s.root_checks = (long long)hc.st_root;
+            s.check_points = (long long)hc.st_points;
+            s.pair_tests = (long long)hc.st_pairs;
+            s.first_solution_ms = hc.first_iter >= 0 ? (double)(hc.t_first - hc.t_start) * 1e-6 : -1.0;
+            s.plan_ms = hc.t_end > hc.t_start ? (double)(hc.t_end - hc.t_start) * 1e-6 : ms;
+            s.U = hc.U;
+            s.C = hc.C;
+            if (hc.err & kErrCapacity) result = STP_ERR_CAPACITY;
+        }
+        if (stats) stats[i] = s;
+    }
+    return result;
+}
+
+extern "C" stp_status stp_batch_path(stp_batch* b, int i, double* path, int cap, int* n_path) {
+    if (!b || i < 0 || i >= (int)b->probs.size() || !n_path) return STP_ERR_INVALID;
+    stp_problem* p = b->probs[i];
+    *n_path = 0;
+    if (b->trivial[i] == 2) {
+        *n_path = 1;
+        if (path) {
+            if (cap < 1) return STP_ERR_CAPACITY;
+            for (int j = 0; j < p->dof; ++j) path[j] = p->qs[j];
+            path[p->dof] = 0.0;
+        }
+        return STP_OK;
+    }
+    if (b->trivial[i] == 1) return STP_OK;
+    int len = 0;
+    STP_CUDA(p, cudaMemcpy(&len, p->sf.path_len, sizeof(int), cudaMemcpyDeviceToHost));
+    if (len < 0) return STP_ERR_CAPACITY;
+    *n_path = len;
+    if (path && len > 0) return copy_path<float>(p, len, path, cap);
+    return STP_OK;
+}
+
+extern "C" void stp_batch_free(stp_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->d_geom) cudaFree(b->d_geom);
+    if (b->d_state) cudaFree(b->d_state);
+    if (b->d_iters) cudaFree(b->d_iters);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}

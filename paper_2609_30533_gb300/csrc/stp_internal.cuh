@@ -312,6 +312,68 @@ __device__ __forceinline__ void obstacle_at(const R* way, const R* vel, int K, R
 }
 
 // ---------------------------------------------------------------------------
+// Planner edge batches: extension entries (2w root check, 2w+1 extension) and
+// bridge entries (w), offsets scanned inside the collision kernel.
+// ---------------------------------------------------------------------------
+template <typename R>
+__host__ __device__ inline EdgeBatch<R> ext_batch(const State<R>& S) {
+    EdgeBatch<R> E;
+    E.qa = S.eqa;
+    E.qb = S.eqb;
+    E.ta = S.eta_;
+    E.tb = S.etb;
+    E.qstride = kDP;
+    E.cnt = S.ecnt;
+    E.off = nullptr;  // offsets scanned in the kernel
+    E.n_dev = nullptr;
+    E.n_host = 2 * S.W;
+    E.hit = S.ehit;
+    E.clear = nullptr;
+    E.points_done = &S.ctl->st_points;
+    E.pairs_done = &S.ctl->st_pairs;
+    E.err = &S.ctl->err;
+    E.done = &S.ctl->done;
+    return E;
+}
+
+template <typename R>
+__host__ __device__ inline EdgeBatch<R> bridge_batch(const State<R>& S) {
+    EdgeBatch<R> E;
+    E.qa = S.bqa;
+    E.qb = S.bqb;
+    E.ta = S.bta;
+    E.tb = S.btb;
+    E.qstride = kDP;
+    E.cnt = S.bcnt;
+    E.off = nullptr;
+    E.n_dev = nullptr;
+    E.n_host = S.W;
+    E.hit = S.bhit;
+    E.clear = nullptr;
+    E.points_done = &S.ctl->st_points;
+    E.pairs_done = &S.ctl->st_pairs;
+    E.err = &S.ctl->err;
+    E.done = &S.ctl->done;
+    return E;
+}
+
+
+// Batched kernels: copy problem p's Geom and State into shared memory.
+template <typename R>
+__device__ __forceinline__ void stage_problem(const Geom<R>* Gs, const State<R>* Ss, int p, Geom<R>& G, State<R>& S,
+                                              bool with_geom = true) {
+    const int* ssrc = reinterpret_cast<const int*>(Ss + p);
+    int* sdst = reinterpret_cast<int*>(&S);
+    if (with_geom) {
+        const int* gsrc = reinterpret_cast<const int*>(Gs + p);
+        int* gdst = reinterpret_cast<int*>(&G);
+        for (int i = threadIdx.x; i < (int)(sizeof(Geom<R>) / sizeof(int)); i += blockDim.x) gdst[i] = gsrc[i];
+    }
+    for (int i = threadIdx.x; i < (int)(sizeof(State<R>) / sizeof(int)); i += blockDim.x) sdst[i] = ssrc[i];
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // Launchers (explicitly instantiated in the .cu files).
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -338,5 +400,24 @@ cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cud
                              cudaEvent_t* ev = nullptr);
 template <typename R>
 cudaError_t launch_extract_path(const State<R>& s, int dof, cudaStream_t st);
+
+// Batched planner (problems of one precision; device arrays of Geom/State).
+struct BatchShape {
+    int P;               // problems
+    int max_W;           // largest W
+    int max_obs;         // largest obstacle count
+    int validate_smem;   // dynamic shared memory of the batched collision kernel
+    int nn_ctas;         // CTAs per problem for the NN and bridge scans
+    int validate_ctas;   // CTAs per problem for the collision kernel
+};
+template <typename R>
+cudaError_t launch_validate_batch(const Geom<R>* Gs, const State<R>* Ss, int P, int which, int max_obs,
+                                  int ctas_per_problem, int smem_bytes, cudaStream_t st);
+template <typename R>
+cudaError_t launch_plan_reset_batch(const State<R>* Ss, const BatchShape& b, const int* max_iters, cudaStream_t st);
+template <typename R>
+cudaError_t launch_iteration_batch(const Geom<R>* Gs, const State<R>* Ss, const BatchShape& b, cudaStream_t st);
+template <typename R>
+cudaError_t launch_extract_path_batch(const State<R>* Ss, const BatchShape& b, cudaStream_t st);
 
 }  // namespace stp

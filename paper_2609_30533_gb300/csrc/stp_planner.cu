@@ -258,7 +258,7 @@ __device__ void recycle(const State<R>& S, double U, int* donors, long long* hel
 // Reset: fresh trees and allocation for a new plan.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void k_reset(State<R> S, int max_iters) {
+__device__ __forceinline__ void reset_body(const State<R>& S, int max_iters) {
     Ctl* c = S.ctl;
     const int t = threadIdx.x;
     if (t == 0) {
@@ -420,7 +420,7 @@ __device__ bool steer_and_emit(const Geom<R>& G, const State<R>& S, int w, int s
 // k_sample: one thread per worker.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(kSampleThreads) k_sample(Geom<R> G, State<R> S) {
+__device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S) {
     const Ctl* c = S.ctl;
     if (c->done) return;
     // Active-slot list (recycling) staged once per block.
@@ -550,7 +550,7 @@ __device__ __forceinline__ unsigned long long pack_key(float k, int idx) {
 // NN scan. Set 0 = forward arena; set 1+i = backward segment i. DQ = number of
 // configuration coordinates compared (3 or 7; missing ones are zero).
 template <typename R, int DQ>
-__global__ void __launch_bounds__(kQT) k_nn(Geom<R> G, State<R> S) {
+__device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S) {
     const Ctl* c = S.ctl;
     if (c->done) return;
     __shared__ TileSets ts;
@@ -741,7 +741,7 @@ __device__ __forceinline__ long long cta_exclusive_scan(long long v, long long* 
 // per-worker bridge state of the iteration.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(kCtaThreads) k_insert(Geom<R> G, State<R> S) {
+__device__ __forceinline__ void insert_body(const Geom<R>& G, const State<R>& S) {
     Ctl* c = S.ctl;
     if (c->done) return;
     __shared__ int wt[kCtaThreads / 32][kMaxRoots + 1];
@@ -954,7 +954,7 @@ __device__ int bridge_emit(const Geom<R>& G, const State<R>& S, int w, R U0, R C
 // tile reduces the per-tile partials in tile order and emits the bridge edges.
 // ---------------------------------------------------------------------------
 template <typename R, int DQ>
-__global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
+__device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S) {
     Ctl* c = S.ctl;
     if (c->done) return;
     __shared__ int seg_pre[kMaxRoots + 1];
@@ -1143,7 +1143,7 @@ __global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) {
 // allocation update.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) {
+__device__ __forceinline__ void publish_body(const Geom<R>& G, const State<R>& S) {
     Ctl* c = S.ctl;
     if (c->done) return;
     __shared__ R rU[kCtaThreads / 32], rC[kCtaThreads / 32];
@@ -1256,7 +1256,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) 
 // Path: forward chain from the start root to inc_f, then backward chain from
 // inc_b to its root. One thread.
 template <typename R>
-__global__ void k_extract_path(State<R> S) {
+__device__ __forceinline__ void extract_path_body(const State<R>& S) {
     const Ctl* c = S.ctl;
     int n = 0;
     if (c->inc_f >= 0) {
@@ -1284,50 +1284,77 @@ __global__ void k_extract_path(State<R> S) {
 }
 
 // ---------------------------------------------------------------------------
-// Host launchers.
+// Kernels: single problem (structs as parameters) and batch (problem
+// blockIdx.y, structs staged in shared memory).
 // ---------------------------------------------------------------------------
 template <typename R>
-static EdgeBatch<R> ext_batch(const State<R>& S) {
-    EdgeBatch<R> E;
-    E.qa = S.eqa;
-    E.qb = S.eqb;
-    E.ta = S.eta_;
-    E.tb = S.etb;
-    E.qstride = kDP;
-    E.cnt = S.ecnt;
-    E.off = nullptr;  // offsets scanned in the kernel
-    E.n_dev = nullptr;
-    E.n_host = 2 * S.W;
-    E.hit = S.ehit;
-    E.clear = nullptr;
-    E.points_done = &S.ctl->st_points;
-    E.pairs_done = &S.ctl->st_pairs;
-    E.err = &S.ctl->err;
-    E.done = &S.ctl->done;
-    return E;
-}
+__global__ void k_reset(State<R> S, int max_iters) { reset_body(S, max_iters); }
+template <typename R>
+__global__ void __launch_bounds__(kSampleThreads) k_sample(Geom<R> G, State<R> S) { sample_body(G, S); }
+template <typename R, int DQ>
+__global__ void __launch_bounds__(kQT) k_nn(Geom<R> G, State<R> S) { nn_body<R, DQ>(G, S); }
+template <typename R>
+__global__ void __launch_bounds__(kCtaThreads) k_insert(Geom<R> G, State<R> S) { insert_body(G, S); }
+template <typename R, int DQ>
+__global__ void __launch_bounds__(kQT) k_bridge(Geom<R> G, State<R> S) { bridge_body<R, DQ>(G, S); }
+template <typename R>
+__global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) { publish_body(G, S); }
+template <typename R>
+__global__ void k_extract_path(State<R> S) { extract_path_body(S); }
 
 template <typename R>
-static EdgeBatch<R> bridge_batch(const State<R>& S) {
-    EdgeBatch<R> E;
-    E.qa = S.bqa;
-    E.qb = S.bqb;
-    E.ta = S.bta;
-    E.tb = S.btb;
-    E.qstride = kDP;
-    E.cnt = S.bcnt;
-    E.off = nullptr;
-    E.n_dev = nullptr;
-    E.n_host = S.W;
-    E.hit = S.bhit;
-    E.clear = nullptr;
-    E.points_done = &S.ctl->st_points;
-    E.pairs_done = &S.ctl->st_pairs;
-    E.err = &S.ctl->err;
-    E.done = &S.ctl->done;
-    return E;
+__global__ void k_reset_b(const State<R>* Ss, const int* max_iters) {
+    __shared__ Geom<R> G;
+    __shared__ State<R> S;
+    stage_problem((const Geom<R>*)nullptr, Ss, blockIdx.y, G, S, false);
+    reset_body(S, max_iters[blockIdx.y]);
+}
+template <typename R>
+__global__ void __launch_bounds__(kSampleThreads) k_sample_b(const Geom<R>* Gs, const State<R>* Ss) {
+    __shared__ Geom<R> G;
+    __shared__ State<R> S;
+    stage_problem(Gs, Ss, blockIdx.y, G, S);
+    sample_body(G, S);
+}
+template <typename R, int DQ>
+__global__ void __launch_bounds__(kQT) k_nn_b(const Geom<R>* Gs, const State<R>* Ss) {
+    __shared__ Geom<R> G;
+    __shared__ State<R> S;
+    stage_problem(Gs, Ss, blockIdx.y, G, S);
+    nn_body<R, DQ>(G, S);
+}
+template <typename R>
+__global__ void __launch_bounds__(kCtaThreads) k_insert_b(const Geom<R>* Gs, const State<R>* Ss) {
+    __shared__ Geom<R> G;
+    __shared__ State<R> S;
+    stage_problem(Gs, Ss, blockIdx.y, G, S);
+    insert_body(G, S);
+}
+template <typename R, int DQ>
+__global__ void __launch_bounds__(kQT) k_bridge_b(const Geom<R>* Gs, const State<R>* Ss) {
+    __shared__ Geom<R> G;
+    __shared__ State<R> S;
+    stage_problem(Gs, Ss, blockIdx.y, G, S);
+    bridge_body<R, DQ>(G, S);
+}
+template <typename R>
+__global__ void __launch_bounds__(kCtaThreads) k_publish_b(const Geom<R>* Gs, const State<R>* Ss) {
+    __shared__ Geom<R> G;
+    __shared__ State<R> S;
+    stage_problem(Gs, Ss, blockIdx.y, G, S);
+    publish_body(G, S);
+}
+template <typename R>
+__global__ void k_extract_path_b(const State<R>* Ss) {
+    __shared__ Geom<R> G;
+    __shared__ State<R> S;
+    stage_problem((const Geom<R>*)nullptr, Ss, blockIdx.y, G, S, false);
+    extract_path_body(S);
 }
 
+// ---------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------
 const char* const kIterKernelNames[kIterKernels] = {"k_sample", "k_nn", "k_validate(ext)", "k_insert",
                                                     "k_bridge", "k_validate(bridge)", "k_publish"};
 
@@ -1375,6 +1402,41 @@ cudaError_t launch_extract_path(const State<R>& s, int dof, cudaStream_t st) {
     k_extract_path<R><<<1, 1, 0, st>>>(s);
     return cudaGetLastError();
 }
+
+template <typename R>
+cudaError_t launch_plan_reset_batch(const State<R>* Ss, const BatchShape& b, const int* max_iters, cudaStream_t st) {
+    k_reset_b<R><<<dim3(1, b.P), 256, 0, st>>>(Ss, max_iters);
+    return cudaGetLastError();
+}
+
+// One batched iteration: every kernel covers all problems (grid y = problem).
+// Mixed degrees of freedom use the 7-coordinate NN key (missing coordinates
+// are zero) and a run-time arm/point choice in the collision kernel.
+template <typename R>
+cudaError_t launch_iteration_batch(const Geom<R>* Gs, const State<R>* Ss, const BatchShape& b, cudaStream_t st) {
+    const int wgrid = (b.max_W + kSampleThreads - 1) / kSampleThreads;
+    k_sample_b<R><<<dim3(wgrid, b.P), kSampleThreads, 0, st>>>(Gs, Ss);
+    k_nn_b<R, kMaxDof><<<dim3(b.nn_ctas, b.P), kQT, 0, st>>>(Gs, Ss);
+    cudaError_t err = launch_validate_batch<R>(Gs, Ss, b.P, 0, b.max_obs, b.validate_ctas, b.validate_smem, st);
+    if (err != cudaSuccess) return err;
+    k_insert_b<R><<<dim3(1, b.P), kCtaThreads, 0, st>>>(Gs, Ss);
+    k_bridge_b<R, kMaxDof><<<dim3(b.nn_ctas, b.P), kQT, 0, st>>>(Gs, Ss);
+    err = launch_validate_batch<R>(Gs, Ss, b.P, 1, b.max_obs, b.validate_ctas, b.validate_smem, st);
+    if (err != cudaSuccess) return err;
+    k_publish_b<R><<<dim3(1, b.P), kCtaThreads, 0, st>>>(Gs, Ss);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_extract_path_batch(const State<R>* Ss, const BatchShape& b, cudaStream_t st) {
+    k_extract_path_b<R><<<dim3(1, b.P), 1, 0, st>>>(Ss);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_plan_reset_batch<float>(const State<float>*, const BatchShape&, const int*, cudaStream_t);
+template cudaError_t launch_iteration_batch<float>(const Geom<float>*, const State<float>*, const BatchShape&,
+                                                   cudaStream_t);
+template cudaError_t launch_extract_path_batch<float>(const State<float>*, const BatchShape&, cudaStream_t);
 
 template cudaError_t launch_plan_reset<float>(const Geom<float>&, const State<float>&, int, cudaStream_t);
 template cudaError_t launch_plan_reset<double>(const Geom<double>&, const State<double>&, int, cudaStream_t);

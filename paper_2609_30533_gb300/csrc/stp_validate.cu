@@ -273,9 +273,10 @@ __device__ __forceinline__ int block_scan_excl(int v, int* sh, int* total) {
 // Edges per shared-memory window in the large-batch mode.
 constexpr int kWin = 256;
 
+// Kernel body: G and E may live in registers/parameters (single problem) or in
+// shared memory (batch); smem_raw is the dynamic shared-memory buffer.
 template <typename R, bool ARM, int MO, bool CLEAR, bool EARLY>
-__global__ void __launch_bounds__(256, (sizeof(R) == 4 && MO <= 16) ? 2 : 1) k_validate(Geom<R> G, EdgeBatch<R> E) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void validate_body(const Geom<R>& G, const EdgeBatch<R>& E, unsigned char* smem_raw) {
     __shared__ __align__(8) uint64_t bar;
     __shared__ int scan_sh[32];
     R* sm = reinterpret_cast<R*>(smem_raw);
@@ -394,6 +395,27 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 && MO <= 16) ? 2 : 1) k_v
     }
 }
 
+template <typename R, bool ARM, int MO, bool CLEAR, bool EARLY>
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && MO <= 16) ? 2 : 1) k_validate(Geom<R> G, EdgeBatch<R> E) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    validate_body<R, ARM, MO, CLEAR, EARLY>(G, E, smem_raw);
+}
+
+// Batched planner form: problem blockIdx.y; its geometry and state are staged
+// in shared memory, its extension (which = 0) or bridge (which = 1) edge
+// entries are validated; arm vs point robot is chosen per problem.
+template <typename R, int MO>
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && MO <= 16) ? 2 : 1)
+    k_validate_batch(const Geom<R>* __restrict__ Gs, const State<R>* __restrict__ Ss, int which) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Geom<R> G;
+    __shared__ State<R> S;
+    stage_problem(Gs, Ss, blockIdx.y, G, S);
+    const EdgeBatch<R> E = which == 0 ? ext_batch(S) : bridge_batch(S);
+    if (G.arm) validate_body<R, true, MO, false, true>(G, E, smem_raw);
+    else validate_body<R, false, MO, false, true>(G, E, smem_raw);
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
@@ -452,6 +474,31 @@ cudaError_t launch_validate(const Geom<R>& g, const EdgeBatch<R>& e, bool cleara
     if (early_exit) return launch_mo<R, false, false, true>(g, e, grid_blocks, st);
     return launch_mo<R, false, false, false>(g, e, grid_blocks, st);
 }
+
+template <typename R, int MO>
+static cudaError_t launch_vb(const Geom<R>* Gs, const State<R>* Ss, int P, int which, int ctas_per_problem,
+                             int smem_bytes, cudaStream_t st) {
+    auto kern = k_validate_batch<R, MO>;
+    static int configured = -1;
+    if (smem_bytes > configured) {
+        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (err != cudaSuccess) return err;
+        configured = smem_bytes;
+    }
+    if (P <= 0) return cudaSuccess;  // configuration only
+    kern<<<dim3(ctas_per_problem, P), 256, smem_bytes, st>>>(Gs, Ss, which);
+    return cudaGetLastError();
+}
+
+// P <= 0 only sets the kernel's shared-memory attribute (nothing is launched).
+template <typename R>
+cudaError_t launch_validate_batch(const Geom<R>* Gs, const State<R>* Ss, int P, int which, int max_obs,
+                                  int ctas_per_problem, int smem_bytes, cudaStream_t st) {
+    if (max_obs <= 8) return launch_vb<R, 8>(Gs, Ss, P, which, ctas_per_problem, smem_bytes, st);
+    return launch_vb<R, 16>(Gs, Ss, P, which, ctas_per_problem, smem_bytes, st);
+}
+template cudaError_t launch_validate_batch<float>(const Geom<float>*, const State<float>*, int, int, int, int, int,
+                                                  cudaStream_t);
 
 // Check-point counts, c = max(1, ceil(max(D, v_max |dt|) / res - 1e-3)),
 // evaluated in double from the stored endpoints.

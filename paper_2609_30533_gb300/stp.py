@@ -54,6 +54,10 @@ class StpStats(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class StpBatchParams(C.Structure):
+    _fields_ = [("nn_ctas", C.c_int), ("validate_ctas", C.c_int), ("iters_per_graph", C.c_int)]
+
+
 class StpError(RuntimeError):
     def __init__(self, status, where, detail=""):
         self.status = status
@@ -93,6 +97,14 @@ def lib():
     L.stp_check_edges_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_void_p]
     L.stp_check_edges_noalloc.restype = C.c_int
+    L.stp_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(StpBatchParams), C.POINTER(C.c_void_p)]
+    L.stp_batch_create.restype = C.c_int
+    L.stp_batch_plan.argtypes = [C.c_void_p, C.POINTER(StpStats), _D]
+    L.stp_batch_plan.restype = C.c_int
+    L.stp_batch_path.argtypes = [C.c_void_p, C.c_int, _D, C.c_int, _I]
+    L.stp_batch_path.restype = C.c_int
+    L.stp_batch_free.argtypes = [C.c_void_p]
+    L.stp_batch_free.restype = None
     L.stp_set_profiling.argtypes = [C.c_void_p, C.c_int]
     L.stp_set_profiling.restype = C.c_int
     L.stp_profile.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), _D, C.POINTER(C.c_longlong), _I]
@@ -114,7 +126,7 @@ def lib():
 EXPORTED = ["stp_create_problem", "stp_plan", "stp_check_edges", "stp_free", "stp_set_stream",
             "stp_status_string", "stp_last_error", "stp_last_validate", "stp_set_profiling", "stp_profile",
             "stp_tree_size", "stp_tree_nodes", "stp_history", "stp_slots", "stp_goal_grid",
-            "stp_check_edges_noalloc"]
+            "stp_check_edges_noalloc", "stp_batch_create", "stp_batch_plan", "stp_batch_path", "stp_batch_free"]
 
 
 def status_string(s: int) -> str:
@@ -323,3 +335,49 @@ def problem_from(prob, params, **over) -> Problem:
     return Problem(dof=prob.dof, arm=prob.arm, dh=prob.dh, q_lo=prob.qlo, q_hi=prob.qhi, spheres=prob.spheres,
                    v_max=prob.vmax, obs_radius=prob.obs_r, obs_way=prob.way, q_start=prob.qs, q_goal=prob.qg,
                    **kw)
+
+
+class Batch:
+    """Many FP32 problems planned together (stp_batch_*). The problems must stay
+    alive while the batch exists."""
+
+    def __init__(self, problems, nn_ctas=0, validate_ctas=0, iters_per_graph=0):
+        L = lib()
+        self.problems = list(problems)
+        arr = (C.c_void_p * len(self.problems))(*[p.handle.value for p in self.problems])
+        bp = StpBatchParams(int(nn_ctas), int(validate_ctas), int(iters_per_graph))
+        h = C.c_void_p()
+        s = L.stp_batch_create(arr, len(self.problems), C.byref(bp), C.byref(h))
+        if s != STP_OK:
+            raise StpError(s, "stp_batch_create", L.stp_last_error(None).decode())
+        self.handle = h
+
+    def plan(self):
+        """Returns (batch_ms, [stats dict per problem])."""
+        n = len(self.problems)
+        st = (StpStats * n)()
+        ms = C.c_double()
+        s = lib().stp_batch_plan(self.handle, st, C.byref(ms))
+        if s != STP_OK:
+            raise StpError(s, "stp_batch_plan", lib().stp_last_error(None).decode())
+        return ms.value, [st[i].as_dict() for i in range(n)]
+
+    def path(self, i, cap=1 << 16):
+        dof = self.problems[i].dof
+        buf = np.zeros((cap, dof + 1))
+        n = C.c_int()
+        s = lib().stp_batch_path(self.handle, int(i), _dp(buf), cap, C.byref(n))
+        if s != STP_OK:
+            raise StpError(s, "stp_batch_path")
+        return buf[:n.value].copy()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().stp_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

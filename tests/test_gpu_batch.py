@@ -1,0 +1,92 @@
+"""Batched planning (many problems in one launch sequence) through the C ABI.
+
+Batching must not change any result: every problem's trees, incumbent and
+statistics from a batch equal those of its single-problem FP32 run (the same
+kernels over a problem grid dimension; the per-pair arithmetic and the NN keys
+do not depend on the batch's chunk width or coordinate padding).
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2609_30533_gb300 import build as B
+    B.build()
+
+
+def _cases():
+    out = []
+    p, q = WL.disc2d(0)
+    out.append((p, dataclasses.replace(q, max_iters=60)))
+    p, q = WL.disc2d(3)
+    out.append((p, dataclasses.replace(q, variant=1, eta=0.05, max_iters=40)))
+    p, q = WL.ur5e(0, n_obs=4, candidate=0)
+    p.qg = p.qs + np.array([0.6, -0.4, 0.5, 0.3, -0.2, 0.4])
+    out.append((p, dataclasses.replace(q, workers=64, max_iters=30)))
+    p, q = WL.ur5e(1)
+    out.append((p, dataclasses.replace(q, workers=256, max_iters=12)))
+    p, q = WL.arm7(0, variant=0)
+    out.append((p, dataclasses.replace(q, workers=96, max_iters=6)))
+    p, q = WL.ur5e(2, n_obs=8)
+    out.append((p, dataclasses.replace(q, workers=512, max_iters=20)))
+    # degenerate members: start == goal, and a start inside an obstacle
+    p, q = WL.disc2d(1)
+    p.qg = p.qs.copy()
+    out.append((p, q))
+    p, q = WL.disc2d(2)
+    p.qs = p.way[0, 0, 1:3].copy()
+    out.append((p, q))
+    return out
+
+
+def _trees(P, n_roots):
+    return [P.tree(a) for a in range(-1, n_roots)]
+
+
+def test_batch_equals_single_problem_runs():
+    from paper_2609_30533_gb300 import stp
+    cases = _cases()
+    probs = [stp.problem_from(p, q, precision=0, iters_per_graph=8) for p, q in cases]
+    single = []
+    for P, (p, q) in zip(probs, cases):
+        out = P.plan()
+        single.append((out, _trees(P, q.n_roots) if out.stats["iterations"] else None, P.history()))
+    B = stp.Batch(probs, iters_per_graph=8)
+    for rep in range(2):       # two batch runs in a row give the same answer
+        ms, stats = B.plan()
+        assert ms > 0
+        for i, (P, (p, q)) in enumerate(zip(probs, cases)):
+            out, trees, hist = single[i]
+            st = stats[i]
+            for k in ("iterations", "first_solution_iter", "nodes", "edges_validated", "bridges_validated",
+                      "root_checks", "check_points"):
+                assert st[k] == out.stats[k], (i, k, st[k], out.stats[k])
+            assert st["U"] == out.U or (np.isinf(st["U"]) and np.isinf(out.U))
+            if trees is not None:
+                for a, t in zip(range(-1, q.n_roots), trees):
+                    g = P.tree(a)
+                    for f in ("x", "parent", "troot", "cost", "tree", "iter"):
+                        assert np.array_equal(g[f], t[f]), (i, a, f)
+                assert np.array_equal(P.history(), hist)
+            path = B.path(i)
+            assert np.array_equal(path, out.path), i
+    B.close()
+    for P in probs:
+        P.close()
+
+
+def test_batch_rejects_fp64_members():
+    from paper_2609_30533_gb300 import stp
+    p, q = WL.disc2d(0)
+    P = stp.problem_from(p, q, precision=1, max_iters=2)
+    with pytest.raises(stp.StpError) as e:
+        stp.Batch([P])
+    assert e.value.status == stp.STP_ERR_INVALID
+    P.close()
