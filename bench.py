@@ -223,8 +223,8 @@ def batched(args, rank):
         return out
 
     sample = list(range(48))
-    choice = autotune.autotune(lambda W: make(sample, W, args.tune_iters), workers=(256, 512),
-                               nn_ctas=(4, 8), validate_ctas=(1, 2))
+    choice = autotune.autotune(lambda W: make(sample, W, args.tune_iters), workers=(128, 256, 512),
+                               nn_ctas=(2, 4, 8), validate_ctas=(2, 4, 8))
     idx = list(range(args.batch_problems))
     probs = make(idx, choice.workers, args.batch_iters)
     B = stp.Batch(probs, nn_ctas=choice.nn_ctas, validate_ctas=choice.validate_ctas, iters_per_graph=16)

@@ -127,8 +127,9 @@ typedef struct {
     long long edges_validated;    /* extension edges sent to edge validation */
     long long bridges_validated;  /* bridge edges sent to edge validation */
     long long root_checks;        /* sampled goal roots checked (interval root) */
-    long long check_points;       /* check points of all validated edges */
-    long long pair_tests;         /* robot-sphere / obstacle pair tests executed */
+    long long check_points;       /* check points evaluated (work counter: with early exit it
+                                     depends on scheduling, not only on the inputs) */
+    long long pair_tests;         /* robot-sphere / obstacle pair tests executed (same caveat) */
     double first_solution_ms;     /* device time from plan start to the first solution */
     double plan_ms;               /* device time of the whole plan */
     double U;
