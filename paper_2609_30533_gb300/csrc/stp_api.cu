@@ -118,7 +118,7 @@ double host_dist(const double* a, const double* b, int d) {
 
 template <typename R>
 void fill_geom(stp_problem* p, Geom<R>& g, const R* blob, unsigned blob_bytes, int off_way, int off_vel,
-               int off_rad, const std::vector<int>& link_start) {
+               int off_rad, int off_tim, const std::vector<int>& link_start) {
     std::memset(&g, 0, sizeof(g));
     g.dof = p->dof;
     g.arm = p->arm;
@@ -145,17 +145,21 @@ void fill_geom(stp_problem* p, Geom<R>& g, const R* blob, unsigned blob_bytes, i
     for (int i = 0; i < 3; ++i) g.ref[i] = R(0);
     if (!p->arm)
         for (int i = 0; i < 3 && i < p->dof; ++i) g.ref[i] = (R)(0.5 * (p->qlo[i] + p->qhi[i]));
-    g.uniform_r = 0;
+    g.uniform_ro = 1;
+    for (int m = 1; m < p->M; ++m)
+        if (p->obs_r[m] != p->obs_r[0]) g.uniform_ro = 0;
+    g.ro_uni = p->M > 0 ? (R)p->obs_r[0] : R(0);
     g.blob = blob;
     g.blob_bytes = blob_bytes;
     g.off_way = off_way;
     g.off_vel = off_vel;
     g.off_rad = off_rad;
+    g.off_tim = off_tim;
 }
 
 // Sizes and layout of the geometry blob in R units; returns bytes.
 template <typename R>
-size_t blob_layout(const stp_problem* p, int* off_way, int* off_vel, int* off_rad) {
+size_t blob_layout(const stp_problem* p, int* off_way, int* off_vel, int* off_rad, int* off_tim) {
     size_t n = 4 * (size_t)p->S;
     *off_way = (int)n;
     n += 4 * (size_t)p->M * p->K;
@@ -163,13 +167,15 @@ size_t blob_layout(const stp_problem* p, int* off_way, int* off_vel, int* off_ra
     n += 4 * (size_t)p->M * p->K;
     *off_rad = (int)n;
     n += align_up((size_t)p->M, 4);
+    *off_tim = (int)n;
+    n += (size_t)kMaxWay * p->M;
     if (n == 0) n = 4;
     return align_up(n * sizeof(R), 16);
 }
 
 template <typename R>
 std::vector<R> blob_host(const stp_problem* p, const std::vector<int>& order, size_t bytes, int off_way,
-                         int off_vel, int off_rad) {
+                         int off_vel, int off_rad, int off_tim) {
     std::vector<R> b(bytes / sizeof(R), R(0));
     for (int s = 0; s < p->S; ++s) {
         const double* sp = &p->sph[5 * order[s]];
@@ -188,6 +194,9 @@ std::vector<R> blob_host(const stp_problem* p, const std::vector<int>& order, si
             for (int i = 0; i < 3; ++i) b[off_vel + ((size_t)m * p->K + k) * 4 + i] = (R)v[i];
         }
         b[off_rad + m] = (R)p->obs_r[m];
+        for (int k = 1; k <= kMaxWay; ++k)
+            b[off_tim + (size_t)m * kMaxWay + k - 1] =
+                k < p->K ? (R)p->way[((size_t)m * p->K + k) * 4] : std::numeric_limits<R>::infinity();
     }
     return b;
 }
@@ -333,8 +342,8 @@ stp_status create_impl(stp_problem* p) {
         }
         link_start[nf] = p->S;
     }
-    int off_way, off_vel, off_rad;
-    const size_t blob_bytes = blob_layout<R>(p, &off_way, &off_vel, &off_rad);
+    int off_way, off_vel, off_rad, off_tim;
+    const size_t blob_bytes = blob_layout<R>(p, &off_way, &off_vel, &off_rad, &off_tim);
     R* blob;
     unsigned char* gfree;
     Ctl* ctl;
@@ -347,10 +356,10 @@ stp_status create_impl(stp_problem* p) {
     p->arena_bytes = bytes;
     layout_state<R>(p, p->d_arena, &blob, blob_bytes, &gfree, &ctl, &qdev, &tdev, &cnt, &off, &hit);
     p->d_ctl = ctl;
-    fill_geom<R>(p, geom_of<R>(p), blob, (unsigned)blob_bytes, off_way, off_vel, off_rad, link_start);
+    fill_geom<R>(p, geom_of<R>(p), blob, (unsigned)blob_bytes, off_way, off_vel, off_rad, off_tim, link_start);
     State<R>& S = state_of<R>(p);
     cudaStream_t st = p->stream;
-    std::vector<R> hb = blob_host<R>(p, order, blob_bytes, off_way, off_vel, off_rad);
+    std::vector<R> hb = blob_host<R>(p, order, blob_bytes, off_way, off_vel, off_rad, off_tim);
     STP_CUDA(p, cudaMemcpyAsync(blob, hb.data(), blob_bytes, cudaMemcpyHostToDevice, st));
     STP_CUDA(p, cudaMemsetAsync(S.tile_cnt, 0, sizeof(int) * (size_t)(p->prm.n_roots + 1) * kMaxQTiles, st));
     STP_CUDA(p, cudaMemsetAsync(S.btile_cnt, 0, sizeof(int) * 2 * kMaxQTiles, st));

@@ -3,7 +3,8 @@
 // Data layout in HBM (one problem):
 //   geometry blob  spheres [S][4] (x,y,z,r; sorted by frame), waypoints
 //                  [M][K][4] (t,x,y,z), segment velocities [M][K][4], radii [M]
-//                  (padded to 4); staged into shared memory by one TMA bulk copy
+//                  (padded to 4), waypoint times [M][8] (t_1..t_{K-1}, +inf
+//                  padded); staged into shared memory by one TMA bulk copy
 //                  per CTA in the collision kernel.
 //   forward arena  SoA: x [cap_f][DP] (q..., zero pad, t at DP-1), parent, cost, iter.
 //   backward arena N segments of cap_s nodes, same SoA plus troot and tree.
@@ -46,10 +47,11 @@ struct Geom {
     R vmax;
     R ref[3];       // reference point subtracted from workspace positions in pair tests
     double vmax_d;  // v_max as given (edge check counts are evaluated in double)
-    int uniform_r;  // all robot spheres share one radius
+    int uniform_ro;  // every obstacle has the radius ro_uni
+    R ro_uni;
     const R* blob;
     unsigned blob_bytes;
-    int off_way, off_vel, off_rad;  // offsets in R units inside the blob
+    int off_way, off_vel, off_rad, off_tim;  // offsets in R units inside the blob
 };
 
 // Flat batch of edges for the collision kernel. Entry e covers check points

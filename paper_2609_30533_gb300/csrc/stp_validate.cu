@@ -24,9 +24,12 @@
 // and an obstacle (o, r_o) collide iff |c - o|^2 - (r_s + r_o)^2 < 0, i.e.
 //   B_o + (-2 o).c + (-2 r_o) r_s  <  r_s^2 - |c|^2,   B_o = |o|^2 - r_o^2,
 // which is four FMAs per pair against per-obstacle terms computed once per
-// check point, plus one min per pair. Positions are O(1 m) relative to the
-// reference, so the FP32 cancellation error near contact is about 1e-6 m; the
-// clearance variant keeps the direct form |c - o| - r_s - r_o.
+// check point, plus one min per pair. In FP32 two pairs share each packed FMA
+// (fma.rn.f32x2) and one three-input min; when all obstacles have one radius
+// the r_s r_o term joins the per-sphere threshold and a pair costs three FMAs.
+// Positions are O(1 m) relative to the reference, so the FP32 cancellation
+// error near contact is about 1e-6 m; the clearance variant keeps the direct
+// form |c - o| - r_s - r_o.
 #include "stp_internal.cuh"
 
 namespace stp {
@@ -57,31 +60,8 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
     return d;
 }
 
-template <int MO>
-__device__ __forceinline__ bool sphere_hits_x2(float cx, float cy, float cz, float rs, const ObsTerms<float, MO>& O) {
-    const float negA = rs * rs - (cx * cx + cy * cy + cz * cz);
-    const unsigned long long CX = pk2(cx, cx), CY = pk2(cy, cy), CZ = pk2(cz, cz), RS = pk2(rs, rs);
-    float m0 = rinf<float>(), m1 = rinf<float>();
-#pragma unroll
-    for (int j = 0; j < MO; j += 2) {
-        unsigned long long a = pk2(O.B[j], O.B[j + 1]);
-        a = ffma2(CX, pk2(O.ox[j], O.ox[j + 1]), a);
-        a = ffma2(CY, pk2(O.oy[j], O.oy[j + 1]), a);
-        a = ffma2(CZ, pk2(O.oz[j], O.oz[j + 1]), a);
-        a = ffma2(RS, pk2(O.ro[j], O.ro[j + 1]), a);
-        float lo, hi;
-        upk2(a, lo, hi);
-        m0 = fminf(m0, lo);
-        m1 = fminf(m1, hi);
-    }
-    return fminf(m0, m1) < negA;
-}
-
 template <typename R, int MO>
 __device__ __forceinline__ bool sphere_hits(R cx, R cy, R cz, R rs, const ObsTerms<R, MO>& O) {
-    if constexpr (sizeof(R) == 4 && MO % 2 == 0) {
-        return sphere_hits_x2<MO>(cx, cy, cz, rs, O);
-    }
     const R negA = rs * rs - (cx * cx + cy * cy + cz * cz);
     R m0 = rinf<R>(), m1 = rinf<R>();
 #pragma unroll
@@ -181,11 +161,140 @@ __device__ __forceinline__ void check_point_fast(const Geom<R>& G, const R* sm, 
     }
 }
 
+// FP32 verdict path. Obstacle position at time t from the shared-memory
+// tables: the segment index is the number of waypoint times t_1..t_{K-1} not
+// after max(t, t_0) (times are strictly increasing; the table is +inf padded),
+// then one waypoint and one velocity record are read as float4.
+__device__ __forceinline__ void obstacle_at_f32(const float4* way, const float4* vel, const float4* tim, int K,
+                                                float t, float& x, float& y, float& z) {
+    const float tc = fmaxf(t, way[0].x);
+    const float4 ta = tim[0];
+    int k = (ta.x <= tc) + (ta.y <= tc) + (ta.z <= tc) + (ta.w <= tc);
+    if (K > 5) {
+        const float4 tb = tim[1];
+        k += (tb.x <= tc) + (tb.y <= tc) + (tb.z <= tc) + (tb.w <= tc);
+    }
+    const float4 w = way[k];
+    const float4 v = vel[k];
+    const float dtk = tc - w.x;
+    x = fmaf(dtk, v.x, w.y);
+    y = fmaf(dtk, v.y, w.z);
+    z = fmaf(dtk, v.z, w.w);
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Packed obstacle terms of one chunk: lanes (2h, 2h+1) of obstacle pairs.
+template <int MO>
+struct ObsPacked {
+    unsigned long long ox[MO / 2], oy[MO / 2], oz[MO / 2], ro[MO / 2], B[MO / 2];
+};
+
+// One robot sphere against a chunk: packed FMAs build
+//   B_o + (-2 o).c [+ (-2 r_o) r_s]
+// for two obstacles per instruction, three-input mins reduce them. With one
+// obstacle radius R_o for all obstacles (UNI) the r_s r_o cross term is
+// per-sphere and moves into the threshold r_s (r_s + 2 R_o) - |c|^2.
+template <int MO, bool UNI>
+__device__ __forceinline__ bool sphere_hits_packed(float cx, float cy, float cz, float rs, float ro_uni,
+                                                   const ObsPacked<MO>& O) {
+    const float thr = rs * (UNI ? rs + 2.f * ro_uni : rs) - (cx * cx + cy * cy + cz * cz);
+    const unsigned long long CX = pk2(cx, cx), CY = pk2(cy, cy), CZ = pk2(cz, cz);
+    const unsigned long long RS = UNI ? 0ull : pk2(rs, rs);
+    float m0 = rinf<float>(), m1 = rinf<float>();
+#pragma unroll
+    for (int h = 0; h < MO / 2; ++h) {
+        unsigned long long a = ffma2(CX, O.ox[h], O.B[h]);
+        a = ffma2(CY, O.oy[h], a);
+        a = ffma2(CZ, O.oz[h], a);
+        if (!UNI) a = ffma2(RS, O.ro[h], a);
+        float lo, hi;
+        upk2(a, lo, hi);
+        if (h & 1) m1 = min3f(m1, lo, hi);
+        else m0 = min3f(m0, lo, hi);
+    }
+    return fminf(m0, m1) < thr;
+}
+
+template <bool ARM, int MO, bool EARLY, bool UNI>
+__device__ __forceinline__ void check_point_f32(const Geom<float>& G, const float* sm, const float (&q)[kMaxDof],
+                                                float t, bool& hit, unsigned& pairs) {
+    const float4* sph = reinterpret_cast<const float4*>(sm);
+    const float4* way = reinterpret_cast<const float4*>(sm + G.off_way);
+    const float4* vel = reinterpret_cast<const float4*>(sm + G.off_vel);
+    const float4* tim = reinterpret_cast<const float4*>(sm + G.off_tim);
+    const float* rad = sm + G.off_rad;
+    const float ro_uni = G.ro_uni;
+    for (int m0 = 0; m0 < G.M; m0 += MO) {
+        ObsPacked<MO> O;
+#pragma unroll
+        for (int h = 0; h < MO / 2; ++h) {
+            float x[2], y[2], z[2], r[2], b[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int m = m0 + 2 * h + u;
+                if (m < G.M) {
+                    obstacle_at_f32(way + G.K * m, vel + G.K * m, tim + 2 * m, G.K, t, x[u], y[u], z[u]);
+                    x[u] -= G.ref[0];
+                    y[u] -= G.ref[1];
+                    z[u] -= G.ref[2];
+                    r[u] = UNI ? ro_uni : rad[m];
+                    b[u] = x[u] * x[u] + y[u] * y[u] + z[u] * z[u] - r[u] * r[u];
+                } else {
+                    x[u] = y[u] = z[u] = r[u] = 0.f;
+                    b[u] = 1e30f;
+                }
+            }
+            O.ox[h] = pk2(-2.f * x[0], -2.f * x[1]);
+            O.oy[h] = pk2(-2.f * y[0], -2.f * y[1]);
+            O.oz[h] = pk2(-2.f * z[0], -2.f * z[1]);
+            O.ro[h] = pk2(-2.f * r[0], -2.f * r[1]);
+            O.B[h] = pk2(b[0], b[1]);
+        }
+        const unsigned real = (unsigned)min(MO, G.M - m0);
+        if (!ARM) {
+            const float px = q[0] - G.ref[0], py = q[1] - G.ref[1], pz = ((G.dof > 2) ? q[2] : 0.f) - G.ref[2];
+            for (int s = 0; s < G.S; ++s) {
+                const float4 sp = sph[s];
+                if (sphere_hits_packed<MO, UNI>(px + sp.x, py + sp.y, pz + sp.z, sp.w, ro_uni, O)) hit = true;
+            }
+            pairs += real * (unsigned)G.S;
+        } else {
+            Frame<float> F;
+            frame_identity(F);
+            for (int j = 0; j <= G.dof; ++j) {
+                if (j > 0) frame_step(F, G.a[j - 1], G.d[j - 1], G.ca[j - 1], G.sa[j - 1], q[j - 1] + G.th0[j - 1]);
+                const float ox = F.o[0] - G.ref[0], oy = F.o[1] - G.ref[1], oz = F.o[2] - G.ref[2];
+                const int s0 = G.link_start[j], s1 = G.link_start[j + 1];
+                for (int s = s0; s < s1; ++s) {
+                    const float4 sp = sph[s];
+                    const float cx = ox + sp.x * F.X[0] + sp.y * F.Y[0] + sp.z * F.Z[0];
+                    const float cy = oy + sp.x * F.X[1] + sp.y * F.Y[1] + sp.z * F.Z[1];
+                    const float cz = oz + sp.x * F.X[2] + sp.y * F.Y[2] + sp.z * F.Z[2];
+                    if (sphere_hits_packed<MO, UNI>(cx, cy, cz, sp.w, ro_uni, O)) hit = true;
+                }
+                pairs += real * (unsigned)(s1 - s0);
+                if (EARLY && hit) break;
+            }
+        }
+        if (EARLY && hit) break;
+    }
+}
+
 template <typename R, bool ARM, int MO, bool CLEAR, bool EARLY>
 __device__ __forceinline__ void check_point(const Geom<R>& G, const R* sm, const R (&q)[kMaxDof], R t, bool& hit,
                                             R& clr, unsigned& pairs) {
     if (!CLEAR) {
-        check_point_fast<R, ARM, MO, EARLY>(G, sm, q, t, hit, pairs);
+        if constexpr (sizeof(R) == 4 && MO % 2 == 0) {
+            if (G.uniform_ro) check_point_f32<ARM, MO, EARLY, true>(G, sm, q, t, hit, pairs);
+            else check_point_f32<ARM, MO, EARLY, false>(G, sm, q, t, hit, pairs);
+        } else {
+            check_point_fast<R, ARM, MO, EARLY>(G, sm, q, t, hit, pairs);
+        }
         return;
     }
     const R* sph = sm;
