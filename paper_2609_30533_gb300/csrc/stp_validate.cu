@@ -270,12 +270,26 @@ __device__ __forceinline__ void check_point_f32(const Geom<float>& G, const floa
                 if (j > 0) frame_step(F, G.a[j - 1], G.d[j - 1], G.ca[j - 1], G.sa[j - 1], q[j - 1] + G.th0[j - 1]);
                 const float ox = F.o[0] - G.ref[0], oy = F.o[1] - G.ref[1], oz = F.o[2] - G.ref[2];
                 const int s0 = G.link_start[j], s1 = G.link_start[j + 1];
-                for (int s = s0; s < s1; ++s) {
+                int s = s0;
+                for (; s + 1 < s1; s += 2) {
+                    const float4 sp = sph[s];
+                    const float4 sq = sph[s + 1];
+                    const float cx = ox + sp.x * F.X[0] + sp.y * F.Y[0] + sp.z * F.Z[0];
+                    const float cy = oy + sp.x * F.X[1] + sp.y * F.Y[1] + sp.z * F.Z[1];
+                    const float cz = oz + sp.x * F.X[2] + sp.y * F.Y[2] + sp.z * F.Z[2];
+                    const float dx = ox + sq.x * F.X[0] + sq.y * F.Y[0] + sq.z * F.Z[0];
+                    const float dy = oy + sq.x * F.X[1] + sq.y * F.Y[1] + sq.z * F.Z[1];
+                    const float dz = oz + sq.x * F.X[2] + sq.y * F.Y[2] + sq.z * F.Z[2];
+                    const bool h0 = sphere_hits_packed<MO, UNI>(cx, cy, cz, sp.w, ro_uni, O);
+                    const bool h1 = sphere_hits_packed<MO, UNI>(dx, dy, dz, sq.w, ro_uni, O);
+                    hit = hit | h0 | h1;
+                }
+                if (s < s1) {
                     const float4 sp = sph[s];
                     const float cx = ox + sp.x * F.X[0] + sp.y * F.Y[0] + sp.z * F.Z[0];
                     const float cy = oy + sp.x * F.X[1] + sp.y * F.Y[1] + sp.z * F.Z[1];
                     const float cz = oz + sp.x * F.X[2] + sp.y * F.Y[2] + sp.z * F.Z[2];
-                    if (sphere_hits_packed<MO, UNI>(cx, cy, cz, sp.w, ro_uni, O)) hit = true;
+                    hit = hit | sphere_hits_packed<MO, UNI>(cx, cy, cz, sp.w, ro_uni, O);
                 }
                 pairs += real * (unsigned)(s1 - s0);
                 if (EARLY && hit) break;
