@@ -272,6 +272,60 @@ stp_status stp_slots(stp_problem *p, double *T, int *has_root, int *active, int 
 /* Goal-time grid checks k = kmin..kmin+n-1 (free flags [cap]). */
 stp_status stp_goal_grid(stp_problem *p, long *kmin, int *n, unsigned char *free_flags, int cap);
 
+/* ---- Learned proposal network --------------------------------------------
+ * The learned sampling branch of the method's GPU form: a 4-layer MLP of
+ * width 256 (BF16 weights, FP32 accumulation on the tensor cores) maps a
+ * problem summary x[STP_MLP_IN] to y[STP_MLP_OUT]: a mixture of 8 Gaussians
+ * over the normalised arrival time tau = U/H (logits y[0:8], means y[8:16],
+ * log standard deviations y[16:24], clamped to [-7, 2]) and 16 waypoints
+ * (y[24 + 8 i + j]: joint j < 7 normalised to [-1, 1] over the joint box,
+ * j = 7 the waypoint time over H); y[152:160] is padding.
+ *   x layout: q_s (7, normalised, zero padded), q_g (7), DOF one-hot (3: d = 2,
+ *   6, 7), mean over obstacles of (first waypoint x, y, z, mean velocity x, y, z,
+ *   radius) (7), H / 60, L_g / H with L_g = D(q_s, q_g) / v_max (2), zeros (6).
+ *   Training targets t[STP_MLP_NTGT]: tau, 16 x 8 waypoint targets (same layout
+ *   as the outputs), d. Loss per sample: mixture negative log-likelihood of tau
+ *   plus the mean squared waypoint error over joints j < d and the time entry;
+ *   the batch loss is the mean over samples. Optimiser: Adam (beta 0.9, 0.999,
+ *   eps 1e-8) on FP32 master weights.
+ * Parameters travel as STP_MLP_NPARAM floats in the order W1 [256][32], b1
+ * [256], W2 [256][256], b2, W3 [256][256], b3, W4 [160][256], b4 [160]
+ * (row-major, W maps inputs to outputs as y = W x + b); W4 rows 152..159 and
+ * b4[152..159] must be zero.
+ * Pointers are host memory unless flags has STP_MLP_DEVICE (device memory).
+ * Every call is stream-ordered on the network's stream and returns after its
+ * results are available. Errors: STP_ERR_INVALID for NULL or out-of-range
+ * arguments, STP_ERR_CUDA for a CUDA failure, STP_ERR_TIMEOUT if a bounded
+ * wait inside a tensor-core kernel ran out (results are then undefined). */
+#define STP_MLP_IN 32
+#define STP_MLP_OUT 160
+#define STP_MLP_NTGT 130
+#define STP_MLP_NPARAM 181152
+#define STP_MLP_MAX_BATCH 65536
+#define STP_MLP_DEVICE 1
+typedef struct stp_mlp stp_mlp;
+/* Device state for batches of up to max_batch samples; parameters start at 0. */
+stp_status stp_mlp_create(int max_batch, stp_mlp **out);
+void stp_mlp_free(stp_mlp *m);
+stp_status stp_mlp_set_stream(stp_mlp *m, void *cuda_stream);
+/* Load parameters (host, STP_MLP_NPARAM floats); resets the Adam state. */
+stp_status stp_mlp_set_params(stp_mlp *m, const float *params);
+stp_status stp_mlp_get_params(stp_mlp *m, float *params);
+/* y [B][STP_MLP_OUT] from x [B][STP_MLP_IN]. */
+stp_status stp_mlp_forward(stp_mlp *m, int B, const float *x, float *y, int flags);
+/* Batch loss and its gradient (parameter order above) without an update. */
+stp_status stp_mlp_gradients(stp_mlp *m, int B, const float *x, const float *targets, float *loss,
+                             float *grads, int flags);
+/* One Adam step at learning rate lr on the batch; *loss (may be NULL) gets
+ * the batch loss before the step. */
+stp_status stp_mlp_train_step(stp_mlp *m, int B, const float *x, const float *targets, float lr, float *loss,
+                              int flags);
+/* With profiling on, every tensor-core GEMM is bracketed by CUDA events;
+ * stp_mlp_profile returns (and clears) their total time and FLOPs. */
+stp_status stp_mlp_set_profiling(stp_mlp *m, int on);
+stp_status stp_mlp_profile(stp_mlp *m, double *gemm_ms, double *gemm_flops);
+const char *stp_mlp_last_error(const stp_mlp *m);
+
 #ifdef __cplusplus
 }
 #endif

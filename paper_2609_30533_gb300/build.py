@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libstp.so")
-SOURCES = ["stp_validate.cu", "stp_planner.cu", "stp_api.cu"]
+SOURCES = ["stp_validate.cu", "stp_planner.cu", "stp_api.cu", "stp_mlp.cu"]
 HEADERS = ["stp_internal.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

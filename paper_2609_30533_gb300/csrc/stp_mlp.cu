@@ -1,0 +1,898 @@
+// Learned proposal network on the 5th-generation tensor cores (sm_103a).
+//
+// A 4-layer MLP of width 256 (input 32 features padded to 64, output 160
+// padded to 256) maps a problem summary to a mixture over the normalised
+// arrival time and to 16 space-time waypoints (the learned sampling branch of
+// the method's GPU form). Weights are BF16 copies of FP32 master weights; every
+// product accumulates in FP32.
+//
+// GEMM: D[M x N] = A[M x K] . B[N x K]^T with A and B K-major BF16 in the
+// canonical no-swizzle tile order (8-row x 16-byte core matrices), so that a
+// 128-row x 64-column stage of A, and the N x 64 stage of B, are contiguous in
+// HBM and move into shared memory with one bulk asynchronous copy each
+// (cp.async.bulk, completion on an mbarrier). One elected thread issues
+// tcgen05.mma (kind::f16, M = 128, N <= 256, K = 16 per instruction) into a
+// TMEM accumulator of N FP32 columns; tcgen05.commit releases a stage when
+// its MMAs have read it. Four warps read the accumulator back with
+// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows) and run the
+// fused epilogue: bias + ReLU with BF16 stores in both operand layouts
+// (forward), bias only with FP32 stores (output layer), ReLU-mask with BF16
+// and FP32 stores (backward), or FP32 split-K partials (weight gradients).
+//
+// Element (r, k) of a tiled [R][K] matrix (R % 8 == 0, K % 64 == 0) sits at
+//   (((k / 64) * (R / 8) + r / 8) * 8 + (k % 64) / 8) * 64 + (r % 8) * 8 + k % 8.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "stp.h"
+#include "stp_internal.cuh"
+
+namespace stp {
+namespace mlp {
+
+constexpr int kIn = 32, kInP = 64, kHid = 256, kOut = 160, kOutP = 256;
+constexpr int kMix = 8, kWp = 16, kWpDim = 8, kTgt = 130;
+constexpr int kTileM = 128, kStageK = 64, kStages = 4, kThreads = 128;
+constexpr float kSMin = -7.f, kSMax = 2.f;
+constexpr int kColChunk = 256;  // rows per bias-gradient partial
+
+enum Mode { kHidden = 0, kOutput = 1, kBackward = 2, kWGrad = 3 };
+
+__host__ __device__ inline size_t tix(int r, int k, int R) {
+    return ((((size_t)(k >> 6) * (size_t)(R >> 3) + (size_t)(r >> 3)) * 8 + (size_t)((k >> 3) & 7)) << 6) +
+           (size_t)((r & 7) << 3) + (size_t)(k & 7);
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05 / TMEM helpers (inline PTX).
+// ---------------------------------------------------------------------------
+// Shared-memory matrix descriptor: start address, leading-dimension byte
+// offset (between core matrices along K), stride-dimension byte offset
+// (between 8-row groups), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct GemmArgs {
+    const __nv_bfloat16* A;  // tiled [RA][K]
+    int RA;
+    const __nv_bfloat16* B;  // tiled [N][K]
+    int KT;                  // 64-wide K stages in total
+    int kt_per_split;        // split-K (blockIdx.z): stages [z*kps, min(KT, (z+1)*kps))
+    const float* bias;       // [N] (kHidden, kOutput)
+    const __nv_bfloat16* act;  // kBackward: forward activation, tiled [RA][N]
+    __nv_bfloat16* out_t;      // tiled [RA][N]
+    __nv_bfloat16* out_tT;     // tiled [N][RA]
+    float* out_f;              // FP32 row-major
+    int ld_f;
+    int m_valid;               // kWGrad: rows written
+    int* err;
+};
+
+// Output bf16 stores of 16 consecutive columns c0..c0+15 of row r.
+__device__ __forceinline__ void store_row16(__nv_bfloat16* t, __nv_bfloat16* tT, int r, int c0, int R, int N,
+                                            const float (&v)[16]) {
+    if (t) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            __align__(16) __nv_bfloat16 b[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) b[i] = __float2bfloat16_rn(v[8 * h + i]);
+            *reinterpret_cast<uint4*>(t + tix(r, c0 + 8 * h, R)) = *reinterpret_cast<const uint4*>(b);
+        }
+    }
+    if (tT) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) tT[tix(c0 + i, r, N)] = __float2bfloat16_rn(v[i]);
+    }
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
+    constexpr uint32_t kABytes = kTileM * kStageK * 2;  // 16 KB
+    constexpr uint32_t kBBytes = N * kStageK * 2;
+    constexpr uint32_t kTmemCols = N < 32 ? 32 : N;
+    constexpr uint32_t kIdesc = idesc_bf16(kTileM, N);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int fail_sh;
+
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + kStages * kABytes;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * kTileM;
+    const int z = blockIdx.z;
+    const int kt0 = z * g.kt_per_split;
+    const int kt1 = min(g.KT, kt0 + g.kt_per_split);
+    const int nk = kt1 > kt0 ? kt1 - kt0 : 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        fail_sh = 0;
+    }
+    if (warp == 0) tmem_alloc(&tmem_base_sh, kTmemCols);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_base_sh;
+
+    // Producer + MMA issuer: one thread, prefetch distance kStages - 1.
+    if (tid == 0 && nk > 0) {
+        const int rgA = g.RA >> 3;
+        int issued = 0, consumed = 0;
+        bool ok = true;
+        for (int it = 0; it < nk + kStages - 1 && ok; ++it) {
+            if (it < nk) {
+                const int s = it % kStages;
+                if (it >= kStages) ok = mbar_wait(&empty[s], ((it / kStages) - 1) & 1);
+                if (!ok) break;
+                const int kt = kt0 + it;
+                const __nv_bfloat16* srcA = g.A + ((size_t)kt * rgA + (size_t)(m0 >> 3)) * 512;
+                const __nv_bfloat16* srcB = g.B + (size_t)kt * (size_t)(N >> 3) * 512;
+                mbar_expect_tx(&full[s], kABytes + kBBytes);
+                bulk_g2s(sA + s * kABytes, srcA, kABytes, &full[s]);
+                bulk_g2s(sB + s * kBBytes, srcB, kBBytes, &full[s]);
+                ++issued;
+            }
+            const int j = it - (kStages - 1);
+            if (j >= 0) {
+                const int s = j % kStages;
+                ok = mbar_wait(&full[s], (j / kStages) & 1);
+                if (!ok) break;
+                fence_after_sync();
+                const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
+#pragma unroll
+                for (int ks = 0; ks < kStageK / 16; ++ks) {
+                    const uint64_t da = smem_desc(a0 + ks * 256, 128, 1024);
+                    const uint64_t db = smem_desc(b0 + ks * 256, 128, 1024);
+                    mma_bf16(tmem, da, db, kIdesc, (j > 0 || ks > 0) ? 1u : 0u);
+                }
+                mma_commit(&empty[s]);
+                ++consumed;
+            }
+        }
+        // Always close with a commit so that `done` tracks every issued MMA.
+        mma_commit(&done);
+        if (!ok) {
+            fail_sh = 1;
+            if (g.err) atomicOr(g.err, kErrTimeout);
+            // Wait (bounded) for copies still in flight before the CTA exits.
+            for (int j = consumed; j < issued; ++j) mbar_wait(&full[j % kStages], (j / kStages) & 1);
+        }
+    }
+    __syncthreads();
+    bool have = nk > 0;
+    if (have) {
+        if (!mbar_wait(&done, 0)) {
+            if (lane == 0 && g.err) atomicOr(g.err, kErrTimeout);
+            fail_sh = 1;
+        }
+    }
+    fence_after_sync();
+    __syncthreads();
+    if (fail_sh) have = false;
+
+    // Epilogue: thread (warp, lane) owns tile row 32 warp + lane.
+    const int r = m0 + 32 * warp + lane;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        if (have) tmem_ld16(trow + (uint32_t)c0, v);
+        else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        }
+        if (MODE == kHidden) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + g.bias[c0 + i], 0.f);
+            store_row16(g.out_t, g.out_tT, r, c0, g.RA, N, v);
+        } else if (MODE == kOutput) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] += g.bias[c0 + i];
+            float4* o = reinterpret_cast<float4*>(g.out_f + (size_t)r * g.ld_f + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else if (MODE == kBackward) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                __align__(16) __nv_bfloat16 a[8];
+                *reinterpret_cast<uint4*>(a) = *reinterpret_cast<const uint4*>(g.act + tix(r, c0 + 8 * h, g.RA));
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (!(__bfloat162float(a[i]) > 0.f)) v[8 * h + i] = 0.f;
+            }
+            store_row16(g.out_t, g.out_tT, r, c0, g.RA, N, v);
+            float4* o = reinterpret_cast<float4*>(g.out_f + (size_t)r * g.ld_f + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {  // kWGrad
+            if (r < g.m_valid) {
+                float4* o = reinterpret_cast<float4*>(g.out_f + ((size_t)z * g.m_valid + r) * g.ld_f + c0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise kernels.
+// ---------------------------------------------------------------------------
+// FP32 features [B][32] -> BF16 tiled [Bp][64] and [64][Bp] (zero padded).
+__global__ void k_pack_input(const float* __restrict__ X, int B, int Bp, __nv_bfloat16* xt, __nv_bfloat16* xtT) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Bp * kInP) return;
+    const int r = i / kInP, c = i % kInP;
+    const float v = (r < B && c < kIn) ? X[(size_t)r * kIn + c] : 0.f;
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    xt[tix(r, c, Bp)] = b;
+    xtT[tix(c, r, kInP)] = b;
+}
+
+// Per-sample loss (mixture NLL of tau + masked waypoint MSE) and dL/dy / B.
+__global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ T, int B, int Bp, float* dyf,
+                       __nv_bfloat16* dyt, __nv_bfloat16* dytT, float* loss) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= Bp) return;
+    float g[kOutP];
+#pragma unroll 1
+    for (int c = 0; c < kOutP; ++c) g[c] = 0.f;
+    if (n < B) {
+        const float* y = Y + (size_t)n * kOutP;
+        const float* t = T + (size_t)n * kTgt;
+        const float tau = t[0];
+        const int dof = (int)t[kTgt - 1];
+        float amax = -INFINITY;
+        for (int k = 0; k < kMix; ++k) amax = fmaxf(amax, y[k]);
+        float asum = 0.f;
+        for (int k = 0; k < kMix; ++k) asum += expf(y[k] - amax);
+        const float lse_a = amax + logf(asum);
+        float l[kMix], z[kMix], sig[kMix];
+        float lmax = -INFINITY;
+        for (int k = 0; k < kMix; ++k) {
+            const float s = fminf(fmaxf(y[2 * kMix + k], kSMin), kSMax);
+            sig[k] = expf(s);
+            z[k] = (tau - y[kMix + k]) / sig[k];
+            l[k] = (y[k] - lse_a) - 0.5f * z[k] * z[k] - s - 0.91893853320467274f;
+            lmax = fmaxf(lmax, l[k]);
+        }
+        float lsum = 0.f;
+        for (int k = 0; k < kMix; ++k) lsum += expf(l[k] - lmax);
+        const float lse_l = lmax + logf(lsum);
+        float L = -lse_l;
+        const float invB = 1.f / (float)B;
+        for (int k = 0; k < kMix; ++k) {
+            const float gam = expf(l[k] - lse_l);
+            const float pi = expf(y[k] - lse_a);
+            const float sr = y[2 * kMix + k];
+            g[k] = (pi - gam) * invB;
+            g[kMix + k] = -gam * z[k] / sig[k] * invB;
+            g[2 * kMix + k] = (sr >= kSMin && sr <= kSMax) ? gam * (1.f - z[k] * z[k]) * invB : 0.f;
+        }
+        const float cnt = (float)(kWp * (dof + 1));
+        float mse = 0.f;
+        for (int i = 0; i < kWp; ++i) {
+            for (int j = 0; j < kWpDim; ++j) {
+                if (j < dof || j == kWpDim - 1) {
+                    const int o = 3 * kMix + i * kWpDim + j;
+                    const float e = y[o] - t[1 + i * kWpDim + j];
+                    mse += e * e;
+                    g[o] = 2.f * e / cnt * invB;
+                }
+            }
+        }
+        L += mse / cnt;
+        loss[n] = L;
+    }
+    for (int c0 = 0; c0 < kOutP; c0 += 16) {
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = g[c0 + i];
+        store_row16(dyt, dytT, n, c0, Bp, kOutP, v);
+        float4* o = reinterpret_cast<float4*>(dyf + (size_t)n * kOutP + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+}
+
+// Column partial sums of an FP32 row-major [rows][256] matrix over chunks of
+// kColChunk rows: part[chunk][c].
+__global__ void k_colsum(const float* __restrict__ X, int rows, float* part) {
+    const int c = threadIdx.x;
+    const int r0 = blockIdx.x * kColChunk, r1 = min(rows, r0 + kColChunk);
+    float s = 0.f;
+    for (int r = r0; r < r1; ++r) s += X[(size_t)r * kOutP + c];
+    part[(size_t)blockIdx.x * kOutP + c] = s;
+}
+
+struct AdamArgs {
+    float* w;                 // FP32 master [rows][cols] row-major (or bias [rows])
+    float* m;
+    float* v;
+    const float* gpart;       // gradient partials [nparts][rows][cols]
+    int nparts;
+    int rows, cols;
+    int rows_used;            // rows beyond stay zero
+    __nv_bfloat16* wt;        // tiled [rows][cols] (weights only)
+    __nv_bfloat16* wtT;       // tiled [cols][rows] (weights only)
+    float* gout;              // optional: summed gradient [rows][cols]
+    float lr, b1, b2, eps, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
+    int update;               // 0: only sum gradients (and refresh BF16 copies)
+};
+
+__global__ void k_adam(AdamArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = a.rows * a.cols;
+    if (i >= n) return;
+    const int r = i / a.cols, c = i % a.cols;
+    float gsum = 0.f;
+    if (a.gpart)
+        for (int p = 0; p < a.nparts; ++p) gsum += a.gpart[(size_t)p * n + i];
+    if (r >= a.rows_used) gsum = 0.f;
+    if (a.gout) a.gout[i] = gsum;
+    float w = a.w[i];
+    if (a.update && r < a.rows_used) {
+        const float m = a.b1 * a.m[i] + (1.f - a.b1) * gsum;
+        const float v = a.b2 * a.v[i] + (1.f - a.b2) * gsum * gsum;
+        a.m[i] = m;
+        a.v[i] = v;
+        w -= a.lr * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
+        a.w[i] = w;
+    }
+    if (a.wt) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(w);
+        a.wt[tix(r, c, a.rows)] = b;
+        a.wtT[tix(c, r, a.cols)] = b;
+    }
+}
+
+// FP32 [Bp][256] -> user [B][160].
+__global__ void k_unpack_out(const float* __restrict__ Y, int B, float* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * kOut) return;
+    out[i] = Y[(size_t)(i / kOut) * kOutP + i % kOut];
+}
+
+}  // namespace mlp
+}  // namespace stp
+
+// ---------------------------------------------------------------------------
+// Host side and C ABI.
+// ---------------------------------------------------------------------------
+using namespace stp;
+using namespace stp::mlp;
+
+namespace {
+// Logical parameter layout (W1 [256][32], b1, W2 [256][256], b2, W3, b3,
+// W4 [160][256], b4 [160]) against the padded device tensors.
+struct Layer {
+    int out, in, out_used, in_used;  // padded / logical
+};
+constexpr Layer kLayers[4] = {{kHid, kInP, kHid, kIn}, {kHid, kHid, kHid, kHid}, {kHid, kHid, kHid, kHid},
+                              {kOutP, kHid, kOut, kHid}};
+}  // namespace
+
+struct stp_mlp {
+    int max_batch = 0, Bp_max = 0;
+    cudaStream_t stream = nullptr;
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    // parameters
+    float* w[4]{};
+    float* b[4]{};
+    float *mw[4]{}, *vw[4]{}, *mb[4]{}, *vb[4]{};
+    __nv_bfloat16 *wt[4]{}, *wtT[4]{};
+    // activations (tiled BF16 in both layouts), FP32 buffers
+    __nv_bfloat16 *xt = nullptr, *xtT = nullptr;
+    __nv_bfloat16 *ht[3]{}, *htT[3]{};
+    __nv_bfloat16 *dt[4]{}, *dtT[4]{};  // gradient wrt layer outputs (dt[3] = dY)
+    float* y = nullptr;       // [Bp][256]
+    float* df[4]{};           // FP32 gradients wrt layer outputs [Bp][256]
+    float* wpart = nullptr;   // weight-gradient partials
+    float* bpart = nullptr;   // bias-gradient partials
+    float* gsum = nullptr;    // summed gradients (gradients API)
+    float* loss = nullptr;    // [Bp]
+    float* X = nullptr;       // staged inputs [max_batch][32]
+    float* T = nullptr;       // staged targets [max_batch][130]
+    float* Yout = nullptr;    // [max_batch][160]
+    int* err = nullptr;
+    int step = 0;
+    bool profiling = false;
+    cudaEvent_t ev[2]{};
+    double gemm_ms = 0, gemm_flops = 0;
+    std::string last_error;
+};
+
+namespace {
+thread_local std::string g_mlp_err;
+
+stp_status fail(stp_mlp* m, stp_status st, const std::string& msg) {
+    if (m) m->last_error = msg;
+    g_mlp_err = msg;
+    return st;
+}
+#define MLP_CUDA(m, call)                                                               \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) return fail((m), STP_ERR_CUDA, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int kSplitMax = 64;
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <int N, int MODE>
+cudaError_t launch_gemm(const GemmArgs& g, int mtiles, int splits, cudaStream_t st) {
+    constexpr int smem = kStages * (kTileM * kStageK * 2 + N * kStageK * 2) + 1024;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_gemm<N, MODE><<<dim3(mtiles, 1, splits), kThreads, smem, st>>>(g);
+    return cudaGetLastError();
+}
+
+struct Timer {
+    stp_mlp* m;
+    double flops;
+    Timer(stp_mlp* mm, double f) : m(mm), flops(f) {
+        if (m->profiling) cudaEventRecord(m->ev[0], m->stream);
+    }
+    void stop() {
+        if (!m->profiling) return;
+        cudaEventRecord(m->ev[1], m->stream);
+        cudaEventSynchronize(m->ev[1]);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, m->ev[0], m->ev[1]);
+        m->gemm_ms += ms;
+        m->gemm_flops += flops;
+    }
+};
+
+stp_status forward_impl(stp_mlp* m, int B) {
+    const int Bp = (B + kTileM - 1) / kTileM * kTileM;
+    const int mt = Bp / kTileM;
+    cudaStream_t st = m->stream;
+    {
+        const int n = Bp * kInP;
+        k_pack_input<<<(n + 255) / 256, 256, 0, st>>>(m->X, B, Bp, m->xt, m->xtT);
+        MLP_CUDA(m, cudaGetLastError());
+    }
+    const __nv_bfloat16* in = m->xt;
+    for (int l = 0; l < 4; ++l) {
+        GemmArgs g{};
+        g.A = in;
+        g.RA = Bp;
+        g.B = m->wt[l];
+        g.KT = kLayers[l].in / kStageK;
+        g.kt_per_split = g.KT;
+        g.bias = m->b[l];
+        g.err = m->err;
+        Timer t(m, 2.0 * Bp * kLayers[l].in * kLayers[l].out);
+        if (l < 3) {
+            g.out_t = m->ht[l];
+            g.out_tT = m->htT[l];
+            MLP_CUDA(m, (launch_gemm<kHid, kHidden>(g, mt, 1, st)));
+            in = m->ht[l];
+        } else {
+            g.out_f = m->y;
+            g.ld_f = kOutP;
+            MLP_CUDA(m, (launch_gemm<kOutP, kOutput>(g, mt, 1, st)));
+        }
+        t.stop();
+    }
+    return STP_OK;
+}
+
+// Backward from dY (already in dt[3] / dtT[3] / df[3]) to every parameter's
+// gradient partials; bias partials from the FP32 copies.
+stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
+    const int Bp = (B + kTileM - 1) / kTileM * kTileM;
+    const int mt = Bp / kTileM;
+    cudaStream_t st = m->stream;
+    const int KTb = Bp / kStageK;
+    const int splits = std::min(kSplitMax, std::max(1, KTb / 4));
+    const int kps = (KTb + splits - 1) / splits;
+    const int nb = (Bp + kColChunk - 1) / kColChunk;
+    *nwpart = splits;
+    *nbpart = nb;
+    for (int l = 3; l >= 0; --l) {
+        // bias gradient partials from df[l]
+        k_colsum<<<nb, kOutP, 0, st>>>(m->df[l], Bp, m->bpart + (size_t)l * (m->Bp_max / kColChunk + 1) * kOutP);
+        MLP_CUDA(m, cudaGetLastError());
+        // weight gradient: dW_l = dT_l^T . act_{l-1}   (M = out, N = in, K = batch)
+        GemmArgs g{};
+        g.A = m->dtT[l];
+        g.RA = kOutP;  // dtT buffers are [256][Bp]
+        g.B = (l == 0) ? m->xtT : m->htT[l - 1];
+        g.KT = KTb;
+        g.kt_per_split = kps;
+        g.out_f = m->wpart + (size_t)l * kSplitMax * kOutP * kHid;
+        g.ld_f = kLayers[l].in;
+        g.m_valid = kLayers[l].out;
+        g.err = m->err;
+        {
+            Timer t(m, 2.0 * Bp * kLayers[l].in * kLayers[l].out);
+            if (l == 0) MLP_CUDA(m, (launch_gemm<kInP, kWGrad>(g, kLayers[l].out / kTileM, splits, st)));
+            else MLP_CUDA(m, (launch_gemm<kHid, kWGrad>(g, kLayers[l].out / kTileM, splits, st)));
+            t.stop();
+        }
+        if (l == 0) break;
+        // input gradient: dH_{l-1} = (dT_l . W_l) * relu'(h_{l-1})   (M = batch, N = in, K = out)
+        GemmArgs h{};
+        h.A = m->dt[l];
+        h.RA = Bp;
+        h.B = m->wtT[l];
+        h.KT = kLayers[l].out / kStageK;
+        h.kt_per_split = h.KT;
+        h.act = m->ht[l - 1];
+        h.out_t = m->dt[l - 1];
+        h.out_tT = m->dtT[l - 1];
+        h.out_f = m->df[l - 1];
+        h.ld_f = kOutP;
+        h.err = m->err;
+        Timer t(m, 2.0 * Bp * kLayers[l].in * kLayers[l].out);
+        MLP_CUDA(m, (launch_gemm<kHid, kBackward>(h, mt, 1, st)));
+        t.stop();
+    }
+    return STP_OK;
+}
+
+stp_status adam_impl(stp_mlp* m, int nwpart, int nbpart, float lr, bool update, bool keep_grads) {
+    if (update) ++m->step;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = update ? 1.f - powf(b1, (float)m->step) : 1.f;
+    const float c2 = update ? 1.f - powf(b2, (float)m->step) : 1.f;
+    float* gout = m->gsum;
+    for (int l = 0; l < 4; ++l) {
+        const Layer& L = kLayers[l];
+        AdamArgs a{};
+        a.w = m->w[l];
+        a.m = m->mw[l];
+        a.v = m->vw[l];
+        a.gpart = m->wpart + (size_t)l * kSplitMax * kOutP * kHid;
+        a.nparts = nwpart;
+        a.rows = L.out;
+        a.cols = L.in;
+        a.rows_used = L.out_used;
+        a.wt = m->wt[l];
+        a.wtT = m->wtT[l];
+        a.gout = keep_grads ? gout : nullptr;
+        a.lr = lr;
+        a.b1 = b1;
+        a.b2 = b2;
+        a.eps = 1e-8f;
+        a.c1 = c1;
+        a.c2 = c2;
+        a.update = update ? 1 : 0;
+        int n = L.out * L.in;
+        k_adam<<<(n + 255) / 256, 256, 0, m->stream>>>(a);
+        MLP_CUDA(m, cudaGetLastError());
+        gout += n;
+        AdamArgs bb = a;
+        bb.w = m->b[l];
+        bb.m = m->mb[l];
+        bb.v = m->vb[l];
+        bb.gpart = m->bpart + (size_t)l * (m->Bp_max / kColChunk + 1) * kOutP;
+        bb.nparts = nbpart;
+        bb.rows = L.out;
+        bb.cols = 1;
+        bb.wt = nullptr;
+        bb.wtT = nullptr;
+        bb.gout = keep_grads ? gout : nullptr;
+        // bias partials are [chunk][256]: view as [rows = 256][cols = 1] per chunk
+        n = L.out;
+        k_adam<<<(n + 255) / 256, 256, 0, m->stream>>>(bb);
+        MLP_CUDA(m, cudaGetLastError());
+        gout += n;
+    }
+    return STP_OK;
+}
+
+stp_status stage_in(stp_mlp* m, float* dst, const float* src, size_t n, int flags) {
+    MLP_CUDA(m, cudaMemcpyAsync(dst, src, n * sizeof(float),
+                                (flags & STP_MLP_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                m->stream));
+    return STP_OK;
+}
+
+stp_status check_err(stp_mlp* m) {
+    int e = 0;
+    MLP_CUDA(m, cudaMemcpyAsync(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+    if (e) {
+        cudaMemsetAsync(m->err, 0, sizeof(int), m->stream);
+        return fail(m, STP_ERR_TIMEOUT, "tensor-core pipeline wait exceeded its limit");
+    }
+    return STP_OK;
+}
+
+// Logical parameter count and offsets.
+size_t nparam() {
+    size_t n = 0;
+    for (const Layer& L : kLayers) n += (size_t)L.out_used * L.in_used + L.out_used;
+    return n;
+}
+}  // namespace
+
+extern "C" {
+
+stp_status stp_mlp_create(int max_batch, stp_mlp** out) {
+    if (nparam() != (size_t)STP_MLP_NPARAM) return fail(nullptr, STP_ERR_INVALID, "parameter layout mismatch");
+    if (!out) return fail(nullptr, STP_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (max_batch <= 0 || max_batch > STP_MLP_MAX_BATCH) return fail(nullptr, STP_ERR_INVALID, "max_batch out of range");
+    stp_mlp* m = new (std::nothrow) stp_mlp();
+    if (!m) return fail(nullptr, STP_ERR_CAPACITY, "host allocation failed");
+    m->max_batch = max_batch;
+    const int Bp = (max_batch + kTileM - 1) / kTileM * kTileM;
+    m->Bp_max = Bp;
+    const int nbmax = Bp / kColChunk + 1;
+    // arena layout
+    std::vector<std::pair<void**, size_t>> parts;
+    for (int l = 0; l < 4; ++l) {
+        const size_t n = (size_t)kLayers[l].out * kLayers[l].in;
+        parts.push_back({(void**)&m->w[l], n * 4});
+        parts.push_back({(void**)&m->mw[l], n * 4});
+        parts.push_back({(void**)&m->vw[l], n * 4});
+        parts.push_back({(void**)&m->wt[l], n * 2});
+        parts.push_back({(void**)&m->wtT[l], n * 2});
+        parts.push_back({(void**)&m->b[l], (size_t)kLayers[l].out * 4});
+        parts.push_back({(void**)&m->mb[l], (size_t)kLayers[l].out * 4});
+        parts.push_back({(void**)&m->vb[l], (size_t)kLayers[l].out * 4});
+    }
+    parts.push_back({(void**)&m->xt, (size_t)Bp * kInP * 2});
+    parts.push_back({(void**)&m->xtT, (size_t)Bp * kInP * 2});
+    for (int l = 0; l < 3; ++l) {
+        parts.push_back({(void**)&m->ht[l], (size_t)Bp * kHid * 2});
+        parts.push_back({(void**)&m->htT[l], (size_t)Bp * kHid * 2});
+    }
+    for (int l = 0; l < 4; ++l) {
+        parts.push_back({(void**)&m->dt[l], (size_t)Bp * kOutP * 2});
+        parts.push_back({(void**)&m->dtT[l], (size_t)Bp * kOutP * 2});
+        parts.push_back({(void**)&m->df[l], (size_t)Bp * kOutP * 4});
+    }
+    parts.push_back({(void**)&m->y, (size_t)Bp * kOutP * 4});
+    parts.push_back({(void**)&m->wpart, (size_t)4 * kSplitMax * kOutP * kHid * 4});
+    parts.push_back({(void**)&m->bpart, (size_t)4 * nbmax * kOutP * 4});
+    parts.push_back({(void**)&m->gsum, (size_t)4 * (kOutP * kHid + kOutP) * 4});
+    parts.push_back({(void**)&m->loss, (size_t)Bp * 4});
+    parts.push_back({(void**)&m->X, (size_t)max_batch * kIn * 4});
+    parts.push_back({(void**)&m->T, (size_t)max_batch * kTgt * 4});
+    parts.push_back({(void**)&m->Yout, (size_t)max_batch * kOut * 4});
+    parts.push_back({(void**)&m->err, 256});
+    size_t total = 0;
+    for (auto& p : parts) total += up256(p.second);
+    if (cudaMalloc(&m->arena, total) != cudaSuccess) {
+        delete m;
+        return fail(nullptr, STP_ERR_CUDA, "device allocation failed");
+    }
+    m->arena_bytes = total;
+    size_t off = 0;
+    for (auto& p : parts) {
+        *p.first = m->arena + off;
+        off += up256(p.second);
+    }
+    if (cudaMemset(m->arena, 0, total) != cudaSuccess || cudaEventCreate(&m->ev[0]) != cudaSuccess ||
+        cudaEventCreate(&m->ev[1]) != cudaSuccess) {
+        cudaFree(m->arena);
+        delete m;
+        return fail(nullptr, STP_ERR_CUDA, "device initialisation failed");
+    }
+    *out = m;
+    return STP_OK;
+}
+
+void stp_mlp_free(stp_mlp* m) {
+    if (!m) return;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(m->arena);
+    cudaEventDestroy(m->ev[0]);
+    cudaEventDestroy(m->ev[1]);
+    delete m;
+}
+
+stp_status stp_mlp_set_stream(stp_mlp* m, void* stream) {
+    if (!m) return fail(nullptr, STP_ERR_INVALID, "mlp is NULL");
+    m->stream = (cudaStream_t)stream;
+    return STP_OK;
+}
+
+stp_status stp_mlp_set_params(stp_mlp* m, const float* params) {
+    if (!m || !params) return fail(m, STP_ERR_INVALID, "NULL argument");
+    const float* p = params;
+    for (int l = 0; l < 4; ++l) {
+        const Layer& L = kLayers[l];
+        std::vector<float> W((size_t)L.out * L.in, 0.f), b(L.out, 0.f);
+        for (int r = 0; r < L.out_used; ++r)
+            for (int c = 0; c < L.in_used; ++c) W[(size_t)r * L.in + c] = *p++;
+        for (int r = 0; r < L.out_used; ++r) b[r] = *p++;
+        MLP_CUDA(m, cudaMemcpyAsync(m->w[l], W.data(), W.size() * 4, cudaMemcpyHostToDevice, m->stream));
+        MLP_CUDA(m, cudaMemcpyAsync(m->b[l], b.data(), b.size() * 4, cudaMemcpyHostToDevice, m->stream));
+        MLP_CUDA(m, cudaMemsetAsync(m->mw[l], 0, W.size() * 4, m->stream));
+        MLP_CUDA(m, cudaMemsetAsync(m->vw[l], 0, W.size() * 4, m->stream));
+        MLP_CUDA(m, cudaMemsetAsync(m->mb[l], 0, b.size() * 4, m->stream));
+        MLP_CUDA(m, cudaMemsetAsync(m->vb[l], 0, b.size() * 4, m->stream));
+        MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+    }
+    m->step = 0;
+    // refresh the BF16 operand copies (no update)
+    stp_status s = adam_impl(m, 0, 0, 0.f, false, false);
+    if (s != STP_OK) return s;
+    MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+    return STP_OK;
+}
+
+stp_status stp_mlp_get_params(stp_mlp* m, float* params) {
+    if (!m || !params) return fail(m, STP_ERR_INVALID, "NULL argument");
+    float* p = params;
+    MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+    for (int l = 0; l < 4; ++l) {
+        const Layer& L = kLayers[l];
+        std::vector<float> W((size_t)L.out * L.in), b(L.out);
+        MLP_CUDA(m, cudaMemcpy(W.data(), m->w[l], W.size() * 4, cudaMemcpyDeviceToHost));
+        MLP_CUDA(m, cudaMemcpy(b.data(), m->b[l], b.size() * 4, cudaMemcpyDeviceToHost));
+        for (int r = 0; r < L.out_used; ++r)
+            for (int c = 0; c < L.in_used; ++c) *p++ = W[(size_t)r * L.in + c];
+        for (int r = 0; r < L.out_used; ++r) *p++ = b[r];
+    }
+    return STP_OK;
+}
+
+stp_status stp_mlp_forward(stp_mlp* m, int B, const float* X, float* Y, int flags) {
+    if (!m || !X || !Y) return fail(m, STP_ERR_INVALID, "NULL argument");
+    if (B <= 0 || B > m->max_batch) return fail(m, STP_ERR_INVALID, "batch out of range");
+    stp_status s = stage_in(m, m->X, X, (size_t)B * kIn, flags);
+    if (s != STP_OK) return s;
+    if ((s = forward_impl(m, B)) != STP_OK) return s;
+    const int n = B * kOut;
+    k_unpack_out<<<(n + 255) / 256, 256, 0, m->stream>>>(m->y, B, m->Yout);
+    MLP_CUDA(m, cudaGetLastError());
+    MLP_CUDA(m, cudaMemcpyAsync(Y, m->Yout, (size_t)n * 4,
+                                (flags & STP_MLP_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                m->stream));
+    return check_err(m);
+}
+
+static stp_status loss_grad(stp_mlp* m, int B, const float* X, const float* T, int flags, int* nw, int* nb) {
+    if (!m || !X || !T) return fail(m, STP_ERR_INVALID, "NULL argument");
+    if (B <= 0 || B > m->max_batch) return fail(m, STP_ERR_INVALID, "batch out of range");
+    stp_status s = stage_in(m, m->X, X, (size_t)B * kIn, flags);
+    if (s != STP_OK) return s;
+    if ((s = stage_in(m, m->T, T, (size_t)B * kTgt, flags)) != STP_OK) return s;
+    if ((s = forward_impl(m, B)) != STP_OK) return s;
+    const int Bp = (B + kTileM - 1) / kTileM * kTileM;
+    k_loss<<<(Bp + 127) / 128, 128, 0, m->stream>>>(m->y, m->T, B, Bp, m->df[3], m->dt[3], m->dtT[3], m->loss);
+    MLP_CUDA(m, cudaGetLastError());
+    return backward_impl(m, B, nw, nb);
+}
+
+static stp_status read_loss(stp_mlp* m, int B, float* loss) {
+    if (!loss) return STP_OK;
+    std::vector<float> l(B);
+    MLP_CUDA(m, cudaMemcpyAsync(l.data(), m->loss, (size_t)B * 4, cudaMemcpyDeviceToHost, m->stream));
+    MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+    double s = 0;
+    for (float v : l) s += v;
+    *loss = (float)(s / B);
+    return STP_OK;
+}
+
+stp_status stp_mlp_gradients(stp_mlp* m, int B, const float* X, const float* T, float* loss, float* grads,
+                             int flags) {
+    int nw = 0, nb = 0;
+    stp_status s = loss_grad(m, B, X, T, flags, &nw, &nb);
+    if (s != STP_OK) return s;
+    if ((s = adam_impl(m, nw, nb, 0.f, false, true)) != STP_OK) return s;
+    if ((s = check_err(m)) != STP_OK) return s;
+    if ((s = read_loss(m, B, loss)) != STP_OK) return s;
+    if (grads) {
+        // padded gradient tensors -> logical order
+        float* p = grads;
+        const float* g = m->gsum;
+        for (int l = 0; l < 4; ++l) {
+            const Layer& L = kLayers[l];
+            std::vector<float> W((size_t)L.out * L.in), b(L.out);
+            MLP_CUDA(m, cudaMemcpy(W.data(), g, W.size() * 4, cudaMemcpyDeviceToHost));
+            g += W.size();
+            MLP_CUDA(m, cudaMemcpy(b.data(), g, b.size() * 4, cudaMemcpyDeviceToHost));
+            g += b.size();
+            for (int r = 0; r < L.out_used; ++r)
+                for (int c = 0; c < L.in_used; ++c) *p++ = W[(size_t)r * L.in + c];
+            for (int r = 0; r < L.out_used; ++r) *p++ = b[r];
+        }
+    }
+    return STP_OK;
+}
+
+stp_status stp_mlp_train_step(stp_mlp* m, int B, const float* X, const float* T, float lr, float* loss, int flags) {
+    if (!(lr >= 0.f)) return fail(m, STP_ERR_INVALID, "learning rate must be >= 0");
+    int nw = 0, nb = 0;
+    stp_status s = loss_grad(m, B, X, T, flags, &nw, &nb);
+    if (s != STP_OK) return s;
+    if ((s = adam_impl(m, nw, nb, lr, true, false)) != STP_OK) return s;
+    if ((s = check_err(m)) != STP_OK) return s;
+    return read_loss(m, B, loss);
+}
+
+stp_status stp_mlp_set_profiling(stp_mlp* m, int on) {
+    if (!m) return fail(nullptr, STP_ERR_INVALID, "mlp is NULL");
+    m->profiling = on != 0;
+    m->gemm_ms = 0;
+    m->gemm_flops = 0;
+    return STP_OK;
+}
+
+stp_status stp_mlp_profile(stp_mlp* m, double* gemm_ms, double* gemm_flops) {
+    if (!m) return fail(nullptr, STP_ERR_INVALID, "mlp is NULL");
+    if (gemm_ms) *gemm_ms = m->gemm_ms;
+    if (gemm_flops) *gemm_flops = m->gemm_flops;
+    m->gemm_ms = 0;
+    m->gemm_flops = 0;
+    return STP_OK;
+}
+
+const char* stp_mlp_last_error(const stp_mlp* m) { return m ? m->last_error.c_str() : g_mlp_err.c_str(); }
+
+}  // extern "C"

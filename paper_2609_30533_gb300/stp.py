@@ -119,6 +119,29 @@ def lib():
     L.stp_slots.restype = C.c_int
     L.stp_goal_grid.argtypes = [C.c_void_p, C.POINTER(C.c_long), _I, C.c_void_p, C.c_int]
     L.stp_goal_grid.restype = C.c_int
+    _F = C.POINTER(C.c_float)
+    L.stp_mlp_create.argtypes = [C.c_int, C.POINTER(C.c_void_p)]
+    L.stp_mlp_create.restype = C.c_int
+    L.stp_mlp_free.argtypes = [C.c_void_p]
+    L.stp_mlp_free.restype = None
+    L.stp_mlp_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+    L.stp_mlp_set_stream.restype = C.c_int
+    L.stp_mlp_set_params.argtypes = [C.c_void_p, _F]
+    L.stp_mlp_set_params.restype = C.c_int
+    L.stp_mlp_get_params.argtypes = [C.c_void_p, _F]
+    L.stp_mlp_get_params.restype = C.c_int
+    L.stp_mlp_forward.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]
+    L.stp_mlp_forward.restype = C.c_int
+    L.stp_mlp_gradients.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, _F, _F, C.c_int]
+    L.stp_mlp_gradients.restype = C.c_int
+    L.stp_mlp_train_step.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_float, _F, C.c_int]
+    L.stp_mlp_train_step.restype = C.c_int
+    L.stp_mlp_set_profiling.argtypes = [C.c_void_p, C.c_int]
+    L.stp_mlp_set_profiling.restype = C.c_int
+    L.stp_mlp_profile.argtypes = [C.c_void_p, _D, _D]
+    L.stp_mlp_profile.restype = C.c_int
+    L.stp_mlp_last_error.argtypes = [C.c_void_p]
+    L.stp_mlp_last_error.restype = C.c_char_p
     _LIB = L
     return L
 
@@ -126,7 +149,10 @@ def lib():
 EXPORTED = ["stp_create_problem", "stp_plan", "stp_check_edges", "stp_free", "stp_set_stream",
             "stp_status_string", "stp_last_error", "stp_last_validate", "stp_set_profiling", "stp_profile",
             "stp_tree_size", "stp_tree_nodes", "stp_history", "stp_slots", "stp_goal_grid",
-            "stp_check_edges_noalloc", "stp_batch_create", "stp_batch_plan", "stp_batch_path", "stp_batch_free"]
+            "stp_check_edges_noalloc", "stp_batch_create", "stp_batch_plan", "stp_batch_path", "stp_batch_free",
+            "stp_mlp_create", "stp_mlp_free", "stp_mlp_set_stream", "stp_mlp_set_params", "stp_mlp_get_params",
+            "stp_mlp_forward", "stp_mlp_gradients", "stp_mlp_train_step", "stp_mlp_set_profiling",
+            "stp_mlp_profile", "stp_mlp_last_error"]
 
 
 def status_string(s: int) -> str:
@@ -374,6 +400,125 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             lib().stp_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# Learned proposal network (stp_mlp_*).
+# ---------------------------------------------------------------------------
+MLP_IN, MLP_OUT, MLP_NTGT, MLP_NPARAM = 32, 160, 130, 181152
+MLP_DEVICE = 1
+_MLP_SHAPES = (("W1", (256, 32)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 256)),
+               ("b3", (256,)), ("W4", (160, 256)), ("b4", (160,)))
+
+
+def flatten_params(P) -> np.ndarray:
+    """dict of arrays (oracle layout) -> STP_MLP_NPARAM float32 vector."""
+    return np.concatenate([np.asarray(P[k], dtype=np.float32)[:s[0]].reshape(-1) if k in ("W4", "b4")
+                           else np.asarray(P[k], dtype=np.float32).reshape(-1) for k, s in _MLP_SHAPES])
+
+
+def unflatten_params(v) -> dict:
+    out, o = {}, 0
+    for k, s in _MLP_SHAPES:
+        n = int(np.prod(s))
+        out[k] = np.asarray(v[o:o + n], dtype=np.float64).reshape(s)
+        o += n
+    return out
+
+
+class Mlp:
+    """The proposal network on the device (stp_mlp_*)."""
+
+    def __init__(self, max_batch: int):
+        L = lib()
+        h = C.c_void_p()
+        s = L.stp_mlp_create(int(max_batch), C.byref(h))
+        if s != STP_OK:
+            raise StpError(s, "stp_mlp_create", L.stp_mlp_last_error(None).decode())
+        self.handle = h
+        self.max_batch = int(max_batch)
+
+    def _err(self, s, where):
+        return StpError(s, where, lib().stp_mlp_last_error(self.handle).decode())
+
+    def set_stream(self, stream_ptr):
+        lib().stp_mlp_set_stream(self.handle, C.c_void_p(stream_ptr) if stream_ptr else None)
+
+    def set_params(self, flat: np.ndarray):
+        v = np.ascontiguousarray(flat, dtype=np.float32)
+        assert v.size == MLP_NPARAM
+        s = lib().stp_mlp_set_params(self.handle, v.ctypes.data_as(C.POINTER(C.c_float)))
+        if s != STP_OK:
+            raise self._err(s, "stp_mlp_set_params")
+
+    def get_params(self) -> np.ndarray:
+        v = np.zeros(MLP_NPARAM, dtype=np.float32)
+        s = lib().stp_mlp_get_params(self.handle, v.ctypes.data_as(C.POINTER(C.c_float)))
+        if s != STP_OK:
+            raise self._err(s, "stp_mlp_get_params")
+        return v
+
+    def forward(self, X: np.ndarray) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        B = X.shape[0]
+        Y = np.zeros((B, MLP_OUT), dtype=np.float32)
+        s = lib().stp_mlp_forward(self.handle, B, X.ctypes.data, Y.ctypes.data, 0)
+        if s != STP_OK:
+            raise self._err(s, "stp_mlp_forward")
+        return Y
+
+    def forward_device(self, B: int, x_ptr: int, y_ptr: int):
+        s = lib().stp_mlp_forward(self.handle, int(B), C.c_void_p(x_ptr), C.c_void_p(y_ptr), MLP_DEVICE)
+        if s != STP_OK:
+            raise self._err(s, "stp_mlp_forward")
+
+    def gradients(self, X: np.ndarray, T: np.ndarray):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        g = np.zeros(MLP_NPARAM, dtype=np.float32)
+        loss = C.c_float()
+        s = lib().stp_mlp_gradients(self.handle, X.shape[0], X.ctypes.data, T.ctypes.data, C.byref(loss),
+                                    g.ctypes.data_as(C.POINTER(C.c_float)), 0)
+        if s != STP_OK:
+            raise self._err(s, "stp_mlp_gradients")
+        return float(loss.value), g
+
+    def train_step(self, X: np.ndarray, T: np.ndarray, lr: float) -> float:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        loss = C.c_float()
+        s = lib().stp_mlp_train_step(self.handle, X.shape[0], X.ctypes.data, T.ctypes.data, float(lr),
+                                     C.byref(loss), 0)
+        if s != STP_OK:
+            raise self._err(s, "stp_mlp_train_step")
+        return float(loss.value)
+
+    def train_step_device(self, B: int, x_ptr: int, t_ptr: int, lr: float) -> float:
+        loss = C.c_float()
+        s = lib().stp_mlp_train_step(self.handle, int(B), C.c_void_p(x_ptr), C.c_void_p(t_ptr), float(lr),
+                                     C.byref(loss), MLP_DEVICE)
+        if s != STP_OK:
+            raise self._err(s, "stp_mlp_train_step")
+        return float(loss.value)
+
+    def set_profiling(self, on: bool):
+        lib().stp_mlp_set_profiling(self.handle, 1 if on else 0)
+
+    def profile(self):
+        ms, fl = C.c_double(), C.c_double()
+        lib().stp_mlp_profile(self.handle, C.byref(ms), C.byref(fl))
+        return ms.value, fl.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().stp_mlp_free(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -109,3 +109,13 @@ def test_no_cpu_fallback_without_gpu(L):
     prob, _ = WL.disc2d(0)
     s, h = _create(prob, _params())
     assert s == 3 and not h.value     # STP_ERR_CUDA
+
+
+def test_mlp_argument_checks_and_no_cpu_fallback(L):
+    h = C.c_void_p()
+    assert L.stp_mlp_create(0, C.byref(h)) == 1          # STP_ERR_INVALID
+    assert L.stp_mlp_create(65537, C.byref(h)) == 1
+    assert L.stp_mlp_create(16, None) == 1
+    import torch
+    if not torch.cuda.is_available():
+        assert L.stp_mlp_create(16, C.byref(h)) == 3     # STP_ERR_CUDA: no device, no fallback

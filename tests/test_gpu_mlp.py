@@ -1,0 +1,155 @@
+"""Proposal network on the tensor cores against the FP64 oracle network:
+an exact identity network (layout pin), forward and gradients on ragged and
+maximum batch sizes within BF16 tolerances, the first Adam step, and a
+training run that lowers a held-out loss."""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def stp():
+    from paper_2609_30533_gb300 import build as B
+    B.build()
+    from paper_2609_30533_gb300 import stp as S
+    return S
+
+
+def _targets(rng, X):
+    """Smooth synthetic targets: tau and waypoints as functions of x."""
+    B = X.shape[0]
+    T = np.zeros((B, M.N_TGT))
+    T[:, 0] = 1 / (1 + np.exp(-(X[:, 0] - X[:, 7])))
+    dof = rng.choice([2, 6, 7], size=B)
+    for i in range(M.N_WP):
+        f = (i + 1) / 17
+        T[:, 1 + 8 * i:1 + 8 * i + 7] = (1 - f) * X[:, 0:7] + f * X[:, 7:14]
+        T[:, 1 + 8 * i + 7] = f * T[:, 0]
+    for n in range(B):
+        for i in range(M.N_WP):
+            T[n, 1 + 8 * i + dof[n]:1 + 8 * i + 7] = 0.0
+    T[:, -1] = dof
+    return T
+
+
+def _inputs(rng, B):
+    X = np.zeros((B, M.IN))
+    X[:, 0:26] = rng.uniform(-1, 1, size=(B, 26))
+    return X
+
+
+def test_identity_network_is_exact(stp):
+    P = {k: np.zeros_like(v) for k, v in M.init_params(np.random.default_rng(0)).items()}
+    P["W1"][0:32, 0:32] = np.eye(32)
+    P["W1"][32:64, 0:32] = -np.eye(32)
+    P["W2"][:] = np.eye(256)
+    P["W3"][:] = np.eye(256)
+    P["W4"][0:32, 0:32] = np.eye(32)
+    P["W4"][0:32, 32:64] = -np.eye(32)
+    net = stp.Mlp(512)
+    net.set_params(stp.flatten_params(P))
+    X = np.random.default_rng(1).normal(size=(300, 32))
+    Y = net.forward(X)
+    assert np.array_equal(Y[:, 0:32].astype(np.float64), M.bf16_round(X))
+    assert np.all(Y[:, 32:] == 0)
+    net.close()
+
+
+def _rel_rows(a, b):
+    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-12)
+
+
+@pytest.mark.parametrize("B", [1, 128, 300])
+def test_forward_matches_oracle(stp, B):
+    rng = np.random.default_rng(10 + B)
+    P = M.init_params(rng)
+    for b in ("b1", "b2", "b3", "b4"):
+        P[b] = rng.normal(scale=0.1, size=P[b].shape)
+    P["b4"][M.OUT_USED:] = 0.0
+    X = _inputs(rng, B)
+    net = stp.Mlp(512)
+    net.set_params(stp.flatten_params(P))
+    Y = net.forward(X).astype(np.float64)
+    Ye, _ = M.forward(P, X, bf16=True)
+    Y64, _ = M.forward(P, X, bf16=False)
+    assert np.max(_rel_rows(Y, Ye[:, :160])) < 1e-2
+    assert np.max(_rel_rows(Y, Y64[:, :160])) < 3e-2
+    net.close()
+
+
+def test_forward_at_maximum_batch_sampled(stp):
+    rng = np.random.default_rng(7)
+    P = M.init_params(rng)
+    B = 65536
+    X = _inputs(rng, B)
+    net = stp.Mlp(B)
+    net.set_params(stp.flatten_params(P))
+    Y = net.forward(X).astype(np.float64)
+    idx = np.r_[0, 1, 127, 128, rng.integers(0, B, size=250), B - 129, B - 1]
+    Ye, _ = M.forward(P, X[idx], bf16=True)
+    assert np.max(_rel_rows(Y[idx], Ye[:, :160])) < 1e-2
+    net.close()
+
+
+@pytest.mark.parametrize("B", [37, 300])
+def test_gradients_match_oracle(stp, B):
+    rng = np.random.default_rng(20 + B)
+    P = M.init_params(rng)
+    X = _inputs(rng, B)
+    T = _targets(rng, X)
+    net = stp.Mlp(512)
+    net.set_params(stp.flatten_params(P))
+    loss, g = net.gradients(X, T)
+    y, cache = M.forward(P, X, bf16=True)
+    Ls, dy = M.loss(y, T)
+    G = M.backward(P, cache, dy, bf16=True)
+    assert abs(loss - Ls.mean()) <= 1e-2 * abs(Ls.mean())
+    Gg = stp.unflatten_params(g)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4"):
+        ref = G[k][:Gg[k].shape[0]]
+        err = np.linalg.norm(Gg[k] - ref) / max(np.linalg.norm(ref), 1e-12)
+        assert err < 2e-2, (k, err)
+    net.close()
+
+
+def test_first_adam_step_against_oracle(stp):
+    rng = np.random.default_rng(3)
+    P = M.init_params(rng)
+    X = _inputs(rng, 256)
+    T = _targets(rng, X)
+    net = stp.Mlp(256)
+    net.set_params(stp.flatten_params(P))
+    lr = 1e-3
+    net.train_step(X, T, lr)
+    P1 = stp.unflatten_params(net.get_params())
+    y, cache = M.forward(P, X, bf16=True)
+    _, dy = M.loss(y, T)
+    G = M.backward(P, cache, dy, bf16=True)
+    Pe = {k: v.copy() for k, v in P.items()}
+    M.adam_step(Pe, G, M.adam_init(Pe), 1, lr)
+    for k in P1:
+        g = G[k][:P1[k].shape[0]]
+        sure = np.abs(g) > 0.05 * np.abs(g).max()      # sign of the step is unambiguous
+        d_gpu = (P1[k] - np.float32(P[k][:P1[k].shape[0]]))[sure]
+        d_ref = (Pe[k][:P1[k].shape[0]] - P[k][:P1[k].shape[0]])[sure]
+        assert np.allclose(d_gpu, d_ref, rtol=0, atol=2e-4 * lr / 1e-3 + 1e-7), k
+    net.close()
+
+
+def test_training_lowers_heldout_loss(stp):
+    rng = np.random.default_rng(4)
+    P = M.init_params(rng)
+    Xtr, Xte = _inputs(rng, 4096), _inputs(rng, 512)
+    Ttr, Tte = _targets(rng, Xtr), _targets(rng, Xte)
+    net = stp.Mlp(4096)
+    net.set_params(stp.flatten_params(P))
+    before = M.batch_loss(stp.unflatten_params(net.get_params()), Xte, Tte)
+    for it in range(300):
+        idx = rng.integers(0, 4096, size=1024)
+        net.train_step(Xtr[idx], Ttr[idx], 1e-3)
+    after = M.batch_loss(stp.unflatten_params(net.get_params()), Xte, Tte)
+    assert after < 0.5 * before, (before, after)
+    net.close()
