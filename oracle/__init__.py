@@ -30,7 +30,8 @@ class OrcParams(C.Structure):
                 ("max_iters", C.c_int), ("eta", C.c_double), ("res", C.c_double),
                 ("dt", C.c_double), ("p_new", C.c_double), ("p_guided", C.c_double),
                 ("H", C.c_double), ("seed", C.c_ulonglong), ("problem_id", C.c_uint),
-                ("flag_tol", C.c_double), ("flag_clear", C.c_double)]
+                ("flag_tol", C.c_double), ("flag_clear", C.c_double), ("learned", C.c_int),
+                ("proposal", _D)]
 
 
 def _dptr(a: np.ndarray):
@@ -59,6 +60,9 @@ def lib():
                                      C.c_double]
     L.orc_recycle_update.restype = C.c_int
     L.orc_plan.argtypes = [C.POINTER(OrcProblem), C.POINTER(OrcParams), C.POINTER(C.c_void_p)]
+    L.orc_learned_sample.argtypes = [_D, _D, _D, C.c_int, C.c_double, C.c_ulonglong, C.c_uint, C.c_uint,
+                                     C.c_uint, _I, _D, _D]
+    L.orc_learned_sample.restype = C.c_int
     L.orc_plan.restype = C.c_int
     L.orc_result_summary.argtypes = [C.c_void_p, _D]
     L.orc_result_path.argtypes = [C.c_void_p, _D]
@@ -238,16 +242,39 @@ class PlanResult:
     goal_clearance: np.ndarray
 
 
-def make_params(params, **over) -> OrcParams:
+def make_params(params, proposal=None, **over) -> OrcParams:
     p = dataclasses.replace(params, **over) if over else params
-    return OrcParams(p.variant, p.n_roots, p.workers, p.max_iters, p.eta, p.res, p.dt, p.p_new,
-                     p.p_guided, p.H, p.seed, p.problem_id, 0.0, 0.0)
+    prm = OrcParams(p.variant, p.n_roots, p.workers, p.max_iters, p.eta, p.res, p.dt, p.p_new,
+                    p.p_guided, p.H, p.seed, p.problem_id, 0.0, 0.0, 0, None)
+    if proposal is not None:
+        prm.learned = 1
+        prm.proposal = _dptr(proposal)
+    return prm
 
 
-def plan(prob, params, **over) -> PlanResult:
+def learned_sample(y, qlo, qhi, H, seed, problem_id, k, w):
+    """Learned-branch draws of worker w at iteration k: (learned, waypoint
+    index, q_r, T_l or NaN)."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    lo = np.ascontiguousarray(qlo, dtype=np.float64)
+    hi = np.ascontiguousarray(qhi, dtype=np.float64)
+    d = len(lo)
+    qr = np.zeros(d)
+    wi = C.c_int()
+    Tl = C.c_double()
+    f = lib().orc_learned_sample(_dptr(y), _dptr(lo), _dptr(hi), d, float(H), C.c_ulonglong(seed),
+                                 C.c_uint(problem_id), C.c_uint(k), C.c_uint(w), C.byref(wi), _dptr(qr),
+                                 C.byref(Tl))
+    return bool(f), wi.value, qr, Tl.value
+
+
+def plan(prob, params, proposal=None, **over) -> PlanResult:
+    """proposal: network output y[160] (float64 array) enables the learned branch."""
     L = lib()
     h = _ProblemHandle(prob)
-    prm = make_params(params, **over)
+    if proposal is not None:
+        proposal = np.ascontiguousarray(proposal, dtype=np.float64)
+    prm = make_params(params, proposal, **over)
     handle = C.c_void_p()
     L.orc_plan(h.ref, C.byref(prm), C.byref(handle))
     try:

@@ -66,9 +66,11 @@ void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t 
 // the draws are slots s = 0,1,2,...: slot s is word s%4 of the Philox block with
 // counter (s/4, w, k, p) and key (seed lo, seed hi).
 // Slot map: 0 group, 1 guided coin, 2 T position, 3 new-root coin,
-// 4..4+d-1 configuration sample q_r, 4+d query time t_r.
+// 4..4+d-1 configuration sample q_r, 4+d query time t_r; the learned branch
+// adds 12 learned coin, 13 waypoint index, 14 mixture component, 15-16
+// Box-Muller uniforms.
 struct Draws {
-    uint32_t raw[16];
+    uint32_t raw[20];
     void fill(uint64_t seed, uint32_t problem, uint32_t iter, uint32_t worker, int nslots) {
         uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
         for (int b = 0; b * 4 < nslots; ++b) {
@@ -492,6 +494,80 @@ std::vector<int> recycle_rule(std::vector<Slot>& slots, double U, long kmin, dou
     return replaced;
 }
 
+// ---------------------------------------------------------------------------
+// Learned sampling branch (the method's GPU form: a learned proposal with 10 %
+// plain samples). A network output y[160] gives a mixture of 8 Gaussians over
+// tau = T/H (logits y[0:8], means y[8:16], log standard deviations y[16:24]
+// clamped to [-7, 2]) and 16 waypoints (y[24 + 8 i + j], joint j normalised to
+// [-1, 1] over the joint box). Readings: a worker is learned when its coin
+// (slot 12) is below p_learned = 0.9 (integer threshold ceil(0.9 2^24)); it
+// then draws q_r uniformly in +-0.1 of each joint's range around waypoint i
+// (slot 13, uniform over the 16), clipped to C, reusing the plain q_r
+// uniforms; in interval root it also draws T from the mixture (component by
+// slot 14, Box-Muller normal from slots 15-16) and keeps it only when it lies
+// in the sampled group's uniform interval, otherwise the plain T stands.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kThrLearned = 15099495u;  // ceil(0.9 * 2^24)
+constexpr double kLearnedHalfWidth = 0.1;    // fraction of each joint range
+
+struct Learned {
+    bool on = false;
+    double cw[8] = {0}, mu[8] = {0}, sig[8] = {0};  // cumulative weights; T mean / sd in seconds
+    std::vector<double> wq;                          // [16][dof]
+};
+
+void build_learned(Learned& L, const double* y, const std::vector<double>& lo, const std::vector<double>& hi,
+                   int dof, double H) {
+    L.on = true;
+    double amax = y[0];
+    for (int k = 1; k < 8; ++k) amax = std::max(amax, y[k]);
+    double e[8], tot = 0.0;
+    for (int k = 0; k < 8; ++k) {
+        e[k] = std::exp(y[k] - amax);
+        tot += e[k];
+    }
+    double acc = 0.0;
+    for (int k = 0; k < 8; ++k) {
+        acc += e[k];
+        L.cw[k] = acc / tot;
+    }
+    L.cw[7] = 1.0;
+    for (int k = 0; k < 8; ++k) {
+        L.mu[k] = y[8 + k] * H;
+        L.sig[k] = std::exp(std::min(std::max(y[16 + k], -7.0), 2.0)) * H;
+    }
+    L.wq.assign(16 * (size_t)dof, 0.0);
+    for (int i = 0; i < 16; ++i)
+        for (int j = 0; j < dof; ++j) {
+            double u = std::min(std::max(y[24 + 8 * i + j], -1.0), 1.0);
+            L.wq[(size_t)i * dof + j] = lo[j] + (u + 1.0) * 0.5 * (hi[j] - lo[j]);
+        }
+}
+
+// q_r of a learned worker (overwrites qr); margins of the clip tests are noted.
+void learned_q(const Learned& L, const Draws& dr, const std::vector<double>& lo, const std::vector<double>& hi,
+               int dof, double* qr) {
+    const int i = dr.group(13, 16);
+    for (int j = 0; j < dof; ++j) {
+        const double half = kLearnedHalfWidth * (hi[j] - lo[j]);
+        double q = L.wq[(size_t)i * dof + j] + half * (2.0 * dr.u(4 + j) - 1.0);
+        qr[j] = std::min(std::max(q, lo[j]), hi[j]);
+    }
+}
+
+// Mixture goal time of a learned worker; returns the component's draw.
+double learned_T(const Learned& L, const Draws& dr, double* comp_margin) {
+    const double u = dr.u(14);
+    int k = 0;
+    while (k < 7 && !(u < L.cw[k])) ++k;
+    double m = std::fabs(L.cw[k] - u);
+    if (k > 0) m = std::min(m, std::fabs(u - L.cw[k - 1]));
+    *comp_margin = m;
+    const double u1 = 1.0 - dr.u(15), u2 = dr.u(16);
+    const double z = std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586476925 * u2);
+    return L.mu[k] + L.sig[k] * z;
+}
+
 struct Params {
     int variant = 0;  // 0 interval root, 1 root recycling
     int N = 4;
@@ -505,6 +581,7 @@ struct Params {
     // eps |q| / alpha per tree level), so 1e-5 keeps a safety factor above it.
     double flag_tol = 1e-5;
     double flag_clear = 1e-5;  // clearance band (m)
+    const double* proposal = nullptr;  // learned branch: network output y[160], or none
 };
 
 // Smallest decision margins seen during one iteration (test diagnostics for
@@ -626,6 +703,7 @@ private:
     Result R;
     GoalGrid grid;
     IntervalAlloc alloc;
+    Learned learned;
     long kend = 0;  // first grid index with k dt >= H (recycling roots lie in [L_grid, H))
 
     int d() const { return P.dof; }
@@ -701,12 +779,22 @@ Proposal Planner::propose_interval(int k, int w, const std::vector<int>& seg_n, 
     Proposal pr;
     int dd = d();
     Draws dr;
-    dr.fill(prm.seed, prm.problem_id, (uint32_t)k, (uint32_t)w, 5 + dd);
+    dr.fill(prm.seed, prm.problem_id, (uint32_t)k, (uint32_t)w, learned.on ? 17 : 5 + dd);
+    const bool lrn = learned.on && (dr.raw[12] >> 8) < kThrLearned;
     pr.forward = ((w + k) % 2) == 0;
     int g = dr.group(0, prm.N);
     pr.seg = g;
     bool guided;
     double T = sample_goal_time(alloc, g, dr.u(1), dr.u(2), prm.p_guided, &guided);
+    if (lrn) {
+        double cm;
+        const double Tl = learned_T(learned, dr, &cm);
+        const double glo = alloc.Lg + (double)g * alloc.width;
+        note(M.interval, cm);
+        note(M.bounds, Tl - glo);
+        note(M.bounds, glo + alloc.width - Tl);
+        if (Tl >= glo && Tl < glo + alloc.width) T = Tl;
+    }
     pr.T = T;
     // Each proposed root is collision-checked at its sampled time; a rejected
     // root skips the attempt (Algorithm 2).
@@ -720,6 +808,7 @@ Proposal Planner::propose_interval(int k, int w, const std::vector<int>& seg_n, 
     // Conditional query sample (Eq. conditional-query-time).
     std::vector<double> qr(dd);
     for (int j = 0; j < dd; ++j) qr[j] = P.qlo[j] + dr.u(4 + j) * (P.qhi[j] - P.qlo[j]);
+    if (lrn) learned_q(learned, dr, P.qlo, P.qhi, dd, qr.data());
     double lo = dist(P.qs.data(), qr.data(), dd) / P.vmax;
     double hi = T - dist(qr.data(), P.qg.data(), dd) / P.vmax;
     note(M.interval, hi - lo);
@@ -783,9 +872,10 @@ Proposal Planner::propose_recycling(int k, int w, const std::vector<int>& seg_n,
         pr.seg = active_slots[(w / 2) % active_slots.size()];
     }
     Draws dr;
-    dr.fill(prm.seed, prm.problem_id, (uint32_t)k, (uint32_t)w, 4 + dd);
+    dr.fill(prm.seed, prm.problem_id, (uint32_t)k, (uint32_t)w, learned.on ? 17 : 4 + dd);
     std::vector<double> qr(dd);
     for (int j = 0; j < dd; ++j) qr[j] = P.qlo[j] + dr.u(4 + j) * (P.qhi[j] - P.qlo[j]);
+    if (learned.on && (dr.raw[12] >> 8) < kThrLearned) learned_q(learned, dr, P.qlo, P.qhi, dd, qr.data());
     const std::vector<Node>& A = pr.forward ? R.fwd : R.seg[pr.seg];
     int n = pr.forward ? fwd_n : seg_n[pr.seg];
     double D;
@@ -832,6 +922,7 @@ void Planner::extract_path() {
 
 Result Planner::run() {
     int dd = d();
+    if (prm.proposal) build_learned(learned, prm.proposal, P.qlo, P.qhi, dd, prm.H);
     R.dof = dd;
     R.N = prm.N;
     R.variant = prm.variant;
@@ -1116,6 +1207,8 @@ typedef struct {
     unsigned long long seed;
     unsigned int problem_id;
     double flag_tol, flag_clear;
+    int learned;              /* 1: learned branch with proposal[160] */
+    const double* proposal;
 } orc_params;
 
 static Problem to_problem(const orc_problem* p) {
@@ -1256,6 +1349,29 @@ struct orc_result {
     Result R;
 };
 
+// Learned-branch draws of worker w at iteration k (pins): learned flag,
+// waypoint index, q_r [dof] (plain uniforms overwritten when learned), the
+// mixture goal time T_l (interval root only: NaN when not learned).
+int orc_learned_sample(const double* y, const double* qlo, const double* qhi, int dof, double H,
+                       unsigned long long seed, unsigned problem_id, unsigned k, unsigned w, int* wp_index,
+                       double* qr, double* Tl) {
+    std::vector<double> lo(qlo, qlo + dof), hi(qhi, qhi + dof);
+    Learned L;
+    build_learned(L, y, lo, hi, dof, H);
+    Draws dr;
+    dr.fill(seed, problem_id, k, w, 17);
+    const bool lrn = (dr.raw[12] >> 8) < kThrLearned;
+    for (int j = 0; j < dof; ++j) qr[j] = lo[j] + dr.u(4 + j) * (hi[j] - lo[j]);
+    *wp_index = dr.group(13, 16);
+    *Tl = std::nan("");
+    if (lrn) {
+        learned_q(L, dr, lo, hi, dof, qr);
+        double cm;
+        *Tl = learned_T(L, dr, &cm);
+    }
+    return lrn ? 1 : 0;
+}
+
 int orc_plan(const orc_problem* prob, const orc_params* p, orc_result** out) {
     Problem P = to_problem(prob);
     Params prm;
@@ -1273,6 +1389,10 @@ int orc_plan(const orc_problem* prob, const orc_params* p, orc_result** out) {
     prm.problem_id = p->problem_id;
     if (p->flag_tol > 0) prm.flag_tol = p->flag_tol;
     if (p->flag_clear > 0) prm.flag_clear = p->flag_clear;
+    if (p->learned) {
+        if (!p->proposal) return -1;
+        prm.proposal = p->proposal;
+    }
     Planner pl(P, prm);
     orc_result* r = new orc_result;
     r->R = pl.run();
