@@ -95,7 +95,10 @@ typedef struct {
  *   t_max          horizon H; arrival times lie in [0, H].
  *   seed, problem_id  Philox4x32-10 key and counter word 3.
  *   precision      0 FP32, 1 FP64.
- *   learned        reserved, must be 0.
+ *   learned        0 plain sampling; 1 learned sampling branch: a proposal from
+ *                  the proposal network (stp_set_proposal) guides 90 % of the
+ *                  workers (the rest sample as with 0); stp_plan and
+ *                  stp_batch_plan return STP_ERR_INVALID until one is set.
  *   capacity       nodes per tree arena; 0 = max_iters * ceil(W/2) + 2 (worst case).
  *   iters_per_graph  iterations captured per CUDA graph launch; 0 = 16. */
 typedef struct {
@@ -325,6 +328,23 @@ stp_status stp_mlp_train_step(stp_mlp *m, int B, const float *x, const float *ta
 stp_status stp_mlp_set_profiling(stp_mlp *m, int on);
 stp_status stp_mlp_profile(stp_mlp *m, double *gemm_ms, double *gemm_flops);
 const char *stp_mlp_last_error(const stp_mlp *m);
+
+/* Problem summary x[STP_MLP_IN] of p (layout above), from its FP64 inputs. */
+stp_status stp_problem_features(const stp_problem *p, float *x);
+/* Install the proposal for the learned branch from a network output
+ * y[STP_MLP_OUT] (host, or device with flags = STP_MLP_DEVICE); host values
+ * must be finite. The library keeps its own copy (the table is built on the
+ * device in the problem's precision): mixture weights softmax(y[0:8]) as
+ * cumulative sums, goal-time means y[8:16] H and standard deviations
+ * exp(clamp(y[16:24], -7, 2)) H, waypoints q_lo + (clamp(y, -1, 1) + 1)/2
+ * (q_hi - q_lo). A learned worker (Philox slot 12 below ceil(0.9 2^24)) draws
+ * q_r uniformly within +-0.1 of each joint range around waypoint i (slot 13,
+ * 16 equally likely), clipped to C; in interval root it also draws
+ * T = mean_k + sd_k z (component k from the cumulative weights with slot 14,
+ * z by Box-Muller from slots 15-16) and keeps T only inside the sampled
+ * group's uniform interval. The paper's GPU form has a learned proposal but
+ * fixes none of these choices. May be called again between plans. */
+stp_status stp_set_proposal(stp_problem *p, const float *y, int flags);
 
 #ifdef __cplusplus
 }

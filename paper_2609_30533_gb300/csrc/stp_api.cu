@@ -71,6 +71,7 @@ struct stp_problem {
     unsigned long long* d_counters = nullptr;  // [2]: points, pairs of stp_check_edges
     std::string last_error;
     bool planned = false;
+    bool has_proposal = false;  // learned branch table set by stp_set_proposal
     // profiling
     int profiling = 0;
     std::vector<cudaEvent_t> prof_ev;
@@ -296,6 +297,8 @@ size_t layout_state(stp_problem* p, char* base, R** blob_out, size_t blob_bytes,
     s.U_hist = cv.take<double>(std::max(p->prm.max_iters, 1));
     s.path = cv.take<R>((size_t)p->path_cap * kDP);
     s.path_len = cv.take<int>(1);
+    s.prop = cv.take<R>(kPropSize);
+    s.prop_y = cv.take<float>(kPropY);
     if (base) {
         s.N = N;
         s.W = W;
@@ -312,6 +315,7 @@ size_t layout_state(stp_problem* p, char* base, R** blob_out, size_t blob_bytes,
         s.H = p->prm.t_max;
         s.thr_guided = (unsigned)std::ceil(p->prm.p_guided * 16777216.0);
         s.thr_new = (unsigned)std::floor(p->prm.p_new * 16777216.0);
+        s.learned = p->prm.learned;
         s.key0 = (unsigned)(p->prm.seed & 0xffffffffull);
         s.key1 = (unsigned)(p->prm.seed >> 32);
         s.problem_id = p->prm.problem_id;
@@ -656,7 +660,7 @@ stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, 
     if (!(P.eta > 0) || !(P.edge_res > 0) || !(P.env_dt > 0) || !(P.t_max > 0)) return STP_ERR_INVALID;
     if (!(P.p_new >= 0 && P.p_new <= 1) || !(P.p_guided >= 0 && P.p_guided <= 1)) return STP_ERR_INVALID;
     if (P.precision != 0 && P.precision != 1) return STP_ERR_INVALID;
-    if (P.learned != 0 || P.capacity < 0 || P.iters_per_graph < 0) return STP_ERR_INVALID;
+    if ((P.learned != 0 && P.learned != 1) || P.capacity < 0 || P.iters_per_graph < 0) return STP_ERR_INVALID;
 
     stp_problem* p = new (std::nothrow) stp_problem();
     if (!p) return STP_ERR_CUDA;
@@ -771,6 +775,11 @@ stp_status stp_plan(stp_problem* p, double* arrival_U, double* length_C, int* n_
     st.first_solution_iter = -1;
     st.U = kInfD;
     st.C = kInfD;
+    if (p->prm.learned && !p->has_proposal) {
+        p->last_error = "learned sampling needs a proposal (stp_set_proposal)";
+        g_last_error = p->last_error;
+        return STP_ERR_INVALID;
+    }
     const int d = p->dof;
     bool same = true;
     for (int j = 0; j < d; ++j) same = same && p->qs[j] == p->qg[j];
@@ -1100,6 +1109,65 @@ struct stp_batch {
     std::string last_error;
 };
 
+// ---------------------------------------------------------------------------
+// Learned proposal: network output -> sampler table; problem summary.
+// ---------------------------------------------------------------------------
+template <typename R>
+static stp_status set_proposal_impl(stp_problem* p, const float* y, int flags) {
+    State<R>& S = state_of<R>(p);
+    STP_CUDA(p, cudaMemcpyAsync(S.prop_y, y, sizeof(float) * kPropY,
+                                (flags & STP_MLP_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                p->stream));
+    STP_CUDA(p, launch_set_proposal<R>(geom_of<R>(p), S, p->stream));
+    STP_CUDA(p, cudaStreamSynchronize(p->stream));
+    return STP_OK;
+}
+
+extern "C" stp_status stp_set_proposal(stp_problem* p, const float* y, int flags) {
+    clear_stale_error();
+    if (!p || !y || (flags & ~STP_MLP_DEVICE)) return STP_ERR_INVALID;
+    if (!(flags & STP_MLP_DEVICE)) {
+        for (int i = 0; i < kPropY; ++i)
+            if (!std::isfinite(y[i])) return STP_ERR_INVALID;
+    }
+    stp_status s = p->precision == 0 ? set_proposal_impl<float>(p, y, flags) : set_proposal_impl<double>(p, y, flags);
+    if (s == STP_OK) p->has_proposal = true;
+    return s;
+}
+
+extern "C" stp_status stp_problem_features(const stp_problem* p, float* x) {
+    if (!p || !x) return STP_ERR_INVALID;
+    double f[STP_MLP_IN] = {0};
+    const int d = p->dof;
+    for (int j = 0; j < d; ++j) {
+        f[j] = 2.0 * (p->qs[j] - p->qlo[j]) / (p->qhi[j] - p->qlo[j]) - 1.0;
+        f[7 + j] = 2.0 * (p->qg[j] - p->qlo[j]) / (p->qhi[j] - p->qlo[j]) - 1.0;
+    }
+    if (d == 2) f[14] = 1.0;
+    else if (d == 6) f[15] = 1.0;
+    else if (d == 7) f[16] = 1.0;
+    if (p->M > 0) {
+        double acc[7] = {0};
+        for (int m = 0; m < p->M; ++m) {
+            const double* w0 = &p->way[(size_t)m * p->K * 4];
+            const double* w1 = &p->way[((size_t)m * p->K + p->K - 1) * 4];
+            for (int i = 0; i < 3; ++i) {
+                acc[i] += w0[1 + i];
+                if (p->K > 1) acc[3 + i] += (w1[1 + i] - w0[1 + i]) / (w1[0] - w0[0]);
+            }
+            acc[6] += p->obs_r[m];
+        }
+        for (int i = 0; i < 7; ++i) f[17 + i] = acc[i] / p->M;
+    }
+    double D = 0.0;
+    for (int j = 0; j < d; ++j) D += (p->qg[j] - p->qs[j]) * (p->qg[j] - p->qs[j]);
+    D = std::sqrt(D);
+    f[24] = p->prm.t_max / 60.0;
+    f[25] = D / p->vmax / p->prm.t_max;
+    for (int i = 0; i < STP_MLP_IN; ++i) x[i] = (float)f[i];
+    return STP_OK;
+}
+
 extern "C" stp_status stp_batch_create(stp_problem* const* problems, int n, const stp_batch_params* bp,
                                        stp_batch** out) {
     clear_stale_error();
@@ -1177,6 +1245,12 @@ extern "C" stp_status stp_batch_plan(stp_batch* b, stp_stats* stats, double* bat
     clear_stale_error();
     if (!b) return STP_ERR_INVALID;
     const int n = (int)b->probs.size();
+    for (int i = 0; i < n; ++i)
+        if (b->probs[i]->prm.learned && !b->probs[i]->has_proposal) {
+            b->last_error = "a learned member problem has no proposal (stp_set_proposal)";
+            g_last_error = b->last_error;
+            return STP_ERR_INVALID;
+        }
     cudaStream_t st = b->stream;
     auto fail = [&](cudaError_t e, const char* where) {
         char buf[256];

@@ -32,6 +32,9 @@ constexpr int kMaxTiles = 64;   // node tiles per query (partials per query)
 constexpr int kMaxQTiles = kMaxWorkers / kQT;
 constexpr int kNodeTileMin = 128;
 constexpr unsigned kWaitLimit = 1u << 24;  // bounded spin on mbarriers
+constexpr int kPropY = 160;                 // network output floats
+constexpr int kPropSize = 24 + 16 * kMaxDof;
+constexpr unsigned kThrLearned = 15099495u;  // learned iff m < ceil(0.9 2^24)
 
 enum ErrBits { kErrCapacity = 1, kErrTimeout = 2, kErrInternal = 4 };
 
@@ -118,6 +121,12 @@ struct State {
     // guided iff m < thr_guided = ceil(p_guided 2^24); new root iff m <= thr_new = floor(p_new 2^24).
     unsigned thr_guided, thr_new;
     R qs[kMaxDof], qg[kMaxDof];
+    // learned branch: table [kPropSize] = cumulative mixture weights (8), goal
+    // time means (8) and standard deviations (8) in seconds, waypoints
+    // [16][kMaxDof]; built from the network output prop_y [160].
+    int learned;
+    R* prop;
+    float* prop_y;
     // forward arena
     R* fx; int* fpar; R* fcost; int* fiter;
     // backward arena [N][cap_s]
@@ -397,6 +406,8 @@ cudaError_t launch_plan_reset(const Geom<R>& g, const State<R>& s, int max_iters
 constexpr int kIterKernels = 7;
 extern const char* const kIterKernelNames[kIterKernels];
 // ev (optional, kIterKernels + 1 events): recorded before each kernel and after the last.
+template <typename R>
+cudaError_t launch_set_proposal(const Geom<R>& g, const State<R>& s, cudaStream_t st);
 template <typename R>
 cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cudaStream_t st,
                              cudaEvent_t* ev = nullptr);

@@ -198,6 +198,91 @@ __device__ R sample_goal_time(const State<R>& S, int g, uint32_t m_coin, R u_pos
 }
 
 // ---------------------------------------------------------------------------
+// Learned sampling branch (the method's GPU form: a learned proposal mixed
+// with 10 % plain samples). A learned worker (slot-12 coin) draws q_r
+// uniformly within +-0.1 of each joint range around waypoint i (slot 13),
+// clipped to C, reusing the plain q_r uniforms; in interval root its goal
+// time comes from the mixture (component by slot 14, Box-Muller normal from
+// slots 15-16) when that time lies in the sampled group's uniform interval.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void learned_q(const Geom<R>& G, const State<R>& S, const uint32_t* d, R* qr) {
+    const int i = (int)(((unsigned long long)(d[13] >> 8) * 16ull) >> 24);
+    const R* wq = S.prop + 24 + i * kMaxDof;
+    for (int j = 0; j < G.dof; ++j) {
+        const R half = R(0.1) * (G.qhi[j] - G.qlo[j]);
+        R q = wq[j] + half * (R(2) * uni_r<R>(d[4 + j]) - R(1));
+        q = q > G.qlo[j] ? q : G.qlo[j];
+        qr[j] = q < G.qhi[j] ? q : G.qhi[j];
+    }
+}
+
+__device__ __forceinline__ float log_r(float x) { return logf(x); }
+__device__ __forceinline__ double log_r(double x) { return log(x); }
+__device__ __forceinline__ float cos_r(float x) { return cosf(x); }
+__device__ __forceinline__ double cos_r(double x) { return cos(x); }
+__device__ __forceinline__ float exp_r(float x) { return expf(x); }
+__device__ __forceinline__ double exp_r(double x) { return exp(x); }
+
+template <typename R>
+__device__ __forceinline__ R learned_T(const State<R>& S, const uint32_t* d) {
+    const R u = uni_r<R>(d[14]);
+    int k = 0;
+    while (k < 7 && !(u < S.prop[k])) ++k;
+    const R u1 = R(1) - uni_r<R>(d[15]), u2 = uni_r<R>(d[16]);
+    const R z = sqrt(R(-2) * log_r(u1)) * cos_r(R(6.283185307179586476925) * u2);
+    return S.prop[8 + k] + S.prop[16 + k] * z;
+}
+
+// Proposal table from the network output (one thread; same operation order
+// as the reference construction).
+template <typename R>
+__global__ void k_set_proposal(Geom<R> G, State<R> S) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const float* y = S.prop_y;
+    R amax = (R)y[0];
+    for (int k = 1; k < 8; ++k) amax = (R)y[k] > amax ? (R)y[k] : amax;
+    R e[8], tot = R(0);
+    for (int k = 0; k < 8; ++k) {
+        e[k] = exp_r((R)y[k] - amax);
+        tot += e[k];
+    }
+    R acc = R(0);
+    for (int k = 0; k < 8; ++k) {
+        acc += e[k];
+        S.prop[k] = acc / tot;
+    }
+    S.prop[7] = R(1);
+    const R H = (R)S.H;
+    for (int k = 0; k < 8; ++k) {
+        S.prop[8 + k] = (R)y[8 + k] * H;
+        R s = (R)y[16 + k];
+        s = s > R(-7) ? s : R(-7);
+        s = s < R(2) ? s : R(2);
+        S.prop[16 + k] = exp_r(s) * H;
+    }
+    for (int i = 0; i < 16; ++i)
+        for (int j = 0; j < kMaxDof; ++j) {
+            R v = R(0);
+            if (j < G.dof) {
+                R u = (R)y[24 + 8 * i + j];
+                u = u > R(-1) ? u : R(-1);
+                u = u < R(1) ? u : R(1);
+                v = G.qlo[j] + (u + R(1)) * R(0.5) * (G.qhi[j] - G.qlo[j]);
+            }
+            S.prop[24 + i * kMaxDof + j] = v;
+        }
+}
+
+template <typename R>
+cudaError_t launch_set_proposal(const Geom<R>& G, const State<R>& S, cudaStream_t st) {
+    k_set_proposal<R><<<1, 1, 0, st>>>(G, S);
+    return cudaGetLastError();
+}
+template cudaError_t launch_set_proposal<float>(const Geom<float>&, const State<float>&, cudaStream_t);
+template cudaError_t launch_set_proposal<double>(const Geom<double>&, const State<double>&, cudaStream_t);
+
+// ---------------------------------------------------------------------------
 // Root recycling (Algorithm 3), one thread.
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -451,17 +536,30 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
     S.w_edge[w] = -1;
     S.w_root_edge[w] = -1;
     S.w_nnkey[w] = ~0ull;
-    uint32_t d[12];
+    uint32_t d[20];
     philox4x32_10(0, (uint32_t)w, (uint32_t)k, S.problem_id, S.key0, S.key1, d);
     philox4x32_10(1, (uint32_t)w, (uint32_t)k, S.problem_id, S.key0, S.key1, d + 4);
     philox4x32_10(2, (uint32_t)w, (uint32_t)k, S.problem_id, S.key0, S.key1, d + 8);
+    bool lrn = false;
+    if (S.learned) {
+        philox4x32_10(3, (uint32_t)w, (uint32_t)k, S.problem_id, S.key0, S.key1, d + 12);
+        philox4x32_10(4, (uint32_t)w, (uint32_t)k, S.problem_id, S.key0, S.key1, d + 16);
+        lrn = (d[12] >> 8) < kThrLearned;
+    }
     R qr[kMaxDof];
 #pragma unroll
     for (int j = 0; j < kMaxDof; ++j) qr[j] = (j < dof) ? G.qlo[j] + uni_r<R>(d[4 + j]) * (G.qhi[j] - G.qlo[j]) : R(0);
+    if (lrn) learned_q(G, S, d, qr);
 
     if (S.variant == 0) {
         const int g = (int)(((unsigned long long)(d[0] >> 8) * (unsigned long long)S.N) >> 24);
-        const R Tr = sample_goal_time(S, g, d[1] >> 8, uni_r<R>(d[2]));
+        R Tr = sample_goal_time(S, g, d[1] >> 8, uni_r<R>(d[2]));
+        if (lrn) {
+            const R Tl = learned_T(S, d);
+            const R width = (R)c->width;
+            const R glo = (R)c->Lg + (R)g * width;
+            if (Tl >= glo && Tl < glo + width) Tr = Tl;
+        }
         S.w_T[w] = Tr;
         // Conditional query time (Eq. conditional-query-time).
         const R lo = qdist(S.qs, qr, dof) / G.vmax;

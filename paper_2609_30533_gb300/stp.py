@@ -142,6 +142,10 @@ def lib():
     L.stp_mlp_profile.restype = C.c_int
     L.stp_mlp_last_error.argtypes = [C.c_void_p]
     L.stp_mlp_last_error.restype = C.c_char_p
+    L.stp_problem_features.argtypes = [C.c_void_p, _F]
+    L.stp_problem_features.restype = C.c_int
+    L.stp_set_proposal.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
+    L.stp_set_proposal.restype = C.c_int
     _LIB = L
     return L
 
@@ -152,7 +156,7 @@ EXPORTED = ["stp_create_problem", "stp_plan", "stp_check_edges", "stp_free", "st
             "stp_check_edges_noalloc", "stp_batch_create", "stp_batch_plan", "stp_batch_path", "stp_batch_free",
             "stp_mlp_create", "stp_mlp_free", "stp_mlp_set_stream", "stp_mlp_set_params", "stp_mlp_get_params",
             "stp_mlp_forward", "stp_mlp_gradients", "stp_mlp_train_step", "stp_mlp_set_profiling",
-            "stp_mlp_profile", "stp_mlp_last_error"]
+            "stp_mlp_profile", "stp_mlp_last_error", "stp_problem_features", "stp_set_proposal"]
 
 
 def status_string(s: int) -> str:
@@ -183,7 +187,7 @@ class Problem:
     def __init__(self, *, dof, arm, dh, q_lo, q_hi, spheres, v_max, obs_radius, obs_way, q_start, q_goal,
                  variant=0, n_roots=4, ext_per_iter=64, max_iters=100, budget_ms=0.0, eta=0.1, edge_res=0.01,
                  env_dt=0.02, p_new=0.05, p_guided=0.95, t_max=10.0, seed=0, problem_id=0, precision=0,
-                 capacity=0, iters_per_graph=0):
+                 capacity=0, iters_per_graph=0, learned=0):
         L = lib()
         self.dof = int(dof)
         self.precision = int(precision)
@@ -205,8 +209,8 @@ class Problem:
                                  _dp(obs_r) if len(obs_r) else None, _dp(way) if len(obs_r) else None)
         self.params = StpParams(int(variant), int(n_roots), int(ext_per_iter), int(max_iters), float(budget_ms),
                                 float(eta), float(edge_res), float(env_dt), float(p_new), float(p_guided),
-                                float(t_max), int(seed), int(problem_id), int(precision), 0, int(capacity),
-                                int(iters_per_graph))
+                                float(t_max), int(seed), int(problem_id), int(precision), int(learned),
+                                int(capacity), int(iters_per_graph))
         h = C.c_void_p()
         s = L.stp_create_problem(C.byref(robot), C.byref(obstacles), _dp(arr(q_start)), _dp(arr(q_goal)),
                                  C.byref(self.params), C.byref(h))
@@ -302,6 +306,27 @@ class Problem:
         if s != STP_OK:
             raise StpError(s, "stp_profile")
         return {names[k].decode(): (float(ms[k]), int(la[k])) for k in range(n.value)}
+
+    def features(self) -> np.ndarray:
+        """Proposal-network input x[32] of this problem."""
+        x = np.zeros(MLP_IN, dtype=np.float32)
+        s = lib().stp_problem_features(self.handle, x.ctypes.data_as(C.POINTER(C.c_float)))
+        if s != STP_OK:
+            raise StpError(s, "stp_problem_features")
+        return x
+
+    def set_proposal(self, y):
+        """Learned-branch proposal from a network output y[160] (host array)."""
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        assert y.size == MLP_OUT
+        s = lib().stp_set_proposal(self.handle, y.ctypes.data, 0)
+        if s != STP_OK:
+            raise StpError(s, "stp_set_proposal", self.last_error())
+
+    def set_proposal_device(self, y_ptr: int):
+        s = lib().stp_set_proposal(self.handle, C.c_void_p(y_ptr), MLP_DEVICE)
+        if s != STP_OK:
+            raise StpError(s, "stp_set_proposal", self.last_error())
 
     def tree(self, arena: int):
         n = C.c_int()

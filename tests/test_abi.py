@@ -77,7 +77,7 @@ def _create(prob, params):
 
 
 @pytest.mark.parametrize("bad", [dict(n_roots=0), dict(ext_per_iter=0), dict(variant=7), dict(eta=0.0),
-                                 dict(p_new=1.5), dict(precision=2), dict(learned=1), dict(max_iters=0)])
+                                 dict(p_new=1.5), dict(precision=2), dict(learned=2), dict(max_iters=0)])
 def test_invalid_params_rejected_before_any_device_call(L, bad):
     prob, _ = WL.disc2d(0)
     s, h = _create(prob, _params(**bad))

@@ -271,3 +271,23 @@ def microbench_edges(prob: Problem, n_edges: int, eta: float, H: float, seed: in
     ta = rng.uniform(0.0, 1.0, size=n_edges) * np.maximum(H - dur, 0.0)
     tb = ta + dur
     return qa, ta, qb, tb
+
+
+def random_proposal(prob: Problem, seed: int = 0) -> np.ndarray:
+    """A seeded stand-in for a proposal-network output y[160] (float32): random
+    mixture logits, means of tau in [0.3, 0.9], log standard deviations in
+    [-3, -1], and 16 waypoints scattered around the straight line from q_s to
+    q_g in normalised joint coordinates."""
+    rng = np.random.default_rng(seed)
+    y = np.zeros(160)
+    y[0:8] = rng.normal(size=8)
+    y[8:16] = rng.uniform(0.3, 0.9, size=8)
+    y[16:24] = rng.uniform(-3.0, -1.0, size=8)
+    lo, hi = np.asarray(prob.qlo, float), np.asarray(prob.qhi, float)
+    us = 2 * (np.asarray(prob.qs, float) - lo) / (hi - lo) - 1
+    ug = 2 * (np.asarray(prob.qg, float) - lo) / (hi - lo) - 1
+    for i in range(16):
+        f = (i + 1) / 17
+        y[24 + 8 * i:24 + 8 * i + prob.dof] = (1 - f) * us + f * ug + rng.normal(scale=0.05, size=prob.dof)
+        y[24 + 8 * i + 7] = f * 0.6
+    return y.astype(np.float32)
