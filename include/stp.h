@@ -281,8 +281,10 @@ stp_status stp_goal_grid(stp_problem *p, long *kmin, int *n, unsigned char *free
  * problem summary x[STP_MLP_IN] to y[STP_MLP_OUT]: a mixture of 8 Gaussians
  * over the normalised arrival time tau = U/H (logits y[0:8], means y[8:16],
  * log standard deviations y[16:24], clamped to [-7, 2]) and 16 waypoints
- * (y[24 + 8 i + j]: joint j < 7 normalised to [-1, 1] over the joint box,
- * j = 7 the waypoint time over H); y[152:160] is padding.
+ * (y[24 + 8 i + j]: joint j < 7 as an offset, in coordinates normalised to
+ * [-1, 1] over the joint box, from the straight line (1 - f_i) u_s + f_i u_g
+ * between the normalised start and goal, f_i = (i + 1) / 17; j = 7 the
+ * waypoint time over H); y[152:160] is padding.
  *   x layout: q_s (7, normalised, zero padded), q_g (7), DOF one-hot (3: d = 2,
  *   6, 7), mean over obstacles of (first waypoint x, y, z, mean velocity x, y, z,
  *   radius) (7), H / 60, L_g / H with L_g = D(q_s, q_g) / v_max (2), zeros (6).
@@ -329,6 +331,13 @@ stp_status stp_mlp_set_profiling(stp_mlp *m, int on);
 stp_status stp_mlp_profile(stp_mlp *m, double *gemm_ms, double *gemm_flops);
 const char *stp_mlp_last_error(const stp_mlp *m);
 
+/* Training targets t[STP_MLP_NTGT] of the path found by the last stp_plan or
+ * stp_batch_plan of p: tau = U/H; the path sampled at t_i = (i+1) U / 17,
+ * i = 0..15, by linear interpolation in time (joints normalised to [-1, 1]
+ * as offsets from the straight line between the path's end states, entry 7 =
+ * t_i / H, unused joints 0); d. Computed on the device.
+ * STP_NO_SOLUTION if there is no path of at least two states. */
+stp_status stp_problem_targets(stp_problem *p, float *t);
 /* Problem summary x[STP_MLP_IN] of p (layout above), from its FP64 inputs. */
 stp_status stp_problem_features(const stp_problem *p, float *x);
 /* Install the proposal for the learned branch from a network output
@@ -336,8 +345,9 @@ stp_status stp_problem_features(const stp_problem *p, float *x);
  * must be finite. The library keeps its own copy (the table is built on the
  * device in the problem's precision): mixture weights softmax(y[0:8]) as
  * cumulative sums, goal-time means y[8:16] H and standard deviations
- * exp(clamp(y[16:24], -7, 2)) H, waypoints q_lo + (clamp(y, -1, 1) + 1)/2
- * (q_hi - q_lo). A learned worker (Philox slot 12 below ceil(0.9 2^24)) draws
+ * exp(clamp(y[16:24], -7, 2)) H, waypoints q_lo + (clamp(y + line, -1, 1) +
+ * 1)/2 (q_hi - q_lo) with line the straight-line point of the layout above.
+ * A learned worker (Philox slot 12 below ceil(0.9 2^24)) draws
  * q_r uniformly within +-0.1 of each joint range around waypoint i (slot 13,
  * 16 equally likely), clipped to C; in interval root it also draws
  * T = mean_k + sd_k z (component k from the cumulative weights with slot 14,

@@ -60,7 +60,7 @@ def lib():
                                      C.c_double]
     L.orc_recycle_update.restype = C.c_int
     L.orc_plan.argtypes = [C.POINTER(OrcProblem), C.POINTER(OrcParams), C.POINTER(C.c_void_p)]
-    L.orc_learned_sample.argtypes = [_D, _D, _D, C.c_int, C.c_double, C.c_ulonglong, C.c_uint, C.c_uint,
+    L.orc_learned_sample.argtypes = [_D, _D, _D, _D, _D, C.c_int, C.c_double, C.c_ulonglong, C.c_uint, C.c_uint,
                                      C.c_uint, _I, _D, _D]
     L.orc_learned_sample.restype = C.c_int
     L.orc_plan.restype = C.c_int
@@ -252,17 +252,22 @@ def make_params(params, proposal=None, **over) -> OrcParams:
     return prm
 
 
-def learned_sample(y, qlo, qhi, H, seed, problem_id, k, w):
+def learned_sample(y, qlo, qhi, H, seed, problem_id, k, w, qs=None, qg=None):
     """Learned-branch draws of worker w at iteration k: (learned, waypoint
-    index, q_r, T_l or NaN)."""
+    index, q_r, T_l or NaN). Waypoint offsets are taken from the straight line
+    between qs and qg (default: both at the box centre)."""
     y = np.ascontiguousarray(y, dtype=np.float64)
     lo = np.ascontiguousarray(qlo, dtype=np.float64)
     hi = np.ascontiguousarray(qhi, dtype=np.float64)
     d = len(lo)
+    c = 0.5 * (lo + hi)
+    s0 = np.ascontiguousarray(c if qs is None else qs, dtype=np.float64)
+    g0 = np.ascontiguousarray(c if qg is None else qg, dtype=np.float64)
     qr = np.zeros(d)
     wi = C.c_int()
     Tl = C.c_double()
-    f = lib().orc_learned_sample(_dptr(y), _dptr(lo), _dptr(hi), d, float(H), C.c_ulonglong(seed),
+    f = lib().orc_learned_sample(_dptr(y), _dptr(lo), _dptr(hi), _dptr(s0), _dptr(g0), d, float(H),
+                                 C.c_ulonglong(seed),
                                  C.c_uint(problem_id), C.c_uint(k), C.c_uint(w), C.byref(wi), _dptr(qr),
                                  C.byref(Tl))
     return bool(f), wi.value, qr, Tl.value

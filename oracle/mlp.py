@@ -14,7 +14,9 @@ Layout (shared by the CUDA path through the C ABI, not through code):
   hidden        h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), h3 = relu(W3 h2 + b3)
   output y[160] mixture logits a[0:8], means mu[8:16] (of T/H), log-stds
                 s[16:24] (clamped to [-7, 2]), waypoints [24:152] as 16 x
-                (q normalised (7), t / H), padding [152:160].
+                (q offset (7), t / H), padding [152:160]; the q offset of
+                waypoint i is its normalised configuration minus
+                (1 - f_i) u_s + f_i u_g, f_i = (i + 1) / 17.
   loss          NLL of tau = U/H under the mixture + masked mean squared error
                 of the waypoints (joints beyond d are masked out).
   targets[130]  tau, 16 x 8 waypoint targets, d.
@@ -207,10 +209,14 @@ def adam_step(P, G, state, step: int, lr: float, b1: float = 0.9, b2: float = 0.
 
 
 def path_targets(path: np.ndarray, U: float, H: float, dof: int, lo, hi) -> np.ndarray:
-    """targets[130] of a solution path [n][d+1] (q..., t) arriving at U: tau =
-    U/H, and the path sampled at times (i+1) U / 17, i = 0..15, by linear
-    interpolation in t, joints normalised to [-1, 1]."""
+    """targets[130] of a solution path [n][d+1] (q..., t) from q_s = path[0]
+    to q_g = path[-1], arriving at U: tau = U/H, and the path sampled at times
+    t_i = (i+1) U / 17, i = 0..15, by linear interpolation in t, joints
+    normalised to [-1, 1] and taken relative to the straight line
+    (1 - f_i) u_s + f_i u_g (f_i = (i+1)/17), time entry t_i / H."""
     lo, hi = np.asarray(lo, float), np.asarray(hi, float)
+    us = 2.0 * (path[0, :dof] - lo) / (hi - lo) - 1.0
+    ug = 2.0 * (path[-1, :dof] - lo) / (hi - lo) - 1.0
     t = path[:, dof]
     out = np.zeros(N_TGT)
     out[0] = U / H
@@ -221,7 +227,8 @@ def path_targets(path: np.ndarray, U: float, H: float, dof: int, lo, hi) -> np.n
         f = (ti - t[k]) / (t[k + 1] - t[k])
         q = path[k, :dof] + f * (path[k + 1, :dof] - path[k, :dof])
         o = 1 + i * WP_DIM
-        out[o:o + dof] = 2.0 * (q - lo) / (hi - lo) - 1.0
+        fi = (i + 1) / (N_WP + 1)
+        out[o:o + dof] = (2.0 * (q - lo) / (hi - lo) - 1.0) - ((1.0 - fi) * us + fi * ug)
         out[o + WP_DIM - 1] = ti / H
     out[-1] = dof
     return out

@@ -498,8 +498,11 @@ std::vector<int> recycle_rule(std::vector<Slot>& slots, double U, long kmin, dou
 // Learned sampling branch (the method's GPU form: a learned proposal with 10 %
 // plain samples). A network output y[160] gives a mixture of 8 Gaussians over
 // tau = T/H (logits y[0:8], means y[8:16], log standard deviations y[16:24]
-// clamped to [-7, 2]) and 16 waypoints (y[24 + 8 i + j], joint j normalised to
-// [-1, 1] over the joint box). Readings: a worker is learned when its coin
+// clamped to [-7, 2]) and 16 waypoints as offsets y[24 + 8 i + j] from the
+// straight line: waypoint i, joint j, in coordinates normalised to [-1, 1]
+// over the joint box, is the offset plus (1 - f_i) u_s + f_i u_g with
+// f_i = (i + 1) / 17 and u_s, u_g the normalised start and goal, clipped to
+// [-1, 1]. Readings: a worker is learned when its coin
 // (slot 12) is below p_learned = 0.9 (integer threshold ceil(0.9 2^24)); it
 // then draws q_r uniformly in +-0.1 of each joint's range around waypoint i
 // (slot 13, uniform over the 16), clipped to C, reusing the plain q_r
@@ -517,7 +520,7 @@ struct Learned {
 };
 
 void build_learned(Learned& L, const double* y, const std::vector<double>& lo, const std::vector<double>& hi,
-                   int dof, double H) {
+                   const std::vector<double>& qs, const std::vector<double>& qg, int dof, double H) {
     L.on = true;
     double amax = y[0];
     for (int k = 1; k < 8; ++k) amax = std::max(amax, y[k]);
@@ -537,11 +540,16 @@ void build_learned(Learned& L, const double* y, const std::vector<double>& lo, c
         L.sig[k] = std::exp(std::min(std::max(y[16 + k], -7.0), 2.0)) * H;
     }
     L.wq.assign(16 * (size_t)dof, 0.0);
-    for (int i = 0; i < 16; ++i)
+    for (int i = 0; i < 16; ++i) {
+        const double f = (double)(i + 1) / 17.0;
         for (int j = 0; j < dof; ++j) {
-            double u = std::min(std::max(y[24 + 8 * i + j], -1.0), 1.0);
+            const double us = 2.0 * (qs[j] - lo[j]) / (hi[j] - lo[j]) - 1.0;
+            const double ug = 2.0 * (qg[j] - lo[j]) / (hi[j] - lo[j]) - 1.0;
+            double u = y[24 + 8 * i + j] + ((1.0 - f) * us + f * ug);
+            u = std::min(std::max(u, -1.0), 1.0);
             L.wq[(size_t)i * dof + j] = lo[j] + (u + 1.0) * 0.5 * (hi[j] - lo[j]);
         }
+    }
 }
 
 // q_r of a learned worker (overwrites qr); margins of the clip tests are noted.
@@ -922,7 +930,7 @@ void Planner::extract_path() {
 
 Result Planner::run() {
     int dd = d();
-    if (prm.proposal) build_learned(learned, prm.proposal, P.qlo, P.qhi, dd, prm.H);
+    if (prm.proposal) build_learned(learned, prm.proposal, P.qlo, P.qhi, P.qs, P.qg, dd, prm.H);
     R.dof = dd;
     R.N = prm.N;
     R.variant = prm.variant;
@@ -1352,12 +1360,12 @@ struct orc_result {
 // Learned-branch draws of worker w at iteration k (pins): learned flag,
 // waypoint index, q_r [dof] (plain uniforms overwritten when learned), the
 // mixture goal time T_l (interval root only: NaN when not learned).
-int orc_learned_sample(const double* y, const double* qlo, const double* qhi, int dof, double H,
-                       unsigned long long seed, unsigned problem_id, unsigned k, unsigned w, int* wp_index,
-                       double* qr, double* Tl) {
-    std::vector<double> lo(qlo, qlo + dof), hi(qhi, qhi + dof);
+int orc_learned_sample(const double* y, const double* qlo, const double* qhi, const double* qs, const double* qg,
+                       int dof, double H, unsigned long long seed, unsigned problem_id, unsigned k, unsigned w,
+                       int* wp_index, double* qr, double* Tl) {
+    std::vector<double> lo(qlo, qlo + dof), hi(qhi, qhi + dof), s0(qs, qs + dof), g0(qg, qg + dof);
     Learned L;
-    build_learned(L, y, lo, hi, dof, H);
+    build_learned(L, y, lo, hi, s0, g0, dof, H);
     Draws dr;
     dr.fill(seed, problem_id, k, w, 17);
     const bool lrn = (dr.raw[12] >> 8) < kThrLearned;

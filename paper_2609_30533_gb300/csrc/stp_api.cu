@@ -299,6 +299,7 @@ size_t layout_state(stp_problem* p, char* base, R** blob_out, size_t blob_bytes,
     s.path_len = cv.take<int>(1);
     s.prop = cv.take<R>(kPropSize);
     s.prop_y = cv.take<float>(kPropY);
+    s.tgt = cv.take<float>(STP_MLP_NTGT + 1);
     if (base) {
         s.N = N;
         s.W = W;
@@ -1133,6 +1134,24 @@ extern "C" stp_status stp_set_proposal(stp_problem* p, const float* y, int flags
     stp_status s = p->precision == 0 ? set_proposal_impl<float>(p, y, flags) : set_proposal_impl<double>(p, y, flags);
     if (s == STP_OK) p->has_proposal = true;
     return s;
+}
+
+template <typename R>
+static stp_status targets_impl(stp_problem* p, float* t) {
+    State<R>& S = state_of<R>(p);
+    STP_CUDA(p, launch_path_targets<R>(geom_of<R>(p), S, S.tgt, p->stream));
+    float h[STP_MLP_NTGT + 1];
+    STP_CUDA(p, cudaMemcpyAsync(h, S.tgt, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
+    STP_CUDA(p, cudaStreamSynchronize(p->stream));
+    if (h[STP_MLP_NTGT] == 0.f) return STP_NO_SOLUTION;
+    std::memcpy(t, h, sizeof(float) * STP_MLP_NTGT);
+    return STP_OK;
+}
+
+extern "C" stp_status stp_problem_targets(stp_problem* p, float* t) {
+    clear_stale_error();
+    if (!p || !t) return STP_ERR_INVALID;
+    return p->precision == 0 ? targets_impl<float>(p, t) : targets_impl<double>(p, t);
 }
 
 extern "C" stp_status stp_problem_features(const stp_problem* p, float* x) {

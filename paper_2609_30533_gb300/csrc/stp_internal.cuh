@@ -127,6 +127,7 @@ struct State {
     int learned;
     R* prop;
     float* prop_y;
+    float* tgt;  // [131] training targets of the last path and a written flag
     // forward arena
     R* fx; int* fpar; R* fcost; int* fiter;
     // backward arena [N][cap_s]
@@ -408,6 +409,8 @@ extern const char* const kIterKernelNames[kIterKernels];
 // ev (optional, kIterKernels + 1 events): recorded before each kernel and after the last.
 template <typename R>
 cudaError_t launch_set_proposal(const Geom<R>& g, const State<R>& s, cudaStream_t st);
+template <typename R>
+cudaError_t launch_path_targets(const Geom<R>& g, const State<R>& s, float* out, cudaStream_t st);
 template <typename R>
 cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cudaStream_t st,
                              cudaEvent_t* ev = nullptr);

@@ -261,18 +261,75 @@ __global__ void k_set_proposal(Geom<R> G, State<R> S) {
         s = s < R(2) ? s : R(2);
         S.prop[16 + k] = exp_r(s) * H;
     }
-    for (int i = 0; i < 16; ++i)
+    // Waypoint offsets are taken from the straight line between the
+    // normalised start and goal.
+    for (int i = 0; i < 16; ++i) {
+        const R f = (R)(i + 1) / R(17);
         for (int j = 0; j < kMaxDof; ++j) {
             R v = R(0);
             if (j < G.dof) {
-                R u = (R)y[24 + 8 * i + j];
+                const R us = R(2) * (S.qs[j] - G.qlo[j]) / (G.qhi[j] - G.qlo[j]) - R(1);
+                const R ug = R(2) * (S.qg[j] - G.qlo[j]) / (G.qhi[j] - G.qlo[j]) - R(1);
+                R u = (R)y[24 + 8 * i + j] + ((R(1) - f) * us + f * ug);
                 u = u > R(-1) ? u : R(-1);
                 u = u < R(1) ? u : R(1);
                 v = G.qlo[j] + (u + R(1)) * R(0.5) * (G.qhi[j] - G.qlo[j]);
             }
             S.prop[24 + i * kMaxDof + j] = v;
         }
+    }
 }
+
+// Training targets [130] of the last extracted path (one thread): tau = U/H,
+// the path sampled at t_i = (i+1) U / 17 by linear interpolation in t (the
+// segment with t_k <= t_i < t_k+1, clamped to the path), joints normalised to
+// [-1, 1] and taken relative to the straight line (1 - f_i) u_s + f_i u_g
+// between the path's normalised end states (f_i = (i+1)/17), the time entry
+// t_i / H, and d. out[130] = 1 if written, 0 if the problem has no path of at
+// least two states.
+template <typename R>
+__global__ void k_path_targets(Geom<R> G, State<R> S, float* out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int n = *S.path_len;
+    out[130] = 0.f;
+    if (n < 2) return;
+    const R* P = S.path;
+    const R U = P[(size_t)(n - 1) * kDP + kDP - 1];
+    const R H = (R)S.H;
+    for (int i = 0; i < 130; ++i) out[i] = 0.f;
+    out[0] = (float)(U / H);
+    for (int i = 0; i < 16; ++i) {
+        const R ti = (R)(i + 1) * U / R(17);
+        int cnt = 0;
+        for (int k = 0; k < n; ++k)
+            if (P[(size_t)k * kDP + kDP - 1] <= ti) ++cnt;
+        int k = cnt - 1;
+        k = k < 0 ? 0 : (k > n - 2 ? n - 2 : k);
+        const R* a = P + (size_t)k * kDP;
+        const R* b = a + kDP;
+        const R f = (ti - a[kDP - 1]) / (b[kDP - 1] - a[kDP - 1]);
+        const R fi = (R)(i + 1) / R(17);
+        const R* e = P + (size_t)(n - 1) * kDP;
+        for (int j = 0; j < G.dof; ++j) {
+            const R q = a[j] + f * (b[j] - a[j]);
+            const R span = G.qhi[j] - G.qlo[j];
+            const R us = R(2) * (P[j] - G.qlo[j]) / span - R(1);
+            const R ug = R(2) * (e[j] - G.qlo[j]) / span - R(1);
+            out[1 + 8 * i + j] = (float)((R(2) * (q - G.qlo[j]) / span - R(1)) - ((R(1) - fi) * us + fi * ug));
+        }
+        out[1 + 8 * i + 7] = (float)(ti / H);
+    }
+    out[129] = (float)G.dof;
+    out[130] = 1.f;
+}
+
+template <typename R>
+cudaError_t launch_path_targets(const Geom<R>& G, const State<R>& S, float* out, cudaStream_t st) {
+    k_path_targets<R><<<1, 1, 0, st>>>(G, S, out);
+    return cudaGetLastError();
+}
+template cudaError_t launch_path_targets<float>(const Geom<float>&, const State<float>&, float*, cudaStream_t);
+template cudaError_t launch_path_targets<double>(const Geom<double>&, const State<double>&, float*, cudaStream_t);
 
 template <typename R>
 cudaError_t launch_set_proposal(const Geom<R>& G, const State<R>& S, cudaStream_t st) {

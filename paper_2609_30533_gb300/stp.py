@@ -146,6 +146,8 @@ def lib():
     L.stp_problem_features.restype = C.c_int
     L.stp_set_proposal.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
     L.stp_set_proposal.restype = C.c_int
+    L.stp_problem_targets.argtypes = [C.c_void_p, _F]
+    L.stp_problem_targets.restype = C.c_int
     _LIB = L
     return L
 
@@ -156,7 +158,8 @@ EXPORTED = ["stp_create_problem", "stp_plan", "stp_check_edges", "stp_free", "st
             "stp_check_edges_noalloc", "stp_batch_create", "stp_batch_plan", "stp_batch_path", "stp_batch_free",
             "stp_mlp_create", "stp_mlp_free", "stp_mlp_set_stream", "stp_mlp_set_params", "stp_mlp_get_params",
             "stp_mlp_forward", "stp_mlp_gradients", "stp_mlp_train_step", "stp_mlp_set_profiling",
-            "stp_mlp_profile", "stp_mlp_last_error", "stp_problem_features", "stp_set_proposal"]
+            "stp_mlp_profile", "stp_mlp_last_error", "stp_problem_features", "stp_set_proposal",
+            "stp_problem_targets"]
 
 
 def status_string(s: int) -> str:
@@ -314,6 +317,16 @@ class Problem:
         if s != STP_OK:
             raise StpError(s, "stp_problem_features")
         return x
+
+    def targets(self):
+        """Training targets [130] of the last plan's path, or None without one."""
+        t = np.zeros(MLP_NTGT, dtype=np.float32)
+        s = lib().stp_problem_targets(self.handle, t.ctypes.data_as(C.POINTER(C.c_float)))
+        if s == STP_NO_SOLUTION:
+            return None
+        if s != STP_OK:
+            raise StpError(s, "stp_problem_targets", self.last_error())
+        return t
 
     def set_proposal(self, y):
         """Learned-branch proposal from a network output y[160] (host array)."""

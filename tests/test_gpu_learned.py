@@ -112,3 +112,22 @@ def test_learned_without_proposal_is_rejected():
     with pytest.raises(stp.StpError):
         P.set_proposal(np.full(160, np.nan, dtype=np.float32))
     P.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_path_targets_match_oracle_definition(precision):
+    from paper_2609_30533_gb300 import stp
+    prob, prm = CASES["ur5e-small-recycling"]()
+    P = stp.problem_from(prob, prm, precision=precision)
+    out = P.plan()
+    assert out.status == stp.STP_OK
+    t = P.targets()
+    ref = M.path_targets(out.path, out.U, prm.H, prob.dof, prob.qlo, prob.qhi)
+    assert np.allclose(t, ref, rtol=0, atol=2e-6 if precision == 0 else 1e-7)
+    P.close()
+    prob, prm = WL.disc2d(0)
+    prob.qs = prob.way[0, 0, 1:3].copy()      # start in collision: no path
+    P = stp.problem_from(prob, prm, precision=0)
+    P.plan()
+    assert P.targets() is None
+    P.close()

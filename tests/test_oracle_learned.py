@@ -106,3 +106,18 @@ def test_waypoint_denormalisation_clips_to_the_box():
         if f:
             assert 1.0 - 0.1 * 1.0 - 1e-12 <= q[0] <= 1.0
             assert -2.0 <= q[1] <= -2.0 + 0.1 * 4.0 + 1e-12
+
+
+def test_zero_offsets_put_waypoints_on_the_straight_line():
+    lo, hi = np.array([-np.pi] * 6), np.array([np.pi] * 6)
+    qs, qg = np.full(6, -1.0), np.array([2.0, 0.5, -0.3, 1.0, 0.0, 2.5])
+    half = 0.1 * (hi - lo)
+    seen = set()
+    for w in range(2000):
+        f, i, q, _ = oracle.learned_sample(_y(), lo, hi, 10.0, SEED, PID, 5, w, qs=qs, qg=qg)
+        if not f:
+            continue
+        c = qs + (i + 1) / 17 * (qg - qs)
+        assert np.all(np.abs(q - c) <= half + 1e-12)
+        seen.add(i)
+    assert seen == set(range(16))

@@ -123,11 +123,20 @@ def test_path_targets_on_a_straight_path():
     assert T[0] == 0.5 and T[-1] == 6
     for i in range(16):
         f = (i + 1) / 17
-        q = qs + f * (qg - qs)
         o = 1 + 8 * i
-        assert np.allclose(T[o:o + 6], q / np.pi, atol=1e-15)
+        # a constant-speed straight path has zero offsets from the line
+        assert np.allclose(T[o:o + 6], 0.0, atol=1e-15)
         assert T[o + 6] == 0.0
         assert abs(T[o + 7] - f * U / H) < 1e-15
+    # a detour through a middle state q_m at t = 4: offsets of the piecewise path
+    qm = np.array([1.0, 0.0, 0.5, -0.5, 2.0, 0.3])
+    path = np.array([np.r_[qs, 0.0], np.r_[qm, 4.0], np.r_[qg, U]])
+    T = M.path_targets(path, U, H, 6, lo, hi)
+    for i in range(16):
+        f = (i + 1) / 17
+        t = f * U
+        q = qs + (t / 4.0) * (qm - qs) if t <= 4.0 else qm + ((t - 4.0) / 4.0) * (qg - qm)
+        assert np.allclose(T[1 + 8 * i:7 + 8 * i], (q - (qs + f * (qg - qs))) / np.pi, atol=1e-14)
 
 
 def test_features_of_a_hand_made_problem():

@@ -213,7 +213,7 @@ def arm7_dh(rng) -> np.ndarray:
 
 
 def arm7(seed: int = 0, n_obs: int = 64, H: float = 60.0, variant: int = 1,
-         candidate: Optional[int] = None):
+         candidate: Optional[int] = None, table: str = "arm7"):
     """7-DoF seeded-DH arm among 64 spheres on 8-waypoint paths."""
     rng = np.random.default_rng(3000 + seed)
     dh = arm7_dh(rng)
@@ -221,13 +221,27 @@ def arm7(seed: int = 0, n_obs: int = 64, H: float = 60.0, variant: int = 1,
     way = _waypoint_paths(rng, n_obs, 8, -1.0, 1.0, H, 0.5)
     obs_r = rng.uniform(0.04, 0.1, size=n_obs)
     cands = arm_candidates(rng, 7, N_CANDIDATES)
-    ci = _accepted("arm7", seed) if candidate is None else candidate
+    ci = _accepted(table, seed) if candidate is None else candidate
     qs, qg = cands[ci, 0], cands[ci, 1]
     prob = Problem(dof=7, arm=True, dh=dh, qlo=np.full(7, -math.pi), qhi=np.full(7, math.pi),
                    spheres=spheres, vmax=math.pi / 2, obs_r=obs_r, way=way, qs=qs, qg=qg,
                    name=f"arm7-s{seed}")
     params = Params(variant=variant, n_roots=16, workers=4096, max_iters=100, eta=0.5,
                     res=0.01, dt=0.02, H=H, seed=seed)
+    return prob, params
+
+
+# Learned-proposal study on the 7-DoF distribution: training problems use
+# seeds C4_TRAIN_BASE + i, held-out problems C4_TEST_BASE + i.
+C4_TRAIN_BASE, C4_TEST_BASE = 1_000_000, 2_000_000
+C4_TRAIN_TABLED, C4_TEST_TABLED = 2048, 1000
+
+
+def arm7_c4(split: str, i: int):
+    """Problem i of the learned-proposal study ("train" or "test")."""
+    base = C4_TRAIN_BASE if split == "train" else C4_TEST_BASE
+    prob, params = arm7(seed=base + i, table="c4")
+    params.problem_id = i
     return prob, params
 
 
@@ -276,18 +290,14 @@ def microbench_edges(prob: Problem, n_edges: int, eta: float, H: float, seed: in
 def random_proposal(prob: Problem, seed: int = 0) -> np.ndarray:
     """A seeded stand-in for a proposal-network output y[160] (float32): random
     mixture logits, means of tau in [0.3, 0.9], log standard deviations in
-    [-3, -1], and 16 waypoints scattered around the straight line from q_s to
-    q_g in normalised joint coordinates."""
+    [-3, -1], and 16 small random waypoint offsets (normal, sd 0.05)."""
     rng = np.random.default_rng(seed)
     y = np.zeros(160)
     y[0:8] = rng.normal(size=8)
     y[8:16] = rng.uniform(0.3, 0.9, size=8)
     y[16:24] = rng.uniform(-3.0, -1.0, size=8)
-    lo, hi = np.asarray(prob.qlo, float), np.asarray(prob.qhi, float)
-    us = 2 * (np.asarray(prob.qs, float) - lo) / (hi - lo) - 1
-    ug = 2 * (np.asarray(prob.qg, float) - lo) / (hi - lo) - 1
     for i in range(16):
         f = (i + 1) / 17
-        y[24 + 8 * i:24 + 8 * i + prob.dof] = (1 - f) * us + f * ug + rng.normal(scale=0.05, size=prob.dof)
+        y[24 + 8 * i:24 + 8 * i + prob.dof] = rng.normal(scale=0.05, size=prob.dof)
         y[24 + 8 * i + 7] = f * 0.6
     return y.astype(np.float32)

@@ -60,6 +60,13 @@ def main():
         else:
             mk = lambda c: WL.arm7(seed=idx, n_obs=n_obs, H=H, candidate=c)  # noqa: E731
         table["mixed"][str(idx)] = first_accepted(mk, H)
+    table["c4"] = {}
+    for i in range(WL.C4_TRAIN_TABLED):
+        seed = WL.C4_TRAIN_BASE + i
+        table["c4"][str(seed)] = first_accepted(lambda c: WL.arm7(seed, candidate=c), 60.0)
+    for i in range(WL.C4_TEST_TABLED):
+        seed = WL.C4_TEST_BASE + i
+        table["c4"][str(seed)] = first_accepted(lambda c: WL.arm7(seed, candidate=c), 60.0)
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "accepted_candidates.json")
     with open(path, "w") as f:
         json.dump(table, f, indent=0, sort_keys=True)
