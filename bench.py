@@ -10,6 +10,11 @@ edge validation, ordered insertion, bridge scan and validation, publish, root
 recycling). The metric counts validated edges (extension + bridge edges sent to
 the collision kernel) per second of device time.
 
+Beside the headline line: the batched form on 512 mixed problems (autotuned),
+and the learned-proposal study on the 7-DoF distribution (training data from
+plain plans, the proposal network trained on the tensor cores, held-out
+problems planned plain and learned at the same budget).
+
 Timing: CUDA events on the library's stream around each step; an L2 flush
 (512 MB write) runs between steps outside the events; a second pass of the same
 steps records CUDA events between the kernels inside the captured graphs to give
@@ -268,6 +273,144 @@ def batched(args, rank):
     }
 
 
+def _equal_success_p50(a, b):
+    """Median first-solution time of each arm over its k fastest solves, with
+    k the smaller of the two arms' solved counts (equal success rate)."""
+    fa = np.sort(a.first_ms[a.solved])
+    fb = np.sort(b.first_ms[b.solved])
+    k = min(len(fa), len(fb))
+    if k == 0:
+        return None, None, 0
+    return float(np.median(fa[:k])), float(np.median(fb[:k])), int(k)
+
+
+def learned(args, rank):
+    """Learned proposal study on the 7-DoF distribution (seeded DH, 48 link
+    spheres, 64 obstacles on 8-waypoint paths, 60 s horizon): training data
+    from plain batched plans of the training problems (both allocation
+    variants, two planner seeds), the proposal network trained on the tensor
+    cores with validation early stopping, then the held-out problems planned
+    plain and learned (batched, same W and iteration budget), a sample of them
+    planned one at a time, and the network's GEMM throughput at a large
+    training batch."""
+    import dataclasses
+
+    from paper_2609_30533_gb300 import proposal as PR
+    from paper_2609_30533_gb300 import stp
+
+    W, iters = args.learned_workers, args.learned_iters
+
+    def make(split, idxs, learned_flag=0, variant=1, seed=None):
+        out = []
+        for i in idxs:
+            prob, prm = WL.arm7_c4(split, i)
+            prm = dataclasses.replace(prm, variant=variant, workers=W, max_iters=iters,
+                                      seed=(prm.seed if seed is None else seed))
+            out.append(stp.problem_from(prob, prm, precision=0, iters_per_graph=16, learned=learned_flag))
+        return out
+
+    def run_chunks(split, n, learned_flag, variant, net=None, seed=None):
+        outs, X, T = [], [], []
+        for c in range(0, n, 512):
+            probs = make(split, range(c, min(n, c + 512)), learned_flag, variant, seed)
+            if net is not None:
+                PR.install(net, probs)
+            o = PR.plan_batch(probs)
+            if split == "train":
+                x, t = PR.collect(probs, o)
+                X.append(x)
+                T.append(t)
+            outs.append(o)
+            for P in probs:
+                P.close()
+        o = PR.Outcome(np.concatenate([x.solved for x in outs]), np.concatenate([x.first_ms for x in outs]),
+                       np.concatenate([x.first_iter for x in outs]), np.concatenate([x.U for x in outs]),
+                       float(sum(x.batch_ms for x in outs)))
+        return o, X, T
+
+    t0 = time.time()
+    Xs, Ts = [], []
+    for variant in (1, 0):
+        for sd in (0, 1):
+            _, X, T = run_chunks("train", args.learned_train, 0, variant, seed=sd)
+            Xs += X
+            Ts += T
+    X, T = np.concatenate(Xs), np.concatenate(Ts)
+    gen_s = time.time() - t0
+    net = stp.Mlp(4096)
+    net.set_params(PR.init_params(rank))
+    t1 = time.time()
+    log = PR.train(net, X, T, args.learned_steps, 128, 3e-4, seed=rank)
+    train_s = time.time() - t1
+
+    def arm(o):
+        return {"solved": int(o.solved.sum()), "success_rate": float(o.solved.mean()), "batch_ms": o.batch_ms}
+
+    res = {}
+    solvable = {}
+    for variant, name in ((1, "recycling"), (0, "interval")):
+        op, _, _ = run_chunks("test", args.learned_test, 0, variant)
+        ol, _, _ = run_chunks("test", args.learned_test, 1, variant, net=net)
+        both = op.solved & ol.solved
+        solvable[variant] = np.nonzero(op.solved | ol.solved)[0][:args.learned_single]
+        pe, le, k = _equal_success_p50(op, ol)
+        res[name] = {
+            "plain_batched": arm(op), "learned_batched": arm(ol),
+            "equal_success": {"k": k, "plain_p50_first_ms": pe, "learned_p50_first_ms": le},
+            "common_solved": int(both.sum()),
+            "plain_p50_first_ms_common": float(np.median(op.first_ms[both])) if both.any() else None,
+            "learned_p50_first_ms_common": float(np.median(ol.first_ms[both])) if both.any() else None,
+            "plain_p50_first_iter_common": float(np.median(op.first_iter[both])) if both.any() else None,
+            "learned_p50_first_iter_common": float(np.median(ol.first_iter[both])) if both.any() else None,
+            "plain_mean_arrival_common": float(np.mean(op.U[both])) if both.any() else None,
+            "learned_mean_arrival_common": float(np.mean(ol.U[both])) if both.any() else None,
+        }
+    # One problem at a time on held-out problems that either batched arm
+    # solved (the first --learned-single of them), plain and learned.
+    single = {}
+    for variant, name in ((1, "recycling"), (0, "interval")):
+        for flag, arm_name in ((0, "plain"), (1, "learned")):
+            probs = make("test", [int(i) for i in solvable[variant]], flag, variant)
+            if flag:
+                PR.install(net, probs)
+            fs = []
+            for P in probs:
+                out = P.plan()
+                if out.stats["first_solution_iter"] >= 0:
+                    fs.append(out.stats["first_solution_ms"])
+                P.close()
+            single["%s_%s" % (name, arm_name)] = {
+                "problems": len(probs), "solved": len(fs),
+                "p50_first_ms": float(np.median(fs)) if fs else None}
+    # Tensor-core GEMM throughput of one training step at a large batch.
+    Bbig = 16384
+    big = stp.Mlp(Bbig)
+    big.set_params(PR.init_params(1))
+    rng = np.random.default_rng(rank)
+    Xb = X[rng.integers(0, len(X), size=Bbig)]
+    Tb = T[rng.integers(0, len(T), size=Bbig)]
+    big.train_step(Xb, Tb, 0.0)
+    big.set_profiling(True)
+    for _ in range(3):
+        big.train_step(Xb, Tb, 0.0)
+    gms, gfl = big.profile()
+    big.close()
+    net.close()
+    peak = float(_peaks().get("bf16_tflops", 1917.3))
+    gemm_tf = gfl / (gms * 1e-3) / 1e12 if gms > 0 else 0.0
+    return {
+        "workload": "7-DoF seeded DH, 48 spheres, 64 obstacles, H 60 s; W %d, %d iterations" % (W, iters),
+        "train": {"problems": args.learned_train, "runs_per_problem": 4, "samples": int(len(X)),
+                  "gen_s": gen_s, "steps": args.learned_steps, "best_step": log.best_step,
+                  "val_loss_first": log.val[0][1], "val_loss_best": log.best_val, "train_s": train_s},
+        "heldout_problems": args.learned_test,
+        "batched": res,
+        "single_sample": single,
+        "mlp_gemm": {"batch": Bbig, "tflops": gemm_tf, "peak_tflops": peak, "frac": gemm_tf / peak,
+                     "note": "BF16 tcgen05 GEMMs of a forward + backward training step, CUDA events per GEMM"},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -285,7 +428,14 @@ def main():
     ap.add_argument("--tune-iters", type=int, default=24)
     ap.add_argument("--plain-sample", type=int, default=48)
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--only", default="", choices=["", "micro", "batch"],
+    ap.add_argument("--learned-train", type=int, default=2048)
+    ap.add_argument("--learned-test", type=int, default=1000)
+    ap.add_argument("--learned-steps", type=int, default=1500)
+    ap.add_argument("--learned-workers", type=int, default=256)
+    ap.add_argument("--learned-iters", type=int, default=96)
+    ap.add_argument("--learned-single", type=int, default=32)
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--only", default="", choices=["", "micro", "batch", "learned"],
                     help="micro: run only the collision microbenchmark (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -320,6 +470,9 @@ def main():
         return
     if args.only == "batch":
         print(json.dumps({"batched": batched(args, rank)}))
+        return
+    if args.only == "learned":
+        print(json.dumps({"learned": learned(args, rank)}))
         return
 
     def step_timed():
@@ -402,6 +555,7 @@ def main():
 
     micro, peak = microbench(args, P, prob, prm, stream, flush, rank, local)
     batch_result = None if args.no_batch else batched(args, rank)
+    learned_result = None if args.no_learned else learned(args, rank)
     n = args.micro_edges
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = float(_peaks().get("sm_max_mhz", 2070.0))
@@ -460,6 +614,8 @@ def main():
         line["clocks"] = clk
     if not args.no_batch:
         line["batched"] = batch_result
+    if not args.no_learned:
+        line["learned"] = learned_result
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line))
