@@ -42,6 +42,11 @@ sys.path.insert(0, ROOT)
 import workloads as WL  # noqa: E402
 
 WORKLOAD = "ur5e-6dof-32sph-16obs-recycling-N8-W1024"
+# DRAM bytes per planner collision launch on this workload, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum, mean of an extension
+# and a bridge launch of the same iteration). Must be retaken whenever the
+# collision kernel changes.
+VALIDATE_DRAM_BYTES_PER_LAUNCH = 189.7e3
 METRIC = "validated space-time edges/s"
 UNIT = "edges/s"
 FLUSH_BYTES = 512 << 20
@@ -284,6 +289,33 @@ def _equal_success_p50(a, b):
     return float(np.median(fa[:k])), float(np.median(fb[:k])), int(k)
 
 
+def mlp_throughput(rank, B=16384, reps=3):
+    """Tensor-core GEMMs of proposal-network training steps at batch B on
+    synthetic inputs and targets (CUDA events around each GEMM)."""
+    from paper_2609_30533_gb300 import proposal as PR
+    from paper_2609_30533_gb300 import stp
+    rng = np.random.default_rng(rank)
+    X = np.zeros((B, stp.MLP_IN), dtype=np.float32)
+    X[:, :26] = rng.uniform(-1, 1, size=(B, 26))
+    T = np.zeros((B, stp.MLP_NTGT), dtype=np.float32)
+    T[:, 0] = rng.uniform(0.05, 0.5, size=B)
+    T[:, 1:-1] = rng.normal(scale=0.1, size=(B, 128))
+    T[:, -1] = 7
+    net = stp.Mlp(B)
+    net.set_params(PR.init_params(1))
+    net.train_step(X, T, 0.0)
+    net.set_profiling(True)
+    for _ in range(reps):
+        net.train_step(X, T, 0.0)
+    gms, gfl = net.profile()
+    net.close()
+    peak = float(_peaks().get("bf16_tflops", 1917.3))
+    tf = gfl / (gms * 1e-3) / 1e12 if gms > 0 else 0.0
+    return {"batch": B, "gemm_ms_per_step": gms / reps, "gemm_flops_per_step": gfl / reps, "tflops": tf,
+            "peak_tflops": peak, "frac": tf / peak,
+            "note": "BF16 tcgen05 GEMMs of forward + backward training steps, CUDA events per GEMM"}
+
+
 def learned(args, rank):
     """Learned proposal study on the 7-DoF distribution (seeded DH, 48 link
     spheres, 64 obstacles on 8-waypoint paths, 60 s horizon): training data
@@ -382,22 +414,7 @@ def learned(args, rank):
             single["%s_%s" % (name, arm_name)] = {
                 "problems": len(probs), "solved": len(fs),
                 "p50_first_ms": float(np.median(fs)) if fs else None}
-    # Tensor-core GEMM throughput of one training step at a large batch.
-    Bbig = 16384
-    big = stp.Mlp(Bbig)
-    big.set_params(PR.init_params(1))
-    rng = np.random.default_rng(rank)
-    Xb = X[rng.integers(0, len(X), size=Bbig)]
-    Tb = T[rng.integers(0, len(T), size=Bbig)]
-    big.train_step(Xb, Tb, 0.0)
-    big.set_profiling(True)
-    for _ in range(3):
-        big.train_step(Xb, Tb, 0.0)
-    gms, gfl = big.profile()
-    big.close()
     net.close()
-    peak = float(_peaks().get("bf16_tflops", 1917.3))
-    gemm_tf = gfl / (gms * 1e-3) / 1e12 if gms > 0 else 0.0
     return {
         "workload": "7-DoF seeded DH, 48 spheres, 64 obstacles, H 60 s; W %d, %d iterations" % (W, iters),
         "train": {"problems": args.learned_train, "runs_per_problem": 4, "samples": int(len(X)),
@@ -406,8 +423,7 @@ def learned(args, rank):
         "heldout_problems": args.learned_test,
         "batched": res,
         "single_sample": single,
-        "mlp_gemm": {"batch": Bbig, "tflops": gemm_tf, "peak_tflops": peak, "frac": gemm_tf / peak,
-                     "note": "BF16 tcgen05 GEMMs of a forward + backward training step, CUDA events per GEMM"},
+        "mlp_gemm": mlp_throughput(rank),
     }
 
 
@@ -435,7 +451,7 @@ def main():
     ap.add_argument("--learned-iters", type=int, default=96)
     ap.add_argument("--learned-single", type=int, default=32)
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--only", default="", choices=["", "micro", "batch", "learned"],
+    ap.add_argument("--only", default="", choices=["", "micro", "batch", "learned", "mlp"],
                     help="micro: run only the collision microbenchmark (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -473,6 +489,9 @@ def main():
         return
     if args.only == "learned":
         print(json.dumps({"learned": learned(args, rank)}))
+        return
+    if args.only == "mlp":
+        print(json.dumps({"mlp_gemm": mlp_throughput(rank)}))
         return
 
     def step_timed():
@@ -598,7 +617,8 @@ def main():
                 "note": "per step: stp_create_problem from host arrays, stp_plan, path read back, stp_free"},
         "gpu_launches": launches * world,
         "roofline": {"bound": "alu", "kernel": "k_validate", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak if peak else None, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
+                     "traffic": VALIDATE_DRAM_BYTES_PER_LAUNCH,
                      "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz (max SM clock)" % (
                          n_sm, max_mhz),
                      "launches": val_launches, "avg_launch_ms": val_ms / max(val_launches, 1),
