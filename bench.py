@@ -289,7 +289,7 @@ def _equal_success_p50(a, b):
     return float(np.median(fa[:k])), float(np.median(fb[:k])), int(k)
 
 
-def mlp_throughput(rank, B=16384, reps=3):
+def mlp_throughput(rank, B=65536, reps=3):
     """Tensor-core GEMMs of proposal-network training steps at batch B on
     synthetic inputs and targets (CUDA events around each GEMM)."""
     from paper_2609_30533_gb300 import proposal as PR
