@@ -239,9 +239,11 @@ __device__ __forceinline__ void check_point_f32(const Geom<float>& G, const floa
                 const int m = m0 + 2 * h + u;
                 if (m < G.M) {
                     obstacle_at_f32(way + G.K * m, vel + G.K * m, tim + 2 * m, G.K, t, x[u], y[u], z[u]);
-                    x[u] -= G.ref[0];
-                    y[u] -= G.ref[1];
-                    z[u] -= G.ref[2];
+                    if (!ARM) {
+                        x[u] -= G.ref[0];
+                        y[u] -= G.ref[1];
+                        z[u] -= G.ref[2];
+                    }
                     r[u] = UNI ? ro_uni : rad[m];
                     b[u] = x[u] * x[u] + y[u] * y[u] + z[u] * z[u] - r[u] * r[u];
                 } else {
@@ -268,7 +270,7 @@ __device__ __forceinline__ void check_point_f32(const Geom<float>& G, const floa
             frame_identity(F);
             for (int j = 0; j <= G.dof; ++j) {
                 if (j > 0) frame_step(F, G.a[j - 1], G.d[j - 1], G.ca[j - 1], G.sa[j - 1], q[j - 1] + G.th0[j - 1]);
-                const float ox = F.o[0] - G.ref[0], oy = F.o[1] - G.ref[1], oz = F.o[2] - G.ref[2];
+                const float ox = F.o[0], oy = F.o[1], oz = F.o[2];
                 const int s0 = G.link_start[j], s1 = G.link_start[j + 1];
                 int s = s0;
                 for (; s + 1 < s1; s += 2) {
