@@ -11,9 +11,10 @@ recycling). The metric counts validated edges (extension + bridge edges sent to
 the collision kernel) per second of device time.
 
 Beside the headline line: the batched form on 512 mixed problems (autotuned),
-and the learned-proposal study on the 7-DoF distribution (training data from
+the learned-proposal study on the 7-DoF distribution (training data from
 plain plans, the proposal network trained on the tensor cores, held-out
-problems planned plain and learned at the same budget).
+problems planned plain and learned at the same budget), and the allocation
+ablation (root recycling against a fixed forest over broad arrival ranges).
 
 Timing: CUDA events on the library's stream around each step; an L2 flush
 (512 MB write) runs between steps outside the events; a second pass of the same
@@ -289,6 +290,49 @@ def _equal_success_p50(a, b):
     return float(np.median(fa[:k])), float(np.median(fb[:k])), int(k)
 
 
+def sweep(args, rank):
+    """Allocation ablation and broad-range sweep on the UR5e workload with 8
+    obstacles (the scene keeps its 15 s obstacle motion; only the arrival-time
+    range H changes): root recycling against no recycling (fixed forest) over
+    H = 25 / 50 / 100 s (16 roots, W 512), root counts 8..128 (W 512, H 100 s)
+    and W 128..2048 (16 roots, H 100 s). Each condition plans the same problems
+    in one batch for a fixed iteration budget; reported: solved count, mean
+    arrival over the problems both variants solved, median first-solution time."""
+    import dataclasses
+
+    from paper_2609_30533_gb300 import proposal as PR
+    from paper_2609_30533_gb300 import stp
+
+    n, iters = args.sweep_problems, args.sweep_iters
+
+    def run(variant, H, N, W):
+        probs = []
+        for i in range(n):
+            prob, prm = WL.ur5e(seed=i, n_obs=8)
+            prm = dataclasses.replace(prm, variant=variant, H=H, n_roots=N, workers=W, max_iters=iters,
+                                      problem_id=i, seed=rank)
+            probs.append(stp.problem_from(prob, prm, precision=0, iters_per_graph=16))
+        o = PR.plan_batch(probs)
+        for P in probs:
+            P.close()
+        return o
+
+    def pair(H, N, W):
+        r, f = run(1, H, N, W), run(2, H, N, W)
+        both = r.solved & f.solved
+        return {"H": H, "roots": N, "W": W,
+                "solved_recycling": int(r.solved.sum()), "solved_fixed": int(f.solved.sum()),
+                "mean_arrival_recycling": float(np.mean(r.U[both])) if both.any() else None,
+                "mean_arrival_fixed": float(np.mean(f.U[both])) if both.any() else None,
+                "p50_first_ms_recycling": float(np.median(r.first_ms[r.solved])) if r.solved.any() else None,
+                "p50_first_ms_fixed": float(np.median(f.first_ms[f.solved])) if f.solved.any() else None}
+
+    return {"workload": "ur5e, 8 obstacles, %d problems, %d iterations, batched" % (n, iters),
+            "range": [pair(H, 16, 512) for H in (25.0, 50.0, 100.0)],
+            "roots": [pair(100.0, N, 512) for N in (8, 16, 32, 64, 128)],
+            "batch": [pair(100.0, 16, W) for W in (128, 256, 512, 1024, 2048)]}
+
+
 def mlp_throughput(rank, B=65536, reps=3):
     """Tensor-core GEMMs of proposal-network training steps at batch B on
     synthetic inputs and targets (CUDA events around each GEMM)."""
@@ -451,7 +495,10 @@ def main():
     ap.add_argument("--learned-iters", type=int, default=96)
     ap.add_argument("--learned-single", type=int, default=32)
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--only", default="", choices=["", "micro", "batch", "learned", "mlp"],
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-problems", type=int, default=64)
+    ap.add_argument("--sweep-iters", type=int, default=64)
+    ap.add_argument("--only", default="", choices=["", "micro", "batch", "learned", "mlp", "sweep"],
                     help="micro: run only the collision microbenchmark (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -492,6 +539,9 @@ def main():
         return
     if args.only == "mlp":
         print(json.dumps({"mlp_gemm": mlp_throughput(rank)}))
+        return
+    if args.only == "sweep":
+        print(json.dumps({"sweep": sweep(args, rank)}))
         return
 
     def step_timed():
@@ -575,6 +625,7 @@ def main():
     micro, peak = microbench(args, P, prob, prm, stream, flush, rank, local)
     batch_result = None if args.no_batch else batched(args, rank)
     learned_result = None if args.no_learned else learned(args, rank)
+    sweep_result = None if args.no_sweep else sweep(args, rank)
     n = args.micro_edges
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = float(_peaks().get("sm_max_mhz", 2070.0))
@@ -636,6 +687,8 @@ def main():
         line["batched"] = batch_result
     if not args.no_learned:
         line["learned"] = learned_result
+    if not args.no_sweep:
+        line["sweep"] = sweep_result
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line))

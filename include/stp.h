@@ -80,7 +80,10 @@ typedef struct {
 } stp_obstacles;
 
 /* Planner settings.
- *   variant        0 interval root (Algorithm 2), 1 root recycling (Algorithm 3).
+ *   variant        0 interval root (Algorithm 2), 1 root recycling (Algorithm 3),
+ *                  2 no recycling (the paper's allocation ablation: the roots of
+ *                  Algorithm 3's initialisation stay fixed; roots at T >= U turn
+ *                  inactive and are never replaced).
  *   n_roots        N: interval-root groups or recycling slots, 1..128.
  *   ext_per_iter   W: GPU workers (one Extend each) per iteration, 1..8192.
  *   max_iters      iteration budget (>= 1). budget_ms > 0 adds a wall-clock

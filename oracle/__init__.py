@@ -315,7 +315,7 @@ def plan(prob, params, proposal=None, **over) -> PlanResult:
         N = prm.n_roots
         sl = {"T": np.zeros(N), "has_root": np.zeros(N, dtype=np.int32),
               "active": np.zeros(N, dtype=np.int32), "gen": np.zeros(N, dtype=np.int32)}
-        if prm.variant == 1:
+        if prm.variant != 0:
             L.orc_result_slots(handle, _dptr(sl["T"]), sl["has_root"].ctypes.data_as(_I),
                                sl["active"].ctypes.data_as(_I), sl["gen"].ctypes.data_as(_I))
         nt = int(s[10])

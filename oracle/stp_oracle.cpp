@@ -577,7 +577,7 @@ double learned_T(const Learned& L, const Draws& dr, double* comp_margin) {
 }
 
 struct Params {
-    int variant = 0;  // 0 interval root, 1 root recycling
+    int variant = 0;  // 0 interval root, 1 root recycling, 2 no recycling (fixed forest)
     int N = 4;
     int W = 64;
     int max_iters = 100;
@@ -1167,8 +1167,13 @@ Result Planner::run() {
         if (decreased) {
             if (prm.variant == 0) {
                 partition(alloc, R.U);
-            } else {
+            } else if (prm.variant == 1) {
                 recycle(R.U);
+            } else {
+                // No recycling (Sec. Goal-Time Range and Capacity Ablations):
+                // the fixed forest keeps its roots; those at T >= U go inactive.
+                for (Slot& sl : R.slots)
+                    if (sl.has_root && sl.T >= R.U) sl.active = false;
             }
         }
         R.U_hist.push_back(R.U);

@@ -654,7 +654,7 @@ stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, 
     if (obs->n_obs < 0 || obs->n_obs > kMaxObs || obs->n_way < 1 || obs->n_way > kMaxWay) return STP_ERR_INVALID;
     if (obs->n_obs > 0 && (!obs->radius || !obs->way)) return STP_ERR_INVALID;
     const stp_params& P = *params;
-    if (P.variant != 0 && P.variant != 1) return STP_ERR_INVALID;
+    if (P.variant < 0 || P.variant > 2) return STP_ERR_INVALID;
     if (P.n_roots < 1 || P.n_roots > kMaxRoots) return STP_ERR_INVALID;
     if (P.ext_per_iter < 1 || P.ext_per_iter > kMaxWorkers) return STP_ERR_INVALID;
     if (P.max_iters < 1) return STP_ERR_INVALID;

@@ -568,7 +568,7 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
     // Active-slot list (recycling) staged once per block.
     __shared__ int s_act[kMaxRoots];
     __shared__ int s_nact;
-    if (S.variant == 1) {
+    if (S.variant != 0) {
         for (int i = threadIdx.x; i < S.N; i += blockDim.x) s_act[i] = c->slot_active[i];
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -1389,7 +1389,15 @@ __device__ __forceinline__ void publish_body(const Geom<R>& G, const State<R>& S
             for (int i = t; i < S.N; i += blockDim.x) c->group_active[i] = s_counts[i];
             if (t == 0) partition(S, sU);
         } else if (t == 0) {
-            recycle(S, sU, s_donors, s_held);
+            if (S.variant == 1) {
+                recycle(S, sU, s_donors, s_held);
+            } else {
+                // No recycling (the allocation ablation): the fixed forest only
+                // loses the roots that can no longer improve U.
+                Ctl* cc = S.ctl;
+                for (int i = 0; i < S.N; ++i)
+                    if (cc->slot_has[i] && cc->slot_T[i] >= sU) cc->slot_active[i] = 0;
+            }
         }
     }
     __syncthreads();

@@ -44,6 +44,9 @@ CASES = {
     "arm7-interval": lambda: (WL.arm7(0)[0], dataclasses.replace(WL.arm7(0)[1], variant=0, workers=96,
                                                                   max_iters=5)),
     "ragged-workers": lambda: (WL.disc2d(2)[0], dataclasses.replace(WL.disc2d(2)[1], workers=1500, max_iters=4)),
+    "ur5e-small-norecycling": lambda: (_small_arm()[0], dataclasses.replace(_small_arm()[1], variant=2)),
+    "disc2d-norecycling": lambda: (WL.disc2d(1)[0], dataclasses.replace(WL.disc2d(1)[1], variant=2, max_iters=80,
+                                                                        eta=0.05)),
 }
 
 
@@ -82,7 +85,7 @@ def test_fp64_trees_match_oracle_node_for_node(case):
     if ref.status == 0:
         assert abs(out.U - ref.U) < 1e-9 and abs(out.C - ref.C) < 1e-9
         assert np.allclose(out.path, ref.path, rtol=0, atol=1e-9)
-    if prm.variant == 1:
+    if prm.variant != 0:
         sl = P.slots()
         for k in ("has_root", "active", "gen"):
             assert np.array_equal(sl[k], ref.slots[k]), k

@@ -179,6 +179,25 @@ def test_root_recycling_invariants(arm_run):
         assert np.all(s.tree == r.slots["gen"][i])
 
 
+def test_no_recycling_keeps_a_fixed_forest(arm_run):
+    """Variant 2 (the paper's allocation ablation): the initial roots are those
+    of root recycling and are never replaced; roots at T >= U turn inactive."""
+    prob, prm, r1 = arm_run
+    r2 = O.plan(prob, dataclasses.replace(prm, variant=2))
+    assert r2.status == 0
+    _check_path(prob, prm, r2)
+    _check_trees(prob, prm, r2)
+    assert np.all(r2.slots["gen"] == 0)
+    for i in range(prm.n_roots):
+        if r2.slots["has_root"][i]:
+            assert bool(r2.slots["active"][i]) == (r2.slots["T"][i] < r2.U)
+            assert np.all(r2.seg[i].tree == 0)
+            if r1.slots["gen"][i] == 0 and r1.slots["has_root"][i]:
+                assert r2.slots["T"][i] == r1.slots["T"][i]
+    # recycling replaced at least one root on this case; the ablation did not
+    assert np.any(r1.slots["gen"] > 0)
+
+
 def test_early_return_and_blocked_start():
     prob, prm = WL.disc2d(0)
     prob.qg = prob.qs.copy()
