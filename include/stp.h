@@ -103,7 +103,13 @@ typedef struct {
  *                  workers (the rest sample as with 0); stp_plan and
  *                  stp_batch_plan return STP_ERR_INVALID until one is set.
  *   capacity       nodes per tree arena; 0 = max_iters * ceil(W/2) + 2 (worst case).
- *   iters_per_graph  iterations captured per CUDA graph launch; 0 = 16. */
+ *   iters_per_graph  iterations captured per CUDA graph launch; 0 = 16.
+ *   t_offset       absolute time of the query's local time 0 (>= 0): obstacle
+ *                  trajectories are shifted by it, as when a goal sequence is
+ *                  planned query by query (Sec. "Problem Formulation": each
+ *                  query resets local time to zero, shifts obstacle
+ *                  trajectories by its absolute start time and uses the
+ *                  remaining horizon, passed as t_max). */
 typedef struct {
     int variant;
     int n_roots;
@@ -122,6 +128,7 @@ typedef struct {
     int learned;
     int capacity;
     int iters_per_graph;
+    double t_offset;
 } stp_params;
 
 /* Per-call statistics filled by stp_plan. Times are GPU times (CUDA events /

@@ -31,7 +31,7 @@ class OrcParams(C.Structure):
                 ("dt", C.c_double), ("p_new", C.c_double), ("p_guided", C.c_double),
                 ("H", C.c_double), ("seed", C.c_ulonglong), ("problem_id", C.c_uint),
                 ("flag_tol", C.c_double), ("flag_clear", C.c_double), ("learned", C.c_int),
-                ("proposal", _D)]
+                ("proposal", _D), ("t_offset", C.c_double)]
 
 
 def _dptr(a: np.ndarray):
@@ -242,10 +242,10 @@ class PlanResult:
     goal_clearance: np.ndarray
 
 
-def make_params(params, proposal=None, **over) -> OrcParams:
+def make_params(params, proposal=None, t_offset=0.0, **over) -> OrcParams:
     p = dataclasses.replace(params, **over) if over else params
     prm = OrcParams(p.variant, p.n_roots, p.workers, p.max_iters, p.eta, p.res, p.dt, p.p_new,
-                    p.p_guided, p.H, p.seed, p.problem_id, 0.0, 0.0, 0, None)
+                    p.p_guided, p.H, p.seed, p.problem_id, 0.0, 0.0, 0, None, float(t_offset))
     if proposal is not None:
         prm.learned = 1
         prm.proposal = _dptr(proposal)
@@ -273,13 +273,14 @@ def learned_sample(y, qlo, qhi, H, seed, problem_id, k, w, qs=None, qg=None):
     return bool(f), wi.value, qr, Tl.value
 
 
-def plan(prob, params, proposal=None, **over) -> PlanResult:
-    """proposal: network output y[160] (float64 array) enables the learned branch."""
+def plan(prob, params, proposal=None, t_offset=0.0, **over) -> PlanResult:
+    """proposal: network output y[160] (float64 array) enables the learned
+    branch; t_offset: absolute time of the query's local time 0."""
     L = lib()
     h = _ProblemHandle(prob)
     if proposal is not None:
         proposal = np.ascontiguousarray(proposal, dtype=np.float64)
-    prm = make_params(params, proposal, **over)
+    prm = make_params(params, proposal, t_offset, **over)
     handle = C.c_void_p()
     L.orc_plan(h.ref, C.byref(prm), C.byref(handle))
     try:
@@ -336,3 +337,30 @@ def plan(prob, params, proposal=None, **over) -> PlanResult:
                           goal_kmin=kmin.value, goal_clearance=gcl[:ng].copy())
     finally:
         L.orc_result_free(handle)
+
+
+def plan_sequence(prob, params, goals, **over):
+    """Goal sequence as successive single-goal queries (Sec. "Problem
+    Formulation"): query i starts at the previous arrival state with local time
+    0, obstacle trajectories shifted by its absolute start time, and the
+    remaining horizon. Returns (status, path [n][d+1] in absolute time, visit
+    times, per-query results)."""
+    t_abs = 0.0
+    q = np.asarray(prob.qs, float)
+    segs, visits, results = [], [], []
+    for i, g in enumerate(goals):
+        H = params.H - t_abs
+        if not H > 0:
+            return 5, None, visits, results
+        pi = dataclasses.replace(prob, qs=q.copy(), qg=np.asarray(g, float).copy())
+        r = plan(pi, dataclasses.replace(params, H=H, problem_id=params.problem_id + i, **over), t_offset=t_abs)
+        results.append(r)
+        if r.status != 0:
+            return r.status, None, visits, results
+        path = r.path.copy()
+        path[:, prob.dof] += t_abs
+        segs.append(path if i == 0 else path[1:])
+        t_abs += r.U
+        visits.append(t_abs)
+        q = np.asarray(g, float)
+    return 0, np.concatenate(segs), visits, results

@@ -1222,6 +1222,7 @@ typedef struct {
     double flag_tol, flag_clear;
     int learned;              /* 1: learned branch with proposal[160] */
     const double* proposal;
+    double t_offset;          /* absolute time of local time 0 */
 } orc_params;
 
 static Problem to_problem(const orc_problem* p) {
@@ -1387,6 +1388,10 @@ int orc_learned_sample(const double* y, const double* qlo, const double* qhi, co
 
 int orc_plan(const orc_problem* prob, const orc_params* p, orc_result** out) {
     Problem P = to_problem(prob);
+    // A query of a goal sequence starts at absolute time t_offset: its local
+    // time 0 sees the obstacle trajectories shifted by t_offset (Sec. "Problem
+    // Formulation").
+    for (size_t i = 0; i < P.way.size(); i += 4) P.way[i] -= p->t_offset;
     Params prm;
     prm.variant = p->variant;
     prm.N = p->n_roots;

@@ -662,6 +662,7 @@ stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, 
     if (!(P.p_new >= 0 && P.p_new <= 1) || !(P.p_guided >= 0 && P.p_guided <= 1)) return STP_ERR_INVALID;
     if (P.precision != 0 && P.precision != 1) return STP_ERR_INVALID;
     if ((P.learned != 0 && P.learned != 1) || P.capacity < 0 || P.iters_per_graph < 0) return STP_ERR_INVALID;
+    if (!(P.t_offset >= 0) || !std::isfinite(P.t_offset)) return STP_ERR_INVALID;
 
     stp_problem* p = new (std::nothrow) stp_problem();
     if (!p) return STP_ERR_CUDA;
@@ -682,6 +683,8 @@ stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, 
     if (p->M > 0) {
         p->obs_r.assign(obs->radius, obs->radius + p->M);
         p->way.assign(obs->way, obs->way + (size_t)p->M * p->K * 4);
+        // Local query time 0 is absolute time t_offset: shift the trajectories.
+        for (size_t i = 0; i < p->way.size(); i += 4) p->way[i] -= P.t_offset;
     }
     bool ok = finite_all(p->qs.data(), d) && finite_all(p->qg.data(), d) && finite_all(p->qlo.data(), d) &&
               finite_all(p->qhi.data(), d) && finite_all(p->sph.data(), p->sph.size()) &&

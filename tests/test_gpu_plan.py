@@ -203,3 +203,30 @@ def test_replanning_is_deterministic():
     fb = P.tree(-1)["x"]
     assert a.U == b.U and np.array_equal(fa, fb)
     P.close()
+
+
+@pytest.mark.parametrize("which", ["disc", "arm"])
+def test_goal_sequence_matches_oracle(which):
+    """Goal sequences chained on the device (FP64) equal the oracle's chain."""
+    from paper_2609_30533_gb300 import sequence as SQ
+    from paper_2609_30533_gb300 import stp
+    if which == "disc":
+        prob, prm = WL.disc2d(0)
+        prm = dataclasses.replace(prm, max_iters=150)
+        goals = [np.array([0.95, 0.95]), np.array([0.1, 0.9])]
+    else:
+        prob, prm = WL.ur5e(0, n_obs=4, candidate=0)
+        prm = dataclasses.replace(prm, workers=64, max_iters=40)
+        goals = [prob.qs + np.array([0.6, -0.4, 0.5, 0.3, -0.2, 0.4]),
+                 prob.qs + np.array([0.2, 0.3, -0.2, 0.1, 0.4, -0.3])]
+    st, path, visits, _ = O.plan_sequence(prob, prm, goals)
+    res = SQ.plan_sequence(prob, prm, goals, precision=1)
+    assert st == 0 and res.status == stp.STP_OK
+    assert np.allclose(res.visits, visits, rtol=0, atol=1e-9)
+    assert res.path.shape == path.shape and np.allclose(res.path, path, rtol=0, atol=1e-9)
+    r32 = SQ.plan_sequence(prob, prm, goals, precision=0)
+    assert r32.status == stp.STP_OK
+    d = prob.dof
+    v, clr, _, _ = O.check_edges(prob, r32.path[:-1, :d], r32.path[:-1, d], r32.path[1:, :d], r32.path[1:, d],
+                                 prm.res)
+    assert np.all(v.astype(bool) | (np.abs(clr) <= 1e-5))
