@@ -336,9 +336,10 @@ stp_status stp_mlp_gradients(stp_mlp *m, int B, const float *x, const float *tar
 stp_status stp_mlp_train_step(stp_mlp *m, int B, const float *x, const float *targets, float lr, float *loss,
                               int flags);
 /* With profiling on, every tensor-core GEMM is bracketed by CUDA events;
- * stp_mlp_profile returns (and clears) their total time and FLOPs. */
+ * stp_mlp_profile returns (and clears) their total time, FLOPs and
+ * algorithmic HBM bytes (operands read once, every output copy written once). */
 stp_status stp_mlp_set_profiling(stp_mlp *m, int on);
-stp_status stp_mlp_profile(stp_mlp *m, double *gemm_ms, double *gemm_flops);
+stp_status stp_mlp_profile(stp_mlp *m, double *gemm_ms, double *gemm_flops, double *gemm_bytes);
 const char *stp_mlp_last_error(const stp_mlp *m);
 
 /* Training targets t[STP_MLP_NTGT] of the path found by the last stp_plan or

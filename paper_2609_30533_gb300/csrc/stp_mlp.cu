@@ -40,9 +40,15 @@ namespace mlp {
 
 constexpr int kIn = 32, kInP = 64, kHid = 256, kOut = 160, kOutP = 256;
 constexpr int kMix = 8, kWp = 16, kWpDim = 8, kTgt = 130;
-constexpr int kTileM = 128, kStageK = 64, kStages = 4, kThreads = 128;
+constexpr int kTileM = 128, kStageK = 64, kThreads = 128;
+// Pipeline depth: products over K = 256 (four stages) use two stages, so that
+// two CTAs (2 x 97 KB of shared memory, 2 x 256 TMEM columns) share an SM and
+// one CTA's epilogue overlaps the other's copies and MMAs; the long-K weight-
+// gradient products keep four stages (one CTA per SM).
+__host__ __device__ constexpr int stages_for(int mode) { return mode == 3 ? 4 : 2; }
 constexpr float kSMin = -7.f, kSMax = 2.f;
-constexpr int kColChunk = 256;  // rows per bias-gradient partial
+// Bias gradients: every 128-row tile (a GEMM CTA or a loss block) writes the
+// column sums of its rows as one partial [256]; Adam adds the partials.
 
 enum Mode { kHidden = 0, kOutput = 1, kBackward = 2, kWGrad = 3 };
 
@@ -111,32 +117,68 @@ struct GemmArgs {
     const __nv_bfloat16* act;  // kBackward: forward activation, tiled [RA][N]
     __nv_bfloat16* out_t;      // tiled [RA][N]
     __nv_bfloat16* out_tT;     // tiled [N][RA]
-    float* out_f;              // FP32 row-major
+    float* out_f;              // FP32 row-major (kOutput), partials (kWGrad), bias-gradient partials [tile][N] (kBackward)
     int ld_f;
     int m_valid;               // kWGrad: rows written
     int* err;
 };
 
-// Output bf16 stores of 16 consecutive columns c0..c0+15 of row r.
-__device__ __forceinline__ void store_row16(__nv_bfloat16* t, __nv_bfloat16* tT, int r, int c0, int R, int N,
-                                            const float (&v)[16]) {
-    if (t) {
+// BF16 stores of 16 consecutive columns c0..c0+15 of row r into a tiled
+// [R][N] matrix (two 16-byte stores).
+__device__ __forceinline__ void store_row16(__nv_bfloat16* t, int r, int c0, int R, const float (&v)[16]) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            __align__(16) __nv_bfloat16 b[8];
+    for (int h = 0; h < 2; ++h) {
+        __align__(16) __nv_bfloat16 b[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) b[i] = __float2bfloat16_rn(v[8 * h + i]);
-            *reinterpret_cast<uint4*>(t + tix(r, c0 + 8 * h, R)) = *reinterpret_cast<const uint4*>(b);
+        for (int i = 0; i < 8; ++i) b[i] = __float2bfloat16_rn(v[8 * h + i]);
+        *reinterpret_cast<uint4*>(t + tix(r, c0 + 8 * h, R)) = *reinterpret_cast<const uint4*>(b);
+    }
+}
+
+// The same 32 rows x 16 columns block of a warp (lane = row r0 + lane, r0 % 32
+// == 0) into the transposed tiled [N][R] matrix: the warp transposes through
+// its 1 KB shared-memory tile sbuf [16][32] and writes 64 rows of 16 bytes
+// (8 consecutive r of one column each). All 32 lanes must call it.
+__device__ __forceinline__ void store_T_warp(__nv_bfloat16* tT, int r0, int c0, int N, const float (&v)[16],
+                                             __nv_bfloat16* sbuf) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) sbuf[c * 32 + lane] = __float2bfloat16_rn(v[c]);
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int rho = lane + 32 * k;
+        const int c = rho >> 2, rg = rho & 3;
+        const uint4 val = *reinterpret_cast<const uint4*>(sbuf + c * 32 + rg * 8);
+        *reinterpret_cast<uint4*>(tT + tix(c0 + c, r0 + rg * 8, N)) = val;
+    }
+    __syncwarp();
+}
+
+// Column sums over the 32 lanes of 16 per-lane values by recursive halving:
+// at offset o each lane keeps the half of its columns selected by its lane
+// bit and adds its partner's copy of them, so lane l ends with the sum of
+// column l & 15 over all 32 lanes (16 shuffles instead of 80).
+__device__ __forceinline__ float warp_colsum16(float (&v)[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 8, n = 8; o >= 1; o >>= 1, n >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i < n) {
+                const float send = up ? v[i] : v[i + n];
+                const float keep = up ? v[i + n] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
         }
     }
-    if (tT) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) tT[tix(c0 + i, r, N)] = __float2bfloat16_rn(v[i]);
-    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
 template <int N, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
+    constexpr int kStages = stages_for(MODE);
     constexpr uint32_t kABytes = kTileM * kStageK * 2;  // 16 KB
     constexpr uint32_t kBBytes = N * kStageK * 2;
     constexpr uint32_t kTmemCols = N < 32 ? 32 : N;
@@ -145,6 +187,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int fail_sh;
+    __shared__ float sbias[N];  // bias (forward) or bias-gradient sums (backward)
+    __shared__ __align__(16) __nv_bfloat16 stile[4][16 * 32];
 
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = smem;
@@ -164,6 +208,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
         mbar_init(&done, 1);
         fail_sh = 0;
     }
+    if (MODE == kHidden || MODE == kOutput)
+        for (int i = tid; i < N; i += kThreads) sbias[i] = g.bias[i];
+    if (MODE == kBackward)
+        for (int i = tid; i < N; i += kThreads) sbias[i] = 0.f;
     if (warp == 0) tmem_alloc(&tmem_base_sh, kTmemCols);
     fence_before_sync();
     __syncthreads();
@@ -239,11 +287,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
         }
         if (MODE == kHidden) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + g.bias[c0 + i], 0.f);
-            store_row16(g.out_t, g.out_tT, r, c0, g.RA, N, v);
+            for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + sbias[c0 + i], 0.f);
+            store_row16(g.out_t, r, c0, g.RA, v);
+            store_T_warp(g.out_tT, m0 + 32 * warp, c0, N, v, stile[warp]);
         } else if (MODE == kOutput) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] += g.bias[c0 + i];
+            for (int i = 0; i < 16; ++i) v[i] += sbias[c0 + i];
             float4* o = reinterpret_cast<float4*>(g.out_f + (size_t)r * g.ld_f + c0);
 #pragma unroll
             for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
@@ -256,10 +305,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
                 for (int i = 0; i < 8; ++i)
                     if (!(__bfloat162float(a[i]) > 0.f)) v[8 * h + i] = 0.f;
             }
-            store_row16(g.out_t, g.out_tT, r, c0, g.RA, N, v);
-            float4* o = reinterpret_cast<float4*>(g.out_f + (size_t)r * g.ld_f + c0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            store_row16(g.out_t, r, c0, g.RA, v);
+            store_T_warp(g.out_tT, m0 + 32 * warp, c0, N, v, stile[warp]);
+            const float cs = warp_colsum16(v);
+            if (lane < 16) atomicAdd(&sbias[c0 + lane], cs);
         } else {  // kWGrad
             if (r < g.m_valid) {
                 float4* o = reinterpret_cast<float4*>(g.out_f + ((size_t)z * g.m_valid + r) * g.ld_f + c0);
@@ -270,6 +319,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
     }
     fence_before_sync();
     __syncthreads();
+    if (MODE == kBackward)
+        for (int i = tid; i < N; i += kThreads) g.out_f[(size_t)blockIdx.x * N + i] = sbias[i];
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
@@ -288,10 +339,10 @@ __global__ void k_pack_input(const float* __restrict__ X, int B, int Bp, __nv_bf
 }
 
 // Per-sample loss (mixture NLL of tau + masked waypoint MSE) and dL/dy / B.
-__global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ T, int B, int Bp, float* dyf,
+__global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ T, int B, int Bp, float* bpart,
                        __nv_bfloat16* dyt, __nv_bfloat16* dytT, float* loss) {
+    // Bp is a multiple of the 128-thread block: every thread has a row.
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= Bp) return;
     float g[kOutP];
 #pragma unroll 1
     for (int c = 0; c < kOutP; ++c) g[c] = 0.f;
@@ -342,25 +393,21 @@ __global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ T,
         L += mse / cnt;
         loss[n] = L;
     }
+    __shared__ __align__(16) __nv_bfloat16 stile[4][16 * 32];
+    __shared__ float sb[kOutP];
+    for (int i = threadIdx.x; i < kOutP; i += blockDim.x) sb[i] = 0.f;
+    __syncthreads();
     for (int c0 = 0; c0 < kOutP; c0 += 16) {
         float v[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = g[c0 + i];
-        store_row16(dyt, dytT, n, c0, Bp, kOutP, v);
-        float4* o = reinterpret_cast<float4*>(dyf + (size_t)n * kOutP + c0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        store_row16(dyt, n, c0, Bp, v);
+        store_T_warp(dytT, n & ~31, c0, kOutP, v, stile[threadIdx.x >> 5]);
+        const float cs = warp_colsum16(v);
+        if ((threadIdx.x & 31) < 16) atomicAdd(&sb[c0 + (threadIdx.x & 31)], cs);
     }
-}
-
-// Column partial sums of an FP32 row-major [rows][256] matrix over chunks of
-// kColChunk rows: part[chunk][c].
-__global__ void k_colsum(const float* __restrict__ X, int rows, float* part) {
-    const int c = threadIdx.x;
-    const int r0 = blockIdx.x * kColChunk, r1 = min(rows, r0 + kColChunk);
-    float s = 0.f;
-    for (int r = r0; r < r1; ++r) s += X[(size_t)r * kOutP + c];
-    part[(size_t)blockIdx.x * kOutP + c] = s;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kOutP; i += blockDim.x) bpart[(size_t)blockIdx.x * kOutP + i] = sb[i];
 }
 
 struct AdamArgs {
@@ -445,9 +492,8 @@ struct stp_mlp {
     __nv_bfloat16 *ht[3]{}, *htT[3]{};
     __nv_bfloat16 *dt[4]{}, *dtT[4]{};  // gradient wrt layer outputs (dt[3] = dY)
     float* y = nullptr;       // [Bp][256]
-    float* df[4]{};           // FP32 gradients wrt layer outputs [Bp][256]
     float* wpart = nullptr;   // weight-gradient partials
-    float* bpart = nullptr;   // bias-gradient partials
+    float* bpart = nullptr;   // bias-gradient partials [4][Bp/128][256]
     float* gsum = nullptr;    // summed gradients (gradients API)
     float* loss = nullptr;    // [Bp]
     float* X = nullptr;       // staged inputs [max_batch][32]
@@ -457,7 +503,7 @@ struct stp_mlp {
     int step = 0;
     bool profiling = false;
     cudaEvent_t ev[2]{};
-    double gemm_ms = 0, gemm_flops = 0;
+    double gemm_ms = 0, gemm_flops = 0, gemm_bytes = 0;
     std::string last_error;
 };
 
@@ -481,7 +527,7 @@ size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 template <int N, int MODE>
 cudaError_t launch_gemm(const GemmArgs& g, int mtiles, int splits, cudaStream_t st) {
-    constexpr int smem = kStages * (kTileM * kStageK * 2 + N * kStageK * 2) + 1024;
+    constexpr int smem = stages_for(MODE) * (kTileM * kStageK * 2 + N * kStageK * 2) + 1024;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_gemm<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -492,10 +538,22 @@ cudaError_t launch_gemm(const GemmArgs& g, int mtiles, int splits, cudaStream_t 
     return cudaGetLastError();
 }
 
+// Algorithmic HBM bytes of one GEMM: operands read once, outputs written once
+// (BF16 tiled and transposed copies, FP32 copies and split-K partials as the
+// mode writes them; the backward mode also reads the forward activation).
+double gemm_bytes(int M, int N, int K, int mode, int splits) {
+    double b = 2.0 * M * K + 2.0 * N * K;
+    if (mode == kHidden) b += 4.0 * M * N;
+    else if (mode == kOutput) b += 4.0 * M * N;
+    else if (mode == kBackward) b += 2.0 * M * N + 4.0 * M * N;
+    else b += 4.0 * M * N * splits;
+    return b;
+}
+
 struct Timer {
     stp_mlp* m;
-    double flops;
-    Timer(stp_mlp* mm, double f) : m(mm), flops(f) {
+    double flops, bytes;
+    Timer(stp_mlp* mm, double f, double by) : m(mm), flops(f), bytes(by) {
         if (m->profiling) cudaEventRecord(m->ev[0], m->stream);
     }
     void stop() {
@@ -506,6 +564,7 @@ struct Timer {
         cudaEventElapsedTime(&ms, m->ev[0], m->ev[1]);
         m->gemm_ms += ms;
         m->gemm_flops += flops;
+        m->gemm_bytes += bytes;
     }
 };
 
@@ -528,7 +587,8 @@ stp_status forward_impl(stp_mlp* m, int B) {
         g.kt_per_split = g.KT;
         g.bias = m->b[l];
         g.err = m->err;
-        Timer t(m, 2.0 * Bp * kLayers[l].in * kLayers[l].out);
+        Timer t(m, 2.0 * Bp * kLayers[l].in * kLayers[l].out,
+                gemm_bytes(Bp, kLayers[l].out, kLayers[l].in, l < 3 ? kHidden : kOutput, 1));
         if (l < 3) {
             g.out_t = m->ht[l];
             g.out_tT = m->htT[l];
@@ -544,8 +604,8 @@ stp_status forward_impl(stp_mlp* m, int B) {
     return STP_OK;
 }
 
-// Backward from dY (already in dt[3] / dtT[3] / df[3]) to every parameter's
-// gradient partials; bias partials from the FP32 copies.
+// Backward from dY (already in dt[3] / dtT[3], its bias partials written by
+// the loss kernel) to every parameter's gradient partials.
 stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
     const int Bp = (B + kTileM - 1) / kTileM * kTileM;
     const int mt = Bp / kTileM;
@@ -553,13 +613,9 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
     const int KTb = Bp / kStageK;
     const int splits = std::min(kSplitMax, std::max(1, KTb / 4));
     const int kps = (KTb + splits - 1) / splits;
-    const int nb = (Bp + kColChunk - 1) / kColChunk;
     *nwpart = splits;
-    *nbpart = nb;
+    *nbpart = mt;
     for (int l = 3; l >= 0; --l) {
-        // bias gradient partials from df[l]
-        k_colsum<<<nb, kOutP, 0, st>>>(m->df[l], Bp, m->bpart + (size_t)l * (m->Bp_max / kColChunk + 1) * kOutP);
-        MLP_CUDA(m, cudaGetLastError());
         // weight gradient: dW_l = dT_l^T . act_{l-1}   (M = out, N = in, K = batch)
         GemmArgs g{};
         g.A = m->dtT[l];
@@ -572,7 +628,8 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
         g.m_valid = kLayers[l].out;
         g.err = m->err;
         {
-            Timer t(m, 2.0 * Bp * kLayers[l].in * kLayers[l].out);
+            Timer t(m, 2.0 * Bp * kLayers[l].in * kLayers[l].out,
+                    gemm_bytes(kLayers[l].out, kLayers[l].in, Bp, kWGrad, splits));
             if (l == 0) MLP_CUDA(m, (launch_gemm<kInP, kWGrad>(g, kLayers[l].out / kTileM, splits, st)));
             else MLP_CUDA(m, (launch_gemm<kHid, kWGrad>(g, kLayers[l].out / kTileM, splits, st)));
             t.stop();
@@ -588,10 +645,10 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
         h.act = m->ht[l - 1];
         h.out_t = m->dt[l - 1];
         h.out_tT = m->dtT[l - 1];
-        h.out_f = m->df[l - 1];
-        h.ld_f = kOutP;
+        h.out_f = m->bpart + (size_t)(l - 1) * (m->Bp_max / kTileM) * kOutP;
         h.err = m->err;
-        Timer t(m, 2.0 * Bp * kLayers[l].in * kLayers[l].out);
+        Timer t(m, 2.0 * Bp * kLayers[l].in * kLayers[l].out,
+                gemm_bytes(Bp, kLayers[l].in, kLayers[l].out, kBackward, 1));
         MLP_CUDA(m, (launch_gemm<kHid, kBackward>(h, mt, 1, st)));
         t.stop();
     }
@@ -633,7 +690,7 @@ stp_status adam_impl(stp_mlp* m, int nwpart, int nbpart, float lr, bool update, 
         bb.w = m->b[l];
         bb.m = m->mb[l];
         bb.v = m->vb[l];
-        bb.gpart = m->bpart + (size_t)l * (m->Bp_max / kColChunk + 1) * kOutP;
+        bb.gpart = m->bpart + (size_t)l * (m->Bp_max / kTileM) * kOutP;
         bb.nparts = nbpart;
         bb.rows = L.out;
         bb.cols = 1;
@@ -687,7 +744,7 @@ stp_status stp_mlp_create(int max_batch, stp_mlp** out) {
     m->max_batch = max_batch;
     const int Bp = (max_batch + kTileM - 1) / kTileM * kTileM;
     m->Bp_max = Bp;
-    const int nbmax = Bp / kColChunk + 1;
+    const int nbmax = Bp / kTileM;
     // arena layout
     std::vector<std::pair<void**, size_t>> parts;
     for (int l = 0; l < 4; ++l) {
@@ -710,7 +767,6 @@ stp_status stp_mlp_create(int max_batch, stp_mlp** out) {
     for (int l = 0; l < 4; ++l) {
         parts.push_back({(void**)&m->dt[l], (size_t)Bp * kOutP * 2});
         parts.push_back({(void**)&m->dtT[l], (size_t)Bp * kOutP * 2});
-        parts.push_back({(void**)&m->df[l], (size_t)Bp * kOutP * 4});
     }
     parts.push_back({(void**)&m->y, (size_t)Bp * kOutP * 4});
     parts.push_back({(void**)&m->wpart, (size_t)4 * kSplitMax * kOutP * kHid * 4});
@@ -823,7 +879,8 @@ static stp_status loss_grad(stp_mlp* m, int B, const float* X, const float* T, i
     if ((s = stage_in(m, m->T, T, (size_t)B * kTgt, flags)) != STP_OK) return s;
     if ((s = forward_impl(m, B)) != STP_OK) return s;
     const int Bp = (B + kTileM - 1) / kTileM * kTileM;
-    k_loss<<<(Bp + 127) / 128, 128, 0, m->stream>>>(m->y, m->T, B, Bp, m->df[3], m->dt[3], m->dtT[3], m->loss);
+    k_loss<<<Bp / 128, 128, 0, m->stream>>>(m->y, m->T, B, Bp, m->bpart + (size_t)3 * (m->Bp_max / kTileM) * kOutP,
+                                            m->dt[3], m->dtT[3], m->loss);
     MLP_CUDA(m, cudaGetLastError());
     return backward_impl(m, B, nw, nb);
 }
@@ -881,13 +938,16 @@ stp_status stp_mlp_set_profiling(stp_mlp* m, int on) {
     m->profiling = on != 0;
     m->gemm_ms = 0;
     m->gemm_flops = 0;
+    m->gemm_bytes = 0;
     return STP_OK;
 }
 
-stp_status stp_mlp_profile(stp_mlp* m, double* gemm_ms, double* gemm_flops) {
+stp_status stp_mlp_profile(stp_mlp* m, double* gemm_ms, double* gemm_flops, double* gemm_bytes) {
     if (!m) return fail(nullptr, STP_ERR_INVALID, "mlp is NULL");
     if (gemm_ms) *gemm_ms = m->gemm_ms;
     if (gemm_flops) *gemm_flops = m->gemm_flops;
+    if (gemm_bytes) *gemm_bytes = m->gemm_bytes;
+    m->gemm_bytes = 0;
     m->gemm_ms = 0;
     m->gemm_flops = 0;
     return STP_OK;

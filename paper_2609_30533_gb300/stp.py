@@ -138,7 +138,7 @@ def lib():
     L.stp_mlp_train_step.restype = C.c_int
     L.stp_mlp_set_profiling.argtypes = [C.c_void_p, C.c_int]
     L.stp_mlp_set_profiling.restype = C.c_int
-    L.stp_mlp_profile.argtypes = [C.c_void_p, _D, _D]
+    L.stp_mlp_profile.argtypes = [C.c_void_p, _D, _D, _D]
     L.stp_mlp_profile.restype = C.c_int
     L.stp_mlp_last_error.argtypes = [C.c_void_p]
     L.stp_mlp_last_error.restype = C.c_char_p
@@ -550,9 +550,10 @@ class Mlp:
         lib().stp_mlp_set_profiling(self.handle, 1 if on else 0)
 
     def profile(self):
-        ms, fl = C.c_double(), C.c_double()
-        lib().stp_mlp_profile(self.handle, C.byref(ms), C.byref(fl))
-        return ms.value, fl.value
+        """(GEMM ms, FLOPs, algorithmic bytes) since the last call."""
+        ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+        lib().stp_mlp_profile(self.handle, C.byref(ms), C.byref(fl), C.byref(by))
+        return ms.value, fl.value, by.value
 
     def close(self):
         if getattr(self, "handle", None):
