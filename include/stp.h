@@ -260,6 +260,15 @@ void stp_free(stp_problem *p);
  * on p; NULL selects the library's own stream. */
 stp_status stp_set_stream(stp_problem *p, void *cuda_stream);
 
+/* Failure-detection self-test (no paper counterpart): launches one kernel
+ * that waits, with the library's bounded wait, on an mbarrier that nothing
+ * ever arrives at, giving up after limit_ns nanoseconds (1 .. 1e10). Returns
+ * STP_ERR_TIMEOUT (the status every library kernel reports when one of its
+ * waits runs out) and the time waited in *waited_us (may be NULL); the CUDA
+ * context stays usable. STP_ERR_CUDA without a device. Every wait inside the
+ * library's kernels is bounded by 1 s the same way. */
+stp_status stp_selftest_bounded_wait(unsigned long long limit_ns, int *waited_us);
+
 /* Human-readable name of a status code (static string). */
 const char *stp_status_string(stp_status s);
 

@@ -1190,6 +1190,36 @@ extern "C" stp_status stp_problem_features(const stp_problem* p, float* x) {
     return STP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Failure-detection self-test: an mbarrier nobody arrives at, waited on with
+// the library's bounded wait.
+// ---------------------------------------------------------------------------
+__global__ void k_wait_selftest(unsigned long long limit_ns, int* result) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    const unsigned long long t0 = global_ns();
+    const bool ok = mbar_wait(&bar, 0, limit_ns);
+    result[0] = ok ? 0 : 1;
+    result[1] = (int)((global_ns() - t0) / 1000ull);  // microseconds waited
+}
+
+extern "C" stp_status stp_selftest_bounded_wait(unsigned long long limit_ns, int* waited_us) {
+    clear_stale_error();
+    if (limit_ns == 0 || limit_ns > 10000000000ull) return STP_ERR_INVALID;
+    int* d = nullptr;
+    int h[2] = {0, 0};
+    cudaError_t e = cudaMalloc(&d, sizeof(h));
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaMalloc");
+    k_wait_selftest<<<1, 32>>>(limit_ns, d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "self-test kernel");
+    if (waited_us) *waited_us = h[1];
+    return h[0] ? STP_ERR_TIMEOUT : STP_OK;
+}
+
 extern "C" stp_status stp_batch_create(stp_problem* const* problems, int n, const stp_batch_params* bp,
                                        stp_batch** out) {
     clear_stale_error();

@@ -31,7 +31,8 @@ constexpr int kQT = 128;        // queries per NN tile (= threads per CTA)
 constexpr int kMaxTiles = 64;   // node tiles per query (partials per query)
 constexpr int kMaxQTiles = kMaxWorkers / kQT;
 constexpr int kNodeTileMin = 128;
-constexpr unsigned kWaitLimit = 1u << 24;  // bounded spin on mbarriers
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // bounded mbarrier waits: 1 s
+constexpr unsigned kWaitLimit = 1u << 28;                   // and an iteration backstop
 constexpr int kPropY = 160;                 // network output floats
 constexpr int kPropSize = 24 + 16 * kMaxDof;
 constexpr unsigned kThrLearned = 15099495u;  // learned iff m < ceil(0.9 2^24)
@@ -247,8 +248,13 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
-// Bounded wait for phase `parity`; returns false if the limit was reached.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+__device__ __forceinline__ unsigned long long global_ns();
+
+// Bounded wait for phase `parity`: gives up after limit_ns of global time (or
+// the iteration backstop) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
+    unsigned long long t0 = 0;
     for (unsigned it = 0; it < kWaitLimit; ++it) {
         unsigned ok;
         asm volatile(
@@ -259,6 +265,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
             : "r"(smem_u32(bar)), "r"(parity)
             : "memory");
         if (ok) return true;
+        if ((it & 255u) == 0) {
+            const unsigned long long now = global_ns();
+            if (it == 0) t0 = now;
+            else if (now - t0 > limit_ns) return false;
+        }
     }
     return false;
 }

@@ -148,6 +148,8 @@ def lib():
     L.stp_set_proposal.restype = C.c_int
     L.stp_problem_targets.argtypes = [C.c_void_p, _F]
     L.stp_problem_targets.restype = C.c_int
+    L.stp_selftest_bounded_wait.argtypes = [C.c_ulonglong, _I]
+    L.stp_selftest_bounded_wait.restype = C.c_int
     _LIB = L
     return L
 
@@ -159,7 +161,7 @@ EXPORTED = ["stp_create_problem", "stp_plan", "stp_check_edges", "stp_free", "st
             "stp_mlp_create", "stp_mlp_free", "stp_mlp_set_stream", "stp_mlp_set_params", "stp_mlp_get_params",
             "stp_mlp_forward", "stp_mlp_gradients", "stp_mlp_train_step", "stp_mlp_set_profiling",
             "stp_mlp_profile", "stp_mlp_last_error", "stp_problem_features", "stp_set_proposal",
-            "stp_problem_targets"]
+            "stp_problem_targets", "stp_selftest_bounded_wait"]
 
 
 def status_string(s: int) -> str:
@@ -565,3 +567,10 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def selftest_bounded_wait(limit_ns: int):
+    """(status, microseconds waited) of the bounded-wait self-test."""
+    us = C.c_int()
+    s = lib().stp_selftest_bounded_wait(C.c_ulonglong(limit_ns), C.byref(us))
+    return s, us.value

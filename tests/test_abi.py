@@ -120,3 +120,11 @@ def test_mlp_argument_checks_and_no_cpu_fallback(L):
     import torch
     if not torch.cuda.is_available():
         assert L.stp_mlp_create(16, C.byref(h)) == 3     # STP_ERR_CUDA: no device, no fallback
+
+
+def test_selftest_rejects_bad_limits_and_fails_loudly_without_device(L):
+    assert L.stp_selftest_bounded_wait(0, None) == 1
+    assert L.stp_selftest_bounded_wait(10 ** 11, None) == 1
+    import torch
+    if not torch.cuda.is_available():
+        assert L.stp_selftest_bounded_wait(1000000, None) == 3
