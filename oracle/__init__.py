@@ -31,7 +31,7 @@ class OrcParams(C.Structure):
                 ("dt", C.c_double), ("p_new", C.c_double), ("p_guided", C.c_double),
                 ("H", C.c_double), ("seed", C.c_ulonglong), ("problem_id", C.c_uint),
                 ("flag_tol", C.c_double), ("flag_clear", C.c_double), ("learned", C.c_int),
-                ("proposal", _D), ("t_offset", C.c_double)]
+                ("proposal", _D), ("t_offset", C.c_double), ("continuous", C.c_int)]
 
 
 def _dptr(a: np.ndarray):
@@ -63,6 +63,8 @@ def lib():
     L.orc_learned_sample.argtypes = [_D, _D, _D, _D, _D, C.c_int, C.c_double, C.c_ulonglong, C.c_uint, C.c_uint,
                                      C.c_uint, _I, _D, _D]
     L.orc_learned_sample.restype = C.c_int
+    L.orc_check_edges_continuous.argtypes = [C.POINTER(OrcProblem), C.c_int, _D, _D, _D, _D, _U8, _D]
+    L.orc_check_edges_continuous.restype = C.c_int
     L.orc_plan.restype = C.c_int
     L.orc_result_summary.argtypes = [C.c_void_p, _D]
     L.orc_result_path.argtypes = [C.c_void_p, _D]
@@ -242,10 +244,11 @@ class PlanResult:
     goal_clearance: np.ndarray
 
 
-def make_params(params, proposal=None, t_offset=0.0, **over) -> OrcParams:
+def make_params(params, proposal=None, t_offset=0.0, continuous=False, **over) -> OrcParams:
     p = dataclasses.replace(params, **over) if over else params
     prm = OrcParams(p.variant, p.n_roots, p.workers, p.max_iters, p.eta, p.res, p.dt, p.p_new,
-                    p.p_guided, p.H, p.seed, p.problem_id, 0.0, 0.0, 0, None, float(t_offset))
+                    p.p_guided, p.H, p.seed, p.problem_id, 0.0, 0.0, 0, None, float(t_offset),
+                    1 if continuous else 0)
     if proposal is not None:
         prm.learned = 1
         prm.proposal = _dptr(proposal)
@@ -273,14 +276,15 @@ def learned_sample(y, qlo, qhi, H, seed, problem_id, k, w, qs=None, qg=None):
     return bool(f), wi.value, qr, Tl.value
 
 
-def plan(prob, params, proposal=None, t_offset=0.0, **over) -> PlanResult:
+def plan(prob, params, proposal=None, t_offset=0.0, continuous=False, **over) -> PlanResult:
     """proposal: network output y[160] (float64 array) enables the learned
-    branch; t_offset: absolute time of the query's local time 0."""
+    branch; t_offset: absolute time of the query's local time 0; continuous:
+    closed-form edge validation (point robots)."""
     L = lib()
     h = _ProblemHandle(prob)
     if proposal is not None:
         proposal = np.ascontiguousarray(proposal, dtype=np.float64)
-    prm = make_params(params, proposal, t_offset, **over)
+    prm = make_params(params, proposal, t_offset, continuous, **over)
     handle = C.c_void_p()
     L.orc_plan(h.ref, C.byref(prm), C.byref(handle))
     try:
@@ -364,3 +368,20 @@ def plan_sequence(prob, params, goals, **over):
         visits.append(t_abs)
         q = np.asarray(g, float)
     return 0, np.concatenate(segs), visits, results
+
+
+def check_edges_continuous(prob, qa, ta, qb, tb):
+    """Closed-form verdicts (1 = free) and exact clearances of point-robot edges."""
+    h = _ProblemHandle(prob)
+    qa = np.ascontiguousarray(qa, dtype=np.float64)
+    qb = np.ascontiguousarray(qb, dtype=np.float64)
+    ta = np.ascontiguousarray(ta, dtype=np.float64)
+    tb = np.ascontiguousarray(tb, dtype=np.float64)
+    n = len(ta)
+    v = np.zeros(n, dtype=np.uint8)
+    clr = np.zeros(n)
+    r = lib().orc_check_edges_continuous(h.ref, n, _dptr(qa), _dptr(ta), _dptr(qb), _dptr(tb),
+                                         v.ctypes.data_as(_U8), _dptr(clr))
+    if r != 0:
+        raise ValueError("continuous validation needs a point robot")
+    return v, clr

@@ -287,6 +287,65 @@ bool edge_free(const Problem& P, const double* qa, double ta, const double* qb, 
     return free;
 }
 
+// Continuous edge validation for a point robot (translation only): between
+// consecutive breakpoints (the edge's end times and every obstacle waypoint
+// time inside them) each robot sphere and each obstacle move linearly, so
+// their difference d(t) runs along the segment from d(tau_i) to d(tau_i+1) and
+// its smallest norm is the distance from the origin to that segment (closed
+// form). Clearance = the exact minimum of |p - o| - r - r_o over [t_a, t_b];
+// a pair collides iff that minimum squared distance < (r + r_o)^2 (touching is
+// free); the segment stays in the convex configuration box iff both ends do.
+bool edge_free_continuous(const Problem& P, const double* qa, double ta, const double* qb, double tb,
+                          double* clearance) {
+    const int S = (int)P.sph_r.size();
+    bool free = in_bounds(P, qa) && in_bounds(P, qb);
+    double clr = kInf;
+    std::vector<Frame> fa, fb;
+    std::vector<double> ca, cb, qm(P.dof);
+    for (int m = 0; m < P.n_obs; ++m) {
+        const double* W = &P.way[(size_t)m * P.n_way * 4];
+        std::vector<double> tau{ta};
+        for (int k = 0; k < P.n_way; ++k)
+            if (W[4 * k] > ta && W[4 * k] < tb) tau.push_back(W[4 * k]);
+        tau.push_back(tb);
+        for (size_t i = 0; i + 1 < tau.size(); ++i) {
+            const double t0 = tau[i], t1 = tau[i + 1];
+            const double f0 = tb > ta ? (t0 - ta) / (tb - ta) : 0.0;
+            const double f1 = tb > ta ? (t1 - ta) / (tb - ta) : 0.0;
+            for (int j = 0; j < P.dof; ++j) qm[j] = qa[j] + f0 * (qb[j] - qa[j]);
+            forward_kinematics(P, qm.data(), fa);
+            sphere_centres(P, fa, ca);
+            for (int j = 0; j < P.dof; ++j) qm[j] = qa[j] + f1 * (qb[j] - qa[j]);
+            forward_kinematics(P, qm.data(), fb);
+            sphere_centres(P, fb, cb);
+            double o0[3], o1[3];
+            obstacle_position(P, m, t0, o0);
+            obstacle_position(P, m, t1, o1);
+            for (int sp = 0; sp < S; ++sp) {
+                double d0[3], w[3];
+                for (int k = 0; k < 3; ++k) {
+                    d0[k] = ca[3 * sp + k] - o0[k];
+                    w[k] = (cb[3 * sp + k] - o1[k]) - d0[k];
+                }
+                const double a = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+                const double b = d0[0] * w[0] + d0[1] * w[1] + d0[2] * w[2];
+                double u = a > 0.0 ? -b / a : 0.0;
+                u = std::min(std::max(u, 0.0), 1.0);
+                double d2 = 0.0;
+                for (int k = 0; k < 3; ++k) {
+                    const double e = d0[k] + u * w[k];
+                    d2 += e * e;
+                }
+                const double rr = P.sph_r[sp] + P.obs_r[m];
+                if (d2 < rr * rr) free = false;
+                clr = std::min(clr, std::sqrt(d2) - rr);
+            }
+        }
+    }
+    if (clearance) *clearance = clr;
+    return free;
+}
+
 // ---------------------------------------------------------------------------
 // Goal-time grid (Eq. goal-time-lower-bound): L_g = D(q_s,q_g)/v_max,
 // k_min = ceil(L_g/dt); goal checks at k dt in [L_g, H].
@@ -590,6 +649,7 @@ struct Params {
     double flag_tol = 1e-5;
     double flag_clear = 1e-5;  // clearance band (m)
     const double* proposal = nullptr;  // learned branch: network output y[160], or none
+    int continuous = 0;                // point robots: closed-form edge validation
 };
 
 // Smallest decision margins seen during one iteration (test diagnostics for
@@ -718,6 +778,11 @@ private:
     void check_edge(const double* qa, double ta, const double* qb, double tb, bool* ok, Margin& M) {
         double clr, im, bm;
         int c;
+        if (prm.continuous) {
+            *ok = edge_free_continuous(P, qa, ta, qb, tb, &clr);
+            note(M.clearance, clr);
+            return;
+        }
         *ok = edge_free(P, qa, ta, qb, tb, prm.res, &clr, &c, &im, &bm);
         note(M.clearance, clr);
         note(M.count, im);
@@ -1223,6 +1288,7 @@ typedef struct {
     int learned;              /* 1: learned branch with proposal[160] */
     const double* proposal;
     double t_offset;          /* absolute time of local time 0 */
+    int continuous;           /* 1: closed-form edge validation (point robots) */
 } orc_params;
 
 static Problem to_problem(const orc_problem* p) {
@@ -1291,6 +1357,21 @@ void orc_check_edges(const orc_problem* prob, int n, const double* qa, const dou
         if (int_margin) int_margin[e] = im;
         if (bound_margin) bound_margin[e] = bm;
     }
+}
+
+// Continuous verdicts and exact clearances of point-robot edges.
+int orc_check_edges_continuous(const orc_problem* prob, int n, const double* qa, const double* ta,
+                               const double* qb, const double* tb, unsigned char* verdict, double* clearance) {
+    Problem P = to_problem(prob);
+    if (P.arm) return -1;
+    int d = P.dof;
+    for (int e = 0; e < n; ++e) {
+        double clr;
+        bool ok = edge_free_continuous(P, qa + (size_t)e * d, ta[e], qb + (size_t)e * d, tb[e], &clr);
+        verdict[e] = ok ? 1 : 0;
+        if (clearance) clearance[e] = clr;
+    }
+    return 0;
 }
 
 // Interval-root partition from explicit grid flags (k = kmin..kmin+nk-1).
@@ -1410,6 +1491,10 @@ int orc_plan(const orc_problem* prob, const orc_params* p, orc_result** out) {
     if (p->learned) {
         if (!p->proposal) return -1;
         prm.proposal = p->proposal;
+    }
+    if (p->continuous) {
+        if (P.arm) return -1;
+        prm.continuous = 1;
     }
     Planner pl(P, prm);
     orc_result* r = new orc_result;
