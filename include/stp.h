@@ -109,7 +109,13 @@ typedef struct {
  *                  planned query by query (Sec. "Problem Formulation": each
  *                  query resets local time to zero, shifts obstacle
  *                  trajectories by its absolute start time and uses the
- *                  remaining horizon, passed as t_max). */
+ *                  remaining horizon, passed as t_max).
+ *   continuous     0 discrete edge validation at edge_res; 1 closed-form
+ *                  validation for point robots (arm = 0 only): between the
+ *                  edge's end times and the obstacle waypoint times inside
+ *                  them, robot spheres and obstacles move linearly, so the
+ *                  exact minimum distance of every pair is the distance from
+ *                  the origin to a segment. Not available in batches. */
 typedef struct {
     int variant;
     int n_roots;
@@ -129,6 +135,7 @@ typedef struct {
     int capacity;
     int iters_per_graph;
     double t_offset;
+    int continuous;
 } stp_params;
 
 /* Per-call statistics filled by stp_plan. Times are GPU times (CUDA events /

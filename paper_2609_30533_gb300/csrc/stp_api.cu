@@ -146,6 +146,7 @@ void fill_geom(stp_problem* p, Geom<R>& g, const R* blob, unsigned blob_bytes, i
     for (int i = 0; i < 3; ++i) g.ref[i] = R(0);
     if (!p->arm)
         for (int i = 0; i < 3 && i < p->dof; ++i) g.ref[i] = (R)(0.5 * (p->qlo[i] + p->qhi[i]));
+    g.continuous = p->prm.continuous;
     g.uniform_ro = 1;
     for (int m = 1; m < p->M; ++m)
         if (p->obs_r[m] != p->obs_r[0]) g.uniform_ro = 0;
@@ -663,6 +664,7 @@ stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, 
     if (P.precision != 0 && P.precision != 1) return STP_ERR_INVALID;
     if ((P.learned != 0 && P.learned != 1) || P.capacity < 0 || P.iters_per_graph < 0) return STP_ERR_INVALID;
     if (!(P.t_offset >= 0) || !std::isfinite(P.t_offset)) return STP_ERR_INVALID;
+    if (P.continuous != 0 && (P.continuous != 1 || robot->arm)) return STP_ERR_INVALID;
 
     stp_problem* p = new (std::nothrow) stp_problem();
     if (!p) return STP_ERR_CUDA;
@@ -1226,7 +1228,7 @@ extern "C" stp_status stp_batch_create(stp_problem* const* problems, int n, cons
     if (!out || !problems || n < 1 || n > 65535) return STP_ERR_INVALID;
     *out = nullptr;
     for (int i = 0; i < n; ++i)
-        if (!problems[i] || problems[i]->precision != 0) return STP_ERR_INVALID;
+        if (!problems[i] || problems[i]->precision != 0 || problems[i]->prm.continuous) return STP_ERR_INVALID;
     stp_batch* b = new (std::nothrow) stp_batch();
     if (!b) return STP_ERR_CUDA;
     b->probs.assign(problems, problems + n);

@@ -51,6 +51,7 @@ struct Geom {
     R vmax;
     R ref[3];       // reference point subtracted from workspace positions in pair tests
     double vmax_d;  // v_max as given (edge check counts are evaluated in double)
+    int continuous;  // point robots: closed-form edge validation
     int uniform_ro;  // every obstacle has the radius ro_uni
     R ro_uni;
     const R* blob;

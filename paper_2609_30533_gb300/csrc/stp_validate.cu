@@ -587,9 +587,106 @@ static cudaError_t launch_mo(const Geom<R>& g, const EdgeBatch<R>& e, int grid_b
     return launch_v<R, ARM, 32, CLEAR, EARLY>(g, e, grid_blocks, st);
 }
 
+// ---------------------------------------------------------------------------
+// Closed-form (continuous) validation of point-robot edges, one lane per
+// edge. Between consecutive breakpoints (the edge's end times and each
+// obstacle waypoint time inside them) a robot sphere and an obstacle both
+// move linearly, so their difference runs along the segment from d(t0) to
+// d(t1) and its smallest norm is the distance from the origin to that segment.
+// A pair collides iff that squared minimum < (r + r_o)^2; the edge stays in
+// the convex configuration box iff both ends do.
+// ---------------------------------------------------------------------------
+template <typename R, bool CLEAR>
+__global__ void __launch_bounds__(256) k_validate_cont(Geom<R> G, EdgeBatch<R> E) {
+    const int n = E.n_dev ? *E.n_dev : E.n_host;
+    if (n <= 0 || (E.done && *E.done)) return;
+    const R* sph = G.blob;
+    const R* way = G.blob + G.off_way;
+    const R* vel = G.blob + G.off_vel;
+    const R* rad = G.blob + G.off_rad;
+    unsigned long long done = 0, pairs_total = 0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        if (E.cnt[e] <= 0) continue;
+        const R* qa = E.qa + (size_t)e * E.qstride;
+        const R* qb = E.qb + (size_t)e * E.qstride;
+        const R ta = E.ta[e], tb = E.tb[e];
+        bool hit = false;
+        for (int j = 0; j < G.dof; ++j)
+            hit = hit || qa[j] < G.qlo[j] || qa[j] > G.qhi[j] || qb[j] < G.qlo[j] || qb[j] > G.qhi[j];
+        const R pa[3] = {qa[0], qa[1], G.dof > 2 ? qa[2] : R(0)};
+        const R pb[3] = {qb[0], qb[1], G.dof > 2 ? qb[2] : R(0)};
+        R clr = rinf<R>();
+        for (int m = 0; m < G.M; ++m) {
+            const R* W = way + 4 * G.K * m;
+            const R* V = vel + 4 * G.K * m;
+            const R ro = rad[m];
+            R t0 = ta;
+            for (int k = 0; k <= G.K; ++k) {
+                // next breakpoint: waypoint k if inside (ta, tb), the end at k == K
+                R t1;
+                if (k < G.K) {
+                    t1 = W[4 * k];
+                    if (!(t1 > ta && t1 < tb)) continue;
+                } else {
+                    t1 = tb;
+                }
+                const R f0 = tb > ta ? (t0 - ta) / (tb - ta) : R(0);
+                const R f1 = tb > ta ? (t1 - ta) / (tb - ta) : R(0);
+                R o0[3], o1[3];
+                obstacle_at(W, V, G.K, t0, o0[0], o0[1], o0[2]);
+                obstacle_at(W, V, G.K, t1, o1[0], o1[1], o1[2]);
+                for (int sp = 0; sp < G.S; ++sp) {
+                    R d0[3], w[3];
+                    for (int i = 0; i < 3; ++i) {
+                        const R c0 = (pa[i] + f0 * (pb[i] - pa[i])) + sph[4 * sp + i];
+                        const R c1 = (pa[i] + f1 * (pb[i] - pa[i])) + sph[4 * sp + i];
+                        d0[i] = c0 - o0[i];
+                        w[i] = (c1 - o1[i]) - d0[i];
+                    }
+                    const R a = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+                    const R b = d0[0] * w[0] + d0[1] * w[1] + d0[2] * w[2];
+                    R u = a > R(0) ? -b / a : R(0);
+                    u = u < R(0) ? R(0) : (u > R(1) ? R(1) : u);
+                    R d2 = R(0);
+                    for (int i = 0; i < 3; ++i) {
+                        const R x = d0[i] + u * w[i];
+                        d2 += x * x;
+                    }
+                    const R rr = sph[4 * sp + 3] + ro;
+                    hit = hit || (d2 < rr * rr);
+                    if (CLEAR) {
+                        const R cl = rsqrt_r(d2) - rr;
+                        clr = cl < clr ? cl : clr;
+                    }
+                }
+                pairs_total += (unsigned long long)G.S;
+                t0 = t1;
+            }
+        }
+        E.hit[e] = hit ? 1 : 0;
+        if (CLEAR) atomic_min_r<R>(E.clear + e, clr);  // order-encoded like the discrete path
+        ++done;
+    }
+    const int lane = threadIdx.x & 31;
+    if (E.points_done) {
+        for (int o = 16; o > 0; o >>= 1) done += __shfl_xor_sync(0xffffffffu, done, o);
+        if (lane == 0 && done) atomicAdd(E.points_done, done);
+    }
+    if (E.pairs_done) {
+        for (int o = 16; o > 0; o >>= 1) pairs_total += __shfl_xor_sync(0xffffffffu, pairs_total, o);
+        if (lane == 0 && pairs_total) atomicAdd(E.pairs_done, pairs_total);
+    }
+}
+
 template <typename R>
 cudaError_t launch_validate(const Geom<R>& g, const EdgeBatch<R>& e, bool clearance, bool early_exit,
                             int grid_blocks, cudaStream_t st) {
+    if (g.continuous) {
+        const int blocks = grid_blocks > 0 ? grid_blocks : validate_grid_blocks() * 2;
+        if (clearance) k_validate_cont<R, true><<<blocks, 256, 0, st>>>(g, e);
+        else k_validate_cont<R, false><<<blocks, 256, 0, st>>>(g, e);
+        return cudaGetLastError();
+    }
     if (g.arm) {
         if (clearance) return launch_mo<R, true, true, false>(g, e, grid_blocks, st);
         if (early_exit) return launch_mo<R, true, false, true>(g, e, grid_blocks, st);

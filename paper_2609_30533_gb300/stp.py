@@ -40,7 +40,8 @@ class StpParams(C.Structure):
                 ("edge_res", C.c_double), ("env_dt", C.c_double), ("p_new", C.c_double),
                 ("p_guided", C.c_double), ("t_max", C.c_double), ("seed", C.c_ulonglong),
                 ("problem_id", C.c_uint), ("precision", C.c_int), ("learned", C.c_int),
-                ("capacity", C.c_int), ("iters_per_graph", C.c_int), ("t_offset", C.c_double)]
+                ("capacity", C.c_int), ("iters_per_graph", C.c_int), ("t_offset", C.c_double),
+                ("continuous", C.c_int)]
 
 
 class StpStats(C.Structure):
@@ -192,7 +193,7 @@ class Problem:
     def __init__(self, *, dof, arm, dh, q_lo, q_hi, spheres, v_max, obs_radius, obs_way, q_start, q_goal,
                  variant=0, n_roots=4, ext_per_iter=64, max_iters=100, budget_ms=0.0, eta=0.1, edge_res=0.01,
                  env_dt=0.02, p_new=0.05, p_guided=0.95, t_max=10.0, seed=0, problem_id=0, precision=0,
-                 capacity=0, iters_per_graph=0, learned=0, t_offset=0.0):
+                 capacity=0, iters_per_graph=0, learned=0, t_offset=0.0, continuous=0):
         L = lib()
         self.dof = int(dof)
         self.precision = int(precision)
@@ -215,7 +216,7 @@ class Problem:
         self.params = StpParams(int(variant), int(n_roots), int(ext_per_iter), int(max_iters), float(budget_ms),
                                 float(eta), float(edge_res), float(env_dt), float(p_new), float(p_guided),
                                 float(t_max), int(seed), int(problem_id), int(precision), int(learned),
-                                int(capacity), int(iters_per_graph), float(t_offset))
+                                int(capacity), int(iters_per_graph), float(t_offset), int(continuous))
         h = C.c_void_p()
         s = L.stp_create_problem(C.byref(robot), C.byref(obstacles), _dp(arr(q_start)), _dp(arr(q_goal)),
                                  C.byref(self.params), C.byref(h))
