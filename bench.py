@@ -580,7 +580,7 @@ def main():
         plan_ms.append(st["plan_ms"])
         if st["first_solution_ms"] >= 0:
             fs_ms.append(st["first_solution_ms"])
-        launches += 2 + 7 * args.iters  # reset, 7 kernels per iteration, path extraction
+        launches += 2 + 8 * args.iters  # reset, 8 kernels per iteration, path extraction
     torch.cuda.synchronize()
     if dist:
         dist.barrier()

@@ -1552,8 +1552,17 @@ cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cud
     if (g.dof <= 3) k_bridge<R, 3><<<nn_grid, kQT, 0, st>>>(g, s);
     else k_bridge<R, kMaxDof><<<nn_grid, kQT, 0, st>>>(g, s);
     mark();
-    err = launch_validate<R>(g, bridge_batch(s), false, true, vgrid, st);
-    if (err != cudaSuccess) return err;
+    // Bridges are long: a coarse pass over every eighth check point finds most
+    // collisions, then only the entries it left free are checked in full.
+    {
+        EdgeBatch<R> bb = bridge_batch(s);
+        bb.phase = 1;
+        err = launch_validate<R>(g, bb, false, true, vgrid, st);
+        if (err != cudaSuccess) return err;
+        bb.phase = 2;
+        err = launch_validate<R>(g, bb, false, true, vgrid, st);
+        if (err != cudaSuccess) return err;
+    }
     mark();
     k_publish<R><<<1, kCtaThreads, 0, st>>>(g, s);
     mark();
@@ -1585,6 +1594,8 @@ cudaError_t launch_iteration_batch(const Geom<R>* Gs, const State<R>* Ss, const 
     k_insert_b<R><<<dim3(1, b.P), kCtaThreads, 0, st>>>(Gs, Ss);
     k_bridge_b<R, kMaxDof><<<dim3(b.nn_ctas, b.P), kQT, 0, st>>>(Gs, Ss);
     err = launch_validate_batch<R>(Gs, Ss, b.P, 1, b.max_obs, b.validate_ctas, b.validate_smem, st);
+    if (err != cudaSuccess) return err;
+    err = launch_validate_batch<R>(Gs, Ss, b.P, 2, b.max_obs, b.validate_ctas, b.validate_smem, st);
     if (err != cudaSuccess) return err;
     k_publish_b<R><<<dim3(1, b.P), kCtaThreads, 0, st>>>(Gs, Ss);
     return cudaGetLastError();

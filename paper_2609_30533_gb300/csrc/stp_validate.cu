@@ -419,13 +419,19 @@ __device__ __forceinline__ void validate_body(const Geom<R>& G, const EdgeBatch<
     if (!E.off) {
         const int per = (n + blockDim.x - 1) / blockDim.x;
         const int i0 = threadIdx.x * per, i1 = min(n, i0 + per);
+        auto eff = [&](int i) -> int {
+            const int c = E.cnt[i];
+            if (E.phase == 1) return (c + 7) >> 3;
+            if (E.phase == 2) return E.hit[i] ? 0 : c;
+            return c;
+        };
         int sum = 0;
-        for (int i = i0; i < i1; ++i) sum += E.cnt[i];
+        for (int i = i0; i < i1; ++i) sum += eff(i);
         int tot;
         int pre = block_scan_excl(sum, scan_sh, &tot);
         for (int i = i0; i < i1; ++i) {
             soff[i] = pre;
-            pre += E.cnt[i];
+            pre += eff(i);
         }
         if (threadIdx.x == 0) soff[n] = tot;
         __syncthreads();
@@ -447,7 +453,12 @@ __device__ __forceinline__ void validate_body(const Geom<R>& G, const EdgeBatch<
             if (*(volatile int*)(E.hit + e)) return;
         }
         const int c = E.cnt[e];
-        const R s = R(g - e_off + 1) / R(c);
+        int jj = (int)(g - e_off) + 1;
+        if (E.phase == 1) {
+            const int c0 = (c + 7) >> 3;
+            jj = (int)(((long long)jj * c + c0 - 1) / c0);
+        }
+        const R s = R(jj) / R(c);
         const R* qa = E.qa + (size_t)e * E.qstride;
         const R* qb = E.qb + (size_t)e * E.qstride;
         R q[kMaxDof];
@@ -536,7 +547,8 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 && MO <= 16) ? 2 : 1)
     __shared__ Geom<R> G;
     __shared__ State<R> S;
     stage_problem(Gs, Ss, blockIdx.y, G, S);
-    const EdgeBatch<R> E = which == 0 ? ext_batch(S) : bridge_batch(S);
+    EdgeBatch<R> E = which == 0 ? ext_batch(S) : bridge_batch(S);
+    E.phase = which >= 1 ? which : 0;   // which 1: coarse bridge pass, 2: remaining bridge points
     if (G.arm) validate_body<R, true, MO, false, true>(G, E, smem_raw);
     else validate_body<R, false, MO, false, true>(G, E, smem_raw);
 }
