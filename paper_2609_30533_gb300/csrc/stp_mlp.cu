@@ -40,7 +40,9 @@ namespace mlp {
 
 constexpr int kIn = 32, kInP = 64, kHid = 256, kOut = 160, kOutP = 256;
 constexpr int kMix = 8, kWp = 16, kWpDim = 8, kTgt = 130;
-constexpr int kTileM = 128, kStageK = 64, kThreads = 128;
+// Eight warps: warp w reads TMEM lane quadrant w % 4 (tile rows 32 (w % 4) ..
+// + 31) and columns [(w / 4) N/2, (w / 4 + 1) N/2) in the epilogue.
+constexpr int kTileM = 128, kStageK = 64, kThreads = 256;
 // Pipeline depth: products over K = 256 (four stages) use two stages, so that
 // two CTAs (2 x 97 KB of shared memory, 2 x 256 TMEM columns) share an SM and
 // one CTA's epilogue overlaps the other's copies and MMAs; the long-K weight-
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
     __shared__ uint32_t tmem_base_sh;
     __shared__ int fail_sh;
     __shared__ float sbias[N];  // bias (forward) or bias-gradient sums (backward)
-    __shared__ __align__(16) __nv_bfloat16 stile[4][16 * 32];
+    __shared__ __align__(16) __nv_bfloat16 stile[kThreads / 32][16 * 32];
 
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = smem;
@@ -274,11 +276,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
     __syncthreads();
     if (fail_sh) have = false;
 
-    // Epilogue: thread (warp, lane) owns tile row 32 warp + lane.
-    const int r = m0 + 32 * warp + lane;
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    // Epilogue: thread (warp, lane) owns tile row 32 (warp % 4) + lane and
+    // half of the columns.
+    const int quad = warp & 3;
+    const int r = m0 + 32 * quad + lane;
+    const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16);
+    const int cb = (warp >> 2) * (N / 2), ce = cb + N / 2;
 #pragma unroll 1
-    for (int c0 = 0; c0 < N; c0 += 16) {
+    for (int c0 = cb; c0 < ce; c0 += 16) {
         float v[16];
         if (have) tmem_ld16(trow + (uint32_t)c0, v);
         else {
@@ -289,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + sbias[c0 + i], 0.f);
             store_row16(g.out_t, r, c0, g.RA, v);
-            store_T_warp(g.out_tT, m0 + 32 * warp, c0, N, v, stile[warp]);
+            store_T_warp(g.out_tT, m0 + 32 * quad, c0, N, v, stile[warp]);
         } else if (MODE == kOutput) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] += sbias[c0 + i];
@@ -306,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
                     if (!(__bfloat162float(a[i]) > 0.f)) v[8 * h + i] = 0.f;
             }
             store_row16(g.out_t, r, c0, g.RA, v);
-            store_T_warp(g.out_tT, m0 + 32 * warp, c0, N, v, stile[warp]);
+            store_T_warp(g.out_tT, m0 + 32 * quad, c0, N, v, stile[warp]);
             const float cs = warp_colsum16(v);
             if (lane < 16) atomicAdd(&sbias[c0 + lane], cs);
         } else {  // kWGrad
