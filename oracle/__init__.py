@@ -22,7 +22,8 @@ _U8 = C.POINTER(C.c_ubyte)
 class OrcProblem(C.Structure):
     _fields_ = [("dof", C.c_int), ("arm", C.c_int), ("dh", _D), ("qlo", _D), ("qhi", _D),
                 ("n_sph", C.c_int), ("sph", _D), ("vmax", C.c_double), ("n_obs", C.c_int),
-                ("n_way", C.c_int), ("obs_r", _D), ("way", _D), ("qs", _D), ("qg", _D)]
+                ("n_way", C.c_int), ("obs_r", _D), ("way", _D), ("qs", _D), ("qg", _D),
+                ("self_collision", C.c_int)]
 
 
 class OrcParams(C.Structure):
@@ -63,6 +64,8 @@ def lib():
     L.orc_learned_sample.argtypes = [_D, _D, _D, _D, _D, C.c_int, C.c_double, C.c_ulonglong, C.c_uint, C.c_uint,
                                      C.c_uint, _I, _D, _D]
     L.orc_learned_sample.restype = C.c_int
+    L.orc_self_pairs.argtypes = [C.POINTER(OrcProblem), _I, C.c_int]
+    L.orc_self_pairs.restype = C.c_int
     L.orc_check_edges_continuous.argtypes = [C.POINTER(OrcProblem), C.c_int, _D, _D, _D, _D, _U8, _D]
     L.orc_check_edges_continuous.restype = C.c_int
     L.orc_plan.restype = C.c_int
@@ -100,7 +103,7 @@ class _ProblemHandle:
         self.s = OrcProblem(prob.dof, 1 if prob.arm else 0, keep(dh), keep(prob.qlo), keep(prob.qhi),
                             len(prob.spheres), keep(prob.spheres), float(prob.vmax),
                             len(prob.obs_r), prob.way.shape[1], keep(prob.obs_r), keep(prob.way),
-                            keep(prob.qs), keep(prob.qg))
+                            keep(prob.qs), keep(prob.qg), 1 if getattr(prob, "self_collision", False) else 0)
 
     @property
     def ref(self):
@@ -385,3 +388,12 @@ def check_edges_continuous(prob, qa, ta, qb, tb):
     if r != 0:
         raise ValueError("continuous validation needs a point robot")
     return v, clr
+
+
+def self_pairs(prob) -> np.ndarray:
+    """Self-collision sphere pairs [n][2] of an arm with self_collision set."""
+    h = _ProblemHandle(prob)
+    n = lib().orc_self_pairs(h.ref, None, 0)
+    out = np.zeros((max(n, 1), 2), dtype=np.int32)
+    lib().orc_self_pairs(h.ref, out.ctypes.data_as(_I), n)
+    return out[:n]

@@ -103,6 +103,9 @@ struct Problem {
     std::vector<double> obs_r;     // [M]
     std::vector<double> way;       // [M][K][4] t, x, y, z
     std::vector<double> qs, qg;    // [dof]
+    // Self-collision (arms, optional): sphere pairs (i < j) on frames at least
+    // two apart that do not already overlap at q = 0.
+    std::vector<std::pair<int, int>> self_pairs;
 };
 
 double dist(const double* a, const double* b, int d) {
@@ -225,6 +228,16 @@ bool state_free(const Problem& P, const double* q, double t, double* clearance) 
     bool free = in_bounds(P, q);
     double clr = kInf;
     int S = (int)P.sph_r.size();
+    // Self-collision: the same predicate between the robot's own spheres.
+    for (const auto& pr : P.self_pairs) {
+        const int a = pr.first, b = pr.second;
+        double dx = c[3 * a] - c[3 * b], dy = c[3 * a + 1] - c[3 * b + 1], dz = c[3 * a + 2] - c[3 * b + 2];
+        double d2 = dx * dx + dy * dy + dz * dz;
+        double rr = P.sph_r[a] + P.sph_r[b];
+        if (d2 < rr * rr) free = false;
+        double cl = std::sqrt(d2) - rr;
+        if (cl < clr) clr = cl;
+    }
     for (int m = 0; m < P.n_obs; ++m) {
         double o[3];
         obstacle_position(P, m, t, o);
@@ -1274,6 +1287,7 @@ typedef struct {
     const double* way;  // [M][K][4]
     const double* qs;
     const double* qg;
+    int self_collision;  // arms: also test sphere pairs of non-adjacent frames
 } orc_problem;
 
 typedef struct {
@@ -1310,7 +1324,36 @@ static Problem to_problem(const orc_problem* p) {
     P.way.assign(p->way, p->way + (size_t)p->n_obs * p->n_way * 4);
     P.qs.assign(p->qs, p->qs + p->dof);
     P.qg.assign(p->qg, p->qg + p->dof);
+    if (p->self_collision && P.arm) {
+        // Reading (self-collision, not in the paper's queries): spheres on the
+        // same or adjacent frames never count; pairs already overlapping at the
+        // zero configuration are treated as permanent contacts and ignored.
+        std::vector<double> zero(P.dof, 0.0), c;
+        std::vector<Frame> frames;
+        forward_kinematics(P, zero.data(), frames);
+        sphere_centres(P, frames, c);
+        const int S = (int)P.sph_r.size();
+        for (int a = 0; a < S; ++a)
+            for (int b = a + 1; b < S; ++b) {
+                if (std::abs(P.sph_link[a] - P.sph_link[b]) < 2) continue;
+                double dx = c[3 * a] - c[3 * b], dy = c[3 * a + 1] - c[3 * b + 1], dz = c[3 * a + 2] - c[3 * b + 2];
+                double rr = P.sph_r[a] + P.sph_r[b];
+                if (dx * dx + dy * dy + dz * dz < rr * rr) continue;
+                P.self_pairs.push_back({a, b});
+            }
+    }
     return P;
+}
+
+// Self-collision pairs of a problem (pins): [n][2].
+int orc_self_pairs(const orc_problem* prob, int* pairs, int cap) {
+    Problem P = to_problem(prob);
+    int n = (int)P.self_pairs.size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        pairs[2 * i] = P.self_pairs[i].first;
+        pairs[2 * i + 1] = P.self_pairs[i].second;
+    }
+    return n;
 }
 
 void orc_philox4x32_10(const unsigned int ctr[4], const unsigned int key[2], unsigned int out[4]) {

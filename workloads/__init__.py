@@ -63,6 +63,7 @@ class Problem:
     qs: np.ndarray                # [dof]
     qg: np.ndarray                # [dof]
     name: str = ""
+    self_collision: bool = False  # arms: also check the robot's own link spheres
 
 
 @dataclasses.dataclass
