@@ -115,7 +115,11 @@ typedef struct {
  *                  edge's end times and the obstacle waypoint times inside
  *                  them, robot spheres and obstacles move linearly, so the
  *                  exact minimum distance of every pair is the distance from
- *                  the origin to a segment. Not available in batches. */
+ *                  the origin to a segment. Not available in batches.
+ *   self_collision 0 off; 1 (arms only) also test the robot's own spheres with
+ *                  the same predicate: pairs on frames at least two apart,
+ *                  except pairs that already overlap at q = 0 (treated as
+ *                  permanent contacts). Not in the paper's queries. */
 typedef struct {
     int variant;
     int n_roots;
@@ -136,6 +140,7 @@ typedef struct {
     int iters_per_graph;
     double t_offset;
     int continuous;
+    int self_collision;
 } stp_params;
 
 /* Per-call statistics filled by stp_plan. Times are GPU times (CUDA events /

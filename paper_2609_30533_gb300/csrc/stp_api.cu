@@ -72,6 +72,7 @@ struct stp_problem {
     std::string last_error;
     bool planned = false;
     bool has_proposal = false;  // learned branch table set by stp_set_proposal
+    std::vector<int> self_pairs;  // self-collision pairs a * 64 + b (device sphere order)
     // profiling
     int profiling = 0;
     std::vector<cudaEvent_t> prof_ev;
@@ -119,7 +120,7 @@ double host_dist(const double* a, const double* b, int d) {
 
 template <typename R>
 void fill_geom(stp_problem* p, Geom<R>& g, const R* blob, unsigned blob_bytes, int off_way, int off_vel,
-               int off_rad, int off_tim, const std::vector<int>& link_start) {
+               int off_rad, int off_tim, int off_self, const std::vector<int>& link_start) {
     std::memset(&g, 0, sizeof(g));
     g.dof = p->dof;
     g.arm = p->arm;
@@ -157,11 +158,62 @@ void fill_geom(stp_problem* p, Geom<R>& g, const R* blob, unsigned blob_bytes, i
     g.off_vel = off_vel;
     g.off_rad = off_rad;
     g.off_tim = off_tim;
+    g.off_self = off_self;
+    g.n_self = (int)p->self_pairs.size();
+}
+
+// Self-collision pairs in the device sphere order (reading: spheres on frames
+// at least two apart, excluding pairs that already overlap at q = 0), encoded
+// a * 64 + b with a < b. Zero-configuration FK in FP64, standard DH.
+void compute_self_pairs(stp_problem* p, const std::vector<int>& order) {
+    p->self_pairs.clear();
+    if (!p->prm.self_collision || !p->arm) return;
+    struct F3 {
+        double X[3], Y[3], Z[3], o[3];
+    };
+    std::vector<F3> fr(1);
+    for (int i = 0; i < 3; ++i) {
+        fr[0].X[i] = i == 0;
+        fr[0].Y[i] = i == 1;
+        fr[0].Z[i] = i == 2;
+        fr[0].o[i] = 0.0;
+    }
+    for (int j = 0; j < p->dof; ++j) {
+        const double a = p->dh[4 * j], al = p->dh[4 * j + 1], d = p->dh[4 * j + 2], th = p->dh[4 * j + 3];
+        const double c = std::cos(th), sn = std::sin(th), ca = std::cos(al), sa = std::sin(al);
+        F3 f = fr.back(), g;
+        for (int i = 0; i < 3; ++i) {
+            const double u = c * f.X[i] + sn * f.Y[i], w = c * f.Y[i] - sn * f.X[i], z = f.Z[i];
+            g.X[i] = u;
+            g.Y[i] = ca * w + sa * z;
+            g.Z[i] = ca * z - sa * w;
+            g.o[i] = f.o[i] + a * u + d * z;
+        }
+        fr.push_back(g);
+    }
+    const int S = p->S;
+    std::vector<double> cs(3 * (size_t)S);
+    std::vector<int> link(S);
+    for (int k = 0; k < S; ++k) {
+        const double* sp = &p->sph[5 * order[k]];
+        const F3& f = fr[(int)sp[0]];
+        link[k] = (int)sp[0];
+        for (int i = 0; i < 3; ++i) cs[3 * k + i] = f.o[i] + sp[1] * f.X[i] + sp[2] * f.Y[i] + sp[3] * f.Z[i];
+    }
+    for (int a = 0; a < S; ++a)
+        for (int b = a + 1; b < S; ++b) {
+            if (std::abs(link[a] - link[b]) < 2) continue;
+            double d2 = 0.0;
+            for (int i = 0; i < 3; ++i) d2 += (cs[3 * a + i] - cs[3 * b + i]) * (cs[3 * a + i] - cs[3 * b + i]);
+            const double rr = p->sph[5 * order[a] + 4] + p->sph[5 * order[b] + 4];
+            if (d2 < rr * rr) continue;
+            p->self_pairs.push_back(a * 64 + b);
+        }
 }
 
 // Sizes and layout of the geometry blob in R units; returns bytes.
 template <typename R>
-size_t blob_layout(const stp_problem* p, int* off_way, int* off_vel, int* off_rad, int* off_tim) {
+size_t blob_layout(const stp_problem* p, int* off_way, int* off_vel, int* off_rad, int* off_tim, int* off_self) {
     size_t n = 4 * (size_t)p->S;
     *off_way = (int)n;
     n += 4 * (size_t)p->M * p->K;
@@ -171,13 +223,15 @@ size_t blob_layout(const stp_problem* p, int* off_way, int* off_vel, int* off_ra
     n += align_up((size_t)p->M, 4);
     *off_tim = (int)n;
     n += (size_t)kMaxWay * p->M;
+    *off_self = (int)n;
+    n += p->self_pairs.size();
     if (n == 0) n = 4;
     return align_up(n * sizeof(R), 16);
 }
 
 template <typename R>
 std::vector<R> blob_host(const stp_problem* p, const std::vector<int>& order, size_t bytes, int off_way,
-                         int off_vel, int off_rad, int off_tim) {
+                         int off_vel, int off_rad, int off_tim, int off_self) {
     std::vector<R> b(bytes / sizeof(R), R(0));
     for (int s = 0; s < p->S; ++s) {
         const double* sp = &p->sph[5 * order[s]];
@@ -200,6 +254,7 @@ std::vector<R> blob_host(const stp_problem* p, const std::vector<int>& order, si
             b[off_tim + (size_t)m * kMaxWay + k - 1] =
                 k < p->K ? (R)p->way[((size_t)m * p->K + k) * 4] : std::numeric_limits<R>::infinity();
     }
+    for (size_t i = 0; i < p->self_pairs.size(); ++i) b[off_self + i] = (R)p->self_pairs[i];
     return b;
 }
 
@@ -348,8 +403,9 @@ stp_status create_impl(stp_problem* p) {
         }
         link_start[nf] = p->S;
     }
-    int off_way, off_vel, off_rad, off_tim;
-    const size_t blob_bytes = blob_layout<R>(p, &off_way, &off_vel, &off_rad, &off_tim);
+    compute_self_pairs(p, order);
+    int off_way, off_vel, off_rad, off_tim, off_self;
+    const size_t blob_bytes = blob_layout<R>(p, &off_way, &off_vel, &off_rad, &off_tim, &off_self);
     R* blob;
     unsigned char* gfree;
     Ctl* ctl;
@@ -362,10 +418,11 @@ stp_status create_impl(stp_problem* p) {
     p->arena_bytes = bytes;
     layout_state<R>(p, p->d_arena, &blob, blob_bytes, &gfree, &ctl, &qdev, &tdev, &cnt, &off, &hit);
     p->d_ctl = ctl;
-    fill_geom<R>(p, geom_of<R>(p), blob, (unsigned)blob_bytes, off_way, off_vel, off_rad, off_tim, link_start);
+    fill_geom<R>(p, geom_of<R>(p), blob, (unsigned)blob_bytes, off_way, off_vel, off_rad, off_tim, off_self,
+                 link_start);
     State<R>& S = state_of<R>(p);
     cudaStream_t st = p->stream;
-    std::vector<R> hb = blob_host<R>(p, order, blob_bytes, off_way, off_vel, off_rad, off_tim);
+    std::vector<R> hb = blob_host<R>(p, order, blob_bytes, off_way, off_vel, off_rad, off_tim, off_self);
     STP_CUDA(p, cudaMemcpyAsync(blob, hb.data(), blob_bytes, cudaMemcpyHostToDevice, st));
     STP_CUDA(p, cudaMemsetAsync(S.tile_cnt, 0, sizeof(int) * (size_t)(p->prm.n_roots + 1) * kMaxQTiles, st));
     STP_CUDA(p, cudaMemsetAsync(S.btile_cnt, 0, sizeof(int) * 2 * kMaxQTiles, st));
@@ -665,6 +722,7 @@ stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, 
     if ((P.learned != 0 && P.learned != 1) || P.capacity < 0 || P.iters_per_graph < 0) return STP_ERR_INVALID;
     if (!(P.t_offset >= 0) || !std::isfinite(P.t_offset)) return STP_ERR_INVALID;
     if (P.continuous != 0 && (P.continuous != 1 || robot->arm)) return STP_ERR_INVALID;
+    if (P.self_collision != 0 && (P.self_collision != 1 || !robot->arm)) return STP_ERR_INVALID;
 
     stp_problem* p = new (std::nothrow) stp_problem();
     if (!p) return STP_ERR_CUDA;

@@ -57,6 +57,7 @@ struct Geom {
     const R* blob;
     unsigned blob_bytes;
     int off_way, off_vel, off_rad, off_tim;  // offsets in R units inside the blob
+    int off_self, n_self;  // self-collision pairs a * 64 + b (R values) and their count
 };
 
 // Flat batch of edges for the collision kernel. Entry e covers check points

@@ -358,6 +358,41 @@ __device__ __forceinline__ void check_point(const Geom<R>& G, const R* sm, const
     }
 }
 
+// Self-collision of an arm state (optional): FK into a lane-private table of
+// sphere centres, then the sphere predicate on the problem's pair list (pairs
+// on frames at least two apart that do not touch at q = 0), read from the
+// geometry blob in shared memory as a * 64 + b.
+template <typename R, bool CLEAR>
+__device__ __noinline__ void self_check(const Geom<R>& G, const R* sm, const R (&q)[kMaxDof], bool& hit, R& clr) {
+    R c[kMaxSpheres][3];
+    const R* sph = sm;
+    Frame<R> F;
+    frame_identity(F);
+    for (int j = 0; j <= G.dof; ++j) {
+        if (j > 0) frame_step(F, G.a[j - 1], G.d[j - 1], G.ca[j - 1], G.sa[j - 1], q[j - 1] + G.th0[j - 1]);
+        for (int s = G.link_start[j]; s < G.link_start[j + 1]; ++s) {
+            const R px = sph[4 * s], py = sph[4 * s + 1], pz = sph[4 * s + 2];
+            for (int i = 0; i < 3; ++i) c[s][i] = F.o[i] + px * F.X[i] + py * F.Y[i] + pz * F.Z[i];
+        }
+    }
+    const R* pairs = sm + G.off_self;
+    for (int k = 0; k < G.n_self; ++k) {
+        const int code = (int)pairs[k];
+        const int a = code >> 6, b = code & 63;
+        const R dx = c[a][0] - c[b][0], dy = c[a][1] - c[b][1], dz = c[a][2] - c[b][2];
+        const R d2 = dx * dx + dy * dy + dz * dz;
+        const R rr = sph[4 * a + 3] + sph[4 * b + 3];
+        if (d2 < rr * rr) {
+            hit = true;
+            if (!CLEAR) return;
+        }
+        if (CLEAR) {
+            const R cl = rsqrt_r(d2) - rr;
+            clr = cl < clr ? cl : clr;
+        }
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ void atomic_min_r(R* addr, R v);
 template <>
@@ -478,6 +513,7 @@ __device__ __forceinline__ void validate_body(const Geom<R>& G, const EdgeBatch<
         unsigned pairs = 0;
         if (ARM) check_point<R, true, MO, CLEAR, EARLY>(G, sm, q, t, hit, clr, pairs);
         else check_point<R, false, MO, CLEAR, EARLY>(G, sm, q, t, hit, clr, pairs);
+        if (ARM && G.n_self > 0 && (CLEAR || !hit)) self_check<R, CLEAR>(G, sm, q, hit, clr);
         if (hit) E.hit[e] = 1;
         if (CLEAR) atomic_min_r<R>(E.clear + e, clr);
         ++done;

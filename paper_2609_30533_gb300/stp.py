@@ -41,7 +41,7 @@ class StpParams(C.Structure):
                 ("p_guided", C.c_double), ("t_max", C.c_double), ("seed", C.c_ulonglong),
                 ("problem_id", C.c_uint), ("precision", C.c_int), ("learned", C.c_int),
                 ("capacity", C.c_int), ("iters_per_graph", C.c_int), ("t_offset", C.c_double),
-                ("continuous", C.c_int)]
+                ("continuous", C.c_int), ("self_collision", C.c_int)]
 
 
 class StpStats(C.Structure):
@@ -193,7 +193,7 @@ class Problem:
     def __init__(self, *, dof, arm, dh, q_lo, q_hi, spheres, v_max, obs_radius, obs_way, q_start, q_goal,
                  variant=0, n_roots=4, ext_per_iter=64, max_iters=100, budget_ms=0.0, eta=0.1, edge_res=0.01,
                  env_dt=0.02, p_new=0.05, p_guided=0.95, t_max=10.0, seed=0, problem_id=0, precision=0,
-                 capacity=0, iters_per_graph=0, learned=0, t_offset=0.0, continuous=0):
+                 capacity=0, iters_per_graph=0, learned=0, t_offset=0.0, continuous=0, self_collision=0):
         L = lib()
         self.dof = int(dof)
         self.precision = int(precision)
@@ -216,7 +216,8 @@ class Problem:
         self.params = StpParams(int(variant), int(n_roots), int(ext_per_iter), int(max_iters), float(budget_ms),
                                 float(eta), float(edge_res), float(env_dt), float(p_new), float(p_guided),
                                 float(t_max), int(seed), int(problem_id), int(precision), int(learned),
-                                int(capacity), int(iters_per_graph), float(t_offset), int(continuous))
+                                int(capacity), int(iters_per_graph), float(t_offset), int(continuous),
+                                int(self_collision))
         h = C.c_void_p()
         s = L.stp_create_problem(C.byref(robot), C.byref(obstacles), _dp(arr(q_start)), _dp(arr(q_goal)),
                                  C.byref(self.params), C.byref(h))
@@ -397,7 +398,7 @@ def problem_from(prob, params, **over) -> Problem:
     kw = dict(variant=params.variant, n_roots=params.n_roots, ext_per_iter=params.workers,
               max_iters=params.max_iters, eta=params.eta, edge_res=params.res, env_dt=params.dt,
               p_new=params.p_new, p_guided=params.p_guided, t_max=params.H, seed=params.seed,
-              problem_id=params.problem_id)
+              problem_id=params.problem_id, self_collision=1 if getattr(prob, "self_collision", False) else 0)
     kw.update(over)
     return Problem(dof=prob.dof, arm=prob.arm, dh=prob.dh, q_lo=prob.qlo, q_hi=prob.qhi, spheres=prob.spheres,
                    v_max=prob.vmax, obs_radius=prob.obs_r, obs_way=prob.way, q_start=prob.qs, q_goal=prob.qg,

@@ -53,7 +53,7 @@ def _params(**kw):
     from paper_2609_30533_gb300 import stp
     base = dict(variant=0, n_roots=4, ext_per_iter=64, max_iters=10, budget_ms=0.0, eta=0.1, edge_res=0.01,
                 env_dt=0.02, p_new=0.05, p_guided=0.95, t_max=20.0, seed=0, problem_id=0, precision=0,
-                learned=0, capacity=0, iters_per_graph=0, t_offset=0.0, continuous=0)
+                learned=0, capacity=0, iters_per_graph=0, t_offset=0.0, continuous=0, self_collision=0)
     base.update(kw)
     return stp.StpParams(**base)
 
@@ -78,7 +78,7 @@ def _create(prob, params):
 
 @pytest.mark.parametrize("bad", [dict(n_roots=0), dict(ext_per_iter=0), dict(variant=7), dict(eta=0.0),
                                  dict(p_new=1.5), dict(precision=2), dict(learned=2), dict(max_iters=0),
-                                 dict(t_offset=-1.0), dict(continuous=2)])
+                                 dict(t_offset=-1.0), dict(continuous=2), dict(self_collision=1)])
 def test_invalid_params_rejected_before_any_device_call(L, bad):
     prob, _ = WL.disc2d(0)
     s, h = _create(prob, _params(**bad))
