@@ -86,7 +86,10 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index)
+        # Raw samples go to $STP_CLOCKS_DIR (default: the system temp directory).
+        import tempfile
+        out_dir = os.environ.get("STP_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, "clocks_rank%d.csv" % gpu_index)
 
     def start(self):
         try:
