@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
     const int cb = (warp >> 2) * (N / 2), ce = cb + N / 2;
 #pragma unroll 1
     for (int c0 = cb; c0 < ce; c0 += 16) {
+        if (MODE == kOutput && c0 >= kOut) continue;  // padding outputs are never read (warp-uniform)
         float v[16];
         if (have) tmem_ld16(trow + (uint32_t)c0, v);
         else {
