@@ -493,7 +493,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--iters", type=int, default=32, help="planner iterations per step")
-    ap.add_argument("--ref-iters", type=int, default=2)
+    ap.add_argument("--ref-iters", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=8)
     ap.add_argument("--micro-edges", type=int, default=1 << 20)
     ap.add_argument("--no-cpu", action="store_true")
