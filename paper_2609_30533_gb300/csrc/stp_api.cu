@@ -461,8 +461,7 @@ stp_status create_impl(stp_problem* p) {
     STP_CUDA(p, cudaMemcpyAsync(cnt, hcnt.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, st));
     STP_CUDA(p, cudaMemcpyAsync(off, hoff.data(), sizeof(long long) * (ng + 1), cudaMemcpyHostToDevice, st));
     STP_CUDA(p, cudaMemsetAsync(hit, 0, sizeof(int) * ng, st));
-    EdgeBatch<R> E;
-    std::memset(&E, 0, sizeof(E));
+    EdgeBatch<R> E{};
     E.done = nullptr;
     E.qa = qall;
     E.qb = qall;
@@ -641,8 +640,7 @@ stp_status check_edges_impl(stp_problem* p, int n, const void* qa, const void* t
         unsigned long long inf_bits = sizeof(R) == 4 ? 0x7f800000ull : 0x7ff0000000000000ull;
         STP_CUDA(p, launch_fill(L.clr, n, (int)sizeof(R), inf_bits, st));
     }
-    EdgeBatch<R> E;
-    std::memset(&E, 0, sizeof(E));
+    EdgeBatch<R> E{};
     E.qa = dqa;
     E.qb = dqb;
     E.ta = dta;
@@ -1124,8 +1122,7 @@ stp_status check_edges_noalloc_impl(stp_problem* p, int n, const void* qa, const
     STP_CUDA(p, launch_scan_counts(cnt, n, off, tmp, st));
     // The array keeps the previous call's flags: clear them.
     STP_CUDA(p, cudaMemsetAsync(hit, 0, sizeof(int) * (size_t)n, st));
-    EdgeBatch<R> E;
-    std::memset(&E, 0, sizeof(E));
+    EdgeBatch<R> E{};
     E.qa = dqa;
     E.qb = dqb;
     E.ta = dta;
