@@ -262,15 +262,22 @@ def batched(args, rank):
     edges = sum(st["edges_validated"] + st["bridges_validated"] for st in stats)
 
     # Plain: the same problems one at a time (sample), same W and budget.
-    plain_fs, plain_ms, plain_solved = [], [], 0
+    # As a queue (one after another from a common start), a problem's first
+    # solution waits for every earlier problem's whole plan.
+    plain_fs, plain_ms, plain_solved, queue_fs = [], [], 0, []
+    elapsed = 0.0
     for i in idx[:args.plain_sample]:
         out = probs[i].plan()
         plain_ms.append(out.stats["plan_ms"])
         if out.stats["first_solution_iter"] >= 0:
             plain_solved += 1
             plain_fs.append(out.stats["first_solution_ms"])
+            queue_fs.append(elapsed + out.stats["first_solution_ms"])
+        elapsed += out.stats["plan_ms"]
     for P in probs:
         P.close()
+    chosen = [t for t in choice.trials if (t.workers, t.nn_ctas, t.validate_ctas) ==
+              (choice.workers, choice.nn_ctas, choice.validate_ctas)][0]
 
     def pct(v, q):
         return float(np.percentile(v, q)) if v else None
@@ -283,6 +290,12 @@ def batched(args, rank):
         "batch_ms": ms, "problems_per_s": len(idx) / (ms * 1e-3), "edges_per_s": edges / (ms * 1e-3),
         "solved": len(fs), "success_rate": len(fs) / len(idx),
         "first_solution_ms_p50": pct(fs, 50), "first_solution_ms_p99": pct(fs, 99),
+        "same_48_problems": {"note": "the autotuner's sample planned as one batch (chosen configuration, "
+                                     "--tune-iters iterations) against the same problems planned one after "
+                                     "another from a common start (--batch-iters iterations each)",
+                             "batched_solved": chosen.solved, "batched_p50_first_ms": chosen.p50_first_ms,
+                             "queue_solved": plain_solved, "queue_p50_first_ms": pct(queue_fs, 50),
+                             "queue_total_ms": elapsed, "batched_total_ms": chosen.batch_ms},
         "plain_sample": {"problems": len(plain_ms), "solved": plain_solved,
                          "first_solution_ms_p50": pct(plain_fs, 50), "first_solution_ms_p99": pct(plain_fs, 99),
                          "ms_per_problem_p50": pct(plain_ms, 50), "sequential_ms_per_problem": float(np.mean(plain_ms)),
