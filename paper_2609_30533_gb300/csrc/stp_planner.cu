@@ -67,6 +67,47 @@ __device__ __forceinline__ R qdist(const R* a, const R* b, int dof) {
     return rsqrt_r(s);
 }
 
+// Node rows (kDP values, 16-byte aligned) moved as 16-byte vectors.
+template <typename R>
+__device__ __forceinline__ void ld_row(const R* src, R (&v)[kDP]) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 a = reinterpret_cast<const float4*>(src)[0], b = reinterpret_cast<const float4*>(src)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kDP / 2; ++k) {
+            const double2 a = reinterpret_cast<const double2*>(src)[k];
+            v[2 * k] = a.x;
+            v[2 * k + 1] = a.y;
+        }
+    }
+}
+template <typename R>
+__device__ __forceinline__ void st_row(R* dst, const R (&v)[kDP]) {
+    if constexpr (sizeof(R) == 4) {
+        reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kDP / 2; ++k) reinterpret_cast<double2*>(dst)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+    }
+}
+// qdist of two rows held in registers (same operations in the same order).
+template <typename R, int N>
+__device__ __forceinline__ R qdist_rows(const R (&a)[N], const R (&b)[N], int dof) {
+    static_assert(N >= kMaxDof, "rows hold every configuration coordinate");
+    R s = R(0);
+#pragma unroll
+    for (int j = 0; j < kMaxDof; ++j) {
+        if (j < dof) {
+            R e = b[j] - a[j];
+            s += e * e;
+        }
+    }
+    return rsqrt_r(s);
+}
+
 __device__ __forceinline__ double qdist_d(const double* a, const double* b, int dof) {
     double s = 0.0;
     for (int j = 0; j < dof; ++j) {
@@ -206,14 +247,18 @@ __device__ R sample_goal_time(const State<R>& S, int g, uint32_t m_coin, R u_pos
 // slots 15-16) when that time lies in the sampled group's uniform interval.
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ __forceinline__ void learned_q(const Geom<R>& G, const State<R>& S, const uint32_t* d, R* qr) {
+__device__ __forceinline__ void learned_q(const Geom<R>& G, const State<R>& S, const uint32_t (&d)[20],
+                                          R (&qr)[kMaxDof]) {
     const int i = (int)(((unsigned long long)(d[13] >> 8) * 16ull) >> 24);
     const R* wq = S.prop + 24 + i * kMaxDof;
-    for (int j = 0; j < G.dof; ++j) {
-        const R half = R(0.1) * (G.qhi[j] - G.qlo[j]);
-        R q = wq[j] + half * (R(2) * uni_r<R>(d[4 + j]) - R(1));
-        q = q > G.qlo[j] ? q : G.qlo[j];
-        qr[j] = q < G.qhi[j] ? q : G.qhi[j];
+#pragma unroll
+    for (int j = 0; j < kMaxDof; ++j) {
+        if (j < G.dof) {
+            const R half = R(0.1) * (G.qhi[j] - G.qlo[j]);
+            R q = wq[j] + half * (R(2) * uni_r<R>(d[4 + j]) - R(1));
+            q = q > G.qlo[j] ? q : G.qlo[j];
+            qr[j] = q < G.qhi[j] ? q : G.qhi[j];
+        }
     }
 }
 
@@ -225,7 +270,7 @@ __device__ __forceinline__ float exp_r(float x) { return expf(x); }
 __device__ __forceinline__ double exp_r(double x) { return exp(x); }
 
 template <typename R>
-__device__ __forceinline__ R learned_T(const State<R>& S, const uint32_t* d) {
+__device__ __forceinline__ R learned_T(const State<R>& S, const uint32_t (&d)[20]) {
     const R u = uni_r<R>(d[14]);
     int k = 0;
     while (k < 7 && !(u < S.prop[k])) ++k;
@@ -490,19 +535,42 @@ __device__ __forceinline__ int check_count_r(const R* qa, R ta, const R* qb, R t
     return c < R(1) ? 1 : (int)c;
 }
 
+// check_count_r of two rows held in registers (same operations and order).
+template <typename R>
+__device__ __forceinline__ int check_count_rows(const R (&qa)[kDP], R ta, const R (&qb)[kDP], R tb, int dof, R vmax,
+                                                R res) {
+    R s2 = R(0);
+#pragma unroll
+    for (int j = 0; j < kMaxDof; ++j) {
+        if (j < dof) {
+            R e = qb[j] - qa[j];
+            s2 += e * e;
+        }
+    }
+    R dt = tb - ta;
+    R L = rsqrt_r(s2);
+    R Lt = vmax * (dt < R(0) ? -dt : dt);
+    if (Lt > L) L = Lt;
+    R c = ceil(L / res - R(1e-3));
+    return c < R(1) ? 1 : (int)c;
+}
+
 // Steer from x_n toward the worker's sample (Algorithm 1 / Eq.
 // max-speed-extension), check the horizon and emit the entries. Returns false
-// when the attempt is skipped.
+// when the attempt is skipped. Rows live in registers and move as vectors.
 template <typename R>
-__device__ bool steer_and_emit(const Geom<R>& G, const State<R>& S, int w, int set, bool virt, const R* xn) {
+__device__ __forceinline__ bool steer_and_emit(const Geom<R>& G, const State<R>& S, int w, int set, bool virt,
+                                               const R (&xn)[kDP]) {
     const int dof = G.dof;
-    const R* xr = S.w_xr + (size_t)w * kDP;
+    R xr[kDP];
+    ld_row(S.w_xr + (size_t)w * kDP, xr);
     R xw[kDP];
+#pragma unroll
     for (int j = 0; j < kDP; ++j) xw[j] = R(0);
     R tnew;
     if (S.variant == 0) {
         const R tn = xn[kDP - 1], tr = xr[kDP - 1];
-        const R D = qdist(xn, xr, dof);
+        const R D = qdist_rows(xn, xr, dof);
         if (virt) {
             // The virtual root is the sole source: rho must be finite.
             const R Delta = tn - tr;
@@ -511,33 +579,36 @@ __device__ bool steer_and_emit(const Geom<R>& G, const State<R>& S, int w, int s
         const R rho = rsqrt_r((D * D + G.vmax * G.vmax * (tr - tn) * (tr - tn)) / R(2));
         const R eta = (R)S.eta;
         const R alpha = (eta / rho) < R(1) ? (eta / rho) : R(1);
-        for (int j = 0; j < dof; ++j) xw[j] = xn[j] + alpha * (xr[j] - xn[j]);
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j)
+            if (j < dof) xw[j] = xn[j] + alpha * (xr[j] - xn[j]);
         tnew = tn + alpha * (tr - tn);
     } else {
-        const R D = qdist(xn, xr, dof);
+        const R D = qdist_rows(xn, xr, dof);
         if (!(D > R(0))) return false;
         const R eta = (R)S.eta;
         const R sc = (eta / D) < R(1) ? (eta / D) : R(1);
-        for (int j = 0; j < dof; ++j) xw[j] = xn[j] + sc * (xr[j] - xn[j]);
-        const R Dn = qdist(xn, xw, dof);
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j)
+            if (j < dof) xw[j] = xn[j] + sc * (xr[j] - xn[j]);
+        const R Dn = qdist_rows(xn, xw, dof);
         tnew = xn[kDP - 1] + (set == 0 ? R(1) : R(-1)) * Dn / G.vmax;
     }
     xw[kDP - 1] = tnew;
     if (tnew < R(0) || tnew > (R)S.H) return false;
-    R* xo = S.w_xnew + (size_t)w * kDP;
-    R* xs = S.w_xn + (size_t)w * kDP;
-    for (int j = 0; j < kDP; ++j) {
-        xo[j] = xw[j];
-        xs[j] = xn[j];
-    }
+    st_row(S.w_xnew + (size_t)w * kDP, xw);
+    st_row(S.w_xn + (size_t)w * kDP, xn);
     const R res = (R)S.res;
     if (S.variant == 0) {
         // Point check of the sampled goal root (q_g, T).
         const int e = 2 * w;
-        R* qa = S.eqa + (size_t)e * kDP;
-        R* qb = S.eqb + (size_t)e * kDP;
-        for (int j = 0; j < kDP; ++j) qa[j] = qb[j] = R(0);
-        for (int j = 0; j < kMaxDof; ++j) qa[j] = qb[j] = S.qg[j];
+        R g[kDP];
+#pragma unroll
+        for (int j = 0; j < kDP; ++j) g[j] = R(0);
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j) g[j] = S.qg[j];
+        st_row(S.eqa + (size_t)e * kDP, g);
+        st_row(S.eqb + (size_t)e * kDP, g);
         const R T = (R)S.w_T[w];
         S.eta_[e] = T;
         S.etb[e] = T;
@@ -545,15 +616,11 @@ __device__ bool steer_and_emit(const Geom<R>& G, const State<R>& S, int w, int s
         S.w_root_edge[w] = e;
     }
     const int e = 2 * w + 1;
-    R* qa = S.eqa + (size_t)e * kDP;
-    R* qb = S.eqb + (size_t)e * kDP;
-    for (int j = 0; j < kDP; ++j) {
-        qa[j] = xn[j];
-        qb[j] = xw[j];
-    }
+    st_row(S.eqa + (size_t)e * kDP, xn);
+    st_row(S.eqb + (size_t)e * kDP, xw);
     S.eta_[e] = xn[kDP - 1];
     S.etb[e] = tnew;
-    S.ecnt[e] = check_count_r(xn, xn[kDP - 1], xw, tnew, dof, G.vmax, res);
+    S.ecnt[e] = check_count_rows(xn, xn[kDP - 1], xw, tnew, dof, G.vmax, res);
     S.w_edge[w] = e;
     return true;
 }
@@ -619,13 +686,20 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
         }
         S.w_T[w] = Tr;
         // Conditional query time (Eq. conditional-query-time).
-        const R lo = qdist(S.qs, qr, dof) / G.vmax;
-        const R hi = Tr - qdist(qr, S.qg, dof) / G.vmax;
+        const R lo = qdist_rows(S.qs, qr, dof) / G.vmax;
+        const R hi = Tr - qdist_rows(qr, S.qg, dof) / G.vmax;
         if (!(lo > hi)) {
-            const R tr = lo + uni_r<R>(d[4 + dof]) * (hi - lo);
+            // Slot 4 + d (selected without a dynamic index into d).
+            uint32_t dword = d[4];
 #pragma unroll
-            for (int j = 0; j < kMaxDof; ++j) xr[j] = qr[j];
-            xr[kDP - 1] = tr;
+            for (int j = 1; j <= kMaxDof; ++j)
+                if (j == dof) dword = d[4 + j];
+            const R tr = lo + uni_r<R>(dword) * (hi - lo);
+            R row[kDP];
+#pragma unroll
+            for (int j = 0; j < kMaxDof; ++j) row[j] = qr[j];
+            row[kDP - 1] = tr;
+            st_row(xr, row);
             set = fwd ? 0 : 1 + g;
             if (fwd) {
                 status = kNN;
@@ -638,9 +712,11 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
         int slot = -1;
         if (!fwd && s_nact > 0) slot = s_act[(w / 2) % s_nact];
         if (fwd || slot >= 0) {
+            R row[kDP];
 #pragma unroll
-            for (int j = 0; j < kMaxDof; ++j) xr[j] = qr[j];
-            xr[kDP - 1] = R(0);
+            for (int j = 0; j < kMaxDof; ++j) row[j] = qr[j];
+            row[kDP - 1] = R(0);
+            st_row(xr, row);
             set = fwd ? 0 : 1 + slot;
             status = kNN;
         }
@@ -648,7 +724,7 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
     if (status == kVirtual) {
         // The virtual root (q_g, T) is the sole source: steer at once.
         R xn[kDP];
-        for (int j = 0; j < kDP; ++j) xn[j] = R(0);
+#pragma unroll
         for (int j = 0; j < kMaxDof; ++j) xn[j] = S.qg[j];
         xn[kDP - 1] = (R)S.w_T[w];
         if (!steer_and_emit(G, S, w, set, true, xn)) status = kSkip;
@@ -665,6 +741,38 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
 // ---------------------------------------------------------------------------
 // Tile scheduler shared by the NN and bridge scans.
 // ---------------------------------------------------------------------------
+// Node tiles in shared memory hold one row per node: DQ coordinates, time,
+// and a flag/root-time word, padded to whole 16-byte vectors so that a scan
+// step reads a node with 16-byte loads (two for DQ = 3 or 6, three for 7).
+template <typename R, int DQ>
+__host__ __device__ constexpr int tile_row() {
+    return (int)((((DQ + 2) * sizeof(R) + 15) / 16) * 16 / sizeof(R));
+}
+
+template <typename R, int N>
+__device__ __forceinline__ void lds_row(const R* row, R (&v)[N]) {
+    static_assert((N * sizeof(R)) % 16 == 0, "tile rows are whole 16-byte vectors");
+    if constexpr (sizeof(R) == 4) {
+        const float4* p = reinterpret_cast<const float4*>(row);
+#pragma unroll
+        for (int k = 0; k < N / 4; ++k) {
+            const float4 a = p[k];
+            v[4 * k] = a.x;
+            v[4 * k + 1] = a.y;
+            v[4 * k + 2] = a.z;
+            v[4 * k + 3] = a.w;
+        }
+    } else {
+        const double2* p = reinterpret_cast<const double2*>(row);
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) {
+            const double2 a = p[k];
+            v[2 * k] = a.x;
+            v[2 * k + 1] = a.y;
+        }
+    }
+}
+
 struct TileSets {
     int pre[kMaxRoots + 2];  // tile prefix per set
     int nq[kMaxRoots + 1];
@@ -709,7 +817,8 @@ __device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S) {
     const Ctl* c = S.ctl;
     if (c->done) return;
     __shared__ TileSets ts;
-    __shared__ R sx[kQT][DQ + 2];
+    constexpr int kRow = tile_row<R, DQ>();
+    __shared__ __align__(16) R sx[kQT][kRow];
     __shared__ int s_last;
     const int t = threadIdx.x;
     const int nsets = S.N + 1;
@@ -779,16 +888,18 @@ __device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S) {
             __syncthreads();
             if (w >= 0) {
                 auto key_of = [&](int i) -> R {
+                    R r[kRow];
+                    lds_row<R, kRow>(sx[i], r);
                     R D2 = R(0);
 #pragma unroll
                     for (int j = 0; j < DQ; ++j) {
-                        R e = sx[i][j] - q[j];
+                        R e = r[j] - q[j];
                         D2 += e * e;
                     }
                     if (!interval) return D2;
-                    const R dt = tr - sx[i][DQ];
+                    const R dt = tr - r[DQ];
                     const R Delta = fwd ? dt : -dt;
-                    const bool ok = (sx[i][DQ + 1] != R(0)) && (Delta > R(0)) && (D2 <= v2 * Delta * Delta);
+                    const bool ok = (r[DQ + 1] != R(0)) && (Delta > R(0)) && (D2 <= v2 * Delta * Delta);
                     return ok ? D2 + v2 * dt * dt : rinf<R>();
                 };
                 // Four independent key chains per step; updates in index order
@@ -850,10 +961,8 @@ __device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S) {
                 S.w_parent[w] = p;
                 bool ok = p >= 0;
                 if (ok) {
-                    const R* x = s == 0 ? fnode(S, p) : bnode(S, s - 1, p);
                     R xn[kDP];
-#pragma unroll
-                    for (int j = 0; j < kDP; ++j) xn[j] = x[j];
+                    ld_row(s == 0 ? fnode(S, p) : bnode(S, s - 1, p), xn);
                     ok = steer_and_emit(G, S, w, s, false, xn);
                 }
                 if (!ok) S.w_status[w] = kSkip;
@@ -893,44 +1002,61 @@ __device__ __forceinline__ long long cta_exclusive_scan(long long v, long long* 
 
 // ---------------------------------------------------------------------------
 // k_insert: single CTA. Ordered insertion in worker order; also clears the
-// per-worker bridge state of the iteration.
+// per-worker bridge state of the iteration. Every load a chunk needs is issued
+// in two rounds (the worker records with the control words, then the parents'
+// records), and the bridge-query lists are filled in worker order from a scan.
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ void insert_body(const Geom<R>& G, const State<R>& S) {
     Ctl* c = S.ctl;
-    if (c->done) return;
     __shared__ int wt[kCtaThreads / 32][kMaxRoots + 1];
     __shared__ int base[kMaxRoots + 1];
     __shared__ long long sh[32];
     __shared__ int tree_base;
     __shared__ int overflow;
+    __shared__ long long bq_base;   // forward count (low 32 bits), backward count (high)
     __shared__ unsigned long long n_ins_total, n_ext_total;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int nsets = S.N + 1;
     const int dof = G.dof;
-    for (int s = t; s < nsets; s += blockDim.x) {
-        base[s] = s == 0 ? c->n_f : c->n_s[s - 1];
-        if (s == 0) c->snap_f = c->n_f;
-        else c->snap_s[s - 1] = c->n_s[s - 1];
-    }
+    const int done = c->done;
+    const int iter = c->iter;
+    const int n_trees = c->n_trees;
+    for (int s = t; s < nsets; s += blockDim.x) base[s] = s == 0 ? c->n_f : c->n_s[s - 1];
     if (t == 0) {
-        tree_base = c->n_trees;
+        tree_base = n_trees;
         overflow = 0;
+        bq_base = 0;
         n_ins_total = 0;
         n_ext_total = 0;
     }
-    __syncthreads();
     for (int r0 = 0; r0 < S.W; r0 += kCtaThreads) {
         const int w = r0 + t;
+        // Round 1: the worker's records (entries of worker w sit at 2w, 2w+1).
+        int e = -1, re = -1, h_root = 0, h_ext = 0, wset = -1, wst = 0, p = -1;
+        R xw[kDP];
+#pragma unroll
+        for (int j = 0; j < kDP; ++j) xw[j] = R(0);
+        if (w < S.W) {
+            e = S.w_edge[w];
+            re = S.w_root_edge[w];
+            h_root = S.ehit[2 * w];
+            h_ext = S.ehit[2 * w + 1];
+            wset = S.w_set[w];
+            wst = S.w_status[w];
+            p = S.w_parent[w];
+            ld_row(S.w_xnew + (size_t)w * kDP, xw);
+        }
+        if (r0 == 0) {
+            __syncthreads();   // base[], tree_base and the counters are set
+            if (done) return;
+            for (int s = t; s < nsets; s += blockDim.x) {
+                if (s == 0) c->snap_f = base[0];
+                else c->snap_s[s - 1] = base[s];
+            }
+        }
         int ok = 0, nodes = 0, set = -1, virt = 0, ext = 0;
         if (w < S.W) {
-            // Independent loads first (entries of worker w sit at 2w, 2w+1).
-            const int e = S.w_edge[w];
-            const int re = S.w_root_edge[w];
-            const int h_root = S.ehit[2 * w];
-            const int h_ext = S.ehit[2 * w + 1];
-            const int wset = S.w_set[w];
-            const int wst = S.w_status[w];
             S.b_idx[w] = -1;
             S.w_bedge[w] = -1;
             S.bcnt[w] = 0;
@@ -946,6 +1072,27 @@ __device__ __forceinline__ void insert_body(const Geom<R>& G, const State<R>& S)
                 nodes = virt ? 2 : 1;
             }
         }
+        // Round 2: the parent's record (or the virtual root's time), in flight
+        // during the scans below.
+        R pcost = R(0), ptroot = R(0), T = R(0);
+        int ptree = 0;
+        R px[kDP];
+#pragma unroll
+        for (int j = 0; j < kDP; ++j) px[j] = R(0);
+        if (ok) {
+            if (set == 0) {
+                pcost = S.fcost[p];
+                ld_row(fnode(S, p), px);
+            } else if (virt) {
+                T = S.w_T[w];
+            } else {
+                const size_t op = bofs(S, set - 1, p);
+                pcost = S.bcost[op];
+                ptroot = S.btroot[op];
+                ptree = S.btree[op];
+                ld_row(bnode(S, set - 1, p), px);
+            }
+        }
         // Rank among earlier lanes of this warp in the same set (weights 1 or 2).
         const unsigned same = __match_any_sync(0xffffffffu, set);
         const unsigned lt = (1u << lane) - 1u;
@@ -957,76 +1104,86 @@ __device__ __forceinline__ void insert_body(const Geom<R>& G, const State<R>& S)
         __syncthreads();
         if (set >= 0 && last_of_set) wt[warp][set] = in_warp + nodes;
         __syncthreads();
-        for (int s = t; s < nsets; s += blockDim.x) {
-            int run = base[s];
-            for (int ww = 0; ww < kCtaThreads / 32; ++ww) {
-                int v = wt[ww][s];
-                wt[ww][s] = run;
-                run += v;
+        // Per set, exclusive scan over the 32 warps' counts: one warp per set,
+        // lane = warp index.
+        static_assert(kCtaThreads / 32 == 32, "one lane per warp of the block");
+        for (int s = warp; s < nsets; s += kCtaThreads / 32) {
+            const int v = wt[lane][s];
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
             }
-            base[s] = run;
+            const int b = base[s];
+            wt[lane][s] = b + x - v;
+            const int tot = __shfl_sync(0xffffffffu, x, 31);
+            __syncwarp();
+            if (lane == 0) base[s] = b + tot;
         }
         // Tree ids for materialised virtual roots, in worker order.
         long long tot_v;
         const long long vrank = cta_exclusive_scan(virt, sh, &tot_v);
         const int my_tree = tree_base + (int)vrank;
-        __syncthreads();
-        if (t == 0) tree_base += (int)tot_v;
+        int idx = ok ? wt[warp][set] + in_warp : 0;
+        bool ins = false;
         if (ok) {
-            int idx = wt[warp][set] + in_warp;
-            const R* xw = S.w_xnew + (size_t)w * kDP;
+            if (set == 0) ins = idx + 1 <= S.cap_f;
+            else ins = idx + nodes <= S.cap_s && !(virt && my_tree >= S.cap_trees);
+        }
+        // Bridge-query positions: forward insertions count in the low word,
+        // backward ones in the high word.
+        const long long flag = ins ? (set == 0 ? 1LL : (1LL << 32)) : 0LL;
+        long long tot_q;
+        const long long qrank = cta_exclusive_scan(flag, sh, &tot_q) + bq_base;
+        __syncthreads();
+        if (t == 0) {
+            tree_base += (int)tot_v;
+            bq_base += tot_q;
+        }
+        if (ok && !ins) overflow = 1;
+        if (ins) {
             if (set == 0) {
-                if (idx + 1 > S.cap_f) {
-                    overflow = 1;
-                } else {
-                    const int p = S.w_parent[w];
-                    R* x = fnode(S, idx);
-                    for (int j = 0; j < kDP; ++j) x[j] = xw[j];
-                    S.fpar[idx] = p;
-                    S.fcost[idx] = S.fcost[p] + qdist(fnode(S, p), xw, dof);
-                    S.fiter[idx] = c->iter;
-                    S.w_ins[w] = idx;
-                    int pos = atomicAdd(&S.bq_count[1], 1);
-                    S.bq_list[S.W + pos] = w;
-                }
+                st_row(fnode(S, idx), xw);
+                S.fpar[idx] = p;
+                S.fcost[idx] = pcost + qdist_rows(px, xw, dof);
+                S.fiter[idx] = iter;
+                S.w_ins[w] = idx;
+                S.bq_list[S.W + (int)(qrank & 0xffffffffLL)] = w;
             } else {
                 const int seg = set - 1;
-                if (idx + nodes > S.cap_s || (virt && my_tree >= S.cap_trees)) {
-                    overflow = 1;
-                } else {
-                    int p;
-                    if (virt) {
-                        const R T = S.w_T[w];
-                        R* x = bnode(S, seg, idx);
-                        for (int j = 0; j < kDP; ++j) x[j] = R(0);
-                        for (int j = 0; j < kMaxDof; ++j) x[j] = S.qg[j];
-                        x[kDP - 1] = (R)T;
-                        size_t o = bofs(S, seg, idx);
-                        S.bpar[o] = -1;
-                        S.bcost[o] = R(0);
-                        S.btroot[o] = (R)T;
-                        S.btree[o] = my_tree;
-                        S.biter[o] = c->iter;
-                        S.tree_group[my_tree] = seg;
-                        S.tree_T[my_tree] = (double)(R)T;  // as stored in the nodes
-                        atomicAdd(&c->group_active[seg], 1);
-                        p = idx;
-                        ++idx;
-                    } else {
-                        p = S.w_parent[w];
-                    }
-                    R* x = bnode(S, seg, idx);
-                    for (int j = 0; j < kDP; ++j) x[j] = xw[j];
-                    const size_t o = bofs(S, seg, idx), op = bofs(S, seg, p);
-                    S.bpar[o] = p;
-                    S.bcost[o] = S.bcost[op] + qdist(bnode(S, seg, p), xw, dof);
-                    S.btroot[o] = S.btroot[op];
-                    S.btree[o] = S.btree[op];
-                    S.biter[o] = c->iter;
-                    S.w_ins[w] = idx;
-                    int pos = atomicAdd(&S.bq_count[0], 1);
-                    S.bq_list[pos] = w;
+                if (virt) {
+                    // The new root (q_g, T) is the parent: its row stays in registers.
+#pragma unroll
+                    for (int j = 0; j < kDP; ++j) px[j] = R(0);
+#pragma unroll
+                    for (int j = 0; j < kMaxDof; ++j) px[j] = S.qg[j];
+                    px[kDP - 1] = (R)T;
+                    st_row(bnode(S, seg, idx), px);
+                    size_t o = bofs(S, seg, idx);
+                    S.bpar[o] = -1;
+                    S.bcost[o] = R(0);
+                    S.btroot[o] = (R)T;
+                    S.btree[o] = my_tree;
+                    S.biter[o] = iter;
+                    S.tree_group[my_tree] = seg;
+                    S.tree_T[my_tree] = (double)(R)T;  // as stored in the nodes
+                    atomicAdd(&c->group_active[seg], 1);
+                    pcost = R(0);
+                    ptroot = (R)T;
+                    ptree = my_tree;
+                    p = idx;
+                    ++idx;
                 }
+                st_row(bnode(S, seg, idx), xw);
+                const size_t o = bofs(S, seg, idx);
+                S.bpar[o] = p;
+                S.bcost[o] = pcost + qdist_rows(px, xw, dof);
+                S.btroot[o] = ptroot;
+                S.btree[o] = ptree;
+                S.biter[o] = iter;
+                S.w_ins[w] = idx;
+                S.bq_list[(int)(qrank >> 32)] = w;
             }
         } else if (w < S.W) {
             S.w_ins[w] = -1;
@@ -1049,6 +1206,8 @@ __device__ __forceinline__ void insert_body(const Geom<R>& G, const State<R>& S)
         c->n_trees = min(tree_base, S.cap_trees);
         c->st_ins += n_ins_total;
         c->st_ext += n_ext_total;
+        S.bq_count[0] = (int)(bq_base >> 32);
+        S.bq_count[1] = (int)(bq_base & 0xffffffffLL);
         if (overflow) {
             c->err |= kErrCapacity;
             c->done = 1;
@@ -1114,7 +1273,8 @@ __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S)
     if (c->done) return;
     __shared__ int seg_pre[kMaxRoots + 1];
     __shared__ int s_nq[2], s_nn[2], s_nt[2], s_nts[2], s_pre[3];
-    __shared__ R sx[kQT][DQ + 2];
+    constexpr int kRow = tile_row<R, DQ>();
+    __shared__ __align__(16) R sx[kQT][kRow];
     __shared__ int s_last;
     __shared__ int s_emitted;
     const int t = threadIdx.x;
@@ -1194,16 +1354,18 @@ __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S)
                 // Rank key of vertex i: (arrival time, rho^2); rho^2 = inf when
                 // the vertex is inactive or not admissible.
                 auto key_of = [&](int i, R& k1) -> R {
-                    const R tro = sx[i][DQ + 1];
+                    R r[kRow];
+                    lds_row<R, kRow>(sx[i], r);
+                    const R tro = r[DQ + 1];
                     k1 = s == 0 ? R(0) : tro;
                     R D2 = R(0);
 #pragma unroll
                     for (int j = 0; j < DQ; ++j) {
-                        R e = sx[i][j] - q[j];
+                        R e = r[j] - q[j];
                         D2 += e * e;
                     }
                     // s = 0: vertex earlier than the query; s = 1: later.
-                    const R dt = s == 0 ? tq - sx[i][DQ] : sx[i][DQ] - tq;
+                    const R dt = s == 0 ? tq - r[DQ] : r[DQ] - tq;
                     const bool ok = (tro < rinf<R>()) && (dt > R(0)) && (D2 <= v2 * dt * dt);
                     return ok ? D2 + v2 * dt * dt : rinf<R>();
                 };
@@ -1300,9 +1462,12 @@ __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S)
 template <typename R>
 __device__ __forceinline__ void publish_body(const Geom<R>& G, const State<R>& S) {
     Ctl* c = S.ctl;
-    if (c->done) return;
+    // The termination flag is read with the candidates (one round of loads);
+    // nothing is written before it is tested.
+    const int done = c->done;
     __shared__ R rU[kCtaThreads / 32], rC[kCtaThreads / 32];
     __shared__ int rW[kCtaThreads / 32];
+    __shared__ int rRec[kCtaThreads / 32][4];
     __shared__ int s_counts[kMaxRoots];
     __shared__ double sU, sC;
     __shared__ int s_iter, s_first, s_err, s_decreased;
@@ -1315,60 +1480,84 @@ __device__ __forceinline__ void publish_body(const Geom<R>& G, const State<R>& S
     if (t == 64) s_iter = c->iter;
     if (t == 96) s_first = c->first_iter;
     if (t == 128) s_err = c->err;
+    // Each lane keeps its best candidate with the records the incumbent update
+    // needs, so the winner needs no further load.
     R bU = rinf<R>(), bC = rinf<R>();
-    int bw = 0x7fffffff;
+    int bw = 0x7fffffff, bws = 0, bwi = -1, bbs = -1, bbi = -1;
     for (int w = t; w < S.W; w += blockDim.x) {
         // Bridge entry of worker w is entry w; all loads independent.
         const int e = S.w_bedge[w];
         const int h = S.bhit[w];
         const R U = S.b_U[w], C = S.b_C[w];
+        const int ws = S.w_set[w], wi = S.w_ins[w], bs = S.b_set[w], bi = S.b_idx[w];
         if (e < 0 || h) continue;
         if (U < bU || (U == bU && (C < bC || (C == bC && w < bw)))) {
             bU = U;
             bC = C;
             bw = w;
+            bws = ws;
+            bwi = wi;
+            bbs = bs;
+            bbi = bi;
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        R U = __shfl_xor_sync(0xffffffffu, bU, o);
-        R C = __shfl_xor_sync(0xffffffffu, bC, o);
-        int ww = __shfl_xor_sync(0xffffffffu, bw, o);
-        if (U < bU || (U == bU && (C < bC || (C == bC && ww < bw)))) {
-            bU = U;
-            bC = C;
-            bw = ww;
+    auto reduce_warp = [&]() {
+        for (int o = 16; o > 0; o >>= 1) {
+            const R U = __shfl_xor_sync(0xffffffffu, bU, o);
+            const R C = __shfl_xor_sync(0xffffffffu, bC, o);
+            const int ww = __shfl_xor_sync(0xffffffffu, bw, o);
+            const int ws = __shfl_xor_sync(0xffffffffu, bws, o), wi = __shfl_xor_sync(0xffffffffu, bwi, o);
+            const int bs = __shfl_xor_sync(0xffffffffu, bbs, o), bi = __shfl_xor_sync(0xffffffffu, bbi, o);
+            if (U < bU || (U == bU && (C < bC || (C == bC && ww < bw)))) {
+                bU = U;
+                bC = C;
+                bw = ww;
+                bws = ws;
+                bwi = wi;
+                bbs = bs;
+                bbi = bi;
+            }
         }
-    }
+    };
+    reduce_warp();
+    if (done) return;
     if (lane == 0) {
         rU[warp] = bU;
         rC[warp] = bC;
         rW[warp] = bw;
+        rRec[warp][0] = bws;
+        rRec[warp][1] = bwi;
+        rRec[warp][2] = bbs;
+        rRec[warp][3] = bbi;
     }
     __syncthreads();
+    if (warp == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        bU = lane < nw ? rU[lane] : rinf<R>();
+        bC = lane < nw ? rC[lane] : rinf<R>();
+        bw = lane < nw ? rW[lane] : 0x7fffffff;
+        bws = lane < nw ? rRec[lane][0] : 0;
+        bwi = lane < nw ? rRec[lane][1] : -1;
+        bbs = lane < nw ? rRec[lane][2] : -1;
+        bbi = lane < nw ? rRec[lane][3] : -1;
+        reduce_warp();
+    }
     if (t == 0) {
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-            if (rU[i] < bU || (rU[i] == bU && (rC[i] < bC || (rC[i] == bC && rW[i] < bw)))) {
-                bU = rU[i];
-                bC = rC[i];
-                bw = rW[i];
-            }
-        }
         s_decreased = 0;
         if (bw != 0x7fffffff) {
-            const int wset = S.w_set[bw], wins = S.w_ins[bw], bset = S.b_set[bw], bidx = S.b_idx[bw];
             s_decreased = bU < (R)sU;
             sU = (double)bU;
             sC = (double)bC;
             c->U = sU;
             c->C = sC;
-            if (wset == 0) {
-                c->inc_f = wins;
-                c->inc_s = bset;
-                c->inc_b = bidx;
+            if (bws == 0) {
+                c->inc_f = bwi;
+                c->inc_s = bbs;
+                c->inc_b = bbi;
             } else {
-                c->inc_f = bidx;
-                c->inc_s = wset - 1;
-                c->inc_b = wins;
+                c->inc_f = bbi;
+                c->inc_s = bws - 1;
+                c->inc_b = bwi;
             }
             if (s_first < 0) {
                 c->first_iter = s_iter;
@@ -1541,7 +1730,10 @@ cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cud
     mark();
     k_sample<R><<<wgrid, kSampleThreads, 0, st>>>(g, s);
     mark();
+    // Coordinates beyond the problem's DOF are zero in every node and query,
+    // so a narrower scan gives the same keys.
     if (g.dof <= 3) k_nn<R, 3><<<nn_grid, kQT, 0, st>>>(g, s);
+    else if (g.dof == 6) k_nn<R, 6><<<nn_grid, kQT, 0, st>>>(g, s);
     else k_nn<R, kMaxDof><<<nn_grid, kQT, 0, st>>>(g, s);
     mark();
     cudaError_t err = launch_validate<R>(g, ext_batch(s), false, true, vgrid, st);
@@ -1550,6 +1742,7 @@ cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cud
     k_insert<R><<<1, kCtaThreads, 0, st>>>(g, s);
     mark();
     if (g.dof <= 3) k_bridge<R, 3><<<nn_grid, kQT, 0, st>>>(g, s);
+    else if (g.dof == 6) k_bridge<R, 6><<<nn_grid, kQT, 0, st>>>(g, s);
     else k_bridge<R, kMaxDof><<<nn_grid, kQT, 0, st>>>(g, s);
     mark();
     // Bridges are long: a coarse pass over every eighth check point finds most
