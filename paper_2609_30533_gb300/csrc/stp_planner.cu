@@ -773,6 +773,32 @@ __device__ __forceinline__ void lds_row(const R* row, R (&v)[N]) {
     }
 }
 
+template <typename R, int N>
+__device__ __forceinline__ void sts_row(R* row, const R (&v)[N]) {
+    static_assert((N * sizeof(R)) % 16 == 0, "tile rows are whole 16-byte vectors");
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+        for (int k = 0; k < N / 4; ++k)
+            reinterpret_cast<float4*>(row)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) reinterpret_cast<double2*>(row)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+    }
+}
+
+// Tile row of a node: coordinates 0..DQ-1, time, flag word, zero padding.
+template <typename R, int DQ, int N>
+__device__ __forceinline__ void make_tile_row(const R* node, R flag, R (&v)[N]) {
+    R x[kDP];
+    ld_row(node, x);
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = R(0);
+#pragma unroll
+    for (int j = 0; j < DQ; ++j) v[j] = x[j];
+    v[DQ] = x[kDP - 1];
+    v[DQ + 1] = flag;
+}
+
 struct TileSets {
     int pre[kMaxRoots + 2];  // tile prefix per set
     int nq[kMaxRoots + 1];
@@ -877,13 +903,11 @@ __device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S) {
             const int cnt = min(kQT, n1 - c0);
             __syncthreads();
             if (t < cnt) {
-                const R* x = base + (size_t)(c0 + t) * kDP;
-#pragma unroll
-                for (int j = 0; j < DQ; ++j) sx[t][j] = x[j];
-                sx[t][DQ] = x[kDP - 1];
                 bool active = true;
                 if (interval && !fwd) active = troot[c0 + t] < U0r;
-                sx[t][DQ + 1] = active ? R(1) : R(0);
+                R v[kRow];
+                make_tile_row<R, DQ>(base + (size_t)(c0 + t) * kDP, active ? R(1) : R(0), v);
+                sts_row(sx[t], v);
             }
             __syncthreads();
             if (w >= 0) {
@@ -1218,7 +1242,7 @@ __device__ __forceinline__ void insert_body(const Geom<R>& G, const State<R>& S)
 // Candidate (U, C) of worker w's bridge and, if it improves the incumbent at
 // the start of the iteration, its edge entry (entry index w of the bridge batch).
 template <typename R>
-__device__ int bridge_emit(const Geom<R>& G, const State<R>& S, int w, R U0, R C0) {
+__device__ __forceinline__ int bridge_emit(const Geom<R>& G, const State<R>& S, int w, R U0, R C0) {
     const bool fwd = S.w_set[w] == 0;
     const R* f;
     const R* b;
@@ -1239,22 +1263,21 @@ __device__ int bridge_emit(const Geom<R>& G, const State<R>& S, int w, R U0, R C
         f = fnode(S, S.b_idx[w]);
         cf = S.fcost[S.b_idx[w]];
     }
-    const R D = qdist(f, b, G.dof);
+    R fr[kDP], br[kDP];
+    ld_row(f, fr);
+    ld_row(b, br);
+    const R D = qdist_rows(fr, br, G.dof);
     const R Uc = troot;
     const R Cc = (cf + D) + cb;
     const bool improves = (Uc < U0) || (Uc == U0 && Cc < C0);
     if (!improves) return 0;
     S.b_U[w] = Uc;
     S.b_C[w] = Cc;
-    R* qa = S.bqa + (size_t)w * kDP;
-    R* qb = S.bqb + (size_t)w * kDP;
-    for (int j = 0; j < kDP; ++j) {
-        qa[j] = f[j];
-        qb[j] = b[j];
-    }
-    S.bta[w] = f[kDP - 1];
-    S.btb[w] = b[kDP - 1];
-    S.bcnt[w] = check_count_r(f, f[kDP - 1], b, b[kDP - 1], G.dof, G.vmax, (R)S.res);
+    st_row(S.bqa + (size_t)w * kDP, fr);
+    st_row(S.bqb + (size_t)w * kDP, br);
+    S.bta[w] = fr[kDP - 1];
+    S.btb[w] = br[kDP - 1];
+    S.bcnt[w] = check_count_rows(fr, fr[kDP - 1], br, br[kDP - 1], G.dof, G.vmax, (R)S.res);
     S.w_bedge[w] = w;
     return 1;
 }
@@ -1344,10 +1367,9 @@ __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S)
                     tro = S.btroot[bofs(S, sg, i)];
                     active = tro < U0r;
                 }
-#pragma unroll
-                for (int j = 0; j < DQ; ++j) sx[t][j] = x[j];
-                sx[t][DQ] = x[kDP - 1];
-                sx[t][DQ + 1] = active ? tro : rinf<R>();
+                R v[kRow];
+                make_tile_row<R, DQ>(x, active ? tro : rinf<R>(), v);
+                sts_row(sx[t], v);
             }
             __syncthreads();
             if (w >= 0) {
