@@ -332,6 +332,7 @@ size_t layout_state(stp_problem* p, char* base, R** blob_out, size_t blob_bytes,
     s.bq_list = cv.take<int>((size_t)2 * W);
     s.bq_count = cv.take<int>(2);
     s.btile_cnt = cv.take<int>((size_t)2 * kMaxQTiles);
+    s.bkey = cv.take<unsigned long long>((size_t)2 * W);
     s.b_set = cv.take<int>(W);
     s.b_idx = cv.take<int>(W);
     s.b_k1 = cv.take<R>(W);

@@ -158,6 +158,7 @@ struct State {
     int* bq_list;      // [2][W]: workers whose new node bridges to set 0 (fwd) / 1 (bwd concat)
     int* bq_count;     // [2]
     int* btile_cnt;    // [2][kMaxQTiles]
+    unsigned long long* bkey;  // [W][2]: FP32 bridge rank (T_root, rho^2, index) packed in 128 bits
     int* b_set; int* b_idx; R* b_k1; R* b_k2;  // per worker best bridge candidate
     R* b_U; R* b_C;
     // edges

@@ -1085,6 +1085,7 @@ __device__ __forceinline__ void insert_body(const Geom<R>& G, const State<R>& S)
             S.w_bedge[w] = -1;
             S.bcnt[w] = 0;
             S.bhit[w] = 0;
+            reinterpret_cast<ulonglong2*>(S.bkey)[w] = make_ulonglong2(~0ull, ~0ull);
             if (e >= 0) {
                 const bool root_ok = re < 0 || h_root == 0;
                 ext = root_ok ? 1 : 0;
@@ -1282,6 +1283,25 @@ __device__ __forceinline__ int bridge_emit(const Geom<R>& G, const State<R>& S, 
     return 1;
 }
 
+// Minimum of a 128-bit key (high word first) by compare-and-swap. Keys only
+// decrease, so a failed exchange means another writer stored a smaller key:
+// the loop ends after at most one retry per competing writer (the bound only
+// guards against a corrupted key). The first exchange assumes the reset value,
+// so no non-atomic read of the key is trusted.
+__device__ __forceinline__ bool cas_min_u128(unsigned long long* base, int w, unsigned long long hi,
+                                             unsigned long long lo) {
+    unsigned __int128* a = reinterpret_cast<unsigned __int128*>(base) + w;
+    const unsigned __int128 v = ((unsigned __int128)hi << 64) | lo;
+    unsigned __int128 cur = ~(unsigned __int128)0;
+    for (int it = 0; it < (1 << 16); ++it) {
+        if (!(v < cur)) return true;
+        const unsigned __int128 prev = atomicCAS(a, cur, v);
+        if (prev == cur) return true;
+        cur = prev;
+    }
+    return false;
+}
+
 // ---------------------------------------------------------------------------
 // k_bridge: best-ranked admissible vertex of the opposite start-of-iteration set.
 // Set 0: queries = backward-inserted nodes, vertices = forward arena [0, snap_f).
@@ -1415,10 +1435,22 @@ __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S)
                 }
             }
         }
-        if (w >= 0) {
-            S.part_k1[(size_t)w * kMaxTiles + ntile] = b1;
-            S.part_k2[(size_t)w * kMaxTiles + ntile] = b2;
-            S.part_idx[(size_t)w * kMaxTiles + ntile] = bidx;
+        if constexpr (sizeof(R) == 4) {
+            // FP32: (k1, k2, index) fits 128 bits; non-negative floats order
+            // like their bit patterns (+ 0 turns a -0 into +0).
+            if (w >= 0 && b2 < rinf<R>()) {
+                const unsigned long long hi = ((unsigned long long)__float_as_uint((float)b1 + 0.0f) << 32) |
+                                              (unsigned long long)__float_as_uint((float)b2 + 0.0f);
+                if (!cas_min_u128(S.bkey, w, hi, (unsigned long long)(unsigned)bidx)) atomicOr(&c->err, kErrInternal);
+            }
+        } else {
+            // FP64 keys do not fit: per-tile partials, reduced in tile order
+            // by the last CTA of the query tile.
+            if (w >= 0) {
+                S.part_k1[(size_t)w * kMaxTiles + ntile] = b1;
+                S.part_k2[(size_t)w * kMaxTiles + ntile] = b2;
+                S.part_idx[(size_t)w * kMaxTiles + ntile] = bidx;
+            }
         }
         __syncthreads();
         if (t == 0) {
@@ -1433,26 +1465,35 @@ __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S)
             if (w >= 0) {
                 R k1 = rinf<R>(), k2 = rinf<R>();
                 int bi = 0x7fffffff;
-                const R* p1 = S.part_k1 + (size_t)w * kMaxTiles;
-                const R* p2 = S.part_k2 + (size_t)w * kMaxTiles;
-                const int* pi = S.part_idx + (size_t)w * kMaxTiles;
-                // Groups of 8 independent loads per round trip, in tile order.
-                for (int j0 = 0; j0 < nt; j0 += 8) {
-                    R a1[8], a2[8];
-                    int ai[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int j = j0 + u < nt ? j0 + u : nt - 1;
-                        a1[u] = __ldcg(p1 + j);
-                        a2[u] = __ldcg(p2 + j);
-                        ai[u] = __ldcg(pi + j);
+                if constexpr (sizeof(R) == 4) {
+                    const ulonglong2 kv = __ldcg(reinterpret_cast<const ulonglong2*>(S.bkey) + w);
+                    if (kv.x != ~0ull || kv.y != ~0ull) {
+                        k1 = __uint_as_float((unsigned)(kv.y >> 32));
+                        k2 = __uint_as_float((unsigned)(kv.y & 0xffffffffull));
+                        bi = (int)(unsigned)kv.x;
                     }
+                } else {
+                    const R* p1 = S.part_k1 + (size_t)w * kMaxTiles;
+                    const R* p2 = S.part_k2 + (size_t)w * kMaxTiles;
+                    const int* pi = S.part_idx + (size_t)w * kMaxTiles;
+                    // Groups of 8 independent loads per round trip, in tile order.
+                    for (int j0 = 0; j0 < nt; j0 += 8) {
+                        R a1[8], a2[8];
+                        int ai[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        if (j0 + u < nt && key_less(a1[u], a2[u], ai[u], k1, k2, bi)) {
-                            k1 = a1[u];
-                            k2 = a2[u];
-                            bi = ai[u];
+                        for (int u = 0; u < 8; ++u) {
+                            const int j = j0 + u < nt ? j0 + u : nt - 1;
+                            a1[u] = __ldcg(p1 + j);
+                            a2[u] = __ldcg(p2 + j);
+                            ai[u] = __ldcg(pi + j);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            if (j0 + u < nt && key_less(a1[u], a2[u], ai[u], k1, k2, bi)) {
+                                k1 = a1[u];
+                                k2 = a2[u];
+                                bi = ai[u];
+                            }
                         }
                     }
                 }
