@@ -631,12 +631,17 @@ __device__ __forceinline__ bool steer_and_emit(const Geom<R>& G, const State<R>&
 template <typename R>
 __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S) {
     const Ctl* c = S.ctl;
-    if (c->done) return;
+    // Control words and the slot flags in one round of loads; nothing is
+    // written before the termination flag is tested.
+    const int done = c->done;
+    const int k = c->iter;
     // Active-slot list (recycling) staged once per block.
     __shared__ int s_act[kMaxRoots];
     __shared__ int s_nact;
-    if (S.variant != 0) {
+    if (S.variant != 0)
         for (int i = threadIdx.x; i < S.N; i += blockDim.x) s_act[i] = c->slot_active[i];
+    if (done) return;
+    if (S.variant != 0) {
         __syncthreads();
         if (threadIdx.x == 0) {
             int n = 0;
@@ -648,7 +653,6 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
     }
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= S.W) return;
-    const int k = c->iter;
     const int dof = G.dof;
     const bool fwd = ((w + k) & 1) == 0;
     int status = kSkip, set = 0;
@@ -799,6 +803,26 @@ __device__ __forceinline__ void make_tile_row(const R* node, R flag, R (&v)[N]) 
     v[DQ + 1] = flag;
 }
 
+// Exclusive prefix of v[0..n) in place by the first warp of the block (lanes
+// 0..31 call it together); returns the total to every calling lane.
+__device__ __forceinline__ int warp_prefix_inplace(int* v, int n) {
+    const int lane = threadIdx.x & 31;
+    int carry = 0;
+    for (int s0 = 0; s0 < n; s0 += 32) {
+        const int s = s0 + lane;
+        const int a = s < n ? v[s] : 0;
+        int x = a;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (s < n) v[s] = carry + x - a;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    return carry;
+}
+
 struct TileSets {
     int pre[kMaxRoots + 2];  // tile prefix per set
     int nq[kMaxRoots + 1];
@@ -841,15 +865,19 @@ __device__ __forceinline__ unsigned long long pack_key(float k, int idx) {
 template <typename R, int DQ>
 __device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S) {
     const Ctl* c = S.ctl;
-    if (c->done) return;
+    // Control words and the per-set counts in one round of loads; nothing is
+    // written to global memory before the termination flag is tested.
+    const int done = c->done;
+    // U holds a value stored in the trees (or +inf), so it converts exactly.
+    const R U0r = (R)c->U;
     __shared__ TileSets ts;
     constexpr int kRow = tile_row<R, DQ>();
     __shared__ __align__(16) R sx[kQT][kRow];
     __shared__ int s_last;
     const int t = threadIdx.x;
     const int nsets = S.N + 1;
-    // One thread per set loads its counts (a single round trip), then thread 0
-    // forms the tile prefix in shared memory.
+    // One thread per set loads its counts, then the first warp forms the tile
+    // prefix in shared memory.
     for (int s = t; s < nsets; s += blockDim.x) {
         const int nq = c->set_count[s];
         const int n = s == 0 ? c->n_f : c->n_s[s - 1];
@@ -862,20 +890,14 @@ __device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S) {
         ts.pre[s] = tiles;
     }
     __syncthreads();
-    if (t == 0) {
-        int acc = 0;
-        for (int s = 0; s < nsets; ++s) {
-            const int tiles = ts.pre[s];
-            ts.pre[s] = acc;
-            acc += tiles;
-        }
-        ts.pre[nsets] = acc;
+    if (done) return;
+    if (t < 32) {
+        const int acc = warp_prefix_inplace(ts.pre, nsets);
+        if (t == 0) ts.pre[nsets] = acc;
     }
     __syncthreads();
     const int total = ts.pre[nsets];
     const R v2 = G.vmax * G.vmax;
-    // U holds a value stored in the trees (or +inf), so it converts exactly.
-    const R U0r = (R)c->U;
     const bool interval = S.variant == 0;
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
         int s = 0;
@@ -1313,7 +1335,10 @@ __device__ __forceinline__ bool cas_min_u128(unsigned long long* base, int w, un
 template <typename R, int DQ>
 __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S) {
     Ctl* c = S.ctl;
-    if (c->done) return;
+    // Control words, segment sizes and query counts in one round of loads;
+    // nothing is written to global memory before the termination flag is tested.
+    const int done = c->done;
+    const R U0r = (R)c->U, C0r = (R)c->C;
     __shared__ int seg_pre[kMaxRoots + 1];
     __shared__ int s_nq[2], s_nn[2], s_nt[2], s_nts[2], s_pre[3];
     constexpr int kRow = tile_row<R, DQ>();
@@ -1322,19 +1347,24 @@ __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S)
     __shared__ int s_emitted;
     const int t = threadIdx.x;
     for (int i = t; i < S.N; i += blockDim.x) seg_pre[i] = c->snap_s[i];
-    __syncthreads();
+    int nq0 = 0, nq1 = 0, nf = 0;
     if (t == 0) {
-        int acc = 0;
-        for (int i = 0; i < S.N; ++i) {
-            const int v = seg_pre[i];
-            seg_pre[i] = acc;
-            acc += v;
-        }
-        seg_pre[S.N] = acc;
+        nq0 = S.bq_count[0];
+        nq1 = S.bq_count[1];
+        nf = c->snap_f;
+    }
+    __syncthreads();
+    if (done) return;
+    if (t < 32) {
+        const int acc = warp_prefix_inplace(seg_pre, S.N);
+        if (t == 0) seg_pre[S.N] = acc;
+    }
+    if (t == 0) {
+        const int acc = seg_pre[S.N];
         int tacc = 0;
         for (int s = 0; s < 2; ++s) {
-            int nq = S.bq_count[s];
-            int n = s == 0 ? c->snap_f : acc;
+            int nq = s == 0 ? nq0 : nq1;
+            int n = s == 0 ? nf : acc;
             int nt, nts, tiles;
             tiles_for(nq, n, nt, nts, tiles);
             s_nq[s] = nq;
@@ -1350,7 +1380,6 @@ __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S)
     __syncthreads();
     const int total = s_pre[2];
     const R v2 = G.vmax * G.vmax;
-    const R U0r = (R)c->U, C0r = (R)c->C;
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
         const int s = tile < s_pre[1] ? 0 : 1;
         const int local = tile - s_pre[s];
