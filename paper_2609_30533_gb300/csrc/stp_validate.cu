@@ -522,11 +522,16 @@ __device__ __forceinline__ void validate_body(const Geom<R>& G, const EdgeBatch<
 
     if (!E.off) {
         // Small batches (offsets scanned into shared memory): the flat range of
-        // check points is spread over every warp of the grid; each lane finds
-        // its edge by binary search in shared memory.
+        // check points is cut into 32-point groups dealt round-robin over the
+        // CTAs first (group k to CTA k mod grid), so that a batch smaller than
+        // the resident grid still spreads over every SM; each lane finds its
+        // edge by binary search in shared memory.
         const long long total = soff[n];
-        const long long stride = (long long)gridDim.x * wpb * 32;
-        for (long long g = ((long long)blockIdx.x * wpb + warp) * 32 + lane; g < total; g += stride) {
+        const long long ngroups = (total + 31) >> 5;
+        const long long gstride = (long long)gridDim.x * wpb;
+        for (long long k = (long long)warp * gridDim.x + blockIdx.x; k < ngroups; k += gstride) {
+            const long long g = k * 32 + lane;
+            if (g >= total) continue;
             int lo = 0, hi = n - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
