@@ -650,7 +650,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(args.steps):
-        Q = stp.problem_from(prob, prm, precision=0, max_iters=args.iters, iters_per_graph=args.iters)
+        Q = stp.problem_from(prob, prm, precision=0, max_iters=args.iters)   # library default graph size
         out = Q.plan(cap=4096)
         e2e_edges += out.stats["edges_validated"] + out.stats["bridges_validated"]
         d2h = out.path.size * 8 + 8 * 16

@@ -103,7 +103,7 @@ typedef struct {
  *                  workers (the rest sample as with 0); stp_plan and
  *                  stp_batch_plan return STP_ERR_INVALID until one is set.
  *   capacity       nodes per tree arena; 0 = max_iters * ceil(W/2) + 2 (worst case).
- *   iters_per_graph  iterations captured per CUDA graph launch; 0 = 16.
+ *   iters_per_graph  iterations captured per CUDA graph launch; 0 = 8.
  *   t_offset       absolute time of the query's local time 0 (>= 0): obstacle
  *                  trajectories are shifted by it, as when a goal sequence is
  *                  planned query by query (Sec. "Problem Formulation": each
@@ -265,8 +265,14 @@ stp_status stp_batch_plan(stp_batch *b, stp_stats *stats, double *batch_ms);
 stp_status stp_batch_path(stp_batch *b, int i, double *path, int cap, int *n_path);
 void stp_batch_free(stp_batch *b);
 
-/* Release all device and host memory of a problem. NULL is allowed. */
+/* Release a problem. NULL is allowed. Waits for the problem's stream(s); its
+ * device blocks and stream then go to a per-process cache (up to 4 GiB of idle
+ * blocks) that later stp_create_problem calls reuse, so short-lived problems
+ * cost no cudaMalloc/cudaFree. */
 void stp_free(stp_problem *p);
+/* Return every cached device block and stream to the driver (thread-safe; call
+ * when no problem created before it is still in use by another thread). */
+void stp_release_cached(void);
 
 /* Use this CUDA stream (a cudaStream_t passed as void*) for every later call
  * on p; NULL selects the library's own stream. */

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -25,6 +26,94 @@ namespace {
 const double kInfD = std::numeric_limits<double>::infinity();
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Device resources kept for reuse across problems: memory blocks (by device
+// and size) and non-blocking streams (by device). Creating and freeing many
+// short-lived problems then costs no cudaMalloc/cudaFree (and none of the
+// device synchronisation of cudaFree). Blocks are handed out only when idle:
+// stp_free synchronises the problem's streams first. stp_release_cached()
+// returns everything to the driver.
+struct DevCache {
+    std::mutex mu;
+    struct Block {
+        int dev;
+        void* ptr;
+    };
+    std::multimap<size_t, Block> blocks;
+    size_t cached = 0;
+    std::vector<std::pair<int, cudaStream_t>> streams;
+};
+constexpr size_t kCacheLimit = size_t(4) << 30;  // bytes of idle blocks kept
+
+DevCache& dev_cache() {
+    // Never destroyed: no CUDA call may run during static destruction.
+    static DevCache* c = new DevCache();
+    return *c;
+}
+
+int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+// A block of at least `bytes` (at most twice that plus 1 MiB, so small
+// requests do not pin large blocks); *got receives its size.
+cudaError_t cache_alloc(void** ptr, size_t bytes, size_t* got) {
+    bytes = align_up(std::max<size_t>(bytes, 256), 256);
+    const int dev = current_device();
+    {
+        DevCache& c = dev_cache();
+        std::lock_guard<std::mutex> g(c.mu);
+        for (auto it = c.blocks.lower_bound(bytes); it != c.blocks.end() && it->first <= 2 * bytes + (1 << 20);
+             ++it) {
+            if (it->second.dev != dev) continue;
+            *ptr = it->second.ptr;
+            *got = it->first;
+            c.cached -= it->first;
+            c.blocks.erase(it);
+            return cudaSuccess;
+        }
+    }
+    *got = bytes;
+    return cudaMalloc(ptr, bytes);
+}
+
+void cache_release(void* ptr, size_t bytes) {
+    if (!ptr) return;
+    {
+        DevCache& c = dev_cache();
+        std::lock_guard<std::mutex> g(c.mu);
+        if (c.cached + bytes <= kCacheLimit) {
+            c.blocks.emplace(bytes, DevCache::Block{current_device(), ptr});
+            c.cached += bytes;
+            return;
+        }
+    }
+    cudaFree(ptr);
+}
+
+cudaError_t cache_stream(cudaStream_t* st) {
+    const int dev = current_device();
+    {
+        DevCache& c = dev_cache();
+        std::lock_guard<std::mutex> g(c.mu);
+        for (size_t i = 0; i < c.streams.size(); ++i) {
+            if (c.streams[i].first != dev) continue;
+            *st = c.streams[i].second;
+            c.streams.erase(c.streams.begin() + (long)i);
+            return cudaSuccess;
+        }
+    }
+    return cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+}
+
+void cache_stream_release(cudaStream_t st) {
+    if (!st) return;
+    DevCache& c = dev_cache();
+    std::lock_guard<std::mutex> g(c.mu);
+    c.streams.emplace_back(current_device(), st);
+}
 
 // Carves aligned sub-buffers out of one device allocation.
 struct Carver {
@@ -54,6 +143,7 @@ struct stp_problem {
     int cap_f = 0, cap_s = 0, cap_trees = 0, max_pieces = 0, path_cap = 0;
     char* d_arena = nullptr;
     size_t arena_bytes = 0;
+    size_t arena_block = 0;   // size of the (possibly reused) block holding the arena
     Geom<float> gf{};
     Geom<double> gd{};
     State<float> sf{};
@@ -69,6 +159,7 @@ struct stp_problem {
     char* d_scratch = nullptr;
     size_t scratch_bytes = 0;
     unsigned long long* d_counters = nullptr;  // [2]: points, pairs of stp_check_edges
+    size_t counters_block = 0;
     std::string last_error;
     bool planned = false;
     bool has_proposal = false;  // learned branch table set by stp_set_proposal
@@ -414,8 +505,10 @@ stp_status create_impl(stp_problem* p) {
     int *cnt, *hit;
     long long* off;
     const size_t bytes = layout_state<R>(p, nullptr, &blob, blob_bytes, &gfree, &ctl, &qdev, &tdev, &cnt, &off, &hit);
-    cudaError_t e = cudaMalloc(&p->d_arena, bytes);
+    void* arena = nullptr;
+    cudaError_t e = cache_alloc(&arena, bytes, &p->arena_block);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudaMalloc(arena)");
+    p->d_arena = static_cast<char*>(arena);
     p->arena_bytes = bytes;
     layout_state<R>(p, p->d_arena, &blob, blob_bytes, &gfree, &ctl, &qdev, &tdev, &cnt, &off, &hit);
     p->d_ctl = ctl;
@@ -493,7 +586,11 @@ stp_status create_impl(stp_problem* p) {
 
 template <typename R>
 stp_status capture_graph(stp_problem* p) {
-    const int G = p->prm.iters_per_graph > 0 ? p->prm.iters_per_graph : 16;
+    // Default 8: capture and instantiation grow with the graph while replays of
+    // small graphs cost the device almost nothing (UR5e, 32 iterations: one
+    // create-plan-free 2.80 ms with 8 against 3.25 ms with 32; plan 2.27 ms
+    // against 2.26 ms).
+    const int G = p->prm.iters_per_graph > 0 ? p->prm.iters_per_graph : 8;
     const bool prof = p->profiling != 0;
     const bool have_prof = !p->prof_ev.empty();
     if (p->graph && p->graph_stream == p->stream && p->graph_iters == G && prof == have_prof) return STP_OK;
@@ -529,12 +626,13 @@ stp_status plan_impl(stp_problem* p, Ctl* hc) {
     cudaStream_t st = p->stream;
     stp_status s = capture_graph<R>(p);
     if (s != STP_OK) return s;
+    const int G = p->graph_iters;
     STP_CUDA(p, cudaMemsetAsync(state_of<R>(p).tile_cnt, 0,
                                 sizeof(int) * (size_t)(p->prm.n_roots + 1) * kMaxQTiles, st));
     STP_CUDA(p, cudaMemsetAsync(state_of<R>(p).btile_cnt, 0, sizeof(int) * 2 * kMaxQTiles, st));
     STP_CUDA(p, cudaEventRecord(p->ev0, st));
     STP_CUDA(p, launch_plan_reset<R>(geom_of<R>(p), state_of<R>(p), p->prm.max_iters, st));
-    const int n_launch = (p->prm.max_iters + p->graph_iters - 1) / p->graph_iters;
+    const int n_launch = (p->prm.max_iters + G - 1) / G;
     auto t0 = std::chrono::steady_clock::now();
     for (int k = 0; k < kIterKernels; ++k) {
         p->prof_ms[k] = 0.0;
@@ -616,12 +714,16 @@ stp_status check_edges_impl(stp_problem* p, int n, const void* qa, const void* t
     };
     lay(nullptr);
     if (cv.off > p->scratch_bytes) {
-        if (p->d_scratch) cudaFree(p->d_scratch);
+        // The previous scratch is idle: every check ends with a stream synchronisation.
+        cache_release(p->d_scratch, p->scratch_bytes);
         p->d_scratch = nullptr;
         p->scratch_bytes = 0;
-        cudaError_t e = cudaMalloc(&p->d_scratch, cv.off);
+        void* sc = nullptr;
+        size_t got = 0;
+        cudaError_t e = cache_alloc(&sc, cv.off, &got);
         if (e != cudaSuccess) return cuda_fail(p, e, "cudaMalloc(edge scratch)");
-        p->scratch_bytes = cv.off;
+        p->d_scratch = static_cast<char*>(sc);
+        p->scratch_bytes = got;
     }
     auto L = lay(p->d_scratch);
     const R* dqa = dev ? (const R*)qa : L.qa;
@@ -796,7 +898,7 @@ stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, 
         delete p;
         return STP_ERR_CUDA;
     }
-    e = cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking);
+    e = cache_stream(&p->own_stream);
     if (e != cudaSuccess) {
         cuda_fail(p, e, "cudaStreamCreateWithFlags");
         delete p;
@@ -807,7 +909,9 @@ stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, 
     cudaEventCreate(&p->ev1);
     cudaEventCreate(&p->ev2);
     cudaEventCreate(&p->ev3);
-    e = cudaMalloc(&p->d_counters, 2 * sizeof(unsigned long long));
+    void* counters = nullptr;
+    e = cache_alloc(&counters, 2 * sizeof(unsigned long long), &p->counters_block);
+    p->d_counters = static_cast<unsigned long long*>(counters);
     if (e != cudaSuccess) {
         cuda_fail(p, e, "cudaMalloc(counters)");
         stp_free(p);
@@ -914,18 +1018,39 @@ stp_status stp_check_edges(stp_problem* p, int n_edges, const void* qa, const vo
                : check_edges_impl<double>(p, n_edges, qa, ta, qb, tb, flags, verdict, min_clearance, n_checks);
 }
 
+void stp_release_cached(void) {
+    DevCache& c = dev_cache();
+    std::lock_guard<std::mutex> g(c.mu);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    for (auto& kv : c.blocks) {
+        cudaSetDevice(kv.second.dev);
+        cudaFree(kv.second.ptr);
+    }
+    c.blocks.clear();
+    c.cached = 0;
+    for (auto& ds : c.streams) {
+        cudaSetDevice(ds.first);
+        cudaStreamDestroy(ds.second);
+    }
+    c.streams.clear();
+    cudaSetDevice(prev);
+}
+
 void stp_free(stp_problem* p) {
     if (!p) return;
+    // Every buffer goes back to the cache idle: wait for the problem's streams.
     if (p->stream) cudaStreamSynchronize(p->stream);
+    if (p->own_stream && p->own_stream != p->stream) cudaStreamSynchronize(p->own_stream);
     if (p->graph) cudaGraphExecDestroy(p->graph);
-    if (p->d_arena) cudaFree(p->d_arena);
-    if (p->d_scratch) cudaFree(p->d_scratch);
+    cache_release(p->d_arena, p->arena_block);
+    cache_release(p->d_scratch, p->scratch_bytes);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
     if (p->ev2) cudaEventDestroy(p->ev2);
     if (p->ev3) cudaEventDestroy(p->ev3);
-    if (p->own_stream) cudaStreamDestroy(p->own_stream);
-    if (p->d_counters) cudaFree(p->d_counters);
+    cache_stream_release(p->own_stream);
+    cache_release(p->d_counters, p->counters_block);
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     delete p;
 }

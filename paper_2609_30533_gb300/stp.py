@@ -87,6 +87,8 @@ def lib():
     L.stp_check_edges.restype = C.c_int
     L.stp_free.argtypes = [C.c_void_p]
     L.stp_free.restype = None
+    L.stp_release_cached.argtypes = []
+    L.stp_release_cached.restype = None
     L.stp_set_stream.argtypes = [C.c_void_p, C.c_void_p]
     L.stp_set_stream.restype = C.c_int
     L.stp_status_string.argtypes = [C.c_int]
@@ -162,7 +164,12 @@ EXPORTED = ["stp_create_problem", "stp_plan", "stp_check_edges", "stp_free", "st
             "stp_mlp_create", "stp_mlp_free", "stp_mlp_set_stream", "stp_mlp_set_params", "stp_mlp_get_params",
             "stp_mlp_forward", "stp_mlp_gradients", "stp_mlp_train_step", "stp_mlp_set_profiling",
             "stp_mlp_profile", "stp_mlp_last_error", "stp_problem_features", "stp_set_proposal",
-            "stp_problem_targets", "stp_selftest_bounded_wait"]
+            "stp_problem_targets", "stp_selftest_bounded_wait", "stp_release_cached"]
+
+
+def release_cached() -> None:
+    """stp_release_cached: return the library's cached device blocks and streams."""
+    lib().stp_release_cached()
 
 
 def status_string(s: int) -> str:

@@ -69,7 +69,17 @@ def test_fp64_trees_match_oracle_node_for_node(case):
     prob, prm = CASES[case]()
     ref = O.plan(prob, prm)
     P = stp.problem_from(prob, prm, precision=1)
-    out = P.plan()
+    # A fresh plan and a replay of the captured graph both equal the oracle.
+    for _ in range(2):
+        out = P.plan()
+        _check_fp64_plan(P, out, ref, prm, stp)
+    st = out.stats
+    print(case, "U=%.6f iters=%d nodes=%d ext=%d bridge=%d" % (ref.U, st["iterations"], st["nodes"],
+                                                               st["edges_validated"], st["bridges_validated"]))
+    P.close()
+
+
+def _check_fp64_plan(P, out, ref, prm, stp):
     assert out.status == (stp.STP_OK if ref.status == 0 else stp.STP_NO_SOLUTION)
     st = out.stats
     assert st["iterations"] == ref.iters
@@ -91,9 +101,6 @@ def test_fp64_trees_match_oracle_node_for_node(case):
             assert np.array_equal(sl[k], ref.slots[k]), k
         fin = ref.slots["has_root"] == 1
         assert np.allclose(sl["T"][fin], ref.slots["T"][fin])
-    print(case, "U=%.6f iters=%d nodes=%d ext=%d bridge=%d" % (out.U, st["iterations"], st["nodes"],
-                                                               st["edges_validated"], st["bridges_validated"]))
-    P.close()
 
 
 def _first_flag(ref, tol=1e-5, band=1e-5):
@@ -193,16 +200,38 @@ def test_capacity_overflow_is_reported():
     P.close()
 
 
+def _snapshot(P, prm, out):
+    trees = [P.tree(a) for a in [-1] + list(range(prm.n_roots))]
+    keys = ("iterations", "first_solution_iter", "nodes", "edges_validated", "bridges_validated", "check_points")
+    return out.U, out.C, [dict((k, v.copy()) for k, v in t.items()) for t in trees], \
+        tuple(out.stats[k] for k in keys), out.path.copy()
+
+
+def _same(a, b):
+    assert a[0] == b[0] and a[1] == b[1] and a[3] == b[3] and np.array_equal(a[4], b[4])
+    for ta, tb in zip(a[2], b[2]):
+        for k in ta:
+            assert np.array_equal(ta[k], tb[k]), k
+
+
 def test_replanning_is_deterministic():
+    """FP32: the first plan, a replay of the captured graph, and a new problem
+    created after the first was freed (reusing its cached device block and
+    stream) give bit-identical trees, statistics and paths."""
     from paper_2609_30533_gb300 import stp
     prob, prm = CASES["ur5e-small-recycling"]()
     P = stp.problem_from(prob, prm, precision=0)
-    a = P.plan()
-    fa = P.tree(-1)["x"].copy()
-    b = P.plan()
-    fb = P.tree(-1)["x"]
-    assert a.U == b.U and np.array_equal(fa, fb)
+    a = _snapshot(P, prm, P.plan())
+    b = _snapshot(P, prm, P.plan())
+    _same(a, b)
     P.close()
+    Q = stp.problem_from(prob, prm, precision=0)
+    _same(a, _snapshot(Q, prm, Q.plan()))
+    Q.close()
+    stp.release_cached()
+    R = stp.problem_from(prob, prm, precision=0)
+    _same(a, _snapshot(R, prm, R.plan()))
+    R.close()
 
 
 @pytest.mark.parametrize("which", ["disc", "arm"])
