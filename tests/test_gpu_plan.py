@@ -168,6 +168,52 @@ def test_fp32_paths_satisfy_invariants(case):
     P.close()
 
 
+def test_fp32_full_size_plan_sampled():
+    """The timed UR5e configuration (W 1024, 32 iterations, root recycling with
+    8 trees, FP32), checked through properties that hold at any size on sampled
+    nodes: every sampled tree edge is collision-free by the FP64 oracle at the
+    problem's resolution (clearance band 1e-5 m), runs forward in time within
+    the velocity bound, and its child stores the parent's cost plus the edge's
+    configuration distance, the parent's root time and tree id."""
+    from paper_2609_30533_gb300 import stp
+    prob, prm = WL.ur5e(0)
+    prm = dataclasses.replace(prm, max_iters=32)
+    assert prm.workers == 1024 and prm.variant == 1 and prm.n_roots == 8
+    P = stp.problem_from(prob, prm, precision=0)
+    out = P.plan()
+    assert out.status in (stp.STP_OK, stp.STP_NO_SOLUTION)
+    st = out.stats
+    assert st["iterations"] == 32 or out.status == stp.STP_OK
+    d = prob.dof
+    rng = np.random.default_rng(7)
+    qa, ta, qb, tb = [], [], [], []
+    n_total = 0
+    for arena in [-1] + list(range(prm.n_roots)):
+        t = P.tree(arena)
+        n_total += len(t["x"])
+        kids = np.flatnonzero(t["parent"] >= 0)
+        if len(kids) == 0:
+            continue
+        pick = rng.choice(kids, size=min(len(kids), 300 if arena < 0 else 60), replace=False)
+        for i in pick:
+            p = t["parent"][i]
+            dist = np.linalg.norm(t["x"][i, :d] - t["x"][p, :d])
+            assert abs(t["cost"][i] - (t["cost"][p] + dist)) <= 1e-4 * (1 + t["cost"][i])
+            assert t["troot"][i] == t["troot"][p] and t["tree"][i] == t["tree"][p]
+            a, b = (p, i) if arena < 0 else (i, p)      # forward: parent earlier; backward: parent later
+            qa.append(t["x"][a, :d]); ta.append(t["x"][a, d]); qb.append(t["x"][b, :d]); tb.append(t["x"][b, d])
+    assert n_total > prm.workers
+    qa, qb, ta, tb = map(np.asarray, (qa, qb, ta, tb))
+    assert len(qa) >= 300
+    dt = tb - ta
+    assert np.all(dt > 0)
+    assert np.all(np.linalg.norm(qb - qa, axis=1) <= prob.vmax * dt * (1 + 1e-4) + 1e-5)
+    v, clr, _, _ = O.check_edges(prob, qa, ta, qb, tb, prm.res)
+    bad = ~v.astype(bool) & (np.abs(clr) > 1e-5)
+    assert not bad.any(), int(bad.sum())
+    P.close()
+
+
 def test_degenerate_queries():
     from paper_2609_30533_gb300 import stp
     prob, prm = WL.disc2d(0)
