@@ -30,7 +30,7 @@ constexpr int kMaxWorkers = 8192;
 constexpr int kQT = 128;        // queries per NN tile (= threads per CTA)
 constexpr int kMaxTiles = 64;   // node tiles per query (partials per query)
 constexpr int kMaxQTiles = kMaxWorkers / kQT;
-constexpr int kNodeTileMin = 64;
+constexpr int kNodeTileMin = 32;
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // bounded mbarrier waits: 1 s
 constexpr unsigned kWaitLimit = 1u << 28;                   // and an iteration backstop
 constexpr int kPropY = 160;                 // network output floats
