@@ -417,9 +417,11 @@ size_t layout_state(stp_problem* p, char* base, R** blob_out, size_t blob_bytes,
     s.w_nnkey = cv.take<unsigned long long>(W);
     s.qlist = cv.take<int>((size_t)(N + 1) * W);
     s.tile_cnt = cv.take<int>((size_t)(N + 1) * kMaxQTiles);
-    s.part_k1 = cv.take<R>((size_t)W * kMaxTiles);
-    s.part_k2 = cv.take<R>((size_t)W * kMaxTiles);
-    s.part_idx = cv.take<int>((size_t)W * kMaxTiles);
+    // Per-tile partials serve the FP64 scans only (FP32 merges keys atomically).
+    const size_t npart = sizeof(R) == 8 ? (size_t)W * kMaxTiles : 0;
+    s.part_k1 = cv.take<R>(npart);
+    s.part_k2 = cv.take<R>(npart);
+    s.part_idx = cv.take<int>(npart);
     s.bq_list = cv.take<int>((size_t)2 * W);
     s.bq_count = cv.take<int>(2);
     s.btile_cnt = cv.take<int>((size_t)2 * kMaxQTiles);

@@ -28,7 +28,7 @@ constexpr int kMaxObs = 128;
 constexpr int kMaxWay = 8;
 constexpr int kMaxWorkers = 8192;
 constexpr int kQT = 128;        // queries per NN tile (= threads per CTA)
-constexpr int kMaxTiles = 64;   // node tiles per query (partials per query)
+constexpr int kMaxTiles = 128;  // node tiles per query (FP64: partials per query)
 constexpr int kMaxQTiles = kMaxWorkers / kQT;
 constexpr int kNodeTileMin = 32;
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // bounded mbarrier waits: 1 s
