@@ -57,16 +57,6 @@ __device__ __forceinline__ size_t bofs(const State<R>& S, int seg, int i) {
     return (size_t)seg * S.cap_s + i;
 }
 
-template <typename R>
-__device__ __forceinline__ R qdist(const R* a, const R* b, int dof) {
-    R s = R(0);
-    for (int j = 0; j < dof; ++j) {
-        R e = b[j] - a[j];
-        s += e * e;
-    }
-    return rsqrt_r(s);
-}
-
 // Node rows (kDP values, 16-byte aligned) moved as 16-byte vectors.
 template <typename R>
 __device__ __forceinline__ void ld_row(const R* src, R (&v)[kDP]) {
@@ -93,7 +83,8 @@ __device__ __forceinline__ void st_row(R* dst, const R (&v)[kDP]) {
         for (int k = 0; k < kDP / 2; ++k) reinterpret_cast<double2*>(dst)[k] = make_double2(v[2 * k], v[2 * k + 1]);
     }
 }
-// qdist of two rows held in registers (same operations in the same order).
+// Configuration distance |b - a| over the first dof coordinates of two rows
+// held in registers (unrolled with a predicate, so the rows stay in registers).
 template <typename R, int N>
 __device__ __forceinline__ R qdist_rows(const R (&a)[N], const R (&b)[N], int dof) {
     static_assert(N >= kMaxDof, "rows hold every configuration coordinate");
@@ -106,28 +97,6 @@ __device__ __forceinline__ R qdist_rows(const R (&a)[N], const R (&b)[N], int do
         }
     }
     return rsqrt_r(s);
-}
-
-__device__ __forceinline__ double qdist_d(const double* a, const double* b, int dof) {
-    double s = 0.0;
-    for (int j = 0; j < dof; ++j) {
-        double e = b[j] - a[j];
-        s = __dadd_rn(s, __dmul_rn(e, e));
-    }
-    return sqrt(s);
-}
-
-// Check-point count in double (same reading as the collision batch helper).
-template <typename R>
-__device__ __forceinline__ int check_count(const R* qa, R ta, const R* qb, R tb, int dof, double vmax, double res) {
-    double s2 = 0.0;
-    for (int j = 0; j < dof; ++j) {
-        double e = (double)qb[j] - (double)qa[j];
-        s2 = __dadd_rn(s2, __dmul_rn(e, e));
-    }
-    double L = fmax(sqrt(s2), __dmul_rn(vmax, fabs((double)tb - (double)ta)));
-    double c = ceil(L / res - 1e-3);
-    return c < 1.0 ? 1 : (int)c;
 }
 
 // Goal-grid time k dt as stored in the trees (rounded to the working precision,
@@ -520,22 +489,9 @@ __device__ __forceinline__ void reset_body(const State<R>& S, int max_iters) {
 // point check of its sampled goal root, interval root only) and 2w+1 (the
 // extension edge); a count of 0 leaves an entry out of the batch.
 // ---------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ int check_count_r(const R* qa, R ta, const R* qb, R tb, int dof, R vmax, R res) {
-    R s2 = R(0);
-    for (int j = 0; j < dof; ++j) {
-        R e = qb[j] - qa[j];
-        s2 += e * e;
-    }
-    R dt = tb - ta;
-    R L = rsqrt_r(s2);
-    R Lt = vmax * (dt < R(0) ? -dt : dt);
-    if (Lt > L) L = Lt;
-    R c = ceil(L / res - R(1e-3));
-    return c < R(1) ? 1 : (int)c;
-}
-
-// check_count_r of two rows held in registers (same operations and order).
+// Check points of the edge (qa, ta) -> (qb, tb): ceil(L / res - 1e-3), at
+// least 1, with L the larger of the configuration length and v_max |tb - ta|;
+// working precision, rows held in registers.
 template <typename R>
 __device__ __forceinline__ int check_count_rows(const R (&qa)[kDP], R ta, const R (&qb)[kDP], R tb, int dof, R vmax,
                                                 R res) {
