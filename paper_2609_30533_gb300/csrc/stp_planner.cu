@@ -511,15 +511,13 @@ __device__ __forceinline__ int check_count_rows(const R (&qa)[kDP], R ta, const 
     return c < R(1) ? 1 : (int)c;
 }
 
-// Steer from x_n toward the worker's sample (Algorithm 1 / Eq.
+// Steer from x_n toward the worker's sample x_r (Algorithm 1 / Eq.
 // max-speed-extension), check the horizon and emit the entries. Returns false
 // when the attempt is skipped. Rows live in registers and move as vectors.
 template <typename R>
 __device__ __forceinline__ bool steer_and_emit(const Geom<R>& G, const State<R>& S, int w, int set, bool virt,
-                                               const R (&xn)[kDP]) {
+                                               const R (&xn)[kDP], const R (&xr)[kDP]) {
     const int dof = G.dof;
-    R xr[kDP];
-    ld_row(S.w_xr + (size_t)w * kDP, xr);
     R xw[kDP];
 #pragma unroll
     for (int j = 0; j < kDP; ++j) xw[j] = R(0);
@@ -634,6 +632,10 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
 #pragma unroll
     for (int j = 0; j < kMaxDof; ++j) qr[j] = (j < dof) ? G.qlo[j] + uni_r<R>(d[4 + j]) * (G.qhi[j] - G.qlo[j]) : R(0);
     if (lrn) learned_q(G, S, d, qr);
+    R row[kDP];   // the sample x_r = (q_r, t_r) as stored
+#pragma unroll
+    for (int j = 0; j < kMaxDof; ++j) row[j] = qr[j];
+    row[kDP - 1] = R(0);
 
     if (S.variant == 0) {
         const int g = (int)(((unsigned long long)(d[0] >> 8) * (unsigned long long)S.N) >> 24);
@@ -654,11 +656,7 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
 #pragma unroll
             for (int j = 1; j <= kMaxDof; ++j)
                 if (j == dof) dword = d[4 + j];
-            const R tr = lo + uni_r<R>(dword) * (hi - lo);
-            R row[kDP];
-#pragma unroll
-            for (int j = 0; j < kMaxDof; ++j) row[j] = qr[j];
-            row[kDP - 1] = tr;
+            row[kDP - 1] = lo + uni_r<R>(dword) * (hi - lo);
             st_row(xr, row);
             set = fwd ? 0 : 1 + g;
             if (fwd) {
@@ -672,10 +670,6 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
         int slot = -1;
         if (!fwd && s_nact > 0) slot = s_act[(w / 2) % s_nact];
         if (fwd || slot >= 0) {
-            R row[kDP];
-#pragma unroll
-            for (int j = 0; j < kMaxDof; ++j) row[j] = qr[j];
-            row[kDP - 1] = R(0);
             st_row(xr, row);
             set = fwd ? 0 : 1 + slot;
             status = kNN;
@@ -687,7 +681,7 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
 #pragma unroll
         for (int j = 0; j < kMaxDof; ++j) xn[j] = S.qg[j];
         xn[kDP - 1] = (R)S.w_T[w];
-        if (!steer_and_emit(G, S, w, set, true, xn)) status = kSkip;
+        if (!steer_and_emit(G, S, w, set, true, xn, row)) status = kSkip;
     }
     S.w_status[w] = status;
     S.w_set[w] = set;
@@ -863,13 +857,15 @@ __device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S) {
         const int qt = local / nt, ntile = local % nt;
         const int qi = qt * kQT + t;
         const int w = qi < ts.nq[s] ? S.qlist[(size_t)s * S.W + qi] : -1;
-        R q[DQ], tr = R(0);
-        if (w >= 0) {
-            const R* xr = S.w_xr + (size_t)w * kDP;
+        // The query row stays in registers for the scan and the steering.
+        R xq[kDP];
 #pragma unroll
-            for (int j = 0; j < DQ; ++j) q[j] = xr[j];
-            tr = xr[kDP - 1];
-        }
+        for (int j = 0; j < kDP; ++j) xq[j] = R(0);
+        if (w >= 0) ld_row(S.w_xr + (size_t)w * kDP, xq);
+        R q[DQ];
+#pragma unroll
+        for (int j = 0; j < DQ; ++j) q[j] = xq[j];
+        const R tr = xq[kDP - 1];
         const int n0 = ntile * ts.nts[s];
         const int n1 = min(ts.nn[s], n0 + ts.nts[s]);
         const R* base = s == 0 ? S.fx : S.bx + (size_t)(s - 1) * S.cap_s * kDP;
@@ -965,7 +961,7 @@ __device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S) {
                 if (ok) {
                     R xn[kDP];
                     ld_row(s == 0 ? fnode(S, p) : bnode(S, s - 1, p), xn);
-                    ok = steer_and_emit(G, S, w, s, false, xn);
+                    ok = steer_and_emit(G, S, w, s, false, xn, xq);
                 }
                 if (!ok) S.w_status[w] = kSkip;
             }
@@ -1343,13 +1339,14 @@ __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S)
         const int qt = local / nt, ntile = local % nt;
         const int qi = qt * kQT + t;
         const int w = qi < s_nq[s] ? S.bq_list[(size_t)s * S.W + qi] : -1;
-        R q[DQ], tq = R(0);
-        if (w >= 0) {
-            const R* xq = S.w_xnew + (size_t)w * kDP;
+        R xq[kDP];
 #pragma unroll
-            for (int j = 0; j < DQ; ++j) q[j] = xq[j];
-            tq = xq[kDP - 1];
-        }
+        for (int j = 0; j < kDP; ++j) xq[j] = R(0);
+        if (w >= 0) ld_row(S.w_xnew + (size_t)w * kDP, xq);
+        R q[DQ];
+#pragma unroll
+        for (int j = 0; j < DQ; ++j) q[j] = xq[j];
+        const R tq = xq[kDP - 1];
         const int n0 = ntile * s_nts[s];
         const int n1 = min(s_nn[s], n0 + s_nts[s]);
         R b1 = rinf<R>(), b2 = rinf<R>();
