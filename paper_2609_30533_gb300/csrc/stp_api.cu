@@ -76,7 +76,30 @@ cudaError_t cache_alloc(void** ptr, size_t bytes, size_t* got) {
         }
     }
     *got = bytes;
-    return cudaMalloc(ptr, bytes);
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        // Out of memory: hand this device's idle blocks back to the driver and retry once.
+        (void)cudaGetLastError();
+        std::vector<void*> idle;
+        {
+            DevCache& c = dev_cache();
+            std::lock_guard<std::mutex> g(c.mu);
+            for (auto it = c.blocks.begin(); it != c.blocks.end();) {
+                if (it->second.dev == dev) {
+                    idle.push_back(it->second.ptr);
+                    c.cached -= it->first;
+                    it = c.blocks.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+        if (!idle.empty()) {
+            for (void* q : idle) cudaFree(q);
+            e = cudaMalloc(ptr, bytes);
+        }
+    }
+    return e;
 }
 
 void cache_release(void* ptr, size_t bytes) {
