@@ -10,7 +10,13 @@ edge validation, ordered insertion, bridge scan and validation, publish, root
 recycling). The metric counts validated edges (extension + bridge edges sent to
 the collision kernel) per second of device time.
 
-Beside the headline line: the batched form on 512 mixed problems (autotuned),
+End to end (`e2e`): per step stp_create_problem from host arrays, stp_plan with
+the library's default graph size, the path read back, stp_free, timed on the
+host.
+
+Beside the headline line: the batched form on 512 mixed problems (autotuned;
+also a 48-problem sample planned as one batch against the same problems planned
+one after another, first-solution times from a common start),
 the learned-proposal study on the 7-DoF distribution (training data from
 plain plans, the proposal network trained on the tensor cores, held-out
 problems planned plain and learned at the same budget), and the allocation
