@@ -317,6 +317,24 @@ def batched(args, rank):
     }
 
 
+def aggregate_over_ranks(edges, total_ms, e2e_edges, e2e_secs, dist=None, device="cpu"):
+    """Whole-job figures over the ranks of an initialised process group (or
+    this process alone): edge counts summed, times the maximum over ranks.
+    Returns (edges, ms, e2e edges, e2e seconds)."""
+    import torch
+    vals = torch.tensor([float(edges), float(total_ms), float(e2e_edges), float(e2e_secs)], dtype=torch.float64,
+                        device=device)
+    if dist is not None:
+        tot = vals.clone()
+        dist.all_reduce(tot[0:1], op=dist.ReduceOp.SUM)
+        dist.all_reduce(tot[2:3], op=dist.ReduceOp.SUM)
+        mx = vals.clone()
+        dist.all_reduce(mx[1:2], op=dist.ReduceOp.MAX)
+        dist.all_reduce(mx[3:4], op=dist.ReduceOp.MAX)
+        vals = torch.stack([tot[0], mx[1], tot[2], mx[3]])
+    return tuple(float(x) for x in vals.cpu())
+
+
 def _equal_success_p50(a, b):
     """Median first-solution time of each arm over its k fastest solves, with
     k the smaller of the two arms' solved counts (equal success rate)."""
@@ -672,17 +690,8 @@ def main():
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = float(_peaks().get("sm_max_mhz", 2070.0))
 
-    # Aggregate over ranks: edges summed, time = max over ranks.
-    vals = torch.tensor([float(edges), total_ms, float(e2e_edges), e2e_secs], dtype=torch.float64, device="cuda")
-    if dist:
-        tot = vals.clone()
-        dist.all_reduce(tot[0:1], op=dist.ReduceOp.SUM)
-        dist.all_reduce(tot[2:3], op=dist.ReduceOp.SUM)
-        mx = vals.clone()
-        dist.all_reduce(mx[1:2], op=dist.ReduceOp.MAX)
-        dist.all_reduce(mx[3:4], op=dist.ReduceOp.MAX)
-        vals = torch.stack([tot[0], mx[1], tot[2], mx[3]])
-    edges_all, ms_max, e2e_edges_all, e2e_max = [float(x) for x in vals.cpu()]
+    edges_all, ms_max, e2e_edges_all, e2e_max = aggregate_over_ranks(edges, total_ms, e2e_edges, e2e_secs,
+                                                                     dist, "cuda")
     if rank != 0:
         if dist:
             dist.destroy_process_group()
