@@ -101,6 +101,7 @@ def test_null_arguments(L):
     assert L.stp_plan(None, None, None, None, None, 0, None) == 1
     assert L.stp_check_edges(None, 0, None, None, None, None, 0, None, None, None) == 1
     L.stp_free(None)
+    L.stp_release_cached()     # an empty cache (no device needed)
 
 
 def test_no_cpu_fallback_without_gpu(L):
