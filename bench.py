@@ -189,6 +189,48 @@ def cpu_baseline(args):
                 args.cpu_iters, WORKLOAD, edges, secs)}
 
 
+def _oracle_mixed(job):
+    """One mixed-batch problem planned by the FP64 oracle in a worker process;
+    returns (edges validated, seconds of planning, construction excluded)."""
+    import dataclasses
+
+    import oracle as O
+    index, workers, iters = job
+    prob, prm = WL.mixed(index)
+    prm = dataclasses.replace(prm, workers=workers, max_iters=iters, problem_id=index)
+    t0 = time.perf_counter()
+    r = O.plan(prob, prm)
+    return r.ext_checked + r.bridge_checked, time.perf_counter() - t0
+
+
+def cpu_batched_baseline(problems, workers, iters, cores=None):
+    """The FP64 oracle on a bounded sample of the mixed batched workload, one
+    problem per process over the host's cores (spawn pool, started and warmed
+    before the timed map). Reports the pool's edges/s over all cores (wall
+    clock of the timed map) and the single-core rate (edges over the summed
+    planning seconds)."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    # Heaviest first (spheres x obstacles), so the pool's tail stays short.
+    cost = {}
+    for i in range(problems):
+        pr, _ = WL.mixed(i)
+        cost[i] = len(pr.spheres) * max(len(pr.obs_r), 1)
+    jobs = [(i, workers, iters) for i in sorted(range(problems), key=lambda i: -cost[i])]
+    with mp.get_context("spawn").Pool(min(cores, problems)) as pool:
+        # Bounded waits: a worker that died would otherwise leave map() waiting.
+        pool.map_async(_oracle_mixed, [(i, workers, 1) for i in range(min(cores, problems))]).get(timeout=300)
+        t0 = time.perf_counter()
+        res = pool.map_async(_oracle_mixed, jobs, chunksize=1).get(timeout=600)
+        wall = time.perf_counter() - t0
+    edges = sum(e for e, _ in res)
+    cpu_s = sum(t for _, t in res)
+    return {"value": edges / wall, "unit": UNIT, "cores": min(cores, problems), "kind": "oracle",
+            "single_core_value": edges / cpu_s if cpu_s > 0 else None,
+            "sample": "%d mixed problems x %d iterations x W=%d, one problem per process (%d edges, %.1f s wall, "
+                      "%.1f s of planning summed over processes)" % (problems, iters, workers, edges, wall, cpu_s)}
+
+
 def microbench(args, P, prob, prm, stream, flush, rank, local):
     """Collision kernel alone on 2^20 UR5e edges resident on the device, with
     and without early exit; kernel time from CUDA events around the launch."""
@@ -295,8 +337,17 @@ def batched(args, rank):
     def pct(v, q):
         return float(np.percentile(v, q)) if v else None
 
+    cpu_all = None
+    if not args.no_cpu and rank == 0 and int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        n_cpu = args.cpu_batch_problems or min(32, 2 * (os.cpu_count() or 1))
+        try:
+            cpu_all = cpu_batched_baseline(n_cpu, choice.workers, args.cpu_batch_iters)
+        except Exception as exc:  # a host-side baseline must not cost the GPU measurement
+            cpu_all = {"error": str(exc)}
+
     return {
         "workload": "mixed 2/6/7-DoF, 4-128 obstacles, 10-60 s horizons",
+        "cpu_oracle_all_cores": cpu_all,
         "problems": len(idx), "iters_budget": args.batch_iters,
         "autotuned": {"workers": choice.workers, "nn_ctas": choice.nn_ctas, "validate_ctas": choice.validate_ctas,
                       "trials": [dataclasses.asdict(t) for t in choice.trials]},
@@ -540,6 +591,8 @@ def main():
     ap.add_argument("--iters", type=int, default=32, help="planner iterations per step")
     ap.add_argument("--ref-iters", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=8)
+    ap.add_argument("--cpu-batch-problems", type=int, default=0, help="0 = one per host core (at most 32)")
+    ap.add_argument("--cpu-batch-iters", type=int, default=2)
     ap.add_argument("--micro-edges", type=int, default=1 << 20)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch-problems", type=int, default=512)
