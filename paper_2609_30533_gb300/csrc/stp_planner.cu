@@ -1281,8 +1281,10 @@ __device__ __forceinline__ bool cas_min_u128(unsigned long long* base, int w, un
 // Set 0: queries = backward-inserted nodes, vertices = forward arena [0, snap_f).
 // Set 1: queries = forward-inserted nodes, vertices = all backward segments
 //        [0, snap_s[i]) concatenated in segment order; active iff troot < U.
-// Rank: (arrival time, rho^2, index) lexicographic. The last CTA of a query
-// tile reduces the per-tile partials in tile order and emits the bridge edges.
+// Rank: (arrival time, rho^2, index) lexicographic. FP32 tiles merge their
+// best into one 128-bit key per query (compare-and-swap minimum); FP64 tiles
+// leave partials that the last CTA of the query tile reduces in tile order.
+// The last CTA of a query tile emits the bridge edges.
 // ---------------------------------------------------------------------------
 template <typename R, int DQ>
 __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S) {
