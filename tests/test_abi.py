@@ -96,6 +96,54 @@ def test_invalid_geometry_rejected(L):
     assert s == 1
 
 
+@pytest.mark.parametrize("bad", [dict(n_roots=129), dict(ext_per_iter=8193), dict(variant=-1),
+                                 dict(edge_res=0.0), dict(env_dt=-0.02), dict(t_max=0.0), dict(p_guided=-0.1),
+                                 dict(capacity=-1), dict(iters_per_graph=-1), dict(t_offset=float("inf"))])
+def test_parameter_limits(L, bad):
+    prob, _ = WL.disc2d(0)
+    s, h = _create(prob, _params(**bad))
+    assert s == 1 and not h.value
+
+
+def _limit_case(which):
+    prob, _ = WL.disc2d(0)
+    if which == "dof1":
+        prob.dof = 1
+    elif which == "point-dof4":
+        prob.dof = 4
+        prob.qlo, prob.qhi = np.zeros(4), np.ones(4)
+        prob.qs, prob.qg = np.full(4, 0.05), np.full(4, 0.95)
+    elif which == "spheres65":
+        prob.spheres = np.tile(prob.spheres[:1], (65, 1))
+    elif which == "spheres0":
+        prob.spheres = prob.spheres[:0]
+    elif which == "obstacles129":
+        prob.obs_r = np.full(129, 0.05)
+        prob.way = np.repeat(prob.way[:1], 129, axis=0)
+    elif which == "waypoints9":
+        t = np.arange(9, dtype=float)
+        prob.way = np.zeros((len(prob.obs_r), 9, 4))
+        prob.way[:, :, 0] = t
+    elif which == "box-inverted":
+        prob.qlo, prob.qhi = prob.qhi.copy(), prob.qlo.copy()
+    elif which == "radius-negative":
+        prob.obs_r = prob.obs_r.copy()
+        prob.obs_r[0] = -0.01
+    elif which == "sphere-frame":
+        prob.spheres = prob.spheres.copy()
+        prob.spheres[0, 0] = 1.0            # a point robot has only frame 0
+    elif which == "vmax0":
+        prob.vmax = 0.0
+    return prob
+
+
+@pytest.mark.parametrize("which", ["dof1", "point-dof4", "spheres65", "spheres0", "obstacles129", "waypoints9",
+                                   "box-inverted", "radius-negative", "sphere-frame", "vmax0"])
+def test_geometry_limits(L, which):
+    s, h = _create(_limit_case(which), _params())
+    assert s == 1 and not h.value
+
+
 def test_null_arguments(L):
     assert L.stp_create_problem(None, None, None, None, None, None) == 1
     assert L.stp_plan(None, None, None, None, None, 0, None) == 1
