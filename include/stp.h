@@ -91,7 +91,11 @@ typedef struct {
  *   eta            range: steering step in rho (interval root, Algorithm 1) or
  *                  configuration step (root recycling, Eq. max-speed-extension).
  *   edge_res       check resolution: an edge is checked at
- *                  c = max(1, ceil(max(D, v_max |dt|) / edge_res)) points j/c.
+ *                  c = max(1, ceil(max(D, v_max |dt|) / edge_res - 1e-3))
+ *                  points j/c, j = 1..c (the paper leaves the resolution rule
+ *                  open; the 1e-3 slack keeps c stable when the length is an
+ *                  exact multiple of edge_res, so the spacing may exceed
+ *                  edge_res by at most 0.1 % of one step).
  *   env_dt         environment grid step dt for goal checks
  *                  (Eq. goal-time-lower-bound).
  *   p_new, p_guided  Sec. "Interval Root" (paper default 0.05 / 0.95).

@@ -32,7 +32,8 @@ class OrcParams(C.Structure):
                 ("dt", C.c_double), ("p_new", C.c_double), ("p_guided", C.c_double),
                 ("H", C.c_double), ("seed", C.c_ulonglong), ("problem_id", C.c_uint),
                 ("flag_tol", C.c_double), ("flag_clear", C.c_double), ("learned", C.c_int),
-                ("proposal", _D), ("t_offset", C.c_double), ("continuous", C.c_int)]
+                ("proposal", _D), ("t_offset", C.c_double), ("continuous", C.c_int),
+                ("follow_rec", _I), ("follow_iters", C.c_int), ("follow_grid", _U8), ("follow_nk", C.c_int)]
 
 
 def _dptr(a: np.ndarray):
@@ -84,8 +85,34 @@ def lib():
     L.orc_result_goal_grid.argtypes = [C.c_void_p, C.POINTER(C.c_long), _D, C.c_int]
     L.orc_result_goal_grid.restype = C.c_int
     L.orc_result_incumbent.argtypes = [C.c_void_p, _I, _I, _I]
+    L.orc_result_C_history.argtypes = [C.c_void_p, _D]
+    L.orc_result_trace.argtypes = [C.c_void_p, _I, _D]
+    L.orc_result_follow.argtypes = [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _I, C.c_int]
+    L.orc_result_follow.restype = C.c_int
+    L.orc_follow_kinds.argtypes = []
+    L.orc_follow_kinds.restype = C.c_int
+    L.orc_nn_config.argtypes = [C.c_int, C.c_int, _D, _D, _D]
+    L.orc_nn_config.restype = C.c_int
+    L.orc_publish_winner.argtypes = [C.c_int, _D, _D, _I]
+    L.orc_publish_winner.restype = C.c_int
+    L.orc_bridge.argtypes = [C.POINTER(OrcProblem), _D, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _D,
+                             _D, _D, _I, C.c_double, C.c_double, C.c_double, _I, _D]
+    L.orc_bridge.restype = C.c_int
     L.orc_result_free.argtypes = [C.c_void_p]
     return L
+
+
+# Decision records (one per worker and iteration), the layout shared with the
+# device library's trace: see TRACE_FIELDS / TRACE_FLAGS.
+TRACE_INTS = 10
+TRACE_FIELDS = ("flags", "group", "parent", "ext_count", "br_set", "br_idx", "br_count", "inserted",
+                "component", "reserved")
+TRACE_FLAGS = {"fwd": 1, "sampled": 2, "virtual": 4, "emit": 8, "root_hit": 16, "ext_hit": 32,
+               "inserted": 64, "br_cand": 128, "br_emit": 256, "br_hit": 512, "winner": 1024,
+               "learned": 2048, "learned_T": 4096}
+FOLLOW_KINDS = ("direction", "group", "learned_component", "learned_T", "root", "window", "virtual",
+                "parent", "emit", "ext_count", "ext_hit", "inserted", "br_cand", "br_emit", "br_count",
+                "br_hit", "winner", "grid")
 
 
 class _ProblemHandle:
@@ -245,13 +272,17 @@ class PlanResult:
     incumbent: tuple
     goal_kmin: int
     goal_clearance: np.ndarray
+    C_hist: np.ndarray = None
+    trace: np.ndarray = None     # [iters][W][TRACE_INTS] int32 decision records
+    trace_d: np.ndarray = None   # [iters][W][4] (T, t_r, window lo, window hi), NaN where not drawn
+    follow: Dict[str, object] = None  # follow mode: adopted / differing counts per kind, unflagged list
 
 
 def make_params(params, proposal=None, t_offset=0.0, continuous=False, **over) -> OrcParams:
     p = dataclasses.replace(params, **over) if over else params
     prm = OrcParams(p.variant, p.n_roots, p.workers, p.max_iters, p.eta, p.res, p.dt, p.p_new,
                     p.p_guided, p.H, p.seed, p.problem_id, 0.0, 0.0, 0, None, float(t_offset),
-                    1 if continuous else 0)
+                    1 if continuous else 0, None, 0, None, 0)
     if proposal is not None:
         prm.learned = 1
         prm.proposal = _dptr(proposal)
@@ -279,15 +310,31 @@ def learned_sample(y, qlo, qhi, H, seed, problem_id, k, w, qs=None, qg=None):
     return bool(f), wi.value, qr, Tl.value
 
 
-def plan(prob, params, proposal=None, t_offset=0.0, continuous=False, **over) -> PlanResult:
+def plan(prob, params, proposal=None, t_offset=0.0, continuous=False, follow=None, **over) -> PlanResult:
     """proposal: network output y[160] (float64 array) enables the learned
     branch; t_offset: absolute time of the query's local time 0; continuous:
-    closed-form edge validation (point robots)."""
+    closed-form edge validation (point robots); follow: (records
+    [iters][W][TRACE_INTS] int32, goal-grid free flags or None) of a device run:
+    the oracle adopts the device's choice at every flagged decision and records
+    every unflagged difference (follow mode)."""
     L = lib()
     h = _ProblemHandle(prob)
     if proposal is not None:
         proposal = np.ascontiguousarray(proposal, dtype=np.float64)
     prm = make_params(params, proposal, t_offset, continuous, **over)
+    keep = []
+    if follow is not None:
+        rec, grid = follow
+        rec = np.ascontiguousarray(rec, dtype=np.int32)
+        assert rec.ndim == 3 and rec.shape[1] == prm.workers and rec.shape[2] == TRACE_INTS, rec.shape
+        keep.append(rec)
+        prm.follow_rec = rec.ctypes.data_as(_I)
+        prm.follow_iters = rec.shape[0]
+        if grid is not None:
+            grid = np.ascontiguousarray(grid, dtype=np.uint8)
+            keep.append(grid)
+            prm.follow_grid = grid.ctypes.data_as(_U8)
+            prm.follow_nk = len(grid)
     handle = C.c_void_p()
     L.orc_plan(h.ref, C.byref(prm), C.byref(handle))
     try:
@@ -336,12 +383,32 @@ def plan(prob, params, proposal=None, t_offset=0.0, continuous=False, **over) ->
         gcap = 1 << 20
         gcl = np.zeros(gcap)
         ng = L.orc_result_goal_grid(handle, C.byref(kmin), _dptr(gcl), gcap)
+        Chh = np.zeros(iters)
+        W = prm.workers
+        trace = np.zeros((iters, W, TRACE_INTS), dtype=np.int32)
+        trace_d = np.zeros((iters, W, 4))
+        if iters:
+            L.orc_result_C_history(handle, _dptr(Chh))
+            L.orc_result_trace(handle, trace.ctypes.data_as(_I), _dptr(trace_d))
+        nk = L.orc_follow_kinds()
+        fo = np.zeros(nk, dtype=np.int64)
+        fd = np.zeros(nk, dtype=np.int64)
+        nu = L.orc_result_follow(handle, fo.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                 fd.ctypes.data_as(C.POINTER(C.c_longlong)), None, 0)
+        un = np.zeros((max(nu, 1), 3), dtype=np.int32)
+        L.orc_result_follow(handle, None, None, un.ctypes.data_as(_I), nu)
+        follow_info = None
+        if follow is not None:
+            follow_info = {"followed": dict(zip(FOLLOW_KINDS, fo.tolist())),
+                           "flagged_diff": dict(zip(FOLLOW_KINDS, fd.tolist())),
+                           "unflagged": [(int(a), int(b), FOLLOW_KINDS[c]) for a, b, c in un[:nu]]}
         return PlanResult(U=s[0], C=s[1], iters=iters, first_iter=int(s[3]), ext_checked=int(s[4]),
                           bridge_checked=int(s[5]), root_checked=int(s[6]), inserted=int(s[7]),
                           path=path, status=int(s[11]), fwd=arena(-1),
                           seg=[arena(i) for i in range(N)], U_hist=Uh, margin_hist=Mh, clear_hist=Ch,
                           margin_types=MT, slots=sl, trees=tr, incumbent=(f.value, sg.value, b.value),
-                          goal_kmin=kmin.value, goal_clearance=gcl[:ng].copy())
+                          goal_kmin=kmin.value, goal_clearance=gcl[:ng].copy(), C_hist=Chh, trace=trace,
+                          trace_d=trace_d, follow=follow_info)
     finally:
         L.orc_result_free(handle)
 
@@ -397,3 +464,39 @@ def self_pairs(prob) -> np.ndarray:
     out = np.zeros((max(n, 1), 2), dtype=np.int32)
     lib().orc_self_pairs(h.ref, out.ctypes.data_as(_I), n)
     return out[:n]
+
+
+def nn_config(x, qr):
+    """Configuration-distance NN (root recycling) over configurations x [n][d]:
+    (index or -1, distance); tie: lowest index."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n, d = x.shape
+    qr = np.ascontiguousarray(qr, dtype=np.float64)
+    D = C.c_double()
+    i = lib().orc_nn_config(n, d, _dptr(x), _dptr(qr), C.byref(D))
+    return i, D.value
+
+
+def publish_winner(U, C_, w):
+    """Index of the lexicographic minimum (U, C, worker) of successful bridges."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    C_ = np.ascontiguousarray(C_, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.int32)
+    return lib().orc_publish_winner(len(U), _dptr(U), _dptr(C_), w.ctypes.data_as(_I))
+
+
+def bridge(prob, qa, ta, troot_a, cost_a, forward, x, troot, cost, seg, U0, C0, res):
+    """One bridge step of node a against candidate rows x [n][d+1]: returns
+    (ok, candidate group or -1, candidate index, improves, validated, U, C)."""
+    h = _ProblemHandle(prob)
+    qa = np.ascontiguousarray(qa, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    troot = np.ascontiguousarray(troot, dtype=np.float64)
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    seg = np.ascontiguousarray(seg if seg is not None else np.zeros(len(x)), dtype=np.int32)
+    out = np.zeros(4, dtype=np.int32)
+    od = np.zeros(2)
+    ok = lib().orc_bridge(h.ref, _dptr(qa), float(ta), float(troot_a), float(cost_a), 1 if forward else 0, len(x),
+                          _dptr(x), _dptr(troot), _dptr(cost), seg.ctypes.data_as(_I), float(U0), float(C0),
+                          float(res), out.ctypes.data_as(_I), _dptr(od))
+    return bool(ok), int(out[0]), int(out[1]), bool(out[2]), int(out[3]), od[0], od[1]

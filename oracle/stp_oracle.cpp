@@ -17,8 +17,17 @@
 //
 // Parity status: every function here is pinned by tests/test_oracle_*.py
 // (worked examples of Figs. interval-root and method, closed forms, brute force,
-// invariants); end-to-end success rates and arrival values of the synthetic
-// workloads are parity unpinned (the paper's suites are not available).
+// invariants); the per-worker decisions (direction, group, new-root coin,
+// conditional query time, NN parents, bridge rank, improvement test, publish
+// order, round-robin slots) are re-derived by brute force from the decision
+// records and by hand cases in tests/test_oracle_decisions.py. End-to-end
+// success rates and arrival values of the synthetic workloads are parity
+// unpinned (the paper's suites are not available).
+//
+// Every run records one decision record per worker and iteration (the layout
+// the device library's trace writes too). Follow mode takes a device run's
+// records: where an FP64 margin is below the flag threshold the oracle adopts
+// the device's choice, elsewhere any difference is reported.
 
 #include <algorithm>
 #include <cmath>
@@ -277,9 +286,13 @@ int edge_check_count(const Problem& P, const double* qa, double ta, const double
 // exit) and check-point count.
 // bound_margin: min over check points and joints of (q - lo, hi - q), the
 // signed distance of the checked states from the configuration-box boundary.
+// force_count > 0 checks that many points instead (follow mode adopts a
+// reduced-precision run's count where the rounding of c is undecided).
 bool edge_free(const Problem& P, const double* qa, double ta, const double* qb, double tb, double res,
-               double* clearance, int* nchk, double* int_margin, double* bound_margin = nullptr) {
+               double* clearance, int* nchk, double* int_margin, double* bound_margin = nullptr,
+               int force_count = 0) {
     int c = edge_check_count(P, qa, ta, qb, tb, res, int_margin);
+    if (force_count > 0) c = force_count;
     bool free = true;
     double clr = kInf, bm = kInf;
     std::vector<double> q(P.dof);
@@ -663,6 +676,44 @@ struct Params {
     double flag_clear = 1e-5;  // clearance band (m)
     const double* proposal = nullptr;  // learned branch: network output y[160], or none
     int continuous = 0;                // point robots: closed-form edge validation
+    // Follow mode (parity of a reduced-precision run, see struct Follow):
+    // decision records [follow_iters][W][kTraceInts] and goal-grid free flags
+    // [follow_nk] of that run, or none.
+    const int* follow_rec = nullptr;
+    int follow_iters = 0;
+    const unsigned char* follow_grid = nullptr;
+    int follow_nk = 0;
+};
+
+// Decision record of one worker in one iteration. The same field meanings are
+// written, independently, by the device library's trace (an interface, not
+// shared code): the oracle records its own decisions here, and in follow mode
+// it reads the device's.
+//   [0] flags (TraceFlag), [1] group (interval) / slot (recycling) or -1,
+//   [2] NN parent index (-1: virtual root or none), [3] extension check count
+//   (0: no edge), [4] bridge candidate arena (-1 forward tree, else backward
+//   group / slot), [5] bridge candidate index (-1), [6] bridge check count,
+//   [7] inserted node index (-1), [8] learned mixture component (-1), [9] 0.
+constexpr int kTraceInts = 10;
+enum TraceFlag {
+    kTrFwd = 1,          // forward worker: (w + k) even
+    kTrSampled = 2,      // interval: non-empty query-time window; recycling: a source tree
+    kTrVirtual = 4,      // backward source is a new (virtual) root
+    kTrEmit = 8,         // extension edge steered and inside the horizon
+    kTrRootHit = 16,     // the sampled goal root collides
+    kTrExtHit = 32,      // the extension edge collides
+    kTrInserted = 64,
+    kTrBrCand = 128,     // an admissible bridge candidate exists
+    kTrBrEmit = 256,     // the candidate would improve (U, C) and is validated
+    kTrBrHit = 512,      // the bridge edge collides
+    kTrWinner = 1024,    // this worker's bridge is the iteration's published solution
+    kTrLearned = 2048,   // learned worker (slot-12 coin)
+    kTrLearnedT = 4096,  // goal time taken from the mixture
+};
+// Decision kinds counted in follow mode.
+enum Kind {
+    kKDirection, kKGroup, kKLearnedComp, kKLearnedT, kKRoot, kKWindow, kKVirtual, kKParent, kKEmit,
+    kKExtCount, kKExtHit, kKInserted, kKBrCand, kKBrEmit, kKBrCount, kKBrHit, kKWinner, kKGrid, kKinds
 };
 
 // Smallest decision margins seen during one iteration (test diagnostics for
@@ -690,11 +741,19 @@ struct Result {
     int iters = 0, first_iter = -1;
     long long ext_checked = 0, bridge_checked = 0, root_checked = 0, inserted = 0;
     std::vector<double> path;  // [len][dof+1]
-    std::vector<double> U_hist, margin_hist, clear_hist;
+    std::vector<double> U_hist, C_hist, margin_hist, clear_hist;
     std::vector<double> margin_types;  // [iters][6]: nn, count, interval, bounds, rank, clearance
     int status = 0;  // 0 solved, 5 no solution
     std::vector<double> goal_clearance;
     long goal_kmin = 0;
+    // Decision records [iters][W][kTraceInts] and per worker (T, t_r, window
+    // lo, window hi) [iters][W][4] (NaN where not drawn).
+    std::vector<int> trace;
+    std::vector<double> trace_d;
+    // Follow mode: decisions adopted from the device run per kind, those where
+    // its choice differed, and unflagged differences as (iter, worker, kind).
+    long long followed[kKinds] = {}, flagged_diff[kKinds] = {};
+    std::vector<int> unflagged;
 };
 
 struct Proposal {
@@ -772,6 +831,106 @@ int nn_config(const std::vector<Node>& A, int n, const double* qr, int d, double
     return best;
 }
 
+// Bridge rank (Algorithm 1, "Connect"; Sec. "Interval Root": a connection is
+// ranked by arrival time, then by space-time distance). For an inserted node a
+// the candidates are the vertices of the opposite start-of-iteration set that
+// a can reach with an admissible edge (rho_sigma finite): a forward node looks
+// at later vertices of the active backward trees (root time < U0), a backward
+// node at earlier vertices of the forward tree. Key (arrival time = root time
+// of the backward end, rho); ties go to the lowest (segment, index). Only the
+// top-ranked candidate is ever validated (by the caller).
+// margin: the smallest gap between the winner's key and a competing key, or
+// between a competitive vertex and an admissibility boundary.
+struct BridgeCand {
+    int s = -1, i = -1;  // s: backward group / slot of the candidate, -1 for the forward tree
+    double U = kInf, rho = kInf;
+    double margin = kInf;
+};
+
+BridgeCand bridge_rank(const Node& a, bool forward, const std::vector<std::vector<Node>>& seg,
+                       const std::vector<int>& seg_n, const std::vector<Node>& fwd, int fwd_n, double U0, int d,
+                       double v, double tol) {
+    BridgeCand c;
+    double s1U = kInf, s1R = kInf;  // runner-up key
+    auto consider = [&](int s, int i, double Uv, double r) {
+        const bool better = (Uv < c.U) || (Uv == c.U && r < c.rho);
+        if (better) {
+            s1U = c.U;
+            s1R = c.rho;
+            c.U = Uv;
+            c.rho = r;
+            c.s = s;
+            c.i = i;
+        } else if ((Uv < s1U) || (Uv == s1U && r < s1R)) {
+            s1U = Uv;
+            s1R = r;
+        }
+    };
+    // First pass: the ranking. Second pass: admissibility margins of vertices
+    // whose key would be competitive with the winner.
+    for (int pass = 0; pass < 2; ++pass) {
+        if (forward) {
+            for (int s = 0; s < (int)seg_n.size(); ++s) {
+                for (int i = 0; i < seg_n[s]; ++i) {
+                    const Node& b = seg[s][i];
+                    if (!(b.troot < U0)) continue;
+                    if (pass == 0) {
+                        const double r = rho_sigma(a.q.data(), a.t, b.q.data(), b.t, 1, d, v);
+                        if (r < kInf) consider(s, i, b.troot, r);
+                        continue;
+                    }
+                    const double Delta = b.t - a.t, D = dist(a.q.data(), b.q.data(), d);
+                    const double madm = std::min(std::fabs(Delta), std::fabs(v * Delta - D));
+                    const double ru = std::sqrt((D * D + v * v * Delta * Delta) / 2.0);
+                    if (madm < tol && b.troot <= c.U + tol && ru <= c.rho + tol) note(c.margin, madm);
+                }
+            }
+        } else {
+            for (int i = 0; i < fwd_n; ++i) {
+                const Node& b = fwd[i];
+                if (pass == 0) {
+                    const double r = rho_sigma(b.q.data(), b.t, a.q.data(), a.t, 1, d, v);
+                    if (r < kInf) consider(-1, i, a.troot, r);
+                    continue;
+                }
+                const double Delta = a.t - b.t, D = dist(a.q.data(), b.q.data(), d);
+                const double madm = std::min(std::fabs(Delta), std::fabs(v * Delta - D));
+                const double ru = std::sqrt((D * D + v * v * Delta * Delta) / 2.0);
+                if (madm < tol && ru <= c.rho + tol) note(c.margin, madm);
+            }
+        }
+    }
+    if (c.i >= 0) {
+        if (s1U == c.U && s1R < kInf) note(c.margin, s1R - c.rho);
+        if (s1U != c.U && s1U < kInf) note(c.margin, s1U - c.U);
+    }
+    return c;
+}
+
+// Publish order (Sec. "GPU-Parallel Space-Time Forest": workers publish
+// improved solutions atomically; batch-synchronous reading: of an iteration's
+// successful bridges the lexicographically smallest (U, C, worker) wins).
+bool publish_before(double U1, double C1, int w1, double U2, double C2, int w2) {
+    if (U1 != U2) return U1 < U2;
+    if (C1 != C2) return C1 < C2;
+    return w1 < w2;
+}
+
+// Follow mode (parity of a reduced-precision device run against this FP64
+// run). At a decision whose FP64 margin lies below the flag threshold the
+// oracle adopts the device's recorded choice and continues; at any other
+// decision a differing device choice is an unflagged mismatch: it is recorded
+// (the parity tests require none) and adopted, so that the comparison still
+// covers the rest of the run.
+struct Follow {
+    const int* rec = nullptr;
+    int iters = 0, W = 0;
+    const int* at(int k, int w) const {
+        if (!rec || k >= iters) return nullptr;
+        return rec + ((size_t)k * W + w) * kTraceInts;
+    }
+};
+
 class Planner {
 public:
     Planner(const Problem& P, const Params& prm) : P(P), prm(prm) {}
@@ -785,28 +944,60 @@ private:
     GoalGrid grid;
     IntervalAlloc alloc;
     Learned learned;
+    Follow F;
     long kend = 0;  // first grid index with k dt >= H (recycling roots lie in [L_grid, H))
 
     int d() const { return P.dof; }
-    void check_edge(const double* qa, double ta, const double* qb, double tb, bool* ok, Margin& M) {
-        double clr, im, bm;
-        int c;
-        if (prm.continuous) {
-            *ok = edge_free_continuous(P, qa, ta, qb, tb, &clr);
-            note(M.clearance, clr);
-            return;
+    // One decision: `mine` with FP64 margin flagged or not, against the device
+    // record's value `dev` when following (dev_rec != nullptr).
+    int decide(int k, int w, int kind, int mine, const void* dev_rec, int dev, bool flagged) {
+        if (!dev_rec) return mine;
+        if (flagged) {
+            R.followed[kind]++;
+            if (dev != mine) R.flagged_diff[kind]++;
+            return dev;
         }
-        *ok = edge_free(P, qa, ta, qb, tb, prm.res, &clr, &c, &im, &bm);
+        if (dev != mine) {
+            R.unflagged.push_back(k);
+            R.unflagged.push_back(w);
+            R.unflagged.push_back(kind);
+            return dev;
+        }
+        return mine;
+    }
+    bool decide_flag(int k, int w, int kind, bool mine, const int* dev_rec, int bit, bool flagged) {
+        const int dev = dev_rec ? ((dev_rec[0] & bit) ? 1 : 0) : 0;
+        return decide(k, w, kind, mine ? 1 : 0, dev_rec, dev, flagged) != 0;
+    }
+    // Edge check with follow decisions on its count and verdict.
+    bool check_edge_follow(int k, int w, const double* qa, double ta, const double* qb, double tb, Margin& M,
+                           const int* dv, int count_field, int kind_count, int hit_bit, int kind_hit, int* count_out) {
+        double clr, im = kInf, bm = kInf;
+        int c = 0;
+        bool ok;
+        if (prm.continuous) {
+            // The count only marks the entry (the verdict is closed-form).
+            ok = edge_free_continuous(P, qa, ta, qb, tb, &clr);
+            c = edge_check_count(P, qa, ta, qb, tb, prm.res, nullptr);
+        } else {
+            c = edge_check_count(P, qa, ta, qb, tb, prm.res, &im);
+            c = decide(k, w, kind_count, c, dv, dv ? dv[count_field] : 0, im < prm.flag_tol);
+            ok = edge_free(P, qa, ta, qb, tb, prm.res, &clr, nullptr, nullptr, &bm, c);
+            note(M.count, im);
+            note(M.bounds, bm);
+        }
         note(M.clearance, clr);
-        note(M.count, im);
-        note(M.bounds, bm);
+        const bool flagged = std::fabs(clr) < prm.flag_clear || std::fabs(bm) < prm.flag_tol;
+        const bool hit = decide_flag(k, w, kind_hit, !ok, dv, hit_bit, flagged);
+        *count_out = c;
+        return !hit;
     }
     void init_recycling();
     void recycle(double U);
     Proposal propose_interval(int k, int w, const std::vector<int>& seg_n, int fwd_n, double U0,
-                              const std::vector<int>& group_active, Margin& M);
+                              const std::vector<int>& group_active, Margin& M, int* rec, double* rd);
     Proposal propose_recycling(int k, int w, const std::vector<int>& seg_n, int fwd_n,
-                               const std::vector<int>& active_slots, Margin& M);
+                               const std::vector<int>& active_slots, Margin& M, int* rec);
     void extract_path();
 };
 
@@ -861,35 +1052,61 @@ void Planner::recycle(double U) {
 }
 
 Proposal Planner::propose_interval(int k, int w, const std::vector<int>& seg_n, int fwd_n, double U0,
-                                   const std::vector<int>& group_active, Margin& M) {
+                                   const std::vector<int>& group_active, Margin& M, int* rec, double* rd) {
     Proposal pr;
     int dd = d();
+    const int* dv = F.at(k, w);
     Draws dr;
     dr.fill(prm.seed, prm.problem_id, (uint32_t)k, (uint32_t)w, learned.on ? 17 : 5 + dd);
     const bool lrn = learned.on && (dr.raw[12] >> 8) < kThrLearned;
     pr.forward = ((w + k) % 2) == 0;
+    pr.forward = decide_flag(k, w, kKDirection, pr.forward, dv, kTrFwd, false);
     int g = dr.group(0, prm.N);
+    g = decide(k, w, kKGroup, g, dv, dv ? dv[1] : 0, false);
     pr.seg = g;
+    rec[0] |= (pr.forward ? kTrFwd : 0) | (lrn ? kTrLearned : 0);
+    rec[1] = g;
     bool guided;
     double T = sample_goal_time(alloc, g, dr.u(1), dr.u(2), prm.p_guided, &guided);
     if (lrn) {
         double cm;
-        const double Tl = learned_T(learned, dr, &cm);
+        double Tl = learned_T(learned, dr, &cm);
+        int comp = 0;
+        while (comp < 7 && !(dr.u(14) < learned.cw[comp])) ++comp;
+        const int comp_f = decide(k, w, kKLearnedComp, comp, dv, dv ? dv[8] : 0, cm < prm.flag_tol);
+        if (comp_f != comp) {
+            // Adopted component: the same normal draw around its mean.
+            const double u1 = 1.0 - dr.u(15), u2 = dr.u(16);
+            const double z = std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586476925 * u2);
+            Tl = learned.mu[comp_f] + learned.sig[comp_f] * z;
+        }
+        rec[8] = comp_f;
         const double glo = alloc.Lg + (double)g * alloc.width;
         note(M.interval, cm);
         note(M.bounds, Tl - glo);
         note(M.bounds, glo + alloc.width - Tl);
-        if (Tl >= glo && Tl < glo + alloc.width) T = Tl;
+        const double mb = std::min(std::fabs(Tl - glo), std::fabs(glo + alloc.width - Tl));
+        const bool take = decide_flag(k, w, kKLearnedT, Tl >= glo && Tl < glo + alloc.width, dv, kTrLearnedT,
+                                      mb < prm.flag_tol);
+        if (take) {
+            T = Tl;
+            rec[0] |= kTrLearnedT;
+        }
     }
     pr.T = T;
+    rd[0] = T;
     // Each proposed root is collision-checked at its sampled time; a rejected
     // root skips the attempt (Algorithm 2).
     {
         double cl;
-        bool ok = state_free(P, P.qg.data(), T, &cl);
+        const bool free = state_free(P, P.qg.data(), T, &cl);
         R.root_checked++;
         note(M.clearance, cl);
-        if (!ok) return pr;
+        const bool hit = decide_flag(k, w, kKRoot, !free, dv, kTrRootHit, std::fabs(cl) < prm.flag_clear);
+        if (hit) {
+            rec[0] |= kTrRootHit;
+            return pr;
+        }
     }
     // Conditional query sample (Eq. conditional-query-time).
     std::vector<double> qr(dd);
@@ -897,39 +1114,64 @@ Proposal Planner::propose_interval(int k, int w, const std::vector<int>& seg_n, 
     if (lrn) learned_q(learned, dr, P.qlo, P.qhi, dd, qr.data());
     double lo = dist(P.qs.data(), qr.data(), dd) / P.vmax;
     double hi = T - dist(qr.data(), P.qg.data(), dd) / P.vmax;
+    rd[2] = lo;
+    rd[3] = hi;
     note(M.interval, hi - lo);
-    if (lo > hi) return pr;
+    const bool sampled = decide_flag(k, w, kKWindow, !(lo > hi), dv, kTrSampled, std::fabs(hi - lo) < prm.flag_tol);
+    if (!sampled) return pr;
+    rec[0] |= kTrSampled;
     double tr = lo + dr.u(4 + dd) * (hi - lo);
+    rd[1] = tr;
 
     // Source set and NN (Algorithm 1).
     const double* qn;
     double tn;
     double rho;
-    int sigma = pr.forward ? 1 : -1;
     if (pr.forward) {
-        int i = nn_spacetime(R.fwd, fwd_n, false, U0, qr.data(), tr, 1, dd, P.vmax, &rho, M, prm.flag_tol);
+        Margin Mw;
+        int i = nn_spacetime(R.fwd, fwd_n, false, U0, qr.data(), tr, 1, dd, P.vmax, &rho, Mw, prm.flag_tol);
+        note(M.nn, Mw.nn);
+        i = decide(k, w, kKParent, i, dv, dv ? dv[2] : 0, Mw.nn < prm.flag_tol);
+        rec[2] = i;
         if (i < 0) return pr;
+        if (i >= fwd_n) return pr;  // an adopted index outside the set (already counted as a mismatch)
+        rho = rho_sigma(R.fwd[i].q.data(), R.fwd[i].t, qr.data(), tr, 1, dd, P.vmax);
         pr.parent = i;
         qn = R.fwd[i].q.data();
         tn = R.fwd[i].t;
     } else {
         bool use_new = (group_active[g] == 0) || (dr.u(3) <= prm.p_new);
+        use_new = decide_flag(k, w, kKVirtual, use_new, dv, kTrVirtual, false);
         if (use_new) {
+            rec[0] |= kTrVirtual;
             rho = rho_sigma(P.qg.data(), T, qr.data(), tr, -1, dd, P.vmax);
-            if (!(rho < kInf)) return pr;
+            // Admissibility of the virtual root (rho finite) is an emit decision.
+            const double Delta = T - tr, D = dist(P.qg.data(), qr.data(), dd);
+            const double madm = std::min(std::fabs(Delta), std::fabs(P.vmax * Delta - D));
+            note(M.bounds, madm);
+            if (!(rho < kInf)) {
+                const bool emit = decide_flag(k, w, kKEmit, false, dv, kTrEmit, madm < prm.flag_tol);
+                if (!emit) return pr;
+                rho = std::sqrt((D * D + P.vmax * P.vmax * Delta * Delta) / 2.0);
+            }
             pr.parent = -1;
+            rec[2] = -1;
             qn = P.qg.data();
             tn = T;
         } else {
-            int i = nn_spacetime(R.seg[g], seg_n[g], true, U0, qr.data(), tr, -1, dd, P.vmax, &rho, M,
+            Margin Mw;
+            int i = nn_spacetime(R.seg[g], seg_n[g], true, U0, qr.data(), tr, -1, dd, P.vmax, &rho, Mw,
                                  prm.flag_tol);
-            if (i < 0) return pr;
+            note(M.nn, Mw.nn);
+            i = decide(k, w, kKParent, i, dv, dv ? dv[2] : 0, Mw.nn < prm.flag_tol);
+            rec[2] = i;
+            if (i < 0 || i >= seg_n[g]) return pr;
+            rho = rho_sigma(R.seg[g][i].q.data(), R.seg[g][i].t, qr.data(), tr, -1, dd, P.vmax);
             pr.parent = i;
             qn = R.seg[g][i].q.data();
             tn = R.seg[g][i].t;
         }
     }
-    (void)sigma;
     // Steering: x_new = x_n + alpha (x_r - x_n), alpha = min(1, eta / rho).
     double alpha = std::min(1.0, prm.eta / rho);
     pr.x.assign(dd + 1, 0.0);
@@ -938,41 +1180,60 @@ Proposal Planner::propose_interval(int k, int w, const std::vector<int>& seg_n, 
     pr.x[dd] = tnew;
     note(M.bounds, tnew);
     note(M.bounds, prm.H - tnew);
-    if (tnew < 0.0 || tnew > prm.H) return pr;
-    bool ok;
-    check_edge(qn, tn, pr.x.data(), tnew, &ok, M);
+    const double mh = std::min(std::fabs(tnew), std::fabs(prm.H - tnew));
+    const bool emit = decide_flag(k, w, kKEmit, !(tnew < 0.0 || tnew > prm.H), dv, kTrEmit, mh < prm.flag_tol);
+    if (!emit) return pr;
+    rec[0] |= kTrEmit;
+    int c;
+    const bool ok = check_edge_follow(k, w, qn, tn, pr.x.data(), tnew, M, dv, 3, kKExtCount, kTrExtHit, kKExtHit, &c);
+    rec[3] = c;
+    if (!ok) rec[0] |= kTrExtHit;
     R.ext_checked++;
     pr.ok = ok;
     return pr;
 }
 
 Proposal Planner::propose_recycling(int k, int w, const std::vector<int>& seg_n, int fwd_n,
-                                    const std::vector<int>& active_slots, Margin& M) {
+                                    const std::vector<int>& active_slots, Margin& M, int* rec) {
     Proposal pr;
     int dd = d();
+    const int* dv = F.at(k, w);
     pr.forward = ((w + k) % 2) == 0;
+    pr.forward = decide_flag(k, w, kKDirection, pr.forward, dv, kTrFwd, false);
+    rec[0] |= pr.forward ? kTrFwd : 0;
     // Reading (round-robin): the backward worker with ordinal floor(w/2) in this
     // iteration takes active slot number ordinal mod (#active), in slot order.
     if (!pr.forward) {
-        if (active_slots.empty()) return pr;
-        pr.seg = active_slots[(w / 2) % active_slots.size()];
+        const int slot = active_slots.empty() ? -1 : active_slots[(w / 2) % active_slots.size()];
+        pr.seg = decide(k, w, kKGroup, slot, dv, dv ? dv[1] : 0, false);
+        rec[1] = pr.seg;
+        if (pr.seg < 0 || pr.seg >= prm.N) return pr;
     }
+    rec[0] |= kTrSampled;
     Draws dr;
     dr.fill(prm.seed, prm.problem_id, (uint32_t)k, (uint32_t)w, learned.on ? 17 : 4 + dd);
     std::vector<double> qr(dd);
     for (int j = 0; j < dd; ++j) qr[j] = P.qlo[j] + dr.u(4 + j) * (P.qhi[j] - P.qlo[j]);
-    if (learned.on && (dr.raw[12] >> 8) < kThrLearned) learned_q(learned, dr, P.qlo, P.qhi, dd, qr.data());
+    if (learned.on && (dr.raw[12] >> 8) < kThrLearned) {
+        rec[0] |= kTrLearned;
+        learned_q(learned, dr, P.qlo, P.qhi, dd, qr.data());
+    }
     const std::vector<Node>& A = pr.forward ? R.fwd : R.seg[pr.seg];
     int n = pr.forward ? fwd_n : seg_n[pr.seg];
     double D;
-    int i = nn_config(A, n, qr.data(), dd, &D, M);
+    Margin Mw;
+    int i = nn_config(A, n, qr.data(), dd, &D, Mw);
+    note(M.nn, Mw.nn);
+    i = decide(k, w, kKParent, i, dv, dv ? dv[2] : 0, Mw.nn < prm.flag_tol);
+    rec[2] = i;
+    if (i < 0 || i >= n) return pr;
+    D = dist(A[i].q.data(), qr.data(), dd);
     note(M.bounds, D);
-    if (i < 0 || !(D > 0.0)) return pr;
     pr.parent = i;
     const double* qn = A[i].q.data();
     double tn = A[i].t;
     // Max-speed extension (Eq. max-speed-extension), configuration step capped at eta.
-    double s = std::min(1.0, prm.eta / D);
+    double s = D > 0.0 ? std::min(1.0, prm.eta / D) : 0.0;
     pr.x.assign(dd + 1, 0.0);
     for (int j = 0; j < dd; ++j) pr.x[j] = qn[j] + s * (qr[j] - qn[j]);
     double Dn = dist(qn, pr.x.data(), dd);
@@ -980,9 +1241,15 @@ Proposal Planner::propose_recycling(int k, int w, const std::vector<int>& seg_n,
     pr.x[dd] = tnew;
     note(M.bounds, tnew);
     note(M.bounds, prm.H - tnew);
-    if (tnew < 0.0 || tnew > prm.H) return pr;
-    bool ok;
-    check_edge(qn, tn, pr.x.data(), tnew, &ok, M);
+    const double mh = std::min(std::min(std::fabs(tnew), std::fabs(prm.H - tnew)), D);
+    const bool emit = decide_flag(k, w, kKEmit, D > 0.0 && !(tnew < 0.0 || tnew > prm.H), dv, kTrEmit,
+                                  mh < prm.flag_tol);
+    if (!emit) return pr;
+    rec[0] |= kTrEmit;
+    int c;
+    const bool ok = check_edge_follow(k, w, qn, tn, pr.x.data(), tnew, M, dv, 3, kKExtCount, kTrExtHit, kKExtHit, &c);
+    rec[3] = c;
+    if (!ok) rec[0] |= kTrExtHit;
     R.ext_checked++;
     pr.ok = ok;
     return pr;
@@ -1009,6 +1276,9 @@ void Planner::extract_path() {
 Result Planner::run() {
     int dd = d();
     if (prm.proposal) build_learned(learned, prm.proposal, P.qlo, P.qhi, P.qs, P.qg, dd, prm.H);
+    F.rec = prm.follow_rec;
+    F.iters = prm.follow_rec ? prm.follow_iters : 0;
+    F.W = prm.W;
     R.dof = dd;
     R.N = prm.N;
     R.variant = prm.variant;
@@ -1044,6 +1314,14 @@ Result Planner::run() {
     }
 
     build_goal_grid(P, prm.H, prm.dt, grid);
+    if (prm.follow_grid) {
+        // Goal checks: adopt the device's verdict inside the clearance band.
+        for (size_t i = 0; i < grid.free.size(); ++i) {
+            const int dev = (int)i < prm.follow_nk ? (prm.follow_grid[i] ? 1 : 0) : 0;
+            const bool flagged = std::fabs(grid.clearance[i]) < prm.flag_clear;
+            grid.free[i] = (char)decide(-1, (int)i, kKGrid, grid.free[i] ? 1 : 0, prm.follow_grid, dev, flagged);
+        }
+    }
     R.goal_clearance = grid.clearance;
     R.goal_kmin = grid.kmin;
     kend = grid.kmin;
@@ -1061,6 +1339,7 @@ Result Planner::run() {
         init_recycling();
     }
 
+    const double nan = std::nan("");
     for (int k = 0; k < prm.max_iters; ++k) {
         if (prm.variant == 0 && !(grid.Lg < std::min(prm.H, R.U))) break;
         Margin M;
@@ -1077,12 +1356,23 @@ Result Planner::run() {
             for (int i = 0; i < prm.N; ++i)
                 if (R.slots[i].active) active_slots.push_back(i);
         }
+        const size_t rec0 = R.trace.size();
+        R.trace.resize(rec0 + (size_t)prm.W * kTraceInts, 0);
+        R.trace_d.resize(R.trace_d.size() + (size_t)prm.W * 4, nan);
+        int* recs = &R.trace[rec0];
+        double* rds = &R.trace_d[R.trace_d.size() - (size_t)prm.W * 4];
+        for (int w = 0; w < prm.W; ++w) {
+            int* r = recs + (size_t)w * kTraceInts;
+            r[1] = r[2] = r[4] = r[5] = r[7] = r[8] = -1;
+        }
 
         // 1. Every worker proposes against the start-of-iteration state.
         std::vector<Proposal> props(prm.W);
         for (int w = 0; w < prm.W; ++w) {
-            props[w] = (prm.variant == 0) ? propose_interval(k, w, seg_n, fwd_n, U0, group_active, M)
-                                          : propose_recycling(k, w, seg_n, fwd_n, active_slots, M);
+            int* r = recs + (size_t)w * kTraceInts;
+            props[w] = (prm.variant == 0)
+                           ? propose_interval(k, w, seg_n, fwd_n, U0, group_active, M, r, rds + (size_t)w * 4)
+                           : propose_recycling(k, w, seg_n, fwd_n, active_slots, M, r);
         }
 
         // 2. Ordered insertion (worker order).
@@ -1100,6 +1390,8 @@ Result Planner::run() {
             nd.q.assign(pr.x.begin(), pr.x.begin() + dd);
             nd.t = pr.x[dd];
             nd.iter = k;
+            int* r = recs + (size_t)w * kTraceInts;
+            r[0] |= kTrInserted;
             if (pr.forward) {
                 const Node& par = R.fwd[pr.parent];
                 nd.parent = pr.parent;
@@ -1133,74 +1425,39 @@ Result Planner::run() {
                 A.push_back(nd);
                 ins.push_back({w, false, pr.seg, (int)A.size() - 1});
             }
+            r[7] = ins.back().idx;
             R.inserted++;
         }
 
         // 3. Bridge: the best-ranked admissible vertex of the opposite
-        // start-of-iteration set (arrival time, then space-time distance; tie:
-        // lowest (segment, index)) is validated if it would improve (U0, C0).
+        // start-of-iteration set is validated if it would improve (U0, C0).
+        // 4. Publish: lexicographic min of (U, C, worker).
         int best_w = -1;
         double bestU = kInf, bestC = kInf;
         int best_f = -1, best_s = -1, best_b = -1;
+        struct Success {
+            int w;
+            double U, C;
+            int f, s, b;
+        };
+        std::vector<Success> wins;
+        const double ctol = prm.flag_tol * std::max(1.0, std::fabs(C0) < kInf ? std::fabs(C0) : 1.0);
         for (const Inserted& in : ins) {
+            int* r = recs + (size_t)in.w * kTraceInts;
+            const int* dv = F.at(k, in.w);
             const Node& a = in.forward ? R.fwd[in.idx] : R.seg[in.seg][in.idx];
-            double cU = kInf, cRho = kInf;
-            int cs = -1, ci = -1;
-            double s1U = kInf, s1R = kInf;  // runner-up key for margins
-            auto consider = [&](int s, int i, double Uv, double r) {
-                bool better = (Uv < cU) || (Uv == cU && r < cRho);
-                if (better) {
-                    s1U = cU;
-                    s1R = cRho;
-                    cU = Uv;
-                    cRho = r;
-                    cs = s;
-                    ci = i;
-                } else if ((Uv < s1U) || (Uv == s1U && r < s1R)) {
-                    s1U = Uv;
-                    s1R = r;
-                }
-            };
-            // Candidate v of the opposite start-of-iteration set, seen from a:
-            // forward a -> later backward v; backward a -> earlier forward v.
-            auto scan = [&](bool second_pass) {
-                if (in.forward) {
-                    for (int s = 0; s < prm.N; ++s) {
-                        for (int i = 0; i < seg_n[s]; ++i) {
-                            const Node& v = R.seg[s][i];
-                            if (!(v.troot < U0)) continue;
-                            double r = rho_sigma(a.q.data(), a.t, v.q.data(), v.t, 1, dd, P.vmax);
-                            if (!second_pass) {
-                                if (r < kInf) consider(s, i, v.troot, r);
-                                continue;
-                            }
-                            double Delta = v.t - a.t, D = dist(a.q.data(), v.q.data(), dd);
-                            double madm = std::min(std::fabs(Delta), std::fabs(P.vmax * Delta - D));
-                            double ru = std::sqrt((D * D + P.vmax * P.vmax * Delta * Delta) / 2.0);
-                            if (madm < prm.flag_tol && v.troot <= cU + prm.flag_tol && ru <= cRho + prm.flag_tol)
-                                note(M.rank, madm);
-                        }
-                    }
-                } else {
-                    for (int i = 0; i < fwd_n; ++i) {
-                        const Node& v = R.fwd[i];
-                        double r = rho_sigma(v.q.data(), v.t, a.q.data(), a.t, 1, dd, P.vmax);
-                        if (!second_pass) {
-                            if (r < kInf) consider(-1, i, a.troot, r);
-                            continue;
-                        }
-                        double Delta = a.t - v.t, D = dist(a.q.data(), v.q.data(), dd);
-                        double madm = std::min(std::fabs(Delta), std::fabs(P.vmax * Delta - D));
-                        double ru = std::sqrt((D * D + P.vmax * P.vmax * Delta * Delta) / 2.0);
-                        if (madm < prm.flag_tol && ru <= cRho + prm.flag_tol) note(M.rank, madm);
-                    }
-                }
-            };
-            scan(false);
-            scan(true);
-            if (ci < 0) continue;
-            if (s1U == cU && s1R < kInf) note(M.rank, s1R - cRho);
-            if (s1U != cU && s1U < kInf) note(M.rank, s1U - cU);
+            BridgeCand bc = bridge_rank(a, in.forward, R.seg, seg_n, R.fwd, fwd_n, U0, dd, P.vmax, prm.flag_tol);
+            note(M.rank, bc.margin);
+            const bool rflag = bc.margin < prm.flag_tol;
+            const bool has = decide_flag(k, in.w, kKBrCand, bc.i >= 0, dv, kTrBrCand, rflag);
+            if (!has) continue;
+            int cs = decide(k, in.w, kKBrCand, bc.s, dv, dv ? dv[4] : 0, rflag);
+            int ci = decide(k, in.w, kKBrCand, bc.i, dv, dv ? dv[5] : 0, rflag);
+            if (in.forward ? (cs < 0 || cs >= prm.N || ci < 0 || ci >= seg_n[cs]) : (ci < 0 || ci >= fwd_n))
+                continue;  // an adopted candidate outside the set (already counted as a mismatch)
+            r[0] |= kTrBrCand;
+            r[4] = in.forward ? cs : -1;
+            r[5] = ci;
             const Node& b = in.forward ? R.seg[cs][ci] : R.fwd[ci];
             const Node& fnode = in.forward ? a : b;
             const Node& bnode = in.forward ? b : a;
@@ -1210,25 +1467,60 @@ Result Planner::run() {
             bool improves = (Uc < U0) || (Uc == U0 && Cc < C0);
             if (Uc != U0 && U0 < kInf) note(M.rank, Uc - U0);
             if (Uc == U0) note(M.cost, Cc - C0);
+            const bool iflag = (Uc != U0 && U0 < kInf && std::fabs(Uc - U0) < prm.flag_tol) ||
+                               (Uc == U0 && std::fabs(Cc - C0) < ctol);
+            improves = decide_flag(k, in.w, kKBrEmit, improves, dv, kTrBrEmit, iflag);
             if (!improves) continue;
-            bool ok;
-            check_edge(fnode.q.data(), fnode.t, bnode.q.data(), bnode.t, &ok, M);
+            r[0] |= kTrBrEmit;
+            int c;
+            const bool ok = check_edge_follow(k, in.w, fnode.q.data(), fnode.t, bnode.q.data(), bnode.t, M, dv, 6,
+                                              kKBrCount, kTrBrHit, kKBrHit, &c);
+            r[6] = c;
             R.bridge_checked++;
-            if (!ok) continue;
-            // 4. Publish: lexicographic min of (U, C), tie: lowest worker.
-            bool win = (Uc < bestU) || (Uc == bestU && Cc < bestC);
-            if (best_w >= 0) {
-                if (Uc != bestU) note(M.rank, Uc - bestU);
-                else note(M.cost, Cc - bestC);
+            if (!ok) {
+                r[0] |= kTrBrHit;
+                continue;
             }
-            if (win) {
-                bestU = Uc;
-                bestC = Cc;
-                best_w = in.w;
-                best_f = in.forward ? in.idx : ci;
-                best_s = in.forward ? cs : in.seg;
-                best_b = in.forward ? ci : in.idx;
+            wins.push_back({in.w, Uc, Cc, in.forward ? in.idx : ci, in.forward ? cs : in.seg,
+                            in.forward ? ci : in.idx});
+        }
+        // Publish: lexicographic (U, C, worker) minimum of the successes.
+        int wi = -1;
+        for (int i = 0; i < (int)wins.size(); ++i)
+            if (wi < 0 || publish_before(wins[i].U, wins[i].C, wins[i].w, wins[wi].U, wins[wi].C, wins[wi].w)) wi = i;
+        bool pflag = false;
+        if (wi >= 0) {
+            const double ptol = prm.flag_tol * std::max(1.0, std::fabs(wins[wi].C));
+            for (int i = 0; i < (int)wins.size(); ++i) {
+                if (i == wi) continue;
+                if (wins[i].U != wins[wi].U) {
+                    note(M.rank, wins[i].U - wins[wi].U);
+                    pflag = pflag || std::fabs(wins[i].U - wins[wi].U) < prm.flag_tol;
+                } else {
+                    note(M.cost, wins[i].C - wins[wi].C);
+                    pflag = pflag || std::fabs(wins[i].C - wins[wi].C) < ptol;
+                }
             }
+        }
+        if (F.rec && k < F.iters) {
+            int dev_w = -1;
+            for (int w = 0; w < prm.W; ++w)
+                if (F.at(k, w)[0] & kTrWinner) dev_w = w;
+            const int mine_w = wi >= 0 ? wins[wi].w : -1;
+            const int chosen = decide(k, mine_w >= 0 ? mine_w : dev_w, kKWinner, mine_w, F.rec, dev_w, pflag);
+            wi = -1;
+            for (int i = 0; i < (int)wins.size(); ++i)
+                if (wins[i].w == chosen) wi = i;
+        }
+        if (wi >= 0) {
+            const Success& s = wins[wi];
+            recs[(size_t)s.w * kTraceInts] |= kTrWinner;
+            best_w = s.w;
+            bestU = s.U;
+            bestC = s.C;
+            best_f = s.f;
+            best_s = s.s;
+            best_b = s.b;
         }
         R.iters = k + 1;
         bool decreased = false;
@@ -1255,6 +1547,7 @@ Result Planner::run() {
             }
         }
         R.U_hist.push_back(R.U);
+        R.C_hist.push_back(R.C);
         R.margin_hist.push_back(M.min_all());
         double mt[6] = {M.nn, M.count, M.interval, M.bounds, M.rank, M.clearance};
         R.margin_types.insert(R.margin_types.end(), mt, mt + 6);
@@ -1303,6 +1596,10 @@ typedef struct {
     const double* proposal;
     double t_offset;          /* absolute time of local time 0 */
     int continuous;           /* 1: closed-form edge validation (point robots) */
+    const int* follow_rec;    /* follow mode: device decision records [iters][W][10], or NULL */
+    int follow_iters;
+    const unsigned char* follow_grid;  /* device goal-grid free flags, or NULL */
+    int follow_nk;
 } orc_params;
 
 static Problem to_problem(const orc_problem* p) {
@@ -1539,6 +1836,10 @@ int orc_plan(const orc_problem* prob, const orc_params* p, orc_result** out) {
         if (P.arm) return -1;
         prm.continuous = 1;
     }
+    prm.follow_rec = p->follow_rec;
+    prm.follow_iters = p->follow_iters;
+    prm.follow_grid = p->follow_grid;
+    prm.follow_nk = p->follow_nk;
     Planner pl(P, prm);
     orc_result* r = new orc_result;
     r->R = pl.run();
@@ -1645,6 +1946,114 @@ void orc_result_incumbent(const orc_result* r, int* f, int* s, int* b) {
     *f = r->R.inc_fwd;
     *s = r->R.inc_seg;
     *b = r->R.inc_bwd;
+}
+
+// Per-iteration incumbent length C (after the iteration's publish).
+void orc_result_C_history(const orc_result* r, double* C) {
+    std::memcpy(C, r->R.C_hist.data(), r->R.C_hist.size() * sizeof(double));
+}
+
+// Decision records [iters][W][10] and (T, t_r, window lo, window hi) [iters][W][4].
+void orc_result_trace(const orc_result* r, int* rec, double* d) {
+    if (rec) std::memcpy(rec, r->R.trace.data(), r->R.trace.size() * sizeof(int));
+    if (d) std::memcpy(d, r->R.trace_d.data(), r->R.trace_d.size() * sizeof(double));
+}
+
+// Follow mode: per decision kind the adopted and differing counts
+// [kinds], and the number of unflagged mismatches; unflagged [n][3] =
+// (iteration, worker, kind) (iteration -1: goal-grid entry `worker`).
+int orc_result_follow(const orc_result* r, long long* followed, long long* flagged_diff, int* unflagged, int cap) {
+    for (int i = 0; i < kKinds; ++i) {
+        if (followed) followed[i] = r->R.followed[i];
+        if (flagged_diff) flagged_diff[i] = r->R.flagged_diff[i];
+    }
+    const int n = (int)(r->R.unflagged.size() / 3);
+    if (unflagged)
+        for (int i = 0; i < 3 * std::min(n, cap); ++i) unflagged[i] = r->R.unflagged[i];
+    return n;
+}
+
+int orc_follow_kinds(void) { return kKinds; }
+
+// Configuration-distance NN (root recycling) over explicit configurations
+// x [n][d]; tie: lowest index. Returns the index (-1 if n == 0) and D.
+int orc_nn_config(int n, int d, const double* x, const double* qr, double* D) {
+    std::vector<Node> A(n);
+    for (int i = 0; i < n; ++i) A[i].q.assign(x + (size_t)i * d, x + (size_t)i * d + d);
+    Margin M;
+    return nn_config(A, n, qr, d, D, M);
+}
+
+// Publish reduction over n successful bridges (U, C, worker): index of the
+// lexicographic minimum (-1 if n == 0).
+int orc_publish_winner(int n, const double* U, const double* C, const int* w) {
+    int b = -1;
+    for (int i = 0; i < n; ++i)
+        if (b < 0 || publish_before(U[i], C[i], w[i], U[b], C[b], w[b])) b = i;
+    return b;
+}
+
+// One bridge step of an inserted node a = (q_a, t_a) with root time troot_a
+// and cost cost_a: rank the candidates, test the top one for improving
+// (U0, C0) and validate only that one. forward: a is a forward node and the
+// candidates are backward nodes of groups seg[i] (non-decreasing); else the
+// candidates are forward nodes. Candidate rows x [n][d+1] (q, t), root times,
+// costs. out[0..3] = (candidate group or -1, index within its group, improves,
+// edges validated); out_d[0..1] = (U, C) of the candidate. Returns 1 if the
+// bridge is collision-free and improves, else 0.
+int orc_bridge(const orc_problem* prob, const double* qa, double ta, double troot_a, double cost_a, int forward,
+               int n, const double* x, const double* troot, const double* cost, const int* seg, double U0,
+               double C0, double res, int* out, double* out_d) {
+    Problem P = to_problem(prob);
+    const int d = P.dof;
+    Node a;
+    a.q.assign(qa, qa + d);
+    a.t = ta;
+    a.troot = troot_a;
+    a.cost = cost_a;
+    std::vector<std::vector<Node>> segs;
+    std::vector<int> seg_n;
+    std::vector<Node> fwd;
+    std::vector<int> local(n, 0);
+    for (int i = 0; i < n; ++i) {
+        Node v;
+        v.q.assign(x + (size_t)i * (d + 1), x + (size_t)i * (d + 1) + d);
+        v.t = x[(size_t)i * (d + 1) + d];
+        v.troot = troot[i];
+        v.cost = cost[i];
+        if (forward) {
+            const int s = seg[i];
+            if (s < 0) return -1;
+            if ((int)segs.size() <= s) segs.resize(s + 1);
+            local[i] = (int)segs[s].size();
+            segs[s].push_back(v);
+        } else {
+            fwd.push_back(v);
+        }
+    }
+    for (const auto& sg : segs) seg_n.push_back((int)sg.size());
+    BridgeCand c = bridge_rank(a, forward != 0, segs, seg_n, fwd, (int)fwd.size(), U0, d, P.vmax, 1e-5);
+    out[0] = c.s;
+    out[1] = c.i;
+    out[2] = 0;
+    out[3] = 0;
+    out_d[0] = out_d[1] = kInf;
+    if (c.i < 0) return 0;
+    const Node& b = forward ? segs[c.s][c.i] : fwd[c.i];
+    const Node& fn = forward ? a : b;
+    const Node& bn = forward ? b : a;
+    const double Uc = bn.troot;
+    const double Cc = fn.cost + dist(fn.q.data(), bn.q.data(), d) + bn.cost;
+    out_d[0] = Uc;
+    out_d[1] = Cc;
+    const bool improves = (Uc < U0) || (Uc == U0 && Cc < C0);
+    out[2] = improves ? 1 : 0;
+    if (!improves) return 0;
+    double clr;
+    int cnt;
+    const bool ok = edge_free(P, fn.q.data(), fn.t, bn.q.data(), bn.t, res, &clr, &cnt, nullptr);
+    out[3] = 1;
+    return ok ? 1 : 0;
 }
 
 void orc_result_free(orc_result* r) { delete r; }
