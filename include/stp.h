@@ -163,6 +163,10 @@ typedef struct {
     double plan_ms;               /* device time of the whole plan */
     double U;
     double C;
+    long long nn_evals;           /* NN scan: (query, vertex) key evaluations (Eq. space-time-metric) */
+    long long nn_nodes;           /* NN scan: vertices of the scanned sets, once per set and iteration */
+    long long bridge_evals;       /* bridge scan: (query, vertex) rank evaluations */
+    long long bridge_nodes;       /* bridge scan: vertices of the scanned sets, once per set and iteration */
 } stp_stats;
 
 /* Create a problem: validates and copies robot, obstacles, start, goal and
@@ -219,6 +223,54 @@ stp_status stp_set_profiling(stp_problem *p, int on);
 /* Per-kernel totals of the last profiled stp_plan: for k < *n (at most cap):
  * names[k] (static strings), ms[k] total device time, launches[k]. */
 stp_status stp_profile(stp_problem *p, int cap, const char **names, double *ms, long long *launches, int *n);
+
+/* Decision trace of stp_plan (and of a batch created afterwards), for parity
+ * tests and debugging: with max_iters > 0 every planned iteration k <
+ * max_iters (clamped to the problem's max_iters) writes one record of
+ * STP_TRACE_INTS ints per worker w at records[(k * W + w) * STP_TRACE_INTS]
+ * describing that worker's decisions in the batch-synchronous iteration
+ * (Algorithms 1-3):
+ *   [0] flags: STP_TR_FWD forward worker ((w + k) even); STP_TR_SAMPLED
+ *       interval root: the query-time window of Eq. conditional-query-time is
+ *       non-empty, root recycling: the worker has a source tree;
+ *       STP_TR_VIRTUAL the source is a new root (Algorithm 2); STP_TR_EMIT the
+ *       extension edge was steered inside [0, H] and sent to validation;
+ *       STP_TR_ROOT_HIT / STP_TR_EXT_HIT the sampled goal root / the extension
+ *       collides (only meaningful with STP_TR_EMIT); STP_TR_INSERTED;
+ *       STP_TR_BR_CAND an admissible bridge candidate exists; STP_TR_BR_EMIT it
+ *       improves (U, C) and was validated; STP_TR_BR_HIT it collides;
+ *       STP_TR_WINNER this worker's bridge was published; STP_TR_LEARNED the
+ *       learned branch drew this worker; STP_TR_LEARNED_T its goal time came
+ *       from the mixture; STP_TR_GUIDED interval root: the goal time came from
+ *       the group's guided pieces (Sec. "Interval Root").
+ *   [1] interval group, or recycling slot of a backward worker, else -1;
+ *   [2] NN parent index (-1: virtual root or none); [3] extension check count;
+ *   [4] bridge candidate arena (-1 forward tree, else backward group / slot);
+ *   [5] candidate index in it; [6] bridge check count; [7] index of the
+ *   inserted node (-1); [8] learned mixture component (-1); [9] interval root:
+ *   the sampled goal time T as IEEE float bits, else 0.
+ * max_iters = 0 turns the trace off. The buffer ([max_iters][W][10] ints) is
+ * allocated here (cudaMalloc) and freed by stp_free; the next stp_plan
+ * recaptures its graph. Errors: STP_ERR_INVALID, STP_ERR_CUDA. */
+#define STP_TRACE_INTS 10
+#define STP_TR_FWD 1
+#define STP_TR_SAMPLED 2
+#define STP_TR_VIRTUAL 4
+#define STP_TR_EMIT 8
+#define STP_TR_ROOT_HIT 16
+#define STP_TR_EXT_HIT 32
+#define STP_TR_INSERTED 64
+#define STP_TR_BR_CAND 128
+#define STP_TR_BR_EMIT 256
+#define STP_TR_BR_HIT 512
+#define STP_TR_WINNER 1024
+#define STP_TR_LEARNED 2048
+#define STP_TR_LEARNED_T 4096
+#define STP_TR_GUIDED 8192
+stp_status stp_set_trace(stp_problem *p, int max_iters);
+/* Records of the last plan: *n_iters = iterations recorded; records may be
+ * NULL (count only), else needs cap_iters >= *n_iters (STP_ERR_CAPACITY). */
+stp_status stp_trace(stp_problem *p, int *records, int cap_iters, int *n_iters);
 
 /* Edge validation that allocates nothing, for callers that cannot allocate
  * device memory while they run: for example a control loop that must not

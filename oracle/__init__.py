@@ -106,13 +106,13 @@ def lib():
 # device library's trace: see TRACE_FIELDS / TRACE_FLAGS.
 TRACE_INTS = 10
 TRACE_FIELDS = ("flags", "group", "parent", "ext_count", "br_set", "br_idx", "br_count", "inserted",
-                "component", "reserved")
+                "component", "T_bits")
 TRACE_FLAGS = {"fwd": 1, "sampled": 2, "virtual": 4, "emit": 8, "root_hit": 16, "ext_hit": 32,
                "inserted": 64, "br_cand": 128, "br_emit": 256, "br_hit": 512, "winner": 1024,
-               "learned": 2048, "learned_T": 4096}
+               "learned": 2048, "learned_T": 4096, "guided": 8192}
 FOLLOW_KINDS = ("direction", "group", "learned_component", "learned_T", "root", "window", "virtual",
                 "parent", "emit", "ext_count", "ext_hit", "inserted", "br_cand", "br_emit", "br_count",
-                "br_hit", "winner", "grid")
+                "br_hit", "winner", "grid", "guided", "goal_time")
 
 
 class _ProblemHandle:

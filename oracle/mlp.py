@@ -232,3 +232,32 @@ def path_targets(path: np.ndarray, U: float, H: float, dof: int, lo, hi) -> np.n
         out[o + WP_DIM - 1] = ti / H
     out[-1] = dof
     return out
+
+
+
+# Element-wise tolerance of the tensor-core path (bfloat16 operands, FP32
+# accumulation) against forward/backward(..., bf16=True), which round the same
+# operands: the two differ by FP32 accumulation order and by activations whose
+# FP32 values straddle a bfloat16 rounding boundary (one bfloat16 ulp, at most
+# 2^-7 relative). An element passes when
+#   |got - ref| <= RTOL * |ref| + RTOL * rms(ref over its slice),
+# RTOL = 2 ulps forward (2^-6), 4 ulps backward (2^-5: the backward pass adds
+# a rounding of every output gradient). The slice RMS term covers elements
+# near zero, where a relative bound is meaningless.
+RTOL_FWD = 2.0 ** -6
+RTOL_BWD = 2.0 ** -5
+# Output slices checked separately: mixture logits, means, log-sds, waypoints, padding.
+OUT_SLICES = (("logits", 0, 8), ("means", 8, 16), ("log_sd", 16, 24), ("waypoints", 24, OUT_USED),
+              ("padding", OUT_USED, OUT))
+
+
+def close_elementwise(got: np.ndarray, ref: np.ndarray, rtol: float):
+    """(all within tolerance, worst |got - ref| / tolerance) for one slice."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    if ref.size == 0:
+        return True, 0.0
+    scale = float(np.sqrt(np.mean(ref * ref)))
+    tol = rtol * np.abs(ref) + rtol * scale + 1e-30
+    worst = float(np.max(np.abs(got - ref) / tol))
+    return worst <= 1.0, worst

@@ -488,8 +488,11 @@ void partition(IntervalAlloc& A, double U) {
 
 // Group i samples T from its guided portions with probability p_guided (falling
 // back to the uniform interval when they are empty), else from I_i.
+// walk_margin (optional): the smallest |p - len| met while walking the
+// pieces (where a rounding of p would move T across a gap between pieces).
 double sample_goal_time(const IntervalAlloc& A, int g, double u_coin, double u_pos, double p_guided,
-                        bool* guided) {
+                        bool* guided, double* walk_margin = nullptr) {
+    if (walk_margin) *walk_margin = kInf;
     if (u_coin < p_guided && A.group_measure[g] > 0.0) {
         *guided = true;
         double p = u_pos * A.group_measure[g];
@@ -497,6 +500,7 @@ double sample_goal_time(const IntervalAlloc& A, int g, double u_coin, double u_p
         for (size_t j = 0; j < idx.size(); ++j) {
             const Piece& pc = A.pieces[idx[j]];
             double len = pc.hi - pc.lo;
+            if (walk_margin && j + 1 < idx.size()) *walk_margin = std::min(*walk_margin, std::fabs(p - len));
             if (p < len || j + 1 == idx.size()) return std::min(pc.lo + p, pc.hi);
             p -= len;
         }
@@ -693,7 +697,8 @@ struct Params {
 //   [2] NN parent index (-1: virtual root or none), [3] extension check count
 //   (0: no edge), [4] bridge candidate arena (-1 forward tree, else backward
 //   group / slot), [5] bridge candidate index (-1), [6] bridge check count,
-//   [7] inserted node index (-1), [8] learned mixture component (-1), [9] 0.
+//   [7] inserted node index (-1), [8] learned mixture component (-1),
+//   [9] the goal time T as float bits (interval root; 0 otherwise).
 constexpr int kTraceInts = 10;
 enum TraceFlag {
     kTrFwd = 1,          // forward worker: (w + k) even
@@ -709,11 +714,13 @@ enum TraceFlag {
     kTrWinner = 1024,    // this worker's bridge is the iteration's published solution
     kTrLearned = 2048,   // learned worker (slot-12 coin)
     kTrLearnedT = 4096,  // goal time taken from the mixture
+    kTrGuided = 8192,    // goal time drawn from the group's guided pieces
 };
 // Decision kinds counted in follow mode.
 enum Kind {
     kKDirection, kKGroup, kKLearnedComp, kKLearnedT, kKRoot, kKWindow, kKVirtual, kKParent, kKEmit,
-    kKExtCount, kKExtHit, kKInserted, kKBrCand, kKBrEmit, kKBrCount, kKBrHit, kKWinner, kKGrid, kKinds
+    kKExtCount, kKExtHit, kKInserted, kKBrCand, kKBrEmit, kKBrCount, kKBrHit, kKWinner, kKGrid, kKGuided,
+    kKGoalTime, kKinds
 };
 
 // Smallest decision margins seen during one iteration (test diagnostics for
@@ -770,6 +777,17 @@ double rho_sigma(const double* q, double t, const double* qr, double tr, int sig
     double Delta = (double)sigma * (tr - t);
     double D = dist(q, qr, d);
     if (!(Delta > 0.0) || !(D <= v * Delta)) return kInf;
+    return std::sqrt((D * D + v * v * (tr - t) * (tr - t)) / 2.0);
+}
+
+// rho of an NN choice: the metric's value, or, for a vertex that a
+// reduced-precision run found admissible while this FP64 run puts it just
+// outside the speed cone (a flagged decision adopted in follow mode), the
+// same formula without the cut, as that run steers with it.
+double rho_sigma_adopted(const double* q, double t, const double* qr, double tr, int sigma, int d, double v) {
+    const double r = rho_sigma(q, t, qr, tr, sigma, d, v);
+    if (r < kInf) return r;
+    const double D = dist(q, qr, d);
     return std::sqrt((D * D + v * v * (tr - t) * (tr - t)) / 2.0);
 }
 
@@ -1067,7 +1085,20 @@ Proposal Planner::propose_interval(int k, int w, const std::vector<int>& seg_n, 
     rec[0] |= (pr.forward ? kTrFwd : 0) | (lrn ? kTrLearned : 0);
     rec[1] = g;
     bool guided;
-    double T = sample_goal_time(alloc, g, dr.u(1), dr.u(2), prm.p_guided, &guided);
+    double walk;
+    double T = sample_goal_time(alloc, g, dr.u(1), dr.u(2), prm.p_guided, &guided, &walk);
+    // The guided measure below U-bar changes discontinuously where a guided
+    // window starts or ends at U-bar, and the piece walk jumps gaps: margins
+    // of the goal-time draw (a reduced-precision U moves U-bar slightly).
+    double tmargin = walk;
+    if (dr.u(1) < prm.p_guided) {
+        tmargin = std::min(tmargin, alloc.group_measure[g]);
+        for (const auto& wdw : alloc.windows)
+            tmargin = std::min(tmargin, std::min(std::fabs(wdw.first - alloc.Ubar), std::fabs(wdw.second - alloc.Ubar)));
+    }
+    const bool tflag = tmargin < prm.flag_tol;
+    guided = decide_flag(k, w, kKGuided, guided, dv, kTrGuided, tflag);
+    if (guided) rec[0] |= kTrGuided;
     if (lrn) {
         double cm;
         double Tl = learned_T(learned, dr, &cm);
@@ -1093,8 +1124,30 @@ Proposal Planner::propose_interval(int k, int w, const std::vector<int>& seg_n, 
             rec[0] |= kTrLearnedT;
         }
     }
+    if (dv) {
+        // The goal time itself (as stored by the device, float): beyond the
+        // rounding of a float time it must agree unless its draw was flagged.
+        float tf;
+        std::memcpy(&tf, &dv[9], sizeof(tf));
+        const double Td = (double)tf;
+        if (std::fabs(Td - T) > 4e-7 * std::max(1.0, std::fabs(T)) + prm.flag_tol * 1e-2) {
+            if (tflag) {
+                R.followed[kKGoalTime]++;
+                R.flagged_diff[kKGoalTime]++;
+            } else {
+                R.unflagged.push_back(k);
+                R.unflagged.push_back(w);
+                R.unflagged.push_back(kKGoalTime);
+            }
+            T = Td;
+        }
+    }
     pr.T = T;
     rd[0] = T;
+    {
+        const float tf = (float)T;
+        std::memcpy(&rec[9], &tf, sizeof(tf));
+    }
     // Each proposed root is collision-checked at its sampled time; a rejected
     // root skips the attempt (Algorithm 2).
     {
@@ -1102,7 +1155,10 @@ Proposal Planner::propose_interval(int k, int w, const std::vector<int>& seg_n, 
         const bool free = state_free(P, P.qg.data(), T, &cl);
         R.root_checked++;
         note(M.clearance, cl);
-        const bool hit = decide_flag(k, w, kKRoot, !free, dv, kTrRootHit, std::fabs(cl) < prm.flag_clear);
+        // The device checks the root together with the extension edge, so its
+        // verdict exists only for workers that emitted one.
+        const int* dvr = (dv && (dv[0] & kTrEmit)) ? dv : nullptr;
+        const bool hit = decide_flag(k, w, kKRoot, !free, dvr, kTrRootHit, std::fabs(cl) < prm.flag_clear);
         if (hit) {
             rec[0] |= kTrRootHit;
             return pr;
@@ -1135,7 +1191,7 @@ Proposal Planner::propose_interval(int k, int w, const std::vector<int>& seg_n, 
         rec[2] = i;
         if (i < 0) return pr;
         if (i >= fwd_n) return pr;  // an adopted index outside the set (already counted as a mismatch)
-        rho = rho_sigma(R.fwd[i].q.data(), R.fwd[i].t, qr.data(), tr, 1, dd, P.vmax);
+        rho = rho_sigma_adopted(R.fwd[i].q.data(), R.fwd[i].t, qr.data(), tr, 1, dd, P.vmax);
         pr.parent = i;
         qn = R.fwd[i].q.data();
         tn = R.fwd[i].t;
@@ -1166,7 +1222,7 @@ Proposal Planner::propose_interval(int k, int w, const std::vector<int>& seg_n, 
             i = decide(k, w, kKParent, i, dv, dv ? dv[2] : 0, Mw.nn < prm.flag_tol);
             rec[2] = i;
             if (i < 0 || i >= seg_n[g]) return pr;
-            rho = rho_sigma(R.seg[g][i].q.data(), R.seg[g][i].t, qr.data(), tr, -1, dd, P.vmax);
+            rho = rho_sigma_adopted(R.seg[g][i].q.data(), R.seg[g][i].t, qr.data(), tr, -1, dd, P.vmax);
             pr.parent = i;
             qn = R.seg[g][i].q.data();
             tn = R.seg[g][i].t;

@@ -187,6 +187,10 @@ struct stp_problem {
     bool planned = false;
     bool has_proposal = false;  // learned branch table set by stp_set_proposal
     std::vector<int> self_pairs;  // self-collision pairs a * 64 + b (device sphere order)
+    // decision trace (stp_set_trace): [trace_iters][W][kTraceInts]
+    int* d_trace = nullptr;
+    int trace_iters = 0;
+    int* graph_trace = nullptr;  // trace pointer the captured graph was built with
     // profiling
     int profiling = 0;
     std::vector<cudaEvent_t> prof_ev;
@@ -618,7 +622,9 @@ stp_status capture_graph(stp_problem* p) {
     const int G = p->prm.iters_per_graph > 0 ? p->prm.iters_per_graph : 8;
     const bool prof = p->profiling != 0;
     const bool have_prof = !p->prof_ev.empty();
-    if (p->graph && p->graph_stream == p->stream && p->graph_iters == G && prof == have_prof) return STP_OK;
+    if (p->graph && p->graph_stream == p->stream && p->graph_iters == G && prof == have_prof &&
+        p->graph_trace == state_of<R>(p).trace)
+        return STP_OK;
     if (p->graph) {
         cudaGraphExecDestroy(p->graph);
         p->graph = nullptr;
@@ -643,6 +649,7 @@ stp_status capture_graph(stp_problem* p) {
     if (err != cudaSuccess) return cuda_fail(p, err, "cudaGraphInstantiate");
     p->graph_iters = G;
     p->graph_stream = p->stream;
+    p->graph_trace = state_of<R>(p).trace;
     return STP_OK;
 }
 
@@ -652,6 +659,9 @@ stp_status plan_impl(stp_problem* p, Ctl* hc) {
     stp_status s = capture_graph<R>(p);
     if (s != STP_OK) return s;
     const int G = p->graph_iters;
+    if (p->d_trace)
+        STP_CUDA(p, cudaMemsetAsync(p->d_trace, 0xff,
+                                    sizeof(int) * (size_t)p->trace_iters * p->prm.ext_per_iter * kTraceInts, st));
     STP_CUDA(p, cudaMemsetAsync(state_of<R>(p).tile_cnt, 0,
                                 sizeof(int) * (size_t)(p->prm.n_roots + 1) * kMaxQTiles, st));
     STP_CUDA(p, cudaMemsetAsync(state_of<R>(p).btile_cnt, 0, sizeof(int) * 2 * kMaxQTiles, st));
@@ -1007,6 +1017,10 @@ stp_status stp_plan(stp_problem* p, double* arrival_U, double* length_C, int* n_
         st.root_checks = (long long)hc.st_root;
         st.check_points = (long long)hc.st_points;
         st.pair_tests = (long long)hc.st_pairs;
+        st.nn_evals = (long long)hc.st_nn_evals;
+        st.nn_nodes = (long long)hc.st_nn_nodes;
+        st.bridge_evals = (long long)hc.st_br_evals;
+        st.bridge_nodes = (long long)hc.st_br_nodes;
         st.first_solution_ms = hc.first_iter >= 0 ? (double)(hc.t_first - hc.t_start) * 1e-6 : -1.0;
         st.U = hc.U;
         st.C = hc.C;
@@ -1077,7 +1091,44 @@ void stp_free(stp_problem* p) {
     cache_stream_release(p->own_stream);
     cache_release(p->d_counters, p->counters_block);
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
+    if (p->d_trace) cudaFree(p->d_trace);
     delete p;
+}
+
+stp_status stp_set_trace(stp_problem* p, int max_iters) {
+    clear_stale_error();
+    if (!p || max_iters < 0) return STP_ERR_INVALID;
+    if (p->stream) STP_CUDA(p, cudaStreamSynchronize(p->stream));
+    if (p->d_trace) {
+        STP_CUDA(p, cudaFree(p->d_trace));
+        p->d_trace = nullptr;
+    }
+    p->trace_iters = std::min(max_iters, std::max(p->prm.max_iters, 1));
+    if (p->trace_iters > 0) {
+        const size_t bytes = sizeof(int) * (size_t)p->trace_iters * p->prm.ext_per_iter * kTraceInts;
+        STP_CUDA(p, cudaMalloc(&p->d_trace, bytes));
+        STP_CUDA(p, cudaMemset(p->d_trace, 0xff, bytes));
+    }
+    p->sf.trace = p->sd.trace = p->d_trace;
+    p->sf.trace_iters = p->sd.trace_iters = p->d_trace ? p->trace_iters : 0;
+    return STP_OK;
+}
+
+stp_status stp_trace(stp_problem* p, int* records, int cap_iters, int* n_iters) {
+    clear_stale_error();
+    if (!p || !n_iters || cap_iters < 0) return STP_ERR_INVALID;
+    *n_iters = 0;
+    if (!p->d_trace || !p->planned) return STP_OK;
+    Ctl hc;
+    STP_CUDA(p, cudaStreamSynchronize(p->stream));
+    STP_CUDA(p, cudaMemcpy(&hc, p->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    const int n = std::min(hc.iter, p->trace_iters);
+    *n_iters = n;
+    if (!records) return STP_OK;
+    if (cap_iters < n) return STP_ERR_CAPACITY;
+    STP_CUDA(p, cudaMemcpy(records, p->d_trace, sizeof(int) * (size_t)n * p->prm.ext_per_iter * kTraceInts,
+                           cudaMemcpyDeviceToHost));
+    return STP_OK;
 }
 
 stp_status stp_last_validate(stp_problem* p, double* ms, long long* points, long long* pairs) {
@@ -1307,6 +1358,7 @@ extern "C" stp_status stp_check_edges_noalloc(stp_problem* p, int n_edges, const
 // ---------------------------------------------------------------------------
 struct stp_batch {
     std::vector<stp_problem*> probs;
+    std::vector<int*> traces;  // each member's trace buffer when the batch was created
     std::vector<int> trivial;  // 0 plan, 1 blocked start, 2 start == goal
     Geom<float>* d_geom = nullptr;
     State<float>* d_state = nullptr;
@@ -1455,6 +1507,7 @@ extern "C" stp_status stp_batch_create(stp_problem* const* problems, int n, cons
         b->trivial[i] = !p->start_free ? 1 : (same ? 2 : 0);
         hg[i] = p->gf;
         hs[i] = p->sf;
+        b->traces.push_back(p->sf.trace);
         iters[i] = b->trivial[i] ? 0 : p->prm.max_iters;
         b->max_iters = std::max(b->max_iters, iters[i]);
         sh.max_W = std::max(sh.max_W, p->prm.ext_per_iter);
@@ -1501,6 +1554,8 @@ extern "C" stp_status stp_batch_create(stp_problem* const* problems, int n, cons
     return STP_OK;
 }
 
+static bool hs_trace_matches(const stp_batch* b, int i) { return b->traces[i] == b->probs[i]->d_trace; }
+
 extern "C" stp_status stp_batch_plan(stp_batch* b, stp_stats* stats, double* batch_ms) {
     clear_stale_error();
     if (!b) return STP_ERR_INVALID;
@@ -1524,6 +1579,10 @@ extern "C" stp_status stp_batch_plan(stp_batch* b, stp_stats* stats, double* bat
         stp_problem* p = b->probs[i];
         e = cudaMemsetAsync(p->sf.tile_cnt, 0, sizeof(int) * (size_t)(p->prm.n_roots + 1) * kMaxQTiles, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(p->sf.btile_cnt, 0, sizeof(int) * 2 * kMaxQTiles, st);
+        // A member's trace is the one it had when the batch was created.
+        if (e == cudaSuccess && p->d_trace && hs_trace_matches(b, i))
+            e = cudaMemsetAsync(p->d_trace, 0xff,
+                                sizeof(int) * (size_t)p->trace_iters * p->prm.ext_per_iter * kTraceInts, st);
     }
     if (e != cudaSuccess) return fail(e, "memset");
     if ((e = cudaEventRecord(b->ev0, st)) != cudaSuccess) return fail(e, "cudaEventRecord");
@@ -1566,6 +1625,10 @@ extern "C" stp_status stp_batch_plan(stp_batch* b, stp_stats* stats, double* bat
             s.root_checks = (long long)hc.st_root;
             s.check_points = (long long)hc.st_points;
             s.pair_tests = (long long)hc.st_pairs;
+            s.nn_evals = (long long)hc.st_nn_evals;
+            s.nn_nodes = (long long)hc.st_nn_nodes;
+            s.bridge_evals = (long long)hc.st_br_evals;
+            s.bridge_nodes = (long long)hc.st_br_nodes;
             s.first_solution_ms = hc.first_iter >= 0 ? (double)(hc.t_first - hc.t_start) * 1e-6 : -1.0;
             s.plan_ms = hc.t_end > hc.t_start ? (double)(hc.t_end - hc.t_start) * 1e-6 : ms;
             s.U = hc.U;

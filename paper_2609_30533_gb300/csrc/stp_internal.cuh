@@ -114,6 +114,8 @@ struct Ctl {
     int pad4, pad5, pad6, pad7;
     // statistics
     unsigned long long st_ext, st_bridge, st_root, st_ins, st_points, st_pairs;
+    // scan work: (query, node) key evaluations and nodes read once per set
+    unsigned long long st_nn_evals, st_nn_nodes, st_br_evals, st_br_nodes;
     unsigned long long t_start, t_first, t_end;
 };
 
@@ -168,7 +170,29 @@ struct State {
     double* U_hist;
     // path
     R* path; int path_cap; int* path_len;
+    // Decision trace (optional, parity tests): [trace_iters][W][kTraceInts]
+    // records written by the iteration's kernels, or nullptr.
+    int* trace; int trace_iters;
 };
+
+// Decision record of one worker in one iteration (fields and flags as in
+// include/stp.h, stp_set_trace).
+constexpr int kTraceInts = 10;
+enum TraceFlag {
+    kTrFwd = 1, kTrSampled = 2, kTrVirtual = 4, kTrEmit = 8, kTrRootHit = 16, kTrExtHit = 32,
+    kTrInserted = 64, kTrBrCand = 128, kTrBrEmit = 256, kTrBrHit = 512, kTrWinner = 1024,
+    kTrLearned = 2048, kTrLearnedT = 4096, kTrGuided = 8192
+};
+enum TraceField {
+    kTfFlags = 0, kTfGroup = 1, kTfParent = 2, kTfExtCount = 3, kTfBrSet = 4, kTfBrIdx = 5, kTfBrCount = 6,
+    kTfInserted = 7, kTfComponent = 8, kTfGoalTime = 9
+};
+// Record of worker w at iteration k, or nullptr when not traced.
+template <typename R>
+__device__ __forceinline__ int* trace_rec(const State<R>& S, int k, int w) {
+    if (S.trace == nullptr || k < 0 || k >= S.trace_iters) return nullptr;
+    return S.trace + ((size_t)k * S.W + w) * kTraceInts;
+}
 
 // ---------------------------------------------------------------------------
 // Small helpers.

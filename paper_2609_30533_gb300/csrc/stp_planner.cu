@@ -189,10 +189,11 @@ __device__ void partition(const State<R>& S, double U) {
 // guided coin is the integer test m_coin < ceil(p_guided 2^24), equivalent to
 // u_coin < p_guided for u = m 2^-24.
 template <typename R>
-__device__ R sample_goal_time(const State<R>& S, int g, uint32_t m_coin, R u_pos) {
+__device__ R sample_goal_time(const State<R>& S, int g, uint32_t m_coin, R u_pos, bool& guided) {
     const Ctl* c = S.ctl;
     const R meas = (R)c->g_meas[g];
-    if (m_coin < S.thr_guided && meas > R(0)) {
+    guided = m_coin < S.thr_guided && meas > R(0);
+    if (guided) {
         R p = u_pos * meas;
         const int f = c->g_first[g], n = c->g_count[g];
         for (int j = 0; j < n; ++j) {
@@ -239,10 +240,11 @@ __device__ __forceinline__ float exp_r(float x) { return expf(x); }
 __device__ __forceinline__ double exp_r(double x) { return exp(x); }
 
 template <typename R>
-__device__ __forceinline__ R learned_T(const State<R>& S, const uint32_t (&d)[20]) {
+__device__ __forceinline__ R learned_T(const State<R>& S, const uint32_t (&d)[20], int& comp) {
     const R u = uni_r<R>(d[14]);
     int k = 0;
     while (k < 7 && !(u < S.prop[k])) ++k;
+    comp = k;
     const R u1 = R(1) - uni_r<R>(d[15]), u2 = uni_r<R>(d[16]);
     const R z = sqrt(R(-2) * log_r(u1)) * cos_r(R(6.283185307179586476925) * u2);
     return S.prop[8 + k] + S.prop[16 + k] * z;
@@ -429,6 +431,7 @@ __device__ __forceinline__ void reset_body(const State<R>& S, int max_iters) {
         c->first_iter = -1;
         c->max_iters = max_iters;
         c->st_ext = c->st_bridge = c->st_root = c->st_ins = c->st_points = c->st_pairs = 0;
+        c->st_nn_evals = c->st_nn_nodes = c->st_br_evals = c->st_br_nodes = 0;
         c->t_start = global_ns();
         c->t_first = 0;
         c->t_end = 0;
@@ -637,16 +640,25 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
     for (int j = 0; j < kMaxDof; ++j) row[j] = qr[j];
     row[kDP - 1] = R(0);
 
+    int tflags = (fwd ? kTrFwd : 0) | (lrn ? kTrLearned : 0), tgroup = -1, tcomp = -1;
+    float tT = 0.f;
     if (S.variant == 0) {
         const int g = (int)(((unsigned long long)(d[0] >> 8) * (unsigned long long)S.N) >> 24);
-        R Tr = sample_goal_time(S, g, d[1] >> 8, uni_r<R>(d[2]));
+        tgroup = g;
+        bool guided;
+        R Tr = sample_goal_time(S, g, d[1] >> 8, uni_r<R>(d[2]), guided);
+        if (guided) tflags |= kTrGuided;
         if (lrn) {
-            const R Tl = learned_T(S, d);
+            const R Tl = learned_T(S, d, tcomp);
             const R width = (R)c->width;
             const R glo = (R)c->Lg + (R)g * width;
-            if (Tl >= glo && Tl < glo + width) Tr = Tl;
+            if (Tl >= glo && Tl < glo + width) {
+                Tr = Tl;
+                tflags |= kTrLearnedT;
+            }
         }
         S.w_T[w] = Tr;
+        tT = (float)Tr;
         // Conditional query time (Eq. conditional-query-time).
         const R lo = qdist_rows(S.qs, qr, dof) / G.vmax;
         const R hi = Tr - qdist_rows(qr, S.qg, dof) / G.vmax;
@@ -658,6 +670,7 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
                 if (j == dof) dword = d[4 + j];
             row[kDP - 1] = lo + uni_r<R>(dword) * (hi - lo);
             st_row(xr, row);
+            tflags |= kTrSampled;
             set = fwd ? 0 : 1 + g;
             if (fwd) {
                 status = kNN;
@@ -669,7 +682,9 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
     } else {
         int slot = -1;
         if (!fwd && s_nact > 0) slot = s_act[(w / 2) % s_nact];
+        tgroup = slot;
         if (fwd || slot >= 0) {
+            tflags |= kTrSampled;
             st_row(xr, row);
             set = fwd ? 0 : 1 + slot;
             status = kNN;
@@ -681,7 +696,21 @@ __device__ __forceinline__ void sample_body(const Geom<R>& G, const State<R>& S)
 #pragma unroll
         for (int j = 0; j < kMaxDof; ++j) xn[j] = S.qg[j];
         xn[kDP - 1] = (R)S.w_T[w];
+        tflags |= kTrVirtual;
         if (!steer_and_emit(G, S, w, set, true, xn, row)) status = kSkip;
+        else tflags |= kTrEmit;
+    }
+    if (int* tr = trace_rec(S, k, w)) {
+        tr[kTfFlags] = tflags;
+        tr[kTfGroup] = tgroup;
+        tr[kTfParent] = -1;
+        tr[kTfExtCount] = (tflags & kTrEmit) ? S.ecnt[2 * w + 1] : 0;
+        tr[kTfBrSet] = -1;
+        tr[kTfBrIdx] = -1;
+        tr[kTfBrCount] = 0;
+        tr[kTfInserted] = -1;
+        tr[kTfComponent] = tcomp;
+        tr[kTfGoalTime] = __float_as_int(tT);
     }
     S.w_status[w] = status;
     S.w_set[w] = set;
@@ -826,6 +855,7 @@ __device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S) {
     __shared__ int s_last;
     const int t = threadIdx.x;
     const int nsets = S.N + 1;
+    const int titer = S.trace ? c->iter : -1;
     // One thread per set loads its counts, then the first warp forms the tile
     // prefix in shared memory.
     for (int s = t; s < nsets; s += blockDim.x) {
@@ -930,6 +960,9 @@ __device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S) {
         // fence (cumulative) publishes them before the completion count.
         __syncthreads();
         if (t == 0) {
+            const unsigned long long nq_t = (unsigned long long)min(kQT, ts.nq[s] - qt * kQT);
+            atomicAdd(&S.ctl->st_nn_evals, nq_t * (unsigned long long)(n1 - n0));
+            if (qt == 0) atomicAdd(&S.ctl->st_nn_nodes, (unsigned long long)(n1 - n0));
             __threadfence();
             int old = atomicAdd(&S.tile_cnt[s * kMaxQTiles + qt], 1);
             s_last = (old == nt - 1);
@@ -964,6 +997,13 @@ __device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S) {
                     ok = steer_and_emit(G, S, w, s, false, xn, xq);
                 }
                 if (!ok) S.w_status[w] = kSkip;
+                if (int* tr = trace_rec(S, titer, w)) {
+                    tr[kTfParent] = p;
+                    if (ok) {
+                        tr[kTfFlags] |= kTrEmit;
+                        tr[kTfExtCount] = S.ecnt[2 * w + 1];
+                    }
+                }
             }
             if (t == 0) S.tile_cnt[s * kMaxQTiles + qt] = 0;
         }
@@ -1141,6 +1181,16 @@ __device__ __forceinline__ void insert_body(const Geom<R>& G, const State<R>& S)
             bq_base += tot_q;
         }
         if (ok && !ins) overflow = 1;
+        if (w < S.W) {
+            if (int* tr = trace_rec(S, iter, w)) {
+                int f = 0;
+                if (re >= 0 && h_root) f |= kTrRootHit;
+                if (e >= 0 && h_ext) f |= kTrExtHit;
+                if (ins) f |= kTrInserted;
+                tr[kTfFlags] |= f;
+                tr[kTfInserted] = ins ? (set == 0 ? idx : idx + (virt ? 1 : 0)) : -1;
+            }
+        }
         if (ins) {
             if (set == 0) {
                 st_row(fnode(S, idx), xw);
@@ -1300,6 +1350,7 @@ __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S)
     __shared__ int s_last;
     __shared__ int s_emitted;
     const int t = threadIdx.x;
+    const int titer = S.trace ? c->iter : -1;
     for (int i = t; i < S.N; i += blockDim.x) seg_pre[i] = c->snap_s[i];
     int nq0 = 0, nq1 = 0, nf = 0;
     if (t == 0) {
@@ -1438,6 +1489,9 @@ __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S)
         }
         __syncthreads();
         if (t == 0) {
+            const unsigned long long nq_t = (unsigned long long)min(kQT, s_nq[s] - qt * kQT);
+            atomicAdd(&c->st_br_evals, nq_t * (unsigned long long)(n1 - n0));
+            if (qt == 0) atomicAdd(&c->st_br_nodes, (unsigned long long)(n1 - n0));
             __threadfence();
             int old = atomicAdd(&S.btile_cnt[s * kMaxQTiles + qt], 1);
             s_last = (old == nt - 1);
@@ -1492,6 +1546,12 @@ __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S)
                         S.b_idx[w] = bi - seg_pre[sg];
                     }
                     emitted = bridge_emit(G, S, w, U0r, C0r);
+                    if (int* tr = trace_rec(S, titer, w)) {
+                        tr[kTfFlags] |= kTrBrCand | (emitted ? kTrBrEmit : 0);
+                        tr[kTfBrSet] = S.b_set[w];
+                        tr[kTfBrIdx] = S.b_idx[w];
+                        if (emitted) tr[kTfBrCount] = S.bcnt[w];
+                    }
                 }
             }
             if (emitted) atomicAdd(&s_emitted, 1);
@@ -1531,12 +1591,15 @@ __device__ __forceinline__ void publish_body(const Geom<R>& G, const State<R>& S
     // needs, so the winner needs no further load.
     R bU = rinf<R>(), bC = rinf<R>();
     int bw = 0x7fffffff, bws = 0, bwi = -1, bbs = -1, bbi = -1;
+    const int titer = (S.trace && !done) ? c->iter : -1;
     for (int w = t; w < S.W; w += blockDim.x) {
         // Bridge entry of worker w is entry w; all loads independent.
         const int e = S.w_bedge[w];
         const int h = S.bhit[w];
         const R U = S.b_U[w], C = S.b_C[w];
         const int ws = S.w_set[w], wi = S.w_ins[w], bs = S.b_set[w], bi = S.b_idx[w];
+        if (e >= 0 && h)
+            if (int* tr = trace_rec(S, titer, w)) tr[kTfFlags] |= kTrBrHit;
         if (e < 0 || h) continue;
         if (U < bU || (U == bU && (C < bC || (C == bC && w < bw)))) {
             bU = U;
@@ -1592,6 +1655,7 @@ __device__ __forceinline__ void publish_body(const Geom<R>& G, const State<R>& S
     if (t == 0) {
         s_decreased = 0;
         if (bw != 0x7fffffff) {
+            if (int* tr = trace_rec(S, s_iter, bw)) tr[kTfFlags] |= kTrWinner;
             s_decreased = bU < (R)sU;
             sU = (double)bU;
             sC = (double)bC;

@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libstp.so")
 
 STP_OK, STP_ERR_INVALID, STP_ERR_CAPACITY, STP_ERR_CUDA, STP_ERR_TIMEOUT, STP_NO_SOLUTION = range(6)
+TRACE_INTS = 10
 STP_EDGES_DEVICE = 1
 STP_EDGES_CLEARANCE = 2
 STP_EDGES_NO_EARLY_EXIT = 4
@@ -49,7 +50,8 @@ class StpStats(C.Structure):
                 ("edges_validated", C.c_longlong), ("bridges_validated", C.c_longlong),
                 ("root_checks", C.c_longlong), ("check_points", C.c_longlong), ("pair_tests", C.c_longlong),
                 ("first_solution_ms", C.c_double), ("plan_ms", C.c_double), ("U", C.c_double),
-                ("C", C.c_double)]
+                ("C", C.c_double), ("nn_evals", C.c_longlong), ("nn_nodes", C.c_longlong),
+                ("bridge_evals", C.c_longlong), ("bridge_nodes", C.c_longlong)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -108,6 +110,10 @@ def lib():
     L.stp_batch_path.restype = C.c_int
     L.stp_batch_free.argtypes = [C.c_void_p]
     L.stp_batch_free.restype = None
+    L.stp_set_trace.argtypes = [C.c_void_p, C.c_int]
+    L.stp_set_trace.restype = C.c_int
+    L.stp_trace.argtypes = [C.c_void_p, _I, C.c_int, _I]
+    L.stp_trace.restype = C.c_int
     L.stp_set_profiling.argtypes = [C.c_void_p, C.c_int]
     L.stp_set_profiling.restype = C.c_int
     L.stp_profile.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), _D, C.POINTER(C.c_longlong), _I]
@@ -164,7 +170,7 @@ EXPORTED = ["stp_create_problem", "stp_plan", "stp_check_edges", "stp_free", "st
             "stp_mlp_create", "stp_mlp_free", "stp_mlp_set_stream", "stp_mlp_set_params", "stp_mlp_get_params",
             "stp_mlp_forward", "stp_mlp_gradients", "stp_mlp_train_step", "stp_mlp_set_profiling",
             "stp_mlp_profile", "stp_mlp_last_error", "stp_problem_features", "stp_set_proposal",
-            "stp_problem_targets", "stp_selftest_bounded_wait", "stp_release_cached"]
+            "stp_problem_targets", "stp_selftest_bounded_wait", "stp_release_cached", "stp_set_trace", "stp_trace"]
 
 
 def release_cached() -> None:
@@ -232,6 +238,7 @@ class Problem:
             raise StpError(s, "stp_create_problem", L.stp_last_error(None).decode())
         self.handle = h
         self.n_roots = int(n_roots)
+        self.workers = int(ext_per_iter)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -320,6 +327,25 @@ class Problem:
         if s != STP_OK:
             raise StpError(s, "stp_profile")
         return {names[k].decode(): (float(ms[k]), int(la[k])) for k in range(n.value)}
+
+    def set_trace(self, max_iters: int):
+        """Record per-worker decision records of the next plans (0: off)."""
+        s = lib().stp_set_trace(self.handle, int(max_iters))
+        if s != STP_OK:
+            raise StpError(s, "stp_set_trace", self.last_error())
+
+    def trace(self) -> np.ndarray:
+        """Decision records [iters][W][TRACE_INTS] (int32) of the last plan."""
+        n = C.c_int()
+        s = lib().stp_trace(self.handle, None, 0, C.byref(n))
+        if s != STP_OK:
+            raise StpError(s, "stp_trace", self.last_error())
+        rec = np.zeros((n.value, self.workers, TRACE_INTS), dtype=np.int32)
+        if n.value:
+            s = lib().stp_trace(self.handle, rec.ctypes.data_as(_I), n.value, C.byref(n))
+            if s != STP_OK:
+                raise StpError(s, "stp_trace", self.last_error())
+        return rec
 
     def features(self) -> np.ndarray:
         """Proposal-network input x[32] of this problem."""

@@ -1,7 +1,8 @@
 """Proposal network on the tensor cores against the FP64 oracle network:
-an exact identity network (layout pin), forward and gradients on ragged and
-maximum batch sizes within BF16 tolerances, the first Adam step, and a
-training run that lowers a held-out loss."""
+an exact identity network (layout pin), forward outputs and every parameter
+gradient element by element (each output slice and each tensor on its own)
+within bfloat16 tolerances on ragged and maximum batch sizes, the first Adam
+step, and a training run that lowers a held-out loss."""
 import numpy as np
 import pytest
 
@@ -62,6 +63,16 @@ def _rel_rows(a, b):
     return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-12)
 
 
+def _check_forward(Y, Ye, label):
+    """Element-wise per output slice against the bf16 reference."""
+    worst = {}
+    for name, a, b in M.OUT_SLICES:
+        ok, w = M.close_elementwise(Y[:, a:b], Ye[:, a:b], M.RTOL_FWD)
+        worst[name] = round(w, 4)
+        assert ok, (label, name, w)
+    print(label, "worst |err|/tol per slice:", worst)
+
+
 @pytest.mark.parametrize("B", [1, 128, 300])
 def test_forward_matches_oracle(stp, B):
     rng = np.random.default_rng(10 + B)
@@ -74,8 +85,10 @@ def test_forward_matches_oracle(stp, B):
     net.set_params(stp.flatten_params(P))
     Y = net.forward(X).astype(np.float64)
     Ye, _ = M.forward(P, X, bf16=True)
+    _check_forward(Y, Ye, "B=%d" % B)
+    # Against the unrounded FP64 network: the bfloat16 rounding itself (a few
+    # ulps through four layers), per row.
     Y64, _ = M.forward(P, X, bf16=False)
-    assert np.max(_rel_rows(Y, Ye[:, :160])) < 1e-2
     assert np.max(_rel_rows(Y, Y64[:, :160])) < 3e-2
     net.close()
 
@@ -90,7 +103,7 @@ def test_forward_at_maximum_batch_sampled(stp):
     Y = net.forward(X).astype(np.float64)
     idx = np.r_[0, 1, 127, 128, rng.integers(0, B, size=250), B - 129, B - 1]
     Ye, _ = M.forward(P, X[idx], bf16=True)
-    assert np.max(_rel_rows(Y[idx], Ye[:, :160])) < 1e-2
+    _check_forward(Y[idx], Ye, "B=65536 sampled")
     net.close()
 
 
@@ -106,12 +119,22 @@ def test_gradients_match_oracle(stp, B):
     y, cache = M.forward(P, X, bf16=True)
     Ls, dy = M.loss(y, T)
     G = M.backward(P, cache, dy, bf16=True)
-    assert abs(loss - Ls.mean()) <= 1e-2 * abs(Ls.mean())
+    assert abs(loss - Ls.mean()) <= M.RTOL_FWD * abs(Ls.mean())
     Gg = stp.unflatten_params(g)
+    worst = {}
     for k in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4"):
         ref = G[k][:Gg[k].shape[0]]
-        err = np.linalg.norm(Gg[k] - ref) / max(np.linalg.norm(ref), 1e-12)
-        assert err < 2e-2, (k, err)
+        if k in ("W4", "b4"):
+            # Output rows per slice: mixture logits, means, log-sds, waypoints.
+            for name, a, b in M.OUT_SLICES[:4]:
+                ok, w = M.close_elementwise(Gg[k][a:b], ref[a:b], M.RTOL_BWD)
+                worst[k + "." + name] = round(w, 4)
+                assert ok, (k, name, w)
+        else:
+            ok, w = M.close_elementwise(Gg[k], ref, M.RTOL_BWD)
+            worst[k] = round(w, 4)
+            assert ok, (k, w)
+    print("B=%d worst |err|/tol per gradient:" % B, worst)
     net.close()
 
 
