@@ -50,14 +50,32 @@ import workloads as WL  # noqa: E402
 
 WORKLOAD = "ur5e-6dof-32sph-16obs-recycling-N8-W1024"
 # DRAM bytes per profiled collision interval of the planner on this workload,
-# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum): the
-# extension launch (237.1 KB) and the two bridge passes together (141.6 + 80.6
-# KB), averaged over the two intervals. Must be retaken whenever the
-# collision kernel changes.
-VALIDATE_DRAM_BYTES_PER_LAUNCH = 229.6e3
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; summary
+# in profiles/k_validate_ur5e_plan_ncu.md): the extension launch (237.1 KB) and
+# the two bridge passes together (141.6 + 80.6 KB), averaged over the two
+# intervals. The figure belongs to the kernel source it was taken from: when
+# the source's hash differs, the bench reports no traffic.
+TRAFFIC_CAPTURE = {"kernel": "k_validate", "bytes_per_launch": 229.6e3,
+                   "source": os.path.join("paper_2609_30533_gb300", "csrc", "stp_validate.cu"),
+                   "sha256_16": "2e753c4f50acea8b", "profile": "profiles/k_validate_ur5e_plan_ncu.md"}
 METRIC = "validated space-time edges/s"
 UNIT = "edges/s"
 FLUSH_BYTES = 512 << 20
+
+
+def _capture_traffic():
+    """(bytes per launch or None, note) of the ncu traffic capture, None when
+    the kernel source changed since it was taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, TRAFFIC_CAPTURE["source"]), "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None, "kernel source not found"
+    if h != TRAFFIC_CAPTURE["sha256_16"]:
+        return None, "kernel source changed since the ncu capture (%s)" % TRAFFIC_CAPTURE["profile"]
+    return TRAFFIC_CAPTURE["bytes_per_launch"], "from the ncu capture in %s (same kernel source)" % (
+        TRAFFIC_CAPTURE["profile"])
 
 
 def _peaks():
@@ -313,6 +331,7 @@ def batched(args, rank):
     # As a queue (one after another from a common start), a problem's first
     # solution waits for every earlier problem's whole plan.
     plain_fs, plain_ms, plain_solved, queue_fs = [], [], 0, []
+    plain_each = []   # per problem: first-solution ms from its own start, or None
     elapsed = 0.0
     for i in idx[:args.plain_sample]:
         out = probs[i].plan()
@@ -321,6 +340,9 @@ def batched(args, rank):
             plain_solved += 1
             plain_fs.append(out.stats["first_solution_ms"])
             queue_fs.append(elapsed + out.stats["first_solution_ms"])
+            plain_each.append(out.stats["first_solution_ms"])
+        else:
+            plain_each.append(None)
         elapsed += out.stats["plan_ms"]
     # The same sample planned as one batch (chosen launch shape, same budget):
     # every problem starts at once.
@@ -331,6 +353,11 @@ def batched(args, rank):
     Bq.close()
     q_ms, q_stats = qruns[len(qruns) // 2]
     batch_fs = [st["first_solution_ms"] for st in q_stats if st["first_solution_iter"] >= 0]
+    # Per problem at equal success: the problems solved both alone and in the
+    # batch; alone a problem's first solution counts from its own start, in the
+    # batch from the batch's start (all problems share the GPU).
+    common = [(pe, st["first_solution_ms"]) for pe, st in zip(plain_each, q_stats)
+              if pe is not None and st["first_solution_iter"] >= 0]
     for P in probs:
         P.close()
 
@@ -361,6 +388,14 @@ def batched(args, rank):
                            "batch_total_ms": q_ms,
                            "queue_solved": len(queue_fs), "queue_first_ms_p50": pct(queue_fs, 50),
                            "queue_total_ms": elapsed},
+        "per_problem_vs_plain": {
+            "problems": nq, "solved_alone": plain_solved, "solved_batched": len(batch_fs), "common": len(common),
+            "note": "first-solution ms on the commonly solved problems: alone from each problem's own start, "
+                    "batched from the start of the batch of the same problems",
+            "alone_first_ms_p50": pct([c[0] for c in common], 50),
+            "alone_first_ms_p99": pct([c[0] for c in common], 99),
+            "batched_first_ms_p50": pct([c[1] for c in common], 50),
+            "batched_first_ms_p99": pct([c[1] for c in common], 99)},
         "plain_sample": {"problems": len(plain_ms), "solved": plain_solved,
                          "first_solution_ms_p50": pct(plain_fs, 50), "first_solution_ms_p99": pct(plain_fs, 99),
                          "ms_per_problem_p50": pct(plain_ms, 50), "sequential_ms_per_problem": float(np.mean(plain_ms)),
@@ -386,15 +421,23 @@ def aggregate_over_ranks(edges, total_ms, e2e_edges, e2e_secs, dist=None, device
     return tuple(float(x) for x in vals.cpu())
 
 
-def _equal_success_p50(a, b):
-    """Median first-solution time of each arm over its k fastest solves, with
-    k the smaller of the two arms' solved counts (equal success rate)."""
-    fa = np.sort(a.first_ms[a.solved])
-    fb = np.sort(b.first_ms[b.solved])
-    k = min(len(fa), len(fb))
-    if k == 0:
-        return None, None, 0
-    return float(np.median(fa[:k])), float(np.median(fb[:k])), int(k)
+def _paired(a, b):
+    """Plain arm a against learned arm b on the problems both solved (equal
+    success by construction): counts, first-solution ms p50/p99, first
+    iteration p50 and mean arrival U over the common set, and each arm's
+    own solved count."""
+    both = a.solved & b.solved
+
+    def q(v, p):
+        return float(np.percentile(v, p)) if len(v) else None
+
+    return {"plain_solved": int(a.solved.sum()), "learned_solved": int(b.solved.sum()),
+            "common_solved": int(both.sum()),
+            "plain_first_ms_p50": q(a.first_ms[both], 50), "learned_first_ms_p50": q(b.first_ms[both], 50),
+            "plain_first_ms_p99": q(a.first_ms[both], 99), "learned_first_ms_p99": q(b.first_ms[both], 99),
+            "plain_first_iter_p50": q(a.first_iter[both], 50), "learned_first_iter_p50": q(b.first_iter[both], 50),
+            "plain_mean_arrival": float(np.mean(a.U[both])) if both.any() else None,
+            "learned_mean_arrival": float(np.mean(b.U[both])) if both.any() else None}
 
 
 def sweep(args, rank):
@@ -438,6 +481,94 @@ def sweep(args, rank):
             "range": [pair(H, 16, 512) for H in (25.0, 50.0, 100.0)],
             "roots": [pair(100.0, N, 512) for N in (8, 16, 32, 64, 128)],
             "batch": [pair(100.0, 16, W) for W in (128, 256, 512, 1024, 2048)]}
+
+
+def scan_bytes_per_node(dof):
+    """Algorithmic bytes of one tree vertex read by an NN or bridge scan:
+    coordinates and time padded to 16-byte vectors, plus a flag / root-time word."""
+    return 16 * ((dof + 1 + 3) // 4) + 4
+
+
+def run_config(name, make, n_problems, peak_tflops, hbm_gbs):
+    """Plans n_problems of one configuration one at a time (FP32, one graph per
+    8 iterations, CUDA events around each plan) and then profiles one of them:
+    validated edges/s, first-solution ms p50/p99 and mean arrival over the
+    solved problems, per-kernel shares, and the NN and bridge scans against
+    their FP32 and HBM rooflines (algorithmic flops: (3d + 5) per (query,
+    vertex) evaluation; bytes: every vertex of a scanned set once per iteration)."""
+    from paper_2609_30533_gb300 import stp
+    edges, ms_total, fs, U, solved = 0, 0.0, [], [], 0
+    for i in range(n_problems):
+        prob, prm = make(i)
+        P = stp.problem_from(prob, prm, precision=0)
+        P.plan()
+        out = P.plan()
+        st = out.stats
+        edges += st["edges_validated"] + st["bridges_validated"]
+        ms_total += st["plan_ms"]
+        if st["first_solution_iter"] >= 0:
+            solved += 1
+            fs.append(st["first_solution_ms"])
+            U.append(out.U)
+        P.close()
+    prob, prm = make(0)
+    P = stp.problem_from(prob, prm, precision=0)
+    P.set_profiling(True)
+    out = P.plan()
+    prof = P.profile()
+    P.close()
+    st = out.stats
+    d = prob.dof
+    total = sum(v[0] for v in prof.values()) or 1e-12
+    scans = {}
+    for key, ev, nd in (("k_nn", "nn_evals", "nn_nodes"), ("k_bridge", "bridge_evals", "bridge_nodes")):
+        ms = prof.get(key, (0.0, 0))[0]
+        fl = st[ev] * (3 * d + 5)
+        by = st[nd] * scan_bytes_per_node(d)
+        tf = fl / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+        gb = by / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        scans[key] = {"ms": ms, "evals": st[ev], "nodes": st[nd], "tflops": tf, "fp32_frac": tf / peak_tflops,
+                      "gbs": gb, "hbm_frac": gb / hbm_gbs}
+
+    def pct(v, q):
+        return float(np.percentile(v, q)) if v else None
+
+    return {"workload": name, "problems": n_problems, "solved": solved,
+            "edges_per_s": edges / (ms_total * 1e-3) if ms_total > 0 else None,
+            "plan_ms_mean": ms_total / n_problems,
+            "first_solution_ms_p50": pct(fs, 50), "first_solution_ms_p99": pct(fs, 99),
+            "mean_arrival": float(np.mean(U)) if U else None,
+            "profiled": {"iterations": st["iterations"], "nodes": st["nodes"],
+                         "kernel_share": {k: round(v[0] / total, 4) for k, v in prof.items()},
+                         "scans": scans}}
+
+
+def stated_configs(args, peak_tflops):
+    """The point-robot and 7-DoF configurations at their stated sizes: disc2d
+    (8 discs, interval root with 4 groups, W 64, 2000 iterations) and the
+    7-DoF arm (48 link spheres, 64 obstacles on 8-waypoint paths, H 60 s,
+    W 4096; root recycling with 16 trees and interval root)."""
+    import dataclasses
+    hbm = float(_peaks().get("hbm_gbs", 6685.8))
+
+    def c0(i):
+        prob, prm = WL.disc2d(i)
+        return prob, dataclasses.replace(prm, max_iters=args.c0_iters, problem_id=i)
+
+    def c2(variant):
+        def mk(i):
+            prob, prm = WL.arm7(i, variant=variant)
+            return prob, dataclasses.replace(prm, workers=4096, max_iters=args.c2_iters, problem_id=i)
+        return mk
+
+    return {
+        "c0_disc2d": run_config("disc2d, 8 discs, interval root N 4, W 64, %d iterations" % args.c0_iters, c0,
+                                args.c0_problems, peak_tflops, hbm),
+        "c2_arm7_recycling": run_config("arm7, 48 spheres, 64 obstacles, root recycling N 16, W 4096, %d iterations"
+                                        % args.c2_iters, c2(1), args.c2_problems, peak_tflops, hbm),
+        "c2_arm7_interval": run_config("arm7, 48 spheres, 64 obstacles, interval root N 16, W 4096, %d iterations"
+                                       % args.c2_iters, c2(0), args.c2_problems, peak_tflops, hbm),
+    }
 
 
 def mlp_throughput(rank, B=65536, reps=3):
@@ -538,20 +669,8 @@ def learned(args, rank):
     for variant, name in ((1, "recycling"), (0, "interval")):
         op, _, _ = run_chunks("test", args.learned_test, 0, variant)
         ol, _, _ = run_chunks("test", args.learned_test, 1, variant, net=net)
-        both = op.solved & ol.solved
         solvable[variant] = np.nonzero(op.solved | ol.solved)[0][:args.learned_single]
-        pe, le, k = _equal_success_p50(op, ol)
-        res[name] = {
-            "plain_batched": arm(op), "learned_batched": arm(ol),
-            "equal_success": {"k": k, "plain_p50_first_ms": pe, "learned_p50_first_ms": le},
-            "common_solved": int(both.sum()),
-            "plain_p50_first_ms_common": float(np.median(op.first_ms[both])) if both.any() else None,
-            "learned_p50_first_ms_common": float(np.median(ol.first_ms[both])) if both.any() else None,
-            "plain_p50_first_iter_common": float(np.median(op.first_iter[both])) if both.any() else None,
-            "learned_p50_first_iter_common": float(np.median(ol.first_iter[both])) if both.any() else None,
-            "plain_mean_arrival_common": float(np.mean(op.U[both])) if both.any() else None,
-            "learned_mean_arrival_common": float(np.mean(ol.U[both])) if both.any() else None,
-        }
+        res[name] = {"plain_batched": arm(op), "learned_batched": arm(ol), "paired": _paired(op, ol)}
     # One problem at a time on held-out problems that either batched arm
     # solved (the first --learned-single of them), plain and learned.
     single = {}
@@ -609,9 +728,14 @@ def main():
     ap.add_argument("--learned-single", type=int, default=32)
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--c0-iters", type=int, default=2000)
+    ap.add_argument("--c0-problems", type=int, default=16)
+    ap.add_argument("--c2-iters", type=int, default=48)
+    ap.add_argument("--c2-problems", type=int, default=8)
     ap.add_argument("--sweep-problems", type=int, default=64)
     ap.add_argument("--sweep-iters", type=int, default=64)
-    ap.add_argument("--only", default="", choices=["", "micro", "batch", "learned", "mlp", "sweep"],
+    ap.add_argument("--only", default="", choices=["", "micro", "batch", "learned", "mlp", "sweep", "configs"],
                     help="micro: run only the collision microbenchmark (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -656,6 +780,11 @@ def main():
     if args.only == "sweep":
         print(json.dumps({"sweep": sweep(args, rank)}))
         return
+    if args.only == "configs":
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+        pk = fp32_peak_tflops(n_sm, float(_peaks().get("sm_max_mhz", 2070.0)))
+        print(json.dumps({"configs": stated_configs(args, pk)}))
+        return
 
     def step_timed():
         with torch.cuda.stream(stream):
@@ -668,14 +797,16 @@ def main():
         e1.synchronize()
         return e0.elapsed_time(e1), out
 
+    # Clock samples cover the warm-up, the timed steps, the kernel-timing pass
+    # and the end-to-end pass.
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         step_timed()
 
-    clocks = ClockSampler(local)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
     total_ms = 0.0
     edges = 0
     launches = 0
@@ -693,7 +824,6 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clk = clocks.stop()
 
     # Kernel-timing pass: the same steps with CUDA events between the kernels
     # inside the captured graphs.
@@ -734,11 +864,13 @@ def main():
         Q.close()
     torch.cuda.synchronize()
     e2e_secs = time.perf_counter() - t0
+    clk = clocks.stop()
 
     micro, peak = microbench(args, P, prob, prm, stream, flush, rank, local)
     batch_result = None if args.no_batch else batched(args, rank)
     learned_result = None if args.no_learned else learned(args, rank)
     sweep_result = None if args.no_sweep else sweep(args, rank)
+    configs_result = None if args.no_configs else stated_configs(args, peak)
     n = args.micro_edges
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = float(_peaks().get("sm_max_mhz", 2070.0))
@@ -751,6 +883,7 @@ def main():
         return
 
     value = edges_all / (ms_max * 1e-3)
+    traffic, traffic_note = _capture_traffic()
     kv = prof_tot.get("k_validate(ext)", [0.0, 0])
     kb = prof_tot.get("k_validate(bridge)", [0.0, 0])
     val_ms = kv[0] + kb[0]
@@ -773,7 +906,7 @@ def main():
         "gpu_launches": launches * world,
         "roofline": {"bound": "alu", "kernel": "k_validate", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
-                     "traffic": VALIDATE_DRAM_BYTES_PER_LAUNCH,
+                     "traffic": traffic, "traffic_note": traffic_note,
                      "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz (max SM clock)" % (
                          n_sm, max_mhz),
                      "launches": val_launches, "avg_launch_ms": val_ms / max(val_launches, 1),
@@ -793,6 +926,8 @@ def main():
         line["learned"] = learned_result
     if not args.no_sweep:
         line["sweep"] = sweep_result
+    if not args.no_configs:
+        line["configs"] = configs_result
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line))
