@@ -312,10 +312,11 @@ def batched(args, rank):
 
     sample = list(range(48))
     choice = autotune.autotune(lambda W: make(sample, W, args.tune_iters), workers=(128, 256, 512),
-                               nn_ctas=(2, 4, 8), validate_ctas=(2, 4, 8))
+                               team_ctas=(2, 4, 8, 16), nn_ctas=(2, 4, 8), validate_ctas=(2, 4, 8))
     idx = list(range(args.batch_problems))
     probs = make(idx, choice.workers, args.batch_iters)
-    B = stp.Batch(probs, nn_ctas=choice.nn_ctas, validate_ctas=choice.validate_ctas, iters_per_graph=16)
+    B = stp.Batch(probs, nn_ctas=choice.nn_ctas, validate_ctas=choice.validate_ctas, iters_per_graph=16,
+                  launch_mode=choice.launch_mode, team_ctas=choice.team_ctas)
     B.plan()
     runs = []
     for _ in range(args.batch_reps):
@@ -347,7 +348,8 @@ def batched(args, rank):
     # The same sample planned as one batch (chosen launch shape, same budget):
     # every problem starts at once.
     nq = len(plain_ms)
-    Bq = stp.Batch(probs[:nq], nn_ctas=choice.nn_ctas, validate_ctas=choice.validate_ctas, iters_per_graph=16)
+    Bq = stp.Batch(probs[:nq], nn_ctas=choice.nn_ctas, validate_ctas=choice.validate_ctas, iters_per_graph=16,
+                   launch_mode=choice.launch_mode, team_ctas=choice.team_ctas)
     Bq.plan()
     qruns = sorted((Bq.plan() for _ in range(args.batch_reps)), key=lambda r: r[0])
     Bq.close()
@@ -376,7 +378,8 @@ def batched(args, rank):
         "workload": "mixed 2/6/7-DoF, 4-128 obstacles, 10-60 s horizons",
         "cpu_oracle_all_cores": cpu_all,
         "problems": len(idx), "iters_budget": args.batch_iters,
-        "autotuned": {"workers": choice.workers, "nn_ctas": choice.nn_ctas, "validate_ctas": choice.validate_ctas,
+        "autotuned": {"workers": choice.workers, "launch_mode": choice.launch_mode, "team_ctas": choice.team_ctas,
+                      "nn_ctas": choice.nn_ctas, "validate_ctas": choice.validate_ctas,
                       "trials": [dataclasses.asdict(t) for t in choice.trials]},
         "batch_ms": ms, "problems_per_s": len(idx) / (ms * 1e-3), "edges_per_s": edges / (ms * 1e-3),
         "solved": len(fs), "success_rate": len(fs) / len(idx),
@@ -866,6 +869,28 @@ def main():
     e2e_secs = time.perf_counter() - t0
     clk = clocks.stop()
 
+    # The same plan as one persistent launch (STP_LAUNCH_PERSISTENT), for comparison.
+    Pp = stp.problem_from(prob, prm, precision=0, max_iters=args.iters, launch_mode=stp.STP_LAUNCH_PERSISTENT)
+    Pp.set_stream(stream.cuda_stream)
+    pers_ms = []
+    for k in range(args.warmup + args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Pp.plan()
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            pers_ms.append(e0.elapsed_time(e1))
+    pers_prof = Pp.profile()
+    Pp.close()
+    persistent_single = {"ms_per_step": statistics.median(pers_ms),
+                         "step_us_per_iteration": {k: v[0] * 1e3 / max(v[1], 1) for k, v in pers_prof.items()},
+                         "note": "the timed plan as one persistent cooperative launch (steps separated by "
+                                 "device-wide barriers); step times barrier to barrier on the device timer"}
+
     micro, peak = microbench(args, P, prob, prm, stream, flush, rank, local)
     batch_result = None if args.no_batch else batched(args, rank)
     learned_result = None if args.no_learned else learned(args, rank)
@@ -917,6 +942,7 @@ def main():
         "plan_ms_p50": statistics.median(plan_ms),
         "first_solution_ms_p50": statistics.median(fs_ms) if fs_ms else None,
         "microbench": dict(micro, n_edges=n, peak_tflops=peak),
+        "persistent_single": persistent_single,
     }
     if clk:
         line["clocks"] = clk

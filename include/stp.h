@@ -123,7 +123,20 @@ typedef struct {
  *   self_collision 0 off; 1 (arms only) also test the robot's own spheres with
  *                  the same predicate: pairs on frames at least two apart,
  *                  except pairs that already overlap at q = 0 (treated as
- *                  permanent contacts). Not in the paper's queries. */
+ *                  permanent contacts). Not in the paper's queries.
+ *   launch_mode    STP_LAUNCH_DEFAULT (0) = STP_LAUNCH_STEPS (1): one kernel
+ *                  per step of the iteration, iterations captured into CUDA
+ *                  graphs (iters_per_graph per graph); STP_LAUNCH_PERSISTENT
+ *                  (2): the whole plan (every step of every iteration) in one
+ *                  persistent, cooperative kernel launch whose steps are
+ *                  separated by device-wide barriers (each wait bounded by 1 s).
+ *                  Both run the same step code and take the same decisions.
+ *                  Closed-form validation (continuous = 1) always uses steps.
+ *   persist_ctas   CTAs of the persistent launch; 0 = every resident CTA
+ *                  (SMs x CTAs per SM). */
+#define STP_LAUNCH_DEFAULT 0
+#define STP_LAUNCH_STEPS 1
+#define STP_LAUNCH_PERSISTENT 2
 typedef struct {
     int variant;
     int n_roots;
@@ -145,6 +158,8 @@ typedef struct {
     double t_offset;
     int continuous;
     int self_collision;
+    int launch_mode;
+    int persist_ctas;
 } stp_params;
 
 /* Per-call statistics filled by stp_plan. Times are GPU times (CUDA events /
@@ -296,25 +311,34 @@ stp_status stp_trace(stp_problem *p, int *records, int cap_iters, int *n_iters);
 stp_status stp_check_edges_noalloc(stp_problem *p, int n_edges, const void *qa, const void *ta, const void *qb,
                                    const void *tb, unsigned char *verdict);
 
-/* ---- Batched planning (many problems in one launch sequence) -------------
- * A batch runs several FP32 problems' planner iterations together: every
- * kernel of an iteration covers all problems (one CUDA grid dimension per
- * problem), and the iterations are captured into one CUDA graph. Problems keep
- * their own parameters (variant, N, W, budget, ...) and arenas; they must stay
- * alive while the batch exists. Problems whose start is in collision, or whose
- * start equals the goal, are resolved without iterations as in stp_plan. */
+/* ---- Batched planning (many problems in one launch) -----------------------
+ * A batch plans several FP32 problems together. STP_LAUNCH_DEFAULT (0) =
+ * STP_LAUNCH_PERSISTENT (2): one persistent, cooperative kernel, captured in a
+ * CUDA graph, whose CTAs form teams of team_ctas CTAs; each team takes the
+ * next problem from a device work queue and plans it to the end (all
+ * iterations, steps separated by team barriers), then takes the next.
+ * STP_LAUNCH_STEPS (1): every kernel of an iteration covers all problems (one
+ * CUDA grid dimension per problem) and iterations are captured into one CUDA
+ * graph. Problems keep their own parameters (variant, N, W, budget, ...) and
+ * arenas; they must stay alive while the batch exists. Problems whose start is
+ * in collision, or whose start equals the goal, are resolved without
+ * iterations as in stp_plan. */
 typedef struct stp_batch stp_batch;
 typedef struct {
-    int nn_ctas;          /* CTAs per problem for the NN and bridge scans; 0 = 8 */
-    int validate_ctas;    /* CTAs per problem for the collision kernel; 0 = 2 */
-    int iters_per_graph;  /* iterations per graph launch; 0 = 16 */
+    int nn_ctas;          /* steps: CTAs per problem for the NN and bridge scans; 0 = 8 */
+    int validate_ctas;    /* steps: CTAs per problem for the collision kernel; 0 = 2 */
+    int iters_per_graph;  /* steps: iterations per graph launch; 0 = 16 */
+    int launch_mode;      /* STP_LAUNCH_DEFAULT / _PERSISTENT: work queue; STP_LAUNCH_STEPS: one kernel per step */
+    int team_ctas;        /* persistent: CTAs per team (problems in flight = resident CTAs / team_ctas); 0 = 8 */
 } stp_batch_params;
 /* problems [n], n >= 1, all created with precision 0; params may be NULL. */
 stp_status stp_batch_create(stp_problem *const *problems, int n, const stp_batch_params *params,
                             stp_batch **out);
 /* Plan every problem from a fresh state. stats [n] (or NULL) receives each
  * problem's statistics (first_solution_ms is measured from the start of the
- * batch); *batch_ms the device time of the whole batch. Returns STP_OK unless
+ * batch, so it includes the time a problem waited in the queue; plan_ms is
+ * the problem's own plan from its start); *batch_ms the device time of the
+ * whole batch. Returns STP_OK unless
  * a CUDA call failed or a problem overflowed (STP_ERR_CAPACITY). */
 stp_status stp_batch_plan(stp_batch *b, stp_stats *stats, double *batch_ms);
 /* Path of problem i after stp_batch_plan: [cap][dof+1]; *n_path = states. */

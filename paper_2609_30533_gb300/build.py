@@ -14,8 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libstp.so")
-SOURCES = ["stp_validate.cu", "stp_planner.cu", "stp_api.cu", "stp_mlp.cu"]
-HEADERS = ["stp_internal.cuh"]
+SOURCES = ["stp_validate.cu", "stp_planner.cu", "stp_persist.cu", "stp_api.cu", "stp_mlp.cu"]
+HEADERS = ["stp_internal.cuh", "stp_planner_body.cuh", "stp_validate_body.cuh", "stp_persist.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -18,6 +18,7 @@
 
 #include "stp.h"
 #include "stp_internal.cuh"
+#include "stp_persist.cuh"
 
 using namespace stp;
 
@@ -187,6 +188,14 @@ struct stp_problem {
     bool planned = false;
     bool has_proposal = false;  // learned branch table set by stp_set_proposal
     std::vector<int> self_pairs;  // self-collision pairs a * 64 + b (device sphere order)
+    // persistent launch: device copies of the problem's Geom / State (refreshed
+    // before each launch), its iteration budget and the launch scratch
+    void* d_pgeom = nullptr;
+    void* d_pstate = nullptr;
+    int* d_pmax_iters = nullptr;
+    PersistScratch pscratch{};
+    size_t pscratch_bytes = 0;
+    int persist_grid = 0, persist_smem = 0, persist_dq = 0;
     // decision trace (stp_set_trace): [trace_iters][W][kTraceInts]
     int* d_trace = nullptr;
     int trace_iters = 0;
@@ -477,6 +486,21 @@ size_t layout_state(stp_problem* p, char* base, R** blob_out, size_t blob_bytes,
     s.prop = cv.take<R>(kPropSize);
     s.prop_y = cv.take<float>(kPropY);
     s.tgt = cv.take<float>(STP_MLP_NTGT + 1);
+    // persistent launch (one team)
+    void* pg = cv.take<Geom<R>>(1);
+    void* ps = cv.take<State<R>>(1);
+    int* pmi = cv.take<int>(1);
+    char* pscr = cv.take<char>(persist_scratch_bytes(1));
+    if (base) {
+        p->d_pgeom = pg;
+        p->d_pstate = ps;
+        p->d_pmax_iters = pmi;
+        p->pscratch_bytes = persist_scratch_bytes(1);
+        p->pscratch.sync = reinterpret_cast<unsigned*>(pscr);
+        p->pscratch.queue = reinterpret_cast<int*>(pscr + sizeof(unsigned) * kPersistSyncStride);
+        p->pscratch.team_prob = p->pscratch.queue + 1;
+        p->pscratch.abort_flag = p->pscratch.queue + 2;
+    }
     if (base) {
         s.N = N;
         s.W = W;
@@ -504,6 +528,12 @@ size_t layout_state(stp_problem* p, char* base, R** blob_out, size_t blob_bytes,
         state_of<R>(p) = s;
     }
     return cv.off;
+}
+
+// Plans of this problem run as one persistent launch (STP_LAUNCH_PERSISTENT),
+// except with closed-form validation, which only the per-step kernels implement.
+bool uses_persistent(const stp_problem* p) {
+    return p->prm.launch_mode == STP_LAUNCH_PERSISTENT && !p->prm.continuous;
 }
 
 template <typename R>
@@ -559,6 +589,7 @@ stp_status create_impl(stp_problem* p) {
     hc.kmin = p->kmin;
     hc.kend = p->kend;
     hc.nk = p->nk;
+    hc.budget_ns = p->prm.budget_ms > 0 ? (unsigned long long)(p->prm.budget_ms * 1e6) : 0ull;
     hc.done = 1;
     STP_CUDA(p, cudaMemcpyAsync(ctl, &hc, sizeof(Ctl), cudaMemcpyHostToDevice, st));
 
@@ -610,6 +641,20 @@ stp_status create_impl(stp_problem* p) {
     E0.n_host = 0;
     STP_CUDA(p, launch_validate<R>(geom_of<R>(p), E0, false, true, 0, st));
     STP_CUDA(p, cudaStreamSynchronize(st));
+    if (uses_persistent(p)) {
+        // One team of every resident CTA (or persist_ctas of them).
+        p->persist_dq = persist_dq(p->dof);
+        p->persist_smem = persist_smem_bytes((int)blob_bytes, p->prm.ext_per_iter);
+        int per_sm = 0;
+        STP_CUDA(p, persist_blocks_per_sm<R>(p->persist_dq, p->persist_smem, &per_sm));
+        if (per_sm < 1) {
+            p->last_error = "persistent planner kernel does not fit on an SM";
+            g_last_error = p->last_error;
+            return STP_ERR_CAPACITY;
+        }
+        const int resident = validate_grid_blocks() * per_sm;
+        p->persist_grid = p->prm.persist_ctas > 0 ? std::min(p->prm.persist_ctas, resident) : resident;
+    }
     return STP_OK;
 }
 
@@ -654,7 +699,49 @@ stp_status capture_graph(stp_problem* p) {
 }
 
 template <typename R>
+stp_status plan_persistent_impl(stp_problem* p, Ctl* hc) {
+    cudaStream_t st = p->stream;
+    State<R>& S = state_of<R>(p);
+    const int mi = p->prm.max_iters;
+    STP_CUDA(p, cudaMemcpyAsync(p->d_pgeom, &geom_of<R>(p), sizeof(Geom<R>), cudaMemcpyHostToDevice, st));
+    STP_CUDA(p, cudaMemcpyAsync(p->d_pstate, &S, sizeof(State<R>), cudaMemcpyHostToDevice, st));
+    STP_CUDA(p, cudaMemcpyAsync(p->d_pmax_iters, &mi, sizeof(int), cudaMemcpyHostToDevice, st));
+    STP_CUDA(p, cudaMemsetAsync(p->pscratch.sync, 0, p->pscratch_bytes, st));
+    if (p->d_trace)
+        STP_CUDA(p, cudaMemsetAsync(p->d_trace, 0xff,
+                                    sizeof(int) * (size_t)p->trace_iters * p->prm.ext_per_iter * kTraceInts, st));
+    STP_CUDA(p, cudaMemsetAsync(S.tile_cnt, 0, sizeof(int) * (size_t)(p->prm.n_roots + 1) * kMaxQTiles, st));
+    STP_CUDA(p, cudaMemsetAsync(S.btile_cnt, 0, sizeof(int) * 2 * kMaxQTiles, st));
+    PersistArgs<R> a{};
+    a.Gs = static_cast<const Geom<R>*>(p->d_pgeom);
+    a.Ss = static_cast<const State<R>*>(p->d_pstate);
+    a.max_iters = p->d_pmax_iters;
+    a.P = 1;
+    a.team_size = p->persist_grid;
+    a.sync = p->pscratch.sync;
+    a.queue = p->pscratch.queue;
+    a.team_prob = p->pscratch.team_prob;
+    a.abort_flag = p->pscratch.abort_flag;
+    STP_CUDA(p, cudaEventRecord(p->ev0, st));
+    STP_CUDA(p, launch_plan_persistent<R>(a, p->persist_dq, p->persist_grid, p->persist_smem, st));
+    STP_CUDA(p, cudaEventRecord(p->ev1, st));
+    STP_CUDA(p, cudaMemcpyAsync(hc, p->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    STP_CUDA(p, cudaStreamSynchronize(st));
+    // Step times (device global timer, barrier to barrier), in the order of
+    // the per-step kernels' profile; the two bridge passes count together.
+    static const int kMap[8] = {0, 1, 2, 3, 4, 5, 5, 6};
+    for (int k = 0; k < kIterKernels; ++k) {
+        p->prof_ms[k] = 0.0;
+        p->prof_launches[k] = 0;
+    }
+    for (int ph = 0; ph < 8; ++ph) p->prof_ms[kMap[ph]] += (double)hc->ph_ns[ph] * 1e-6;
+    for (int k = 0; k < kIterKernels; ++k) p->prof_launches[k] = hc->iter;
+    return STP_OK;
+}
+
+template <typename R>
 stp_status plan_impl(stp_problem* p, Ctl* hc) {
+    if (uses_persistent(p)) return plan_persistent_impl<R>(p, hc);
     cudaStream_t st = p->stream;
     stp_status s = capture_graph<R>(p);
     if (s != STP_OK) return s;
@@ -856,6 +943,8 @@ stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, 
     if (!(P.p_new >= 0 && P.p_new <= 1) || !(P.p_guided >= 0 && P.p_guided <= 1)) return STP_ERR_INVALID;
     if (P.precision != 0 && P.precision != 1) return STP_ERR_INVALID;
     if ((P.learned != 0 && P.learned != 1) || P.capacity < 0 || P.iters_per_graph < 0) return STP_ERR_INVALID;
+    if (P.launch_mode < STP_LAUNCH_DEFAULT || P.launch_mode > STP_LAUNCH_PERSISTENT || P.persist_ctas < 0)
+        return STP_ERR_INVALID;
     if (!(P.t_offset >= 0) || !std::isfinite(P.t_offset)) return STP_ERR_INVALID;
     if (P.continuous != 0 && (P.continuous != 1 || robot->arm)) return STP_ERR_INVALID;
     if (P.self_collision != 0 && (P.self_collision != 1 || !robot->arm)) return STP_ERR_INVALID;
@@ -1357,6 +1446,13 @@ extern "C" stp_status stp_check_edges_noalloc(stp_problem* p, int n_edges, const
 // Batched planning.
 // ---------------------------------------------------------------------------
 struct stp_batch {
+    int launch_mode = 0;          // 0 persistent work queue, 1 one kernel per step
+    int team_ctas = 8;
+    int persist_grid = 0, persist_smem = 0;
+    PersistScratch scratch{};
+    void* d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    bool graph_direct = false;    // the cooperative launch could not be captured: launch it directly
     std::vector<stp_problem*> probs;
     std::vector<int*> traces;  // each member's trace buffer when the batch was created
     std::vector<int> trivial;  // 0 plan, 1 blocked start, 2 start == goal
@@ -1480,6 +1576,20 @@ extern "C" stp_status stp_selftest_bounded_wait(unsigned long long limit_ns, int
     return h[0] ? STP_ERR_TIMEOUT : STP_OK;
 }
 
+static PersistArgs<float> batch_args(const stp_batch* b) {
+    PersistArgs<float> a{};
+    a.Gs = b->d_geom;
+    a.Ss = b->d_state;
+    a.max_iters = b->d_iters;
+    a.P = (int)b->probs.size();
+    a.team_size = b->team_ctas;
+    a.sync = b->scratch.sync;
+    a.queue = b->scratch.queue;
+    a.team_prob = b->scratch.team_prob;
+    a.abort_flag = b->scratch.abort_flag;
+    return a;
+}
+
 extern "C" stp_status stp_batch_create(stp_problem* const* problems, int n, const stp_batch_params* bp,
                                        stp_batch** out) {
     clear_stale_error();
@@ -1491,6 +1601,13 @@ extern "C" stp_status stp_batch_create(stp_problem* const* problems, int n, cons
     if (!b) return STP_ERR_CUDA;
     b->probs.assign(problems, problems + n);
     b->iters_per_graph = bp && bp->iters_per_graph > 0 ? bp->iters_per_graph : 16;
+    const int mode = bp ? bp->launch_mode : STP_LAUNCH_DEFAULT;
+    if (mode < STP_LAUNCH_DEFAULT || mode > STP_LAUNCH_PERSISTENT || (bp && bp->team_ctas < 0)) {
+        delete b;
+        return STP_ERR_INVALID;
+    }
+    b->launch_mode = mode == STP_LAUNCH_STEPS ? 1 : 0;   // 0: persistent work queue, 1: per-step kernels
+    b->team_ctas = bp && bp->team_ctas > 0 ? bp->team_ctas : 8;
     BatchShape& sh = b->shape;
     sh.P = n;
     sh.nn_ctas = bp && bp->nn_ctas > 0 ? bp->nn_ctas : 8;
@@ -1524,6 +1641,62 @@ extern "C" stp_status stp_batch_create(stp_problem* const* problems, int n, cons
     if (e == cudaSuccess) e = cudaMemcpy(b->d_iters, iters.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    if (e == cudaSuccess && b->launch_mode == 0) {
+        // Persistent work queue: teams of team_ctas resident CTAs.
+        b->persist_smem = persist_smem_bytes(max_blob, sh.max_W);
+        int per_sm = 0;
+        e = persist_blocks_per_sm<float>(7, b->persist_smem, &per_sm);
+        if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+        if (e == cudaSuccess) {
+            const int resident = validate_grid_blocks() * per_sm;
+            b->team_ctas = std::min(b->team_ctas, resident);
+            const int teams = std::max(1, std::min(resident / b->team_ctas, n));
+            b->persist_grid = teams * b->team_ctas;
+            b->scratch_bytes = persist_scratch_bytes(teams);
+            e = cudaMalloc(&b->d_scratch, b->scratch_bytes);
+        }
+        if (e == cudaSuccess) {
+            char* base = static_cast<char*>(b->d_scratch);
+            const int teams = b->persist_grid / b->team_ctas;
+            b->scratch.sync = reinterpret_cast<unsigned*>(base);
+            b->scratch.queue = reinterpret_cast<int*>(base + sizeof(unsigned) * (size_t)teams * kPersistSyncStride);
+            b->scratch.team_prob = b->scratch.queue + 1;
+            b->scratch.abort_flag = b->scratch.queue + 1 + teams;
+            // One graph: clear the scratch, then the persistent launch.
+            cudaGraph_t g;
+            PersistArgs<float> a = batch_args(b);
+            cudaError_t ce = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+            cudaError_t le = cudaSuccess;
+            if (ce == cudaSuccess) {
+                le = cudaMemsetAsync(b->d_scratch, 0, b->scratch_bytes, b->stream);
+                if (le == cudaSuccess) le = launch_plan_persistent<float>(a, 7, b->persist_grid, b->persist_smem,
+                                                                         b->stream);
+                cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+                if (le == cudaSuccess && ee == cudaSuccess) {
+                    le = cudaGraphInstantiate(&b->graph, g, 0);
+                    cudaGraphDestroy(g);
+                } else if (ee == cudaSuccess) {
+                    cudaGraphDestroy(g);
+                }
+            }
+            if (ce != cudaSuccess || le != cudaSuccess || !b->graph) {
+                // Not capturable here: plan with direct launches instead.
+                (void)cudaGetLastError();
+                b->graph = nullptr;
+                b->graph_direct = true;
+            }
+        }
+        if (e != cudaSuccess) {
+            char buf[256];
+            snprintf(buf, sizeof(buf), "stp_batch_create: %s", cudaGetErrorString(e));
+            g_last_error = buf;
+            stp_batch_free(b);
+            return STP_ERR_CUDA;
+        }
+        b->ctl.resize(n);
+        *out = b;
+        return STP_OK;
+    }
     if (e == cudaSuccess) {
         // Configure the batched collision kernel outside the capture.
         e = launch_validate_batch<float>(b->d_geom, b->d_state, 0, 0, sh.max_obs, 1, sh.validate_smem, b->stream);
@@ -1586,13 +1759,26 @@ extern "C" stp_status stp_batch_plan(stp_batch* b, stp_stats* stats, double* bat
     }
     if (e != cudaSuccess) return fail(e, "memset");
     if ((e = cudaEventRecord(b->ev0, st)) != cudaSuccess) return fail(e, "cudaEventRecord");
-    if ((e = launch_plan_reset_batch<float>(b->d_state, b->shape, b->d_iters, st)) != cudaSuccess)
-        return fail(e, "reset");
-    const int n_launch = (b->max_iters + b->iters_per_graph - 1) / b->iters_per_graph;
-    for (int i = 0; i < n_launch; ++i)
-        if ((e = cudaGraphLaunch(b->graph, st)) != cudaSuccess) return fail(e, "cudaGraphLaunch");
-    if ((e = cudaEventRecord(b->ev1, st)) != cudaSuccess) return fail(e, "cudaEventRecord");
-    if ((e = launch_extract_path_batch<float>(b->d_state, b->shape, st)) != cudaSuccess) return fail(e, "path");
+    if (b->launch_mode == 0) {
+        // One persistent launch plans every problem (reset to path extraction).
+        if (b->graph_direct) {
+            if ((e = cudaMemsetAsync(b->d_scratch, 0, b->scratch_bytes, st)) != cudaSuccess) return fail(e, "memset");
+            if ((e = launch_plan_persistent<float>(batch_args(b), 7, b->persist_grid, b->persist_smem, st)) !=
+                cudaSuccess)
+                return fail(e, "persistent launch");
+        } else if ((e = cudaGraphLaunch(b->graph, st)) != cudaSuccess) {
+            return fail(e, "cudaGraphLaunch");
+        }
+        if ((e = cudaEventRecord(b->ev1, st)) != cudaSuccess) return fail(e, "cudaEventRecord");
+    } else {
+        if ((e = launch_plan_reset_batch<float>(b->d_state, b->shape, b->d_iters, st)) != cudaSuccess)
+            return fail(e, "reset");
+        const int n_launch = (b->max_iters + b->iters_per_graph - 1) / b->iters_per_graph;
+        for (int i = 0; i < n_launch; ++i)
+            if ((e = cudaGraphLaunch(b->graph, st)) != cudaSuccess) return fail(e, "cudaGraphLaunch");
+        if ((e = cudaEventRecord(b->ev1, st)) != cudaSuccess) return fail(e, "cudaEventRecord");
+        if ((e = launch_extract_path_batch<float>(b->d_state, b->shape, st)) != cudaSuccess) return fail(e, "path");
+    }
     for (int i = 0; i < n && e == cudaSuccess; ++i)
         e = cudaMemcpyAsync(&b->ctl[i], b->probs[i]->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1601,6 +1787,11 @@ extern "C" stp_status stp_batch_plan(stp_batch* b, stp_stats* stats, double* bat
     cudaEventElapsedTime(&ms, b->ev0, b->ev1);
     if (batch_ms) *batch_ms = ms;
     stp_status result = STP_OK;
+    // First solutions count from the start of the batch: the earliest start
+    // of any problem (a queued problem starts when a team takes it).
+    unsigned long long t0 = ~0ull;
+    for (int i = 0; i < n; ++i)
+        if (b->trivial[i] == 0) t0 = std::min(t0, b->ctl[i].t_start);
     for (int i = 0; i < n; ++i) {
         const Ctl& hc = b->ctl[i];
         stp_problem* p = b->probs[i];
@@ -1629,11 +1820,12 @@ extern "C" stp_status stp_batch_plan(stp_batch* b, stp_stats* stats, double* bat
             s.nn_nodes = (long long)hc.st_nn_nodes;
             s.bridge_evals = (long long)hc.st_br_evals;
             s.bridge_nodes = (long long)hc.st_br_nodes;
-            s.first_solution_ms = hc.first_iter >= 0 ? (double)(hc.t_first - hc.t_start) * 1e-6 : -1.0;
+            s.first_solution_ms = hc.first_iter >= 0 ? (double)(hc.t_first - t0) * 1e-6 : -1.0;
             s.plan_ms = hc.t_end > hc.t_start ? (double)(hc.t_end - hc.t_start) * 1e-6 : ms;
             s.U = hc.U;
             s.C = hc.C;
             if (hc.err & kErrCapacity) result = STP_ERR_CAPACITY;
+            if ((hc.err & kErrTimeout) && result == STP_OK) result = STP_ERR_TIMEOUT;
         }
         if (stats) stats[i] = s;
     }
@@ -1666,6 +1858,7 @@ extern "C" void stp_batch_free(stp_batch* b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->d_scratch) cudaFree(b->d_scratch);
     if (b->d_geom) cudaFree(b->d_geom);
     if (b->d_state) cudaFree(b->d_state);
     if (b->d_iters) cudaFree(b->d_iters);

@@ -117,6 +117,12 @@ struct Ctl {
     // scan work: (query, node) key evaluations and nodes read once per set
     unsigned long long st_nn_evals, st_nn_nodes, st_br_evals, st_br_nodes;
     unsigned long long t_start, t_first, t_end;
+    // wall-clock budget of the plan in device global-timer ns (0: none),
+    // checked after every iteration
+    unsigned long long budget_ns;
+    // persistent planner kernel: device time of each step (ns, summed over
+    // iterations, measured barrier to barrier by the team's first CTA)
+    unsigned long long ph_ns[8];
 };
 
 // Device pointers of one problem's planner state (passed by value).

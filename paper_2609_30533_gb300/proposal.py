@@ -27,8 +27,10 @@ class Outcome:
     batch_ms: float
 
 
-def plan_batch(problems: Sequence["stp.Problem"], nn_ctas=4, validate_ctas=8, iters_per_graph=16) -> Outcome:
-    B = stp.Batch(problems, nn_ctas=nn_ctas, validate_ctas=validate_ctas, iters_per_graph=iters_per_graph)
+def plan_batch(problems: Sequence["stp.Problem"], nn_ctas=4, validate_ctas=8, iters_per_graph=16, launch_mode=0,
+               team_ctas=0) -> Outcome:
+    B = stp.Batch(problems, nn_ctas=nn_ctas, validate_ctas=validate_ctas, iters_per_graph=iters_per_graph,
+                  launch_mode=launch_mode, team_ctas=team_ctas)
     ms, stats = B.plan()
     B.close()
     fi = np.array([s["first_solution_iter"] for s in stats])

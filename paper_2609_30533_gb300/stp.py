@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libstp.so")
 
 STP_OK, STP_ERR_INVALID, STP_ERR_CAPACITY, STP_ERR_CUDA, STP_ERR_TIMEOUT, STP_NO_SOLUTION = range(6)
 TRACE_INTS = 10
+STP_LAUNCH_DEFAULT, STP_LAUNCH_STEPS, STP_LAUNCH_PERSISTENT = 0, 1, 2
 STP_EDGES_DEVICE = 1
 STP_EDGES_CLEARANCE = 2
 STP_EDGES_NO_EARLY_EXIT = 4
@@ -42,7 +43,8 @@ class StpParams(C.Structure):
                 ("p_guided", C.c_double), ("t_max", C.c_double), ("seed", C.c_ulonglong),
                 ("problem_id", C.c_uint), ("precision", C.c_int), ("learned", C.c_int),
                 ("capacity", C.c_int), ("iters_per_graph", C.c_int), ("t_offset", C.c_double),
-                ("continuous", C.c_int), ("self_collision", C.c_int)]
+                ("continuous", C.c_int), ("self_collision", C.c_int), ("launch_mode", C.c_int),
+                ("persist_ctas", C.c_int)]
 
 
 class StpStats(C.Structure):
@@ -58,7 +60,8 @@ class StpStats(C.Structure):
 
 
 class StpBatchParams(C.Structure):
-    _fields_ = [("nn_ctas", C.c_int), ("validate_ctas", C.c_int), ("iters_per_graph", C.c_int)]
+    _fields_ = [("nn_ctas", C.c_int), ("validate_ctas", C.c_int), ("iters_per_graph", C.c_int),
+                ("launch_mode", C.c_int), ("team_ctas", C.c_int)]
 
 
 class StpError(RuntimeError):
@@ -206,7 +209,8 @@ class Problem:
     def __init__(self, *, dof, arm, dh, q_lo, q_hi, spheres, v_max, obs_radius, obs_way, q_start, q_goal,
                  variant=0, n_roots=4, ext_per_iter=64, max_iters=100, budget_ms=0.0, eta=0.1, edge_res=0.01,
                  env_dt=0.02, p_new=0.05, p_guided=0.95, t_max=10.0, seed=0, problem_id=0, precision=0,
-                 capacity=0, iters_per_graph=0, learned=0, t_offset=0.0, continuous=0, self_collision=0):
+                 capacity=0, iters_per_graph=0, learned=0, t_offset=0.0, continuous=0, self_collision=0,
+                 launch_mode=0, persist_ctas=0):
         L = lib()
         self.dof = int(dof)
         self.precision = int(precision)
@@ -230,7 +234,7 @@ class Problem:
                                 float(eta), float(edge_res), float(env_dt), float(p_new), float(p_guided),
                                 float(t_max), int(seed), int(problem_id), int(precision), int(learned),
                                 int(capacity), int(iters_per_graph), float(t_offset), int(continuous),
-                                int(self_collision))
+                                int(self_collision), int(launch_mode), int(persist_ctas))
         h = C.c_void_p()
         s = L.stp_create_problem(C.byref(robot), C.byref(obstacles), _dp(arr(q_start)), _dp(arr(q_goal)),
                                  C.byref(self.params), C.byref(h))
@@ -442,11 +446,12 @@ class Batch:
     """Many FP32 problems planned together (stp_batch_*). The problems must stay
     alive while the batch exists."""
 
-    def __init__(self, problems, nn_ctas=0, validate_ctas=0, iters_per_graph=0):
+    def __init__(self, problems, nn_ctas=0, validate_ctas=0, iters_per_graph=0, launch_mode=0, team_ctas=0):
         L = lib()
         self.problems = list(problems)
         arr = (C.c_void_p * len(self.problems))(*[p.handle.value for p in self.problems])
-        bp = StpBatchParams(int(nn_ctas), int(validate_ctas), int(iters_per_graph))
+        bp = StpBatchParams(int(nn_ctas), int(validate_ctas), int(iters_per_graph), int(launch_mode),
+                            int(team_ctas))
         h = C.c_void_p()
         s = L.stp_batch_create(arr, len(self.problems), C.byref(bp), C.byref(h))
         if s != STP_OK:

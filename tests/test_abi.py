@@ -53,7 +53,8 @@ def _params(**kw):
     from paper_2609_30533_gb300 import stp
     base = dict(variant=0, n_roots=4, ext_per_iter=64, max_iters=10, budget_ms=0.0, eta=0.1, edge_res=0.01,
                 env_dt=0.02, p_new=0.05, p_guided=0.95, t_max=20.0, seed=0, problem_id=0, precision=0,
-                learned=0, capacity=0, iters_per_graph=0, t_offset=0.0, continuous=0, self_collision=0)
+                learned=0, capacity=0, iters_per_graph=0, t_offset=0.0, continuous=0, self_collision=0,
+                launch_mode=0, persist_ctas=0)
     base.update(kw)
     return stp.StpParams(**base)
 
@@ -98,7 +99,8 @@ def test_invalid_geometry_rejected(L):
 
 @pytest.mark.parametrize("bad", [dict(n_roots=129), dict(ext_per_iter=8193), dict(variant=-1),
                                  dict(edge_res=0.0), dict(env_dt=-0.02), dict(t_max=0.0), dict(p_guided=-0.1),
-                                 dict(capacity=-1), dict(iters_per_graph=-1), dict(t_offset=float("inf"))])
+                                 dict(capacity=-1), dict(iters_per_graph=-1), dict(t_offset=float("inf")),
+                                 dict(launch_mode=3), dict(launch_mode=-1), dict(persist_ctas=-1)])
 def test_parameter_limits(L, bad):
     prob, _ = WL.disc2d(0)
     s, h = _create(prob, _params(**bad))
