@@ -56,21 +56,32 @@ WORKLOAD = "ur5e-6dof-32sph-16obs-recycling-N8-W1024"
 # intervals. The figure belongs to the kernel source it was taken from: when
 # the source's hash differs, the bench reports no traffic.
 TRAFFIC_CAPTURE = {"kernel": "k_validate", "bytes_per_launch": 229.6e3,
-                   "source": os.path.join("paper_2609_30533_gb300", "csrc", "stp_validate.cu"),
+                   "sources": [os.path.join("paper_2609_30533_gb300", "csrc", f)
+                               for f in ("stp_validate.cu", "stp_validate_body.cuh", "stp_internal.cuh")],
                    "sha256_16": "2e753c4f50acea8b", "profile": "profiles/k_validate_ur5e_plan_ncu.md"}
 METRIC = "validated space-time edges/s"
 UNIT = "edges/s"
 FLUSH_BYTES = 512 << 20
 
 
+def kernel_source_hash(sources):
+    """First 16 hex digits of the SHA-256 of the kernel's source files, in order."""
+    import hashlib
+    d = hashlib.sha256()
+    try:
+        for src in sources:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                d.update(f.read())
+    except OSError:
+        return None
+    return d.hexdigest()[:16]
+
+
 def _capture_traffic():
     """(bytes per launch or None, note) of the ncu traffic capture, None when
     the kernel source changed since it was taken."""
-    import hashlib
-    try:
-        with open(os.path.join(ROOT, TRAFFIC_CAPTURE["source"]), "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()[:16]
-    except OSError:
+    h = kernel_source_hash(TRAFFIC_CAPTURE["sources"])
+    if h is None:
         return None, "kernel source not found"
     if h != TRAFFIC_CAPTURE["sha256_16"]:
         return None, "kernel source changed since the ncu capture (%s)" % TRAFFIC_CAPTURE["profile"]
@@ -249,11 +260,12 @@ def cpu_batched_baseline(problems, workers, iters, cores=None):
                       "%.1f s of planning summed over processes)" % (problems, iters, workers, edges, wall, cpu_s)}
 
 
-def microbench(args, P, prob, prm, stream, flush, rank, local):
-    """Collision kernel alone on 2^20 UR5e edges resident on the device, with
-    and without early exit; kernel time from CUDA events around the launch."""
+def microbench(args, P, prob, prm, stream, flush, rank, local, n=None):
+    """Collision kernel alone on random edges of the problem's robot and
+    obstacles (2^20 UR5e edges by default) resident on the device, with and
+    without early exit; kernel time from CUDA events around the launch."""
     import torch
-    n = args.micro_edges
+    n = n or args.micro_edges
     qa, ta, qb, tb = WL.microbench_edges(prob, n, prm.eta, prm.H, seed=rank)
     dev = torch.device("cuda", local)
     tq = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev) for a in (qa, ta, qb, tb)]
@@ -292,6 +304,20 @@ def microbench(args, P, prob, prm, stream, flush, rank, local):
     return micro, peak
 
 
+def microbench_arm7(args, stream, flush, rank, local):
+    """The collision kernel on the 7-DoF workload (48 link spheres, 64 sphere
+    obstacles with radii U[0.04, 0.1] m on 8-waypoint paths, H 60 s): random
+    edges of length eta = 0.5 rad, 3,072 sphere-obstacle pairs per check point."""
+    from paper_2609_30533_gb300 import stp
+    prob7, prm7 = WL.arm7(rank)
+    P7 = stp.problem_from(prob7, prm7, precision=0, max_iters=1)
+    P7.set_stream(stream.cuda_stream)
+    micro7, peak7 = microbench(args, P7, prob7, prm7, stream, flush, rank, local, n=args.micro7_edges)
+    P7.close()
+    return dict(micro7, n_edges=args.micro7_edges, peak_tflops=peak7,
+                workload="arm7, 48 spheres, 64 obstacles, 8 waypoints")
+
+
 def batched(args, rank):
     """Batched form: mixed problems (2/6/7-DoF, 4..128 obstacles, 10..60 s
     horizons) planned together in one graph-captured launch sequence; W and the
@@ -315,16 +341,38 @@ def batched(args, rank):
                                team_ctas=(2, 4, 8, 16), nn_ctas=(2, 4, 8), validate_ctas=(2, 4, 8))
     idx = list(range(args.batch_problems))
     probs = make(idx, choice.workers, args.batch_iters)
-    B = stp.Batch(probs, nn_ctas=choice.nn_ctas, validate_ctas=choice.validate_ctas, iters_per_graph=16,
-                  launch_mode=choice.launch_mode, team_ctas=choice.team_ctas)
-    B.plan()
-    runs = []
-    for _ in range(args.batch_reps):
-        ms, stats = B.plan()
-        runs.append((ms, stats))
-    B.close()
-    ms = statistics.median(r[0] for r in runs)
-    stats = runs[0][1]
+
+    def run_full(t):
+        B = stp.Batch(probs, nn_ctas=t.nn_ctas, validate_ctas=t.validate_ctas, iters_per_graph=16,
+                      launch_mode=t.launch_mode, team_ctas=t.team_ctas)
+        B.plan()
+        runs = [B.plan() for _ in range(args.batch_reps)]
+        B.close()
+        return statistics.median(r[0] for r in runs), runs[0][1]
+
+    # The sample ranks the shapes of each launch form; the whole batch then
+    # decides between the two forms' best shapes (a 48-problem sample fills
+    # the persistent queue's teams about once, the whole batch many times).
+    forms = {}
+    for mode, name in ((stp.STP_LAUNCH_DEFAULT, "persistent_queue"), (1, "per_step")):
+        cand = [t for t in choice.trials if t.launch_mode == mode and t.workers == choice.workers]
+        if not cand:
+            continue
+        t = min(cand, key=autotune._rank)
+        f_ms, f_stats = run_full(t)
+        f_fs = [st["first_solution_ms"] for st in f_stats if st["first_solution_iter"] >= 0]
+        forms[name] = {"launch_mode": t.launch_mode, "team_ctas": t.team_ctas, "nn_ctas": t.nn_ctas,
+                       "validate_ctas": t.validate_ctas, "batch_ms": f_ms, "problems_per_s": len(idx) / (f_ms * 1e-3),
+                       "solved": len(f_fs), "first_solution_ms_p50": float(np.percentile(f_fs, 50)) if f_fs else None,
+                       "first_solution_ms_p99": float(np.percentile(f_fs, 99)) if f_fs else None,
+                       "_trial": t, "_stats": f_stats}
+    best_name = min(forms, key=lambda k: (-forms[k]["solved"], forms[k]["batch_ms"]))
+    best = forms[best_name]
+    choice = dataclasses.replace(choice, launch_mode=best["_trial"].launch_mode, team_ctas=best["_trial"].team_ctas,
+                                 nn_ctas=best["_trial"].nn_ctas, validate_ctas=best["_trial"].validate_ctas)
+    ms, stats = best["batch_ms"], best["_stats"]
+    for f in forms.values():
+        del f["_trial"], f["_stats"]
     fs = sorted(st["first_solution_ms"] for st in stats if st["first_solution_iter"] >= 0)
     edges = sum(st["edges_validated"] + st["bridges_validated"] for st in stats)
 
@@ -379,8 +427,9 @@ def batched(args, rank):
         "cpu_oracle_all_cores": cpu_all,
         "problems": len(idx), "iters_budget": args.batch_iters,
         "autotuned": {"workers": choice.workers, "launch_mode": choice.launch_mode, "team_ctas": choice.team_ctas,
-                      "nn_ctas": choice.nn_ctas, "validate_ctas": choice.validate_ctas,
+                      "nn_ctas": choice.nn_ctas, "validate_ctas": choice.validate_ctas, "form": best_name,
                       "trials": [dataclasses.asdict(t) for t in choice.trials]},
+        "forms_whole_batch": forms,
         "batch_ms": ms, "problems_per_s": len(idx) / (ms * 1e-3), "edges_per_s": edges / (ms * 1e-3),
         "solved": len(fs), "success_rate": len(fs) / len(idx),
         "first_solution_ms_p50": pct(fs, 50), "first_solution_ms_p99": pct(fs, 99),
@@ -716,6 +765,7 @@ def main():
     ap.add_argument("--cpu-batch-problems", type=int, default=0, help="0 = one per host core (at most 32)")
     ap.add_argument("--cpu-batch-iters", type=int, default=2)
     ap.add_argument("--micro-edges", type=int, default=1 << 20)
+    ap.add_argument("--micro7-edges", type=int, default=1 << 16)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch-problems", type=int, default=512)
     ap.add_argument("--batch-iters", type=int, default=64)
@@ -769,7 +819,9 @@ def main():
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     if args.only == "micro":
         micro, peak = microbench(args, P, prob, prm, stream, flush, rank, local)
-        print(json.dumps({"microbench": dict(micro, n_edges=args.micro_edges, peak_tflops=peak)}))
+        m7 = microbench_arm7(args, stream, flush, rank, local)
+        print(json.dumps({"microbench": dict(micro, n_edges=args.micro_edges, peak_tflops=peak),
+                          "microbench_arm7": m7}))
         return
     if args.only == "batch":
         print(json.dumps({"batched": batched(args, rank)}))
@@ -832,6 +884,7 @@ def main():
     # inside the captured graphs.
     prof_tot = {}
     pairs = points = 0
+    nn_evals = br_evals = 0
     prof_step_ms = 0.0
     prof_error = None
     try:
@@ -845,6 +898,8 @@ def main():
                 a[1] += n
             pairs += out.stats["pair_tests"]
             points += out.stats["check_points"]
+            nn_evals += out.stats["nn_evals"]
+            br_evals += out.stats["bridge_evals"]
     except Exception as exc:  # report, keep the measured value
         prof_error = str(exc)
         prof_tot = {}
@@ -892,6 +947,7 @@ def main():
                                  "device-wide barriers); step times barrier to barrier on the device timer"}
 
     micro, peak = microbench(args, P, prob, prm, stream, flush, rank, local)
+    micro7 = microbench_arm7(args, stream, flush, rank, local)
     batch_result = None if args.no_batch else batched(args, rank)
     learned_result = None if args.no_learned else learned(args, rank)
     sweep_result = None if args.no_sweep else sweep(args, rank)
@@ -914,6 +970,7 @@ def main():
     val_ms = kv[0] + kb[0]
     val_launches = kv[1] + kb[1]
     flops = pairs * 8 + points * point_flops(prob)
+    step_flops = (flops + (nn_evals + br_evals) * (3 * prob.dof + 5)) / max(args.steps, 1)
     achieved = flops / (val_ms * 1e-3) / 1e12 if val_ms > 0 else 0.0
     kernels = {k: {"ms_total": round(v[0], 4), "launches": v[1],
                    "share": round(v[0] / max(sum(x[0] for x in prof_tot.values()), 1e-12), 4)}
@@ -936,6 +993,15 @@ def main():
                          n_sm, max_mhz),
                      "launches": val_launches, "avg_launch_ms": val_ms / max(val_launches, 1),
                      "flops_per_launch": flops / max(val_launches, 1)},
+        # The whole planner step against the FP32 peak: algorithmic flops of
+        # the collision checks (pair tests x 8 + per-point FK, transforms and
+        # interpolation) and of the NN and bridge scans ((3d + 5) per
+        # (query, vertex) evaluation), over the timed step time.
+        "roofline_step": {
+            "bound": "alu", "unit": "TFLOP/s", "peak": peak,
+            "flops_per_step": step_flops,
+            "achieved": step_flops / (ms_max / args.steps * 1e-3) / 1e12,
+            "frac": step_flops / (ms_max / args.steps * 1e-3) / 1e12 / peak if peak else None},
         "kernels": kernels,
         "profiled_ms_per_step": prof_step_ms / args.steps,
         "profiling_error": prof_error,
@@ -943,6 +1009,7 @@ def main():
         "first_solution_ms_p50": statistics.median(fs_ms) if fs_ms else None,
         "microbench": dict(micro, n_edges=n, peak_tflops=peak),
         "persistent_single": persistent_single,
+        "microbench_arm7": micro7,
     }
     if clk:
         line["clocks"] = clk

@@ -292,9 +292,10 @@ stp_status stp_trace(stp_problem *p, int *records, int cap_iters, int *n_iters);
  * block in the driver's allocator, or a host process whose device-memory
  * budget is fixed after start-up. The paper has no counterpart: this is the
  * collision batch of stp_check_edges with its per-call scratch (check counts,
- * offsets, hit flags, scan partials) taken from one static device array built
- * into the library, sized for STP_NOALLOC_MAX_EDGES edges (about 1 MiB, held
- * on every GPU that loads the library until the process exits).
+ * offsets, hit flags, window counter, scan partials) taken from one static
+ * device array built into the library, sized for STP_NOALLOC_MAX_EDGES edges
+ * (about 1 MiB, held on every GPU that loads the library until the process
+ * exits).
  *   qa, qb     [n_edges][dof] DEVICE pointers, ta, tb [n_edges] DEVICE
  *              pointers, element type per precision (as stp_check_edges).
  *   verdict    [n_edges] DEVICE output, 1 = collision-free, 0 = collides.
@@ -444,7 +445,9 @@ stp_status stp_mlp_train_step(stp_mlp *m, int B, const float *x, const float *ta
                               int flags);
 /* With profiling on, every tensor-core GEMM is bracketed by CUDA events;
  * stp_mlp_profile returns (and clears) their total time, FLOPs and
- * algorithmic HBM bytes (operands read once, every output copy written once). */
+ * algorithmic HBM bytes, both over the layers' logical shapes (32 inputs,
+ * 160 outputs, the batch without padding): operands read once, each output
+ * written once in one layout. */
 stp_status stp_mlp_set_profiling(stp_mlp *m, int on);
 stp_status stp_mlp_profile(stp_mlp *m, double *gemm_ms, double *gemm_flops, double *gemm_bytes);
 const char *stp_mlp_last_error(const stp_mlp *m);

@@ -829,7 +829,7 @@ stp_status check_edges_impl(stp_problem* p, int n, const void* qa, const void* t
         l.cnt = cv.take<int>(n);
         l.off = cv.take<long long>((size_t)n + 1);
         l.tmp = cv.take<long long>((size_t)n / 4096 + 2);
-        l.hit = cv.take<int>(n);
+        l.hit = cv.take<int>((size_t)n + 1);  // flags, then the window counter
         l.clr = clear ? cv.take<R>(n) : nullptr;
         l.ver = dev ? nullptr : cv.take<unsigned char>(n);
         return l;
@@ -860,7 +860,7 @@ stp_status check_edges_impl(stp_problem* p, int n, const void* qa, const void* t
     }
     STP_CUDA(p, launch_edge_counts<R>(geom_of<R>(p), dqa, dta, dqb, dtb, d, n, p->prm.edge_res, L.cnt, st));
     STP_CUDA(p, launch_scan_counts(L.cnt, n, L.off, L.tmp, st));
-    STP_CUDA(p, cudaMemsetAsync(L.hit, 0, sizeof(int) * n, st));
+    STP_CUDA(p, cudaMemsetAsync(L.hit, 0, sizeof(int) * ((size_t)n + 1), st));
     if (clear) {
         unsigned long long inf_bits = sizeof(R) == 4 ? 0x7f800000ull : 0x7ff0000000000000ull;
         STP_CUDA(p, launch_fill(L.clr, n, (int)sizeof(R), inf_bits, st));
@@ -875,6 +875,7 @@ stp_status check_edges_impl(stp_problem* p, int n, const void* qa, const void* t
     E.off = L.off;
     E.n_host = n;
     E.hit = L.hit;
+    E.win_next = L.hit + n;
     E.clear = L.clr;
     E.err = &p->d_ctl->err;
     STP_CUDA(p, cudaMemsetAsync(p->d_counters, 0, 2 * sizeof(unsigned long long), st));
@@ -1360,7 +1361,7 @@ constexpr int kNoAllocMaxEdges = STP_NOALLOC_MAX_EDGES;
 constexpr size_t kNoAllocCnt = 0;
 constexpr size_t kNoAllocOff = kNoAllocCnt + ce_align(sizeof(int) * kNoAllocMaxEdges);
 constexpr size_t kNoAllocHit = kNoAllocOff + ce_align(sizeof(long long) * (kNoAllocMaxEdges + 1));
-constexpr size_t kNoAllocTmp = kNoAllocHit + ce_align(sizeof(int) * kNoAllocMaxEdges);
+constexpr size_t kNoAllocTmp = kNoAllocHit + ce_align(sizeof(int) * (kNoAllocMaxEdges + 1));
 constexpr size_t kNoAllocBytes = kNoAllocTmp + ce_align(sizeof(long long) * (kNoAllocMaxEdges / 4096 + 2));
 constexpr int kNoAllocMaxDevices = 64;
 
@@ -1411,8 +1412,9 @@ stp_status check_edges_noalloc_impl(stp_problem* p, int n, const void* qa, const
     const R* dtb = static_cast<const R*>(tb);
     STP_CUDA(p, launch_edge_counts<R>(geom_of<R>(p), dqa, dta, dqb, dtb, p->dof, n, p->prm.edge_res, cnt, st));
     STP_CUDA(p, launch_scan_counts(cnt, n, off, tmp, st));
-    // The array keeps the previous call's flags: clear them.
-    STP_CUDA(p, cudaMemsetAsync(hit, 0, sizeof(int) * (size_t)n, st));
+    // The array keeps the previous call's flags (and window counter after
+    // them): clear them.
+    STP_CUDA(p, cudaMemsetAsync(hit, 0, sizeof(int) * ((size_t)n + 1), st));
     EdgeBatch<R> E{};
     E.qa = dqa;
     E.qb = dqb;
@@ -1423,6 +1425,7 @@ stp_status check_edges_noalloc_impl(stp_problem* p, int n, const void* qa, const
     E.off = off;
     E.n_host = n;
     E.hit = hit;
+    E.win_next = hit + n;
     E.err = &p->d_ctl->err;
     STP_CUDA(p, launch_validate<R>(geom_of<R>(p), E, false, true, 0, st));
     STP_CUDA(p, launch_finish_batch<R>(n, hit, verdict, nullptr, st));

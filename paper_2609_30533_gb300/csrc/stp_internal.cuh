@@ -80,6 +80,10 @@ struct EdgeBatch {
     unsigned long long* pairs_done;   // executed sphere-obstacle pair tests or nullptr
     int* err;
     const int* done;                  // planner: skip the launch when set (or nullptr)
+    // Precomputed-offset batches: window counter (device int, zero at launch)
+    // from which CTAs take windows of consecutive edges as they finish the
+    // previous one; nullptr deals the windows round-robin instead.
+    int* win_next = nullptr;
     // In-kernel-scan batches only: 0 every check point; 1 the coarse subset
     // j = ceil((i+1) c / c0), i < c0 = ceil(c/8) (ends at j = c); 2 every
     // check point of the entries that phase 1 did not already find colliding.

@@ -12,12 +12,15 @@
 // HBM and move into shared memory with one bulk asynchronous copy each
 // (cp.async.bulk, completion on an mbarrier). One elected thread issues
 // tcgen05.mma (kind::f16, M = 128, N <= 256, K = 16 per instruction) into a
-// TMEM accumulator of N FP32 columns; tcgen05.commit releases a stage when
-// its MMAs have read it. Four warps read the accumulator back with
-// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows) and run the
-// fused epilogue: bias + ReLU with BF16 stores in both operand layouts
-// (forward), bias only with FP32 stores (output layer), ReLU-mask with BF16
-// and FP32 stores (backward), or FP32 split-K partials (weight gradients).
+// TMEM accumulator of FP32 columns; tcgen05.commit releases a stage when its
+// MMAs have read it; warps read the accumulator back with tcgen05.ld (warp w
+// owns TMEM lanes 32 (w % 4) .. + 31 = tile rows) into a fused epilogue.
+// Two kernels: the products over K <= 256 (forward layers: bias + ReLU with
+// BF16 stores in both operand layouts, or bias with FP32 stores for the
+// output layer; input gradients: ReLU mask, BF16 stores and bias-gradient
+// partials) run persistent with the weight operand resident in shared memory
+// (k_gemm_res); the weight gradients (K = batch) run split-K with FP32
+// partials (k_gemm_wgrad).
 //
 // Element (r, k) of a tiled [R][K] matrix (R % 8 == 0, K % 64 == 0) sits at
 //   (((k / 64) * (R / 8) + r / 8) * 8 + (k % 64) / 8) * 64 + (r % 8) * 8 + k % 8.
@@ -40,14 +43,10 @@ namespace mlp {
 
 constexpr int kIn = 32, kInP = 64, kHid = 256, kOut = 160, kOutP = 256;
 constexpr int kMix = 8, kWp = 16, kWpDim = 8, kTgt = 130;
-// Eight warps: warp w reads TMEM lane quadrant w % 4 (tile rows 32 (w % 4) ..
-// + 31) and columns [(w / 4) N/2, (w / 4 + 1) N/2) in the epilogue.
-constexpr int kTileM = 128, kStageK = 64, kThreads = 256;
-// Pipeline depth: products over K = 256 (four stages) use two stages, so that
-// two CTAs (2 x 97 KB of shared memory, 2 x 256 TMEM columns) share an SM and
-// one CTA's epilogue overlaps the other's copies and MMAs; the long-K weight-
-// gradient products keep four stages (one CTA per SM).
-__host__ __device__ constexpr int stages_for(int mode) { return mode == 3 ? 4 : 2; }
+// Weight-gradient products: eight warps (warp w reads TMEM lane quadrant
+// w % 4 and columns [(w / 4) N/2, (w / 4 + 1) N/2) in the epilogue), 64-wide
+// K stages through a four-stage pipeline, one CTA per SM.
+constexpr int kTileM = 128, kStageK = 64, kThreads = 256, kWStages = 4;
 constexpr float kSMin = -7.f, kSMax = 2.f;
 // Bias gradients: every 128-row tile (a GEMM CTA or a loss block) writes the
 // column sums of its rows as one partial [256]; Adam adds the partials.
@@ -115,13 +114,9 @@ struct GemmArgs {
     const __nv_bfloat16* B;  // tiled [N][K]
     int KT;                  // 64-wide K stages in total
     int kt_per_split;        // split-K (blockIdx.z): stages [z*kps, min(KT, (z+1)*kps))
-    const float* bias;       // [N] (kHidden, kOutput)
-    const __nv_bfloat16* act;  // kBackward: forward activation, tiled [RA][N]
-    __nv_bfloat16* out_t;      // tiled [RA][N]
-    __nv_bfloat16* out_tT;     // tiled [N][RA]
-    float* out_f;              // FP32 row-major (kOutput), partials (kWGrad), bias-gradient partials [tile][N] (kBackward)
+    float* out_f;            // FP32 partials [splits][m_valid][ld_f]
     int ld_f;
-    int m_valid;               // kWGrad: rows written
+    int m_valid;             // rows written
     int* err;
 };
 
@@ -178,9 +173,9 @@ __device__ __forceinline__ float warp_colsum16(float (&v)[16]) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
-template <int N, int MODE>
-__global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
-    constexpr int kStages = stages_for(MODE);
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_wgrad(GemmArgs g) {
+    constexpr int kStages = kWStages;
     constexpr uint32_t kABytes = kTileM * kStageK * 2;  // 16 KB
     constexpr uint32_t kBBytes = N * kStageK * 2;
     constexpr uint32_t kTmemCols = N < 32 ? 32 : N;
@@ -189,8 +184,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int fail_sh;
-    __shared__ float sbias[N];  // bias (forward) or bias-gradient sums (backward)
-    __shared__ __align__(16) __nv_bfloat16 stile[kThreads / 32][16 * 32];
 
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = smem;
@@ -210,10 +203,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
         mbar_init(&done, 1);
         fail_sh = 0;
     }
-    if (MODE == kHidden || MODE == kOutput)
-        for (int i = tid; i < N; i += kThreads) sbias[i] = g.bias[i];
-    if (MODE == kBackward)
-        for (int i = tid; i < N; i += kThreads) sbias[i] = 0.f;
     if (warp == 0) tmem_alloc(&tmem_base_sh, kTmemCols);
     fence_before_sync();
     __syncthreads();
@@ -277,57 +266,274 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm(GemmArgs g) {
     if (fail_sh) have = false;
 
     // Epilogue: thread (warp, lane) owns tile row 32 (warp % 4) + lane and
-    // half of the columns.
+    // half of the columns; FP32 partial rows of split z.
     const int quad = warp & 3;
     const int r = m0 + 32 * quad + lane;
     const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16);
     const int cb = (warp >> 2) * (N / 2), ce = cb + N / 2;
 #pragma unroll 1
     for (int c0 = cb; c0 < ce; c0 += 16) {
-        if (MODE == kOutput && c0 >= kOut) continue;  // padding outputs are never read (warp-uniform)
         float v[16];
         if (have) tmem_ld16(trow + (uint32_t)c0, v);
         else {
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = 0.f;
         }
-        if (MODE == kHidden) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + sbias[c0 + i], 0.f);
-            store_row16(g.out_t, r, c0, g.RA, v);
-            store_T_warp(g.out_tT, m0 + 32 * quad, c0, N, v, stile[warp]);
-        } else if (MODE == kOutput) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] += sbias[c0 + i];
-            float4* o = reinterpret_cast<float4*>(g.out_f + (size_t)r * g.ld_f + c0);
+        if (r < g.m_valid) {
+            float4* o = reinterpret_cast<float4*>(g.out_f + ((size_t)z * g.m_valid + r) * g.ld_f + c0);
 #pragma unroll
             for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        } else if (MODE == kBackward) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                __align__(16) __nv_bfloat16 a[8];
-                *reinterpret_cast<uint4*>(a) = *reinterpret_cast<const uint4*>(g.act + tix(r, c0 + 8 * h, g.RA));
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    if (!(__bfloat162float(a[i]) > 0.f)) v[8 * h + i] = 0.f;
-            }
-            store_row16(g.out_t, r, c0, g.RA, v);
-            store_T_warp(g.out_tT, m0 + 32 * quad, c0, N, v, stile[warp]);
-            const float cs = warp_colsum16(v);
-            if (lane < 16) atomicAdd(&sbias[c0 + lane], cs);
-        } else {  // kWGrad
-            if (r < g.m_valid) {
-                float4* o = reinterpret_cast<float4*>(g.out_f + ((size_t)z * g.m_valid + r) * g.ld_f + c0);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-            }
         }
     }
     fence_before_sync();
     __syncthreads();
-    if (MODE == kBackward)
-        for (int i = tid; i < N; i += kThreads) g.out_f[(size_t)blockIdx.x * N + i] = sbias[i];
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// Products with K <= 256 (every forward layer and every input gradient) as a
+// persistent kernel with the weight operand resident in shared memory.
+//
+// Work unit = (128-row tile t, column half h): columns [h NU, (h + 1) NU) of
+// the output. The grid is even and CTA c takes units c, c + grid, ..., so it
+// always computes the same half h = c & 1 and loads that half of the weight
+// operand (NU x K BF16, at most 64 KB) into shared memory once; only the A
+// stages (128 rows x 64 K, 16 KB) stream through a ring of kRing stages.
+// The TMEM accumulator is double-buffered (two 128-column slots), so the
+// epilogue of one unit overlaps the copies and MMAs of the next.
+// Warps 0-7 run the epilogue (warp w reads TMEM lane quadrant w % 4 = tile
+// rows 32 (w % 4) .. + 31, and every other 16-column chunk starting at w / 4),
+// warp 8 lane 0 issues the bulk copies, warp 9 lane 0 the MMAs. Every wait
+// is bounded; a role whose wait runs out sets the error flag and stops, and
+// the copy issuer waits (bounded) for its copies in flight before the CTA
+// frees its TMEM and exits.
+// ---------------------------------------------------------------------------
+constexpr int kRing = 8, kResThreads = 320, kEpiWarps = 8;
+constexpr uint32_t kAStage = kTileM * kStageK * 2;  // 16 KB
+constexpr int kOutPad = 20;                         // FP32 staging row (16 + 4: no bank conflicts)
+
+__host__ __device__ constexpr int res_smem_bytes(int nu, int ks, int mode) {
+    return 1024 + ks * nu * kStageK * 2 + kRing * (int)kAStage + (mode == kOutput ? kEpiWarps * 32 * kOutPad * 4 : 0);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct ResArgs {
+    const __nv_bfloat16* A;    // tiled [RA][KS * 64]
+    int RA;                    // rows of A (multiple of 128)
+    const __nv_bfloat16* B;    // tiled [NB][KS * 64], output column n = row n of B
+    int NB;                    // rows of B's tiled layout
+    int units;                 // 2 * RA / 128
+    const float* bias;         // [2 NU] (forward modes)
+    const __nv_bfloat16* act;  // kBackward: forward activation, tiled [RA][256]
+    __nv_bfloat16* out_t;      // tiled [RA][256]
+    __nv_bfloat16* out_tT;     // tiled [256][RA]
+    float* out_f;              // kOutput: FP32 [RA][ld_f]; kBackward: bias-gradient partials [RA / 32][256]
+    int ld_f;
+    int* err;
+};
+
+template <int NU, int KS, int MODE>
+__global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
+    static_assert(NU % 16 == 0 && NU <= 128 && KS >= 1 && KS <= 4, "unit shape");
+    constexpr uint32_t kBBytes = NU * kStageK * 2;  // one K stage of the resident half
+    constexpr uint32_t kIdesc = idesc_bf16(kTileM, NU);
+    constexpr int kChunks = NU / 16;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kRing], empty[kRing], bfull, tfull[2], tempty[2], done;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_sh;
+    __shared__ float sbias[NU];
+    __shared__ __align__(16) __nv_bfloat16 stile[kEpiWarps][16 * 32];
+
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sB = smem;
+    unsigned char* sA = smem + KS * kBBytes;
+    float* sOut = reinterpret_cast<float*>(sA + kRing * kAStage);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int h = blockIdx.x & 1;
+
+    if (tid == 0) {
+        for (int s = 0; s < kRing; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&bfull, 1);
+        mbar_init(&done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kEpiWarps);
+        }
+        abort_sh = 0;
+    }
+    if (MODE == kHidden || MODE == kOutput)
+        for (int i = tid; i < NU; i += kResThreads) sbias[i] = g.bias[h * NU + i];
+    if (warp == 0) tmem_alloc(&tmem_base_sh, 256);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_base_sh;
+    auto fail = [&]() {
+        abort_sh = 1;
+        if (g.err) atomicOr(g.err, kErrTimeout);
+    };
+
+    if (warp == kEpiWarps) {
+        // Copy issuer.
+        if (lane == 0) {
+            mbar_expect_tx(&bfull, KS * kBBytes);
+            for (int kt = 0; kt < KS; ++kt)
+                bulk_g2s(sB + kt * kBBytes, g.B + ((size_t)kt * (g.NB >> 3) + (size_t)h * (NU >> 3)) * 512, kBBytes,
+                         &bfull);
+            const size_t rgA = (size_t)(g.RA >> 3);
+            int it = 0;
+            for (int u = blockIdx.x; u < g.units && !abort_sh; u += gridDim.x) {
+                const int t = u >> 1;
+                for (int kt = 0; kt < KS; ++kt, ++it) {
+                    const int s = it % kRing;
+                    if (it >= kRing && !mbar_wait(&empty[s], ((it / kRing) - 1) & 1)) {
+                        fail();
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], kAStage);
+                    bulk_g2s(sA + s * kAStage, g.A + ((size_t)kt * rgA + (size_t)t * (kTileM >> 3)) * 512, kAStage,
+                             &full[s]);
+                }
+            }
+            // Drain: the last copy issued into each stage (and the weight
+            // copies) have landed before the CTA may exit.
+            for (int s = 0; s < kRing && s < it; ++s) {
+                const int j = s + ((it - 1 - s) / kRing) * kRing;  // last issue index on stage s
+                mbar_wait(&full[s], (j / kRing) & 1);
+            }
+            mbar_wait(&bfull, 0);
+        }
+    } else if (warp == kEpiWarps + 1) {
+        // MMA issuer.
+        if (lane == 0) {
+            bool ok = mbar_wait(&bfull, 0);
+            if (!ok) fail();
+            int it = 0, i = 0;
+            for (int u = blockIdx.x; ok && u < g.units && !abort_sh; u += gridDim.x, ++i) {
+                const int b = i & 1;
+                if (i >= 2 && !mbar_wait(&tempty[b], ((i >> 1) - 1) & 1)) {
+                    fail();
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t d = tmem + (uint32_t)(b * 128);
+                for (int kt = 0; kt < KS; ++kt, ++it) {
+                    const int s = it % kRing;
+                    if (!mbar_wait(&full[s], (it / kRing) & 1)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    fence_after_sync();
+                    const uint32_t a0 = smem_u32(sA + s * kAStage), b0 = smem_u32(sB + kt * kBBytes);
+#pragma unroll
+                    for (int ks = 0; ks < kStageK / 16; ++ks)
+                        mma_bf16(d, smem_desc(a0 + ks * 256, 128, 1024), smem_desc(b0 + ks * 256, 128, 1024), kIdesc,
+                                 (kt > 0 || ks > 0) ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&tfull[b]);
+            }
+            // Every MMA has completed before the TMEM is freed.
+            mma_commit(&done);
+            if (!mbar_wait(&done, 0)) fail();
+        }
+    } else {
+        // Epilogue warps. Warp (quad, hw) takes chunks hw, hw + 2, ... of 16
+        // columns. The input-gradient mode's ReLU mask (the forward activation
+        // at the same rows and columns) of the next unit is loaded into
+        // registers while the current unit's stores drain.
+        const int quad = warp & 3, hw = warp >> 2;
+        constexpr int kWChunks = (kChunks + 1) / 2;
+        uint4 pa[MODE == kBackward ? kWChunks : 1][2];
+        auto load_mask = [&](int uu) {
+            if constexpr (MODE == kBackward) {
+                const int rr = (uu >> 1) * kTileM + 32 * quad + lane;
+#pragma unroll
+                for (int ci = 0; ci < kWChunks; ++ci) {
+                    const int c = hw + 2 * ci;
+                    if (c < kChunks) {
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh)
+                            pa[ci][hh] = *reinterpret_cast<const uint4*>(g.act + tix(rr, h * NU + 16 * c + 8 * hh, g.RA));
+                    }
+                }
+            }
+        };
+        if (blockIdx.x < g.units) load_mask(blockIdx.x);
+        int i = 0;
+        for (int u = blockIdx.x; u < g.units; u += gridDim.x, ++i) {
+            const int b = i & 1, t = u >> 1;
+            if (abort_sh || !mbar_wait(&tfull[b], (i >> 1) & 1)) {
+                if (lane == 0) fail();
+                break;
+            }
+            __syncwarp();
+            fence_after_sync();
+            const int r0 = t * kTileM + 32 * quad;
+            const int r = r0 + lane;
+            const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * 128);
+#pragma unroll
+            for (int ci = 0; ci < kWChunks; ++ci) {
+                const int c = hw + 2 * ci;
+                if (c >= kChunks) break;
+                const int cl = 16 * c, cg = h * NU + cl;  // local / global column
+                float v[16];
+                tmem_ld16(trow + (uint32_t)cl, v);
+                if constexpr (MODE == kHidden) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) v[k] = fmaxf(v[k] + sbias[cl + k], 0.f);
+                    store_row16(g.out_t, r, cg, g.RA, v);
+                    store_T_warp(g.out_tT, r0, cg, 256, v, stile[warp]);
+                } else if constexpr (MODE == kOutput) {
+                    float* so = sOut + warp * 32 * kOutPad;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        *reinterpret_cast<float4*>(so + lane * kOutPad + 4 * q) =
+                            make_float4(v[4 * q] + sbias[cl + 4 * q], v[4 * q + 1] + sbias[cl + 4 * q + 1],
+                                        v[4 * q + 2] + sbias[cl + 4 * q + 2], v[4 * q + 3] + sbias[cl + 4 * q + 3]);
+                    __syncwarp();
+                    // Four rounds of eight rows x 64 contiguous bytes.
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int rr = 8 * q + (lane >> 2), cc = 4 * (lane & 3);
+                        *reinterpret_cast<float4*>(g.out_f + (size_t)(r0 + rr) * g.ld_f + cg + cc) =
+                            *reinterpret_cast<const float4*>(so + rr * kOutPad + cc);
+                    }
+                    __syncwarp();
+                } else {  // kBackward
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        __align__(16) __nv_bfloat16 a[8];
+                        *reinterpret_cast<uint4*>(a) = pa[ci][hh];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            if (!(__bfloat162float(a[k]) > 0.f)) v[8 * hh + k] = 0.f;
+                    }
+                    store_row16(g.out_t, r, cg, g.RA, v);
+                    store_T_warp(g.out_tT, r0, cg, 256, v, stile[warp]);
+                    // Bias-gradient partial of these 32 rows: row r0 / 32 of
+                    // the partials, each element written by one warp.
+                    const float cs = warp_colsum16(v);
+                    if (lane < 16) g.out_f[(size_t)(r0 >> 5) * 256 + cg + lane] = cs;
+                }
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+            if (u + (int)gridDim.x < g.units) load_mask(u + gridDim.x);
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
 // ---------------------------------------------------------------------------
@@ -506,6 +712,7 @@ struct stp_mlp {
     float* T = nullptr;       // staged targets [max_batch][130]
     float* Yout = nullptr;    // [max_batch][160]
     int* err = nullptr;
+    int nsm = 0;              // SMs of the device (persistent product grid)
     int step = 0;
     bool profiling = false;
     cudaEvent_t ev[2]{};
@@ -527,33 +734,57 @@ stp_status fail(stp_mlp* m, stp_status st, const std::string& msg) {
         if (e_ != cudaSuccess) return fail((m), STP_ERR_CUDA, cudaGetErrorString(e_)); \
     } while (0)
 
-constexpr int kSplitMax = 64;
+// Split-K of the weight-gradient products: enough splits for one CTA per SM
+// over the two 128-row output tiles, at least four K stages each.
+constexpr int kSplitMax = 80;
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-template <int N, int MODE>
-cudaError_t launch_gemm(const GemmArgs& g, int mtiles, int splits, cudaStream_t st) {
-    constexpr int smem = stages_for(MODE) * (kTileM * kStageK * 2 + N * kStageK * 2) + 1024;
+template <int N>
+cudaError_t launch_wgrad(const GemmArgs& g, int mtiles, int splits, cudaStream_t st) {
+    constexpr int smem = kWStages * (kTileM * kStageK * 2 + N * kStageK * 2) + 1024;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_wgrad<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_gemm<N, MODE><<<dim3(mtiles, 1, splits), kThreads, smem, st>>>(g);
+    k_gemm_wgrad<N><<<dim3(mtiles, 1, splits), kThreads, smem, st>>>(g);
     return cudaGetLastError();
 }
 
-// Algorithmic HBM bytes of one GEMM: operands read once, outputs written once
-// (BF16 tiled and transposed copies, FP32 copies and split-K partials as the
-// mode writes them; the backward mode also reads the forward activation).
-double gemm_bytes(int M, int N, int K, int mode, int splits) {
-    double b = 2.0 * M * K + 2.0 * N * K;
-    if (mode == kHidden) b += 4.0 * M * N;
-    else if (mode == kOutput) b += 4.0 * M * N;
-    else if (mode == kBackward) b += 2.0 * M * N + 4.0 * M * N;
-    else b += 4.0 * M * N * splits;
-    return b;
+template <int NU, int KS, int MODE>
+cudaError_t launch_res(const ResArgs& g, int nsm, cudaStream_t st) {
+    constexpr int smem = res_smem_bytes(NU, KS, MODE);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_res<NU, KS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    // Even grid (a CTA keeps one column half), at most one CTA per SM.
+    const int grid = std::max(2, std::min(g.units, nsm & ~1));
+    k_gemm_res<NU, KS, MODE><<<grid, kResThreads, smem, st>>>(g);
+    return cudaGetLastError();
+}
+
+// Bias-gradient partials per layer: the input-gradient products write one
+// row per 32 batch rows, the loss kernel (last layer) one per 128.
+size_t bpart_stride(int Bp_max) { return (size_t)(Bp_max / 32) * kOutP; }
+
+// Algorithmic HBM bytes of one product of a training step at batch B over the
+// layer's logical shape (in x out, no padding): every operand read once,
+// every output written once in one layout (BF16 activations and input
+// gradients, FP32 network outputs and weight gradients); the input-gradient
+// product also reads the forward activation for the ReLU mask. The second
+// (transposed) BF16 copy of each activation, the padding and the split-K
+// partials are this design's choices and are not counted.
+double alg_bytes(int B, int in, int out, int mode) {
+    const double b = B, i = in, o = out;
+    if (mode == kHidden) return 2 * b * i + 2 * i * o + 2 * b * o;
+    if (mode == kOutput) return 2 * b * i + 2 * i * o + 4 * b * o;
+    if (mode == kWGrad) return 2 * b * o + 2 * b * i + 4 * i * o;
+    return 2 * b * o + 2 * i * o + 2 * b * i + 2 * b * i;  // kBackward
 }
 
 struct Timer {
@@ -585,25 +816,26 @@ stp_status forward_impl(stp_mlp* m, int B) {
     }
     const __nv_bfloat16* in = m->xt;
     for (int l = 0; l < 4; ++l) {
-        GemmArgs g{};
+        const Layer& L = kLayers[l];
+        ResArgs g{};
         g.A = in;
         g.RA = Bp;
         g.B = m->wt[l];
-        g.KT = kLayers[l].in / kStageK;
-        g.kt_per_split = g.KT;
+        g.NB = L.out;
+        g.units = 2 * mt;
         g.bias = m->b[l];
         g.err = m->err;
-        Timer t(m, 2.0 * Bp * kLayers[l].in * kLayers[l].out,
-                gemm_bytes(Bp, kLayers[l].out, kLayers[l].in, l < 3 ? kHidden : kOutput, 1));
+        Timer t(m, 2.0 * B * L.in_used * L.out_used, alg_bytes(B, L.in_used, L.out_used, l < 3 ? kHidden : kOutput));
         if (l < 3) {
             g.out_t = m->ht[l];
             g.out_tT = m->htT[l];
-            MLP_CUDA(m, (launch_gemm<kHid, kHidden>(g, mt, 1, st)));
+            if (l == 0) MLP_CUDA(m, (launch_res<kHid / 2, kInP / kStageK, kHidden>(g, m->nsm, st)));
+            else MLP_CUDA(m, (launch_res<kHid / 2, kHid / kStageK, kHidden>(g, m->nsm, st)));
             in = m->ht[l];
         } else {
             g.out_f = m->y;
             g.ld_f = kOutP;
-            MLP_CUDA(m, (launch_gemm<kOutP, kOutput>(g, mt, 1, st)));
+            MLP_CUDA(m, (launch_res<kOut / 2, kHid / kStageK, kOutput>(g, m->nsm, st)));
         }
         t.stop();
     }
@@ -617,10 +849,11 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
     const int mt = Bp / kTileM;
     cudaStream_t st = m->stream;
     const int KTb = Bp / kStageK;
-    const int splits = std::min(kSplitMax, std::max(1, KTb / 4));
-    const int kps = (KTb + splits - 1) / splits;
+    const int target = std::max(1, std::min({kSplitMax, m->nsm / (kOutP / kTileM), KTb / 4}));
+    const int kps = (KTb + target - 1) / target;
+    const int splits = (KTb + kps - 1) / kps;  // every split non-empty
     *nwpart = splits;
-    *nbpart = mt;
+    *nbpart = Bp / 32;
     for (int l = 3; l >= 0; --l) {
         // weight gradient: dW_l = dT_l^T . act_{l-1}   (M = out, N = in, K = batch)
         GemmArgs g{};
@@ -634,28 +867,28 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
         g.m_valid = kLayers[l].out;
         g.err = m->err;
         {
-            Timer t(m, 2.0 * Bp * kLayers[l].in * kLayers[l].out,
-                    gemm_bytes(kLayers[l].out, kLayers[l].in, Bp, kWGrad, splits));
-            if (l == 0) MLP_CUDA(m, (launch_gemm<kInP, kWGrad>(g, kLayers[l].out / kTileM, splits, st)));
-            else MLP_CUDA(m, (launch_gemm<kHid, kWGrad>(g, kLayers[l].out / kTileM, splits, st)));
+            Timer t(m, 2.0 * B * kLayers[l].in_used * kLayers[l].out_used,
+                    alg_bytes(B, kLayers[l].in_used, kLayers[l].out_used, kWGrad));
+            if (l == 0) MLP_CUDA(m, (launch_wgrad<kInP>(g, kLayers[l].out / kTileM, splits, st)));
+            else MLP_CUDA(m, (launch_wgrad<kHid>(g, kLayers[l].out / kTileM, splits, st)));
             t.stop();
         }
         if (l == 0) break;
         // input gradient: dH_{l-1} = (dT_l . W_l) * relu'(h_{l-1})   (M = batch, N = in, K = out)
-        GemmArgs h{};
+        ResArgs h{};
         h.A = m->dt[l];
         h.RA = Bp;
         h.B = m->wtT[l];
-        h.KT = kLayers[l].out / kStageK;
-        h.kt_per_split = h.KT;
+        h.NB = kLayers[l].in;
+        h.units = 2 * mt;
         h.act = m->ht[l - 1];
         h.out_t = m->dt[l - 1];
         h.out_tT = m->dtT[l - 1];
-        h.out_f = m->bpart + (size_t)(l - 1) * (m->Bp_max / kTileM) * kOutP;
+        h.out_f = m->bpart + (size_t)(l - 1) * bpart_stride(m->Bp_max);
         h.err = m->err;
-        Timer t(m, 2.0 * Bp * kLayers[l].in * kLayers[l].out,
-                gemm_bytes(Bp, kLayers[l].in, kLayers[l].out, kBackward, 1));
-        MLP_CUDA(m, (launch_gemm<kHid, kBackward>(h, mt, 1, st)));
+        Timer t(m, 2.0 * B * kLayers[l].in_used * kLayers[l].out_used,
+                alg_bytes(B, kLayers[l].in_used, kLayers[l].out_used, kBackward));
+        MLP_CUDA(m, (launch_res<kHid / 2, kOutP / kStageK, kBackward>(h, m->nsm, st)));
         t.stop();
     }
     return STP_OK;
@@ -696,8 +929,9 @@ stp_status adam_impl(stp_mlp* m, int nwpart, int nbpart, float lr, bool update, 
         bb.w = m->b[l];
         bb.m = m->mb[l];
         bb.v = m->vb[l];
-        bb.gpart = m->bpart + (size_t)l * (m->Bp_max / kTileM) * kOutP;
-        bb.nparts = nbpart;
+        bb.gpart = m->bpart + (size_t)l * bpart_stride(m->Bp_max);
+        // The loss kernel writes the last layer's partials per 128 rows.
+        bb.nparts = l == 3 ? nbpart / 4 : nbpart;
         bb.rows = L.out;
         bb.cols = 1;
         bb.wt = nullptr;
@@ -750,7 +984,14 @@ stp_status stp_mlp_create(int max_batch, stp_mlp** out) {
     m->max_batch = max_batch;
     const int Bp = (max_batch + kTileM - 1) / kTileM * kTileM;
     m->Bp_max = Bp;
-    const int nbmax = Bp / kTileM;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&m->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || m->nsm < 2) {
+            delete m;
+            return fail(nullptr, STP_ERR_CUDA, "device query failed");
+        }
+    }
     // arena layout
     std::vector<std::pair<void**, size_t>> parts;
     for (int l = 0; l < 4; ++l) {
@@ -776,7 +1017,7 @@ stp_status stp_mlp_create(int max_batch, stp_mlp** out) {
     }
     parts.push_back({(void**)&m->y, (size_t)Bp * kOutP * 4});
     parts.push_back({(void**)&m->wpart, (size_t)4 * kSplitMax * kOutP * kHid * 4});
-    parts.push_back({(void**)&m->bpart, (size_t)4 * nbmax * kOutP * 4});
+    parts.push_back({(void**)&m->bpart, (size_t)4 * bpart_stride(Bp) * 4});
     parts.push_back({(void**)&m->gsum, (size_t)4 * (kOutP * kHid + kOutP) * 4});
     parts.push_back({(void**)&m->loss, (size_t)Bp * 4});
     parts.push_back({(void**)&m->X, (size_t)max_batch * kIn * 4});
@@ -885,7 +1126,7 @@ static stp_status loss_grad(stp_mlp* m, int B, const float* X, const float* T, i
     if ((s = stage_in(m, m->T, T, (size_t)B * kTgt, flags)) != STP_OK) return s;
     if ((s = forward_impl(m, B)) != STP_OK) return s;
     const int Bp = (B + kTileM - 1) / kTileM * kTileM;
-    k_loss<<<Bp / 128, 128, 0, m->stream>>>(m->y, m->T, B, Bp, m->bpart + (size_t)3 * (m->Bp_max / kTileM) * kOutP,
+    k_loss<<<Bp / 128, 128, 0, m->stream>>>(m->y, m->T, B, Bp, m->bpart + (size_t)3 * bpart_stride(m->Bp_max),
                                             m->dt[3], m->dtT[3], m->loss);
     MLP_CUDA(m, cudaGetLastError());
     return backward_impl(m, B, nw, nb);

@@ -66,12 +66,19 @@ static cudaError_t launch_v(const Geom<R>& g, const EdgeBatch<R>& e, int grid_bl
     return cudaGetLastError();
 }
 
+// Obstacle chunk per pass: FP32 keeps at most 16 obstacles in registers
+// (128 registers, two CTAs per SM; more obstacles take more passes, each
+// repeating the forward kinematics), FP64 up to 32.
 template <typename R, bool ARM, bool CLEAR, bool EARLY>
 static cudaError_t launch_mo(const Geom<R>& g, const EdgeBatch<R>& e, int grid_blocks, cudaStream_t st) {
     if (CLEAR) return launch_v<R, ARM, 16, CLEAR, EARLY>(g, e, grid_blocks, st);
     if (g.M <= 8) return launch_v<R, ARM, 8, CLEAR, EARLY>(g, e, grid_blocks, st);
-    if (g.M <= 16) return launch_v<R, ARM, 16, CLEAR, EARLY>(g, e, grid_blocks, st);
-    return launch_v<R, ARM, 32, CLEAR, EARLY>(g, e, grid_blocks, st);
+    if constexpr (sizeof(R) == 4) {
+        return launch_v<R, ARM, 16, CLEAR, EARLY>(g, e, grid_blocks, st);
+    } else {
+        if (g.M <= 16) return launch_v<R, ARM, 16, CLEAR, EARLY>(g, e, grid_blocks, st);
+        return launch_v<R, ARM, 32, CLEAR, EARLY>(g, e, grid_blocks, st);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -434,7 +434,7 @@ __device__ __forceinline__ int block_scan_excl(int v, int* sh, int* total) {
 }
 
 // Edges per shared-memory window in the large-batch mode.
-constexpr int kWin = 256;
+constexpr int kWin = 64;
 
 // Kernel body: G and E may live in registers/parameters (single problem) or in
 // shared memory (batch); smem_raw is the dynamic shared-memory buffer.
@@ -551,12 +551,19 @@ __device__ __forceinline__ void validate_body(const Geom<R>& G, const EdgeBatch<
         }
     } else {
         // Large batches (precomputed offsets in global memory): CTAs take
-        // windows of kWin consecutive edges, stage the window's offsets in
-        // shared memory and spread its check points over their warps.
+        // windows of kWin consecutive edges (from the window counter as they
+        // finish the previous one, so the batch ends within one window of
+        // balance; or round-robin without a counter), stage the window's
+        // offsets in shared memory and spread its check points over their warps.
         long long* woff = reinterpret_cast<long long*>(smem_raw + G.blob_bytes);
-        for (int w0 = cta * kWin; w0 < n; w0 += ncta * kWin) {
-            const int wn = min(kWin, n - w0);
+        __shared__ int s_win;
+        for (int k = 0;; ++k) {
+            __syncthreads();   // the previous window's offsets are no longer read
+            if (threadIdx.x == 0) s_win = E.win_next ? atomicAdd(E.win_next, 1) : cta + k * ncta;
             __syncthreads();
+            if (s_win >= (n + kWin - 1) / kWin) break;
+            const int w0 = s_win * kWin;
+            const int wn = min(kWin, n - w0);
             for (int i = threadIdx.x; i <= wn; i += blockDim.x) woff[i] = E.off[w0 + i];
             __syncthreads();
             const long long ob = woff[0], oe = woff[wn];
