@@ -6,24 +6,29 @@
 // the method's GPU form). Weights are BF16 copies of FP32 master weights; every
 // product accumulates in FP32.
 //
-// GEMM: D[M x N] = A[M x K] . B[N x K]^T with A and B K-major BF16 in the
-// canonical no-swizzle tile order (8-row x 16-byte core matrices), so that a
-// 128-row x 64-column stage of A, and the N x 64 stage of B, are contiguous in
-// HBM and move into shared memory with one bulk asynchronous copy each
-// (cp.async.bulk, completion on an mbarrier). One elected thread issues
-// tcgen05.mma (kind::f16, M = 128, N <= 256, K = 16 per instruction) into a
-// TMEM accumulator of FP32 columns; tcgen05.commit releases a stage when its
-// MMAs have read it; warps read the accumulator back with tcgen05.ld (warp w
-// owns TMEM lanes 32 (w % 4) .. + 31 = tile rows) into a fused epilogue.
+// GEMM: D[M x N] = A[M x K] . B[N x K]^T, BF16 operands in the canonical
+// no-swizzle tile order of the tensor cores (core matrices of 8 rows x 16
+// bytes), FP32 accumulation in TMEM. Every BF16 matrix [R][K] (activations,
+// their gradients, weights) is stored once, tiled: element (r, k) sits at
+//   (((k / BW) * (R / 8) + r / 8) * (BW / 8) + (k % BW) / 8) * 64 + (r % 8) * 8 + k % 8
+// with column blocks of BW = 128 (BW = 64 for the 64-wide input): the BW / 8
+// core matrices of one 8-row group and one column block are consecutive, then
+// the row groups, then the column blocks. So a 128-row x BW stage is one
+// contiguous block for a K-major operand (the forward products and the input
+// gradients, K = features), and the 64 rows of one column block are one
+// contiguous block for an MN-major operand (the weight gradients, K = batch,
+// which read the same activations without a transposed copy). Stages move
+// into shared memory by bulk asynchronous copies (cp.async.bulk, completion
+// on an mbarrier); one elected thread issues tcgen05.mma (kind::f16, M = 128,
+// K = 16 per instruction) and tcgen05.commit releases a stage when its MMAs
+// have read it; warps read the accumulator back with tcgen05.ld (warp w owns
+// TMEM lanes 32 (w % 4) .. + 31 = tile rows) into a fused epilogue.
 // Two kernels: the products over K <= 256 (forward layers: bias + ReLU with
-// BF16 stores in both operand layouts, or bias with FP32 stores for the
-// output layer; input gradients: ReLU mask, BF16 stores and bias-gradient
-// partials) run persistent with the weight operand resident in shared memory
+// BF16 stores, or bias with FP32 stores for the output layer; input
+// gradients: ReLU mask, BF16 stores and bias-gradient partials) run
+// persistent with the weight operand resident in shared memory
 // (k_gemm_res); the weight gradients (K = batch) run split-K with FP32
 // partials (k_gemm_wgrad).
-//
-// Element (r, k) of a tiled [R][K] matrix (R % 8 == 0, K % 64 == 0) sits at
-//   (((k / 64) * (R / 8) + r / 8) * 8 + (k % 64) / 8) * 64 + (r % 8) * 8 + k % 8.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -53,17 +58,25 @@ constexpr float kSMin = -7.f, kSMax = 2.f;
 
 enum Mode { kHidden = 0, kOutput = 1, kBackward = 2, kWGrad = 3 };
 
-__host__ __device__ inline size_t tix(int r, int k, int R) {
-    return ((((size_t)(k >> 6) * (size_t)(R >> 3) + (size_t)(r >> 3)) * 8 + (size_t)((k >> 3) & 7)) << 6) +
+// Tiled index (layout above) with column blocks of 1 << lbw (lbw 6 or 7).
+__host__ __device__ inline size_t tixb(int r, int k, int R, int lbw) {
+    const int cpb = 1 << (lbw - 3);  // core matrices per 8-row group and block
+    return ((((size_t)(k >> lbw) * (size_t)(R >> 3) + (size_t)(r >> 3)) * (size_t)cpb +
+             (size_t)((k >> 3) & (cpb - 1)))
+            << 6) +
            (size_t)((r & 7) << 3) + (size_t)(k & 7);
 }
+__host__ __device__ constexpr int lbw_of(int K) { return K >= 128 ? 7 : 6; }
+constexpr int kActLbw = 7;  // the 256-wide activations and gradients
 
 // ---------------------------------------------------------------------------
 // tcgen05 / TMEM helpers (inline PTX).
 // ---------------------------------------------------------------------------
 // Shared-memory matrix descriptor: start address, leading-dimension byte
-// offset (between core matrices along K), stride-dimension byte offset
-// (between 8-row groups), descriptor version 1, no swizzle.
+// offset (between core matrices adjacent along K), stride-dimension byte
+// offset (between core matrices adjacent along M or N), descriptor version 1,
+// no swizzle. A K-major core matrix holds 8 rows (M or N) of 16 bytes of K;
+// an MN-major one holds 8 rows of K of 16 bytes of M or N.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
@@ -72,6 +85,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// The same with A and B MN-major (bit 15: A, bit 16: B).
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N) {
+    return idesc_bf16(M, N) | (1u << 15) | (1u << 16);
 }
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
@@ -109,10 +126,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 struct GemmArgs {
-    const __nv_bfloat16* A;  // tiled [RA][K]
-    int RA;
-    const __nv_bfloat16* B;  // tiled [N][K]
-    int KT;                  // 64-wide K stages in total
+    const __nv_bfloat16* A;  // output gradient, tiled [RA][256] (M = its columns)
+    int RA;                  // batch rows (multiple of 128)
+    const __nv_bfloat16* B;  // layer input, tiled [RA][N] (N = its columns)
+    int KT;                  // 64-row K stages (batch) in total
     int kt_per_split;        // split-K (blockIdx.z): stages [z*kps, min(KT, (z+1)*kps))
     float* out_f;            // FP32 partials [splits][m_valid][ld_f]
     int ld_f;
@@ -120,36 +137,16 @@ struct GemmArgs {
     int* err;
 };
 
-// BF16 stores of 16 consecutive columns c0..c0+15 of row r into a tiled
-// [R][N] matrix (two 16-byte stores).
+// BF16 stores of 16 consecutive columns c0..c0+15 (c0 % 16 == 0) of row r
+// into a tiled [R][256] activation (two 16-byte stores).
 __device__ __forceinline__ void store_row16(__nv_bfloat16* t, int r, int c0, int R, const float (&v)[16]) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         __align__(16) __nv_bfloat16 b[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) b[i] = __float2bfloat16_rn(v[8 * h + i]);
-        *reinterpret_cast<uint4*>(t + tix(r, c0 + 8 * h, R)) = *reinterpret_cast<const uint4*>(b);
+        *reinterpret_cast<uint4*>(t + tixb(r, c0 + 8 * h, R, kActLbw)) = *reinterpret_cast<const uint4*>(b);
     }
-}
-
-// The same 32 rows x 16 columns block of a warp (lane = row r0 + lane, r0 % 32
-// == 0) into the transposed tiled [N][R] matrix: the warp transposes through
-// its 1 KB shared-memory tile sbuf [16][32] and writes 64 rows of 16 bytes
-// (8 consecutive r of one column each). All 32 lanes must call it.
-__device__ __forceinline__ void store_T_warp(__nv_bfloat16* tT, int r0, int c0, int N, const float (&v)[16],
-                                             __nv_bfloat16* sbuf) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int c = 0; c < 16; ++c) sbuf[c * 32 + lane] = __float2bfloat16_rn(v[c]);
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int rho = lane + 32 * k;
-        const int c = rho >> 2, rg = rho & 3;
-        const uint4 val = *reinterpret_cast<const uint4*>(sbuf + c * 32 + rg * 8);
-        *reinterpret_cast<uint4*>(tT + tix(c0 + c, r0 + rg * 8, N)) = val;
-    }
-    __syncwarp();
 }
 
 // Column sums over the 32 lanes of 16 per-lane values by recursive halving:
@@ -173,13 +170,29 @@ __device__ __forceinline__ float warp_colsum16(float (&v)[16]) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
-template <int N>
+// Weight gradient dW = dT^T . X: M = 128 output features (column block
+// blockIdx.x of dT), N = the layer's input features, K = the batch rows of
+// split blockIdx.z. Both operands are MN-major: a stage is 64 batch rows, so
+// A is one contiguous 16 KB piece of dT's column block and B one piece of 8
+// row groups per column block of X (one MMA of N = BW per block and K step).
+// The dynamic shared memory ends with a guard region so that every
+// descriptor-addressed read stays inside the allocation.
+template <int N, int LBWB>
+__host__ __device__ constexpr int wgrad_smem_bytes() {
+    return 1024 + kWStages * (kTileM * kStageK * 2 + N * kStageK * 2) + 21 * 2048 + 256 - (1 << LBWB) * kStageK * 2;
+}
+template <int N, int LBWB>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_wgrad(GemmArgs g) {
     constexpr int kStages = kWStages;
+    constexpr int kBW = 1 << LBWB;                      // B column block
+    constexpr int kNB = N / kBW;                        // B blocks (MMAs per K step)
     constexpr uint32_t kABytes = kTileM * kStageK * 2;  // 16 KB
-    constexpr uint32_t kBBytes = N * kStageK * 2;
+    constexpr uint32_t kBBlk = kBW * kStageK * 2;
+    constexpr uint32_t kBBytes = kNB * kBBlk;
     constexpr uint32_t kTmemCols = N < 32 ? 32 : N;
-    constexpr uint32_t kIdesc = idesc_bf16(kTileM, N);
+    constexpr uint32_t kIdesc = idesc_bf16_mn(kTileM, kBW);
+    constexpr uint32_t kALbo = 16 * 128, kBLbo = (kBW / 8) * 128;  // one 8-row group of a column block
+    static_assert(N % kBW == 0, "whole column blocks");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_base_sh;
@@ -211,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_wgrad(GemmArgs g) {
 
     // Producer + MMA issuer: one thread, prefetch distance kStages - 1.
     if (tid == 0 && nk > 0) {
-        const int rgA = g.RA >> 3;
+        const size_t rg = (size_t)(g.RA >> 3);
         int issued = 0, consumed = 0;
         bool ok = true;
         for (int it = 0; it < nk + kStages - 1 && ok; ++it) {
@@ -219,12 +232,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_wgrad(GemmArgs g) {
                 const int s = it % kStages;
                 if (it >= kStages) ok = mbar_wait(&empty[s], ((it / kStages) - 1) & 1);
                 if (!ok) break;
-                const int kt = kt0 + it;
-                const __nv_bfloat16* srcA = g.A + ((size_t)kt * rgA + (size_t)(m0 >> 3)) * 512;
-                const __nv_bfloat16* srcB = g.B + (size_t)kt * (size_t)(N >> 3) * 512;
+                const size_t kg = (size_t)(kt0 + it) * (kStageK / 8);  // first 8-row group of the stage
                 mbar_expect_tx(&full[s], kABytes + kBBytes);
-                bulk_g2s(sA + s * kABytes, srcA, kABytes, &full[s]);
-                bulk_g2s(sB + s * kBBytes, srcB, kBBytes, &full[s]);
+                bulk_g2s(sA + s * kABytes, g.A + (((size_t)blockIdx.x * rg + kg) * 16) * 64, kABytes, &full[s]);
+#pragma unroll
+                for (int nb = 0; nb < kNB; ++nb)
+                    bulk_g2s(sB + s * kBBytes + nb * kBBlk, g.B + (((size_t)nb * rg + kg) * (kBW / 8)) * 64, kBBlk,
+                             &full[s]);
                 ++issued;
             }
             const int j = it - (kStages - 1);
@@ -236,9 +250,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_wgrad(GemmArgs g) {
                 const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
 #pragma unroll
                 for (int ks = 0; ks < kStageK / 16; ++ks) {
-                    const uint64_t da = smem_desc(a0 + ks * 256, 128, 1024);
-                    const uint64_t db = smem_desc(b0 + ks * 256, 128, 1024);
-                    mma_bf16(tmem, da, db, kIdesc, (j > 0 || ks > 0) ? 1u : 0u);
+                    // K step of 16 batch rows = two 8-row groups.
+                    const uint64_t da = smem_desc(a0 + ks * 2 * kALbo, kALbo, 128);
+#pragma unroll
+                    for (int nb = 0; nb < kNB; ++nb) {
+                        const uint64_t db = smem_desc(b0 + nb * kBBlk + ks * 2 * kBLbo, kBLbo, 128);
+                        mma_bf16(tmem + (uint32_t)(nb * kBW), da, db, kIdesc, (j > 0 || ks > 0) ? 1u : 0u);
+                    }
                 }
                 mma_commit(&empty[s]);
                 ++consumed;
@@ -308,12 +326,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_wgrad(GemmArgs g) {
 // the copy issuer waits (bounded) for its copies in flight before the CTA
 // frees its TMEM and exits.
 // ---------------------------------------------------------------------------
-constexpr int kRing = 8, kResThreads = 320, kEpiWarps = 8;
-constexpr uint32_t kAStage = kTileM * kStageK * 2;  // 16 KB
-constexpr int kOutPad = 20;                         // FP32 staging row (16 + 4: no bank conflicts)
+constexpr int kRingBytes = 128 * 1024, kResThreads = 320, kEpiWarps = 8;
+constexpr int kOutPad = 20;  // FP32 staging row (16 + 4: no bank conflicts)
 
-__host__ __device__ constexpr int res_smem_bytes(int nu, int ks, int mode) {
-    return 1024 + ks * nu * kStageK * 2 + kRing * (int)kAStage + (mode == kOutput ? kEpiWarps * 32 * kOutPad * 4 : 0);
+// K stage = one column block of A (BW = 1 << lbw wide): 16 or 32 KB.
+__host__ __device__ constexpr int res_smem_bytes(int nu, int kb, int lbw, int mode) {
+    return 1024 + kb * nu * (1 << lbw) * 2 + kRingBytes + (mode == kOutput ? kEpiWarps * 32 * kOutPad * 4 : 0);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -321,24 +339,27 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 struct ResArgs {
-    const __nv_bfloat16* A;    // tiled [RA][KS * 64]
+    const __nv_bfloat16* A;    // tiled [RA][KB * BW]
     int RA;                    // rows of A (multiple of 128)
-    const __nv_bfloat16* B;    // tiled [NB][KS * 64], output column n = row n of B
+    const __nv_bfloat16* B;    // tiled [NB][KB * BW], output column n = row n of B
     int NB;                    // rows of B's tiled layout
     int units;                 // 2 * RA / 128
     const float* bias;         // [2 NU] (forward modes)
     const __nv_bfloat16* act;  // kBackward: forward activation, tiled [RA][256]
     __nv_bfloat16* out_t;      // tiled [RA][256]
-    __nv_bfloat16* out_tT;     // tiled [256][RA]
     float* out_f;              // kOutput: FP32 [RA][ld_f]; kBackward: bias-gradient partials [RA / 32][256]
     int ld_f;
     int* err;
 };
 
-template <int NU, int KS, int MODE>
+template <int NU, int KB, int LBW, int MODE>
 __global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
-    static_assert(NU % 16 == 0 && NU <= 128 && KS >= 1 && KS <= 4, "unit shape");
-    constexpr uint32_t kBBytes = NU * kStageK * 2;  // one K stage of the resident half
+    static_assert(NU % 16 == 0 && NU <= 128 && KB >= 1 && KB <= 2 && (LBW == 6 || LBW == 7), "unit shape");
+    constexpr int kBW = 1 << LBW;
+    constexpr uint32_t kAStage = kTileM * kBW * 2;  // one column block of a 128-row tile
+    constexpr int kRing = kRingBytes / (int)kAStage;
+    constexpr uint32_t kBBytes = NU * kBW * 2;      // one column block of the resident half
+    constexpr uint32_t kSbo = (kBW / 8) * 128;      // between 8-row groups
     constexpr uint32_t kIdesc = idesc_bf16(kTileM, NU);
     constexpr int kChunks = NU / 16;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -346,11 +367,10 @@ __global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
     __shared__ float sbias[NU];
-    __shared__ __align__(16) __nv_bfloat16 stile[kEpiWarps][16 * 32];
 
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sB = smem;
-    unsigned char* sA = smem + KS * kBBytes;
+    unsigned char* sA = smem + KB * kBBytes;
     float* sOut = reinterpret_cast<float*>(sA + kRing * kAStage);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int h = blockIdx.x & 1;
@@ -383,22 +403,23 @@ __global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
     if (warp == kEpiWarps) {
         // Copy issuer.
         if (lane == 0) {
-            mbar_expect_tx(&bfull, KS * kBBytes);
-            for (int kt = 0; kt < KS; ++kt)
-                bulk_g2s(sB + kt * kBBytes, g.B + ((size_t)kt * (g.NB >> 3) + (size_t)h * (NU >> 3)) * 512, kBBytes,
-                         &bfull);
+            mbar_expect_tx(&bfull, KB * kBBytes);
+            for (int kb = 0; kb < KB; ++kb)
+                bulk_g2s(sB + kb * kBBytes,
+                         g.B + (((size_t)kb * (g.NB >> 3) + (size_t)h * (NU >> 3)) * (kBW / 8)) * 64, kBBytes, &bfull);
             const size_t rgA = (size_t)(g.RA >> 3);
             int it = 0;
             for (int u = blockIdx.x; u < g.units && !abort_sh; u += gridDim.x) {
                 const int t = u >> 1;
-                for (int kt = 0; kt < KS; ++kt, ++it) {
+                for (int kb = 0; kb < KB; ++kb, ++it) {
                     const int s = it % kRing;
                     if (it >= kRing && !mbar_wait(&empty[s], ((it / kRing) - 1) & 1)) {
                         fail();
                         break;
                     }
                     mbar_expect_tx(&full[s], kAStage);
-                    bulk_g2s(sA + s * kAStage, g.A + ((size_t)kt * rgA + (size_t)t * (kTileM >> 3)) * 512, kAStage,
+                    bulk_g2s(sA + s * kAStage,
+                             g.A + (((size_t)kb * rgA + (size_t)t * (kTileM >> 3)) * (kBW / 8)) * 64, kAStage,
                              &full[s]);
                 }
             }
@@ -424,7 +445,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
                 }
                 fence_after_sync();
                 const uint32_t d = tmem + (uint32_t)(b * 128);
-                for (int kt = 0; kt < KS; ++kt, ++it) {
+                for (int kb = 0; kb < KB; ++kb, ++it) {
                     const int s = it % kRing;
                     if (!mbar_wait(&full[s], (it / kRing) & 1)) {
                         fail();
@@ -432,11 +453,11 @@ __global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
                         break;
                     }
                     fence_after_sync();
-                    const uint32_t a0 = smem_u32(sA + s * kAStage), b0 = smem_u32(sB + kt * kBBytes);
+                    const uint32_t a0 = smem_u32(sA + s * kAStage), b0 = smem_u32(sB + kb * kBBytes);
 #pragma unroll
-                    for (int ks = 0; ks < kStageK / 16; ++ks)
-                        mma_bf16(d, smem_desc(a0 + ks * 256, 128, 1024), smem_desc(b0 + ks * 256, 128, 1024), kIdesc,
-                                 (kt > 0 || ks > 0) ? 1u : 0u);
+                    for (int ks = 0; ks < kBW / 16; ++ks)
+                        mma_bf16(d, smem_desc(a0 + ks * 256, 128, kSbo), smem_desc(b0 + ks * 256, 128, kSbo), kIdesc,
+                                 (kb > 0 || ks > 0) ? 1u : 0u);
                     mma_commit(&empty[s]);
                 }
                 mma_commit(&tfull[b]);
@@ -462,7 +483,8 @@ __global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
                     if (c < kChunks) {
 #pragma unroll
                         for (int hh = 0; hh < 2; ++hh)
-                            pa[ci][hh] = *reinterpret_cast<const uint4*>(g.act + tix(rr, h * NU + 16 * c + 8 * hh, g.RA));
+                            pa[ci][hh] = *reinterpret_cast<const uint4*>(
+                                g.act + tixb(rr, h * NU + 16 * c + 8 * hh, g.RA, kActLbw));
                     }
                 }
             }
@@ -491,7 +513,6 @@ __global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
 #pragma unroll
                     for (int k = 0; k < 16; ++k) v[k] = fmaxf(v[k] + sbias[cl + k], 0.f);
                     store_row16(g.out_t, r, cg, g.RA, v);
-                    store_T_warp(g.out_tT, r0, cg, 256, v, stile[warp]);
                 } else if constexpr (MODE == kOutput) {
                     float* so = sOut + warp * 32 * kOutPad;
 #pragma unroll
@@ -518,7 +539,6 @@ __global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
                             if (!(__bfloat162float(a[k]) > 0.f)) v[8 * hh + k] = 0.f;
                     }
                     store_row16(g.out_t, r, cg, g.RA, v);
-                    store_T_warp(g.out_tT, r0, cg, 256, v, stile[warp]);
                     // Bias-gradient partial of these 32 rows: row r0 / 32 of
                     // the partials, each element written by one warp.
                     const float cs = warp_colsum16(v);
@@ -539,20 +559,18 @@ __global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
 // ---------------------------------------------------------------------------
 // Elementwise kernels.
 // ---------------------------------------------------------------------------
-// FP32 features [B][32] -> BF16 tiled [Bp][64] and [64][Bp] (zero padded).
-__global__ void k_pack_input(const float* __restrict__ X, int B, int Bp, __nv_bfloat16* xt, __nv_bfloat16* xtT) {
+// FP32 features [B][32] -> BF16 tiled [Bp][64] (zero padded).
+__global__ void k_pack_input(const float* __restrict__ X, int B, int Bp, __nv_bfloat16* xt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Bp * kInP) return;
     const int r = i / kInP, c = i % kInP;
     const float v = (r < B && c < kIn) ? X[(size_t)r * kIn + c] : 0.f;
-    const __nv_bfloat16 b = __float2bfloat16_rn(v);
-    xt[tix(r, c, Bp)] = b;
-    xtT[tix(c, r, kInP)] = b;
+    xt[tixb(r, c, Bp, lbw_of(kInP))] = __float2bfloat16_rn(v);
 }
 
 // Per-sample loss (mixture NLL of tau + masked waypoint MSE) and dL/dy / B.
 __global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ T, int B, int Bp, float* bpart,
-                       __nv_bfloat16* dyt, __nv_bfloat16* dytT, float* loss) {
+                       __nv_bfloat16* dyt, float* loss) {
     // Bp is a multiple of the 128-thread block: every thread has a row.
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     float g[kOutP];
@@ -605,7 +623,6 @@ __global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ T,
         L += mse / cnt;
         loss[n] = L;
     }
-    __shared__ __align__(16) __nv_bfloat16 stile[4][16 * 32];
     __shared__ float sb[kOutP];
     for (int i = threadIdx.x; i < kOutP; i += blockDim.x) sb[i] = 0.f;
     __syncthreads();
@@ -614,7 +631,6 @@ __global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ T,
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = g[c0 + i];
         store_row16(dyt, n, c0, Bp, v);
-        store_T_warp(dytT, n & ~31, c0, kOutP, v, stile[threadIdx.x >> 5]);
         const float cs = warp_colsum16(v);
         if ((threadIdx.x & 31) < 16) atomicAdd(&sb[c0 + (threadIdx.x & 31)], cs);
     }
@@ -658,8 +674,8 @@ __global__ void k_adam(AdamArgs a) {
     }
     if (a.wt) {
         const __nv_bfloat16 b = __float2bfloat16_rn(w);
-        a.wt[tix(r, c, a.rows)] = b;
-        a.wtT[tix(c, r, a.cols)] = b;
+        a.wt[tixb(r, c, a.rows, lbw_of(a.cols))] = b;
+        a.wtT[tixb(c, r, a.cols, lbw_of(a.rows))] = b;
     }
 }
 
@@ -700,9 +716,9 @@ struct stp_mlp {
     float *mw[4]{}, *vw[4]{}, *mb[4]{}, *vb[4]{};
     __nv_bfloat16 *wt[4]{}, *wtT[4]{};
     // activations (tiled BF16 in both layouts), FP32 buffers
-    __nv_bfloat16 *xt = nullptr, *xtT = nullptr;
-    __nv_bfloat16 *ht[3]{}, *htT[3]{};
-    __nv_bfloat16 *dt[4]{}, *dtT[4]{};  // gradient wrt layer outputs (dt[3] = dY)
+    __nv_bfloat16* xt = nullptr;
+    __nv_bfloat16* ht[3]{};
+    __nv_bfloat16* dt[4]{};  // gradient wrt layer outputs (dt[3] = dY)
     float* y = nullptr;       // [Bp][256]
     float* wpart = nullptr;   // weight-gradient partials
     float* bpart = nullptr;   // bias-gradient partials [4][Bp/128][256]
@@ -740,31 +756,32 @@ constexpr int kSplitMax = 80;
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-template <int N>
+template <int N, int LBWB>
 cudaError_t launch_wgrad(const GemmArgs& g, int mtiles, int splits, cudaStream_t st) {
-    constexpr int smem = kWStages * (kTileM * kStageK * 2 + N * kStageK * 2) + 1024;
+    constexpr int smem = wgrad_smem_bytes<N, LBWB>();
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_wgrad<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_wgrad<N, LBWB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_gemm_wgrad<N><<<dim3(mtiles, 1, splits), kThreads, smem, st>>>(g);
+    k_gemm_wgrad<N, LBWB><<<dim3(mtiles, 1, splits), kThreads, smem, st>>>(g);
     return cudaGetLastError();
 }
 
-template <int NU, int KS, int MODE>
+template <int NU, int KB, int LBW, int MODE>
 cudaError_t launch_res(const ResArgs& g, int nsm, cudaStream_t st) {
-    constexpr int smem = res_smem_bytes(NU, KS, MODE);
+    constexpr int smem = res_smem_bytes(NU, KB, LBW, MODE);
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_res<NU, KS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_gemm_res<NU, KB, LBW, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     // Even grid (a CTA keeps one column half), at most one CTA per SM.
     const int grid = std::max(2, std::min(g.units, nsm & ~1));
-    k_gemm_res<NU, KS, MODE><<<grid, kResThreads, smem, st>>>(g);
+    k_gemm_res<NU, KB, LBW, MODE><<<grid, kResThreads, smem, st>>>(g);
     return cudaGetLastError();
 }
 
@@ -811,7 +828,7 @@ stp_status forward_impl(stp_mlp* m, int B) {
     cudaStream_t st = m->stream;
     {
         const int n = Bp * kInP;
-        k_pack_input<<<(n + 255) / 256, 256, 0, st>>>(m->X, B, Bp, m->xt, m->xtT);
+        k_pack_input<<<(n + 255) / 256, 256, 0, st>>>(m->X, B, Bp, m->xt);
         MLP_CUDA(m, cudaGetLastError());
     }
     const __nv_bfloat16* in = m->xt;
@@ -828,21 +845,20 @@ stp_status forward_impl(stp_mlp* m, int B) {
         Timer t(m, 2.0 * B * L.in_used * L.out_used, alg_bytes(B, L.in_used, L.out_used, l < 3 ? kHidden : kOutput));
         if (l < 3) {
             g.out_t = m->ht[l];
-            g.out_tT = m->htT[l];
-            if (l == 0) MLP_CUDA(m, (launch_res<kHid / 2, kInP / kStageK, kHidden>(g, m->nsm, st)));
-            else MLP_CUDA(m, (launch_res<kHid / 2, kHid / kStageK, kHidden>(g, m->nsm, st)));
+            if (l == 0) MLP_CUDA(m, (launch_res<kHid / 2, 1, lbw_of(kInP), kHidden>(g, m->nsm, st)));
+            else MLP_CUDA(m, (launch_res<kHid / 2, 2, kActLbw, kHidden>(g, m->nsm, st)));
             in = m->ht[l];
         } else {
             g.out_f = m->y;
             g.ld_f = kOutP;
-            MLP_CUDA(m, (launch_res<kOut / 2, kHid / kStageK, kOutput>(g, m->nsm, st)));
+            MLP_CUDA(m, (launch_res<kOut / 2, 2, kActLbw, kOutput>(g, m->nsm, st)));
         }
         t.stop();
     }
     return STP_OK;
 }
 
-// Backward from dY (already in dt[3] / dtT[3], its bias partials written by
+// Backward from dY (already in dt[3], its bias partials written by
 // the loss kernel) to every parameter's gradient partials.
 stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
     const int Bp = (B + kTileM - 1) / kTileM * kTileM;
@@ -857,9 +873,9 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
     for (int l = 3; l >= 0; --l) {
         // weight gradient: dW_l = dT_l^T . act_{l-1}   (M = out, N = in, K = batch)
         GemmArgs g{};
-        g.A = m->dtT[l];
-        g.RA = kOutP;  // dtT buffers are [256][Bp]
-        g.B = (l == 0) ? m->xtT : m->htT[l - 1];
+        g.A = m->dt[l];
+        g.RA = Bp;
+        g.B = (l == 0) ? m->xt : m->ht[l - 1];
         g.KT = KTb;
         g.kt_per_split = kps;
         g.out_f = m->wpart + (size_t)l * kSplitMax * kOutP * kHid;
@@ -869,8 +885,8 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
         {
             Timer t(m, 2.0 * B * kLayers[l].in_used * kLayers[l].out_used,
                     alg_bytes(B, kLayers[l].in_used, kLayers[l].out_used, kWGrad));
-            if (l == 0) MLP_CUDA(m, (launch_wgrad<kInP>(g, kLayers[l].out / kTileM, splits, st)));
-            else MLP_CUDA(m, (launch_wgrad<kHid>(g, kLayers[l].out / kTileM, splits, st)));
+            if (l == 0) MLP_CUDA(m, (launch_wgrad<kInP, lbw_of(kInP)>(g, kLayers[l].out / kTileM, splits, st)));
+            else MLP_CUDA(m, (launch_wgrad<kHid, kActLbw>(g, kLayers[l].out / kTileM, splits, st)));
             t.stop();
         }
         if (l == 0) break;
@@ -883,12 +899,11 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
         h.units = 2 * mt;
         h.act = m->ht[l - 1];
         h.out_t = m->dt[l - 1];
-        h.out_tT = m->dtT[l - 1];
         h.out_f = m->bpart + (size_t)(l - 1) * bpart_stride(m->Bp_max);
         h.err = m->err;
         Timer t(m, 2.0 * B * kLayers[l].in_used * kLayers[l].out_used,
                 alg_bytes(B, kLayers[l].in_used, kLayers[l].out_used, kBackward));
-        MLP_CUDA(m, (launch_res<kHid / 2, kOutP / kStageK, kBackward>(h, m->nsm, st)));
+        MLP_CUDA(m, (launch_res<kHid / 2, 2, kActLbw, kBackward>(h, m->nsm, st)));
         t.stop();
     }
     return STP_OK;
@@ -1006,14 +1021,11 @@ stp_status stp_mlp_create(int max_batch, stp_mlp** out) {
         parts.push_back({(void**)&m->vb[l], (size_t)kLayers[l].out * 4});
     }
     parts.push_back({(void**)&m->xt, (size_t)Bp * kInP * 2});
-    parts.push_back({(void**)&m->xtT, (size_t)Bp * kInP * 2});
     for (int l = 0; l < 3; ++l) {
         parts.push_back({(void**)&m->ht[l], (size_t)Bp * kHid * 2});
-        parts.push_back({(void**)&m->htT[l], (size_t)Bp * kHid * 2});
     }
     for (int l = 0; l < 4; ++l) {
         parts.push_back({(void**)&m->dt[l], (size_t)Bp * kOutP * 2});
-        parts.push_back({(void**)&m->dtT[l], (size_t)Bp * kOutP * 2});
     }
     parts.push_back({(void**)&m->y, (size_t)Bp * kOutP * 4});
     parts.push_back({(void**)&m->wpart, (size_t)4 * kSplitMax * kOutP * kHid * 4});
@@ -1127,7 +1139,7 @@ static stp_status loss_grad(stp_mlp* m, int B, const float* X, const float* T, i
     if ((s = forward_impl(m, B)) != STP_OK) return s;
     const int Bp = (B + kTileM - 1) / kTileM * kTileM;
     k_loss<<<Bp / 128, 128, 0, m->stream>>>(m->y, m->T, B, Bp, m->bpart + (size_t)3 * bpart_stride(m->Bp_max),
-                                            m->dt[3], m->dtT[3], m->loss);
+                                            m->dt[3], m->loss);
     MLP_CUDA(m, cudaGetLastError());
     return backward_impl(m, B, nw, nb);
 }

@@ -107,13 +107,16 @@ def test_forward_at_maximum_batch_sampled(stp):
     net.close()
 
 
-@pytest.mark.parametrize("B", [37, 300])
+# 37 and 300: one split of the weight-gradient products over a ragged batch;
+# 20000: 314 K stages of 64 batch rows in 63 splits, and 314 work units of the
+# resident-weight products (two or three per CTA).
+@pytest.mark.parametrize("B", [37, 300, 20000])
 def test_gradients_match_oracle(stp, B):
     rng = np.random.default_rng(20 + B)
     P = M.init_params(rng)
     X = _inputs(rng, B)
     T = _targets(rng, X)
-    net = stp.Mlp(512)
+    net = stp.Mlp(max(512, B))
     net.set_params(stp.flatten_params(P))
     loss, g = net.gradients(X, T)
     y, cache = M.forward(P, X, bf16=True)
