@@ -55,10 +55,10 @@ WORKLOAD = "ur5e-6dof-32sph-16obs-recycling-N8-W1024"
 # the two bridge passes together (141.6 + 80.6 KB), averaged over the two
 # intervals. The figure belongs to the kernel source it was taken from: when
 # the source's hash differs, the bench reports no traffic.
-TRAFFIC_CAPTURE = {"kernel": "k_validate", "bytes_per_launch": 229.6e3,
+TRAFFIC_CAPTURE = {"kernel": "k_validate", "bytes_per_launch": 229.0e3,
                    "sources": [os.path.join("paper_2609_30533_gb300", "csrc", f)
                                for f in ("stp_validate.cu", "stp_validate_body.cuh", "stp_internal.cuh")],
-                   "sha256_16": "2e753c4f50acea8b", "profile": "profiles/k_validate_ur5e_plan_ncu.md"}
+                   "sha256_16": "94f810cf14e84a42", "profile": "profiles/k_validate_ur5e_plan_ncu.md"}
 METRIC = "validated space-time edges/s"
 UNIT = "edges/s"
 FLUSH_BYTES = 512 << 20
@@ -781,6 +781,7 @@ def main():
     ap.add_argument("--learned-single", type=int, default=32)
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-micro", action="store_true", help="skip the collision microbenchmarks")
     ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--c0-iters", type=int, default=2000)
     ap.add_argument("--c0-problems", type=int, default=16)
@@ -946,8 +947,13 @@ def main():
                          "note": "the timed plan as one persistent cooperative launch (steps separated by "
                                  "device-wide barriers); step times barrier to barrier on the device timer"}
 
-    micro, peak = microbench(args, P, prob, prm, stream, flush, rank, local)
-    micro7 = microbench_arm7(args, stream, flush, rank, local)
+    if args.no_micro:
+        micro, micro7 = None, None
+        peak = fp32_peak_tflops(torch.cuda.get_device_properties(local).multi_processor_count,
+                                float(_peaks().get("sm_max_mhz", 2070.0)))
+    else:
+        micro, peak = microbench(args, P, prob, prm, stream, flush, rank, local)
+        micro7 = microbench_arm7(args, stream, flush, rank, local)
     batch_result = None if args.no_batch else batched(args, rank)
     learned_result = None if args.no_learned else learned(args, rank)
     sweep_result = None if args.no_sweep else sweep(args, rank)
@@ -1007,7 +1013,7 @@ def main():
         "profiling_error": prof_error,
         "plan_ms_p50": statistics.median(plan_ms),
         "first_solution_ms_p50": statistics.median(fs_ms) if fs_ms else None,
-        "microbench": dict(micro, n_edges=n, peak_tflops=peak),
+        "microbench": dict(micro, n_edges=n, peak_tflops=peak) if micro is not None else None,
         "persistent_single": persistent_single,
         "microbench_arm7": micro7,
     }

@@ -110,10 +110,10 @@ typedef struct {
  *   iters_per_graph  iterations captured per CUDA graph launch; 0 = 8.
  *   t_offset       absolute time of the query's local time 0 (>= 0): obstacle
  *                  trajectories are shifted by it, as when a goal sequence is
- *                  planned query by query (Sec. "Problem Formulation": each
- *                  query resets local time to zero, shifts obstacle
- *                  trajectories by its absolute start time and uses the
- *                  remaining horizon, passed as t_max).
+ *                  planned query by query (Sec. "Problem Formulation": a
+ *                  query starts its own clock at zero, sees the obstacles
+ *                  moved along by the absolute time at which it starts, and
+ *                  gets what is left of the horizon, passed as t_max).
  *   continuous     0 discrete edge validation at edge_res; 1 closed-form
  *                  validation for point robots (arm = 0 only): between the
  *                  edge's end times and the obstacle waypoint times inside

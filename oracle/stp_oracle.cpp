@@ -423,8 +423,9 @@ struct IntervalAlloc {
     std::vector<double> group_measure;
 };
 
-// Each collision-free check k marks [k dt - dt/2, k dt + dt/2] clipped to
-// [L_g, H]; adjacent windows merge into guided windows.
+// A goal check k that finds (q_g, k dt) free contributes the window
+// [k dt - dt/2, k dt + dt/2], cut to [L_g, H]; windows that touch are joined,
+// and the joined windows are the guided windows.
 void build_windows(IntervalAlloc& A, long kmin, long kmax, const char* free_flags) {
     A.windows.clear();
     long k = kmin;
@@ -486,8 +487,9 @@ void partition(IntervalAlloc& A, double U) {
     }
 }
 
-// Group i samples T from its guided portions with probability p_guided (falling
-// back to the uniform interval when they are empty), else from I_i.
+// Group i draws T, with probability p_guided, from the guided pieces of its
+// interval (the uniform interval when there are none), otherwise uniformly
+// from I_i.
 // walk_margin (optional): the smallest |p - len| met while walking the
 // pieces (where a rounding of p would move T across a gap between pieces).
 double sample_goal_time(const IntervalAlloc& A, int g, double u_coin, double u_pos, double p_guided,
@@ -1055,7 +1057,8 @@ void Planner::init_recycling() {
 void Planner::recycle(double U) {
     std::vector<int> rep = recycle_rule(R.slots, U, grid.kmin, prm.dt, [&](long k) { return grid.is_free(k); });
     for (int i : rep) {
-        // Invalidate the old generation and install the empty root (q_g, T_i').
+        // The slot's old tree is retired; a fresh root (q_g, T_i') with no
+        // children takes its place.
         const Slot& s = R.slots[i];
         Node root;
         root.q = P.qg;
@@ -1148,8 +1151,8 @@ Proposal Planner::propose_interval(int k, int w, const std::vector<int>& seg_n, 
         const float tf = (float)T;
         std::memcpy(&rec[9], &tf, sizeof(tf));
     }
-    // Each proposed root is collision-checked at its sampled time; a rejected
-    // root skips the attempt (Algorithm 2).
+    // A new root is checked for collision at the goal time drawn for it; if
+    // it collides, the worker makes no attempt this iteration (Algorithm 2).
     {
         double cl;
         const bool free = state_free(P, P.qg.data(), T, &cl);

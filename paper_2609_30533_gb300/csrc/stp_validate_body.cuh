@@ -1,6 +1,7 @@
 // Edge validation device code (collision checking of space-time edges
-// against moving obstacles; Sec. "Simulation Protocol": obstacle positions
-// are interpolated at each absolute query time), shared by the stand-alone
+// against moving obstacles; Sec. "Simulation Protocol": every check point
+// takes the obstacles where their trajectories put them at its own absolute
+// time), shared by the stand-alone
 // collision kernels and the persistent planner kernel.
 //
 // Mapping: a persistent grid walks the flat list of check points of a batch

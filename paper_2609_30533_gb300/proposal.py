@@ -27,8 +27,12 @@ class Outcome:
     batch_ms: float
 
 
-def plan_batch(problems: Sequence["stp.Problem"], nn_ctas=4, validate_ctas=8, iters_per_graph=16, launch_mode=0,
-               team_ctas=0) -> Outcome:
+def plan_batch(problems: Sequence["stp.Problem"], nn_ctas=4, validate_ctas=8, iters_per_graph=16,
+               launch_mode=stp.STP_LAUNCH_STEPS, team_ctas=0) -> Outcome:
+    """Plan the problems as one batch. The default launch form is the per-step
+    kernels: at the hundreds to thousands of problems planned here they finish
+    the batch sooner than the persistent work queue, and every problem starts
+    at the batch's start, so first-solution times are not queue positions."""
     B = stp.Batch(problems, nn_ctas=nn_ctas, validate_ctas=validate_ctas, iters_per_graph=iters_per_graph,
                   launch_mode=launch_mode, team_ctas=team_ctas)
     ms, stats = B.plan()

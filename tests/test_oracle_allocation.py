@@ -2,8 +2,8 @@
 
 The interval-root partitions are pinned exactly by the worked example drawn in
 Fig. interval-root; the recycling rule by the example drawn in Fig. method and
-the rule that a root at U becomes a donor only after a strict improvement
-(Sec. "Practical Root Recycling").
+the rule that a slot whose root sits exactly at U is recycled only once U
+improves strictly below it (Sec. "Practical Root Recycling").
 """
 import json
 import os

@@ -3,8 +3,8 @@
 Each pin is computed from the paper's definition, by hand or by brute force
 over the oracle's own decision records, so that a plausible slip fails:
 
-* Bridge rank (Algorithm 1; Sec. "Interval Root": connect by arrival time,
-  then space-time distance): hand cases where the earliest-arrival candidate
+* Bridge rank (Algorithm 1; Sec. "Interval Root": earliest arrival first,
+  the space-time metric breaks ties): hand cases where the earliest-arrival candidate
   has the larger rho, an inadmissible earlier arrival, ties on arrival broken
   by rho and on both by the lowest index; only the top candidate is validated
   (a blocked top candidate is not replaced by the runner-up); the improvement
