@@ -353,6 +353,9 @@ def batched(args, rank):
     # The sample ranks the shapes of each launch form; the whole batch then
     # decides between the two forms' best shapes (a 48-problem sample fills
     # the persistent queue's teams about once, the whole batch many times).
+    # The queue's best team size also depends on how many problems each team
+    # plans, so every team size of the sample's best W is timed on the whole
+    # batch (each a few hundred ms).
     forms = {}
     for mode, name in ((stp.STP_LAUNCH_DEFAULT, "persistent_queue"), (1, "per_step")):
         cand = [t for t in choice.trials if t.launch_mode == mode and t.workers == choice.workers]
@@ -360,9 +363,18 @@ def batched(args, rank):
             continue
         t = min(cand, key=autotune._rank)
         f_ms, f_stats = run_full(t)
+        if mode == stp.STP_LAUNCH_DEFAULT:
+            team_ms = {t.team_ctas: f_ms}
+            for alt in cand:
+                if alt.team_ctas not in team_ms:
+                    a_ms, a_stats = run_full(alt)
+                    team_ms[alt.team_ctas] = a_ms
+                    if a_ms < f_ms:
+                        t, f_ms, f_stats = alt, a_ms, a_stats
         f_fs = [st["first_solution_ms"] for st in f_stats if st["first_solution_iter"] >= 0]
         forms[name] = {"launch_mode": t.launch_mode, "team_ctas": t.team_ctas, "nn_ctas": t.nn_ctas,
                        "validate_ctas": t.validate_ctas, "batch_ms": f_ms, "problems_per_s": len(idx) / (f_ms * 1e-3),
+                       "batch_ms_per_team_size": team_ms if mode == stp.STP_LAUNCH_DEFAULT else None,
                        "solved": len(f_fs), "first_solution_ms_p50": float(np.percentile(f_fs, 50)) if f_fs else None,
                        "first_solution_ms_p99": float(np.percentile(f_fs, 99)) if f_fs else None,
                        "_trial": t, "_stats": f_stats}
