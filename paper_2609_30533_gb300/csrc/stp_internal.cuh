@@ -18,7 +18,38 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace stp {
+
+// ---------------------------------------------------------------------------
+// Host: per-device kernel configuration. Function attributes and SM counts
+// belong to a device, so a process that uses several devices configures each
+// one; a mutex guards the records against concurrent launches.
+// ---------------------------------------------------------------------------
+constexpr int kMaxDevices = 64;
+
+struct SmemAttr {
+    std::mutex mu;
+    int bytes[kMaxDevices] = {};  // dynamic shared memory configured on each device
+};
+
+// Raises the kernel's dynamic shared-memory limit on the current device to at
+// least smem bytes; *raised tells whether this call changed it.
+inline cudaError_t ensure_smem(const void* kern, SmemAttr& a, int smem, bool* raised = nullptr) {
+    if (raised) *raised = false;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(a.mu);
+    if (smem <= a.bytes[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    a.bytes[dev] = smem;
+    if (raised) *raised = true;
+    return cudaSuccess;
+}
 
 constexpr int kMaxDof = 7;
 constexpr int kDP = 8;          // padded node width for dof > 3

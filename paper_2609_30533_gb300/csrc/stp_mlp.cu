@@ -759,12 +759,9 @@ size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 template <int N, int LBWB>
 cudaError_t launch_wgrad(const GemmArgs& g, int mtiles, int splits, cudaStream_t st) {
     constexpr int smem = wgrad_smem_bytes<N, LBWB>();
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_wgrad<N, LBWB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static SmemAttr attr;
+    cudaError_t e = ensure_smem((const void*)k_gemm_wgrad<N, LBWB>, attr, smem);
+    if (e != cudaSuccess) return e;
     k_gemm_wgrad<N, LBWB><<<dim3(mtiles, 1, splits), kThreads, smem, st>>>(g);
     return cudaGetLastError();
 }
@@ -772,13 +769,9 @@ cudaError_t launch_wgrad(const GemmArgs& g, int mtiles, int splits, cudaStream_t
 template <int NU, int KB, int LBW, int MODE>
 cudaError_t launch_res(const ResArgs& g, int nsm, cudaStream_t st) {
     constexpr int smem = res_smem_bytes(NU, KB, LBW, MODE);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_gemm_res<NU, KB, LBW, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static SmemAttr attr;
+    cudaError_t e = ensure_smem((const void*)k_gemm_res<NU, KB, LBW, MODE>, attr, smem);
+    if (e != cudaSuccess) return e;
     // Even grid (a CTA keeps one column half), at most one CTA per SM.
     const int grid = std::max(2, std::min(g.units, nsm & ~1));
     k_gemm_res<NU, KB, LBW, MODE><<<grid, kResThreads, smem, st>>>(g);

@@ -161,15 +161,19 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
     }
 }
 
+// One shared-memory record per kernel instance, used by launches and
+// occupancy queries alike (the attribute only ever grows).
+template <typename R, int DQ, int MO>
+static SmemAttr& attr_pk() {
+    static SmemAttr attr;
+    return attr;
+}
+
 template <typename R, int DQ, int MO>
 static cudaError_t launch_pk(const PersistArgs<R>& a, int grid, int smem, cudaStream_t st) {
     auto kern = k_plan_persistent<R, DQ, MO>;
-    static int configured = -1;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    cudaError_t e = ensure_smem((const void*)kern, attr_pk<R, DQ, MO>(), smem);
+    if (e != cudaSuccess) return e;
     if (grid <= 0) return cudaSuccess;  // configuration only
     void* args[] = {const_cast<PersistArgs<R>*>(&a)};
     return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kPersistThreads), args, (size_t)smem, st);
@@ -178,7 +182,7 @@ static cudaError_t launch_pk(const PersistArgs<R>& a, int grid, int smem, cudaSt
 template <typename R, int DQ, int MO>
 static cudaError_t occupancy_pk(int smem, int* blocks) {
     auto kern = k_plan_persistent<R, DQ, MO>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = ensure_smem((const void*)kern, attr_pk<R, DQ, MO>(), smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, kPersistThreads, smem);
 }

@@ -31,37 +31,40 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 && MO <= 16) ? 2 : 1)
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
-static int g_num_sms = 0;
-
 int validate_grid_blocks() {
-    if (g_num_sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_num_sms <= 0) g_num_sms = 1;
+    static std::mutex mu;
+    static int sms[kMaxDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 1;
+    std::lock_guard<std::mutex> lock(mu);
+    if (sms[dev] == 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        sms[dev] = n > 0 ? n : 1;
     }
-    return g_num_sms;
+    return sms[dev];
 }
 
 template <typename R, bool ARM, int MO, bool CLEAR, bool EARLY>
 static cudaError_t launch_v(const Geom<R>& g, const EdgeBatch<R>& e, int grid_blocks, cudaStream_t st) {
     auto kern = k_validate<R, ARM, MO, CLEAR, EARLY>;
-    static int configured_bytes = -1;
-    static int blocks_per_sm = 0;
+    static SmemAttr attr;
+    static int blocks_per_sm[kMaxDevices] = {};  // resident CTAs at the configured size
     int smem = (int)g.blob_bytes + (e.off ? (int)(sizeof(long long) * (kWin + 1))
                                           : (int)(sizeof(int) * (e.n_host + 1)));
-    if (smem > configured_bytes) {
-        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    bool raised = false;
+    cudaError_t err = ensure_smem((const void*)kern, attr, smem, &raised);
+    if (err != cudaSuccess) return err;
+    int dev = 0;
+    err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (raised || blocks_per_sm[dev] == 0) {
+        int b = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 256, smem);
         if (err != cudaSuccess) return err;
-        configured_bytes = smem;
-        blocks_per_sm = 0;
+        blocks_per_sm[dev] = b < 1 ? 1 : b;
     }
-    if (blocks_per_sm == 0) {
-        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, 256, smem);
-        if (err != cudaSuccess) return err;
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
-    }
-    int grid = grid_blocks > 0 ? grid_blocks : validate_grid_blocks() * blocks_per_sm;
+    int grid = grid_blocks > 0 ? grid_blocks : validate_grid_blocks() * blocks_per_sm[dev];
     kern<<<grid, 256, smem, st>>>(g, e);
     return cudaGetLastError();
 }
@@ -195,12 +198,9 @@ template <typename R, int MO>
 static cudaError_t launch_vb(const Geom<R>* Gs, const State<R>* Ss, int P, int which, int ctas_per_problem,
                              int smem_bytes, cudaStream_t st) {
     auto kern = k_validate_batch<R, MO>;
-    static int configured = -1;
-    if (smem_bytes > configured) {
-        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-        if (err != cudaSuccess) return err;
-        configured = smem_bytes;
-    }
+    static SmemAttr attr;
+    cudaError_t err = ensure_smem((const void*)kern, attr, smem_bytes);
+    if (err != cudaSuccess) return err;
     if (P <= 0) return cudaSuccess;  // configuration only
     kern<<<dim3(ctas_per_problem, P), 256, smem_bytes, st>>>(Gs, Ss, which);
     return cudaGetLastError();
