@@ -914,6 +914,29 @@ __device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S, int
     const int total = ts.pre[nsets];
     const R v2 = G.vmax * G.vmax;
     const bool interval = S.variant == 0;
+    // The CTA scans its tiles chunk by chunk (kQT nodes each). The node rows
+    // of the next chunk (of this tile, or the first of the CTA's next tile)
+    // are loaded into registers while the current chunk is scanned, so only
+    // the first chunk's global loads are exposed.
+    auto tile_range = [&](int tl, int& s_, int& n0_, int& n1_) {
+        s_ = 0;
+        while (ts.pre[s_ + 1] <= tl) ++s_;
+        const int ntile_ = (tl - ts.pre[s_]) % ts.nt[s_];
+        n0_ = ntile_ * ts.nts[s_];
+        n1_ = min(ts.nn[s_], n0_ + ts.nts[s_]);
+    };
+    R px[kDP];   // prefetched node row
+    R ptro = R(0);  // and its root time (interval root, backward sets)
+    auto prefetch = [&](int s_, int idx) {
+        const R* b_ = s_ == 0 ? S.fx : S.bx + (size_t)(s_ - 1) * S.cap_s * kDP;
+        ld_row(b_ + (size_t)idx * kDP, px);
+        if (interval && s_ != 0) ptro = S.btroot[(size_t)(s_ - 1) * S.cap_s + idx];
+    };
+    if (vcta < total) {
+        int s_, n0_, n1_;
+        tile_range(vcta, s_, n0_, n1_);
+        if (t < min(kQT, n1_ - n0_)) prefetch(s_, n0_ + t);
+    }
     for (int tile = vcta; tile < total; tile += nvcta) {
         int s = 0;
         while (ts.pre[s + 1] <= tile) ++s;
@@ -933,8 +956,6 @@ __device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S, int
         const R tr = xq[kDP - 1];
         const int n0 = ntile * ts.nts[s];
         const int n1 = min(ts.nn[s], n0 + ts.nts[s]);
-        const R* base = s == 0 ? S.fx : S.bx + (size_t)(s - 1) * S.cap_s * kDP;
-        const R* troot = s == 0 ? nullptr : S.btroot + (size_t)(s - 1) * S.cap_s;
         const bool fwd = s == 0;
         R best = rinf<R>();
         int bidx = 0x7fffffff;
@@ -942,13 +963,27 @@ __device__ __forceinline__ void nn_body(const Geom<R>& G, const State<R>& S, int
             const int cnt = min(kQT, n1 - c0);
             group_sync<NG>();
             if (t < cnt) {
-                bool active = true;
-                if (interval && !fwd) active = troot[c0 + t] < U0r;
+                const bool active = !(interval && !fwd) || ptro < U0r;
                 R v[kRow];
-                make_tile_row<R, DQ>(base + (size_t)(c0 + t) * kDP, active ? R(1) : R(0), v);
+#pragma unroll
+                for (int j = 0; j < kRow; ++j) v[j] = R(0);
+#pragma unroll
+                for (int j = 0; j < DQ; ++j) v[j] = px[j];
+                v[DQ] = px[kDP - 1];
+                v[DQ + 1] = active ? R(1) : R(0);
                 sts_row(sx[t], v);
             }
             group_sync<NG>();
+            {
+                // Next chunk: the rest of this tile, else the CTA's next tile.
+                int s_ = s, nc = c0 + kQT, ne = n1;
+                bool more = nc < n1;
+                if (!more && tile + nvcta < total) {
+                    tile_range(tile + nvcta, s_, nc, ne);
+                    more = true;
+                }
+                if (more && t < min(kQT, ne - nc)) prefetch(s_, nc + t);
+            }
             if (w >= 0) {
                 auto key_of = [&](int i) -> R {
                     R r[kRow];
@@ -1436,6 +1471,33 @@ __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S,
     group_sync<NG>();
     const int total = s_pre[2];
     const R v2 = G.vmax * G.vmax;
+    // Chunks of kQT nodes as in the NN scan: the next chunk's node rows (and
+    // root times) are loaded into registers while the current one is ranked.
+    auto tile_range = [&](int tl, int& s_, int& n0_, int& n1_) {
+        s_ = tl < s_pre[1] ? 0 : 1;
+        const int ntile_ = (tl - s_pre[s_]) % s_nt[s_];
+        n0_ = ntile_ * s_nts[s_];
+        n1_ = min(s_nn[s_], n0_ + s_nts[s_]);
+    };
+    R px[kDP];      // prefetched node row
+    R ptro = R(0);  // its root time (0 for forward nodes)
+    auto prefetch = [&](int s_, int li) {
+        if (s_ == 0) {
+            ld_row(fnode(S, li), px);
+            ptro = R(0);
+        } else {
+            int sg = 0;
+            while (seg_pre[sg + 1] <= li) ++sg;
+            const int i = li - seg_pre[sg];
+            ld_row(bnode(S, sg, i), px);
+            ptro = S.btroot[bofs(S, sg, i)];
+        }
+    };
+    if (vcta < total) {
+        int s_, n0_, n1_;
+        tile_range(vcta, s_, n0_, n1_);
+        if (t < min(kQT, n1_ - n0_)) prefetch(s_, n0_ + t);
+    }
     for (int tile = vcta; tile < total; tile += nvcta) {
         const int s = tile < s_pre[1] ? 0 : 1;
         const int local = tile - s_pre[s];
@@ -1459,25 +1521,27 @@ __device__ __forceinline__ void bridge_body(const Geom<R>& G, const State<R>& S,
             const int cnt = min(kQT, n1 - c0);
             group_sync<NG>();
             if (t < cnt) {
-                const int li = c0 + t;
-                const R* x;
-                R tro = R(0);
-                bool active = true;
-                if (s == 0) {
-                    x = fnode(S, li);
-                } else {
-                    int sg = 0;
-                    while (seg_pre[sg + 1] <= li) ++sg;
-                    const int i = li - seg_pre[sg];
-                    x = bnode(S, sg, i);
-                    tro = S.btroot[bofs(S, sg, i)];
-                    active = tro < U0r;
-                }
+                const bool active = s == 0 || ptro < U0r;
                 R v[kRow];
-                make_tile_row<R, DQ>(x, active ? tro : rinf<R>(), v);
+#pragma unroll
+                for (int j = 0; j < kRow; ++j) v[j] = R(0);
+#pragma unroll
+                for (int j = 0; j < DQ; ++j) v[j] = px[j];
+                v[DQ] = px[kDP - 1];
+                v[DQ + 1] = active ? ptro : rinf<R>();
                 sts_row(sx[t], v);
             }
             group_sync<NG>();
+            {
+                // Next chunk: the rest of this tile, else the CTA's next tile.
+                int s_ = s, nc = c0 + kQT, ne = n1;
+                bool more = nc < n1;
+                if (!more && tile + nvcta < total) {
+                    tile_range(tile + nvcta, s_, nc, ne);
+                    more = true;
+                }
+                if (more && t < min(kQT, ne - nc)) prefetch(s_, nc + t);
+            }
             if (w >= 0) {
                 // Rank key of vertex i: (arrival time, rho^2); rho^2 = inf when
                 // the vertex is inactive or not admissible.

@@ -105,7 +105,7 @@ def test_persistent_equals_per_step_kernels(case, precision):
     print(case, "fp%d" % (64 if precision else 32), snaps[0]["stats"])
 
 
-@pytest.mark.parametrize("ctas", [2, 16, 64])
+@pytest.mark.parametrize("ctas", [1, 2, 16, 64])
 def test_persistent_team_size_does_not_change_results(ctas):
     from paper_2609_30533_gb300 import stp
     prob, prm = CASES["ur5e-small-recycling"]()
