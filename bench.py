@@ -338,7 +338,7 @@ def batched(args, rank):
 
     sample = list(range(48))
     choice = autotune.autotune(lambda W: make(sample, W, args.tune_iters), workers=(128, 256, 512),
-                               team_ctas=(1, 2, 4, 8, 16), nn_ctas=(2, 4, 8), validate_ctas=(2, 4, 8))
+                               team_ctas=(1, 2, 4, 8, 16), nn_ctas=(2, 4, 8, 16), validate_ctas=(2, 4, 8, 16))
     idx = list(range(args.batch_problems))
     probs = make(idx, choice.workers, args.batch_iters)
 

@@ -45,12 +45,14 @@ __global__ void __launch_bounds__(kQT) k_nn_b(const Geom<R>* Gs, const State<R>*
     stage_problem(Gs, Ss, blockIdx.y, G, S);
     nn_body<R, DQ>(G, S, blockIdx.x, gridDim.x);
 }
-template <typename R>
-__global__ void __launch_bounds__(kCtaThreads) k_insert_b(const Geom<R>* Gs, const State<R>* Ss) {
+// Batched single-CTA steps run NT threads a problem: 256 when no problem has
+// more workers (one insertion round, eight CTAs an SM), else 1024.
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT) k_insert_b(const Geom<R>* Gs, const State<R>* Ss) {
     __shared__ Geom<R> G;
     __shared__ State<R> S;
     stage_problem(Gs, Ss, blockIdx.y, G, S);
-    insert_body(G, S);
+    insert_body<R, NT>(G, S);
 }
 template <typename R, int DQ>
 __global__ void __launch_bounds__(kQT) k_bridge_b(const Geom<R>* Gs, const State<R>* Ss) {
@@ -59,8 +61,8 @@ __global__ void __launch_bounds__(kQT) k_bridge_b(const Geom<R>* Gs, const State
     stage_problem(Gs, Ss, blockIdx.y, G, S);
     bridge_body<R, DQ>(G, S, blockIdx.x, gridDim.x);
 }
-template <typename R>
-__global__ void __launch_bounds__(kCtaThreads) k_publish_b(const Geom<R>* Gs, const State<R>* Ss) {
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT) k_publish_b(const Geom<R>* Gs, const State<R>* Ss) {
     __shared__ Geom<R> G;
     __shared__ State<R> S;
     stage_problem(Gs, Ss, blockIdx.y, G, S);
@@ -154,13 +156,16 @@ cudaError_t launch_iteration_batch(const Geom<R>* Gs, const State<R>* Ss, const 
     k_nn_b<R, kMaxDof><<<dim3(b.nn_ctas, b.P), kQT, 0, st>>>(Gs, Ss);
     cudaError_t err = launch_validate_batch<R>(Gs, Ss, b.P, 0, b.max_obs, b.validate_ctas, b.validate_smem, st);
     if (err != cudaSuccess) return err;
-    k_insert_b<R><<<dim3(1, b.P), kCtaThreads, 0, st>>>(Gs, Ss);
+    const bool narrow = b.max_W <= 256;
+    if (narrow) k_insert_b<R, 256><<<dim3(1, b.P), 256, 0, st>>>(Gs, Ss);
+    else k_insert_b<R, kCtaThreads><<<dim3(1, b.P), kCtaThreads, 0, st>>>(Gs, Ss);
     k_bridge_b<R, kMaxDof><<<dim3(b.nn_ctas, b.P), kQT, 0, st>>>(Gs, Ss);
     err = launch_validate_batch<R>(Gs, Ss, b.P, 1, b.max_obs, b.validate_ctas, b.validate_smem, st);
     if (err != cudaSuccess) return err;
     err = launch_validate_batch<R>(Gs, Ss, b.P, 2, b.max_obs, b.validate_ctas, b.validate_smem, st);
     if (err != cudaSuccess) return err;
-    k_publish_b<R><<<dim3(1, b.P), kCtaThreads, 0, st>>>(Gs, Ss);
+    if (narrow) k_publish_b<R, 256><<<dim3(1, b.P), 256, 0, st>>>(Gs, Ss);
+    else k_publish_b<R, kCtaThreads><<<dim3(1, b.P), kCtaThreads, 0, st>>>(Gs, Ss);
     return cudaGetLastError();
 }
 
