@@ -646,7 +646,7 @@ stp_status create_impl(stp_problem* p) {
         p->persist_dq = persist_dq(p->dof);
         p->persist_smem = persist_smem_bytes((int)blob_bytes, p->prm.ext_per_iter);
         int per_sm = 0;
-        STP_CUDA(p, persist_blocks_per_sm<R>(p->persist_dq, p->persist_smem, &per_sm));
+        STP_CUDA(p, persist_blocks_per_sm<R>(p->persist_dq, p->persist_smem, &per_sm, persist_threads(false)));
         if (per_sm < 1) {
             p->last_error = "persistent planner kernel does not fit on an SM";
             g_last_error = p->last_error;
@@ -723,7 +723,8 @@ stp_status plan_persistent_impl(stp_problem* p, Ctl* hc) {
     a.team_prob = p->pscratch.team_prob;
     a.abort_flag = p->pscratch.abort_flag;
     STP_CUDA(p, cudaEventRecord(p->ev0, st));
-    STP_CUDA(p, launch_plan_persistent<R>(a, p->persist_dq, p->persist_grid, p->persist_smem, st));
+    STP_CUDA(p, launch_plan_persistent<R>(a, p->persist_dq, p->persist_grid, p->persist_smem, st,
+                                          persist_threads(false)));
     STP_CUDA(p, cudaEventRecord(p->ev1, st));
     STP_CUDA(p, cudaMemcpyAsync(hc, p->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     STP_CUDA(p, cudaStreamSynchronize(st));
@@ -1648,7 +1649,7 @@ extern "C" stp_status stp_batch_create(stp_problem* const* problems, int n, cons
         // Persistent work queue: teams of team_ctas resident CTAs.
         b->persist_smem = persist_smem_bytes(max_blob, sh.max_W);
         int per_sm = 0;
-        e = persist_blocks_per_sm<float>(7, b->persist_smem, &per_sm);
+        e = persist_blocks_per_sm<float>(7, b->persist_smem, &per_sm, persist_threads(true));
         if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
         if (e == cudaSuccess) {
             const int resident = validate_grid_blocks() * per_sm;
@@ -1672,8 +1673,9 @@ extern "C" stp_status stp_batch_create(stp_problem* const* problems, int n, cons
             cudaError_t le = cudaSuccess;
             if (ce == cudaSuccess) {
                 le = cudaMemsetAsync(b->d_scratch, 0, b->scratch_bytes, b->stream);
-                if (le == cudaSuccess) le = launch_plan_persistent<float>(a, 7, b->persist_grid, b->persist_smem,
-                                                                         b->stream);
+                if (le == cudaSuccess)
+                    le = launch_plan_persistent<float>(a, 7, b->persist_grid, b->persist_smem, b->stream,
+                                                       persist_threads(true));
                 cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
                 if (le == cudaSuccess && ee == cudaSuccess) {
                     le = cudaGraphInstantiate(&b->graph, g, 0);
@@ -1766,8 +1768,8 @@ extern "C" stp_status stp_batch_plan(stp_batch* b, stp_stats* stats, double* bat
         // One persistent launch plans every problem (reset to path extraction).
         if (b->graph_direct) {
             if ((e = cudaMemsetAsync(b->d_scratch, 0, b->scratch_bytes, st)) != cudaSuccess) return fail(e, "memset");
-            if ((e = launch_plan_persistent<float>(batch_args(b), 7, b->persist_grid, b->persist_smem, st)) !=
-                cudaSuccess)
+            if ((e = launch_plan_persistent<float>(batch_args(b), 7, b->persist_grid, b->persist_smem, st,
+                                                   persist_threads(true))) != cudaSuccess)
                 return fail(e, "persistent launch");
         } else if ((e = cudaGraphLaunch(b->graph, st)) != cudaSuccess) {
             return fail(e, "cudaGraphLaunch");

@@ -25,7 +25,10 @@
 
 namespace stp {
 
-constexpr int kPersistThreads = 512;
+// CTA sizes: 512 threads for a lone problem (one CTA an SM, every CTA on the
+// problem's team); 256 for the batch queue (two CTAs an SM, so two teams share
+// an SM and one computes while the other waits at a barrier).
+constexpr int kPersistThreads = 512, kPersistBatchThreads = 256;
 constexpr int kPhases = 8;
 
 // Team barrier (sense reversal on one word). Each barrier adds exactly 2^31
@@ -75,8 +78,8 @@ __device__ __forceinline__ void validate_step(const Geom<R>& G, const EdgeBatch<
     else validate_body<R, false, MO, false, true>(G, E, smem, cta, ncta, true);
 }
 
-template <typename R, int DQ, int MO>
-__global__ void __launch_bounds__(kPersistThreads, 1)
+template <typename R, int DQ, int MO, int NT>
+__global__ void __launch_bounds__(NT, kPersistThreads / NT)
     k_plan_persistent(const __grid_constant__ PersistArgs<R> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Geom<R> G;
@@ -130,13 +133,13 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             if (*(volatile int*)&S.ctl->done) break;
             sample_body(G, S, rank, ts);
             if (!(ok = step_done(0))) break;
-            nn_body<R, DQ, kPersistThreads / kQT>(G, S, rank, ts);
+            nn_body<R, DQ, NT / kQT>(G, S, rank, ts);
             if (!(ok = step_done(1))) break;
             validate_step<R, MO>(G, ext_batch(S), smem_raw, rank, ts);
             if (!(ok = step_done(2))) break;
-            if (rank == 0) insert_body<R, kPersistThreads>(G, S);
+            if (rank == 0) insert_body<R, NT>(G, S);
             if (!(ok = step_done(3))) break;
-            bridge_body<R, DQ, kPersistThreads / kQT>(G, S, rank, ts);
+            bridge_body<R, DQ, NT / kQT>(G, S, rank, ts);
             if (!(ok = step_done(4))) break;
             // Bridges are long: a coarse pass over every eighth check point
             // finds most collisions, then the entries it left free in full.
@@ -163,42 +166,50 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
 
 // One shared-memory record per kernel instance, used by launches and
 // occupancy queries alike (the attribute only ever grows).
-template <typename R, int DQ, int MO>
+template <typename R, int DQ, int MO, int NT>
 static SmemAttr& attr_pk() {
     static SmemAttr attr;
     return attr;
 }
 
-template <typename R, int DQ, int MO>
+template <typename R, int DQ, int MO, int NT>
 static cudaError_t launch_pk(const PersistArgs<R>& a, int grid, int smem, cudaStream_t st) {
-    auto kern = k_plan_persistent<R, DQ, MO>;
-    cudaError_t e = ensure_smem((const void*)kern, attr_pk<R, DQ, MO>(), smem);
+    auto kern = k_plan_persistent<R, DQ, MO, NT>;
+    cudaError_t e = ensure_smem((const void*)kern, attr_pk<R, DQ, MO, NT>(), smem);
     if (e != cudaSuccess) return e;
     if (grid <= 0) return cudaSuccess;  // configuration only
     void* args[] = {const_cast<PersistArgs<R>*>(&a)};
-    return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kPersistThreads), args, (size_t)smem, st);
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(NT), args, (size_t)smem, st);
 }
 
-template <typename R, int DQ, int MO>
+template <typename R, int DQ, int MO, int NT>
 static cudaError_t occupancy_pk(int smem, int* blocks) {
-    auto kern = k_plan_persistent<R, DQ, MO>;
-    cudaError_t e = ensure_smem((const void*)kern, attr_pk<R, DQ, MO>(), smem);
+    auto kern = k_plan_persistent<R, DQ, MO, NT>;
+    cudaError_t e = ensure_smem((const void*)kern, attr_pk<R, DQ, MO, NT>(), smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, kPersistThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, NT, smem);
+}
+
+template <typename R, int DQ, int MO, int NT>
+static cudaError_t run_pk(const PersistArgs<R>* a, int grid, int smem, cudaStream_t st, int* blocks) {
+    return blocks ? occupancy_pk<R, DQ, MO, NT>(smem, blocks) : launch_pk<R, DQ, MO, NT>(*a, grid, smem, st);
 }
 
 // Kernel variants: FP32 with 3, 6 or 7 coordinates in the NN keys (point
-// robots, six-axis and seven-axis arms) and 16-obstacle register chunks; FP64
+// robots, six-axis and seven-axis arms) and 16-obstacle register chunks at 512
+// threads, and the batch queue's 7-coordinate variant at 256 threads; FP64
 // (the parity mode) with 7 coordinates (missing ones are zero in nodes and
 // queries, so the keys are the same) and 8-obstacle chunks.
 template <typename R>
-static cudaError_t dispatch(int dq, const PersistArgs<R>* a, int grid, int smem, cudaStream_t st, int* blocks) {
+static cudaError_t dispatch(int dq, int nt, const PersistArgs<R>* a, int grid, int smem, cudaStream_t st,
+                           int* blocks) {
     if constexpr (sizeof(R) == 8) {
-        return blocks ? occupancy_pk<R, 7, 8>(smem, blocks) : launch_pk<R, 7, 8>(*a, grid, smem, st);
+        return run_pk<R, 7, 8, kPersistThreads>(a, grid, smem, st, blocks);
     } else {
-        if (dq <= 3) return blocks ? occupancy_pk<R, 3, 16>(smem, blocks) : launch_pk<R, 3, 16>(*a, grid, smem, st);
-        if (dq == 6) return blocks ? occupancy_pk<R, 6, 16>(smem, blocks) : launch_pk<R, 6, 16>(*a, grid, smem, st);
-        return blocks ? occupancy_pk<R, 7, 16>(smem, blocks) : launch_pk<R, 7, 16>(*a, grid, smem, st);
+        if (nt == kPersistBatchThreads) return run_pk<R, 7, 16, kPersistBatchThreads>(a, grid, smem, st, blocks);
+        if (dq <= 3) return run_pk<R, 3, 16, kPersistThreads>(a, grid, smem, st, blocks);
+        if (dq == 6) return run_pk<R, 6, 16, kPersistThreads>(a, grid, smem, st, blocks);
+        return run_pk<R, 7, 16, kPersistThreads>(a, grid, smem, st, blocks);
     }
 }
 
@@ -207,20 +218,22 @@ int persist_smem_bytes(int max_blob_bytes, int max_W) {
     return ((max_blob_bytes + 15) / 16) * 16 + (int)sizeof(int) * (2 * max_W + 1);
 }
 
+int persist_threads(bool batch) { return batch ? kPersistBatchThreads : kPersistThreads; }
+
 template <typename R>
-cudaError_t persist_blocks_per_sm(int dq, int smem, int* blocks) {
+cudaError_t persist_blocks_per_sm(int dq, int smem, int* blocks, int threads) {
     *blocks = 0;
-    return dispatch<R>(dq, nullptr, 0, smem, nullptr, blocks);
+    return dispatch<R>(dq, threads, nullptr, 0, smem, nullptr, blocks);
 }
 
 template <typename R>
-cudaError_t launch_plan_persistent(const PersistArgs<R>& a, int dq, int grid, int smem, cudaStream_t st) {
-    return dispatch<R>(dq, &a, grid, smem, st, nullptr);
+cudaError_t launch_plan_persistent(const PersistArgs<R>& a, int dq, int grid, int smem, cudaStream_t st, int threads) {
+    return dispatch<R>(dq, threads, &a, grid, smem, st, nullptr);
 }
 
-template cudaError_t persist_blocks_per_sm<float>(int, int, int*);
-template cudaError_t persist_blocks_per_sm<double>(int, int, int*);
-template cudaError_t launch_plan_persistent<float>(const PersistArgs<float>&, int, int, int, cudaStream_t);
-template cudaError_t launch_plan_persistent<double>(const PersistArgs<double>&, int, int, int, cudaStream_t);
+template cudaError_t persist_blocks_per_sm<float>(int, int, int*, int);
+template cudaError_t persist_blocks_per_sm<double>(int, int, int*, int);
+template cudaError_t launch_plan_persistent<float>(const PersistArgs<float>&, int, int, int, cudaStream_t, int);
+template cudaError_t launch_plan_persistent<double>(const PersistArgs<double>&, int, int, int, cudaStream_t, int);
 
 }  // namespace stp

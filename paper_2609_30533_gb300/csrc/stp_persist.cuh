@@ -40,11 +40,13 @@ int persist_dq(int max_dof);
 // Dynamic shared memory of a launch: the largest geometry blob and the
 // collision batch's offsets (2 W + 1 ints).
 int persist_smem_bytes(int max_blob_bytes, int max_W);
+// Threads of a persistent CTA: the batch queue's (FP32 only) or a lone problem's.
+int persist_threads(bool batch);
 template <typename R>
-cudaError_t persist_blocks_per_sm(int dq, int smem, int* blocks);
-// Cooperative launch of grid CTAs of kPersistThreads threads; grid <= 0 only
-// configures the kernel's shared-memory limit.
+cudaError_t persist_blocks_per_sm(int dq, int smem, int* blocks, int threads);
+// Cooperative launch of grid CTAs of `threads` threads (persist_threads);
+// grid <= 0 only configures the kernel's shared-memory limit.
 template <typename R>
-cudaError_t launch_plan_persistent(const PersistArgs<R>& a, int dq, int grid, int smem, cudaStream_t st);
+cudaError_t launch_plan_persistent(const PersistArgs<R>& a, int dq, int grid, int smem, cudaStream_t st, int threads);
 
 }  // namespace stp
