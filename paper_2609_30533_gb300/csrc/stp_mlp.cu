@@ -170,29 +170,37 @@ __device__ __forceinline__ float warp_colsum16(float (&v)[16]) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
-// Weight gradient dW = dT^T . X: M = 128 output features (column block
-// blockIdx.x of dT), N = the layer's input features, K = the batch rows of
-// split blockIdx.z. Both operands are MN-major: a stage is 64 batch rows, so
-// A is one contiguous 16 KB piece of dT's column block and B one piece of 8
-// row groups per column block of X (one MMA of N = BW per block and K step).
-// The dynamic shared memory ends with a guard region so that every
+// Weight gradient dW = dT^T . X: M = 128 output features per tile (column
+// block of dT), N = the layer's input features, K = the batch rows of split
+// blockIdx.z. MT = 1: the CTA computes tile blockIdx.x; MT = 2: both 128-row
+// tiles (two accumulators in TMEM), reading each activation stage once. Both
+// operands are MN-major: a stage is 64 batch rows, so an A tile is one
+// contiguous 16 KB piece of dT's column block and B one piece of 8 row groups
+// per column block of X (one MMA of N = BW per tile, block and K step). The
+// dynamic shared memory ends with a guard region so that every
 // descriptor-addressed read stays inside the allocation.
-template <int N, int LBWB>
-__host__ __device__ constexpr int wgrad_smem_bytes() {
-    return 1024 + kWStages * (kTileM * kStageK * 2 + N * kStageK * 2) + 21 * 2048 + 256 - (1 << LBWB) * kStageK * 2;
+template <int N, int MT>
+__host__ __device__ constexpr int wgrad_stages() {
+    return (MT == 2 && N > 64) ? 3 : kWStages;
 }
-template <int N, int LBWB>
+template <int N, int LBWB, int MT>
+__host__ __device__ constexpr int wgrad_smem_bytes() {
+    return 1024 + wgrad_stages<N, MT>() * (MT * kTileM * kStageK * 2 + N * kStageK * 2) + 21 * 2048 + 256 -
+           (1 << LBWB) * kStageK * 2;
+}
+template <int N, int LBWB, int MT>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_wgrad(GemmArgs g) {
-    constexpr int kStages = kWStages;
+    constexpr int kStages = wgrad_stages<N, MT>();
     constexpr int kBW = 1 << LBWB;                      // B column block
-    constexpr int kNB = N / kBW;                        // B blocks (MMAs per K step)
-    constexpr uint32_t kABytes = kTileM * kStageK * 2;  // 16 KB
+    constexpr int kNB = N / kBW;                        // B blocks (MMAs per K step and tile)
+    constexpr uint32_t kATile = kTileM * kStageK * 2;   // 16 KB
+    constexpr uint32_t kABytes = MT * kATile;
     constexpr uint32_t kBBlk = kBW * kStageK * 2;
     constexpr uint32_t kBBytes = kNB * kBBlk;
-    constexpr uint32_t kTmemCols = N < 32 ? 32 : N;
+    constexpr uint32_t kTmemCols = MT * N < 32 ? 32 : MT * N;
     constexpr uint32_t kIdesc = idesc_bf16_mn(kTileM, kBW);
     constexpr uint32_t kALbo = 16 * 128, kBLbo = (kBW / 8) * 128;  // one 8-row group of a column block
-    static_assert(N % kBW == 0, "whole column blocks");
+    static_assert(N % kBW == 0 && (MT == 1 || MT == 2), "whole column blocks");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_base_sh;
@@ -202,7 +210,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_wgrad(GemmArgs g) {
     unsigned char* sA = smem;
     unsigned char* sB = smem + kStages * kABytes;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * kTileM;
     const int z = blockIdx.z;
     const int kt0 = z * g.kt_per_split;
     const int kt1 = min(g.KT, kt0 + g.kt_per_split);
@@ -234,7 +241,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_wgrad(GemmArgs g) {
                 if (!ok) break;
                 const size_t kg = (size_t)(kt0 + it) * (kStageK / 8);  // first 8-row group of the stage
                 mbar_expect_tx(&full[s], kABytes + kBBytes);
-                bulk_g2s(sA + s * kABytes, g.A + (((size_t)blockIdx.x * rg + kg) * 16) * 64, kABytes, &full[s]);
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    const size_t cb = MT == 2 ? (size_t)mt : (size_t)blockIdx.x;  // column block of dT
+                    bulk_g2s(sA + s * kABytes + mt * kATile, g.A + ((cb * rg + kg) * 16) * 64, kATile, &full[s]);
+                }
 #pragma unroll
                 for (int nb = 0; nb < kNB; ++nb)
                     bulk_g2s(sB + s * kBBytes + nb * kBBlk, g.B + (((size_t)nb * rg + kg) * (kBW / 8)) * 64, kBBlk,
@@ -251,11 +262,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_wgrad(GemmArgs g) {
 #pragma unroll
                 for (int ks = 0; ks < kStageK / 16; ++ks) {
                     // K step of 16 batch rows = two 8-row groups.
-                    const uint64_t da = smem_desc(a0 + ks * 2 * kALbo, kALbo, 128);
 #pragma unroll
-                    for (int nb = 0; nb < kNB; ++nb) {
-                        const uint64_t db = smem_desc(b0 + nb * kBBlk + ks * 2 * kBLbo, kBLbo, 128);
-                        mma_bf16(tmem + (uint32_t)(nb * kBW), da, db, kIdesc, (j > 0 || ks > 0) ? 1u : 0u);
+                    for (int mt = 0; mt < MT; ++mt) {
+                        const uint64_t da = smem_desc(a0 + mt * kATile + ks * 2 * kALbo, kALbo, 128);
+#pragma unroll
+                        for (int nb = 0; nb < kNB; ++nb) {
+                            const uint64_t db = smem_desc(b0 + nb * kBBlk + ks * 2 * kBLbo, kBLbo, 128);
+                            mma_bf16(tmem + (uint32_t)(mt * N + nb * kBW), da, db, kIdesc,
+                                     (j > 0 || ks > 0) ? 1u : 0u);
+                        }
                     }
                 }
                 mma_commit(&empty[s]);
@@ -283,24 +298,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_wgrad(GemmArgs g) {
     __syncthreads();
     if (fail_sh) have = false;
 
-    // Epilogue: thread (warp, lane) owns tile row 32 (warp % 4) + lane and
-    // half of the columns; FP32 partial rows of split z.
+    // Epilogue: thread (warp, lane) owns row 32 (warp % 4) + lane of each
+    // tile and half of the columns; FP32 partial rows of split z.
     const int quad = warp & 3;
-    const int r = m0 + 32 * quad + lane;
-    const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16);
     const int cb = (warp >> 2) * (N / 2), ce = cb + N / 2;
 #pragma unroll 1
-    for (int c0 = cb; c0 < ce; c0 += 16) {
-        float v[16];
-        if (have) tmem_ld16(trow + (uint32_t)c0, v);
-        else {
+    for (int mt = 0; mt < MT; ++mt) {
+        const int r = (MT == 2 ? mt : (int)blockIdx.x) * kTileM + 32 * quad + lane;
+        const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(mt * N);
+#pragma unroll 1
+        for (int c0 = cb; c0 < ce; c0 += 16) {
+            float v[16];
+            if (have) tmem_ld16(trow + (uint32_t)c0, v);
+            else {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = 0.f;
-        }
-        if (r < g.m_valid) {
-            float4* o = reinterpret_cast<float4*>(g.out_f + ((size_t)z * g.m_valid + r) * g.ld_f + c0);
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+            }
+            if (r < g.m_valid) {
+                float4* o = reinterpret_cast<float4*>(g.out_f + ((size_t)z * g.m_valid + r) * g.ld_f + c0);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                for (int q = 0; q < 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
         }
     }
     fence_before_sync();
@@ -653,14 +671,10 @@ struct AdamArgs {
     int update;               // 0: only sum gradients (and refresh BF16 copies)
 };
 
-__global__ void k_adam(AdamArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = a.rows * a.cols;
-    if (i >= n) return;
+// Element i of a parameter tensor: store the summed gradient (optional),
+// take the Adam step, refresh the BF16 operand copies.
+__device__ __forceinline__ void adam_apply(const AdamArgs& a, int i, float gsum) {
     const int r = i / a.cols, c = i % a.cols;
-    float gsum = 0.f;
-    if (a.gpart)
-        for (int p = 0; p < a.nparts; ++p) gsum += a.gpart[(size_t)p * n + i];
     if (r >= a.rows_used) gsum = 0.f;
     if (a.gout) a.gout[i] = gsum;
     float w = a.w[i];
@@ -676,6 +690,37 @@ __global__ void k_adam(AdamArgs a) {
         const __nv_bfloat16 b = __float2bfloat16_rn(w);
         a.wt[tixb(r, c, a.rows, lbw_of(a.cols))] = b;
         a.wtT[tixb(c, r, a.cols, lbw_of(a.rows))] = b;
+    }
+}
+
+// Weights: one thread per element sums its split-K partials in split order.
+__global__ void k_adam(AdamArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = a.rows * a.cols;
+    if (i >= n) return;
+    float gsum = 0.f;
+    if (a.gpart)
+        for (int p = 0; p < a.nparts; ++p) gsum += a.gpart[(size_t)p * n + i];
+    adam_apply(a, i, gsum);
+}
+
+// Biases: thousands of partial rows (one per 32 batch rows). A block takes
+// 32 elements; warp w sums partials w, w + warps, ... (coalesced rows), the
+// warps' sums are added in warp order, and the first warp takes the step.
+__global__ void k_adam_vec(AdamArgs a) {
+    __shared__ float part[32][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int n = a.rows * a.cols;
+    const int i = blockIdx.x * 32 + lane;
+    float s = 0.f;
+    if (a.gpart && i < n)
+        for (int p = w; p < a.nparts; p += nw) s += a.gpart[(size_t)p * n + i];
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && i < n) {
+        float g = 0.f;
+        for (int k = 0; k < nw; ++k) g += part[k][lane];
+        adam_apply(a, i, g);
     }
 }
 
@@ -729,6 +774,8 @@ struct stp_mlp {
     float* Yout = nullptr;    // [max_batch][160]
     int* err = nullptr;
     int nsm = 0;              // SMs of the device (persistent product grid)
+    cudaStream_t side = nullptr;          // weight gradients beside the input gradients
+    cudaEvent_t fork = nullptr, join = nullptr;
     int step = 0;
     bool profiling = false;
     cudaEvent_t ev[2]{};
@@ -756,24 +803,25 @@ constexpr int kSplitMax = 80;
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-template <int N, int LBWB>
-cudaError_t launch_wgrad(const GemmArgs& g, int mtiles, int splits, cudaStream_t st) {
-    constexpr int smem = wgrad_smem_bytes<N, LBWB>();
+template <int N, int LBWB, int MT>
+cudaError_t launch_wgrad(const GemmArgs& g, int splits, cudaStream_t st) {
+    constexpr int smem = wgrad_smem_bytes<N, LBWB, MT>();
     static SmemAttr attr;
-    cudaError_t e = ensure_smem((const void*)k_gemm_wgrad<N, LBWB>, attr, smem);
+    cudaError_t e = ensure_smem((const void*)k_gemm_wgrad<N, LBWB, MT>, attr, smem);
     if (e != cudaSuccess) return e;
-    k_gemm_wgrad<N, LBWB><<<dim3(mtiles, 1, splits), kThreads, smem, st>>>(g);
+    k_gemm_wgrad<N, LBWB, MT><<<dim3(MT == 2 ? 1 : kOutP / kTileM, 1, splits), kThreads, smem, st>>>(g);
     return cudaGetLastError();
 }
 
+// max_ctas: the SMs this launch may take (the rest run a concurrent product).
 template <int NU, int KB, int LBW, int MODE>
-cudaError_t launch_res(const ResArgs& g, int nsm, cudaStream_t st) {
+cudaError_t launch_res(const ResArgs& g, int max_ctas, cudaStream_t st) {
     constexpr int smem = res_smem_bytes(NU, KB, LBW, MODE);
     static SmemAttr attr;
     cudaError_t e = ensure_smem((const void*)k_gemm_res<NU, KB, LBW, MODE>, attr, smem);
     if (e != cudaSuccess) return e;
     // Even grid (a CTA keeps one column half), at most one CTA per SM.
-    const int grid = std::max(2, std::min(g.units, nsm & ~1));
+    const int grid = std::max(2, std::min(g.units, max_ctas & ~1));
     k_gemm_res<NU, KB, LBW, MODE><<<grid, kResThreads, smem, st>>>(g);
     return cudaGetLastError();
 }
@@ -875,14 +923,16 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
         g.ld_f = kLayers[l].in;
         g.m_valid = kLayers[l].out;
         g.err = m->err;
-        {
-            Timer t(m, 2.0 * B * kLayers[l].in_used * kLayers[l].out_used,
-                    alg_bytes(B, kLayers[l].in_used, kLayers[l].out_used, kWGrad));
-            if (l == 0) MLP_CUDA(m, (launch_wgrad<kInP, lbw_of(kInP)>(g, kLayers[l].out / kTileM, splits, st)));
-            else MLP_CUDA(m, (launch_wgrad<kHid, kActLbw>(g, kLayers[l].out / kTileM, splits, st)));
+        const double wflops = 2.0 * B * kLayers[l].in_used * kLayers[l].out_used;
+        const double wbytes = alg_bytes(B, kLayers[l].in_used, kLayers[l].out_used, kWGrad);
+        if (l == 0) {
+            // The last weight gradient runs alone: both tiles of a split on
+            // their own CTAs, over every SM.
+            Timer t(m, wflops, wbytes);
+            MLP_CUDA(m, (launch_wgrad<kInP, lbw_of(kInP), 1>(g, splits, st)));
             t.stop();
+            break;
         }
-        if (l == 0) break;
         // input gradient: dH_{l-1} = (dT_l . W_l) * relu'(h_{l-1})   (M = batch, N = in, K = out)
         ResArgs h{};
         h.A = m->dt[l];
@@ -894,9 +944,18 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
         h.out_t = m->dt[l - 1];
         h.out_f = m->bpart + (size_t)(l - 1) * bpart_stride(m->Bp_max);
         h.err = m->err;
-        Timer t(m, 2.0 * B * kLayers[l].in_used * kLayers[l].out_used,
-                alg_bytes(B, kLayers[l].in_used, kLayers[l].out_used, kBackward));
-        MLP_CUDA(m, (launch_res<kHid / 2, 2, kActLbw, kBackward>(h, m->nsm, st)));
+        // The two products of a layer are independent: the weight gradient
+        // (one CTA per split computing both output tiles, so each activation
+        // stage is read once) runs on the side stream beside the input
+        // gradient, which takes the remaining SMs.
+        Timer t(m, wflops + 2.0 * B * kLayers[l].in_used * kLayers[l].out_used,
+                wbytes + alg_bytes(B, kLayers[l].in_used, kLayers[l].out_used, kBackward));
+        MLP_CUDA(m, cudaEventRecord(m->fork, st));
+        MLP_CUDA(m, cudaStreamWaitEvent(m->side, m->fork, 0));
+        MLP_CUDA(m, (launch_wgrad<kHid, kActLbw, 2>(g, splits, m->side)));
+        MLP_CUDA(m, (launch_res<kHid / 2, 2, kActLbw, kBackward>(h, std::max(2, m->nsm - splits), st)));
+        MLP_CUDA(m, cudaEventRecord(m->join, m->side));
+        MLP_CUDA(m, cudaStreamWaitEvent(st, m->join, 0));
         t.stop();
     }
     return STP_OK;
@@ -947,7 +1006,7 @@ stp_status adam_impl(stp_mlp* m, int nwpart, int nbpart, float lr, bool update, 
         bb.gout = keep_grads ? gout : nullptr;
         // bias partials are [chunk][256]: view as [rows = 256][cols = 1] per chunk
         n = L.out;
-        k_adam<<<(n + 255) / 256, 256, 0, m->stream>>>(bb);
+        k_adam_vec<<<(n + 31) / 32, 1024, 0, m->stream>>>(bb);
         MLP_CUDA(m, cudaGetLastError());
         gout += n;
     }
@@ -1042,9 +1101,11 @@ stp_status stp_mlp_create(int max_batch, stp_mlp** out) {
         off += up256(p.second);
     }
     if (cudaMemset(m->arena, 0, total) != cudaSuccess || cudaEventCreate(&m->ev[0]) != cudaSuccess ||
-        cudaEventCreate(&m->ev[1]) != cudaSuccess) {
-        cudaFree(m->arena);
-        delete m;
+        cudaEventCreate(&m->ev[1]) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->join, cudaEventDisableTiming) != cudaSuccess) {
+        stp_mlp_free(m);
         return fail(nullptr, STP_ERR_CUDA, "device initialisation failed");
     }
     *out = m;
@@ -1055,9 +1116,13 @@ void stp_mlp_free(stp_mlp* m) {
     if (!m) return;
     if (m->stream) cudaStreamSynchronize(m->stream);
     else cudaDeviceSynchronize();
+    if (m->side) cudaStreamSynchronize(m->side);
     cudaFree(m->arena);
-    cudaEventDestroy(m->ev[0]);
-    cudaEventDestroy(m->ev[1]);
+    if (m->ev[0]) cudaEventDestroy(m->ev[0]);
+    if (m->ev[1]) cudaEventDestroy(m->ev[1]);
+    if (m->fork) cudaEventDestroy(m->fork);
+    if (m->join) cudaEventDestroy(m->join);
+    if (m->side) cudaStreamDestroy(m->side);
     delete m;
 }
 
