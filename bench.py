@@ -637,7 +637,8 @@ def stated_configs(args, peak_tflops):
 
 def mlp_throughput(rank, B=65536, reps=3):
     """Tensor-core GEMMs of proposal-network training steps at batch B on
-    synthetic inputs and targets (CUDA events around each GEMM)."""
+    synthetic inputs and targets (CUDA events around the forward chain and
+    the backward pass, which hold GEMM launches only)."""
     from paper_2609_30533_gb300 import proposal as PR
     from paper_2609_30533_gb300 import stp
     rng = np.random.default_rng(rank)
@@ -662,8 +663,11 @@ def mlp_throughput(rank, B=65536, reps=3):
     return {"batch": B, "gemm_ms_per_step": gms / reps, "gemm_flops_per_step": gfl / reps,
             "gemm_bytes_per_step": gby / reps, "tflops": tf, "peak_tflops": peak, "frac": tf / peak,
             "gbs": gbs, "peak_gbs": hbm, "hbm_frac": gbs / hbm,
-            "note": "BF16 tcgen05 GEMMs of forward + backward training steps, CUDA events per GEMM; "
-                    "K = 256 products at 100 flop/byte sit below the BF16 ridge (about 280), so HBM bounds them"}
+            "note": "BF16 tcgen05 GEMMs of forward + backward training steps; CUDA events around the forward "
+                    "chain (four products) and around the backward pass (input gradients on the main stream, "
+                    "weight gradients beside them), GEMM launches only; algorithmic bytes over the logical layer "
+                    "shapes; K = 256 products at about 100 flop/byte sit below the BF16 ridge (about 290), "
+                    "so HBM bounds them"}
 
 
 def learned(args, rank):

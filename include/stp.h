@@ -443,8 +443,9 @@ stp_status stp_mlp_gradients(stp_mlp *m, int B, const float *x, const float *tar
  * the batch loss before the step. */
 stp_status stp_mlp_train_step(stp_mlp *m, int B, const float *x, const float *targets, float lr, float *loss,
                               int flags);
-/* With profiling on, every tensor-core GEMM is bracketed by CUDA events;
- * stp_mlp_profile returns (and clears) their total time, FLOPs and
+/* With profiling on, the forward chain of tensor-core GEMMs and the backward
+ * pass's GEMMs are each bracketed by CUDA events (intervals that hold GEMM
+ * launches only); stp_mlp_profile returns (and clears) their total time, FLOPs and
  * algorithmic HBM bytes, both over the layers' logical shapes (32 inputs,
  * 160 outputs, the batch without padding): operands read once, each output
  * written once in one layout. */

@@ -352,6 +352,13 @@ __host__ __device__ constexpr int res_smem_bytes(int nu, int kb, int lbw, int mo
     return 1024 + kb * nu * (1 << lbw) * 2 + kRingBytes + (mode == kOutput ? kEpiWarps * 32 * kOutPad * 4 : 0);
 }
 
+// Programmatic dependent launch: let the next kernel in the stream start its
+// CTAs (and their prologue) as this kernel's CTAs finish, and wait for the
+// previous kernel's completion and memory before touching its outputs. Both
+// are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -417,6 +424,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
         abort_sh = 1;
         if (g.err) atomicOr(g.err, kErrTimeout);
     };
+    if (tid == 0) pdl_launch_dependents();
 
     if (warp == kEpiWarps) {
         // Copy issuer.
@@ -425,6 +433,9 @@ __global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
             for (int kb = 0; kb < KB; ++kb)
                 bulk_g2s(sB + kb * kBBytes,
                          g.B + (((size_t)kb * (g.NB >> 3) + (size_t)h * (NU >> 3)) * (kBW / 8)) * 64, kBBytes, &bfull);
+            // The weights are no kernel's output within a pass; the A
+            // operand is the previous kernel's.
+            pdl_wait();
             const size_t rgA = (size_t)(g.RA >> 3);
             int it = 0;
             for (int u = blockIdx.x; u < g.units && !abort_sh; u += gridDim.x) {
@@ -452,6 +463,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
     } else if (warp == kEpiWarps + 1) {
         // MMA issuer.
         if (lane == 0) {
+            pdl_wait();
             bool ok = mbar_wait(&bfull, 0);
             if (!ok) fail();
             int it = 0, i = 0;
@@ -507,6 +519,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
                 }
             }
         };
+        pdl_wait();
         if (blockIdx.x < g.units) load_mask(blockIdx.x);
         int i = 0;
         for (int u = blockIdx.x; u < g.units; u += gridDim.x, ++i) {
@@ -813,17 +826,31 @@ cudaError_t launch_wgrad(const GemmArgs& g, int splits, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// max_ctas: the SMs this launch may take (the rest run a concurrent product).
+// max_ctas: the SMs this launch may take (the rest run a concurrent product);
+// pdl: launch as a programmatic dependent of the previous kernel in st.
 template <int NU, int KB, int LBW, int MODE>
-cudaError_t launch_res(const ResArgs& g, int max_ctas, cudaStream_t st) {
+cudaError_t launch_res(const ResArgs& g, int max_ctas, cudaStream_t st, bool pdl = false) {
     constexpr int smem = res_smem_bytes(NU, KB, LBW, MODE);
     static SmemAttr attr;
     cudaError_t e = ensure_smem((const void*)k_gemm_res<NU, KB, LBW, MODE>, attr, smem);
     if (e != cudaSuccess) return e;
     // Even grid (a CTA keeps one column half), at most one CTA per SM.
     const int grid = std::max(2, std::min(g.units, max_ctas & ~1));
-    k_gemm_res<NU, KB, LBW, MODE><<<grid, kResThreads, smem, st>>>(g);
-    return cudaGetLastError();
+    if (!pdl) {
+        k_gemm_res<NU, KB, LBW, MODE><<<grid, kResThreads, smem, st>>>(g);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kResThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute la[1];
+    la[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    la[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = la;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_gemm_res<NU, KB, LBW, MODE>, g);
 }
 
 // Bias-gradient partials per layer: the input-gradient products write one
@@ -872,6 +899,16 @@ stp_status forward_impl(stp_mlp* m, int B) {
         k_pack_input<<<(n + 255) / 256, 256, 0, st>>>(m->X, B, Bp, m->xt);
         MLP_CUDA(m, cudaGetLastError());
     }
+    // The four products are timed as one interval: each is launched as a
+    // programmatic dependent of the previous kernel, so its prologue (barriers,
+    // TMEM, the resident weights) overlaps the previous product's tail.
+    double chain_flops = 0.0, chain_bytes = 0.0;
+    for (int l = 0; l < 4; ++l) {
+        const Layer& L = kLayers[l];
+        chain_flops += 2.0 * B * L.in_used * L.out_used;
+        chain_bytes += alg_bytes(B, L.in_used, L.out_used, l < 3 ? kHidden : kOutput);
+    }
+    Timer t(m, chain_flops, chain_bytes);
     const __nv_bfloat16* in = m->xt;
     for (int l = 0; l < 4; ++l) {
         const Layer& L = kLayers[l];
@@ -883,19 +920,18 @@ stp_status forward_impl(stp_mlp* m, int B) {
         g.units = 2 * mt;
         g.bias = m->b[l];
         g.err = m->err;
-        Timer t(m, 2.0 * B * L.in_used * L.out_used, alg_bytes(B, L.in_used, L.out_used, l < 3 ? kHidden : kOutput));
         if (l < 3) {
             g.out_t = m->ht[l];
-            if (l == 0) MLP_CUDA(m, (launch_res<kHid / 2, 1, lbw_of(kInP), kHidden>(g, m->nsm, st)));
-            else MLP_CUDA(m, (launch_res<kHid / 2, 2, kActLbw, kHidden>(g, m->nsm, st)));
+            if (l == 0) MLP_CUDA(m, (launch_res<kHid / 2, 1, lbw_of(kInP), kHidden>(g, m->nsm, st, true)));
+            else MLP_CUDA(m, (launch_res<kHid / 2, 2, kActLbw, kHidden>(g, m->nsm, st, true)));
             in = m->ht[l];
         } else {
             g.out_f = m->y;
             g.ld_f = kOutP;
-            MLP_CUDA(m, (launch_res<kOut / 2, 2, kActLbw, kOutput>(g, m->nsm, st)));
+            MLP_CUDA(m, (launch_res<kOut / 2, 2, kActLbw, kOutput>(g, m->nsm, st, true)));
         }
-        t.stop();
     }
+    t.stop();
     return STP_OK;
 }
 
@@ -911,6 +947,22 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
     const int splits = (KTb + kps - 1) / kps;  // every split non-empty
     *nwpart = splits;
     *nbpart = Bp / 32;
+    // The weight gradients (one CTA per split computing both output tiles, so
+    // each activation stage is read once) run on the side stream, each as
+    // soon as its output gradient exists; the input gradients run back to
+    // back on the main stream over the remaining SMs. The whole backward
+    // pass is timed as one interval.
+    double chain_flops = 0.0, chain_bytes = 0.0;
+    for (int l = 3; l >= 0; --l) {
+        chain_flops += 2.0 * B * kLayers[l].in_used * kLayers[l].out_used;
+        chain_bytes += alg_bytes(B, kLayers[l].in_used, kLayers[l].out_used, kWGrad);
+        if (l > 0) {
+            chain_flops += 2.0 * B * kLayers[l].in_used * kLayers[l].out_used;
+            chain_bytes += alg_bytes(B, kLayers[l].in_used, kLayers[l].out_used, kBackward);
+        }
+    }
+    Timer t(m, chain_flops, chain_bytes);
+    MLP_CUDA(m, cudaEventRecord(m->fork, st));  // dT_3 (the loss gradient) is ready
     for (int l = 3; l >= 0; --l) {
         // weight gradient: dW_l = dT_l^T . act_{l-1}   (M = out, N = in, K = batch)
         GemmArgs g{};
@@ -923,16 +975,13 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
         g.ld_f = kLayers[l].in;
         g.m_valid = kLayers[l].out;
         g.err = m->err;
-        const double wflops = 2.0 * B * kLayers[l].in_used * kLayers[l].out_used;
-        const double wbytes = alg_bytes(B, kLayers[l].in_used, kLayers[l].out_used, kWGrad);
-        if (l == 0) {
-            // The last weight gradient runs alone: both tiles of a split on
-            // their own CTAs, over every SM.
-            Timer t(m, wflops, wbytes);
-            MLP_CUDA(m, (launch_wgrad<kInP, lbw_of(kInP), 1>(g, splits, st)));
-            t.stop();
-            break;
-        }
+        MLP_CUDA(m, cudaStreamWaitEvent(m->side, m->fork, 0));
+        // The first layer's weight gradient follows the last input gradient,
+        // when the main stream has no more work: its two output tiles take
+        // separate CTAs, so it spreads over every SM as they free up.
+        if (l == 0) MLP_CUDA(m, (launch_wgrad<kInP, lbw_of(kInP), 1>(g, splits, m->side)));
+        else MLP_CUDA(m, (launch_wgrad<kHid, kActLbw, 2>(g, splits, m->side)));
+        if (l == 0) break;
         // input gradient: dH_{l-1} = (dT_l . W_l) * relu'(h_{l-1})   (M = batch, N = in, K = out)
         ResArgs h{};
         h.A = m->dt[l];
@@ -944,20 +993,12 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
         h.out_t = m->dt[l - 1];
         h.out_f = m->bpart + (size_t)(l - 1) * bpart_stride(m->Bp_max);
         h.err = m->err;
-        // The two products of a layer are independent: the weight gradient
-        // (one CTA per split computing both output tiles, so each activation
-        // stage is read once) runs on the side stream beside the input
-        // gradient, which takes the remaining SMs.
-        Timer t(m, wflops + 2.0 * B * kLayers[l].in_used * kLayers[l].out_used,
-                wbytes + alg_bytes(B, kLayers[l].in_used, kLayers[l].out_used, kBackward));
-        MLP_CUDA(m, cudaEventRecord(m->fork, st));
-        MLP_CUDA(m, cudaStreamWaitEvent(m->side, m->fork, 0));
-        MLP_CUDA(m, (launch_wgrad<kHid, kActLbw, 2>(g, splits, m->side)));
         MLP_CUDA(m, (launch_res<kHid / 2, 2, kActLbw, kBackward>(h, std::max(2, m->nsm - splits), st)));
-        MLP_CUDA(m, cudaEventRecord(m->join, m->side));
-        MLP_CUDA(m, cudaStreamWaitEvent(st, m->join, 0));
-        t.stop();
+        MLP_CUDA(m, cudaEventRecord(m->fork, st));  // dT_{l-1} is ready
     }
+    MLP_CUDA(m, cudaEventRecord(m->join, m->side));
+    MLP_CUDA(m, cudaStreamWaitEvent(st, m->join, 0));
+    t.stop();
     return STP_OK;
 }
 
