@@ -810,8 +810,8 @@ stp_status fail(stp_mlp* m, stp_status st, const std::string& msg) {
         if (e_ != cudaSuccess) return fail((m), STP_ERR_CUDA, cudaGetErrorString(e_)); \
     } while (0)
 
-// Split-K of the weight-gradient products: enough splits for one CTA per SM
-// over the two 128-row output tiles, at least four K stages each.
+// Split-K of the weight-gradient products: at most kSplitMax splits (the
+// partial buffers), at least four K stages each.
 constexpr int kSplitMax = 80;
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -942,7 +942,10 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
     const int mt = Bp / kTileM;
     cudaStream_t st = m->stream;
     const int KTb = Bp / kStageK;
-    const int target = std::max(1, std::min({kSplitMax, m->nsm / (kOutP / kTileM), KTb / 4}));
+    // Splits: the weight gradients of layers 2-4 take about 7/16 of the SMs
+    // (one CTA a split), the input gradients beside them the rest (measured
+    // balance of the two streams).
+    const int target = std::max(1, std::min({kSplitMax, m->nsm * 7 / 16, KTb / 4}));
     const int kps = (KTb + target - 1) / target;
     const int splits = (KTb + kps - 1) / kps;  // every split non-empty
     *nwpart = splits;
