@@ -53,8 +53,9 @@ constexpr int kMix = 8, kWp = 16, kWpDim = 8, kTgt = 130;
 // K stages through a four-stage pipeline, one CTA per SM.
 constexpr int kTileM = 128, kStageK = 64, kThreads = 256, kWStages = 4;
 constexpr float kSMin = -7.f, kSMax = 2.f;
-// Bias gradients: every 128-row tile (a GEMM CTA or a loss block) writes the
-// column sums of its rows as one partial [256]; Adam adds the partials.
+// Bias gradients: every 32 batch rows (a warp of an input-gradient epilogue
+// or of the loss kernel) write the column sums of their rows as one partial
+// [256]; Adam adds the partials in a fixed order.
 
 enum Mode { kHidden = 0, kOutput = 1, kBackward = 2, kWGrad = 3 };
 
@@ -654,19 +655,17 @@ __global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ T,
         L += mse / cnt;
         loss[n] = L;
     }
-    __shared__ float sb[kOutP];
-    for (int i = threadIdx.x; i < kOutP; i += blockDim.x) sb[i] = 0.f;
-    __syncthreads();
+    // Bias-gradient partial of each warp's 32 rows: row n / 32 of the
+    // partials, as the input-gradient products write theirs (no atomics, so
+    // the sums are the same on every run).
     for (int c0 = 0; c0 < kOutP; c0 += 16) {
         float v[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = g[c0 + i];
         store_row16(dyt, n, c0, Bp, v);
         const float cs = warp_colsum16(v);
-        if ((threadIdx.x & 31) < 16) atomicAdd(&sb[c0 + (threadIdx.x & 31)], cs);
+        if ((threadIdx.x & 31) < 16) bpart[(size_t)(n >> 5) * kOutP + c0 + (threadIdx.x & 31)] = cs;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kOutP; i += blockDim.x) bpart[(size_t)blockIdx.x * kOutP + i] = sb[i];
 }
 
 struct AdamArgs {
@@ -853,8 +852,8 @@ cudaError_t launch_res(const ResArgs& g, int max_ctas, cudaStream_t st, bool pdl
     return cudaLaunchKernelEx(&cfg, k_gemm_res<NU, KB, LBW, MODE>, g);
 }
 
-// Bias-gradient partials per layer: the input-gradient products write one
-// row per 32 batch rows, the loss kernel (last layer) one per 128.
+// Bias-gradient partials per layer: one row per 32 batch rows (written by the
+// input-gradient products, and for the last layer by the loss kernel).
 size_t bpart_stride(int Bp_max) { return (size_t)(Bp_max / 32) * kOutP; }
 
 // Algorithmic HBM bytes of one product of a training step at batch B over the
@@ -1041,8 +1040,7 @@ stp_status adam_impl(stp_mlp* m, int nwpart, int nbpart, float lr, bool update, 
         bb.m = m->mb[l];
         bb.v = m->vb[l];
         bb.gpart = m->bpart + (size_t)l * bpart_stride(m->Bp_max);
-        // The loss kernel writes the last layer's partials per 128 rows.
-        bb.nparts = l == 3 ? nbpart / 4 : nbpart;
+        bb.nparts = nbpart;
         bb.rows = L.out;
         bb.cols = 1;
         bb.wt = nullptr;

@@ -179,3 +179,29 @@ def test_training_lowers_heldout_loss(stp):
     after = M.batch_loss(stp.unflatten_params(net.get_params()), Xte, Tte)
     assert after < 0.5 * before, (before, after)
     net.close()
+
+
+def test_gradients_and_steps_are_reproducible(stp):
+    """The backward pass runs on two streams (weight gradients beside the input
+    gradients) and the forward products as dependent launches: two gradient
+    evaluations of the same batch, and two networks trained identically,
+    agree bit for bit (no order-dependent reductions, no races)."""
+    rng = np.random.default_rng(77)
+    B = 20000
+    P = M.init_params(rng)
+    X = _inputs(rng, B)
+    T = _targets(rng, X)
+    nets = [stp.Mlp(B), stp.Mlp(B)]
+    for net in nets:
+        net.set_params(stp.flatten_params(P))
+    l0, g0 = nets[0].gradients(X, T)
+    l1, g1 = nets[0].gradients(X, T)
+    assert l0 == l1 and np.array_equal(g0, g1)
+    for net in nets:
+        for _ in range(3):
+            net.train_step(X, T, 1e-3)
+    p0, p1 = nets[0].get_params(), nets[1].get_params()
+    assert np.array_equal(p0, p1)
+    assert not np.array_equal(p0, stp.flatten_params(P))
+    for net in nets:
+        net.close()
