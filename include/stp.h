@@ -182,6 +182,10 @@ typedef struct {
     long long nn_nodes;           /* NN scan: vertices of the scanned sets, once per set and iteration */
     long long bridge_evals;       /* bridge scan: (query, vertex) rank evaluations */
     long long bridge_nodes;       /* bridge scan: vertices of the scanned sets, once per set and iteration */
+    double step_ms;               /* device time of every GPU operation of the call (state reset, all
+                                     iterations, path extraction, statistics copy): CUDA events on the
+                                     problem's stream around them, so host-side gaps after the work
+                                     (synchronisation, return) are not counted; 0 without a plan */
 } stp_stats;
 
 /* Create a problem: validates and copies robot, obstacles, start, goal and

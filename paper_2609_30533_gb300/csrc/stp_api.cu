@@ -179,6 +179,7 @@ struct stp_problem {
     cudaStream_t graph_stream = nullptr;
     int graph_iters = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+    cudaEvent_t ev_step0 = nullptr, ev_step1 = nullptr;  // every GPU operation of a stp_plan call
     // batch scratch for stp_check_edges
     char* d_scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -703,6 +704,7 @@ stp_status plan_persistent_impl(stp_problem* p, Ctl* hc) {
     cudaStream_t st = p->stream;
     State<R>& S = state_of<R>(p);
     const int mi = p->prm.max_iters;
+    STP_CUDA(p, cudaEventRecord(p->ev_step0, st));
     STP_CUDA(p, cudaMemcpyAsync(p->d_pgeom, &geom_of<R>(p), sizeof(Geom<R>), cudaMemcpyHostToDevice, st));
     STP_CUDA(p, cudaMemcpyAsync(p->d_pstate, &S, sizeof(State<R>), cudaMemcpyHostToDevice, st));
     STP_CUDA(p, cudaMemcpyAsync(p->d_pmax_iters, &mi, sizeof(int), cudaMemcpyHostToDevice, st));
@@ -727,6 +729,7 @@ stp_status plan_persistent_impl(stp_problem* p, Ctl* hc) {
                                           persist_threads(false)));
     STP_CUDA(p, cudaEventRecord(p->ev1, st));
     STP_CUDA(p, cudaMemcpyAsync(hc, p->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    STP_CUDA(p, cudaEventRecord(p->ev_step1, st));
     STP_CUDA(p, cudaStreamSynchronize(st));
     // Step times (device global timer, barrier to barrier), in the order of
     // the per-step kernels' profile; the two bridge passes count together.
@@ -747,6 +750,7 @@ stp_status plan_impl(stp_problem* p, Ctl* hc) {
     stp_status s = capture_graph<R>(p);
     if (s != STP_OK) return s;
     const int G = p->graph_iters;
+    STP_CUDA(p, cudaEventRecord(p->ev_step0, st));
     if (p->d_trace)
         STP_CUDA(p, cudaMemsetAsync(p->d_trace, 0xff,
                                     sizeof(int) * (size_t)p->trace_iters * p->prm.ext_per_iter * kTraceInts, st));
@@ -789,6 +793,7 @@ stp_status plan_impl(stp_problem* p, Ctl* hc) {
     STP_CUDA(p, cudaEventRecord(p->ev1, st));
     STP_CUDA(p, launch_extract_path<R>(state_of<R>(p), p->dof, st));
     STP_CUDA(p, cudaMemcpyAsync(hc, p->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    STP_CUDA(p, cudaEventRecord(p->ev_step1, st));
     STP_CUDA(p, cudaStreamSynchronize(st));
     return STP_OK;
 }
@@ -1035,6 +1040,8 @@ stp_status stp_create_problem(const stp_robot* robot, const stp_obstacles* obs, 
     cudaEventCreate(&p->ev1);
     cudaEventCreate(&p->ev2);
     cudaEventCreate(&p->ev3);
+    cudaEventCreate(&p->ev_step0);
+    cudaEventCreate(&p->ev_step1);
     void* counters = nullptr;
     e = cache_alloc(&counters, 2 * sizeof(unsigned long long), &p->counters_block);
     p->d_counters = static_cast<unsigned long long*>(counters);
@@ -1100,6 +1107,9 @@ stp_status stp_plan(stp_problem* p, double* arrival_U, double* length_C, int* n_
         float ms = 0.f;
         cudaEventElapsedTime(&ms, p->ev0, p->ev1);
         st.plan_ms = ms;
+        float sms = 0.f;
+        cudaEventElapsedTime(&sms, p->ev_step0, p->ev_step1);
+        st.step_ms = sms;
         st.iterations = hc.iter;
         st.first_solution_iter = hc.first_iter;
         st.nodes = (long long)hc.st_ins;
@@ -1179,6 +1189,8 @@ void stp_free(stp_problem* p) {
     if (p->ev1) cudaEventDestroy(p->ev1);
     if (p->ev2) cudaEventDestroy(p->ev2);
     if (p->ev3) cudaEventDestroy(p->ev3);
+    if (p->ev_step0) cudaEventDestroy(p->ev_step0);
+    if (p->ev_step1) cudaEventDestroy(p->ev_step1);
     cache_stream_release(p->own_stream);
     cache_release(p->d_counters, p->counters_block);
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);

@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(NT, kPersistThreads / NT)
             }
             return;
         }
-        if (rank == 0 && threadIdx.x == 0) extract_path_body(S);
+        if (rank == 0) extract_path_body(S);  // the first CTA, every thread
     }
 }
 

@@ -424,6 +424,7 @@ __device__ __forceinline__ void reset_body(const State<R>& S, int max_iters) {
     if (t == 0) {
         c->iter = 0;
         c->err = 0;
+        c->v_arrive = 0;
         c->n_f = 1;
         c->snap_f = 1;
         c->n_trees = 0;
@@ -1710,7 +1711,9 @@ __device__ __forceinline__ void publish_body(const Geom<R>& G, const State<R>& S
     for (int w = t; w < S.W; w += blockDim.x) {
         // Bridge entry of worker w is entry w; all loads independent.
         const int e = S.w_bedge[w];
-        const int h = S.bhit[w];
+        // The bridge verdicts may have been written by other CTAs of the same
+        // launch (publish fused into the final bridge pass): read them from L2.
+        const int h = __ldcg(S.bhit + w);
         const R U = S.b_U[w], C = S.b_C[w];
         const int ws = S.w_set[w], wi = S.w_ins[w], bs = S.b_set[w], bi = S.b_idx[w];
         if (e >= 0 && h)
@@ -1836,30 +1839,60 @@ __device__ __forceinline__ void publish_body(const Geom<R>& G, const State<R>& S
 // inc_b to its root. One thread.
 template <typename R>
 __device__ __forceinline__ void extract_path_body(const State<R>& S) {
+    // The forward branch (incumbent's forward node back to the start) and the
+    // backward branch (its backward node up to the goal root) are walked once
+    // each, concurrently, by the first lanes of two warps into shared index
+    // lists; then every thread copies rows. Walks are bounded by the path
+    // capacity (parents always precede children, so a longer walk cannot occur
+    // in a consistent tree); a branch longer than the lists falls back to a
+    // second walk by one thread.
+    constexpr int kList = 512;
+    __shared__ int s_idx[2][kList];
+    __shared__ int s_len[2];
     const Ctl* c = S.ctl;
-    int n = 0;
-    if (c->inc_f >= 0) {
-        // Walks are bounded by the path capacity (parents always precede
-        // children, so a longer walk cannot occur in a consistent tree).
-        int len_f = 0;
-        for (int i = c->inc_f; i >= 0 && len_f <= S.path_cap; i = S.fpar[i]) ++len_f;
-        int len_b = 0;
-        for (int i = c->inc_b; i >= 0 && len_b <= S.path_cap; i = S.bpar[bofs(S, c->inc_s, i)]) ++len_b;
-        if (len_f + len_b <= S.path_cap) {
-            int k = len_f - 1;
-            for (int i = c->inc_f; i >= 0; i = S.fpar[i], --k) {
-                for (int j = 0; j < kDP; ++j) S.path[(size_t)k * kDP + j] = fnode(S, i)[j];
-            }
-            k = len_f;
-            for (int i = c->inc_b; i >= 0; i = S.bpar[bofs(S, c->inc_s, i)], ++k) {
-                for (int j = 0; j < kDP; ++j) S.path[(size_t)k * kDP + j] = bnode(S, c->inc_s, i)[j];
-            }
-            n = len_f + len_b;
-        } else {
-            n = -(len_f + len_b);
-        }
+    const int t = threadIdx.x;
+    const int inc_f = c->inc_f, inc_b = c->inc_b, inc_s = c->inc_s;
+    if (inc_f < 0) {
+        if (t == 0) *S.path_len = 0;
+        return;
     }
-    *S.path_len = n;
+    const int walker = blockDim.x >= 64 ? 32 : 0;  // thread of the backward walk
+    if (t == 0) {
+        int len = 0;
+        for (int i = inc_f; i >= 0 && len <= S.path_cap; i = S.fpar[i]) {
+            if (len < kList) s_idx[0][len] = i;
+            ++len;
+        }
+        s_len[0] = len;
+    }
+    if (t == walker) {
+        int len = 0;
+        for (int i = inc_b; i >= 0 && len <= S.path_cap; i = S.bpar[bofs(S, inc_s, i)]) {
+            if (len < kList) s_idx[1][len] = i;
+            ++len;
+        }
+        s_len[1] = len;
+    }
+    __syncthreads();
+    const int len_f = s_len[0], len_b = s_len[1];
+    if (len_f + len_b > S.path_cap) {
+        if (t == 0) *S.path_len = -(len_f + len_b);
+        return;
+    }
+    if (len_f <= kList && len_b <= kList) {
+        for (int k = t; k < len_f + len_b; k += blockDim.x) {
+            const R* x = k < len_f ? fnode(S, s_idx[0][len_f - 1 - k]) : bnode(S, inc_s, s_idx[1][k - len_f]);
+            for (int j = 0; j < kDP; ++j) S.path[(size_t)k * kDP + j] = x[j];
+        }
+    } else if (t == 0) {
+        int k = len_f - 1;
+        for (int i = inc_f; i >= 0; i = S.fpar[i], --k)
+            for (int j = 0; j < kDP; ++j) S.path[(size_t)k * kDP + j] = fnode(S, i)[j];
+        k = len_f;
+        for (int i = inc_b; i >= 0; i = S.bpar[bofs(S, inc_s, i)], ++k)
+            for (int j = 0; j < kDP; ++j) S.path[(size_t)k * kDP + j] = bnode(S, inc_s, i)[j];
+    }
+    if (t == 0) *S.path_len = len_f + len_b;
 }
 
 }  // namespace stp

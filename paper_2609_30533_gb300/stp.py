@@ -53,7 +53,7 @@ class StpStats(C.Structure):
                 ("root_checks", C.c_longlong), ("check_points", C.c_longlong), ("pair_tests", C.c_longlong),
                 ("first_solution_ms", C.c_double), ("plan_ms", C.c_double), ("U", C.c_double),
                 ("C", C.c_double), ("nn_evals", C.c_longlong), ("nn_nodes", C.c_longlong),
-                ("bridge_evals", C.c_longlong), ("bridge_nodes", C.c_longlong)]
+                ("bridge_evals", C.c_longlong), ("bridge_nodes", C.c_longlong), ("step_ms", C.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
