@@ -901,9 +901,7 @@ def main():
         plan_ms.append(st["plan_ms"])
         if st["first_solution_ms"] >= 0:
             fs_ms.append(st["first_solution_ms"])
-        # reset, 7 kernels per iteration (the FP32 chain publishes from the
-        # final bridge pass), path extraction
-        launches += 2 + 7 * args.iters
+        launches += 2 + 8 * args.iters  # reset, 8 kernels per iteration, path extraction
     torch.cuda.synchronize()
     if dist:
         dist.barrier()

@@ -125,7 +125,7 @@ struct EdgeBatch {
 // Planner control block (device memory).
 // ---------------------------------------------------------------------------
 struct Ctl {
-    int iter, done, err, v_arrive;  // v_arrive: CTAs done with the final bridge pass (fused publish)
+    int iter, done, err, pad0;
     int n_f, snap_f, n_trees, n_windows;
     int n_pieces, first_iter, inc_f, inc_s;
     int inc_b, max_iters, pad1, pad2;

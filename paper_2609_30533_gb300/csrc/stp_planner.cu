@@ -2,7 +2,6 @@
 // launchers (single problem and batched form); the device code of every step
 // lives in stp_planner_body.cuh, shared with the persistent planner kernel.
 #include "stp_planner_body.cuh"
-#include "stp_validate_body.cuh"
 
 namespace stp {
 
@@ -24,58 +23,6 @@ template <typename R>
 __global__ void __launch_bounds__(kCtaThreads) k_publish(Geom<R> G, State<R> S) { publish_body(G, S); }
 template <typename R>
 __global__ void k_extract_path(State<R> S) { extract_path_body(S); }
-
-// FP32 chain: the final bridge pass and the publish step in one launch. Every
-// CTA validates its share of the pass; the last CTA to arrive (counter in the
-// control block, reset by that CTA) publishes, so the iteration's critical
-// path loses one kernel boundary. The arrival follows the CTA's barrier and a
-// fence by its first thread, so every verdict is visible to the publisher.
-template <bool ARM, int MO>
-__global__ void __launch_bounds__(256, 2) k_validate_publish(Geom<float> G, State<float> S) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_last;
-    EdgeBatch<float> E = bridge_batch(S);
-    E.phase = 2;
-    validate_body<float, ARM, MO, false, true>(G, E, smem_raw, blockIdx.x, gridDim.x);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(&S.ctl->v_arrive, 1) == (int)gridDim.x - 1;
-    }
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        publish_body(G, S);
-        if (threadIdx.x == 0) S.ctl->v_arrive = 0;
-    }
-}
-
-template <bool ARM, int MO>
-static cudaError_t launch_vp(const Geom<float>& g, const State<float>& s, int grid_blocks, cudaStream_t st) {
-    auto kern = k_validate_publish<ARM, MO>;
-    static SmemAttr attr;
-    static int blocks_per_sm[kMaxDevices] = {};
-    const int smem = (int)g.blob_bytes + (int)sizeof(int) * (s.W + 1);
-    bool raised = false;
-    cudaError_t err = ensure_smem((const void*)kern, attr, smem, &raised);
-    if (err != cudaSuccess) return err;
-    int dev = 0;
-    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
-    if (raised || blocks_per_sm[dev] == 0) {
-        int b = 0;
-        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 256, smem)) != cudaSuccess) return err;
-        blocks_per_sm[dev] = b < 1 ? 1 : b;
-    }
-    const int grid = grid_blocks > 0 ? grid_blocks : validate_grid_blocks() * blocks_per_sm[dev];
-    kern<<<grid, 256, smem, st>>>(g, s);
-    return cudaGetLastError();
-}
-
-static cudaError_t launch_validate_publish(const Geom<float>& g, const State<float>& s, int grid_blocks,
-                                           cudaStream_t st) {
-    if (g.arm) return g.M <= 8 ? launch_vp<true, 8>(g, s, grid_blocks, st) : launch_vp<true, 16>(g, s, grid_blocks, st);
-    return g.M <= 8 ? launch_vp<false, 8>(g, s, grid_blocks, st) : launch_vp<false, 16>(g, s, grid_blocks, st);
-}
 
 template <typename R>
 __global__ void k_reset_b(const State<R>* Ss, const int* max_iters) {
@@ -172,24 +119,17 @@ cudaError_t launch_iteration(const Geom<R>& g, const State<R>& s, int vgrid, cud
     mark();
     // Bridges are long: a coarse pass over every eighth check point finds most
     // collisions, then only the entries it left free are checked in full.
-    // FP32: the full pass publishes from its last CTA (the publish interval of
-    // the kernel profile is then empty and its time counts in the bridge
-    // passes); FP64 keeps a separate publish kernel.
     {
         EdgeBatch<R> bb = bridge_batch(s);
         bb.phase = 1;
         err = launch_validate<R>(g, bb, false, true, vgrid, st);
         if (err != cudaSuccess) return err;
-        if constexpr (sizeof(R) == 4) {
-            err = launch_validate_publish(g, s, vgrid, st);
-        } else {
-            bb.phase = 2;
-            err = launch_validate<R>(g, bb, false, true, vgrid, st);
-        }
+        bb.phase = 2;
+        err = launch_validate<R>(g, bb, false, true, vgrid, st);
         if (err != cudaSuccess) return err;
     }
     mark();
-    if constexpr (sizeof(R) != 4) k_publish<R><<<1, kCtaThreads, 0, st>>>(g, s);
+    k_publish<R><<<1, kCtaThreads, 0, st>>>(g, s);
     mark();
     return cudaGetLastError();
 }

@@ -424,7 +424,6 @@ __device__ __forceinline__ void reset_body(const State<R>& S, int max_iters) {
     if (t == 0) {
         c->iter = 0;
         c->err = 0;
-        c->v_arrive = 0;
         c->n_f = 1;
         c->snap_f = 1;
         c->n_trees = 0;
@@ -1711,9 +1710,7 @@ __device__ __forceinline__ void publish_body(const Geom<R>& G, const State<R>& S
     for (int w = t; w < S.W; w += blockDim.x) {
         // Bridge entry of worker w is entry w; all loads independent.
         const int e = S.w_bedge[w];
-        // The bridge verdicts may have been written by other CTAs of the same
-        // launch (publish fused into the final bridge pass): read them from L2.
-        const int h = __ldcg(S.bhit + w);
+        const int h = S.bhit[w];
         const R U = S.b_U[w], C = S.b_C[w];
         const int ws = S.w_set[w], wi = S.w_ins[w], bs = S.b_set[w], bi = S.b_idx[w];
         if (e >= 0 && h)
