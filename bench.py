@@ -657,6 +657,7 @@ def mlp_throughput(rank, B=65536, reps=3):
     for _ in range(reps):
         net.train_step(X, T, 0.0)
     gms, gfl, gby = net.profile()
+    sms, nst = net.profile_step()
     net.close()
     peak = float(_peaks().get("bf16_tflops", 1917.3))
     hbm = float(_peaks().get("hbm_gbs", 6801.7))
@@ -665,6 +666,9 @@ def mlp_throughput(rank, B=65536, reps=3):
     return {"batch": B, "gemm_ms_per_step": gms / reps, "gemm_flops_per_step": gfl / reps,
             "gemm_bytes_per_step": gby / reps, "tflops": tf, "peak_tflops": peak, "frac": tf / peak,
             "gbs": gbs, "peak_gbs": hbm, "hbm_frac": gbs / hbm,
+            "train_ms_per_step": sms / nst if nst else None,
+            "train_note": "device time of the whole training step (input packing, forward chain, loss, backward "
+                          "pass, gradient sums, Adam), CUDA events on the network's stream, inputs staged",
             "note": "BF16 tcgen05 GEMMs of forward + backward training steps; CUDA events around the forward "
                     "chain (four products) and around the backward pass (input gradients on the main stream, "
                     "weight gradients beside them), GEMM launches only; algorithmic bytes over the logical layer "

@@ -455,6 +455,13 @@ stp_status stp_mlp_train_step(stp_mlp *m, int B, const float *x, const float *ta
  * written once in one layout. */
 stp_status stp_mlp_set_profiling(stp_mlp *m, int on);
 stp_status stp_mlp_profile(stp_mlp *m, double *gemm_ms, double *gemm_flops, double *gemm_bytes);
+/* With profiling on, the device work of each stp_mlp_train_step and
+ * stp_mlp_gradients call (input packing, forward chain, loss, backward pass,
+ * gradient sums and parameter update; not the staging copies of x and the
+ * targets, nor the loss read-back) is bracketed by CUDA events on the
+ * network's stream; stp_mlp_profile_step returns (and clears) the total ms
+ * and the number of steps. Either pointer may be NULL. */
+stp_status stp_mlp_profile_step(stp_mlp *m, double *step_ms, int *steps);
 const char *stp_mlp_last_error(const stp_mlp *m);
 
 /* Training targets t[STP_MLP_NTGT] of the path found by the last stp_plan or

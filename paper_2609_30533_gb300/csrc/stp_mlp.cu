@@ -591,80 +591,192 @@ __global__ void __launch_bounds__(kResThreads, 1) k_gemm_res(ResArgs g) {
 // ---------------------------------------------------------------------------
 // Elementwise kernels.
 // ---------------------------------------------------------------------------
-// FP32 features [B][32] -> BF16 tiled [Bp][64] (zero padded).
+// FP32 features [B][32] -> BF16 tiled [Bp][64] (zero padded). Thread i
+// writes the 16-byte piece i of the tiled buffer: row 8 (i / 64) + i % 8,
+// columns 8 ((i / 8) % 8) .. + 7, so consecutive threads store consecutive
+// pieces.
 __global__ void k_pack_input(const float* __restrict__ X, int B, int Bp, __nv_bfloat16* xt) {
+    static_assert(lbw_of(kInP) == 6 && kInP == 64 && kIn % 8 == 0, "one 64-wide column block");
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Bp * kInP) return;
-    const int r = i / kInP, c = i % kInP;
-    const float v = (r < B && c < kIn) ? X[(size_t)r * kIn + c] : 0.f;
-    xt[tixb(r, c, Bp, lbw_of(kInP))] = __float2bfloat16_rn(v);
+    if (i >= Bp * (kInP / 8)) return;
+    const int r = 8 * (i >> 6) + (i & 7), c = (i >> 3) & 7;
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (r < B && 8 * c < kIn) {
+        const float4* src = reinterpret_cast<const float4*>(X + (size_t)r * kIn + 8 * c);
+        const float4 u0 = __ldg(src), u1 = __ldg(src + 1);
+        v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
+        v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
+    }
+    __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) h[q] = __float2bfloat16_rn(v[q]);
+    *reinterpret_cast<uint4*>(xt + (size_t)i * 8) = *reinterpret_cast<const uint4*>(h);
 }
 
 // Per-sample loss (mixture NLL of tau + masked waypoint MSE) and dL/dy / B.
-__global__ void k_loss(const float* __restrict__ Y, const float* __restrict__ T, int B, int Bp, float* bpart,
-                       __nv_bfloat16* dyt, float* loss) {
-    // Bp is a multiple of the 128-thread block: every thread has a row.
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    float g[kOutP];
-#pragma unroll 1
-    for (int c = 0; c < kOutP; ++c) g[c] = 0.f;
-    if (n < B) {
-        const float* y = Y + (size_t)n * kOutP;
-        const float* t = T + (size_t)n * kTgt;
-        const float tau = t[0];
-        const int dof = (int)t[kTgt - 1];
-        float amax = -INFINITY;
-        for (int k = 0; k < kMix; ++k) amax = fmaxf(amax, y[k]);
-        float asum = 0.f;
-        for (int k = 0; k < kMix; ++k) asum += expf(y[k] - amax);
-        const float lse_a = amax + logf(asum);
-        float l[kMix], z[kMix], sig[kMix];
-        float lmax = -INFINITY;
-        for (int k = 0; k < kMix; ++k) {
-            const float s = fminf(fmaxf(y[2 * kMix + k], kSMin), kSMax);
-            sig[k] = expf(s);
-            z[k] = (tau - y[kMix + k]) / sig[k];
-            l[k] = (y[k] - lse_a) - 0.5f * z[k] * z[k] - s - 0.91893853320467274f;
-            lmax = fmaxf(lmax, l[k]);
-        }
-        float lsum = 0.f;
-        for (int k = 0; k < kMix; ++k) lsum += expf(l[k] - lmax);
-        const float lse_l = lmax + logf(lsum);
-        float L = -lse_l;
-        const float invB = 1.f / (float)B;
-        for (int k = 0; k < kMix; ++k) {
-            const float gam = expf(l[k] - lse_l);
-            const float pi = expf(y[k] - lse_a);
-            const float sr = y[2 * kMix + k];
-            g[k] = (pi - gam) * invB;
-            g[kMix + k] = -gam * z[k] / sig[k] * invB;
-            g[2 * kMix + k] = (sr >= kSMin && sr <= kSMax) ? gam * (1.f - z[k] * z[k]) * invB : 0.f;
-        }
-        const float cnt = (float)(kWp * (dof + 1));
-        float mse = 0.f;
-        for (int i = 0; i < kWp; ++i) {
-            for (int j = 0; j < kWpDim; ++j) {
-                if (j < dof || j == kWpDim - 1) {
-                    const int o = 3 * kMix + i * kWpDim + j;
-                    const float e = y[o] - t[1 + i * kWpDim + j];
-                    mse += e * e;
-                    g[o] = 2.f * e / cnt * invB;
-                }
-            }
-        }
-        L += mse / cnt;
-        loss[n] = L;
-    }
-    // Bias-gradient partial of each warp's 32 rows: row n / 32 of the
-    // partials, as the input-gradient products write theirs (no atomics, so
-    // the sums are the same on every run).
-    for (int c0 = 0; c0 < kOutP; c0 += 16) {
-        float v[16];
+// A CTA takes 32 consecutive rows (one bias-gradient partial): their network
+// outputs and targets are staged in shared memory by coalesced 16-byte loads
+// (the 32 target rows are one contiguous block), four threads share a row
+// (mixture components p and p + 4, waypoint elements p, p + 4, ...; the row's
+// reductions are shuffles within the four lanes), the gradient overwrites
+// the staged outputs, and the CTA then writes its BF16 tiles with consecutive
+// threads on consecutive 16-byte pieces, the 256 column sums of its rows, and
+// the row losses.
+constexpr int kLossRows = 32, kLossThreads = 128;
+constexpr int kLossYS = kOut + 4;                 // staged row stride (floats)
+constexpr int kOutUsed = 3 * kMix + kWp * kWpDim;  // 152 network outputs in use
+static_assert(kLossThreads == 4 * kLossRows, "four threads per row");
+static_assert(kMix == 8 && kWpDim == 8 && (kWp * kWpDim) % 4 == 0, "components and elements split over four lanes");
+static_assert((kLossRows * kTgt) % 4 == 0 && (kLossYS * 4) % 16 == 0, "16-byte staging");
+
+__global__ void __launch_bounds__(kLossThreads) k_loss(const float* __restrict__ Y, const float* __restrict__ T,
+                                                       int B, float* bpart, __nv_bfloat16* dyt, int Bp,
+                                                       float* loss) {
+    __shared__ __align__(16) float sy[kLossRows * kLossYS];
+    __shared__ __align__(16) float st[kLossRows * kTgt];
+    const int tid = threadIdx.x;
+    const int n0 = blockIdx.x * kLossRows;
+    const int nrow = max(0, min(kLossRows, B - n0));  // rows of this CTA inside the batch
+    constexpr int kYv = kOut / 4;                     // float4 per output row
+    constexpr int kTv = kLossRows * kTgt / 4;         // float4 of a full target block
+    if (nrow == kLossRows) {
+        // Row n0 of the targets starts at byte 520 n0, a multiple of 16 (n0 % 32 == 0).
+        float4 yv[kLossRows * kYv / kLossThreads];
+        float4 tv[(kTv + kLossThreads - 1) / kLossThreads];
+        const float4* t4 = reinterpret_cast<const float4*>(T + (size_t)n0 * kTgt);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = g[c0 + i];
-        store_row16(dyt, n, c0, Bp, v);
-        const float cs = warp_colsum16(v);
-        if ((threadIdx.x & 31) < 16) bpart[(size_t)(n >> 5) * kOutP + c0 + (threadIdx.x & 31)] = cs;
+        for (int q = 0; q < kLossRows * kYv / kLossThreads; ++q) {
+            const int i = tid + q * kLossThreads, r = i / kYv, c = i % kYv;
+            yv[q] = __ldg(reinterpret_cast<const float4*>(Y + (size_t)(n0 + r) * kOutP) + c);
+        }
+#pragma unroll
+        for (int q = 0; q < (kTv + kLossThreads - 1) / kLossThreads; ++q) {
+            const int i = tid + q * kLossThreads;
+            if (i < kTv) tv[q] = __ldg(t4 + i);
+        }
+#pragma unroll
+        for (int q = 0; q < kLossRows * kYv / kLossThreads; ++q) {
+            const int i = tid + q * kLossThreads, r = i / kYv, c = i % kYv;
+            *reinterpret_cast<float4*>(sy + r * kLossYS + 4 * c) = yv[q];
+        }
+#pragma unroll
+        for (int q = 0; q < (kTv + kLossThreads - 1) / kLossThreads; ++q) {
+            const int i = tid + q * kLossThreads;
+            if (i < kTv) reinterpret_cast<float4*>(st)[i] = tv[q];
+        }
+    } else if (nrow > 0) {  // the batch's last, partial CTA
+        for (int i = tid; i < nrow * kYv; i += kLossThreads) {
+            const int r = i / kYv, c = i % kYv;
+            *reinterpret_cast<float4*>(sy + r * kLossYS + 4 * c) =
+                __ldg(reinterpret_cast<const float4*>(Y + (size_t)(n0 + r) * kOutP) + c);
+        }
+        for (int i = tid; i < nrow * kTgt; i += kLossThreads) st[i] = __ldg(T + (size_t)n0 * kTgt + i);
+    }
+    __syncthreads();
+
+    // Every lane runs the row arithmetic (the shuffles need the whole warp);
+    // rows past the batch read zeros and write nothing.
+    const int r = tid >> 2, p = tid & 3;
+    const bool valid = r < nrow;
+    float* y = sy + r * kLossYS;
+    const float* t = st + r * kTgt;
+    const float invB = 1.f / (float)B;
+    const float tau = valid ? t[0] : 0.f;
+    const int dof = valid ? (int)t[kTgt - 1] : 0;
+    // Mixture over tau: this thread's components p and p + 4.
+    float a[2], l[2], z[2], sig[2], sr[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = p + 4 * h;
+        a[h] = valid ? y[k] : 0.f;
+        sr[h] = valid ? y[2 * kMix + k] : 0.f;
+        const float mu = valid ? y[kMix + k] : 0.f;
+        const float s = fminf(fmaxf(sr[h], kSMin), kSMax);
+        sig[h] = expf(s);
+        z[h] = (tau - mu) / sig[h];
+        l[h] = -0.5f * z[h] * z[h] - s - 0.91893853320467274f;  // log N(tau; mu, sig)
+    }
+    float amax = fmaxf(a[0], a[1]);
+    amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 1));
+    amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, 2));
+    float asum = expf(a[0] - amax) + expf(a[1] - amax);
+    asum += __shfl_xor_sync(0xffffffffu, asum, 1);
+    asum += __shfl_xor_sync(0xffffffffu, asum, 2);
+    const float lse_a = amax + logf(asum);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) l[h] += a[h] - lse_a;
+    float lmax = fmaxf(l[0], l[1]);
+    lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, 1));
+    lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, 2));
+    float lsum = expf(l[0] - lmax) + expf(l[1] - lmax);
+    lsum += __shfl_xor_sync(0xffffffffu, lsum, 1);
+    lsum += __shfl_xor_sync(0xffffffffu, lsum, 2);
+    const float lse_l = lmax + logf(lsum);
+    // Waypoints: element e = 4 m + p (waypoint e / 8, coordinate e % 8);
+    // the coordinates in use are the arm's dof joints and the time.
+    const float cnt = (float)(kWp * (dof + 1));
+    float mse = 0.f;
+    if (valid) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = p + 4 * h;
+            const float gam = expf(l[h] - lse_l);
+            const float pi = expf(a[h] - lse_a);
+            y[k] = (pi - gam) * invB;
+            y[kMix + k] = -gam * z[h] / sig[h] * invB;
+            y[2 * kMix + k] = (sr[h] >= kSMin && sr[h] <= kSMax) ? gam * (1.f - z[h] * z[h]) * invB : 0.f;
+        }
+#pragma unroll 8
+        for (int m = 0; m < kWp * kWpDim / 4; ++m) {
+            const int e = 4 * m + p, j = e & (kWpDim - 1);
+            const int o = 3 * kMix + e;
+            float g = 0.f;
+            if (j < dof || j == kWpDim - 1) {
+                const float d = y[o] - t[1 + e];
+                mse += d * d;
+                g = 2.f * d / cnt * invB;
+            }
+            y[o] = g;
+        }
+    }
+    mse += __shfl_xor_sync(0xffffffffu, mse, 1);
+    mse += __shfl_xor_sync(0xffffffffu, mse, 2);
+    if (valid && p == 0) loss[n0 + r] = -lse_l + mse / cnt;
+    __syncthreads();
+
+    // dL/dy as BF16 tiles: piece c = (s, core matrix cm, row i) holds columns
+    // 128 (s & 1) + 8 cm .. + 7 of row 8 (s >> 1) + i; the 128 pieces of one
+    // (s, cm) range are 2 KB of contiguous memory.
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int c = tid + s * kLossThreads;
+        const int i = c & 7, cm = (c >> 3) & 15;
+        const int rr = 8 * (s >> 1) + i, k0 = 128 * (s & 1) + 8 * cm;
+        float v[8];
+        if (rr < nrow && k0 < kOutUsed) {
+            const float4 u0 = *reinterpret_cast<const float4*>(sy + rr * kLossYS + k0);
+            const float4 u1 = *reinterpret_cast<const float4*>(sy + rr * kLossYS + k0 + 4);
+            v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
+            v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = 0.f;
+        }
+        __align__(16) __nv_bfloat16 b[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) b[q] = __float2bfloat16_rn(v[q]);
+        *reinterpret_cast<uint4*>(dyt + tixb(n0 + rr, k0, Bp, kActLbw)) = *reinterpret_cast<const uint4*>(b);
+    }
+    // Bias-gradient partial of these 32 rows (row n0 / 32 of the partials,
+    // as the input-gradient products write theirs; rows added in order, no
+    // atomics, so the sums are the same on every run).
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int col = tid + h * kLossThreads;
+        float sum = 0.f;
+        if (col < kOutUsed)
+            for (int rr = 0; rr < nrow; ++rr) sum += sy[rr * kLossYS + col];
+        bpart[(size_t)blockIdx.x * kOutP + col] = sum;
     }
 }
 
@@ -705,34 +817,87 @@ __device__ __forceinline__ void adam_apply(const AdamArgs& a, int i, float gsum)
     }
 }
 
-// Weights: one thread per element sums its split-K partials in split order.
-__global__ void k_adam(AdamArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = a.rows * a.cols;
-    if (i >= n) return;
-    float gsum = 0.f;
-    if (a.gpart)
-        for (int p = 0; p < a.nparts; ++p) gsum += a.gpart[(size_t)p * n + i];
-    adam_apply(a, i, gsum);
-}
+// Every parameter tensor of one Adam step in one launch. Blocks
+// [0, wblk[4]) take 1,024 weight elements each: a thread sums the split-K
+// partials of four consecutive elements in split order, eight 16-byte loads in
+// flight. The remaining blocks take 16 bias elements each: 64 row lanes sum
+// the per-32-row partials (lane k: rows k, k + 64, ...) and the lanes' sums
+// are added in lane order. Fixed orders throughout, so every run gives the
+// same sums.
+struct AdamAll {
+    AdamArgs t[8];  // weights of layer l at 2 l, its bias at 2 l + 1
+    int wblk[5];    // weight blocks before layer l
+    int bblk[5];    // bias blocks before layer l
+};
+constexpr int kAdamThreads = 256, kAdamWElems = 4 * kAdamThreads, kAdamBElems = 16, kAdamLanes = 64;
+static_assert(kAdamLanes * (kAdamBElems / 4) == kAdamThreads, "bias block shape");
 
-// Biases: thousands of partial rows (one per 32 batch rows). A block takes
-// 32 elements; warp w sums partials w, w + warps, ... (coalesced rows), the
-// warps' sums are added in warp order, and the first warp takes the step.
-__global__ void k_adam_vec(AdamArgs a) {
-    __shared__ float part[32][33];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int n = a.rows * a.cols;
-    const int i = blockIdx.x * 32 + lane;
-    float s = 0.f;
-    if (a.gpart && i < n)
-        for (int p = w; p < a.nparts; p += nw) s += a.gpart[(size_t)p * n + i];
-    part[w][lane] = s;
+__global__ void __launch_bounds__(kAdamThreads) k_adam_all(const __grid_constant__ AdamAll A) {
+    __shared__ float part[kAdamLanes][kAdamBElems + 1];
+    int b = blockIdx.x;
+    if (b < A.wblk[4]) {
+        int l = 0;
+        while (l < 3 && b >= A.wblk[l + 1]) ++l;
+        const AdamArgs& a = A.t[2 * l];
+        const int n = a.rows * a.cols;
+        const int i0 = (b - A.wblk[l]) * kAdamWElems + 4 * (int)threadIdx.x;
+        if (i0 >= n) return;
+        float g[4] = {0.f, 0.f, 0.f, 0.f};
+        if (a.gpart) {
+            const float4* src = reinterpret_cast<const float4*>(a.gpart + i0);
+            const size_t stride = (size_t)n / 4;
+            int p = 0;
+            for (; p + 8 <= a.nparts; p += 8) {
+                float4 v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = src[(size_t)(p + q) * stride];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    g[0] += v[q].x;
+                    g[1] += v[q].y;
+                    g[2] += v[q].z;
+                    g[3] += v[q].w;
+                }
+            }
+            for (; p < a.nparts; ++p) {
+                const float4 v = src[(size_t)p * stride];
+                g[0] += v.x;
+                g[1] += v.y;
+                g[2] += v.z;
+                g[3] += v.w;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) adam_apply(a, i0 + q, g[q]);
+        return;
+    }
+    b -= A.wblk[4];
+    int l = 0;
+    while (l < 3 && b >= A.bblk[l + 1]) ++l;
+    const AdamArgs& a = A.t[2 * l + 1];
+    const int n = a.rows;  // a bias: rows x 1
+    const int c0 = (b - A.bblk[l]) * kAdamBElems;
+    const int quad = threadIdx.x & 3, lane = threadIdx.x >> 2;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    if (a.gpart && c0 + 4 * quad < n) {
+        const float* src = a.gpart + c0 + 4 * quad;
+#pragma unroll 8
+        for (int p = lane; p < a.nparts; p += kAdamLanes) {
+            const float4 v = *reinterpret_cast<const float4*>(src + (size_t)p * n);
+            s[0] += v.x;
+            s[1] += v.y;
+            s[2] += v.z;
+            s[3] += v.w;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) part[lane][4 * quad + q] = s[q];
     __syncthreads();
-    if (w == 0 && i < n) {
+    const int e = threadIdx.x;
+    if (e < kAdamBElems && c0 + e < n) {
         float g = 0.f;
-        for (int k = 0; k < nw; ++k) g += part[k][lane];
-        adam_apply(a, i, g);
+        for (int k = 0; k < kAdamLanes; ++k) g += part[k][e];
+        adam_apply(a, c0 + e, g);
     }
 }
 
@@ -790,8 +955,14 @@ struct stp_mlp {
     cudaEvent_t fork = nullptr, join = nullptr;
     int step = 0;
     bool profiling = false;
-    cudaEvent_t ev[2]{};
+    // Profiling intervals: 0 forward chain, 1 backward pass, 2 whole training
+    // step (event pairs 2i, 2i + 1), read once the stream has been synchronised.
+    cudaEvent_t ev[6]{};
+    bool ev_pending[3]{};
+    double ev_flops[3]{}, ev_bytes[3]{};
     double gemm_ms = 0, gemm_flops = 0, gemm_bytes = 0;
+    double step_ms = 0;
+    int steps = 0;
     std::string last_error;
 };
 
@@ -871,30 +1042,41 @@ double alg_bytes(int B, int in, int out, int mode) {
     return 2 * b * o + 2 * i * o + 2 * b * i + 2 * b * i;  // kBackward
 }
 
-struct Timer {
-    stp_mlp* m;
-    double flops, bytes;
-    Timer(stp_mlp* mm, double f, double by) : m(mm), flops(f), bytes(by) {
-        if (m->profiling) cudaEventRecord(m->ev[0], m->stream);
-    }
-    void stop() {
-        if (!m->profiling) return;
-        cudaEventRecord(m->ev[1], m->stream);
-        cudaEventSynchronize(m->ev[1]);
+// Event interval `slot` on the main stream (no host synchronisation inside
+// a call: the intervals are read by collect_profile after the stream sync).
+void interval_start(stp_mlp* m, int slot) {
+    if (m->profiling) cudaEventRecord(m->ev[2 * slot], m->stream);
+}
+void interval_stop(stp_mlp* m, int slot, double flops, double bytes) {
+    if (!m->profiling) return;
+    cudaEventRecord(m->ev[2 * slot + 1], m->stream);
+    m->ev_pending[slot] = true;
+    m->ev_flops[slot] = flops;
+    m->ev_bytes[slot] = bytes;
+}
+void collect_profile(stp_mlp* m) {
+    for (int slot = 0; slot < 3; ++slot) {
+        if (!m->ev_pending[slot]) continue;
+        m->ev_pending[slot] = false;
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, m->ev[0], m->ev[1]);
-        m->gemm_ms += ms;
-        m->gemm_flops += flops;
-        m->gemm_bytes += bytes;
+        if (cudaEventElapsedTime(&ms, m->ev[2 * slot], m->ev[2 * slot + 1]) != cudaSuccess) continue;
+        if (slot == 2) {
+            m->step_ms += ms;
+            ++m->steps;
+        } else {
+            m->gemm_ms += ms;
+            m->gemm_flops += m->ev_flops[slot];
+            m->gemm_bytes += m->ev_bytes[slot];
+        }
     }
-};
+}
 
 stp_status forward_impl(stp_mlp* m, int B) {
     const int Bp = (B + kTileM - 1) / kTileM * kTileM;
     const int mt = Bp / kTileM;
     cudaStream_t st = m->stream;
     {
-        const int n = Bp * kInP;
+        const int n = Bp * (kInP / 8);
         k_pack_input<<<(n + 255) / 256, 256, 0, st>>>(m->X, B, Bp, m->xt);
         MLP_CUDA(m, cudaGetLastError());
     }
@@ -907,7 +1089,7 @@ stp_status forward_impl(stp_mlp* m, int B) {
         chain_flops += 2.0 * B * L.in_used * L.out_used;
         chain_bytes += alg_bytes(B, L.in_used, L.out_used, l < 3 ? kHidden : kOutput);
     }
-    Timer t(m, chain_flops, chain_bytes);
+    interval_start(m, 0);
     const __nv_bfloat16* in = m->xt;
     for (int l = 0; l < 4; ++l) {
         const Layer& L = kLayers[l];
@@ -930,7 +1112,7 @@ stp_status forward_impl(stp_mlp* m, int B) {
             MLP_CUDA(m, (launch_res<kOut / 2, 2, kActLbw, kOutput>(g, m->nsm, st, true)));
         }
     }
-    t.stop();
+    interval_stop(m, 0, chain_flops, chain_bytes);
     return STP_OK;
 }
 
@@ -963,7 +1145,7 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
             chain_bytes += alg_bytes(B, kLayers[l].in_used, kLayers[l].out_used, kBackward);
         }
     }
-    Timer t(m, chain_flops, chain_bytes);
+    interval_start(m, 1);
     MLP_CUDA(m, cudaEventRecord(m->fork, st));  // dT_3 (the loss gradient) is ready
     for (int l = 3; l >= 0; --l) {
         // weight gradient: dW_l = dT_l^T . act_{l-1}   (M = out, N = in, K = batch)
@@ -1000,7 +1182,7 @@ stp_status backward_impl(stp_mlp* m, int B, int* nwpart, int* nbpart) {
     }
     MLP_CUDA(m, cudaEventRecord(m->join, m->side));
     MLP_CUDA(m, cudaStreamWaitEvent(st, m->join, 0));
-    t.stop();
+    interval_stop(m, 1, chain_flops, chain_bytes);
     return STP_OK;
 }
 
@@ -1010,6 +1192,7 @@ stp_status adam_impl(stp_mlp* m, int nwpart, int nbpart, float lr, bool update, 
     const float c1 = update ? 1.f - powf(b1, (float)m->step) : 1.f;
     const float c2 = update ? 1.f - powf(b2, (float)m->step) : 1.f;
     float* gout = m->gsum;
+    AdamAll A{};
     for (int l = 0; l < 4; ++l) {
         const Layer& L = kLayers[l];
         AdamArgs a{};
@@ -1031,14 +1214,13 @@ stp_status adam_impl(stp_mlp* m, int nwpart, int nbpart, float lr, bool update, 
         a.c1 = c1;
         a.c2 = c2;
         a.update = update ? 1 : 0;
-        int n = L.out * L.in;
-        k_adam<<<(n + 255) / 256, 256, 0, m->stream>>>(a);
-        MLP_CUDA(m, cudaGetLastError());
+        const int n = L.out * L.in;
         gout += n;
         AdamArgs bb = a;
         bb.w = m->b[l];
         bb.m = m->mb[l];
         bb.v = m->vb[l];
+        // bias partials are [chunk][256]: element e of chunk p at p * 256 + e
         bb.gpart = m->bpart + (size_t)l * bpart_stride(m->Bp_max);
         bb.nparts = nbpart;
         bb.rows = L.out;
@@ -1046,12 +1228,14 @@ stp_status adam_impl(stp_mlp* m, int nwpart, int nbpart, float lr, bool update, 
         bb.wt = nullptr;
         bb.wtT = nullptr;
         bb.gout = keep_grads ? gout : nullptr;
-        // bias partials are [chunk][256]: view as [rows = 256][cols = 1] per chunk
-        n = L.out;
-        k_adam_vec<<<(n + 31) / 32, 1024, 0, m->stream>>>(bb);
-        MLP_CUDA(m, cudaGetLastError());
-        gout += n;
+        gout += L.out;
+        A.t[2 * l] = a;
+        A.t[2 * l + 1] = bb;
+        A.wblk[l + 1] = A.wblk[l] + (n + kAdamWElems - 1) / kAdamWElems;
+        A.bblk[l + 1] = A.bblk[l] + (L.out + kAdamBElems - 1) / kAdamBElems;
     }
+    k_adam_all<<<A.wblk[4] + A.bblk[4], kAdamThreads, 0, m->stream>>>(A);
+    MLP_CUDA(m, cudaGetLastError());
     return STP_OK;
 }
 
@@ -1066,6 +1250,7 @@ stp_status check_err(stp_mlp* m) {
     int e = 0;
     MLP_CUDA(m, cudaMemcpyAsync(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
     MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+    collect_profile(m);
     if (e) {
         cudaMemsetAsync(m->err, 0, sizeof(int), m->stream);
         return fail(m, STP_ERR_TIMEOUT, "tensor-core pipeline wait exceeded its limit");
@@ -1142,8 +1327,9 @@ stp_status stp_mlp_create(int max_batch, stp_mlp** out) {
         *p.first = m->arena + off;
         off += up256(p.second);
     }
-    if (cudaMemset(m->arena, 0, total) != cudaSuccess || cudaEventCreate(&m->ev[0]) != cudaSuccess ||
-        cudaEventCreate(&m->ev[1]) != cudaSuccess ||
+    bool events_ok = true;
+    for (cudaEvent_t& e : m->ev) events_ok = events_ok && cudaEventCreate(&e) == cudaSuccess;
+    if (cudaMemset(m->arena, 0, total) != cudaSuccess || !events_ok ||
         cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->join, cudaEventDisableTiming) != cudaSuccess) {
@@ -1160,8 +1346,8 @@ void stp_mlp_free(stp_mlp* m) {
     else cudaDeviceSynchronize();
     if (m->side) cudaStreamSynchronize(m->side);
     cudaFree(m->arena);
-    if (m->ev[0]) cudaEventDestroy(m->ev[0]);
-    if (m->ev[1]) cudaEventDestroy(m->ev[1]);
+    for (cudaEvent_t e : m->ev)
+        if (e) cudaEventDestroy(e);
     if (m->fork) cudaEventDestroy(m->fork);
     if (m->join) cudaEventDestroy(m->join);
     if (m->side) cudaStreamDestroy(m->side);
@@ -1236,10 +1422,11 @@ static stp_status loss_grad(stp_mlp* m, int B, const float* X, const float* T, i
     stp_status s = stage_in(m, m->X, X, (size_t)B * kIn, flags);
     if (s != STP_OK) return s;
     if ((s = stage_in(m, m->T, T, (size_t)B * kTgt, flags)) != STP_OK) return s;
+    interval_start(m, 2);  // the training step's device work, inputs staged
     if ((s = forward_impl(m, B)) != STP_OK) return s;
     const int Bp = (B + kTileM - 1) / kTileM * kTileM;
-    k_loss<<<Bp / 128, 128, 0, m->stream>>>(m->y, m->T, B, Bp, m->bpart + (size_t)3 * bpart_stride(m->Bp_max),
-                                            m->dt[3], m->loss);
+    k_loss<<<Bp / kLossRows, kLossThreads, 0, m->stream>>>(
+        m->y, m->T, B, m->bpart + (size_t)3 * bpart_stride(m->Bp_max), m->dt[3], Bp, m->loss);
     MLP_CUDA(m, cudaGetLastError());
     return backward_impl(m, B, nw, nb);
 }
@@ -1261,6 +1448,7 @@ stp_status stp_mlp_gradients(stp_mlp* m, int B, const float* X, const float* T, 
     stp_status s = loss_grad(m, B, X, T, flags, &nw, &nb);
     if (s != STP_OK) return s;
     if ((s = adam_impl(m, nw, nb, 0.f, false, true)) != STP_OK) return s;
+    interval_stop(m, 2, 0.0, 0.0);
     if ((s = check_err(m)) != STP_OK) return s;
     if ((s = read_loss(m, B, loss)) != STP_OK) return s;
     if (grads) {
@@ -1288,6 +1476,7 @@ stp_status stp_mlp_train_step(stp_mlp* m, int B, const float* X, const float* T,
     stp_status s = loss_grad(m, B, X, T, flags, &nw, &nb);
     if (s != STP_OK) return s;
     if ((s = adam_impl(m, nw, nb, lr, true, false)) != STP_OK) return s;
+    interval_stop(m, 2, 0.0, 0.0);
     if ((s = check_err(m)) != STP_OK) return s;
     return read_loss(m, B, loss);
 }
@@ -1298,6 +1487,9 @@ stp_status stp_mlp_set_profiling(stp_mlp* m, int on) {
     m->gemm_ms = 0;
     m->gemm_flops = 0;
     m->gemm_bytes = 0;
+    m->step_ms = 0;
+    m->steps = 0;
+    for (bool& p : m->ev_pending) p = false;
     return STP_OK;
 }
 
@@ -1309,6 +1501,14 @@ stp_status stp_mlp_profile(stp_mlp* m, double* gemm_ms, double* gemm_flops, doub
     m->gemm_bytes = 0;
     m->gemm_ms = 0;
     m->gemm_flops = 0;
+    return STP_OK;
+}
+stp_status stp_mlp_profile_step(stp_mlp* m, double* step_ms, int* steps) {
+    if (!m) return fail(nullptr, STP_ERR_INVALID, "mlp is NULL");
+    if (step_ms) *step_ms = m->step_ms;
+    if (steps) *steps = m->steps;
+    m->step_ms = 0;
+    m->steps = 0;
     return STP_OK;
 }
 

@@ -152,6 +152,8 @@ def lib():
     L.stp_mlp_set_profiling.restype = C.c_int
     L.stp_mlp_profile.argtypes = [C.c_void_p, _D, _D, _D]
     L.stp_mlp_profile.restype = C.c_int
+    L.stp_mlp_profile_step.argtypes = [C.c_void_p, _D, C.POINTER(C.c_int)]
+    L.stp_mlp_profile_step.restype = C.c_int
     L.stp_mlp_last_error.argtypes = [C.c_void_p]
     L.stp_mlp_last_error.restype = C.c_char_p
     L.stp_problem_features.argtypes = [C.c_void_p, _F]
@@ -172,7 +174,7 @@ EXPORTED = ["stp_create_problem", "stp_plan", "stp_check_edges", "stp_free", "st
             "stp_check_edges_noalloc", "stp_batch_create", "stp_batch_plan", "stp_batch_path", "stp_batch_free",
             "stp_mlp_create", "stp_mlp_free", "stp_mlp_set_stream", "stp_mlp_set_params", "stp_mlp_get_params",
             "stp_mlp_forward", "stp_mlp_gradients", "stp_mlp_train_step", "stp_mlp_set_profiling",
-            "stp_mlp_profile", "stp_mlp_last_error", "stp_problem_features", "stp_set_proposal",
+            "stp_mlp_profile", "stp_mlp_profile_step", "stp_mlp_last_error", "stp_problem_features", "stp_set_proposal",
             "stp_problem_targets", "stp_selftest_bounded_wait", "stp_release_cached", "stp_set_trace", "stp_trace"]
 
 
@@ -596,6 +598,14 @@ class Mlp:
         ms, fl, by = C.c_double(), C.c_double(), C.c_double()
         lib().stp_mlp_profile(self.handle, C.byref(ms), C.byref(fl), C.byref(by))
         return ms.value, fl.value, by.value
+
+    def profile_step(self):
+        """(device ms of whole training steps, steps) since the last call."""
+        ms, n = C.c_double(), C.c_int()
+        s = lib().stp_mlp_profile_step(self.handle, C.byref(ms), C.byref(n))
+        if s != STP_OK:
+            raise StpError(s, "stp_mlp_profile_step")
+        return ms.value, n.value
 
     def close(self):
         if getattr(self, "handle", None):

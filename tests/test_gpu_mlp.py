@@ -205,3 +205,30 @@ def test_gradients_and_steps_are_reproducible(stp):
     assert not np.array_equal(p0, stp.flatten_params(P))
     for net in nets:
         net.close()
+
+
+def test_profiling_intervals(stp):
+    """With profiling on, every training step yields one whole-step interval
+    and the GEMM intervals inside it (forward chain, backward pass) take less
+    device time than the whole step; turning profiling off records nothing."""
+    rng = np.random.default_rng(5)
+    B = 4096
+    P = M.init_params(rng)
+    X = _inputs(rng, B)
+    T = _targets(rng, X)
+    net = stp.Mlp(B)
+    net.set_params(stp.flatten_params(P))
+    net.train_step(X, T, 1e-3)
+    assert net.profile_step() == (0.0, 0)
+    net.set_profiling(True)
+    for _ in range(3):
+        net.train_step(X, T, 1e-3)
+    gms, gfl, gby = net.profile()
+    sms, n = net.profile_step()
+    assert n == 3 and sms > 0 and 0 < gms < sms
+    assert gfl > 0 and gby > 0
+    assert net.profile_step() == (0.0, 0)     # read and cleared
+    net.set_profiling(False)
+    net.train_step(X, T, 1e-3)
+    assert net.profile_step() == (0.0, 0) and net.profile()[0] == 0.0
+    net.close()
