@@ -29,11 +29,14 @@ const double kInfD = std::numeric_limits<double>::infinity();
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Device resources kept for reuse across problems: memory blocks (by device
-// and size) and non-blocking streams (by device). Creating and freeing many
-// short-lived problems then costs no cudaMalloc/cudaFree (and none of the
-// device synchronisation of cudaFree). Blocks are handed out only when idle:
-// stp_free synchronises the problem's streams first. stp_release_cached()
-// returns everything to the driver.
+// and size), non-blocking streams (by device) and instantiated iteration
+// graphs (by device). Creating and freeing many short-lived problems then
+// costs no cudaMalloc/cudaFree (and none of the device synchronisation of
+// cudaFree), and a new problem's captured iteration graph updates an idle
+// executable graph of the same topology (cudaGraphExecUpdate: new kernel
+// parameters) instead of being instantiated. Resources are handed out only
+// when idle: stp_free synchronises the problem's streams first.
+// stp_release_cached() returns everything to the driver.
 struct DevCache {
     std::mutex mu;
     struct Block {
@@ -43,8 +46,10 @@ struct DevCache {
     std::multimap<size_t, Block> blocks;
     size_t cached = 0;
     std::vector<std::pair<int, cudaStream_t>> streams;
+    std::vector<std::pair<int, cudaGraphExec_t>> graphs;
 };
 constexpr size_t kCacheLimit = size_t(4) << 30;  // bytes of idle blocks kept
+constexpr size_t kGraphCache = 8;                // idle executable graphs kept
 
 DevCache& dev_cache() {
     // Never destroyed: no CUDA call may run during static destruction.
@@ -137,6 +142,49 @@ void cache_stream_release(cudaStream_t st) {
     DevCache& c = dev_cache();
     std::lock_guard<std::mutex> g(c.mu);
     c.streams.emplace_back(current_device(), st);
+}
+
+// An executable graph for the captured graph g: the most recently released
+// idle one of this device updated to g, else a new instantiation. An update
+// that fails (another topology) leaves nothing behind: that executable graph
+// is destroyed and the error state cleared.
+cudaError_t cache_graph_exec(cudaGraph_t g, cudaGraphExec_t* out) {
+    const int dev = current_device();
+    cudaGraphExec_t ex = nullptr;
+    {
+        DevCache& c = dev_cache();
+        std::lock_guard<std::mutex> lock(c.mu);
+        for (size_t i = c.graphs.size(); i-- > 0;) {
+            if (c.graphs[i].first != dev) continue;
+            ex = c.graphs[i].second;
+            c.graphs.erase(c.graphs.begin() + (long)i);
+            break;
+        }
+    }
+    if (ex) {
+        cudaGraphExecUpdateResultInfo info{};
+        if (cudaGraphExecUpdate(ex, g, &info) == cudaSuccess) {
+            *out = ex;
+            return cudaSuccess;
+        }
+        (void)cudaGetLastError();
+        cudaGraphExecDestroy(ex);
+    }
+    return cudaGraphInstantiate(out, g, 0);
+}
+
+// Keep an idle executable graph (its launches finished) for cache_graph_exec.
+void cache_graph_release(cudaGraphExec_t ex) {
+    if (!ex) return;
+    {
+        DevCache& c = dev_cache();
+        std::lock_guard<std::mutex> g(c.mu);
+        if (c.graphs.size() < kGraphCache) {
+            c.graphs.emplace_back(current_device(), ex);
+            return;
+        }
+    }
+    cudaGraphExecDestroy(ex);
 }
 
 // Carves aligned sub-buffers out of one device allocation.
@@ -636,12 +684,8 @@ stp_status create_impl(stp_problem* p) {
     p->start_free = hh[0] == 0;
     std::vector<unsigned char> gf(std::max(p->nk, 1), 0);
     for (int i = 0; i < p->nk; ++i) gf[i] = hh[i + 1] == 0 ? 1 : 0;
-    STP_CUDA(p, cudaMemcpy(gfree, gf.data(), gf.size(), cudaMemcpyHostToDevice));
-    // Configure the per-iteration launch shapes outside any capture.
-    EdgeBatch<R> E0 = E;
-    E0.n_host = 0;
-    STP_CUDA(p, launch_validate<R>(geom_of<R>(p), E0, false, true, 0, st));
-    STP_CUDA(p, cudaStreamSynchronize(st));
+    // Pageable source: the call returns once the bytes are staged.
+    STP_CUDA(p, cudaMemcpyAsync(gfree, gf.data(), gf.size(), cudaMemcpyHostToDevice, st));
     if (uses_persistent(p)) {
         // One team of every resident CTA (or persist_ctas of them).
         p->persist_dq = persist_dq(p->dof);
@@ -672,7 +716,9 @@ stp_status capture_graph(stp_problem* p) {
         p->graph_trace == state_of<R>(p).trace)
         return STP_OK;
     if (p->graph) {
-        cudaGraphExecDestroy(p->graph);
+        // Graphs holding this problem's profiling events are not kept.
+        if (have_prof) cudaGraphExecDestroy(p->graph);
+        else cache_graph_release(p->graph);
         p->graph = nullptr;
     }
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
@@ -690,7 +736,7 @@ stp_status capture_graph(stp_problem* p) {
     cudaError_t e2 = cudaStreamEndCapture(p->stream, &g);
     if (err != cudaSuccess) return cuda_fail(p, err, "capture(iteration)");
     if (e2 != cudaSuccess) return cuda_fail(p, e2, "cudaStreamEndCapture");
-    err = cudaGraphInstantiate(&p->graph, g, 0);
+    err = prof ? cudaGraphInstantiate(&p->graph, g, 0) : cache_graph_exec(g, &p->graph);
     cudaGraphDestroy(g);
     if (err != cudaSuccess) return cuda_fail(p, err, "cudaGraphInstantiate");
     p->graph_iters = G;
@@ -1174,6 +1220,11 @@ void stp_release_cached(void) {
         cudaStreamDestroy(ds.second);
     }
     c.streams.clear();
+    for (auto& dg : c.graphs) {
+        cudaSetDevice(dg.first);
+        cudaGraphExecDestroy(dg.second);
+    }
+    c.graphs.clear();
     cudaSetDevice(prev);
 }
 
@@ -1182,7 +1233,10 @@ void stp_free(stp_problem* p) {
     // Every buffer goes back to the cache idle: wait for the problem's streams.
     if (p->stream) cudaStreamSynchronize(p->stream);
     if (p->own_stream && p->own_stream != p->stream) cudaStreamSynchronize(p->own_stream);
-    if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->graph) {
+        if (p->prof_ev.empty()) cache_graph_release(p->graph);
+        else cudaGraphExecDestroy(p->graph);
+    }
     cache_release(p->d_arena, p->arena_block);
     cache_release(p->d_scratch, p->scratch_bytes);
     if (p->ev0) cudaEventDestroy(p->ev0);
