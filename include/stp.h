@@ -351,12 +351,15 @@ stp_status stp_batch_path(stp_batch *b, int i, double *path, int cap, int *n_pat
 void stp_batch_free(stp_batch *b);
 
 /* Release a problem. NULL is allowed. Waits for the problem's stream(s); its
- * device blocks and stream then go to a per-process cache (up to 4 GiB of idle
- * blocks) that later stp_create_problem calls reuse, so short-lived problems
- * cost no cudaMalloc/cudaFree. */
+ * device blocks, stream and executable iteration graph then go to a
+ * per-process cache (up to 4 GiB of idle blocks, 8 idle graphs) that later
+ * problems reuse, so short-lived problems cost no cudaMalloc/cudaFree, and a
+ * later problem whose iteration graph has the same topology updates an idle
+ * graph with its own kernel parameters instead of instantiating one. */
 void stp_free(stp_problem *p);
-/* Return every cached device block and stream to the driver (thread-safe; call
- * when no problem created before it is still in use by another thread). */
+/* Return every cached device block, stream and executable graph to the driver
+ * (thread-safe; call when no problem created before it is still in use by
+ * another thread). */
 void stp_release_cached(void);
 
 /* Use this CUDA stream (a cudaStream_t passed as void*) for every later call
