@@ -715,6 +715,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const float* __restrict__
     // Waypoints: element e = 4 m + p (waypoint e / 8, coordinate e % 8);
     // the coordinates in use are the arm's dof joints and the time.
     const float cnt = (float)(kWp * (dof + 1));
+    const float gscale = 2.f * invB / cnt;  // d(mse / cnt) / B per unit error
     float mse = 0.f;
     if (valid) {
 #pragma unroll
@@ -734,7 +735,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const float* __restrict__
             if (j < dof || j == kWpDim - 1) {
                 const float d = y[o] - t[1 + e];
                 mse += d * d;
-                g = 2.f * d / cnt * invB;
+                g = d * gscale;
             }
             y[o] = g;
         }
