@@ -459,7 +459,11 @@ __device__ __forceinline__ void validate_body(const Geom<R>& G, const EdgeBatch<
         }
     }
     // Without precomputed offsets every CTA scans the (small) count array
-    // into shared memory while the geometry copy is in flight.
+    // into shared memory while the geometry copy is in flight. Every CTA must
+    // derive the same offsets: the remaining-points pass (phase 2) skips the
+    // edges the coarse pass found hit (flag bit 0, written by the previous
+    // launch) and marks its own hits with 2, so flags set while other CTAs
+    // are still scanning never change a count.
     int* soff = reinterpret_cast<int*>(smem_raw + G.blob_bytes);
     if (!E.off) {
         const int per = (n + blockDim.x - 1) / blockDim.x;
@@ -467,16 +471,34 @@ __device__ __forceinline__ void validate_body(const Geom<R>& G, const EdgeBatch<
         auto eff = [&](int i) -> int {
             const int c = E.cnt[i];
             if (E.phase == 1) return (c + 7) >> 3;
-            if (E.phase == 2) return E.hit[i] ? 0 : c;
+            if (E.phase == 2) return (E.hit[i] & 1) ? 0 : c;
             return c;
         };
+        constexpr int kStage = 8;  // counts a thread keeps in registers
+        int cv[kStage];
         int sum = 0;
-        for (int i = i0; i < i1; ++i) sum += eff(i);
+        if (per <= kStage) {
+            // One round of independent loads.
+#pragma unroll
+            for (int k = 0; k < kStage; ++k) cv[k] = i0 + k < i1 ? eff(i0 + k) : 0;
+#pragma unroll
+            for (int k = 0; k < kStage; ++k) sum += cv[k];
+        } else {
+            for (int i = i0; i < i1; ++i) sum += eff(i);
+        }
         int tot;
         int pre = block_scan_excl(sum, scan_sh, &tot);
-        for (int i = i0; i < i1; ++i) {
-            soff[i] = pre;
-            pre += eff(i);
+        if (per <= kStage) {
+#pragma unroll
+            for (int k = 0; k < kStage; ++k) {
+                if (i0 + k < i1) soff[i0 + k] = pre;
+                pre += cv[k];
+            }
+        } else {
+            for (int i = i0; i < i1; ++i) {
+                soff[i] = pre;
+                pre += eff(i);
+            }
         }
         if (threadIdx.x == 0) soff[n] = tot;
         __syncthreads();
@@ -524,7 +546,7 @@ __device__ __forceinline__ void validate_body(const Geom<R>& G, const EdgeBatch<
         if (ARM) check_point<R, true, MO, CLEAR, EARLY>(G, sm, q, t, hit, clr, pairs);
         else check_point<R, false, MO, CLEAR, EARLY>(G, sm, q, t, hit, clr, pairs);
         if (ARM && G.n_self > 0 && (CLEAR || !hit)) self_check<R, CLEAR>(G, sm, q, hit, clr);
-        if (hit) E.hit[e] = 1;
+        if (hit) E.hit[e] = E.phase == 2 ? 2 : 1;
         if (CLEAR) atomic_min_r<R>(E.clear + e, clr);
         ++done;
         pairs_total += pairs;
