@@ -705,8 +705,9 @@ stp_status create_impl(stp_problem* p) {
 
 template <typename R>
 stp_status capture_graph(stp_problem* p) {
-    // Default 8: capture and instantiation grow with the graph while replays of
-    // small graphs cost the device almost nothing (UR5e, 32 iterations: one
+    // Default 8: capture and instantiation (or the update of a cached graph)
+    // grow with the graph while replays of small graphs cost the device almost
+    // nothing (UR5e, 32 iterations, before graphs were cached: one
     // create-plan-free 2.80 ms with 8 against 3.25 ms with 32; plan 2.27 ms
     // against 2.26 ms).
     const int G = p->prm.iters_per_graph > 0 ? p->prm.iters_per_graph : 8;
@@ -734,7 +735,10 @@ stp_status capture_graph(stp_problem* p) {
         err = launch_iteration<R>(geom_of<R>(p), state_of<R>(p), 0, p->stream,
                                   prof ? &p->prof_ev[(size_t)i * (kIterKernels + 1)] : nullptr);
     cudaError_t e2 = cudaStreamEndCapture(p->stream, &g);
-    if (err != cudaSuccess) return cuda_fail(p, err, "capture(iteration)");
+    if (err != cudaSuccess) {
+        if (e2 == cudaSuccess) cudaGraphDestroy(g);
+        return cuda_fail(p, err, "capture(iteration)");
+    }
     if (e2 != cudaSuccess) return cuda_fail(p, e2, "cudaStreamEndCapture");
     err = prof ? cudaGraphInstantiate(&p->graph, g, 0) : cache_graph_exec(g, &p->graph);
     cudaGraphDestroy(g);
@@ -1781,10 +1785,8 @@ extern "C" stp_status stp_batch_create(stp_problem* const* problems, int n, cons
             le = launch_iteration_batch<float>(b->d_geom, b->d_state, sh, b->stream);
         cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
         if (e == cudaSuccess) e = le != cudaSuccess ? le : ee;
-        if (e == cudaSuccess) {
-            e = cudaGraphInstantiate(&b->graph, g, 0);
-            cudaGraphDestroy(g);
-        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+        if (ee == cudaSuccess) cudaGraphDestroy(g);
     }
     if (e != cudaSuccess) {
         char buf[256];
