@@ -53,9 +53,9 @@ constexpr int kMix = 8, kWp = 16, kWpDim = 8, kTgt = 130;
 // K stages through a four-stage pipeline, one CTA per SM.
 constexpr int kTileM = 128, kStageK = 64, kThreads = 256, kWStages = 4;
 constexpr float kSMin = -7.f, kSMax = 2.f;
-// Bias gradients: every 32 batch rows (a warp of an input-gradient epilogue
-// or of the loss kernel) write the column sums of their rows as one partial
-// [256]; Adam adds the partials in a fixed order.
+// Bias gradients: every 32 batch rows (a warp of an input-gradient epilogue,
+// or a CTA of the loss kernel) write the column sums of their rows as one
+// partial [256]; Adam adds the partials in a fixed order.
 
 enum Mode { kHidden = 0, kOutput = 1, kBackward = 2, kWGrad = 3 };
 
@@ -944,7 +944,7 @@ struct stp_mlp {
     __nv_bfloat16* dt[4]{};  // gradient wrt layer outputs (dt[3] = dY)
     float* y = nullptr;       // [Bp][256]
     float* wpart = nullptr;   // weight-gradient partials
-    float* bpart = nullptr;   // bias-gradient partials [4][Bp/128][256]
+    float* bpart = nullptr;   // bias-gradient partials [4][Bp/32][256]
     float* gsum = nullptr;    // summed gradients (gradients API)
     float* loss = nullptr;    // [Bp]
     float* X = nullptr;       // staged inputs [max_batch][32]
